@@ -1,0 +1,199 @@
+/*
+ * mfns.h -- C ABI of the GB300 matrix-free Stokes / stabilised Navier--Stokes
+ * multigrid library (libmfns.so).
+ *
+ * The operations follow the problem statement of the paper "Solving the
+ * (Navier--)Stokes equations with space and time adaptivity using deal.II":
+ *   - Eq. 1 (stationary Stokes) with Taylor--Hood Q_k / Q_{k-1} elements and the
+ *     block system of Eq. 5 ([[A, B], [B^T, 0]]: continuity row -(div u, q));
+ *   - the A block alone (vector Laplacian nu (grad u, grad v), Eq. 5);
+ *   - Eq. 3 with the SUPG/PSPG terms of Section 5, BDF2 in time, linearised by
+ *     Newton's method at a frozen state (equal-order Q_k Q_k);
+ *   - matrix-free evaluation (Section 1), global-coarsening h- and
+ *     p-multigrid with hanging-node constraints resolved in smoother and
+ *     transfer (Section 2, Eq. 4), Chebyshev/Jacobi smoothing around point
+ *     Jacobi (Sections 3 and 5), one V-cycle as preconditioner inside FGMRES
+ *     (Section 3) and the block-triangular preconditioner of Eq. 5.
+ *
+ * Conventions (all entry points):
+ *   - Every call returns an int status: MFNS_OK (0) or a negative error code.
+ *     mfns_last_error() returns a thread-local message for the last failure.
+ *     No C++ exception crosses this boundary.
+ *   - Vectors passed as `const void*` / `void*` are DEVICE pointers owned by
+ *     the caller (for example the data pointers of torch tensors), laid out as
+ *     described in mfns_problem_info and aligned to 16 bytes.  They are read
+ *     and written asynchronously on `stream` (a cudaStream_t, NULL = the
+ *     legacy default stream); the caller synchronises.  src and dst must not
+ *     alias.  Host pointers are only used where the name says so (`_host`).
+ *   - Precision: MFNS_FP64 vectors hold double, MFNS_FP32 vectors hold float.
+ *   - The library owns meshes, hierarchies, diagonals, frozen states and
+ *     workspaces; they are allocated against the context's HBM budget at
+ *     create time (MFNS_ERR_BUDGET when it would be exceeded), so vmult,
+ *     smooth, vcycle and solve allocate nothing.
+ *   - One problem is used by one stream at a time (not thread-safe per
+ *     problem); distinct problems may run concurrently on distinct streams.
+ *
+ * Vector layout of a problem's system operator (MFNS_OP_SYSTEM):
+ *   STAB_NS:  node-interleaved [u_x, u_y, (u_z), p] per Q_k node.
+ *   STOKES:   node-interleaved velocity [u_x, u_y, (u_z)] per Q_k node, then
+ *             one pressure entry per Q_{k-1} node (offset = n_velocity_dofs).
+ *   STOKES_A: node-interleaved velocity only.   PMASS: one entry per node.
+ *   Node numbering is the library's own; mfns_dof_support_points exports the
+ *   coordinates and field of every entry.  Constrained entries (Dirichlet
+ *   velocity on the boundary, hanging nodes) are identity rows of every
+ *   operator: vmult returns dst_i = src_i there and ignores them elsewhere.
+ */
+#ifndef MFNS_H
+#define MFNS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define MFNS_OK 0
+#define MFNS_ERR_ARG (-1)            /* invalid argument (null pointer, bad level, misaligned vector) */
+#define MFNS_ERR_OOM (-2)            /* cudaMalloc failed */
+#define MFNS_ERR_BUDGET (-3)         /* the context's HBM budget would be exceeded */
+#define MFNS_ERR_UNSUPPORTED (-4)    /* (dim, degree, kind) not built */
+#define MFNS_ERR_CUDA (-5)           /* a CUDA runtime call failed */
+#define MFNS_ERR_TIMEOUT (-6)        /* a bounded device-side wait gave up */
+#define MFNS_ERR_NOT_CONVERGED (-7)  /* solve hit maxit; the iterate is still written */
+
+/* problem kinds */
+#define MFNS_STOKES 0   /* Taylor--Hood Q_k/Q_{k-1}, Eq. 1 / Eq. 5 */
+#define MFNS_STOKES_A 1 /* vector Laplacian (A block of Eq. 5) */
+#define MFNS_STAB_NS 2  /* linearised SUPG/PSPG BDF2 Navier--Stokes, Q_k Q_k (Section 5) */
+#define MFNS_PMASS 3    /* pressure mass matrix on Q_k */
+
+/* precisions */
+#define MFNS_FP64 0
+#define MFNS_FP32 1
+
+/* operator selectors for mfns_vmult / mfns_diagonal (levels are >= 0) */
+#define MFNS_OP_SYSTEM (-1) /* the problem's own operator on the finest mesh */
+#define MFNS_OP_PMASS (-2)  /* STOKES only: pressure mass matrix (Schur approximation) */
+
+/* stabilised-NS term flags (Section 5); default MFNS_TERMS_ALL */
+#define MFNS_TERM_MASS 1         /* BDF2 mass 3/(2 dt) (du, v) and its part of the residual */
+#define MFNS_TERM_CONV 2         /* ub . grad du */
+#define MFNS_TERM_NEWTON 4       /* du . grad ub */
+#define MFNS_TERM_SUPG 8         /* tau (Rlin, ub . grad v) */
+#define MFNS_TERM_SUPG_NEWTON 16 /* tau (Rbar, du . grad v) */
+#define MFNS_TERM_PSPG 32        /* tau (Rlin, grad q) */
+#define MFNS_TERM_STRONG_VISC 64 /* -nu lap du inside Rlin */
+#define MFNS_TERMS_ALL 127
+
+typedef struct mfns_ctx mfns_ctx;
+typedef struct mfns_mesh mfns_mesh;
+typedef struct mfns_problem mfns_problem;
+
+typedef struct {
+  int kind;             /* MFNS_STOKES, MFNS_STOKES_A, MFNS_STAB_NS, MFNS_PMASS */
+  int degree;           /* velocity degree k (STOKES: k >= 2, pressure k-1; PMASS: its own degree) */
+  double nu;            /* viscosity */
+  double dt;            /* time step of BDF2 (STAB_NS); <= 0 means stationary (no mass term) */
+  int terms;            /* STAB_NS term flags; 0 is taken as MFNS_TERMS_ALL */
+  double div_sign;      /* sign of the continuity row; 0 = default (STOKES -1, STAB_NS +1) */
+  int smoother;         /* 0 = Chebyshev around point Jacobi, 1 = Jacobi relaxation */
+  int smoother_degree;  /* Chebyshev degree / relaxation sweeps; 0 = default (5) */
+  int mg_order;         /* 0 default (STOKES_A: p then h; STAB_NS: h then p), 1 p_then_h, 2 h_then_p */
+  int mg_precision;     /* MFNS_FP64 or MFNS_FP32: precision of the multigrid preconditioner */
+  int coarse_stop_n;    /* uniform h-coarsening stops when n is odd or n <= this; 0 = 2 */
+  int fgmres_restart;   /* 0 = 30 */
+  double tol;           /* relative residual tolerance of mfns_solve; 0 = 1e-8 */
+  int maxit;            /* 0 = 500 */
+  int cg_iterations;    /* STOKES: Jacobi-CG steps for the Schur complement; 0 = 10 */
+  double lambda_max;    /* > 0: use this lambda_max of D^-1 A on every level instead of the estimate */
+} mfns_problem_desc;
+
+typedef struct {
+  int dim, degree, kind;
+  int n_levels;                 /* multigrid levels, 0 = finest */
+  int64_t n_dofs;               /* system vector length */
+  int64_t n_velocity_dofs;      /* STOKES: start of the pressure block */
+  int64_t n_cells;
+  int n_colors;                 /* colours of the finest level */
+  int64_t level_dofs[32];       /* vector length per multigrid level */
+  int level_degree[32];
+  int64_t level_cells[32];
+  double lambda_max[32];        /* smoother bound per level (estimate x 1.2, or the override) */
+  size_t device_bytes;          /* HBM held by this problem */
+} mfns_info;
+
+typedef struct {
+  int iterations;
+  double rel_residual;          /* ||b - A x|| / ||b||, true residual in FP64 */
+  double seconds;
+  int converged;
+} mfns_solve_info;
+
+/* ---- context --------------------------------------------------------------------------- */
+/* device: CUDA ordinal; hbm_budget_bytes: 0 = unlimited.  Errors: ARG, CUDA. */
+int mfns_ctx_create(int device, size_t hbm_budget_bytes, mfns_ctx** out);
+int mfns_ctx_destroy(mfns_ctx* ctx);
+/* bytes currently charged to the context */
+int mfns_ctx_memory(const mfns_ctx* ctx, size_t* used, size_t* peak);
+const char* mfns_last_error(void);
+
+/* ---- meshes (host objects) -------------------------------------------------------------- */
+/* Unit square (dim 2) or cube (dim 3) with n cells per direction. */
+int mfns_mesh_uniform(mfns_ctx* ctx, int dim, int n, mfns_mesh** out);
+/* Refine cells with centre strictly inside the ball, `levels` times (level by level),
+ * then 2:1 closure over faces, edges and vertices.  centre[2] is ignored in 2D. */
+int mfns_mesh_refine_ball(mfns_mesh* mesh, const double centre[3], double radius, int levels);
+int mfns_mesh_info(const mfns_mesh* mesh, int64_t* n_cells, int* max_level);
+int mfns_mesh_destroy(mfns_mesh* mesh);
+
+/* ---- problems ------------------------------------------------------------------------------ */
+/* Builds the operator, its global-coarsening hierarchy, diagonals, smoother bounds,
+ * the dense coarse inverse and all workspaces.  The mesh may be destroyed afterwards. */
+int mfns_problem_create(mfns_ctx* ctx, const mfns_mesh* mesh, const mfns_problem_desc* desc,
+                        mfns_problem** out);
+int mfns_problem_info(const mfns_problem* p, mfns_info* out);
+/* Support point (xyz_host[3*i..], z = 0 in 2D) and field (0..dim-1 velocity component,
+ * dim pressure) of every entry of the vector of `which` (MFNS_OP_SYSTEM, MFNS_OP_PMASS
+ * or a level).  Host arrays of length n (n = that vector's length). */
+int mfns_dof_support_points(const mfns_problem* p, int which, double* xyz_host, int* field_host);
+/* Constrained entries (identity rows) of `which`: writes up to cap indices, returns count in *n. */
+int mfns_constrained_dofs(const mfns_problem* p, int which, int64_t* idx_host, int64_t cap, int64_t* n);
+/* Replace the smoother bound of one level (parity tests pass the bound explicitly). */
+int mfns_set_lambda_max(mfns_problem* p, int level, double lambda_max);
+int mfns_problem_destroy(mfns_problem* p);
+
+/* ---- operators ----------------------------------------------------------------------------- */
+/* dst = A src (matrix-free, Section 1 / Eq. 4 per cell); constrained rows dst_i = src_i. */
+int mfns_vmult(mfns_problem* p, int which, int precision, const void* src, void* dst, void* stream);
+/* diag = diag(A) (exact, per-cell unit-vector evaluation; 1 on constrained rows). */
+int mfns_diagonal(mfns_problem* p, int which, int precision, void* diag, void* stream);
+/* Hanging entries of x from their masters (x_h = sum_j w_hj x_j), Dirichlet entries kept. */
+int mfns_apply_constraints(mfns_problem* p, int which, int precision, void* x, void* stream);
+
+/* ---- multigrid ----------------------------------------------------------------------------- */
+/* One smoothing step on level `level`: Chebyshev of the problem's degree (or the Jacobi
+ * relaxation) around point Jacobi, starting from x (x_is_zero = 1 skips the first product). */
+int mfns_smooth(mfns_problem* p, int level, int precision, const void* b, void* x, int x_is_zero,
+                void* stream);
+/* Transfers between level `level` (fine) and level+1 (coarse), Eq. 4:
+ * fine += P coarse;  coarse = P^T fine. */
+int mfns_prolongate_add(mfns_problem* p, int level, int precision, const void* coarse, void* fine,
+                        void* stream);
+int mfns_restrict(mfns_problem* p, int level, int precision, const void* fine, void* coarse, void* stream);
+/* x = V-cycle(b) on the multigrid hierarchy (zero initial guess). */
+int mfns_vcycle(mfns_problem* p, int precision, const void* b, void* x, void* stream);
+
+/* ---- solve ---------------------------------------------------------------------------------- */
+/* FGMRES(m) in FP64 on the system operator, preconditioned by one V-cycle (STAB_NS, STOKES_A)
+ * or the block-triangular preconditioner of Eq. 5 (STOKES), with the multigrid in
+ * desc.mg_precision.  b and x are FP64 device vectors; x is overwritten (zero start).
+ * The pressure l2 mean of b and of every preconditioned vector is removed when the
+ * pressure is only fixed up to a constant.  Returns MFNS_ERR_NOT_CONVERGED when maxit is hit. */
+int mfns_solve(mfns_problem* p, const void* b, void* x, mfns_solve_info* info, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MFNS_H */

@@ -1,0 +1,190 @@
+"""Thin Python layer over the C ABI (names follow include/mfns.h).
+
+Torch tensors supply device memory and streams; every step of the path runs
+in libmfns.so.  There is no CPU fallback: without the built library or a GPU
+these calls raise.
+"""
+import ctypes as C
+
+import numpy as np
+import torch
+
+from . import _lib as L
+
+
+def _ptr(t):
+    if not t.is_cuda:
+        raise ValueError("vectors must be CUDA tensors")
+    if not t.is_contiguous():
+        raise ValueError("vectors must be contiguous")
+    return C.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    s = torch.cuda.current_stream() if stream is None else stream
+    return C.c_void_p(s.cuda_stream)
+
+
+def _dtype(prec):
+    return torch.float64 if prec == L.FP64 else torch.float32
+
+
+class Context:
+    def __init__(self, device=0, hbm_budget_bytes=0):
+        self.lib = L.load()
+        h = C.c_void_p()
+        L.check(self.lib.mfns_ctx_create(device, hbm_budget_bytes, C.byref(h)))
+        self.h = h
+        self.device = device
+
+    def memory(self):
+        u, p = C.c_size_t(), C.c_size_t()
+        L.check(self.lib.mfns_ctx_memory(self.h, C.byref(u), C.byref(p)))
+        return u.value, p.value
+
+    def close(self):
+        if self.h:
+            self.lib.mfns_ctx_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Mesh:
+    def __init__(self, ctx, dim, n):
+        self.lib = ctx.lib
+        h = C.c_void_p()
+        L.check(self.lib.mfns_mesh_uniform(ctx.h, dim, n, C.byref(h)))
+        self.h = h
+        self.dim, self.n = dim, n
+
+    def refine_ball(self, centre, radius, levels):
+        c = (C.c_double * 3)(*[float(v) for v in (list(centre) + [0.0, 0.0, 0.0])[:3]])
+        L.check(self.lib.mfns_mesh_refine_ball(self.h, c, float(radius), int(levels)))
+        return self
+
+    def info(self):
+        n, l = C.c_int64(), C.c_int()
+        L.check(self.lib.mfns_mesh_info(self.h, C.byref(n), C.byref(l)))
+        return n.value, l.value
+
+    def close(self):
+        if self.h:
+            self.lib.mfns_mesh_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def make_desc(kind, degree, nu=1.0, dt=0.0, terms=0, div_sign=0.0, smoother=0, smoother_degree=0,
+              mg_order=0, mg_precision=L.FP64, coarse_stop_n=0, fgmres_restart=0, tol=0.0, maxit=0,
+              cg_iterations=0, lambda_max=0.0):
+    return L.ProblemDesc(kind, degree, nu, dt, terms, div_sign, smoother, smoother_degree, mg_order,
+                         mg_precision, coarse_stop_n, fgmres_restart, tol, maxit, cg_iterations, lambda_max)
+
+
+class Problem:
+    def __init__(self, ctx, mesh, **desc):
+        self.ctx = ctx
+        self.lib = ctx.lib
+        self.desc = make_desc(**desc)
+        h = C.c_void_p()
+        L.check(self.lib.mfns_problem_create(ctx.h, mesh.h, C.byref(self.desc), C.byref(h)))
+        self.h = h
+        self.info = self.get_info()
+
+    def get_info(self):
+        inf = L.Info()
+        L.check(self.lib.mfns_problem_info(self.h, C.byref(inf)))
+        return inf
+
+    def n_dofs(self, which=L.OP_SYSTEM):
+        if which == L.OP_SYSTEM:
+            return self.info.n_dofs
+        if which == L.OP_PMASS:
+            return self.info.n_dofs - self.info.n_velocity_dofs
+        return self.info.level_dofs[which]
+
+    def support_points(self, which=L.OP_SYSTEM):
+        n = self.n_dofs(which)
+        xyz = np.zeros((n, 3))
+        field = np.zeros(n, dtype=np.int32)
+        L.check(self.lib.mfns_dof_support_points(self.h, which, xyz.ctypes.data_as(C.c_void_p),
+                                                 field.ctypes.data_as(C.c_void_p)))
+        return xyz[:, : self.info.dim], field
+
+    def constrained(self, which=L.OP_SYSTEM):
+        n = C.c_int64()
+        L.check(self.lib.mfns_constrained_dofs(self.h, which, None, 0, C.byref(n)))
+        idx = np.zeros(n.value, dtype=np.int64)
+        L.check(self.lib.mfns_constrained_dofs(self.h, which, idx.ctypes.data_as(C.c_void_p), n.value,
+                                               C.byref(n)))
+        return idx
+
+    def set_lambda_max(self, level, lmax):
+        L.check(self.lib.mfns_set_lambda_max(self.h, level, float(lmax)))
+        self.info = self.get_info()
+
+    def vector(self, which=L.OP_SYSTEM, prec=L.FP64, device="cuda"):
+        return torch.zeros(self.n_dofs(which), dtype=_dtype(prec), device=device)
+
+    def vmult(self, src, dst, which=L.OP_SYSTEM, prec=None, stream=None):
+        prec = (L.FP64 if src.dtype == torch.float64 else L.FP32) if prec is None else prec
+        L.check(self.lib.mfns_vmult(self.h, which, prec, _ptr(src), _ptr(dst), _stream(stream)))
+        return dst
+
+    def diagonal(self, diag, which=L.OP_SYSTEM, stream=None):
+        prec = L.FP64 if diag.dtype == torch.float64 else L.FP32
+        L.check(self.lib.mfns_diagonal(self.h, which, prec, _ptr(diag), _stream(stream)))
+        return diag
+
+    def apply_constraints(self, x, which=L.OP_SYSTEM, stream=None):
+        prec = L.FP64 if x.dtype == torch.float64 else L.FP32
+        L.check(self.lib.mfns_apply_constraints(self.h, which, prec, _ptr(x), _stream(stream)))
+        return x
+
+    def smooth(self, level, b, x, x_is_zero=False, stream=None):
+        prec = L.FP64 if b.dtype == torch.float64 else L.FP32
+        L.check(self.lib.mfns_smooth(self.h, level, prec, _ptr(b), _ptr(x), int(bool(x_is_zero)), _stream(stream)))
+        return x
+
+    def prolongate_add(self, level, coarse, fine, stream=None):
+        prec = L.FP64 if coarse.dtype == torch.float64 else L.FP32
+        L.check(self.lib.mfns_prolongate_add(self.h, level, prec, _ptr(coarse), _ptr(fine), _stream(stream)))
+        return fine
+
+    def restrict(self, level, fine, coarse, stream=None):
+        prec = L.FP64 if fine.dtype == torch.float64 else L.FP32
+        L.check(self.lib.mfns_restrict(self.h, level, prec, _ptr(fine), _ptr(coarse), _stream(stream)))
+        return coarse
+
+    def vcycle(self, b, x, stream=None):
+        prec = L.FP64 if b.dtype == torch.float64 else L.FP32
+        L.check(self.lib.mfns_vcycle(self.h, prec, _ptr(b), _ptr(x), _stream(stream)))
+        return x
+
+    def solve(self, b, x, stream=None, raise_on_nonconvergence=True):
+        si = L.SolveInfo()
+        code = self.lib.mfns_solve(self.h, _ptr(b), _ptr(x), C.byref(si), _stream(stream))
+        if code != L.OK and (code != L.ERR_NOT_CONVERGED or raise_on_nonconvergence):
+            L.check(code)
+        return si
+
+    def close(self):
+        if self.h:
+            self.lib.mfns_problem_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

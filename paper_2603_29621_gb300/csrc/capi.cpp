@@ -1,0 +1,308 @@
+// C ABI (include/mfns.h): argument checking, error translation, dispatch.
+#include "../../include/mfns.h"
+
+#include <chrono>
+#include <cstring>
+#include <string>
+
+#include "problem.hpp"
+#include "vec.hpp"
+
+namespace mfns {
+bool op_supported(int dim, int k, int op);
+}
+using namespace mfns;
+static bool op_supported_kind(int dim, int kind, int k);
+
+struct mfns_ctx {
+  int device = 0;
+  Budget budget;
+};
+struct mfns_mesh {
+  mfns_ctx* ctx = nullptr;
+  Forest forest;
+};
+struct mfns_problem {
+  mfns_ctx* ctx = nullptr;
+  std::unique_ptr<Problem> p;
+};
+
+static thread_local std::string g_err;
+
+static int fail(int code, const std::string& msg) {
+  g_err = msg;
+  return code;
+}
+
+#define API_BEGIN try {
+#define API_END                                                      \
+  }                                                                  \
+  catch (const Error& e) { return fail(e.code, e.what()); }          \
+  catch (const std::bad_alloc&) { return fail(kErrOom, "host allocation failed"); } \
+  catch (const std::exception& e) { return fail(kErrArg, e.what()); } \
+  return MFNS_OK;
+
+static cudaStream_t S(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+static bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+extern "C" {
+
+const char* mfns_last_error(void) { return g_err.c_str(); }
+
+int mfns_ctx_create(int device, size_t hbm_budget_bytes, mfns_ctx** out) {
+  API_BEGIN
+  if (!out) return fail(MFNS_ERR_ARG, "out is null");
+  int n = 0;
+  MFNS_CUDA(cudaGetDeviceCount(&n));
+  if (device < 0 || device >= n) return fail(MFNS_ERR_ARG, "invalid device");
+  MFNS_CUDA(cudaSetDevice(device));
+  auto* c = new mfns_ctx;
+  c->device = device;
+  c->budget.limit = hbm_budget_bytes;
+  *out = c;
+  API_END
+}
+
+int mfns_ctx_destroy(mfns_ctx* ctx) {
+  delete ctx;
+  return MFNS_OK;
+}
+
+int mfns_ctx_memory(const mfns_ctx* ctx, size_t* used, size_t* peak) {
+  if (!ctx) return fail(MFNS_ERR_ARG, "ctx is null");
+  if (used) *used = ctx->budget.used;
+  if (peak) *peak = ctx->budget.peak;
+  return MFNS_OK;
+}
+
+int mfns_mesh_uniform(mfns_ctx* ctx, int dim, int n, mfns_mesh** out) {
+  API_BEGIN
+  if (!ctx || !out) return fail(MFNS_ERR_ARG, "null argument");
+  if ((dim != 2 && dim != 3) || n < 1 || n > 1024) return fail(MFNS_ERR_ARG, "dim must be 2 or 3, 1 <= n <= 1024");
+  auto* m = new mfns_mesh;
+  m->ctx = ctx;
+  m->forest = forest_uniform(dim, n);
+  *out = m;
+  API_END
+}
+
+int mfns_mesh_refine_ball(mfns_mesh* mesh, const double centre[3], double radius, int levels) {
+  API_BEGIN
+  if (!mesh || !centre || levels < 0 || levels > 6 || !(radius > 0)) return fail(MFNS_ERR_ARG, "bad refinement");
+  mesh->forest = forest_refine_ball(mesh->forest, centre, radius, levels);
+  API_END
+}
+
+int mfns_mesh_info(const mfns_mesh* mesh, int64_t* n_cells, int* max_level) {
+  if (!mesh) return fail(MFNS_ERR_ARG, "mesh is null");
+  if (n_cells) *n_cells = (int64_t)mesh->forest.n_cells();
+  if (max_level) *max_level = mesh->forest.max_level();
+  return MFNS_OK;
+}
+
+int mfns_mesh_destroy(mfns_mesh* mesh) {
+  delete mesh;
+  return MFNS_OK;
+}
+
+int mfns_problem_create(mfns_ctx* ctx, const mfns_mesh* mesh, const mfns_problem_desc* desc, mfns_problem** out) {
+  API_BEGIN
+  if (!ctx || !mesh || !desc || !out) return fail(MFNS_ERR_ARG, "null argument");
+  if (desc->kind < 0 || desc->kind > 3) return fail(MFNS_ERR_ARG, "unknown kind");
+  if (!(desc->nu > 0)) return fail(MFNS_ERR_ARG, "nu must be positive");
+  if (desc->mg_precision != MFNS_FP64 && desc->mg_precision != MFNS_FP32) return fail(MFNS_ERR_ARG, "bad precision");
+  const int dim = mesh->forest.dim, k = desc->degree;
+  if (!op_supported_kind(dim, desc->kind, k)) return fail(MFNS_ERR_UNSUPPORTED, "unsupported (dim, kind, degree)");
+  MFNS_CUDA(cudaSetDevice(ctx->device));
+  Physics ph;
+  ph.nu = desc->nu;
+  ph.dt = desc->dt > 0 ? desc->dt : 0.0;
+  ph.terms = desc->terms == 0 ? MFNS_TERMS_ALL : desc->terms;
+  ph.div_sign = desc->div_sign != 0 ? desc->div_sign : (desc->kind == MFNS_STAB_NS ? 1.0 : -1.0);
+  const size_t used0 = ctx->budget.used;
+  std::unique_ptr<Problem> p = build_problem(mesh->forest, desc->kind, k, ph, desc->mg_order,
+                                             desc->coarse_stop_n > 0 ? desc->coarse_stop_n : 2, &ctx->budget);
+  p->smoother = desc->smoother;
+  p->smoother_degree = desc->smoother_degree > 0 ? desc->smoother_degree : 5;
+  p->mg_precision = desc->mg_precision;
+  p->restart = desc->fgmres_restart > 0 ? desc->fgmres_restart : 30;
+  if (p->restart >= kMaxDots) return fail(MFNS_ERR_ARG, "fgmres_restart must be < 32");
+  p->tol = desc->tol > 0 ? desc->tol : 1e-8;
+  p->maxit = desc->maxit > 0 ? desc->maxit : 500;
+  p->cg_iterations = desc->cg_iterations > 0 ? desc->cg_iterations : 10;
+  if (desc->lambda_max > 0)
+    for (auto& lv : p->levels) lv->lmax = desc->lambda_max;
+  alloc_workspaces(*p);
+  cudaStream_t s = 0;
+  estimate_lambda(*p, s);
+  setup_coarse(*p, s);
+  MFNS_CUDA(cudaStreamSynchronize(s));
+  p->bytes = ctx->budget.used - used0;
+  auto* w = new mfns_problem;
+  w->ctx = ctx;
+  w->p = std::move(p);
+  *out = w;
+  API_END
+}
+
+int mfns_problem_destroy(mfns_problem* p) {
+  if (p && p->ctx) cudaSetDevice(p->ctx->device);
+  delete p;
+  return MFNS_OK;
+}
+
+static OpLevel* select_op(mfns_problem* p, int which) {
+  Problem& P = *p->p;
+  if (which == MFNS_OP_SYSTEM) return P.system ? P.system.get() : P.levels[0].get();
+  if (which == MFNS_OP_PMASS) return P.pmass ? P.pmass.get() : nullptr;
+  if (which >= 0 && which < (int)P.levels.size()) return P.levels[which].get();
+  return nullptr;
+}
+
+int mfns_problem_info(const mfns_problem* pc, mfns_info* out) {
+  if (!pc || !out) return fail(MFNS_ERR_ARG, "null argument");
+  mfns_problem* p = const_cast<mfns_problem*>(pc);
+  Problem& P = *p->p;
+  std::memset(out, 0, sizeof(*out));
+  OpLevel& S = *select_op(p, MFNS_OP_SYSTEM);
+  out->dim = P.dim;
+  out->degree = P.k;
+  out->kind = P.kind;
+  out->n_levels = (int)P.levels.size();
+  out->n_dofs = S.n_dofs;
+  out->n_velocity_dofs = S.n_main_dofs;
+  out->n_cells = (int64_t)S.forest.n_cells();
+  out->n_colors = S.L.n_colors;
+  for (size_t l = 0; l < P.levels.size() && l < 32; ++l) {
+    out->level_dofs[l] = P.levels[l]->n_dofs;
+    out->level_degree[l] = P.levels[l]->k;
+    out->level_cells[l] = (int64_t)P.levels[l]->forest.n_cells();
+    out->lambda_max[l] = P.levels[l]->lmax;
+  }
+  out->device_bytes = P.bytes;
+  return MFNS_OK;
+}
+
+int mfns_dof_support_points(const mfns_problem* pc, int which, double* xyz, int* field) {
+  API_BEGIN
+  OpLevel* lv = pc ? select_op(const_cast<mfns_problem*>(pc), which) : nullptr;
+  if (!lv || !xyz || !field) return fail(MFNS_ERR_ARG, "bad operator selector or null output");
+  oplevel_support(*lv, xyz, field);
+  API_END
+}
+
+int mfns_constrained_dofs(const mfns_problem* pc, int which, int64_t* idx, int64_t cap, int64_t* n) {
+  API_BEGIN
+  OpLevel* lv = pc ? select_op(const_cast<mfns_problem*>(pc), which) : nullptr;
+  if (!lv || !n) return fail(MFNS_ERR_ARG, "bad operator selector");
+  *n = (int64_t)lv->constrained_host.size();
+  if (idx)
+    for (int64_t i = 0; i < *n && i < cap; ++i) idx[i] = lv->constrained_host[i];
+  API_END
+}
+
+int mfns_set_lambda_max(mfns_problem* p, int level, double lmax) {
+  if (!p || level < 0 || level >= (int)p->p->levels.size() || !(lmax > 0)) return fail(MFNS_ERR_ARG, "bad level");
+  p->p->levels[level]->lmax = lmax;
+  return MFNS_OK;
+}
+
+int mfns_vmult(mfns_problem* p, int which, int prec, const void* src, void* dst, void* stream) {
+  API_BEGIN
+  OpLevel* lv = p ? select_op(p, which) : nullptr;
+  if (!lv || !src || !dst || src == dst) return fail(MFNS_ERR_ARG, "bad arguments");
+  if (prec != 0 && prec != 1) return fail(MFNS_ERR_ARG, "bad precision");
+  if (!aligned16(src) || !aligned16(dst)) return fail(MFNS_ERR_ARG, "vectors must be 16-byte aligned");
+  MFNS_CUDA(cudaSetDevice(p->ctx->device));
+  oplevel_vmult(*lv, prec, src, dst, S(stream));
+  API_END
+}
+
+int mfns_diagonal(mfns_problem* p, int which, int prec, void* diag, void* stream) {
+  API_BEGIN
+  OpLevel* lv = p ? select_op(p, which) : nullptr;
+  if (!lv || !diag || (prec != 0 && prec != 1)) return fail(MFNS_ERR_ARG, "bad arguments");
+  MFNS_CUDA(cudaSetDevice(p->ctx->device));
+  oplevel_diag(*lv, prec, diag, S(stream));
+  API_END
+}
+
+int mfns_apply_constraints(mfns_problem* p, int which, int prec, void* x, void* stream) {
+  API_BEGIN
+  OpLevel* lv = p ? select_op(p, which) : nullptr;
+  if (!lv || !x || (prec != 0 && prec != 1)) return fail(MFNS_ERR_ARG, "bad arguments");
+  MFNS_CUDA(cudaSetDevice(p->ctx->device));
+  oplevel_distribute(*lv, prec, x, S(stream));
+  API_END
+}
+
+int mfns_smooth(mfns_problem* p, int level, int prec, const void* b, void* x, int x_is_zero, void* stream) {
+  API_BEGIN
+  if (!p || level < 0 || level >= (int)p->p->levels.size() || !b || !x || (prec != 0 && prec != 1))
+    return fail(MFNS_ERR_ARG, "bad arguments");
+  MFNS_CUDA(cudaSetDevice(p->ctx->device));
+  smooth(*p->p, level, prec, b, x, x_is_zero != 0, S(stream));
+  API_END
+}
+
+int mfns_prolongate_add(mfns_problem* p, int level, int prec, const void* coarse, void* fine, void* stream) {
+  API_BEGIN
+  if (!p || level < 0 || level + 1 >= (int)p->p->levels.size() || !coarse || !fine || (prec != 0 && prec != 1))
+    return fail(MFNS_ERR_ARG, "bad arguments");
+  MFNS_CUDA(cudaSetDevice(p->ctx->device));
+  Problem& P = *p->p;
+  transfer_prolongate_add(*P.transfers[level], *P.levels[level], *P.levels[level + 1], prec, coarse, fine, S(stream));
+  API_END
+}
+
+int mfns_restrict(mfns_problem* p, int level, int prec, const void* fine, void* coarse, void* stream) {
+  API_BEGIN
+  if (!p || level < 0 || level + 1 >= (int)p->p->levels.size() || !coarse || !fine || (prec != 0 && prec != 1))
+    return fail(MFNS_ERR_ARG, "bad arguments");
+  MFNS_CUDA(cudaSetDevice(p->ctx->device));
+  Problem& P = *p->p;
+  transfer_restrict(*P.transfers[level], *P.levels[level], *P.levels[level + 1], prec, fine, coarse, S(stream));
+  API_END
+}
+
+int mfns_vcycle(mfns_problem* p, int prec, const void* b, void* x, void* stream) {
+  API_BEGIN
+  if (!p || !b || !x || (prec != 0 && prec != 1)) return fail(MFNS_ERR_ARG, "bad arguments");
+  MFNS_CUDA(cudaSetDevice(p->ctx->device));
+  vcycle(*p->p, prec, b, x, S(stream));
+  API_END
+}
+
+int mfns_solve(mfns_problem* p, const void* b, void* x, mfns_solve_info* info, void* stream) {
+  API_BEGIN
+  if (!p || !b || !x) return fail(MFNS_ERR_ARG, "bad arguments");
+  if (p->p->kind == MFNS_PMASS) return fail(MFNS_ERR_UNSUPPORTED, "no solver for the pressure mass problem");
+  MFNS_CUDA(cudaSetDevice(p->ctx->device));
+  auto t0 = std::chrono::steady_clock::now();
+  double rel = 0;
+  bool conv = false;
+  int it = fgmres_solve(*p->p, (const double*)b, (double*)x, &rel, &conv, S(stream));
+  MFNS_CUDA(cudaStreamSynchronize(S(stream)));
+  auto t1 = std::chrono::steady_clock::now();
+  if (info) {
+    info->iterations = it;
+    info->rel_residual = rel;
+    info->seconds = std::chrono::duration<double>(t1 - t0).count();
+    info->converged = conv ? 1 : 0;
+  }
+  if (!conv) return fail(MFNS_ERR_NOT_CONVERGED, "FGMRES reached maxit");
+  API_END
+}
+
+}  // extern "C"
+
+static bool op_supported_kind(int dim, int kind, int k) {
+  switch (kind) {
+    case MFNS_STOKES: return mfns::op_supported(dim, k, OP_STOKES) && mfns::op_supported(dim, k - 1, OP_PMASS);
+    case MFNS_STOKES_A: return mfns::op_supported(dim, k, OP_STOKES_A);
+    case MFNS_STAB_NS: return mfns::op_supported(dim, k, OP_STAB_NS);
+    case MFNS_PMASS: return mfns::op_supported(dim, k, OP_PMASS);
+  }
+  return false;
+}

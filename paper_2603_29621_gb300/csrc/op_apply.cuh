@@ -1,0 +1,480 @@
+// The operator kernel (see op_kernel.cuh for the building blocks).
+#pragma once
+#include "op_kernel.cuh"
+
+namespace mfns {
+
+constexpr int kOpWarps = 4;  // warps per block
+
+template <int DIM, int Q>
+struct Team {
+  static constexpr int TPC = ipow(Q, DIM - 1);   // lanes per cell
+  static constexpr int CPW = 32 / TPC;           // cells per warp
+  static constexpr int BUF = ipow(Q, DIM);       // elements per team buffer
+};
+
+template <int OP, int DIM, int N, int NP>
+struct Layout {
+  using Tr = OpTraits<OP, DIM>;
+  static constexpr int NB = ipow(N, DIM);
+  static constexpr int NBP = ipow(NP, DIM);
+  // team buffers: scratch (3) + frozen needs none extra (kept in registers)
+  static constexpr int NBUF = 3;
+};
+
+// Node id of slot (a,b,c) of a structured cell, and whether it is on the boundary.
+template <int DIM, int K>
+__device__ __forceinline__ int64_t structured_node(int n, const int cc[3], int a, int b, int c, bool& bnd) {
+  const int64_t M = (int64_t)K * n + 1;
+  const int64_t ix = (int64_t)K * cc[0] + a, iy = (int64_t)K * cc[1] + b, iz = DIM == 3 ? (int64_t)K * cc[2] + c : 0;
+  bnd = ix == 0 || ix == M - 1 || iy == 0 || iy == M - 1 || (DIM == 3 && (iz == 0 || iz == M - 1));
+  return ix + M * (iy + M * iz);
+}
+
+template <int DIM, int K, int OP, typename T, bool STRUCT, bool DIAG>
+__global__ void __launch_bounds__(kOpWarps * 32)
+op_kernel(const OpArgs<T, K + 1, K + 1, (OP == OP_STOKES ? K : K + 1)> args) {
+  constexpr int Q = K + 1, N = K + 1, NP = OP == OP_STOKES ? K : K + 1;
+  using Tr = OpTraits<OP, DIM>;
+  using TM = Team<DIM, Q>;
+  constexpr int NU = Tr::NU;
+  constexpr int NB = ipow(N, DIM);
+  constexpr int NBP = ipow(NP, DIM);
+  constexpr int BUF = TM::BUF;
+  constexpr int NBUF = 3;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* smem = reinterpret_cast<T*>(smem_raw);
+
+  const int lane = lane_id();
+  const int warp = threadIdx.x >> 5;
+  int team = lane / TM::TPC;
+  const int tid = lane % TM::TPC;
+  const bool lane_active = team < TM::CPW;
+  if (!lane_active) team = TM::CPW;  // dummy team for the spare lanes
+  const int ti = tid % Q;
+  const int tj = DIM == 3 ? tid / Q : 0;
+  T* buf0 = smem + ((size_t)(warp * (TM::CPW + 1) + team) * NBUF) * BUF;
+  T* buf1 = buf0 + BUF;
+  T* buf2 = buf1 + BUF;
+
+  // ---- which cell
+  int64_t cell;
+  bool valid;
+  int cc[3] = {0, 0, 0};
+  {
+    const int64_t t = (int64_t)blockIdx.x * (kOpWarps * TM::CPW) + warp * TM::CPW + (lane_active ? team : 0);
+    if (STRUCT) {
+      const int n = args.n;
+      int m[3], bits[3];
+      int64_t total = 1;
+      for (int d = 0; d < 3; ++d) {
+        bits[d] = d < DIM ? (args.color >> d) & 1 : 0;
+        m[d] = d < DIM ? (n - bits[d] + 1) / 2 : 1;
+        total *= m[d];
+      }
+      valid = lane_active && t < total;
+      const int64_t tt = t < total ? t : total - 1;
+      cc[0] = 2 * (int)(tt % m[0]) + bits[0];
+      cc[1] = 2 * (int)((tt / m[0]) % m[1]) + bits[1];
+      cc[2] = DIM == 3 ? 2 * (int)(tt / ((int64_t)m[0] * m[1])) + bits[2] : 0;
+      cell = cc[0] + (int64_t)n * (cc[1] + (int64_t)n * cc[2]);
+    } else {
+      const int64_t c = args.cell_begin + t;
+      valid = lane_active && c < args.cell_end;
+      cell = c < args.cell_end ? c : args.cell_end - 1;
+    }
+  }
+  const T h = STRUCT ? args.h : args.hcell[cell];
+  const uint32_t mask = STRUCT ? 0u : args.mask[cell];
+  // warp-uniform: every team of the warp takes the constraint path if one needs it
+  // (a team with mask 0 leaves its values unchanged), so all __syncwarp calls match
+  const bool constrained = __any_sync(0xffffffffu, (mask & 0x3FFFFu) != 0);
+  const T inv_h = T(1) / h;
+  T hd = h;
+#pragma unroll
+  for (int d = 1; d < DIM; ++d) hd *= h;
+
+  const bool own = ti < N && tj < N;      // lane owns a nodal line of the main field
+  const bool ownp = ti < NP && tj < NP;   // ... of the pressure field (Taylor--Hood)
+  const int ti_n = ti < N ? ti : 0, tj_n = tj < N ? tj : 0;
+  const int ti_p = ti < NP ? ti : 0, tj_p = tj < NP ? tj : 0;
+
+  // ---- node ids of the owned slots
+  int64_t node[N];
+  bool bnd[N];
+  int64_t fnode[N];
+#pragma unroll
+  for (int c = 0; c < N; ++c) {
+    const int slot = DIM == 3 ? (c * N + tj_n) * N + ti_n : c * N + ti_n;
+    if (STRUCT) {
+      node[c] = DIM == 3 ? structured_node<DIM, K>(args.n, cc, ti_n, tj_n, c, bnd[c])
+                         : structured_node<DIM, K>(args.n, cc, ti_n, c, 0, bnd[c]);
+      fnode[c] = node[c];
+    } else {
+      const int32_t v = args.cell_u[cell * NB + slot];
+      node[c] = v & 0x7fffffff;
+      bnd[c] = v < 0;
+      fnode[c] = (Tr::FROZEN && args.cell_f) ? (int64_t)args.cell_f[cell * NB + slot] : node[c];
+    }
+  }
+  int64_t pnode[NP];
+  if (Tr::SPLIT_P) {
+#pragma unroll
+    for (int c = 0; c < NP; ++c) {
+      const int slot = DIM == 3 ? (c * NP + tj_p) * NP + ti_p : c * NP + ti_p;
+      if (STRUCT) {
+        bool dummy;
+        pnode[c] = DIM == 3 ? structured_node<DIM, K - 1>(args.n, cc, ti_p, tj_p, c, dummy)
+                            : structured_node<DIM, K - 1>(args.n, cc, ti_p, c, 0, dummy);
+      } else {
+        pnode[c] = args.cell_p[cell * NBP + slot];
+      }
+    }
+  }
+
+  const auto& tab = args.tab;
+  const T nu = args.nu;
+
+  // weights of the lane's column
+  T jxw[Q];
+#pragma unroll
+  for (int l = 0; l < Q; ++l) jxw[l] = (DIM == 3 ? tab.W[ti] * tab.W[tj] : tab.W[ti]) * tab.W[l] * hd;
+
+  // ---- gather (or unit vectors in diagonal mode)
+  constexpr int NLOC = NU * NB + (Tr::SPLIT_P ? NBP : 0);
+  T dacc[NU][N];   // diagonal mode: accumulated diagonal entries of the owned slots
+  T daccp[NP];
+#pragma unroll
+  for (int f = 0; f < NU; ++f)
+#pragma unroll
+    for (int c = 0; c < N; ++c) dacc[f][c] = 0;
+#pragma unroll
+  for (int c = 0; c < NP; ++c) daccp[c] = 0;
+
+  // frozen state (stabilised NS) at the lane's Gauss points
+  T Ub[DIM][Q], Gb[DIM][DIM][Q], Rb[DIM][Q], tau[Q];
+  if constexpr (Tr::FROZEN) {
+    T fz[DIM + 1][N];
+#pragma unroll
+    for (int c = 0; c < N; ++c) {
+#pragma unroll
+      for (int f = 0; f <= DIM; ++f) fz[f][c] = own ? args.frozen[fnode[c] * NU + f] : T(0);
+    }
+    T gp[DIM][Q], lb[DIM][Q];
+#pragma unroll
+    for (int f = 0; f <= DIM; ++f) {
+      T val[Q], g[DIM][Q], h2[DIM][Q];
+      values<DIM, Q, N, T>(fz[f], val, buf0, ti, tj, tab.S);
+      if (f < DIM) {
+        derivatives<DIM, Q, true, T>(val, g, h2, buf1, ti, tj, tab.D, tab.D2);
+#pragma unroll
+        for (int l = 0; l < Q; ++l) {
+          Ub[f][l] = val[l];
+          T lap = 0;
+#pragma unroll
+          for (int d = 0; d < DIM; ++d) {
+            Gb[f][d][l] = g[d][l] * inv_h;
+            lap += h2[d][l];
+          }
+          lb[f][l] = lap * inv_h * inv_h;
+        }
+      } else {
+        derivatives<DIM, Q, false, T>(val, g, h2, buf1, ti, tj, tab.D, tab.D2);
+#pragma unroll
+        for (int l = 0; l < Q; ++l)
+#pragma unroll
+          for (int d = 0; d < DIM; ++d) gp[d][l] = g[d][l] * inv_h;
+      }
+    }
+#pragma unroll
+    for (int l = 0; l < Q; ++l) {
+      T un2 = 0;
+#pragma unroll
+      for (int i = 0; i < DIM; ++i) {
+        T s = gp[i][l] - nu * lb[i][l];
+#pragma unroll
+        for (int j = 0; j < DIM; ++j) s += Ub[j][l] * Gb[i][j][l];
+        Rb[i][l] = s;
+        un2 += Ub[i][l] * Ub[i][l];
+      }
+      const T a = T(2) * args.dt_inv, b2 = T(4) * un2 * inv_h * inv_h, c = T(12) * nu * inv_h * inv_h;
+      tau[l] = T(1) / sqrt(a * a + b2 + c * c);
+    }
+  }
+
+  // the local loop: one pass for vmult, NLOC passes (unit vectors) for the diagonal
+  const int npass = DIAG ? NLOC : 1;
+  for (int pass = 0; pass < npass; ++pass) {
+    T u[NU][N];
+    T pv[NP];
+    if (!DIAG) {
+      if (own) {
+#pragma unroll
+        for (int c = 0; c < N; ++c) {
+          if constexpr (NU == 4) {
+            if constexpr (sizeof(T) == 4) {
+              const float4 v = *reinterpret_cast<const float4*>(args.src + node[c] * 4);
+              u[0][c] = v.x; u[1][c] = v.y; u[2][c] = v.z; u[3][c] = v.w;
+            } else {
+              const double2 v0 = *reinterpret_cast<const double2*>(args.src + node[c] * 4);
+              const double2 v1 = *reinterpret_cast<const double2*>(args.src + node[c] * 4 + 2);
+              u[0][c] = v0.x; u[1][c] = v0.y; u[2][c] = v1.x; u[3][c] = v1.y;
+            }
+          } else {
+#pragma unroll
+            for (int f = 0; f < NU; ++f) u[f][c] = args.src[node[c] * NU + f];
+          }
+          if (OP != OP_PMASS && bnd[c]) {
+#pragma unroll
+            for (int f = 0; f < DIM; ++f) u[f][c] = 0;
+          }
+        }
+      } else {
+#pragma unroll
+        for (int f = 0; f < NU; ++f)
+#pragma unroll
+          for (int c = 0; c < N; ++c) u[f][c] = 0;
+      }
+      if (Tr::SPLIT_P) {
+#pragma unroll
+        for (int c = 0; c < NP; ++c) pv[c] = ownp ? args.src[args.p_offset + pnode[c]] : T(0);
+      }
+    } else {
+      // unit vector of local DoF `pass` (component-major over the main nodes, then pressure)
+#pragma unroll
+      for (int f = 0; f < NU; ++f)
+#pragma unroll
+        for (int c = 0; c < N; ++c) {
+          const int slot = DIM == 3 ? (c * N + tj_n) * N + ti_n : c * N + ti_n;
+          u[f][c] = (own && pass == f * NB + slot) ? T(1) : T(0);
+          if (OP != OP_PMASS && f < DIM && bnd[c]) u[f][c] = 0;
+        }
+      if (Tr::SPLIT_P) {
+#pragma unroll
+        for (int c = 0; c < NP; ++c) {
+          const int slot = DIM == 3 ? (c * NP + tj_p) * NP + ti_p : c * NP + ti_p;
+          pv[c] = (ownp && pass == NU * NB + slot) ? T(1) : T(0);
+        }
+      }
+    }
+    if (!STRUCT && constrained) {
+#pragma unroll
+      for (int f = 0; f < NU; ++f) apply_constraints<DIM, N, false, T>(u[f], buf0, mask, ti_n, tj_n, tab.P, own);
+      if (Tr::SPLIT_P) apply_constraints<DIM, NP, false, T>(pv, buf0, mask, ti_p, tj_p, tab.Pp, ownp);
+    }
+
+    // ---- physics; result r[f][c] per component (and rp for the pressure block)
+    T r[NU][N];
+    T rp[NP];
+    if constexpr (OP == OP_STOKES_A) {
+#pragma unroll
+      for (int f = 0; f < NU; ++f) {
+        T val[Q], g[DIM][Q], h2[DIM][Q], c0[Q];
+        values<DIM, Q, N, T>(u[f], val, buf0, ti, tj, tab.S);
+        derivatives<DIM, Q, false, T>(val, g, h2, buf1, ti, tj, tab.D, tab.D2);
+#pragma unroll
+        for (int l = 0; l < Q; ++l) {
+          const T s = nu * jxw[l] * inv_h * inv_h;
+#pragma unroll
+          for (int d = 0; d < DIM; ++d) g[d][l] *= s;
+        }
+        integrate<DIM, Q, N, false, true, T>(c0, g, r[f], buf1, buf2, ti, tj, tab.S, tab.D);
+      }
+    } else if constexpr (OP == OP_PMASS) {
+      T val[Q], c0[Q], g[DIM][Q];
+      values<DIM, Q, N, T>(u[0], val, buf0, ti, tj, tab.S);
+#pragma unroll
+      for (int l = 0; l < Q; ++l) c0[l] = val[l] * jxw[l];
+      integrate<DIM, Q, N, true, false, T>(c0, g, r[0], buf1, buf2, ti, tj, tab.S, tab.D);
+    } else if constexpr (OP == OP_STOKES) {
+      T gu[DIM][DIM][Q];
+      T div[Q];
+#pragma unroll
+      for (int l = 0; l < Q; ++l) div[l] = 0;
+#pragma unroll
+      for (int f = 0; f < DIM; ++f) {
+        T val[Q], g[DIM][Q], h2[DIM][Q];
+        values<DIM, Q, N, T>(u[f], val, buf0, ti, tj, tab.S);
+        derivatives<DIM, Q, false, T>(val, g, h2, buf1, ti, tj, tab.D, tab.D2);
+#pragma unroll
+        for (int l = 0; l < Q; ++l) {
+#pragma unroll
+          for (int d = 0; d < DIM; ++d) gu[f][d][l] = g[d][l] * inv_h;
+          div[l] += g[f][l] * inv_h;
+        }
+      }
+      T p[Q];
+      values<DIM, Q, NP, T>(pv, p, buf0, ti, tj, tab.Sp);
+#pragma unroll
+      for (int f = 0; f < DIM; ++f) {
+        T cg[DIM][Q], c0[Q];
+#pragma unroll
+        for (int l = 0; l < Q; ++l) {
+          const T s = jxw[l] * inv_h;
+#pragma unroll
+          for (int d = 0; d < DIM; ++d) cg[d][l] = (nu * gu[f][d][l] - (d == f ? p[l] : T(0))) * s;
+        }
+        integrate<DIM, Q, N, false, true, T>(c0, cg, r[f], buf1, buf2, ti, tj, tab.S, tab.D);
+      }
+      {
+        T c0[Q], cg[DIM][Q];
+#pragma unroll
+        for (int l = 0; l < Q; ++l) c0[l] = args.div_sign * div[l] * jxw[l];
+        integrate<DIM, Q, NP, true, false, T>(c0, cg, rp, buf1, buf2, ti, tj, tab.Sp, tab.D);
+      }
+    } else {  // OP_STAB_NS
+      const T cfm = args.cf[0], cfc = args.cf[1], cfn = args.cf[2], cfs = args.cf[3], cfsn = args.cf[4],
+              cfp = args.cf[5], cfl = args.cf[6];
+      const T cm = args.cm;
+      T Rl[DIM][Q], vc[DIM][Q], gc[DIM][DIM][Q], dv[Q];
+#pragma unroll
+      for (int l = 0; l < Q; ++l) {
+        dv[l] = 0;
+#pragma unroll
+        for (int i = 0; i < DIM; ++i) {
+          Rl[i][l] = 0;
+          vc[i][l] = 0;
+#pragma unroll
+          for (int d = 0; d < DIM; ++d) gc[i][d][l] = 0;
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < DIM; ++j) {
+        T val[Q], g[DIM][Q], h2[DIM][Q];
+        values<DIM, Q, N, T>(u[j], val, buf0, ti, tj, tab.S);
+        derivatives<DIM, Q, true, T>(val, g, h2, buf1, ti, tj, tab.D, tab.D2);
+#pragma unroll
+        for (int l = 0; l < Q; ++l) {
+          T ugu = 0, lap = 0;
+#pragma unroll
+          for (int d = 0; d < DIM; ++d) {
+            g[d][l] *= inv_h;
+            ugu += Ub[d][l] * g[d][l];
+            lap += h2[d][l];
+          }
+          lap *= inv_h * inv_h;
+          const T gal = cfm * cm * val[l] + cfc * ugu;  // component-diagonal Galerkin/residual part
+          vc[j][l] += gal;
+          Rl[j][l] += gal - cfl * nu * lap;
+#pragma unroll
+          for (int i = 0; i < DIM; ++i) {
+            const T nt = cfn * val[l] * Gb[i][j][l];   // (du . grad ub)_i from component j
+            vc[i][l] += nt;
+            Rl[i][l] += nt;
+            gc[i][j][l] += cfsn * tau[l] * Rb[i][l] * val[l];  // tau Rbar_i (du . grad v_i)
+          }
+#pragma unroll
+          for (int d = 0; d < DIM; ++d) gc[j][d][l] += nu * g[d][l];
+          dv[l] += g[j][l];
+        }
+      }
+      T pval[Q];
+      {
+        T g[DIM][Q], h2[DIM][Q];
+        values<DIM, Q, N, T>(u[DIM], pval, buf0, ti, tj, tab.S);
+        derivatives<DIM, Q, false, T>(pval, g, h2, buf1, ti, tj, tab.D, tab.D2);
+#pragma unroll
+        for (int l = 0; l < Q; ++l)
+#pragma unroll
+          for (int i = 0; i < DIM; ++i) {
+            Rl[i][l] += g[i][l] * inv_h;
+            gc[i][i][l] -= pval[l];
+          }
+      }
+      // SUPG (test ub.grad v), scaling, then integrate the velocity components
+#pragma unroll
+      for (int i = 0; i < DIM; ++i) {
+        T c0[Q], cg[DIM][Q];
+#pragma unroll
+        for (int l = 0; l < Q; ++l) {
+          const T st = cfs * tau[l] * Rl[i][l];
+          c0[l] = vc[i][l] * jxw[l];
+#pragma unroll
+          for (int d = 0; d < DIM; ++d) cg[d][l] = (gc[i][d][l] + st * Ub[d][l]) * jxw[l] * inv_h;
+        }
+        integrate<DIM, Q, N, true, true, T>(c0, cg, r[i], buf1, buf2, ti, tj, tab.S, tab.D);
+      }
+      {
+        T c0[Q], cg[DIM][Q];
+#pragma unroll
+        for (int l = 0; l < Q; ++l) {
+          c0[l] = args.div_sign * dv[l] * jxw[l];
+#pragma unroll
+          for (int d = 0; d < DIM; ++d) cg[d][l] = cfp * tau[l] * Rl[d][l] * jxw[l] * inv_h;
+        }
+        integrate<DIM, Q, N, true, true, T>(c0, cg, r[DIM], buf1, buf2, ti, tj, tab.S, tab.D);
+      }
+    }
+
+    if (!STRUCT && constrained) {
+#pragma unroll
+      for (int f = 0; f < NU; ++f) apply_constraints<DIM, N, true, T>(r[f], buf0, mask, ti_n, tj_n, tab.P, own);
+      if (Tr::SPLIT_P) apply_constraints<DIM, NP, true, T>(rp, buf0, mask, ti_p, tj_p, tab.Pp, ownp);
+    }
+
+    if (DIAG) {
+#pragma unroll
+      for (int f = 0; f < NU; ++f)
+#pragma unroll
+        for (int c = 0; c < N; ++c) {
+          const int slot = DIM == 3 ? (c * N + tj_n) * N + ti_n : c * N + ti_n;
+          if (own && pass == f * NB + slot) dacc[f][c] = r[f][c];
+        }
+      if (Tr::SPLIT_P) {
+#pragma unroll
+        for (int c = 0; c < NP; ++c) {
+          const int slot = DIM == 3 ? (c * NP + tj_p) * NP + ti_p : c * NP + ti_p;
+          if (ownp && pass == NU * NB + slot) daccp[c] = rp[c];
+        }
+      }
+    } else if (valid) {
+      // ---- scatter (plain read-modify-write: no other cell of this colour touches these DoFs)
+      if (own) {
+#pragma unroll
+        for (int c = 0; c < N; ++c) {
+          T* d = args.dst + node[c] * NU;
+          if constexpr (NU == 4) {
+            if constexpr (sizeof(T) == 4) {
+              float4 v = *reinterpret_cast<float4*>(d);
+              v.x += r[0][c]; v.y += r[1][c]; v.z += r[2][c]; v.w += r[3][c];
+              *reinterpret_cast<float4*>(d) = v;
+            } else {
+              double2 v0 = *reinterpret_cast<double2*>(d);
+              double2 v1 = *reinterpret_cast<double2*>(d + 2);
+              v0.x += r[0][c]; v0.y += r[1][c]; v1.x += r[2][c]; v1.y += r[3][c];
+              *reinterpret_cast<double2*>(d) = v0;
+              *reinterpret_cast<double2*>(d + 2) = v1;
+            }
+          } else {
+#pragma unroll
+            for (int f = 0; f < NU; ++f) d[f] += r[f][c];
+          }
+        }
+      }
+      if (Tr::SPLIT_P && ownp) {
+#pragma unroll
+        for (int c = 0; c < NP; ++c) args.dst[args.p_offset + pnode[c]] += rp[c];
+      }
+    }
+  }
+  if (DIAG && valid) {
+    if (own) {
+#pragma unroll
+      for (int c = 0; c < N; ++c)
+#pragma unroll
+        for (int f = 0; f < NU; ++f) args.dst[node[c] * NU + f] += dacc[f][c];
+    }
+    if (Tr::SPLIT_P && ownp) {
+#pragma unroll
+      for (int c = 0; c < NP; ++c) args.dst[args.p_offset + pnode[c]] += daccp[c];
+    }
+  }
+}
+
+template <int DIM, int K, int OP, typename T>
+constexpr size_t op_smem_bytes() {
+  using TM = Team<DIM, K + 1>;
+  return sizeof(T) * (size_t)kOpWarps * (TM::CPW + 1) * 3 * TM::BUF;
+}
+
+}  // namespace mfns

@@ -1,0 +1,100 @@
+// Runtime dispatch of the operator kernels and the host-side 1D tables.
+#include <string>
+
+#include "mesh.hpp"
+#include "op_kernel.cuh"
+#include "op_launch.hpp"
+#include "common.hpp"
+
+namespace mfns {
+
+#define MFNS_DECL(DIM, K, OP)                                                                                    \
+  extern template void op_launch<DIM, K, OP, double>(const OpLaunch&, const double*, double*, bool, cudaStream_t); \
+  extern template void op_launch<DIM, K, OP, float>(const OpLaunch&, const float*, float*, bool, cudaStream_t);
+
+MFNS_DECL(3, 1, OP_STAB_NS) MFNS_DECL(3, 2, OP_STAB_NS) MFNS_DECL(3, 3, OP_STAB_NS)
+MFNS_DECL(2, 1, OP_STAB_NS) MFNS_DECL(2, 2, OP_STAB_NS) MFNS_DECL(2, 3, OP_STAB_NS) MFNS_DECL(2, 4, OP_STAB_NS)
+MFNS_DECL(3, 2, OP_STOKES) MFNS_DECL(3, 3, OP_STOKES) MFNS_DECL(3, 4, OP_STOKES)
+MFNS_DECL(2, 2, OP_STOKES) MFNS_DECL(2, 3, OP_STOKES) MFNS_DECL(2, 4, OP_STOKES)
+MFNS_DECL(3, 1, OP_STOKES_A) MFNS_DECL(3, 2, OP_STOKES_A) MFNS_DECL(3, 3, OP_STOKES_A) MFNS_DECL(3, 4, OP_STOKES_A)
+MFNS_DECL(2, 1, OP_STOKES_A) MFNS_DECL(2, 2, OP_STOKES_A) MFNS_DECL(2, 3, OP_STOKES_A) MFNS_DECL(2, 4, OP_STOKES_A)
+MFNS_DECL(2, 1, OP_PMASS) MFNS_DECL(2, 2, OP_PMASS) MFNS_DECL(2, 3, OP_PMASS)
+MFNS_DECL(3, 1, OP_PMASS) MFNS_DECL(3, 2, OP_PMASS) MFNS_DECL(3, 3, OP_PMASS)
+
+bool op_supported(int dim, int k, int op) {
+  if (dim != 2 && dim != 3) return false;
+  switch (op) {
+    case OP_STAB_NS: return k >= 1 && k <= (dim == 3 ? 3 : 4);
+    case OP_STOKES: return k >= 2 && k <= 4;
+    case OP_STOKES_A: return k >= 1 && k <= 4;
+    case OP_PMASS: return k >= 1 && k <= 3;
+  }
+  return false;
+}
+
+template <typename T>
+static void dispatch(const OpLaunch& L, const T* s, T* d, bool diag, cudaStream_t st) {
+#define MFNS_CASE(DIM, K, OP) \
+  if (L.dim == DIM && L.k == K && L.op == OP) return op_launch<DIM, K, OP, T>(L, s, d, diag, st);
+  MFNS_CASE(3, 1, OP_STAB_NS) MFNS_CASE(3, 2, OP_STAB_NS) MFNS_CASE(3, 3, OP_STAB_NS)
+  MFNS_CASE(2, 1, OP_STAB_NS) MFNS_CASE(2, 2, OP_STAB_NS) MFNS_CASE(2, 3, OP_STAB_NS) MFNS_CASE(2, 4, OP_STAB_NS)
+  MFNS_CASE(3, 2, OP_STOKES) MFNS_CASE(3, 3, OP_STOKES) MFNS_CASE(3, 4, OP_STOKES)
+  MFNS_CASE(2, 2, OP_STOKES) MFNS_CASE(2, 3, OP_STOKES) MFNS_CASE(2, 4, OP_STOKES)
+  MFNS_CASE(3, 1, OP_STOKES_A) MFNS_CASE(3, 2, OP_STOKES_A) MFNS_CASE(3, 3, OP_STOKES_A) MFNS_CASE(3, 4, OP_STOKES_A)
+  MFNS_CASE(2, 1, OP_STOKES_A) MFNS_CASE(2, 2, OP_STOKES_A) MFNS_CASE(2, 3, OP_STOKES_A) MFNS_CASE(2, 4, OP_STOKES_A)
+  MFNS_CASE(2, 1, OP_PMASS) MFNS_CASE(2, 2, OP_PMASS) MFNS_CASE(2, 3, OP_PMASS)
+  MFNS_CASE(3, 1, OP_PMASS) MFNS_CASE(3, 2, OP_PMASS) MFNS_CASE(3, 3, OP_PMASS)
+#undef MFNS_CASE
+  throw Error(kErrUnsupported, "unsupported (dim, degree, operator) combination");
+}
+
+void op_apply(const OpLaunch& L, int prec, const void* src, void* dst, bool diag, cudaStream_t s) {
+  if (prec == 0)
+    dispatch<double>(L, static_cast<const double*>(src), static_cast<double*>(dst), diag, s);
+  else
+    dispatch<float>(L, static_cast<const float*>(src), static_cast<float*>(dst), diag, s);
+}
+
+// Collocation derivative on the Gauss points: D[i][j] = l_j'(x_i), Lagrange basis on the Gauss points.
+void fill_tables(OpLaunch& L) {
+  const int q = L.op == OP_PMASS ? L.k + 1 : L.k + 1;
+  L.Q = q;
+  L.N = L.k + 1;
+  L.NP = L.op == OP_STOKES ? L.k : L.k + 1;
+  std::vector<double> xg, wg;
+  gauss_rule(q, xg, wg);
+  std::vector<double> xn = gll_nodes(L.k);
+  L.S.assign(q * L.N, 0.0);
+  for (int i = 0; i < q; ++i)
+    for (int a = 0; a < L.N; ++a) L.S[i * L.N + a] = lagrange(xn, a, xg[i]);
+  L.Sp.assign(q * L.NP, 0.0);
+  if (L.op == OP_STOKES) {
+    std::vector<double> xp = gll_nodes(L.k - 1);
+    for (int i = 0; i < q; ++i)
+      for (int a = 0; a < L.NP; ++a) L.Sp[i * L.NP + a] = lagrange(xp, a, xg[i]);
+  }
+  L.D.assign(q * q, 0.0);
+  for (int i = 0; i < q; ++i)
+    for (int j = 0; j < q; ++j) L.D[i * q + j] = lagrange_deriv(xg, j, xg[i]);
+  L.D2.assign(q * q, 0.0);
+  for (int i = 0; i < q; ++i)
+    for (int j = 0; j < q; ++j) {
+      double s = 0;
+      for (int r = 0; r < q; ++r) s += L.D[i * q + r] * L.D[r * q + j];
+      L.D2[i * q + j] = s;
+    }
+  L.W = wg;
+  auto halves = [](int k, std::vector<double>& P) {
+    std::vector<double> x = gll_nodes(k);
+    int n = k + 1;
+    P.assign(2 * n * n, 0.0);
+    for (int h = 0; h < 2; ++h)
+      for (int s = 0; s < n; ++s)
+        for (int m = 0; m < n; ++m) P[(h * n + s) * n + m] = lagrange(x, m, 0.5 * (h + x[s]));
+  };
+  halves(L.k, L.P);
+  if (L.op == OP_STOKES) halves(L.k - 1, L.Pp);
+  else L.Pp.assign(2 * L.NP * L.NP, 0.0);
+}
+
+}  // namespace mfns

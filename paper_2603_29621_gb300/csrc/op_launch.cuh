@@ -1,0 +1,86 @@
+// Templated launcher of the operator kernel; included by the per-operator
+// instantiation units (op_<kind>_<dim>d.cu).
+#pragma once
+#include "common.hpp"
+#include "op_apply.cuh"
+#include "op_launch.hpp"
+
+namespace mfns {
+
+template <typename T, int Q, int N, int NP>
+static void build_tables(const OpLaunch& L, Tables<T, Q, N, NP>& t) {
+  for (int q = 0; q < Q; ++q) {
+    for (int a = 0; a < N; ++a) t.S[q][a] = (T)L.S[q * N + a];
+    for (int a = 0; a < NP; ++a) t.Sp[q][a] = L.Sp.empty() ? T(0) : (T)L.Sp[q * NP + a];
+    for (int r = 0; r < Q; ++r) {
+      t.D[q][r] = (T)L.D[q * Q + r];
+      t.D2[q][r] = (T)L.D2[q * Q + r];
+    }
+    t.W[q] = (T)L.W[q];
+  }
+  for (int h = 0; h < 2; ++h) {
+    for (int s = 0; s < N; ++s)
+      for (int m = 0; m < N; ++m) t.P[h][s][m] = (T)L.P[(h * N + s) * N + m];
+    for (int s = 0; s < NP; ++s)
+      for (int m = 0; m < NP; ++m) t.Pp[h][s][m] = L.Pp.empty() ? T(0) : (T)L.Pp[(h * NP + s) * NP + m];
+  }
+}
+
+template <int DIM, int K, int OP, typename T>
+void op_launch(const OpLaunch& L, const T* src, T* dst, bool diag, cudaStream_t s) {
+  constexpr int Q = K + 1, N = K + 1, NP = OP == OP_STOKES ? K : K + 1;
+  OpArgs<T, Q, N, NP> a{};
+  if (L.Q != Q || L.N != N || L.NP != NP) throw Error(kErrArg, "operator tables do not match the degree");
+  build_tables(L, a.tab);
+  const int prec = sizeof(T) == 8 ? 0 : 1;
+  a.src = src;
+  a.dst = dst;
+  a.frozen = reinterpret_cast<const T*>(L.frozen[prec]);
+  a.cell_u = L.cell_u;
+  a.cell_p = L.cell_p;
+  a.cell_f = L.cell_f;
+  a.mask = L.mask;
+  a.hcell = reinterpret_cast<const T*>(L.hcell[prec]);
+  a.n = L.n;
+  a.p_offset = L.p_offset;
+  a.h = (T)L.h;
+  a.nu = (T)L.nu;
+  const double dt_inv = L.dt > 0 ? 1.0 / L.dt : 0.0;
+  a.dt_inv = (T)dt_inv;
+  a.cm = (T)(1.5 * dt_inv);
+  a.div_sign = (T)L.div_sign;
+  for (int b = 0; b < 7; ++b) a.cf[b] = (L.terms >> b) & 1 ? T(1) : T(0);
+  a.diag = diag;
+  using TM = Team<DIM, Q>;
+  constexpr int cells_per_block = kOpWarps * TM::CPW;
+  const size_t smem = op_smem_bytes<DIM, K, OP, T>();
+  const bool structured = L.structured && !diag;
+  for (int c = 0; c < L.n_colors; ++c) {
+    int64_t ncell;
+    if (structured) {
+      a.color = c;
+      ncell = 1;
+      for (int d = 0; d < DIM; ++d) ncell *= (L.n - ((c >> d) & 1) + 1) / 2;
+    } else {
+      a.cell_begin = L.color_ptr[c];
+      a.cell_end = L.color_ptr[c + 1];
+      ncell = a.cell_end - a.cell_begin;
+    }
+    if (ncell <= 0) continue;
+    const unsigned grid = (unsigned)((ncell + cells_per_block - 1) / cells_per_block);
+    if (structured) {
+      op_kernel<DIM, K, OP, T, true, false><<<grid, kOpWarps * 32, smem, s>>>(a);
+    } else if (diag) {
+      op_kernel<DIM, K, OP, T, false, true><<<grid, kOpWarps * 32, smem, s>>>(a);
+    } else {
+      op_kernel<DIM, K, OP, T, false, false><<<grid, kOpWarps * 32, smem, s>>>(a);
+    }
+    MFNS_CUDA(cudaGetLastError());
+  }
+}
+
+#define MFNS_INSTANTIATE_OP(DIM, K, OP)                                                                   \
+  template void op_launch<DIM, K, OP, double>(const OpLaunch&, const double*, double*, bool, cudaStream_t); \
+  template void op_launch<DIM, K, OP, float>(const OpLaunch&, const float*, float*, bool, cudaStream_t);
+
+}  // namespace mfns

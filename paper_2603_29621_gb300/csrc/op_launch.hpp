@@ -1,0 +1,44 @@
+// Host description of one operator on one mesh level, as needed to launch the
+// operator kernels (filled by level.cpp, consumed by the templated launchers).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <vector>
+
+namespace mfns {
+
+struct OpLaunch {
+  int dim = 3, k = 2, op = 0;        // main-field degree k, op = OpKind
+  bool structured = false;          // uniform mesh with lexicographic numbering
+  int n = 0;                        // structured: cells per direction
+  double h = 0.0;                   // structured: edge length
+  int64_t n_cells = 0;
+  int n_colors = 0;
+  std::vector<int32_t> color_ptr;   // indexed: colour c = cells [color_ptr[c], color_ptr[c+1])
+  const int32_t* cell_u = nullptr;  // device, colour-sorted
+  const int32_t* cell_p = nullptr;
+  const int32_t* cell_f = nullptr;
+  const uint32_t* mask = nullptr;
+  const void* hcell[2] = {nullptr, nullptr};     // fp64 / fp32 edge lengths
+  const void* frozen[2] = {nullptr, nullptr};    // fp64 / fp32 frozen state
+  int64_t p_offset = 0;
+  double nu = 1.0, dt = 0.0, div_sign = -1.0;    // dt <= 0: stationary
+  int terms = 127;
+  // 1D tables in double (converted to the kernel precision at launch)
+  int Q = 3, N = 3, NP = 3;
+  std::vector<double> S, Sp, D, D2, W, P, Pp;
+};
+
+// Fill the 1D tables of `L` for its degree (needs L.dim, L.k, L.op).
+void fill_tables(OpLaunch& L);
+
+// dst = A src on the free rows (dst must be zeroed by the caller); diag = true
+// accumulates the diagonal instead (src ignored).  Constrained rows untouched.
+template <int DIM, int K, int OP, typename T>
+void op_launch(const OpLaunch& L, const T* src, T* dst, bool diag, cudaStream_t s);
+
+// Runtime dispatch over (dim, k, op, precision); prec 0 = fp64, 1 = fp32.
+void op_apply(const OpLaunch& L, int prec, const void* src, void* dst, bool diag, cudaStream_t s);
+
+}  // namespace mfns

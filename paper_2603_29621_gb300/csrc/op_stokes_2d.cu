@@ -1,0 +1,7 @@
+// Instantiations: Taylor--Hood Stokes, 2D.
+#include "op_launch.cuh"
+namespace mfns {
+MFNS_INSTANTIATE_OP(2, 2, OP_STOKES)
+MFNS_INSTANTIATE_OP(2, 3, OP_STOKES)
+MFNS_INSTANTIATE_OP(2, 4, OP_STOKES)
+}  // namespace mfns

@@ -1,0 +1,8 @@
+// Instantiations: vector Laplacian (A block), 3D.
+#include "op_launch.cuh"
+namespace mfns {
+MFNS_INSTANTIATE_OP(3, 1, OP_STOKES_A)
+MFNS_INSTANTIATE_OP(3, 2, OP_STOKES_A)
+MFNS_INSTANTIATE_OP(3, 3, OP_STOKES_A)
+MFNS_INSTANTIATE_OP(3, 4, OP_STOKES_A)
+}  // namespace mfns

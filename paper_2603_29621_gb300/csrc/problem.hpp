@@ -1,0 +1,112 @@
+// Problem = operator + global-coarsening hierarchy + smoothers + coarse solver
+// + workspaces, all resident on one device.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "common.hpp"
+#include "mesh.hpp"
+#include "opkind.hpp"
+#include "op_launch.hpp"
+
+namespace mfns {
+
+struct Physics {
+  double nu = 1.0, dt = 0.0, div_sign = -1.0;
+  int terms = 127;
+};
+
+// One operator on one mesh (one multigrid level, the system operator or the pressure mass).
+struct OpLevel {
+  int op = 0, dim = 3, k = 1, NU = 1;
+  Forest forest;
+  NodeSpace nu, np;                     // main nodes, Taylor--Hood pressure nodes
+  int64_t n_dofs = 0, n_main_dofs = 0;  // vector length, main-node block length
+  OpLaunch L;
+  std::vector<int32_t> perm;            // colour-sorted position -> forest cell id
+  DevBuf cell_u, cell_p, cell_f, mask, hcell[2], frozen[2];
+  std::vector<int32_t> constrained_host;
+  DevBuf constrained;                   // identity rows
+  int64_t n_hang = 0;
+  DevBuf hang_dof, hang_ptr, hang_src, hang_w[2];
+  std::vector<int32_t> pres_host;
+  DevBuf pres;                          // free pressure entries (constant-pressure null space)
+  int64_t n_pres = 0;
+  // transfer support: true fine node per slot with flags (bit 31 skip, bit 30 boundary)
+  DevBuf tnodes, tpnodes;
+  // smoother
+  DevBuf dinv[2];
+  double lmax = 0.0;
+  size_t bytes() const;
+};
+
+void build_oplevel(OpLevel& lv, const Forest& f, int op, int k, const Physics& ph, Budget* bud);
+void oplevel_vmult(const OpLevel& lv, int prec, const void* src, void* dst, cudaStream_t s);
+void oplevel_diag(const OpLevel& lv, int prec, void* diag, cudaStream_t s);
+void oplevel_distribute(const OpLevel& lv, int prec, void* x, cudaStream_t s);
+void oplevel_support(const OpLevel& lv, double* xyz, int* field);
+
+// Transfer between fine level (index l) and coarse level (l+1), Eq. 4.
+struct Transfer {
+  bool hkind = true;                    // true: h (children), false: p (same cells)
+  int dim = 3, kf = 1, kc = 1, ncomp = 1;
+  int64_t n_coarse_cells = 0;
+  std::vector<int32_t> color_ptr;       // colours of the coarse level
+  DevBuf child_cell;                    // n_coarse * 2^dim fine cell ids (-1: none)
+  DevBuf child_code;                    // per child: child bits, or 8 = same cell
+  std::vector<double> E;                // h: P_half[2][NF][NC]; p: S[NF][NC]
+  std::vector<double> Pc;               // coarse hanging interpolation P[2][NC][NC]
+};
+void build_transfer(Transfer& t, const OpLevel& fine, const OpLevel& coarse, Budget* bud);
+void transfer_prolongate_add(const Transfer& t, const OpLevel& fine, const OpLevel& coarse, int prec,
+                             const void* xc, void* xf, cudaStream_t s);
+void transfer_restrict(const Transfer& t, const OpLevel& fine, const OpLevel& coarse, int prec,
+                       const void* rf, void* rc, cudaStream_t s);
+
+struct Workspace {
+  DevBuf r, d, t, b, x;                 // per level, per precision
+};
+
+struct Problem {
+  int kind = 0, dim = 3, k = 2;
+  Physics phys;
+  int smoother = 0, smoother_degree = 5, mg_precision = 0, restart = 30, maxit = 500, cg_iterations = 10;
+  double tol = 1e-8;
+  Budget* bud = nullptr;
+  std::unique_ptr<OpLevel> system;      // the problem's operator on the finest mesh
+  std::unique_ptr<OpLevel> pmass;       // Stokes: pressure mass
+  std::vector<std::unique_ptr<OpLevel>> levels;  // multigrid levels (0 = finest)
+  std::vector<std::unique_ptr<Transfer>> transfers;  // transfers[l]: level l <-> l+1
+  // coarse solver
+  bool coarse_dense = true;
+  int64_t coarse_n = 0;
+  DevBuf coarse_inv[2];
+  int coarse_cheby_degree = 30;
+  // workspaces [precision][level]
+  std::vector<Workspace> ws[2];
+  // FGMRES / Krylov (fp64)
+  DevBuf V, Z, w, tmp, hvec, yvec, part, ptrV, ptrZ, scal;
+  DevBuf sys_r, sys_z;                  // fp64 system-size temporaries
+  DevBuf mg_b32, mg_x32;                // fp32 copies for the mixed-precision preconditioner
+  DevBuf cg_r, cg_z, cg_p, cg_q, cg_x;  // Stokes Schur CG (mg precision)
+  DevBuf stokes_u_rhs, stokes_u_sol;    // Stokes A-block rhs/solution (mg precision)
+  size_t bytes = 0;
+};
+
+// Build everything for a mesh and a description; throws Error.
+std::unique_ptr<Problem> build_problem(const Forest& f, int kind, int k, const Physics& ph, int mg_order,
+                                       int coarse_stop_n, Budget* bud);
+
+// Multigrid
+void smooth(Problem& p, int level, int prec, const void* b, void* x, bool x_is_zero, cudaStream_t s);
+void vcycle(Problem& p, int prec, const void* b, void* x, cudaStream_t s);
+void estimate_lambda(Problem& p, cudaStream_t s);
+void setup_coarse(Problem& p, cudaStream_t s);
+void alloc_workspaces(Problem& p);
+// Solve (FP64 FGMRES); returns iterations, writes relres; throws on CUDA errors
+int fgmres_solve(Problem& p, const double* b, double* x, double* relres, bool* converged, cudaStream_t s);
+
+}  // namespace mfns

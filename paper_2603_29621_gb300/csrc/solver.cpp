@@ -1,0 +1,529 @@
+// Hierarchy set-up, smoothers, V-cycle, coarse solver and FGMRES.
+//
+// Section 3: A^{-1} is approximated by one V-cycle of global-coarsening
+// multigrid (p-coarsening to linear elements first, then h); Section 5: the
+// stabilised system uses a monolithic hierarchy with h-coarsening first.
+// Smoothers: Chebyshev iteration around point Jacobi (Saad, Alg. 12.1 on
+// D^{-1} A, lmin = lmax / 20) or Jacobi relaxation with w = 2 / (lmin + lmax).
+// Coarse level: dense inverse (host LU), or Chebyshev of degree 30 when the
+// coarse system is larger than 4096 unknowns.  FGMRES(m) with classical
+// Gram--Schmidt applied twice (Section 3 "We solve the Stokes system with FGMRES").
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <random>
+
+#include "problem.hpp"
+#include "vec.hpp"
+
+namespace mfns {
+
+static int mg_op_of(int kind) {
+  switch (kind) {
+    case 0: return OP_STOKES_A;  // Stokes: multigrid on the A block
+    case 1: return OP_STOKES_A;
+    case 2: return OP_STAB_NS;
+    default: return OP_PMASS;
+  }
+}
+static int sys_op_of(int kind) {
+  switch (kind) {
+    case 0: return OP_STOKES;
+    case 1: return OP_STOKES_A;
+    case 2: return OP_STAB_NS;
+    default: return OP_PMASS;
+  }
+}
+
+std::unique_ptr<Problem> build_problem(const Forest& f, int kind, int k, const Physics& ph, int mg_order,
+                                       int coarse_stop_n, Budget* bud) {
+  auto p = std::make_unique<Problem>();
+  p->kind = kind;
+  p->dim = f.dim;
+  p->k = k;
+  p->phys = ph;
+  p->bud = bud;
+  const int mop = mg_op_of(kind);
+  if (mg_order == 0) mg_order = kind == 2 ? 2 : 1;
+  // (forest, degree) sequence of the hierarchy, finest first
+  std::vector<std::pair<Forest, int>> seq;
+  if (kind == 3) {
+    seq.push_back({f, k});
+  } else {
+    std::vector<Forest> fs{f};
+    while (forest_can_coarsen(fs.back(), coarse_stop_n)) fs.push_back(forest_coarsen(fs.back()));
+    if (mg_order == 1) {
+      for (int kk = k; kk >= 1; --kk) seq.push_back({f, kk});
+      for (size_t i = 1; i < fs.size(); ++i) seq.push_back({fs[i], 1});
+    } else {
+      for (auto& ff : fs) seq.push_back({ff, k});
+      for (int kk = k - 1; kk >= 1; --kk) seq.push_back({fs.back(), kk});
+    }
+  }
+  if (seq.size() > 32) throw Error(kErrUnsupported, "more than 32 multigrid levels");
+  for (auto& s : seq) {
+    auto lv = std::make_unique<OpLevel>();
+    build_oplevel(*lv, s.first, mop, s.second, ph, bud);
+    p->levels.push_back(std::move(lv));
+  }
+  for (size_t l = 0; l + 1 < p->levels.size(); ++l) {
+    auto t = std::make_unique<Transfer>();
+    build_transfer(*t, *p->levels[l], *p->levels[l + 1], bud);
+    p->transfers.push_back(std::move(t));
+  }
+  if (kind == 0) {
+    p->system = std::make_unique<OpLevel>();
+    build_oplevel(*p->system, f, OP_STOKES, k, ph, bud);
+    p->pmass = std::make_unique<OpLevel>();
+    build_oplevel(*p->pmass, f, OP_PMASS, k - 1, ph, bud);
+  }
+  return p;
+}
+
+static OpLevel& sys_of(Problem& p) { return p.system ? *p.system : *p.levels[0]; }
+
+void alloc_workspaces(Problem& p) {
+  Budget* bud = p.bud;
+  for (int prec = 0; prec < 2; ++prec) {
+    p.ws[prec].clear();
+    p.ws[prec].resize(p.levels.size());
+    for (size_t l = 0; l < p.levels.size(); ++l) {
+      const size_t b = p.levels[l]->n_dofs * esize(prec);
+      Workspace& w = p.ws[prec][l];
+      w.r.alloc(bud, b);
+      w.d.alloc(bud, b);
+      w.t.alloc(bud, b);
+      w.b.alloc(bud, b);
+      w.x.alloc(bud, b);
+    }
+  }
+  OpLevel& S = sys_of(p);
+  const int64_t n = S.n_dofs;
+  const int m = p.restart;
+  p.V.alloc(bud, (size_t)(m + 1) * n * 8);
+  p.Z.alloc(bud, (size_t)m * n * 8);
+  p.w.alloc(bud, n * 8);
+  p.tmp.alloc(bud, n * 8);
+  p.sys_r.alloc(bud, n * 8);
+  p.sys_z.alloc(bud, n * 8);
+  p.hvec.alloc(bud, 2 * kMaxDots * 8);
+  p.yvec.alloc(bud, kMaxDots * 8);
+  p.part.alloc(bud, (size_t)kRedBlocks * kMaxDots * 8);
+  p.scal.alloc(bud, 16 * 8);
+  std::vector<const double*> pv(m + 1), pz(m);
+  for (int j = 0; j <= m; ++j) pv[j] = p.V.as<double>() + (size_t)j * n;
+  for (int j = 0; j < m; ++j) pz[j] = p.Z.as<double>() + (size_t)j * n;
+  p.ptrV = upload(bud, pv);
+  p.ptrZ = upload(bud, pz);
+  p.mg_b32.alloc(bud, n * 4);
+  p.mg_x32.alloc(bud, n * 4);
+  if (p.kind == 0) {
+    const int64_t np = p.pmass->n_dofs;
+    const size_t es = 8;  // the Stokes preconditioner keeps fp64 and fp32 copies in separate buffers
+    p.cg_r.alloc(bud, np * es);
+    p.cg_z.alloc(bud, np * es);
+    p.cg_p.alloc(bud, np * es);
+    p.cg_q.alloc(bud, np * es);
+    p.cg_x.alloc(bud, np * es);
+    p.stokes_u_rhs.alloc(bud, n * es);
+    p.stokes_u_sol.alloc(bud, n * es);
+    p.pmass->dinv[0].alloc(bud, np * 8);
+    p.pmass->dinv[1].alloc(bud, np * 4);
+  }
+}
+
+static void level_dinv(Problem& p, OpLevel& lv, cudaStream_t s) {
+  const int64_t n = lv.n_dofs;
+  lv.dinv[0].alloc(p.bud, n * 8);
+  lv.dinv[1].alloc(p.bud, n * 4);
+  // the diagonal in the multigrid precision (fp32 mode never evaluates fp64 cell kernels here)
+  if (p.mg_precision == 1) {
+    oplevel_diag(lv, 1, lv.dinv[1].get(), s);
+    vrecip<float>(lv.dinv[1].as<float>(), lv.dinv[1].as<float>(), n, s);
+    vcast_f2d(lv.dinv[0].as<double>(), lv.dinv[1].as<float>(), n, s);
+  } else {
+    oplevel_diag(lv, 0, lv.dinv[0].get(), s);
+    vrecip<double>(lv.dinv[0].as<double>(), lv.dinv[0].as<double>(), n, s);
+    vcast_d2f(lv.dinv[1].as<float>(), lv.dinv[0].as<double>(), n, s);
+  }
+}
+
+void estimate_lambda(Problem& p, cudaStream_t s) {
+  // diagonals, then 20 power iterations on D^{-1} A (seed 1), lmax = 1.2 x estimate
+  for (auto& lv : p.levels) level_dinv(p, *lv, s);
+  if (p.kind == 0) {
+    OpLevel& pm = *p.pmass;
+    oplevel_diag(pm, 0, pm.dinv[0].get(), s);
+    vrecip<double>(pm.dinv[0].as<double>(), pm.dinv[0].as<double>(), pm.n_dofs, s);
+    vcast_d2f(pm.dinv[1].as<float>(), pm.dinv[0].as<double>(), pm.n_dofs, s);
+  }
+  const int prec = p.mg_precision;
+  for (size_t l = 0; l < p.levels.size(); ++l) {
+    OpLevel& lv = *p.levels[l];
+    if (lv.lmax > 0) continue;
+    const int64_t n = lv.n_dofs;
+    std::mt19937_64 rng(1);
+    std::uniform_real_distribution<double> U(-1.0, 1.0);
+    std::vector<double> v0(n);
+    for (auto& v : v0) v = U(rng);
+    Workspace& w = p.ws[prec][l];
+    if (prec == 0) {
+      MFNS_CUDA(cudaMemcpyAsync(w.x.get(), v0.data(), n * 8, cudaMemcpyHostToDevice, s));
+    } else {
+      std::vector<float> vf(v0.begin(), v0.end());
+      MFNS_CUDA(cudaMemcpyAsync(w.x.get(), vf.data(), n * 4, cudaMemcpyHostToDevice, s));
+      MFNS_CUDA(cudaStreamSynchronize(s));
+    }
+    double lam = 0.0;
+    double* d_out = p.scal.as<double>();
+    for (int it = 0; it < 20; ++it) {
+      oplevel_vmult(lv, prec, w.x.get(), w.t.get(), s);
+      double nv = 0, nw = 0;
+      if (prec == 0) {
+        vmul<double>(w.r.as<double>(), lv.dinv[0].as<double>(), w.t.as<double>(), n, s);
+        dot<double>(d_out, w.x.as<double>(), w.x.as<double>(), n, p.part.as<double>(), s);
+        dot<double>(d_out + 1, w.r.as<double>(), w.r.as<double>(), n, p.part.as<double>(), s);
+      } else {
+        vmul<float>(w.r.as<float>(), lv.dinv[1].as<float>(), w.t.as<float>(), n, s);
+        dot<float>(d_out, w.x.as<float>(), w.x.as<float>(), n, p.part.as<double>(), s);
+        dot<float>(d_out + 1, w.r.as<float>(), w.r.as<float>(), n, p.part.as<double>(), s);
+      }
+      double hv[2];
+      MFNS_CUDA(cudaMemcpyAsync(hv, d_out, 16, cudaMemcpyDeviceToHost, s));
+      MFNS_CUDA(cudaStreamSynchronize(s));
+      nv = std::sqrt(hv[0]);
+      nw = std::sqrt(hv[1]);
+      if (nv == 0 || nw == 0 || !std::isfinite(nw)) break;
+      lam = nw / nv;
+      if (prec == 0) {
+        vcopy<double>(w.x.as<double>(), w.r.as<double>(), n, s);
+        vscale<double>(w.x.as<double>(), 1.0 / nw, n, s);
+      } else {
+        vcopy<float>(w.x.as<float>(), w.r.as<float>(), n, s);
+        vscale<float>(w.x.as<float>(), (float)(1.0 / nw), n, s);
+      }
+    }
+    lv.lmax = 1.2 * lam;
+  }
+}
+
+// Dense LU inverse with partial pivoting (host, in place).
+static bool invert_dense(std::vector<double>& A, int64_t n) {
+  std::vector<double> I(n * n, 0.0);
+  for (int64_t i = 0; i < n; ++i) I[i * n + i] = 1.0;
+  for (int64_t c = 0; c < n; ++c) {
+    int64_t piv = c;
+    for (int64_t r = c + 1; r < n; ++r)
+      if (std::fabs(A[r * n + c]) > std::fabs(A[piv * n + c])) piv = r;
+    if (A[piv * n + c] == 0.0) return false;
+    if (piv != c)
+      for (int64_t j = 0; j < n; ++j) {
+        std::swap(A[c * n + j], A[piv * n + j]);
+        std::swap(I[c * n + j], I[piv * n + j]);
+      }
+    const double inv = 1.0 / A[c * n + c];
+    for (int64_t j = 0; j < n; ++j) {
+      A[c * n + j] *= inv;
+      I[c * n + j] *= inv;
+    }
+    for (int64_t r = 0; r < n; ++r) {
+      if (r == c) continue;
+      const double f = A[r * n + c];
+      if (f == 0.0) continue;
+      for (int64_t j = 0; j < n; ++j) {
+        A[r * n + j] -= f * A[c * n + j];
+        I[r * n + j] -= f * I[c * n + j];
+      }
+    }
+  }
+  A.swap(I);
+  return true;
+}
+
+void setup_coarse(Problem& p, cudaStream_t s) {
+  OpLevel& cl = *p.levels.back();
+  const int64_t n = cl.n_dofs;
+  p.coarse_n = n;
+  p.coarse_dense = n <= 4096;
+  if (!p.coarse_dense) return;
+  // assemble the coarse matrix column by column with the fp64 operator
+  std::vector<double> A(n * n), col(n);
+  Workspace& w = p.ws[0].back();
+  std::vector<double> e(n, 0.0);
+  for (int64_t j = 0; j < n; ++j) {
+    e[j] = 1.0;
+    MFNS_CUDA(cudaMemcpyAsync(w.x.get(), e.data(), n * 8, cudaMemcpyHostToDevice, s));
+    oplevel_vmult(cl, 0, w.x.get(), w.t.get(), s);
+    MFNS_CUDA(cudaMemcpyAsync(col.data(), w.t.get(), n * 8, cudaMemcpyDeviceToHost, s));
+    MFNS_CUDA(cudaStreamSynchronize(s));
+    e[j] = 0.0;
+    for (int64_t i = 0; i < n; ++i) A[i * n + j] = col[i];
+  }
+  // constant-pressure null space: add e e^T over the free pressure entries
+  if (cl.n_pres > 0 && (cl.op == OP_STAB_NS || cl.op == OP_STOKES)) {
+    const double v = 1.0 / (double)cl.n_pres;
+    for (int32_t i : cl.pres_host)
+      for (int32_t j : cl.pres_host) A[(int64_t)i * n + j] += v;
+  }
+  if (!invert_dense(A, n)) throw Error(kErrArg, "singular coarse matrix");
+  p.coarse_inv[0] = upload(p.bud, A);
+  std::vector<float> Af(A.begin(), A.end());
+  p.coarse_inv[1] = upload(p.bud, Af);
+}
+
+// ---------------------------------------------------------------------- smoothing
+template <typename T>
+static void smooth_t(Problem& p, int level, int prec, const T* b, T* x, bool x_is_zero, int degree, cudaStream_t s) {
+  OpLevel& lv = *p.levels[level];
+  Workspace& w = p.ws[prec][level];
+  const int64_t n = lv.n_dofs;
+  const T* dinv = lv.dinv[prec].as<T>();
+  T* d = w.d.as<T>();
+  T* t = w.t.as<T>();
+  const double lmax = lv.lmax, lmin = lmax / 20.0;
+  if (p.smoother == 1) {  // Jacobi relaxation
+    const T omega = (T)(2.0 / (lmin + lmax));
+    for (int it = 0; it < degree; ++it) {
+      if (it == 0 && x_is_zero) {
+        vcheby0<T>(x, d, b, dinv, omega, n, s);
+      } else {
+        oplevel_vmult(lv, prec, x, t, s);
+        vcheby<T>(x, d, b, t, dinv, T(0), omega, n, s);
+      }
+    }
+    return;
+  }
+  const double theta = 0.5 * (lmax + lmin), delta = 0.5 * (lmax - lmin), sigma = theta / delta;
+  double rho_old = 1.0 / sigma;
+  if (x_is_zero) {
+    vcheby0<T>(x, d, b, dinv, (T)(1.0 / theta), n, s);
+  } else {
+    oplevel_vmult(lv, prec, x, t, s);
+    vcheby<T>(x, d, b, t, dinv, T(0), (T)(1.0 / theta), n, s);
+  }
+  for (int j = 1; j < degree; ++j) {
+    oplevel_vmult(lv, prec, x, t, s);
+    const double rho = 1.0 / (2.0 * sigma - rho_old);
+    vcheby<T>(x, d, b, t, dinv, (T)(rho * rho_old), (T)(2.0 * rho / delta), n, s);
+    rho_old = rho;
+  }
+}
+
+void smooth(Problem& p, int level, int prec, const void* b, void* x, bool x_is_zero, cudaStream_t s) {
+  if (prec == 0)
+    smooth_t<double>(p, level, 0, (const double*)b, (double*)x, x_is_zero, p.smoother_degree, s);
+  else
+    smooth_t<float>(p, level, 1, (const float*)b, (float*)x, x_is_zero, p.smoother_degree, s);
+}
+
+template <typename T>
+static void coarse_solve(Problem& p, int prec, const T* b, T* x, cudaStream_t s) {
+  const int L = (int)p.levels.size() - 1;
+  if (p.coarse_dense) {
+    vgemv<T>(x, p.coarse_inv[prec].as<T>(), b, p.coarse_n, s);
+  } else {
+    smooth_t<T>(p, L, prec, b, x, true, p.coarse_cheby_degree, s);
+  }
+}
+
+template <typename T>
+static void vcycle_level(Problem& p, int prec, int l, const T* b, T* x, cudaStream_t s) {
+  const int L = (int)p.levels.size() - 1;
+  if (l == L) {
+    coarse_solve<T>(p, prec, b, x, s);
+    return;
+  }
+  OpLevel& lv = *p.levels[l];
+  Workspace& w = p.ws[prec][l];
+  Workspace& wc = p.ws[prec][l + 1];
+  const int64_t n = lv.n_dofs;
+  smooth_t<T>(p, l, prec, b, x, true, p.smoother_degree, s);
+  oplevel_vmult(lv, prec, x, w.t.get(), s);
+  vsub<T>(w.r.as<T>(), b, w.t.as<T>(), n, s);
+  transfer_restrict(*p.transfers[l], lv, *p.levels[l + 1], prec, w.r.get(), wc.b.get(), s);
+  vcycle_level<T>(p, prec, l + 1, wc.b.as<T>(), wc.x.as<T>(), s);
+  transfer_prolongate_add(*p.transfers[l], lv, *p.levels[l + 1], prec, wc.x.get(), x, s);
+  smooth_t<T>(p, l, prec, b, x, false, p.smoother_degree, s);
+}
+
+void vcycle(Problem& p, int prec, const void* b, void* x, cudaStream_t s) {
+  if (prec == 0)
+    vcycle_level<double>(p, 0, 0, (const double*)b, (double*)x, s);
+  else
+    vcycle_level<float>(p, 1, 0, (const float*)b, (float*)x, s);
+}
+
+// ---------------------------------------------------------------------- FGMRES
+static double host_dot(Problem& p, const double* a, const double* b, int64_t n, cudaStream_t s) {
+  double* d = p.scal.as<double>();
+  dot<double>(d, a, b, n, p.part.as<double>(), s);
+  double h;
+  MFNS_CUDA(cudaMemcpyAsync(&h, d, 8, cudaMemcpyDeviceToHost, s));
+  MFNS_CUDA(cudaStreamSynchronize(s));
+  return h;
+}
+
+template <typename T>
+static void project_pressure(OpLevel& S, T* x, double* scal, double* part, cudaStream_t s) {
+  if (S.n_pres == 0) return;
+  sum_idx<T>(scal + 8, x, S.pres.as<int32_t>(), S.n_pres, part, s);
+  sub_mean_idx<T>(x, S.pres.as<int32_t>(), S.n_pres, scal + 8, s);
+}
+
+// Stokes block preconditioner (Eq. 5) in precision T: in/out are T vectors of system length.
+template <typename T>
+static void stokes_block(Problem& p, int prec, const T* r, T* z, cudaStream_t s) {
+  OpLevel& S = *p.system;
+  OpLevel& M = *p.pmass;
+  const int64_t nu = S.n_main_dofs, np = M.n_dofs, n = S.n_dofs;
+  T* cx = p.cg_x.as<T>();
+  T* cr = p.cg_r.as<T>();
+  T* cz = p.cg_z.as<T>();
+  T* cp = p.cg_p.as<T>();
+  T* cq = p.cg_q.as<T>();
+  const T* dinv = M.dinv[prec].as<T>();
+  double* sc = p.scal.as<double>();
+  // z_p = -nu M_p^{-1} r_p by a fixed number of Jacobi-preconditioned CG steps from zero
+  vzero<T>(cx, np, s);
+  vcopy<T>(cr, r + nu, np, s);
+  vmul<T>(cz, dinv, cr, np, s);
+  vcopy<T>(cp, cz, np, s);
+  dot<T>(sc, cr, cz, np, p.part.as<double>(), s);
+  double rz;
+  MFNS_CUDA(cudaMemcpyAsync(&rz, sc, 8, cudaMemcpyDeviceToHost, s));
+  MFNS_CUDA(cudaStreamSynchronize(s));
+  for (int it = 0; it < p.cg_iterations && rz != 0.0; ++it) {
+    oplevel_vmult(M, prec, cp, cq, s);
+    dot<T>(sc, cp, cq, np, p.part.as<double>(), s);
+    double pq;
+    MFNS_CUDA(cudaMemcpyAsync(&pq, sc, 8, cudaMemcpyDeviceToHost, s));
+    MFNS_CUDA(cudaStreamSynchronize(s));
+    const double alpha = rz / pq;
+    vaxpy<T>(cx, (T)alpha, cp, np, s);
+    vaxpy<T>(cr, (T)(-alpha), cq, np, s);
+    vmul<T>(cz, dinv, cr, np, s);
+    dot<T>(sc, cr, cz, np, p.part.as<double>(), s);
+    double rz_new;
+    MFNS_CUDA(cudaMemcpyAsync(&rz_new, sc, 8, cudaMemcpyDeviceToHost, s));
+    MFNS_CUDA(cudaStreamSynchronize(s));
+    vaxpby<T>(cp, T(1), cz, (T)(rz_new / rz), np, s);
+    rz = rz_new;
+  }
+  // full = [0, z_p]; B z_p = velocity part of the Stokes operator applied to it
+  T* full = p.stokes_u_rhs.as<T>();
+  T* Bz = p.stokes_u_sol.as<T>();
+  vzero<T>(full, n, s);
+  vcopy<T>(full + nu, cx, np, s);
+  vscale<T>(full + nu, (T)(-p.phys.nu), np, s);
+  vcopy<T>(z + nu, full + nu, np, s);
+  oplevel_vmult(S, prec, full, Bz, s);
+  // velocity rhs r_u - B z_p, then one V-cycle on the A block
+  vsub<T>(Bz, r, Bz, nu, s);
+  vcycle_level<T>(p, prec, 0, Bz, z, s);
+}
+
+static void precondition(Problem& p, const double* v, double* z, cudaStream_t s) {
+  OpLevel& S = sys_of(p);
+  const int64_t n = S.n_dofs;
+  if (p.mg_precision == 0) {
+    if (p.kind == 0)
+      stokes_block<double>(p, 0, v, z, s);
+    else
+      vcycle_level<double>(p, 0, 0, v, z, s);
+  } else {
+    vcast_d2f(p.mg_b32.as<float>(), v, n, s);
+    if (p.kind == 0)
+      stokes_block<float>(p, 1, p.mg_b32.as<float>(), p.mg_x32.as<float>(), s);
+    else
+      vcycle_level<float>(p, 1, 0, p.mg_b32.as<float>(), p.mg_x32.as<float>(), s);
+    vcast_f2d(z, p.mg_x32.as<float>(), n, s);
+  }
+}
+
+int fgmres_solve(Problem& p, const double* b_in, double* x, double* relres, bool* converged, cudaStream_t s) {
+  OpLevel& S = sys_of(p);
+  const int64_t n = S.n_dofs;
+  const int m = p.restart;
+  double* b = p.sys_r.as<double>();   // projected right-hand side
+  double* r = p.tmp.as<double>();
+  double* w = p.w.as<double>();
+  double* V = p.V.as<double>();
+  double* Z = p.Z.as<double>();
+  const double** Vp = (const double**)p.ptrV.as<const double*>();
+  const double** Zp = (const double**)p.ptrZ.as<const double*>();
+  vcopy<double>(b, b_in, n, s);
+  project_pressure<double>(S, b, p.scal.as<double>(), p.part.as<double>(), s);
+  vzero<double>(x, n, s);
+  const double bnorm = std::sqrt(host_dot(p, b, b, n, s));
+  *converged = true;
+  *relres = 0.0;
+  if (bnorm == 0.0) return 0;
+  vcopy<double>(r, b, n, s);
+  int it = 0;
+  std::vector<double> H((m + 1) * m), cs(m), sn(m), g(m + 1), h(m + 2);
+  while (true) {
+    const double beta = std::sqrt(host_dot(p, r, r, n, s));
+    *relres = beta / bnorm;
+    if (beta <= p.tol * bnorm) break;
+    if (it >= p.maxit) {
+      *converged = false;
+      break;
+    }
+    vcopy<double>(V, r, n, s);
+    vscale<double>(V, 1.0 / beta, n, s);
+    std::fill(g.begin(), g.end(), 0.0);
+    g[0] = beta;
+    int jdone = 0;
+    for (int j = 0; j < m; ++j) {
+      double* zj = Z + (size_t)j * n;
+      precondition(p, V + (size_t)j * n, zj, s);
+      project_pressure<double>(S, zj, p.scal.as<double>(), p.part.as<double>(), s);
+      oplevel_vmult(S, 0, zj, w, s);
+      // classical Gram--Schmidt, two passes
+      double* hd = p.hvec.as<double>();
+      multidot(hd, nullptr, w, j + 1, n, p.part.as<double>(), Vp, s);
+      multi_axpy(w, Vp, hd, j + 1, n, s);
+      multidot(hd + kMaxDots, nullptr, w, j + 1, n, p.part.as<double>(), Vp, s);
+      multi_axpy(w, Vp, hd + kMaxDots, j + 1, n, s);
+      std::vector<double> hh(2 * kMaxDots);
+      MFNS_CUDA(cudaMemcpyAsync(hh.data(), hd, 2 * kMaxDots * 8, cudaMemcpyDeviceToHost, s));
+      const double hn = std::sqrt(host_dot(p, w, w, n, s));
+      for (int i = 0; i <= j; ++i) H[i * m + j] = hh[i] + hh[kMaxDots + i];
+      H[(j + 1) * m + j] = hn;
+      if (hn > 0) {
+        vcopy<double>(V + (size_t)(j + 1) * n, w, n, s);
+        vscale<double>(V + (size_t)(j + 1) * n, 1.0 / hn, n, s);
+      }
+      for (int i = 0; i < j; ++i) {
+        const double t = cs[i] * H[i * m + j] + sn[i] * H[(i + 1) * m + j];
+        H[(i + 1) * m + j] = -sn[i] * H[i * m + j] + cs[i] * H[(i + 1) * m + j];
+        H[i * m + j] = t;
+      }
+      const double den = std::hypot(H[j * m + j], H[(j + 1) * m + j]);
+      cs[j] = H[j * m + j] / den;
+      sn[j] = H[(j + 1) * m + j] / den;
+      H[j * m + j] = den;
+      H[(j + 1) * m + j] = 0.0;
+      g[j + 1] = -sn[j] * g[j];
+      g[j] = cs[j] * g[j];
+      ++it;
+      jdone = j + 1;
+      if (std::fabs(g[j + 1]) <= p.tol * bnorm || it >= p.maxit) break;
+    }
+    std::vector<double> y(jdone);
+    for (int i = jdone - 1; i >= 0; --i) {
+      double sacc = g[i];
+      for (int k2 = i + 1; k2 < jdone; ++k2) sacc -= H[i * m + k2] * y[k2];
+      y[i] = sacc / H[i * m + i];
+    }
+    MFNS_CUDA(cudaMemcpyAsync(p.yvec.get(), y.data(), jdone * 8, cudaMemcpyHostToDevice, s));
+    multi_axpy_add(x, Zp, p.yvec.as<double>(), jdone, n, s);
+    MFNS_CUDA(cudaStreamSynchronize(s));
+    oplevel_vmult(S, 0, x, w, s);
+    vsub<double>(r, b, w, n, s);
+  }
+  return it;
+}
+
+}  // namespace mfns

@@ -1,0 +1,57 @@
+// Vector kernels used by the smoothers, transfers and Krylov solvers.
+// Reductions are deterministic: a fixed grid writes per-block partial sums that
+// a single block adds in a fixed order.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+namespace mfns {
+
+constexpr int kRedBlocks = 304;   // 2 x 152 SMs; fixed for determinism
+constexpr int kRedThreads = 256;
+constexpr int kMaxDots = 32;      // vectors per multi-dot
+
+template <typename T> void vzero(T* x, int64_t n, cudaStream_t s);
+template <typename T> void vcopy(T* y, const T* x, int64_t n, cudaStream_t s);
+template <typename T> void vaxpy(T* y, T a, const T* x, int64_t n, cudaStream_t s);          // y += a x
+template <typename T> void vaxpby(T* y, T a, const T* x, T b, int64_t n, cudaStream_t s);   // y = a x + b y
+template <typename T> void vsub(T* r, const T* b, const T* ax, int64_t n, cudaStream_t s);   // r = b - ax
+template <typename T> void vscale(T* y, T a, int64_t n, cudaStream_t s);
+void vcast_d2f(float* y, const double* x, int64_t n, cudaStream_t s);
+void vcast_f2d(double* y, const float* x, int64_t n, cudaStream_t s);
+// y[idx[i]] = x[idx[i]]
+template <typename T> void vcopy_idx(T* y, const T* x, const int32_t* idx, int64_t n, cudaStream_t s);
+// y[idx[i]] = v
+template <typename T> void vset_idx(T* y, T v, const int32_t* idx, int64_t n, cudaStream_t s);
+// hanging entries: x[dof[i]] = sum_{j in ptr[i]..ptr[i+1]} w[j] x[src[j]]
+template <typename T>
+void vdistribute(T* x, const int32_t* dof, const int32_t* ptr, const int32_t* src, const T* w, int64_t n,
+                 cudaStream_t s);
+// Chebyshev step (Saad, Alg. 12.1 on D^-1 A): d = c1 d + c2 dinv (b - ax); x += d
+template <typename T>
+void vcheby(T* x, T* d, const T* b, const T* ax, const T* dinv, T c1, T c2, int64_t n, cudaStream_t s);
+// first step from a zero iterate: d = c2 dinv b; x = d
+template <typename T> void vcheby0(T* x, T* d, const T* b, const T* dinv, T c2, int64_t n, cudaStream_t s);
+// y = dinv * x (pointwise)
+template <typename T> void vmul(T* y, const T* dinv, const T* x, int64_t n, cudaStream_t s);
+// y = 1 / x
+template <typename T> void vrecip(T* y, const T* x, int64_t n, cudaStream_t s);
+// dense gemv y = M x (row-major n x n)
+template <typename T> void vgemv(T* y, const T* M, const T* x, int64_t n, cudaStream_t s);
+
+// Deterministic reductions into device scratch `part` (kRedBlocks * kMaxDots doubles) and
+// the final result `out` (device, double): out[k] = sum_i V_k[i] w[i], k < m.
+void multidot(double* out, const double* const* V, const double* w, int m, int64_t n, double* part,
+              const double** Vdev, cudaStream_t s);
+template <typename T> void dot(double* out, const T* a, const T* b, int64_t n, double* part, cudaStream_t s);
+// w -= sum_k h[k] V_k (h on device)
+void multi_axpy(double* w, const double* const* Vdev, const double* h, int m, int64_t n, cudaStream_t s);
+// x += sum_k y[k] Z_k (y on device)
+void multi_axpy_add(double* x, const double* const* Zdev, const double* y, int m, int64_t n, cudaStream_t s);
+// sum of x over idx (device double result)
+template <typename T> void sum_idx(double* out, const T* x, const int32_t* idx, int64_t n, double* part, cudaStream_t s);
+// x[idx] -= (*mean_sum) / n
+template <typename T> void sub_mean_idx(T* x, const int32_t* idx, int64_t n, const double* sum, cudaStream_t s);
+
+}  // namespace mfns

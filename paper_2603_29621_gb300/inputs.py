@@ -1,0 +1,27 @@
+"""Seeded synthetic inputs shared by the tests, the benchmark and the oracle checks.
+
+This module only draws random numbers and maps vectors between the library's
+DoF order and another order by support-point coordinates; it holds none of the
+method's arithmetic.
+"""
+import numpy as np
+
+SEED_SRC = 0      # source vectors
+SEED_LAMBDA = 1   # eigenvalue-estimate start vectors (inside the library)
+SEED_SERVE = 2    # serving request stream
+
+
+def uniform_vector(n, seed=SEED_SRC, low=-1.0, high=1.0):
+    """PCG64 U(low, high) vector of length n (float64)."""
+    return np.random.default_rng(seed).uniform(low, high, n)
+
+
+def match_dofs(xa, fa, xb, fb, digits=9):
+    """Permutation perm with (xa[perm[i]], fa[perm[i]]) == (xb[i], fb[i]) (coordinates rounded)."""
+    key = lambda x, f: [tuple(np.round(r, digits)) + (int(g),) for r, g in zip(x, f)]
+    ka = key(xa, fa)
+    where = {k: i for i, k in enumerate(ka)}
+    if len(where) != len(ka):
+        raise ValueError("duplicate support points")
+    perm = np.array([where[k] for k in key(xb, fb)], dtype=np.int64)
+    return perm
