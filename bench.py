@@ -1,0 +1,320 @@
+#!/usr/bin/env python
+"""Benchmark of the matrix-free stabilised Navier--Stokes operator (GB300).
+
+Workload (one step): one application of the Newton-linearised SUPG/PSPG BDF2
+Navier--Stokes operator, equal-order Q2Q2 on a uniform 64^3 hexahedral mesh of
+the unit cube (129^3 nodes x 4 fields = 8,586,756 DoFs), nu = 1e-2, dt = 1e-2,
+frozen Taylor--Green state, on a seeded U(-1,1) vector; FP32 arithmetic.
+Alongside: the FP64 apply, a degree-3 Chebyshev--Jacobi sweep and an FP32
+V-cycle of the same problem, the end-to-end apply through the public API with
+host buffers, clocks, the roofline of the cell kernel and the CPU oracle.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--n 64]
+Multi-GPU (torchrun): every rank runs an independent replica (no collective on
+the data path); value = DoFs processed by all ranks / max time over ranks.
+"""
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "DoF/s stab-NS Q2 vmult; solves/s + p50/p99 latency, FP32-MG vs FP64 @1e-8"
+UNIT = "DoF/s"
+FLOP_PER_CELL = 22700.0          # algorithmic flops per Q2Q2 cell apply (frozen state recomputed)
+FP32_LANES, N_SM, SM_MHZ_MAX = 128, 152, 2070.0
+CPU_SAMPLE_N = 12                # oracle sample: 12^3 cells of the same operator
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=64)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--vmult-only", action="store_true", help="time only the FP32 apply (profiling runs)")
+    return ap.parse_args()
+
+
+def dist_setup(gpus):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+class Clocks:
+    """nvidia-smi sampler during the timed region."""
+
+    def __init__(self, device):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(device), f"--query-gpu={q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except FileNotFoundError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        self.p.wait()
+        self.f.seek(0)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f.read().strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.f.name)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def kernel_src_hash():
+    h = hashlib.sha256()
+    for f in ("op_apply.cuh", "op_kernel.cuh", "op_launch.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2603_29621_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic():
+    """DRAM bytes per launch of the FP32 structured cell kernel from the committed ncu summary,
+    or None when the kernel sources changed since the capture."""
+    path = os.path.join(ROOT, "profiles", "op_kernel_stabns_q2_fp32.md")
+    if not os.path.exists(path):
+        return None
+    vals = {}
+    for line in open(path):
+        if line.startswith("- ") and ":" in line:
+            k, v = line[2:].split(":", 1)
+            vals[k.strip()] = v.strip()
+    if vals.get("kernel_source_sha256_16") != kernel_src_hash():
+        return None
+    try:
+        return float(vals["dram_bytes_per_full_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+def cpu_baseline(seconds=10.0):
+    """The oracle (assembled CSR, scipy, one thread) on a 16^3-cell sample of the same operator."""
+    from oracle import assemble, mesh
+    from paper_2603_29621_gb300 import inputs
+
+    t0 = time.perf_counter()
+    op = assemble.Problem(mesh.uniform(3, CPU_SAMPLE_N), "stab_ns", 2, nu=1e-2, dt=1e-2)
+    A = op.assemble()
+    t_asm = time.perf_counter() - t0
+    x = inputs.uniform_vector(A.shape[0])
+    y = A @ x
+    reps, t0 = 0, time.perf_counter()
+    while time.perf_counter() - t0 < seconds:
+        y = A @ x
+        reps += 1
+    dt = time.perf_counter() - t0
+    return {"value": A.shape[0] * reps / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": (f"oracle vmult (scipy CSR SpMV, 1 thread) on {CPU_SAMPLE_N}^3 Q2Q2 cells of the same "
+                       f"operator ({A.shape[0]} DoFs, {A.nnz} nnz), {reps} products in {dt:.1f} s; "
+                       f"assembly {t_asm:.1f} s not timed"),
+            "ms_per_step": 1e3 * dt / reps, "n_dofs": int(A.shape[0])}
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    from oracle import assemble, mesh
+    from paper_2603_29621_gb300 import inputs
+
+    op = assemble.Problem(mesh.uniform(3, CPU_SAMPLE_N), "stab_ns", 2, nu=1e-2, dt=1e-2)
+    A = op.assemble()
+    x = inputs.uniform_vector(A.shape[0])
+    for _ in range(args.warmup):
+        A @ x
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        A @ x
+    dt = time.perf_counter() - t0
+    val = A.shape[0] * args.steps / dt
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": 0,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": f"stab-NS Q2Q2 vmult on {CPU_SAMPLE_N}^3 cells (bounded sample of the 64^3 "
+                                   "workload), nu=1e-2, dt=1e-2, Taylor-Green frozen state"},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"oracle scipy CSR SpMV on {CPU_SAMPLE_N}^3 Q2Q2 cells, {A.shape[0]} DoFs"},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, world, rank, local):
+    import torch
+
+    import __graft_entry__ as g
+    from paper_2603_29621_gb300 import _lib as L
+    from paper_2603_29621_gb300 import api, inputs
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    g.build()
+    dev = torch.device("cuda", local)
+    ctx = api.Context(local)
+    n = args.n
+    m = api.Mesh(ctx, 3, n)
+    prob = api.Problem(ctx, m, kind=L.STAB_NS, degree=2, nu=1e-2, dt=1e-2, smoother_degree=3,
+                       mg_precision=L.FP32)
+    ndof = prob.info.n_dofs
+    ncell = prob.info.n_cells
+    x64 = torch.tensor(inputs.uniform_vector(ndof), device=dev)
+    src32, src64 = x64.float(), x64
+    dst32, dst64 = torch.empty_like(src32), torch.empty_like(src64)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2 (129 MB)
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+            torch.cuda.synchronize()
+
+    def timed(fn, steps, warmup, nvtx=None):
+        for _ in range(warmup):
+            fn()
+        barrier()
+        if nvtx:
+            torch.cuda.nvtx.range_push(nvtx)
+        total = 0.0
+        for s in range(steps):
+            flush.fill_(float(s))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            total += e0.elapsed_time(e1)
+        if nvtx:
+            torch.cuda.nvtx.range_pop()
+        barrier()
+        return total / steps  # ms per step
+
+    # ---- headline: FP32 vmult
+    clocks = Clocks(local)
+    prob.kernel_timing(1)
+    ms32 = timed(lambda: prob.vmult(src32, dst32), args.steps, args.warmup, nvtx="timed_vmult_fp32")
+    kms, klaunch = prob.kernel_timing(2)
+    prob.kernel_timing(0)
+    clk = clocks.stop()
+    # the warm-up launches were recorded as well: use the average over all recorded launches
+    avg_launch_ms = kms / max(klaunch, 1)
+    launches_per_step = klaunch // (args.steps + args.warmup)
+    if args.vmult_only:
+        if rank == 0:
+            print(json.dumps({"vmult_fp32_ms": ms32, "dofs_per_s": world * ndof / (ms32 * 1e-3),
+                              "avg_launch_ms": avg_launch_ms, "launches_per_step": launches_per_step}))
+        return
+    # ---- FP64 vmult, Chebyshev-3 sweep, V-cycle (FP32)
+    steps64 = max(3, args.steps // 4)
+    ms64 = timed(lambda: prob.vmult(src64, dst64), steps64, 3)
+    b32 = src32.clone()
+    xs = torch.zeros_like(b32)
+    ms_cheb = timed(lambda: prob.smooth(0, b32, xs, x_is_zero=False), max(3, args.steps // 2), 3)
+    ms_vc = timed(lambda: prob.vcycle(b32, xs), max(3, args.steps // 4), 3)
+    # ---- end to end through the public API with host buffers (pinned)
+    h_src = torch.empty(ndof, dtype=torch.float32, pin_memory=True)
+    h_src.copy_(src32.cpu())
+    h_dst = torch.empty(ndof, dtype=torch.float32, pin_memory=True)
+
+    def e2e_step():
+        src32.copy_(h_src, non_blocking=True)
+        prob.vmult(src32, dst32)
+        h_dst.copy_(dst32, non_blocking=True)
+
+    ms_e2e = timed(e2e_step, args.steps, args.warmup)
+    # ---- max over ranks
+    tt = torch.tensor([ms32, ms64, ms_cheb, ms_vc, ms_e2e], device=dev, dtype=torch.float64)
+    if world > 1:
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+    ms32, ms64, ms_cheb, ms_vc, ms_e2e = tt.tolist()
+    if rank != 0:
+        return
+    value = world * ndof / (ms32 * 1e-3)
+    cells_per_launch = ncell / launches_per_step if launches_per_step else ncell
+    flops_launch = FLOP_PER_CELL * cells_per_launch
+    peak_alu = N_SM * FP32_LANES * 2 * SM_MHZ_MAX * 1e6 / 1e12    # TFLOP/s
+    achieved = flops_launch / (avg_launch_ms * 1e-3) / 1e12
+    traffic = ncu_traffic()
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    alg_bytes = 12 * (ndof // 4) * 4                               # src 4 + dst 4 + frozen 4 fields, fp32
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms32, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"stab-NS Q2Q2 vmult, uniform {n}^3 hex unit cube, nu=1e-2, dt=1e-2 (BDF2), "
+                               "Taylor-Green frozen state, seeded U(-1,1) input",
+                   "n_cells": ncell, "n_dofs": ndof, "parallelism": f"replicas x{world}",
+                   "l2": "flushed between timed steps (512 MiB write)"},
+        "clocks": clk,
+        "gpu_launches": launches_per_step * args.steps + args.steps,  # cell-kernel colours + constrained-row copy
+        "e2e": {"value": world * ndof / (ms_e2e * 1e-3), "unit": UNIT, "h2d_bytes_per_step": ndof * 4,
+                "d2h_bytes_per_step": ndof * 4},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_alu, "unit": "TFLOP/s",
+                     "frac": achieved / peak_alu, "traffic": traffic,
+                     "kernel": "op_kernel<3,2,STAB_NS,float,structured>",
+                     "flop_per_cell": FLOP_PER_CELL, "cells_per_launch": cells_per_launch,
+                     "avg_launch_ms": avg_launch_ms,
+                     "hbm_equiv": {"achieved_gbs": alg_bytes / (ms32 * 1e-3) / 1e9, "peak_gbs": hbm_peak,
+                                   "frac": alg_bytes / (ms32 * 1e-3) / 1e9 / hbm_peak,
+                                   "alg_bytes_per_apply": alg_bytes}},
+        "fp64": {"value": world * ndof / (ms64 * 1e-3), "unit": UNIT, "ms_per_apply": ms64},
+        "chebyshev3_fp32": {"ms_per_sweep": ms_cheb, "dofs_per_s": world * ndof / (ms_cheb * 1e-3)},
+        "vcycle_fp32": {"ms": ms_vc, "levels": prob.info.n_levels},
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        cb = cpu_baseline()
+        cb.pop("ms_per_step", None)
+        cb.pop("n_dofs", None)
+        line["cpu_baseline"] = cb
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_setup(args.gpus)
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        return
+    run_ours(args, world, rank, local)
+
+
+if __name__ == "__main__":
+    main()

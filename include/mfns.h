@@ -172,6 +172,12 @@ int mfns_diagonal(mfns_problem* p, int which, int precision, void* diag, void* s
 /* Hanging entries of x from their masters (x_h = sum_j w_hj x_j), Dirichlet entries kept. */
 int mfns_apply_constraints(mfns_problem* p, int which, int precision, void* x, void* stream);
 
+/* Per-kernel timing of the operator-kernel launches of `which` with CUDA events recorded on
+ * the launching stream: mode 1 = reset and enable, 0 = disable, 2 = read (synchronises on the
+ * recorded events; writes the summed kernel time in ms and the number of timed launches,
+ * then resets).  The timed launches are the colour launches of the cell kernel only. */
+int mfns_kernel_timing(mfns_problem* p, int which, int mode, double* total_ms, int64_t* launches);
+
 /* ---- multigrid ----------------------------------------------------------------------------- */
 /* One smoothing step on level `level`: Chebyshev of the problem's degree (or the Jacobi
  * relaxation) around point Jacobi, starting from x (x_is_zero = 1 skips the first product). */

@@ -146,6 +146,12 @@ class Problem:
         L.check(self.lib.mfns_diagonal(self.h, which, prec, _ptr(diag), _stream(stream)))
         return diag
 
+    def kernel_timing(self, mode, which=L.OP_SYSTEM):
+        """mode 1: reset+enable, 0: disable, 2: read -> (total kernel ms, launches)."""
+        ms, n = C.c_double(), C.c_int64()
+        L.check(self.lib.mfns_kernel_timing(self.h, which, mode, C.byref(ms), C.byref(n)))
+        return ms.value, n.value
+
     def apply_constraints(self, x, which=L.OP_SYSTEM, stream=None):
         prec = L.FP64 if x.dtype == torch.float64 else L.FP32
         L.check(self.lib.mfns_apply_constraints(self.h, which, prec, _ptr(x), _stream(stream)))

@@ -219,6 +219,24 @@ int mfns_vmult(mfns_problem* p, int which, int prec, const void* src, void* dst,
   API_END
 }
 
+int mfns_kernel_timing(mfns_problem* p, int which, int mode, double* total_ms, int64_t* launches) {
+  API_BEGIN
+  OpLevel* lv = p ? select_op(p, which) : nullptr;
+  if (!lv || mode < 0 || mode > 2) return fail(MFNS_ERR_ARG, "bad arguments");
+  MFNS_CUDA(cudaSetDevice(p->ctx->device));
+  KernelTimer& t = *lv->timer;
+  if (mode == 1) {
+    t.read_ms(nullptr);
+    t.enabled = true;
+  } else if (mode == 0) {
+    t.enabled = false;
+  } else {
+    const double ms = t.read_ms(launches);
+    if (total_ms) *total_ms = ms;
+  }
+  API_END
+}
+
 int mfns_diagonal(mfns_problem* p, int which, int prec, void* diag, void* stream) {
   API_BEGIN
   OpLevel* lv = p ? select_op(p, which) : nullptr;

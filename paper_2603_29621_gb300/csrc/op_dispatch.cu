@@ -48,6 +48,36 @@ static void dispatch(const OpLaunch& L, const T* s, T* d, bool diag, cudaStream_
   throw Error(kErrUnsupported, "unsupported (dim, degree, operator) combination");
 }
 
+void KernelTimer::record_pair_begin(cudaStream_t s) {
+  if (used + 2 > ev.size()) {
+    for (int i = 0; i < 64; ++i) {
+      cudaEvent_t e;
+      MFNS_CUDA(cudaEventCreate(&e));
+      ev.push_back(e);
+    }
+  }
+  MFNS_CUDA(cudaEventRecord(ev[used], s));
+}
+void KernelTimer::record_pair_end(cudaStream_t s) {
+  MFNS_CUDA(cudaEventRecord(ev[used + 1], s));
+  used += 2;
+}
+double KernelTimer::read_ms(int64_t* launches) {
+  double total = 0.0;
+  for (size_t i = 0; i + 1 < used; i += 2) {
+    MFNS_CUDA(cudaEventSynchronize(ev[i + 1]));
+    float ms = 0.f;
+    MFNS_CUDA(cudaEventElapsedTime(&ms, ev[i], ev[i + 1]));
+    total += ms;
+  }
+  if (launches) *launches = (int64_t)(used / 2);
+  used = 0;
+  return total;
+}
+KernelTimer::~KernelTimer() {
+  for (cudaEvent_t e : ev) cudaEventDestroy(e);
+}
+
 void op_apply(const OpLaunch& L, int prec, const void* src, void* dst, bool diag, cudaStream_t s) {
   if (prec == 0)
     dispatch<double>(L, static_cast<const double*>(src), static_cast<double*>(dst), diag, s);

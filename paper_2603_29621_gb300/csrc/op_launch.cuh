@@ -68,6 +68,7 @@ void op_launch(const OpLaunch& L, const T* src, T* dst, bool diag, cudaStream_t 
     }
     if (ncell <= 0) continue;
     const unsigned grid = (unsigned)((ncell + cells_per_block - 1) / cells_per_block);
+    if (L.timer && L.timer->enabled) L.timer->record_pair_begin(s);
     if (structured) {
       op_kernel<DIM, K, OP, T, true, false><<<grid, kOpWarps * 32, smem, s>>>(a);
     } else if (diag) {
@@ -76,6 +77,7 @@ void op_launch(const OpLaunch& L, const T* src, T* dst, bool diag, cudaStream_t 
       op_kernel<DIM, K, OP, T, false, false><<<grid, kOpWarps * 32, smem, s>>>(a);
     }
     MFNS_CUDA(cudaGetLastError());
+    if (L.timer && L.timer->enabled) L.timer->record_pair_end(s);
   }
 }
 

@@ -8,6 +8,17 @@
 
 namespace mfns {
 
+// CUDA-event timer of the operator-kernel launches of one level (per-kernel tracing).
+struct KernelTimer {
+  bool enabled = false;
+  std::vector<cudaEvent_t> ev;   // pairs (start, stop)
+  size_t used = 0;               // events recorded since the last read
+  void record_pair_begin(cudaStream_t s);
+  void record_pair_end(cudaStream_t s);
+  double read_ms(int64_t* launches);  // synchronises, sums and resets
+  ~KernelTimer();
+};
+
 struct OpLaunch {
   int dim = 3, k = 2, op = 0;        // main-field degree k, op = OpKind
   bool structured = false;          // uniform mesh with lexicographic numbering
@@ -28,6 +39,7 @@ struct OpLaunch {
   // 1D tables in double (converted to the kernel precision at launch)
   int Q = 3, N = 3, NP = 3;
   std::vector<double> S, Sp, D, D2, W, P, Pp;
+  KernelTimer* timer = nullptr;     // optional per-launch timing
 };
 
 // Fill the 1D tables of `L` for its degree (needs L.dim, L.k, L.op).

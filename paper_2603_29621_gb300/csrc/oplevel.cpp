@@ -84,6 +84,7 @@ void build_oplevel(OpLevel& lv, const Forest& f, int op, int k, const Physics& p
   L.div_sign = ph.div_sign;
   L.terms = ph.terms;
   fill_tables(L);
+  L.timer = lv.timer.get();
 
   // cell tables in colour order
   const int nb = lv.nu.nb;

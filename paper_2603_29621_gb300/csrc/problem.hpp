@@ -40,6 +40,7 @@ struct OpLevel {
   // smoother
   DevBuf dinv[2];
   double lmax = 0.0;
+  std::unique_ptr<KernelTimer> timer = std::make_unique<KernelTimer>();
   size_t bytes() const;
 };
 
