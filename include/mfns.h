@@ -183,6 +183,20 @@ int mfns_kernel_timing(mfns_problem* p, int which, int mode, double* total_ms, i
  * relaxation) around point Jacobi, starting from x (x_is_zero = 1 skips the first product). */
 int mfns_smooth(mfns_problem* p, int level, int precision, const void* b, void* x, int x_is_zero,
                 void* stream);
+/* Same smoothing step as mfns_smooth, for callers that must not allocate device memory
+ * when they call in -- for example code running while a stream is being captured into a
+ * CUDA graph, or a service that forbids cudaMalloc/cudaFree after start-up -- and that
+ * should not depend on per-call workspace.  The paper has no counterpart; this is an
+ * operational variant.  Its two scratch vectors (the Chebyshev direction and the operator
+ * product) live in one fixed device array of 16 MiB that every GPU loading the library
+ * holds until exit, so the level may have at most 1,048,576 entries (larger levels are
+ * rejected with MFNS_ERR_ARG and a message).  The call performs no cudaMalloc/cudaFree.
+ * The first call on a device looks up that array's device address (cudaGetSymbolAddress);
+ * make that first call before any stream capture.  All calls share the array and it keeps
+ * the last call's contents: calls whose GPU work overlaps in time (different streams,
+ * different problems) race on it and must be serialised by the caller. */
+int mfns_smooth_noalloc(mfns_problem* p, int level, int precision, const void* b, void* x, int x_is_zero,
+                        void* stream);
 /* Transfers between level `level` (fine) and level+1 (coarse), Eq. 4:
  * fine += P coarse;  coarse = P^T fine. */
 int mfns_prolongate_add(mfns_problem* p, int level, int precision, const void* coarse, void* fine,

@@ -5,6 +5,7 @@
 #include <cstring>
 #include <string>
 
+#include "capi_types.hpp"
 #include "problem.hpp"
 #include "vec.hpp"
 
@@ -14,25 +15,16 @@ bool op_supported(int dim, int k, int op);
 using namespace mfns;
 static bool op_supported_kind(int dim, int kind, int k);
 
-struct mfns_ctx {
-  int device = 0;
-  Budget budget;
-};
-struct mfns_mesh {
-  mfns_ctx* ctx = nullptr;
-  Forest forest;
-};
-struct mfns_problem {
-  mfns_ctx* ctx = nullptr;
-  std::unique_ptr<Problem> p;
-};
-
 static thread_local std::string g_err;
 
 static int fail(int code, const std::string& msg) {
   g_err = msg;
   return code;
 }
+
+namespace mfns {
+int capi_fail(int code, const char* msg) { return fail(code, msg); }
+}  // namespace mfns
 
 #define API_BEGIN try {
 #define API_END                                                      \
