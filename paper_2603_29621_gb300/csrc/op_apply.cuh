@@ -11,6 +11,28 @@ struct Team {
   static constexpr int TPC = ipow(Q, DIM - 1);   // lanes per cell
   static constexpr int CPW = 32 / TPC;           // cells per warp
   static constexpr int BUF = ipow(Q, DIM);       // elements per team buffer
+  static constexpr int NBUF = 3;                 // buffers per team
+  // Team stride padded so that the teams of a warp start TPC banks apart: lanes of different
+  // teams touching the same relative element then hit disjoint banks.
+  template <typename T>
+  __host__ __device__ static constexpr int stride() {
+    constexpr int w = sizeof(T) / 4, m = 32 / w;
+    return NBUF * BUF + (((TPC - NBUF * BUF) % m) + m) % m;
+  }
+};
+
+// Minimum resident blocks per SM for the register allocator (occupancy vs spills), per
+// instantiation; 1 lets the compiler use up to 255 registers.
+template <int DIM, int K, int OP, typename T>
+struct OpMinBlocks {
+  static constexpr int value = 1;
+};
+#ifndef MFNS_STABNS_Q2_F32_MINBLOCKS
+#define MFNS_STABNS_Q2_F32_MINBLOCKS 4
+#endif
+template <>
+struct OpMinBlocks<3, 2, OP_STAB_NS, float> {
+  static constexpr int value = MFNS_STABNS_Q2_F32_MINBLOCKS;
 };
 
 template <int OP, int DIM, int N, int NP>
@@ -32,7 +54,7 @@ __device__ __forceinline__ int64_t structured_node(int n, const int cc[3], int a
 }
 
 template <int DIM, int K, int OP, typename T, bool STRUCT, bool DIAG>
-__global__ void __launch_bounds__(kOpWarps * 32)
+__global__ void __launch_bounds__(kOpWarps * 32, OpMinBlocks<DIM, K, OP, T>::value)
 op_kernel(const OpArgs<T, K + 1, K + 1, (OP == OP_STOKES ? K : K + 1)> args) {
   constexpr int Q = K + 1, N = K + 1, NP = OP == OP_STOKES ? K : K + 1;
   using Tr = OpTraits<OP, DIM>;
@@ -53,7 +75,7 @@ op_kernel(const OpArgs<T, K + 1, K + 1, (OP == OP_STOKES ? K : K + 1)> args) {
   if (!lane_active) team = TM::CPW;  // dummy team for the spare lanes
   const int ti = tid % Q;
   const int tj = DIM == 3 ? tid / Q : 0;
-  T* buf0 = smem + ((size_t)(warp * (TM::CPW + 1) + team) * NBUF) * BUF;
+  T* buf0 = smem + (size_t)(warp * (TM::CPW + 1) + team) * TM::template stride<T>();
   T* buf1 = buf0 + BUF;
   T* buf2 = buf1 + BUF;
 
@@ -151,14 +173,65 @@ op_kernel(const OpArgs<T, K + 1, K + 1, (OP == OP_STOKES ? K : K + 1)> args) {
 #pragma unroll
   for (int c = 0; c < NP; ++c) daccp[c] = 0;
 
+  // vmult: issue the loads of src and of the dst values to be updated together with the
+  // frozen state, so that each cell waits for global memory once
+  T u0[NU][N];
+  T pv0[NP];
+  T d0[NU][N];
+  if (!DIAG) {
+#pragma unroll
+    for (int c = 0; c < N; ++c) {
+      if constexpr (NU == 4) {
+        if constexpr (sizeof(T) == 4) {
+          const float4 v = own ? __ldg(reinterpret_cast<const float4*>(args.src + node[c] * 4)) : make_float4(0, 0, 0, 0);
+          u0[0][c] = v.x; u0[1][c] = v.y; u0[2][c] = v.z; u0[3][c] = v.w;
+          const float4 w = (own && valid) ? *reinterpret_cast<const float4*>(args.dst + node[c] * 4) : make_float4(0, 0, 0, 0);
+          d0[0][c] = w.x; d0[1][c] = w.y; d0[2][c] = w.z; d0[3][c] = w.w;
+        } else {
+          const double2 v0 = own ? __ldg(reinterpret_cast<const double2*>(args.src + node[c] * 4)) : make_double2(0, 0);
+          const double2 v1 = own ? __ldg(reinterpret_cast<const double2*>(args.src + node[c] * 4 + 2)) : make_double2(0, 0);
+          u0[0][c] = v0.x; u0[1][c] = v0.y; u0[2][c] = v1.x; u0[3][c] = v1.y;
+          const double2 w0 = (own && valid) ? *reinterpret_cast<const double2*>(args.dst + node[c] * 4) : make_double2(0, 0);
+          const double2 w1 = (own && valid) ? *reinterpret_cast<const double2*>(args.dst + node[c] * 4 + 2) : make_double2(0, 0);
+          d0[0][c] = w0.x; d0[1][c] = w0.y; d0[2][c] = w1.x; d0[3][c] = w1.y;
+        }
+      } else {
+#pragma unroll
+        for (int f = 0; f < NU; ++f) {
+          u0[f][c] = own ? args.src[node[c] * NU + f] : T(0);
+          d0[f][c] = 0;
+        }
+      }
+      if (OP != OP_PMASS && bnd[c]) {
+#pragma unroll
+        for (int f = 0; f < DIM; ++f) u0[f][c] = 0;
+      }
+    }
+    if (Tr::SPLIT_P) {
+#pragma unroll
+      for (int c = 0; c < NP; ++c) pv0[c] = ownp ? args.src[args.p_offset + pnode[c]] : T(0);
+    }
+  }
+
   // frozen state (stabilised NS) at the lane's Gauss points
   T Ub[DIM][Q], Gb[DIM][DIM][Q], Rb[DIM][Q], tau[Q];
   if constexpr (Tr::FROZEN) {
     T fz[DIM + 1][N];
 #pragma unroll
     for (int c = 0; c < N; ++c) {
+      if constexpr (NU == 4) {
+        if constexpr (sizeof(T) == 4) {
+          const float4 v = own ? *reinterpret_cast<const float4*>(args.frozen + fnode[c] * 4) : make_float4(0, 0, 0, 0);
+          fz[0][c] = v.x; fz[1][c] = v.y; fz[2][c] = v.z; fz[3][c] = v.w;
+        } else {
+          const double2 v0 = own ? *reinterpret_cast<const double2*>(args.frozen + fnode[c] * 4) : make_double2(0, 0);
+          const double2 v1 = own ? *reinterpret_cast<const double2*>(args.frozen + fnode[c] * 4 + 2) : make_double2(0, 0);
+          fz[0][c] = v0.x; fz[1][c] = v0.y; fz[2][c] = v1.x; fz[3][c] = v1.y;
+        }
+      } else {
 #pragma unroll
-      for (int f = 0; f <= DIM; ++f) fz[f][c] = own ? args.frozen[fnode[c] * NU + f] : T(0);
+        for (int f = 0; f <= DIM; ++f) fz[f][c] = own ? args.frozen[fnode[c] * NU + f] : T(0);
+      }
     }
     T gp[DIM][Q], lb[DIM][Q];
 #pragma unroll
@@ -208,37 +281,12 @@ op_kernel(const OpArgs<T, K + 1, K + 1, (OP == OP_STOKES ? K : K + 1)> args) {
     T u[NU][N];
     T pv[NP];
     if (!DIAG) {
-      if (own) {
 #pragma unroll
-        for (int c = 0; c < N; ++c) {
-          if constexpr (NU == 4) {
-            if constexpr (sizeof(T) == 4) {
-              const float4 v = *reinterpret_cast<const float4*>(args.src + node[c] * 4);
-              u[0][c] = v.x; u[1][c] = v.y; u[2][c] = v.z; u[3][c] = v.w;
-            } else {
-              const double2 v0 = *reinterpret_cast<const double2*>(args.src + node[c] * 4);
-              const double2 v1 = *reinterpret_cast<const double2*>(args.src + node[c] * 4 + 2);
-              u[0][c] = v0.x; u[1][c] = v0.y; u[2][c] = v1.x; u[3][c] = v1.y;
-            }
-          } else {
+      for (int f = 0; f < NU; ++f)
 #pragma unroll
-            for (int f = 0; f < NU; ++f) u[f][c] = args.src[node[c] * NU + f];
-          }
-          if (OP != OP_PMASS && bnd[c]) {
+        for (int c = 0; c < N; ++c) u[f][c] = u0[f][c];
 #pragma unroll
-            for (int f = 0; f < DIM; ++f) u[f][c] = 0;
-          }
-        }
-      } else {
-#pragma unroll
-        for (int f = 0; f < NU; ++f)
-#pragma unroll
-          for (int c = 0; c < N; ++c) u[f][c] = 0;
-      }
-      if (Tr::SPLIT_P) {
-#pragma unroll
-        for (int c = 0; c < NP; ++c) pv[c] = ownp ? args.src[args.p_offset + pnode[c]] : T(0);
-      }
+      for (int c = 0; c < NP; ++c) pv[c] = pv0[c];
     } else {
       // unit vector of local DoF `pass` (component-major over the main nodes, then pressure)
 #pragma unroll
@@ -434,16 +482,13 @@ op_kernel(const OpArgs<T, K + 1, K + 1, (OP == OP_STOKES ? K : K + 1)> args) {
         for (int c = 0; c < N; ++c) {
           T* d = args.dst + node[c] * NU;
           if constexpr (NU == 4) {
+            // dst values were loaded with the gather (no other cell of this colour touches them)
             if constexpr (sizeof(T) == 4) {
-              float4 v = *reinterpret_cast<float4*>(d);
-              v.x += r[0][c]; v.y += r[1][c]; v.z += r[2][c]; v.w += r[3][c];
-              *reinterpret_cast<float4*>(d) = v;
+              *reinterpret_cast<float4*>(d) = make_float4(d0[0][c] + r[0][c], d0[1][c] + r[1][c],
+                                                          d0[2][c] + r[2][c], d0[3][c] + r[3][c]);
             } else {
-              double2 v0 = *reinterpret_cast<double2*>(d);
-              double2 v1 = *reinterpret_cast<double2*>(d + 2);
-              v0.x += r[0][c]; v0.y += r[1][c]; v1.x += r[2][c]; v1.y += r[3][c];
-              *reinterpret_cast<double2*>(d) = v0;
-              *reinterpret_cast<double2*>(d + 2) = v1;
+              *reinterpret_cast<double2*>(d) = make_double2(d0[0][c] + r[0][c], d0[1][c] + r[1][c]);
+              *reinterpret_cast<double2*>(d + 2) = make_double2(d0[2][c] + r[2][c], d0[3][c] + r[3][c]);
             }
           } else {
 #pragma unroll
@@ -474,7 +519,7 @@ op_kernel(const OpArgs<T, K + 1, K + 1, (OP == OP_STOKES ? K : K + 1)> args) {
 template <int DIM, int K, int OP, typename T>
 constexpr size_t op_smem_bytes() {
   using TM = Team<DIM, K + 1>;
-  return sizeof(T) * (size_t)kOpWarps * (TM::CPW + 1) * 3 * TM::BUF;
+  return sizeof(T) * (size_t)kOpWarps * (TM::CPW + 1) * TM::template stride<T>();
 }
 
 }  // namespace mfns
