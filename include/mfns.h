@@ -108,6 +108,9 @@ typedef struct {
   int maxit;            /* 0 = 500 */
   int cg_iterations;    /* STOKES: Jacobi-CG steps for the Schur complement; 0 = 10 */
   double lambda_max;    /* > 0: use this lambda_max of D^-1 A on every level instead of the estimate */
+  int recompute_frozen; /* STAB_NS: 1 = interpolate the frozen state inside every apply; 0 (default) =
+                           store its point values (u, grad u, Rbar, tau) once per level (more HBM,
+                           fewer shared-memory contractions per apply) */
 } mfns_problem_desc;
 
 typedef struct {

@@ -28,6 +28,7 @@ class ProblemDesc(C.Structure):
         ("smoother_degree", C.c_int), ("mg_order", C.c_int), ("mg_precision", C.c_int),
         ("coarse_stop_n", C.c_int), ("fgmres_restart", C.c_int), ("tol", C.c_double),
         ("maxit", C.c_int), ("cg_iterations", C.c_int), ("lambda_max", C.c_double),
+        ("recompute_frozen", C.c_int),
     ]
 
 

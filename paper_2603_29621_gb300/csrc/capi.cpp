@@ -112,6 +112,7 @@ int mfns_problem_create(mfns_ctx* ctx, const mfns_mesh* mesh, const mfns_problem
   ph.dt = desc->dt > 0 ? desc->dt : 0.0;
   ph.terms = desc->terms == 0 ? MFNS_TERMS_ALL : desc->terms;
   ph.div_sign = desc->div_sign != 0 ? desc->div_sign : (desc->kind == MFNS_STAB_NS ? 1.0 : -1.0);
+  ph.precompute_frozen = desc->recompute_frozen == 0;
   const size_t used0 = ctx->budget.used;
   std::unique_ptr<Problem> p = build_problem(mesh->forest, desc->kind, k, ph, desc->mg_order,
                                              desc->coarse_stop_n > 0 ? desc->coarse_stop_n : 2, &ctx->budget);

@@ -53,7 +53,14 @@ __device__ __forceinline__ int64_t structured_node(int n, const int cc[3], int a
   return ix + M * (iy + M * iz);
 }
 
-template <int DIM, int K, int OP, typename T, bool STRUCT, bool DIAG>
+// FQ: 0 = frozen state interpolated in the kernel, 1 = read the precomputed point values,
+// 2 = compute the point values, write them to args.fq and stop (set-up pass).
+template <int DIM>
+struct FrozenPoint {
+  static constexpr int NFQ = DIM + DIM * DIM + DIM + 1;  // u, grad u, Rbar, tau
+};
+
+template <int DIM, int K, int OP, typename T, bool STRUCT, bool DIAG, int FQ = 0>
 __global__ void __launch_bounds__(kOpWarps * 32, OpMinBlocks<DIM, K, OP, T>::value)
 op_kernel(const OpArgs<T, K + 1, K + 1, (OP == OP_STOKES ? K : K + 1)> args) {
   constexpr int Q = K + 1, N = K + 1, NP = OP == OP_STOKES ? K : K + 1;
@@ -83,6 +90,7 @@ op_kernel(const OpArgs<T, K + 1, K + 1, (OP == OP_STOKES ? K : K + 1)> args) {
   int64_t cell;
   bool valid;
   int cc[3] = {0, 0, 0};
+  int64_t cellpos;  // position in the colour-major enumeration (precomputed frozen data)
   {
     const int64_t t = (int64_t)blockIdx.x * (kOpWarps * TM::CPW) + warp * TM::CPW + (lane_active ? team : 0);
     if (STRUCT) {
@@ -100,10 +108,12 @@ op_kernel(const OpArgs<T, K + 1, K + 1, (OP == OP_STOKES ? K : K + 1)> args) {
       cc[1] = 2 * (int)((tt / m[0]) % m[1]) + bits[1];
       cc[2] = DIM == 3 ? 2 * (int)(tt / ((int64_t)m[0] * m[1])) + bits[2] : 0;
       cell = cc[0] + (int64_t)n * (cc[1] + (int64_t)n * cc[2]);
+      cellpos = args.color_offset + tt;
     } else {
       const int64_t c = args.cell_begin + t;
       valid = lane_active && c < args.cell_end;
       cell = c < args.cell_end ? c : args.cell_end - 1;
+      cellpos = cell;
     }
   }
   const T h = STRUCT ? args.h : args.hcell[cell];
@@ -215,7 +225,39 @@ op_kernel(const OpArgs<T, K + 1, K + 1, (OP == OP_STOKES ? K : K + 1)> args) {
 
   // frozen state (stabilised NS) at the lane's Gauss points
   T Ub[DIM][Q], Gb[DIM][DIM][Q], Rb[DIM][Q], tau[Q];
-  if constexpr (Tr::FROZEN) {
+  constexpr int NFQ = FrozenPoint<DIM>::NFQ;
+  if constexpr (Tr::FROZEN && FQ == 1) {
+    const T* fp = args.fq + ((size_t)cellpos * TM::TPC + tid) * Q * NFQ;
+#pragma unroll
+    for (int l = 0; l < Q; ++l) {
+      T v[NFQ];
+      if constexpr (NFQ % 4 == 0 && sizeof(T) == 4) {
+#pragma unroll
+        for (int q4 = 0; q4 < NFQ / 4; ++q4) {
+          const float4 w = lane_active ? __ldg(reinterpret_cast<const float4*>(fp + l * NFQ) + q4) : make_float4(0, 0, 0, 0);
+          v[4 * q4] = w.x; v[4 * q4 + 1] = w.y; v[4 * q4 + 2] = w.z; v[4 * q4 + 3] = w.w;
+        }
+      } else if constexpr (NFQ % 2 == 0 && sizeof(T) == 8) {
+#pragma unroll
+        for (int q2 = 0; q2 < NFQ / 2; ++q2) {
+          const double2 w = lane_active ? __ldg(reinterpret_cast<const double2*>(fp + l * NFQ) + q2) : make_double2(0, 0);
+          v[2 * q2] = w.x; v[2 * q2 + 1] = w.y;
+        }
+      } else {
+#pragma unroll
+        for (int q = 0; q < NFQ; ++q) v[q] = lane_active ? fp[l * NFQ + q] : T(0);
+      }
+#pragma unroll
+      for (int i = 0; i < DIM; ++i) {
+        Ub[i][l] = v[i];
+#pragma unroll
+        for (int j = 0; j < DIM; ++j) Gb[i][j][l] = v[DIM + i * DIM + j];
+        Rb[i][l] = v[DIM + DIM * DIM + i];
+      }
+      tau[l] = v[NFQ - 1];
+    }
+  }
+  if constexpr (Tr::FROZEN && FQ != 1) {
     T fz[DIM + 1][N];
 #pragma unroll
     for (int c = 0; c < N; ++c) {
@@ -272,6 +314,23 @@ op_kernel(const OpArgs<T, K + 1, K + 1, (OP == OP_STOKES ? K : K + 1)> args) {
       }
       const T a = T(2) * args.dt_inv, b2 = T(4) * un2 * inv_h * inv_h, c = T(12) * nu * inv_h * inv_h;
       tau[l] = T(1) / sqrt(a * a + b2 + c * c);
+    }
+    if constexpr (FQ == 2) {
+      if (valid) {
+        T* fp = args.fq + ((size_t)cellpos * TM::TPC + tid) * Q * NFQ;
+#pragma unroll
+        for (int l = 0; l < Q; ++l) {
+#pragma unroll
+          for (int i = 0; i < DIM; ++i) {
+            fp[l * NFQ + i] = Ub[i][l];
+#pragma unroll
+            for (int j = 0; j < DIM; ++j) fp[l * NFQ + DIM + i * DIM + j] = Gb[i][j][l];
+            fp[l * NFQ + DIM + DIM * DIM + i] = Rb[i][l];
+          }
+          fp[l * NFQ + NFQ - 1] = tau[l];
+        }
+      }
+      return;  // set-up pass: nothing else to do (no __syncwarp follows)
     }
   }
 

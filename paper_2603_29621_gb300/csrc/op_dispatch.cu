@@ -8,9 +8,9 @@
 
 namespace mfns {
 
-#define MFNS_DECL(DIM, K, OP)                                                                                    \
-  extern template void op_launch<DIM, K, OP, double>(const OpLaunch&, const double*, double*, bool, cudaStream_t); \
-  extern template void op_launch<DIM, K, OP, float>(const OpLaunch&, const float*, float*, bool, cudaStream_t);
+#define MFNS_DECL(DIM, K, OP)                                                                                         \
+  extern template void op_launch<DIM, K, OP, double>(const OpLaunch&, const double*, double*, bool, cudaStream_t, int); \
+  extern template void op_launch<DIM, K, OP, float>(const OpLaunch&, const float*, float*, bool, cudaStream_t, int);
 
 MFNS_DECL(3, 1, OP_STAB_NS) MFNS_DECL(3, 2, OP_STAB_NS) MFNS_DECL(3, 3, OP_STAB_NS)
 MFNS_DECL(2, 1, OP_STAB_NS) MFNS_DECL(2, 2, OP_STAB_NS) MFNS_DECL(2, 3, OP_STAB_NS) MFNS_DECL(2, 4, OP_STAB_NS)
@@ -33,9 +33,9 @@ bool op_supported(int dim, int k, int op) {
 }
 
 template <typename T>
-static void dispatch(const OpLaunch& L, const T* s, T* d, bool diag, cudaStream_t st) {
+static void dispatch(const OpLaunch& L, const T* s, T* d, bool diag, cudaStream_t st, int fq_mode = -1) {
 #define MFNS_CASE(DIM, K, OP) \
-  if (L.dim == DIM && L.k == K && L.op == OP) return op_launch<DIM, K, OP, T>(L, s, d, diag, st);
+  if (L.dim == DIM && L.k == K && L.op == OP) return op_launch<DIM, K, OP, T>(L, s, d, diag, st, fq_mode);
   MFNS_CASE(3, 1, OP_STAB_NS) MFNS_CASE(3, 2, OP_STAB_NS) MFNS_CASE(3, 3, OP_STAB_NS)
   MFNS_CASE(2, 1, OP_STAB_NS) MFNS_CASE(2, 2, OP_STAB_NS) MFNS_CASE(2, 3, OP_STAB_NS) MFNS_CASE(2, 4, OP_STAB_NS)
   MFNS_CASE(3, 2, OP_STOKES) MFNS_CASE(3, 3, OP_STOKES) MFNS_CASE(3, 4, OP_STOKES)
@@ -76,6 +76,21 @@ double KernelTimer::read_ms(int64_t* launches) {
 }
 KernelTimer::~KernelTimer() {
   for (cudaEvent_t e : ev) cudaEventDestroy(e);
+}
+
+int64_t frozen_point_values_per_cell(int dim, int k) {
+  const int q = k + 1;
+  const int64_t lanes = dim == 3 ? q * q : q;
+  const int nfq = dim + dim * dim + dim + 1;
+  return lanes * q * nfq;
+}
+
+void op_precompute_frozen(const OpLaunch& L, int prec, cudaStream_t s) {
+  if (L.op != OP_STAB_NS || !L.fq[prec]) return;
+  if (prec == 0)
+    dispatch<double>(L, nullptr, nullptr, false, s, 2);
+  else
+    dispatch<float>(L, nullptr, nullptr, false, s, 2);
 }
 
 void op_apply(const OpLaunch& L, int prec, const void* src, void* dst, bool diag, cudaStream_t s) {

@@ -66,6 +66,10 @@ struct OpArgs {
   T cf[7];                     // term factors: mass conv newton supg supgN pspg strongvisc
   // diagonal mode: compute (C e_m)^T A_cell (C e_m) for every local slot m
   int diag;
+  // stabilised NS: frozen quantities at the Gauss points, precomputed (u, grad u, Rbar, tau per
+  // point), laid out [cell position][lane][point][NFQ] with cell position = colour offset + index
+  T* fq;
+  int64_t color_offset;  // structured: cells of the colours before this one
 };
 
 // ------------------------------------------------------------ small helpers

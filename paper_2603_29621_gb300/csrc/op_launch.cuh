@@ -27,7 +27,7 @@ static void build_tables(const OpLaunch& L, Tables<T, Q, N, NP>& t) {
 }
 
 template <int DIM, int K, int OP, typename T>
-void op_launch(const OpLaunch& L, const T* src, T* dst, bool diag, cudaStream_t s) {
+void op_launch(const OpLaunch& L, const T* src, T* dst, bool diag, cudaStream_t s, int fq_mode) {
   constexpr int Q = K + 1, N = K + 1, NP = OP == OP_STOKES ? K : K + 1;
   OpArgs<T, Q, N, NP> a{};
   if (L.Q != Q || L.N != N || L.NP != NP) throw Error(kErrArg, "operator tables do not match the degree");
@@ -51,16 +51,22 @@ void op_launch(const OpLaunch& L, const T* src, T* dst, bool diag, cudaStream_t 
   a.div_sign = (T)L.div_sign;
   for (int b = 0; b < 7; ++b) a.cf[b] = (L.terms >> b) & 1 ? T(1) : T(0);
   a.diag = diag;
+  // frozen state: -1 = use the precomputed point data when present; 2 = write it (set-up pass)
+  a.fq = reinterpret_cast<T*>(L.fq[prec]);
+  const int fq = OP != OP_STAB_NS ? 0 : fq_mode == 2 ? 2 : (a.fq ? 1 : 0);
   using TM = Team<DIM, Q>;
   constexpr int cells_per_block = kOpWarps * TM::CPW;
   const size_t smem = op_smem_bytes<DIM, K, OP, T>();
   const bool structured = L.structured && !diag;
+  int64_t color_offset = 0;
   for (int c = 0; c < L.n_colors; ++c) {
     int64_t ncell;
     if (structured) {
       a.color = c;
+      a.color_offset = color_offset;
       ncell = 1;
       for (int d = 0; d < DIM; ++d) ncell *= (L.n - ((c >> d) & 1) + 1) / 2;
+      color_offset += ncell;
     } else {
       a.cell_begin = L.color_ptr[c];
       a.cell_end = L.color_ptr[c + 1];
@@ -69,20 +75,42 @@ void op_launch(const OpLaunch& L, const T* src, T* dst, bool diag, cudaStream_t 
     if (ncell <= 0) continue;
     const unsigned grid = (unsigned)((ncell + cells_per_block - 1) / cells_per_block);
     if (L.timer && L.timer->enabled) L.timer->record_pair_begin(s);
-    if (structured) {
-      op_kernel<DIM, K, OP, T, true, false><<<grid, kOpWarps * 32, smem, s>>>(a);
-    } else if (diag) {
-      op_kernel<DIM, K, OP, T, false, true><<<grid, kOpWarps * 32, smem, s>>>(a);
+    if constexpr (OP == OP_STAB_NS) {
+      if (fq == 2) {
+        if (L.structured)
+          op_kernel<DIM, K, OP, T, true, false, 2><<<grid, kOpWarps * 32, smem, s>>>(a);
+        else
+          op_kernel<DIM, K, OP, T, false, false, 2><<<grid, kOpWarps * 32, smem, s>>>(a);
+      } else if (fq == 1) {
+        if (structured)
+          op_kernel<DIM, K, OP, T, true, false, 1><<<grid, kOpWarps * 32, smem, s>>>(a);
+        else if (diag)
+          op_kernel<DIM, K, OP, T, false, true, 1><<<grid, kOpWarps * 32, smem, s>>>(a);
+        else
+          op_kernel<DIM, K, OP, T, false, false, 1><<<grid, kOpWarps * 32, smem, s>>>(a);
+      } else {
+        if (structured)
+          op_kernel<DIM, K, OP, T, true, false, 0><<<grid, kOpWarps * 32, smem, s>>>(a);
+        else if (diag)
+          op_kernel<DIM, K, OP, T, false, true, 0><<<grid, kOpWarps * 32, smem, s>>>(a);
+        else
+          op_kernel<DIM, K, OP, T, false, false, 0><<<grid, kOpWarps * 32, smem, s>>>(a);
+      }
     } else {
-      op_kernel<DIM, K, OP, T, false, false><<<grid, kOpWarps * 32, smem, s>>>(a);
+      if (structured)
+        op_kernel<DIM, K, OP, T, true, false><<<grid, kOpWarps * 32, smem, s>>>(a);
+      else if (diag)
+        op_kernel<DIM, K, OP, T, false, true><<<grid, kOpWarps * 32, smem, s>>>(a);
+      else
+        op_kernel<DIM, K, OP, T, false, false><<<grid, kOpWarps * 32, smem, s>>>(a);
     }
     MFNS_CUDA(cudaGetLastError());
     if (L.timer && L.timer->enabled) L.timer->record_pair_end(s);
   }
 }
 
-#define MFNS_INSTANTIATE_OP(DIM, K, OP)                                                                   \
-  template void op_launch<DIM, K, OP, double>(const OpLaunch&, const double*, double*, bool, cudaStream_t); \
-  template void op_launch<DIM, K, OP, float>(const OpLaunch&, const float*, float*, bool, cudaStream_t);
+#define MFNS_INSTANTIATE_OP(DIM, K, OP)                                                                        \
+  template void op_launch<DIM, K, OP, double>(const OpLaunch&, const double*, double*, bool, cudaStream_t, int); \
+  template void op_launch<DIM, K, OP, float>(const OpLaunch&, const float*, float*, bool, cudaStream_t, int);
 
 }  // namespace mfns

@@ -40,7 +40,13 @@ struct OpLaunch {
   int Q = 3, N = 3, NP = 3;
   std::vector<double> S, Sp, D, D2, W, P, Pp;
   KernelTimer* timer = nullptr;     // optional per-launch timing
+  void* fq[2] = {nullptr, nullptr}; // stabilised NS: precomputed frozen point data (fp64 / fp32)
 };
+
+// Stabilised NS: number of precomputed values per cell (lanes x points x values per point).
+int64_t frozen_point_values_per_cell(int dim, int k);
+// Fill L.fq[prec] (device buffer of n_cells * frozen_point_values_per_cell) from the frozen state.
+void op_precompute_frozen(const OpLaunch& L, int prec, cudaStream_t s);
 
 // Fill the 1D tables of `L` for its degree (needs L.dim, L.k, L.op).
 void fill_tables(OpLaunch& L);
@@ -48,7 +54,7 @@ void fill_tables(OpLaunch& L);
 // dst = A src on the free rows (dst must be zeroed by the caller); diag = true
 // accumulates the diagonal instead (src ignored).  Constrained rows untouched.
 template <int DIM, int K, int OP, typename T>
-void op_launch(const OpLaunch& L, const T* src, T* dst, bool diag, cudaStream_t s);
+void op_launch(const OpLaunch& L, const T* src, T* dst, bool diag, cudaStream_t s, int fq_mode = -1);
 
 // Runtime dispatch over (dim, k, op, precision); prec 0 = fp64, 1 = fp32.
 void op_apply(const OpLaunch& L, int prec, const void* src, void* dst, bool diag, cudaStream_t s);

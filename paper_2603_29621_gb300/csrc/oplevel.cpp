@@ -11,7 +11,7 @@
 namespace mfns {
 
 size_t OpLevel::bytes() const {
-  size_t b = cell_u.bytes() + cell_p.bytes() + cell_f.bytes() + mask.bytes() + constrained.bytes() +
+  size_t b = fq[0].bytes() + fq[1].bytes() + cell_u.bytes() + cell_p.bytes() + cell_f.bytes() + mask.bytes() + constrained.bytes() +
              hang_dof.bytes() + hang_ptr.bytes() + hang_src.bytes() + pres.bytes() + tnodes.bytes() +
              tpnodes.bytes();
   for (int i = 0; i < 2; ++i) b += hcell[i].bytes() + frozen[i].bytes() + hang_w[i].bytes() + dinv[i].bytes();
@@ -137,6 +137,16 @@ void build_oplevel(OpLevel& lv, const Forest& f, int op, int k, const Physics& p
     lv.frozen[1] = upload_as<float>(bud, fz);
     L.frozen[0] = lv.frozen[0].get();
     L.frozen[1] = lv.frozen[1].get();
+    if (ph.precompute_frozen) {
+      // point values of the frozen state (u, grad u, Rbar, tau), computed once by the cell kernel
+      const int64_t per_cell = frozen_point_values_per_cell(dim, k);
+      for (int prec = 0; prec < 2; ++prec) {
+        lv.fq[prec].alloc(bud, (size_t)nc * per_cell * esize(prec));
+        L.fq[prec] = lv.fq[prec].get();
+        op_precompute_frozen(L, prec, 0);
+      }
+      MFNS_CUDA(cudaStreamSynchronize(0));
+    }
   }
 
   // constrained rows, hanging distribution, pressure entries

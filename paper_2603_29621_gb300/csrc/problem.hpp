@@ -17,6 +17,7 @@ namespace mfns {
 struct Physics {
   double nu = 1.0, dt = 0.0, div_sign = -1.0;
   int terms = 127;
+  bool precompute_frozen = true;  // stabilised NS: store the frozen state's point values
 };
 
 // One operator on one mesh (one multigrid level, the system operator or the pressure mass).
@@ -27,7 +28,7 @@ struct OpLevel {
   int64_t n_dofs = 0, n_main_dofs = 0;  // vector length, main-node block length
   OpLaunch L;
   std::vector<int32_t> perm;            // colour-sorted position -> forest cell id
-  DevBuf cell_u, cell_p, cell_f, mask, hcell[2], frozen[2];
+  DevBuf cell_u, cell_p, cell_f, mask, hcell[2], frozen[2], fq[2];
   std::vector<int32_t> constrained_host;
   DevBuf constrained;                   // identity rows
   int64_t n_hang = 0;
