@@ -128,6 +128,7 @@ int mfns_problem_create(mfns_ctx* ctx, const mfns_mesh* mesh, const mfns_problem
     for (auto& lv : p->levels) lv->lmax = desc->lambda_max;
   alloc_workspaces(*p);
   cudaStream_t s = 0;
+  autotune(*p, s);
   estimate_lambda(*p, s);
   setup_coarse(*p, s);
   MFNS_CUDA(cudaStreamSynchronize(s));
@@ -198,6 +199,7 @@ int mfns_constrained_dofs(const mfns_problem* pc, int which, int64_t* idx, int64
 int mfns_set_lambda_max(mfns_problem* p, int level, double lmax) {
   if (!p || level < 0 || level >= (int)p->p->levels.size() || !(lmax > 0)) return fail(MFNS_ERR_ARG, "bad level");
   p->p->levels[level]->lmax = lmax;
+  invalidate_graphs(*p->p);
   return MFNS_OK;
 }
 
@@ -281,7 +283,10 @@ int mfns_vcycle(mfns_problem* p, int prec, const void* b, void* x, void* stream)
   API_BEGIN
   if (!p || !b || !x || (prec != 0 && prec != 1)) return fail(MFNS_ERR_ARG, "bad arguments");
   MFNS_CUDA(cudaSetDevice(p->ctx->device));
-  vcycle(*p->p, prec, b, x, S(stream));
+  if (p->p->use_graphs)
+    vcycle_graph(*p->p, prec, b, x, S(stream));
+  else
+    vcycle(*p->p, prec, b, x, S(stream));
   API_END
 }
 

@@ -4,7 +4,7 @@
 
 namespace mfns {
 
-constexpr int kOpWarps = 4;  // warps per block
+constexpr int kOpWarps = 4;  // largest number of warps per block (the block size is tuned at run time)
 
 template <int DIM, int Q>
 struct Team {
@@ -92,7 +92,7 @@ op_kernel(const OpArgs<T, K + 1, K + 1, (OP == OP_STOKES ? K : K + 1)> args) {
   int cc[3] = {0, 0, 0};
   int64_t cellpos;  // position in the colour-major enumeration (precomputed frozen data)
   {
-    const int64_t t = (int64_t)blockIdx.x * (kOpWarps * TM::CPW) + warp * TM::CPW + (lane_active ? team : 0);
+    const int64_t t = (int64_t)blockIdx.x * ((blockDim.x >> 5) * TM::CPW) + warp * TM::CPW + (lane_active ? team : 0);
     if (STRUCT) {
       const int n = args.n;
       int m[3], bits[3];
@@ -576,9 +576,9 @@ op_kernel(const OpArgs<T, K + 1, K + 1, (OP == OP_STOKES ? K : K + 1)> args) {
 }
 
 template <int DIM, int K, int OP, typename T>
-constexpr size_t op_smem_bytes() {
+constexpr size_t op_smem_bytes(int warps = kOpWarps) {
   using TM = Team<DIM, K + 1>;
-  return sizeof(T) * (size_t)kOpWarps * (TM::CPW + 1) * TM::template stride<T>();
+  return sizeof(T) * (size_t)warps * (TM::CPW + 1) * TM::template stride<T>();
 }
 
 }  // namespace mfns

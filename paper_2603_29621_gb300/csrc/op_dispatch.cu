@@ -1,5 +1,8 @@
 // Runtime dispatch of the operator kernels and the host-side 1D tables.
+#include <map>
+#include <mutex>
 #include <string>
+#include <tuple>
 
 #include "mesh.hpp"
 #include "op_kernel.cuh"
@@ -7,6 +10,8 @@
 #include "common.hpp"
 
 namespace mfns {
+
+constexpr int kOpWarpsDefault = 4;
 
 #define MFNS_DECL(DIM, K, OP)                                                                                         \
   extern template void op_launch<DIM, K, OP, double>(const OpLaunch&, const double*, double*, bool, cudaStream_t, int); \
@@ -91,6 +96,46 @@ void op_precompute_frozen(const OpLaunch& L, int prec, cudaStream_t s) {
     dispatch<double>(L, nullptr, nullptr, false, s, 2);
   else
     dispatch<float>(L, nullptr, nullptr, false, s, 2);
+}
+
+int autotune_warps(OpLaunch& L, int prec, void* src, void* dst, int64_t n, cudaStream_t s) {
+  static std::mutex mu;
+  static std::map<std::tuple<int, int, int, int, bool>, int> cache;
+  const auto key = std::make_tuple(L.dim, L.k, L.op, prec, L.structured);
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = cache.find(key);
+    if (it != cache.end()) return L.warps[prec] = it->second;
+  }
+  (void)n;
+  cudaEvent_t e0, e1;
+  MFNS_CUDA(cudaEventCreate(&e0));
+  MFNS_CUDA(cudaEventCreate(&e1));
+  KernelTimer* saved = L.timer;
+  L.timer = nullptr;
+  int best = kOpWarpsDefault;
+  float best_ms = 1e30f;
+  for (int w : {1, 2, 4}) {
+    L.warps[prec] = w;
+    op_apply(L, prec, src, dst, false, s);  // warm-up
+    MFNS_CUDA(cudaEventRecord(e0, s));
+    for (int r = 0; r < 3; ++r) op_apply(L, prec, src, dst, false, s);
+    MFNS_CUDA(cudaEventRecord(e1, s));
+    MFNS_CUDA(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    MFNS_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    if (ms < best_ms * 0.98f) {  // prefer the earlier (smaller) block size unless clearly slower
+      best_ms = ms;
+      best = w;
+    }
+  }
+  L.timer = saved;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  L.warps[prec] = best;
+  std::lock_guard<std::mutex> lock(mu);
+  cache[key] = best;
+  return best;
 }
 
 void op_apply(const OpLaunch& L, int prec, const void* src, void* dst, bool diag, cudaStream_t s) {

@@ -55,8 +55,9 @@ void op_launch(const OpLaunch& L, const T* src, T* dst, bool diag, cudaStream_t 
   a.fq = reinterpret_cast<T*>(L.fq[prec]);
   const int fq = OP != OP_STAB_NS ? 0 : fq_mode == 2 ? 2 : (a.fq ? 1 : 0);
   using TM = Team<DIM, Q>;
-  constexpr int cells_per_block = kOpWarps * TM::CPW;
-  const size_t smem = op_smem_bytes<DIM, K, OP, T>();
+  const int warps = L.warps[prec] > 0 ? L.warps[prec] : kOpWarps;
+  const int cells_per_block = warps * TM::CPW;
+  const size_t smem = op_smem_bytes<DIM, K, OP, T>(warps);
   const bool structured = L.structured && !diag;
   int64_t color_offset = 0;
   for (int c = 0; c < L.n_colors; ++c) {
@@ -78,31 +79,31 @@ void op_launch(const OpLaunch& L, const T* src, T* dst, bool diag, cudaStream_t 
     if constexpr (OP == OP_STAB_NS) {
       if (fq == 2) {
         if (L.structured)
-          op_kernel<DIM, K, OP, T, true, false, 2><<<grid, kOpWarps * 32, smem, s>>>(a);
+          op_kernel<DIM, K, OP, T, true, false, 2><<<grid, warps * 32, smem, s>>>(a);
         else
-          op_kernel<DIM, K, OP, T, false, false, 2><<<grid, kOpWarps * 32, smem, s>>>(a);
+          op_kernel<DIM, K, OP, T, false, false, 2><<<grid, warps * 32, smem, s>>>(a);
       } else if (fq == 1) {
         if (structured)
-          op_kernel<DIM, K, OP, T, true, false, 1><<<grid, kOpWarps * 32, smem, s>>>(a);
+          op_kernel<DIM, K, OP, T, true, false, 1><<<grid, warps * 32, smem, s>>>(a);
         else if (diag)
-          op_kernel<DIM, K, OP, T, false, true, 1><<<grid, kOpWarps * 32, smem, s>>>(a);
+          op_kernel<DIM, K, OP, T, false, true, 1><<<grid, warps * 32, smem, s>>>(a);
         else
-          op_kernel<DIM, K, OP, T, false, false, 1><<<grid, kOpWarps * 32, smem, s>>>(a);
+          op_kernel<DIM, K, OP, T, false, false, 1><<<grid, warps * 32, smem, s>>>(a);
       } else {
         if (structured)
-          op_kernel<DIM, K, OP, T, true, false, 0><<<grid, kOpWarps * 32, smem, s>>>(a);
+          op_kernel<DIM, K, OP, T, true, false, 0><<<grid, warps * 32, smem, s>>>(a);
         else if (diag)
-          op_kernel<DIM, K, OP, T, false, true, 0><<<grid, kOpWarps * 32, smem, s>>>(a);
+          op_kernel<DIM, K, OP, T, false, true, 0><<<grid, warps * 32, smem, s>>>(a);
         else
-          op_kernel<DIM, K, OP, T, false, false, 0><<<grid, kOpWarps * 32, smem, s>>>(a);
+          op_kernel<DIM, K, OP, T, false, false, 0><<<grid, warps * 32, smem, s>>>(a);
       }
     } else {
       if (structured)
-        op_kernel<DIM, K, OP, T, true, false><<<grid, kOpWarps * 32, smem, s>>>(a);
+        op_kernel<DIM, K, OP, T, true, false><<<grid, warps * 32, smem, s>>>(a);
       else if (diag)
-        op_kernel<DIM, K, OP, T, false, true><<<grid, kOpWarps * 32, smem, s>>>(a);
+        op_kernel<DIM, K, OP, T, false, true><<<grid, warps * 32, smem, s>>>(a);
       else
-        op_kernel<DIM, K, OP, T, false, false><<<grid, kOpWarps * 32, smem, s>>>(a);
+        op_kernel<DIM, K, OP, T, false, false><<<grid, warps * 32, smem, s>>>(a);
     }
     MFNS_CUDA(cudaGetLastError());
     if (L.timer && L.timer->enabled) L.timer->record_pair_end(s);

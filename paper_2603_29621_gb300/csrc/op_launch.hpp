@@ -41,7 +41,13 @@ struct OpLaunch {
   std::vector<double> S, Sp, D, D2, W, P, Pp;
   KernelTimer* timer = nullptr;     // optional per-launch timing
   void* fq[2] = {nullptr, nullptr}; // stabilised NS: precomputed frozen point data (fp64 / fp32)
+  int warps[2] = {0, 0};            // warps per block per precision (0 = not tuned yet: use 4)
 };
+
+// Autotuner: pick the warps per block (1, 2 or 4) of the cell kernel for this operator and
+// precision by timing a few applications on scratch vectors; results are cached per
+// (dim, degree, operator, precision, structured) for the process.
+int autotune_warps(OpLaunch& L, int prec, void* src, void* dst, int64_t n, cudaStream_t s);
 
 // Stabilised NS: number of precomputed values per cell (lanes x points x values per point).
 int64_t frozen_point_values_per_cell(int dim, int k);

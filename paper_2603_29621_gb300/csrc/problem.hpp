@@ -95,7 +95,14 @@ struct Problem {
   DevBuf mg_b32, mg_x32;                // fp32 copies for the mixed-precision preconditioner
   DevBuf cg_r, cg_z, cg_p, cg_q, cg_x;  // Stokes Schur CG (mg precision)
   DevBuf stokes_u_rhs, stokes_u_sol;    // Stokes A-block rhs/solution (mg precision)
+  // CUDA graphs: the preconditioner (fp64 in/out) and the V-cycle per precision
+  bool use_graphs = true;
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t pc_graph = nullptr;
+  cudaGraphExec_t vc_graph[2] = {nullptr, nullptr};
+  DevBuf pc_in, pc_out, vc_in[2], vc_out[2];
   size_t bytes = 0;
+  ~Problem();
 };
 
 // Build everything for a mesh and a description; throws Error.
@@ -105,7 +112,13 @@ std::unique_ptr<Problem> build_problem(const Forest& f, int kind, int k, const P
 // Multigrid
 void smooth(Problem& p, int level, int prec, const void* b, void* x, bool x_is_zero, cudaStream_t s);
 void vcycle(Problem& p, int prec, const void* b, void* x, cudaStream_t s);
+// V-cycle through its captured CUDA graph (captured on first use)
+void vcycle_graph(Problem& p, int prec, const void* b, void* x, cudaStream_t s);
+// Drop captured graphs (after a change of smoother bounds or settings)
+void invalidate_graphs(Problem& p);
 void estimate_lambda(Problem& p, cudaStream_t s);
+// choose the cell kernel's block size for every operator of the problem (cached per process)
+void autotune(Problem& p, cudaStream_t s);
 void setup_coarse(Problem& p, cudaStream_t s);
 void alloc_workspaces(Problem& p);
 // Solve (FP64 FGMRES); returns iterations, writes relres; throws on CUDA errors

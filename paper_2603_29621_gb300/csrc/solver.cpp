@@ -36,6 +36,11 @@ static int sys_op_of(int kind) {
   }
 }
 
+Problem::~Problem() {
+  invalidate_graphs(*this);
+  if (cap_stream) cudaStreamDestroy(cap_stream);
+}
+
 std::unique_ptr<Problem> build_problem(const Forest& f, int kind, int k, const Physics& ph, int mg_order,
                                        int coarse_stop_n, Budget* bud) {
   auto p = std::make_unique<Problem>();
@@ -83,6 +88,23 @@ std::unique_ptr<Problem> build_problem(const Forest& f, int kind, int k, const P
 
 static OpLevel& sys_of(Problem& p) { return p.system ? *p.system : *p.levels[0]; }
 
+// Timers record events on the launching stream; they are paused while a graph is captured.
+struct TimerPause {
+  std::vector<std::pair<KernelTimer*, bool>> saved;
+  explicit TimerPause(Problem& p) {
+    for (auto& lv : p.levels) keep(lv->timer.get());
+    if (p.system) keep(p.system->timer.get());
+    if (p.pmass) keep(p.pmass->timer.get());
+  }
+  void keep(KernelTimer* t) {
+    saved.push_back({t, t->enabled});
+    t->enabled = false;
+  }
+  ~TimerPause() {
+    for (auto& s : saved) s.first->enabled = s.second;
+  }
+};
+
 void alloc_workspaces(Problem& p) {
   Budget* bud = p.bud;
   for (int prec = 0; prec < 2; ++prec) {
@@ -118,6 +140,12 @@ void alloc_workspaces(Problem& p) {
   p.ptrZ = upload(bud, pz);
   p.mg_b32.alloc(bud, n * 4);
   p.mg_x32.alloc(bud, n * 4);
+  p.pc_in.alloc(bud, n * 8);
+  p.pc_out.alloc(bud, n * 8);
+  for (int prec = 0; prec < 2; ++prec) {
+    p.vc_in[prec].alloc(bud, p.levels[0]->n_dofs * esize(prec));
+    p.vc_out[prec].alloc(bud, p.levels[0]->n_dofs * esize(prec));
+  }
   if (p.kind == 0) {
     const int64_t np = p.pmass->n_dofs;
     const size_t es = 8;  // the Stokes preconditioner keeps fp64 and fp32 copies in separate buffers
@@ -146,6 +174,26 @@ static void level_dinv(Problem& p, OpLevel& lv, cudaStream_t s) {
     oplevel_diag(lv, 0, lv.dinv[0].get(), s);
     vrecip<double>(lv.dinv[0].as<double>(), lv.dinv[0].as<double>(), n, s);
     vcast_d2f(lv.dinv[1].as<float>(), lv.dinv[0].as<double>(), n, s);
+  }
+}
+
+void autotune(Problem& p, cudaStream_t s) {
+  // scratch: the level workspaces (contents are overwritten before any use)
+  for (int prec = 0; prec < 2; ++prec)
+    for (size_t l = 0; l < p.levels.size(); ++l) {
+      Workspace& w = p.ws[prec][l];
+      MFNS_CUDA(cudaMemsetAsync(w.x.get(), 0, p.levels[l]->n_dofs * esize(prec), s));
+      autotune_warps(p.levels[l]->L, prec, w.x.get(), w.t.get(), p.levels[l]->n_dofs, s);
+    }
+  for (OpLevel* lv : {p.system.get(), p.pmass.get()}) {
+    if (!lv) continue;
+    for (int prec = 0; prec < 2; ++prec) {
+      void* a = prec == 0 ? p.w.get() : p.mg_b32.get();
+      void* b = prec == 0 ? p.tmp.get() : p.mg_x32.get();
+      if ((int64_t)lv->n_dofs > (int64_t)sys_of(p).n_dofs) continue;
+      MFNS_CUDA(cudaMemsetAsync(a, 0, lv->n_dofs * esize(prec), s));
+      autotune_warps(lv->L, prec, a, b, lv->n_dofs, s);
+    }
   }
 }
 
@@ -384,31 +432,22 @@ static void stokes_block(Problem& p, int prec, const T* r, T* z, cudaStream_t s)
   T* cq = p.cg_q.as<T>();
   const T* dinv = M.dinv[prec].as<T>();
   double* sc = p.scal.as<double>();
-  // z_p = -nu M_p^{-1} r_p by a fixed number of Jacobi-preconditioned CG steps from zero
+  // z_p = -nu M_p^{-1} r_p by a fixed number of Jacobi-preconditioned CG steps from zero; the CG
+  // scalars stay on the device (sc[2 + (it & 1)] = r.z of the current and next step, sc[4] = p.q)
   vzero<T>(cx, np, s);
   vcopy<T>(cr, r + nu, np, s);
   vmul<T>(cz, dinv, cr, np, s);
   vcopy<T>(cp, cz, np, s);
-  dot<T>(sc, cr, cz, np, p.part.as<double>(), s);
-  double rz;
-  MFNS_CUDA(cudaMemcpyAsync(&rz, sc, 8, cudaMemcpyDeviceToHost, s));
-  MFNS_CUDA(cudaStreamSynchronize(s));
-  for (int it = 0; it < p.cg_iterations && rz != 0.0; ++it) {
+  dot<T>(sc + 2, cr, cz, np, p.part.as<double>(), s);
+  for (int it = 0; it < p.cg_iterations; ++it) {
+    double* rz = sc + 2 + (it & 1);
+    double* rz_new = sc + 2 + ((it + 1) & 1);
     oplevel_vmult(M, prec, cp, cq, s);
-    dot<T>(sc, cp, cq, np, p.part.as<double>(), s);
-    double pq;
-    MFNS_CUDA(cudaMemcpyAsync(&pq, sc, 8, cudaMemcpyDeviceToHost, s));
-    MFNS_CUDA(cudaStreamSynchronize(s));
-    const double alpha = rz / pq;
-    vaxpy<T>(cx, (T)alpha, cp, np, s);
-    vaxpy<T>(cr, (T)(-alpha), cq, np, s);
+    dot<T>(sc + 4, cp, cq, np, p.part.as<double>(), s);
+    cg_step_xr<T>(cx, cr, cp, cq, rz, sc + 4, np, s);
     vmul<T>(cz, dinv, cr, np, s);
-    dot<T>(sc, cr, cz, np, p.part.as<double>(), s);
-    double rz_new;
-    MFNS_CUDA(cudaMemcpyAsync(&rz_new, sc, 8, cudaMemcpyDeviceToHost, s));
-    MFNS_CUDA(cudaStreamSynchronize(s));
-    vaxpby<T>(cp, T(1), cz, (T)(rz_new / rz), np, s);
-    rz = rz_new;
+    dot<T>(rz_new, cr, cz, np, p.part.as<double>(), s);
+    cg_step_p<T>(cp, cz, rz_new, rz, np, s);
   }
   // full = [0, z_p]; B z_p = velocity part of the Stokes operator applied to it
   T* full = p.stokes_u_rhs.as<T>();
@@ -423,7 +462,58 @@ static void stokes_block(Problem& p, int prec, const T* r, T* z, cudaStream_t s)
   vcycle_level<T>(p, prec, 0, Bz, z, s);
 }
 
+static void precondition_body(Problem& p, const double* v, double* z, cudaStream_t s);
+
+// The preconditioner is a fixed sequence of kernels on fixed buffers: it is captured once into
+// a CUDA graph (input p.pc_in, output p.pc_out) and replayed.
 static void precondition(Problem& p, const double* v, double* z, cudaStream_t s) {
+  OpLevel& S = p.system ? *p.system : *p.levels[0];
+  const int64_t n = S.n_dofs;
+  if (!p.use_graphs) return precondition_body(p, v, z, s);
+  if (!p.pc_graph) {
+    if (!p.cap_stream) MFNS_CUDA(cudaStreamCreateWithFlags(&p.cap_stream, cudaStreamNonBlocking));
+    TimerPause pause(p);
+    MFNS_CUDA(cudaStreamBeginCapture(p.cap_stream, cudaStreamCaptureModeThreadLocal));
+    precondition_body(p, p.pc_in.as<double>(), p.pc_out.as<double>(), p.cap_stream);
+    cudaGraph_t g;
+    MFNS_CUDA(cudaStreamEndCapture(p.cap_stream, &g));
+    MFNS_CUDA(cudaGraphInstantiate(&p.pc_graph, g, 0));
+    MFNS_CUDA(cudaGraphDestroy(g));
+  }
+  MFNS_CUDA(cudaMemcpyAsync(p.pc_in.get(), v, n * 8, cudaMemcpyDeviceToDevice, s));
+  MFNS_CUDA(cudaGraphLaunch(p.pc_graph, s));
+  MFNS_CUDA(cudaMemcpyAsync(z, p.pc_out.get(), n * 8, cudaMemcpyDeviceToDevice, s));
+}
+
+void invalidate_graphs(Problem& p) {
+  if (p.pc_graph) cudaGraphExecDestroy(p.pc_graph);
+  p.pc_graph = nullptr;
+  for (int i = 0; i < 2; ++i) {
+    if (p.vc_graph[i]) cudaGraphExecDestroy(p.vc_graph[i]);
+    p.vc_graph[i] = nullptr;
+  }
+}
+
+void vcycle_graph(Problem& p, int prec, const void* b, void* x, cudaStream_t s) {
+  Workspace& w = p.ws[prec][0];
+  const size_t bytes = p.levels[0]->n_dofs * esize(prec);
+  if (!p.vc_graph[prec]) {
+    if (!p.cap_stream) MFNS_CUDA(cudaStreamCreateWithFlags(&p.cap_stream, cudaStreamNonBlocking));
+    TimerPause pause(p);
+    MFNS_CUDA(cudaStreamBeginCapture(p.cap_stream, cudaStreamCaptureModeThreadLocal));
+    vcycle(p, prec, p.vc_in[prec].get(), p.vc_out[prec].get(), p.cap_stream);
+    cudaGraph_t g;
+    MFNS_CUDA(cudaStreamEndCapture(p.cap_stream, &g));
+    MFNS_CUDA(cudaGraphInstantiate(&p.vc_graph[prec], g, 0));
+    MFNS_CUDA(cudaGraphDestroy(g));
+  }
+  (void)w;
+  MFNS_CUDA(cudaMemcpyAsync(p.vc_in[prec].get(), b, bytes, cudaMemcpyDeviceToDevice, s));
+  MFNS_CUDA(cudaGraphLaunch(p.vc_graph[prec], s));
+  MFNS_CUDA(cudaMemcpyAsync(x, p.vc_out[prec].get(), bytes, cudaMemcpyDeviceToDevice, s));
+}
+
+static void precondition_body(Problem& p, const double* v, double* z, cudaStream_t s) {
   OpLevel& S = sys_of(p);
   const int64_t n = S.n_dofs;
   if (p.mg_precision == 0) {

@@ -130,6 +130,21 @@ __global__ void k_multi_axpy_add(double* x, const double* const* Z, const double
     x[i] = s;
   }
 }
+template <typename T>
+__global__ void k_cg_xr(T* x, T* r, const T* p, const T* q, const double* num, const double* den, int64_t n) {
+  const double d = *den;
+  const T alpha = (T)(d != 0.0 ? *num / d : 0.0);
+  GRID_STRIDE(i, n) {
+    x[i] += alpha * p[i];
+    r[i] -= alpha * q[i];
+  }
+}
+template <typename T>
+__global__ void k_cg_p(T* p, const T* z, const double* num, const double* den, int64_t n) {
+  const double d = *den;
+  const T beta = (T)(d != 0.0 ? *num / d : 0.0);
+  GRID_STRIDE(i, n) p[i] = z[i] + beta * p[i];
+}
 }  // namespace
 
 #define LAUNCH(kern, n, s, ...)                                    \
@@ -204,6 +219,15 @@ template <typename T> void sub_mean_idx(T* x, const int32_t* idx, int64_t n, con
   LAUNCH(k_sub_mean_idx<T>, n, s, x, idx, n, sum);
 }
 
+template <typename T>
+void cg_step_xr(T* x, T* r, const T* p, const T* q, const double* num, const double* den, int64_t n, cudaStream_t s) {
+  LAUNCH(k_cg_xr<T>, n, s, x, r, p, q, num, den, n);
+}
+template <typename T>
+void cg_step_p(T* p, const T* z, const double* num, const double* den, int64_t n, cudaStream_t s) {
+  LAUNCH(k_cg_p<T>, n, s, p, z, num, den, n);
+}
+
 #define INST(T)                                                                                     \
   template void vzero<T>(T*, int64_t, cudaStream_t);                                                \
   template void vcopy<T>(T*, const T*, int64_t, cudaStream_t);                                      \
@@ -221,7 +245,9 @@ template <typename T> void sub_mean_idx(T* x, const int32_t* idx, int64_t n, con
   template void vgemv<T>(T*, const T*, const T*, int64_t, cudaStream_t);                            \
   template void dot<T>(double*, const T*, const T*, int64_t, double*, cudaStream_t);                \
   template void sum_idx<T>(double*, const T*, const int32_t*, int64_t, double*, cudaStream_t);      \
-  template void sub_mean_idx<T>(T*, const int32_t*, int64_t, const double*, cudaStream_t);
+  template void sub_mean_idx<T>(T*, const int32_t*, int64_t, const double*, cudaStream_t);        \
+  template void cg_step_xr<T>(T*, T*, const T*, const T*, const double*, const double*, int64_t, cudaStream_t); \
+  template void cg_step_p<T>(T*, const T*, const double*, const double*, int64_t, cudaStream_t);
 INST(float)
 INST(double)
 

@@ -54,4 +54,12 @@ template <typename T> void sum_idx(double* out, const T* x, const int32_t* idx, 
 // x[idx] -= (*mean_sum) / n
 template <typename T> void sub_mean_idx(T* x, const int32_t* idx, int64_t n, const double* sum, cudaStream_t s);
 
+// CG steps with device-resident scalars (no host round trip, capturable into CUDA graphs):
+// alpha = num/den (0 when den == 0): x += alpha p, r -= alpha q
+template <typename T>
+void cg_step_xr(T* x, T* r, const T* p, const T* q, const double* num, const double* den, int64_t n, cudaStream_t s);
+// beta = num/den (0 when den == 0): p = z + beta p
+template <typename T>
+void cg_step_p(T* p, const T* z, const double* num, const double* den, int64_t n, cudaStream_t s);
+
 }  // namespace mfns
