@@ -51,8 +51,19 @@ void oplevel_diag(const OpLevel& lv, int prec, void* diag, cudaStream_t s);
 void oplevel_distribute(const OpLevel& lv, int prec, void* x, cudaStream_t s);
 void oplevel_support(const OpLevel& lv, double* xyz, int* field);
 
+// Separable transfer between uniform meshes: 1D stencils P1 (fine x coarse) and P1^T per axis.
+struct SepTransfer {
+  int dim = 3, ncomp = 1, nvel = 0;
+  int64_t Mf = 0, Mc = 0;               // 1D node counts
+  DevBuf p_ptr, p_idx, p_w[2];          // rows = fine nodes
+  DevBuf r_ptr, r_idx, r_w[2];          // rows = coarse nodes
+  DevBuf tmp1[2], tmp2[2];              // intermediate grids per precision
+};
+
 // Transfer between fine level (index l) and coarse level (l+1), Eq. 4.
 struct Transfer {
+  bool separable = false;
+  SepTransfer sep;
   bool hkind = true;                    // true: h (children), false: p (same cells)
   int dim = 3, kf = 1, kc = 1, ncomp = 1;
   int64_t n_coarse_cells = 0;
@@ -63,6 +74,9 @@ struct Transfer {
   std::vector<double> Pc;               // coarse hanging interpolation P[2][NC][NC]
 };
 void build_transfer(Transfer& t, const OpLevel& fine, const OpLevel& coarse, Budget* bud);
+bool build_separable(SepTransfer& t, const OpLevel& fine, const OpLevel& coarse, Budget* bud);
+void sep_restrict(const SepTransfer& t, int prec, const void* fine, void* coarse, cudaStream_t s);
+void sep_prolongate_add(const SepTransfer& t, int prec, const void* coarse, void* fine, cudaStream_t s);
 void transfer_prolongate_add(const Transfer& t, const OpLevel& fine, const OpLevel& coarse, int prec,
                              const void* xc, void* xf, cudaStream_t s);
 void transfer_restrict(const Transfer& t, const OpLevel& fine, const OpLevel& coarse, int prec,

@@ -10,6 +10,7 @@
 // coarse finite-element function at its free nodes.  Restriction is the exact
 // transpose; its scatter into the coarse vector follows the coarse colours.
 #include <algorithm>
+#include <cstdlib>
 #include <cstring>
 #include <unordered_map>
 
@@ -232,6 +233,15 @@ __global__ void __launch_bounds__(128) transfer_kernel(const TransferArgs<T, NF,
 // ------------------------------------------------------------------------ host side
 void build_transfer(Transfer& t, const OpLevel& fine, const OpLevel& coarse, Budget* bud) {
   const int dim = fine.dim;
+  if (build_separable(t.sep, fine, coarse, bud)) {  // uniform -> uniform: tensor-product stencils
+    t.separable = true;
+    t.dim = dim;
+    t.kf = fine.k;
+    t.kc = coarse.k;
+    t.ncomp = fine.NU;
+    t.hkind = fine.k == coarse.k;
+    return;
+  }
   t.dim = dim;
   t.kf = fine.k;
   t.kc = coarse.k;
@@ -384,6 +394,7 @@ static void dispatch_transfer(const Transfer& t, const OpLevel& fine, const OpLe
 
 void transfer_prolongate_add(const Transfer& t, const OpLevel& fine, const OpLevel& coarse, int prec, const void* xc,
                              void* xf, cudaStream_t s) {
+  if (t.separable) return sep_prolongate_add(t.sep, prec, xc, xf, s);
   if (prec == 0)
     dispatch_transfer<double>(t, fine, coarse, (const double*)xc, (double*)xf, false, s);
   else
@@ -392,11 +403,15 @@ void transfer_prolongate_add(const Transfer& t, const OpLevel& fine, const OpLev
 
 void transfer_restrict(const Transfer& t, const OpLevel& fine, const OpLevel& coarse, int prec, const void* rf,
                        void* rc, cudaStream_t s) {
-  MFNS_CUDA(cudaMemsetAsync(rc, 0, coarse.n_dofs * esize(prec), s));
-  if (prec == 0)
-    dispatch_transfer<double>(t, fine, coarse, (const double*)rf, (double*)rc, true, s);
-  else
-    dispatch_transfer<float>(t, fine, coarse, (const float*)rf, (float*)rc, true, s);
+  if (t.separable) {
+    sep_restrict(t.sep, prec, rf, rc, s);
+  } else {
+    MFNS_CUDA(cudaMemsetAsync(rc, 0, coarse.n_dofs * esize(prec), s));
+    if (prec == 0)
+      dispatch_transfer<double>(t, fine, coarse, (const double*)rf, (double*)rc, true, s);
+    else
+      dispatch_transfer<float>(t, fine, coarse, (const float*)rf, (float*)rc, true, s);
+  }
   const int64_t nc = (int64_t)coarse.constrained_host.size();
   if (prec == 0)
     vset_idx<double>((double*)rc, 0.0, coarse.constrained.as<int32_t>(), nc, s);
