@@ -186,7 +186,7 @@ def run_ours(args, world, rank, local):
     ctx = api.Context(local)
     n = args.n
     m = api.Mesh(ctx, 3, n)
-    prob = api.Problem(ctx, m, kind=L.STAB_NS, degree=2, nu=1e-2, dt=1e-2, smoother_degree=3,
+    prob = api.Problem(ctx, m, kind=L.STAB_NS, degree=2, nu=1e-2, dt=1e-2, smoother=1, smoother_degree=3,
                        mg_precision=L.FP32)
     ndof = prob.info.n_dofs
     ncell = prob.info.n_cells

@@ -98,7 +98,9 @@ typedef struct {
   double dt;            /* time step of BDF2 (STAB_NS); <= 0 means stationary (no mass term) */
   int terms;            /* STAB_NS term flags; 0 is taken as MFNS_TERMS_ALL */
   double div_sign;      /* sign of the continuity row; 0 = default (STOKES -1, STAB_NS +1) */
-  int smoother;         /* 0 = Chebyshev around point Jacobi, 1 = Jacobi relaxation */
+  int smoother;         /* 0 = default for the kind: STAB_NS relaxation around point Jacobi (Section 5,
+                           Exp. 3), otherwise Chebyshev around point Jacobi (Section 3);
+                           1 = Chebyshev, 2 = Jacobi relaxation */
   int smoother_degree;  /* Chebyshev degree / relaxation sweeps; 0 = default (5) */
   int mg_order;         /* 0 default (STOKES_A: p then h; STAB_NS: h then p), 1 p_then_h, 2 h_then_p */
   int mg_precision;     /* MFNS_FP64 or MFNS_FP32: precision of the multigrid preconditioner */

@@ -116,7 +116,9 @@ int mfns_problem_create(mfns_ctx* ctx, const mfns_mesh* mesh, const mfns_problem
   const size_t used0 = ctx->budget.used;
   std::unique_ptr<Problem> p = build_problem(mesh->forest, desc->kind, k, ph, desc->mg_order,
                                              desc->coarse_stop_n > 0 ? desc->coarse_stop_n : 2, &ctx->budget);
-  p->smoother = desc->smoother;
+  if (desc->smoother < 0 || desc->smoother > 2) return fail(MFNS_ERR_ARG, "smoother must be 0, 1 or 2");
+  // internal: 0 = Chebyshev, 1 = Jacobi relaxation
+  p->smoother = desc->smoother == 0 ? (desc->kind == MFNS_STAB_NS ? 1 : 0) : desc->smoother - 1;
   p->smoother_degree = desc->smoother_degree > 0 ? desc->smoother_degree : 5;
   p->mg_precision = desc->mg_precision;
   p->restart = desc->fgmres_restart > 0 ? desc->fgmres_restart : 30;

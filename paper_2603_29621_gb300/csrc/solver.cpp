@@ -87,6 +87,8 @@ std::unique_ptr<Problem> build_problem(const Forest& f, int kind, int k, const P
 }
 
 static OpLevel& sys_of(Problem& p) { return p.system ? *p.system : *p.levels[0]; }
+static double host_dot(Problem& p, const double* a, const double* b, int64_t n, cudaStream_t s);
+double arnoldi_spectral_radius(Problem& p, OpLevel& lv, cudaStream_t s);
 
 // Timers record events on the launching stream; they are paused while a graph is captured.
 struct TimerPause {
@@ -198,7 +200,7 @@ void autotune(Problem& p, cudaStream_t s) {
 }
 
 void estimate_lambda(Problem& p, cudaStream_t s) {
-  // diagonals, then 20 power iterations on D^{-1} A (seed 1), lmax = 1.2 x estimate
+  // diagonals, then the Arnoldi estimate of lambda_max(D^{-1} A) per level
   for (auto& lv : p.levels) level_dinv(p, *lv, s);
   if (p.kind == 0) {
     OpLevel& pm = *p.pmass;
@@ -206,54 +208,78 @@ void estimate_lambda(Problem& p, cudaStream_t s) {
     vrecip<double>(pm.dinv[0].as<double>(), pm.dinv[0].as<double>(), pm.n_dofs, s);
     vcast_d2f(pm.dinv[1].as<float>(), pm.dinv[0].as<double>(), pm.n_dofs, s);
   }
-  const int prec = p.mg_precision;
+  // lambda_max of D^{-1} A per level: Arnoldi (classical Gram--Schmidt twice) in FP64 from a
+  // seeded random start; the estimate is the spectral radius of the m x m Hessenberg matrix
+  // (its Ritz values), times 1.2.
   for (size_t l = 0; l < p.levels.size(); ++l) {
     OpLevel& lv = *p.levels[l];
     if (lv.lmax > 0) continue;
-    const int64_t n = lv.n_dofs;
-    std::mt19937_64 rng(1);
-    std::uniform_real_distribution<double> U(-1.0, 1.0);
-    std::vector<double> v0(n);
-    for (auto& v : v0) v = U(rng);
-    Workspace& w = p.ws[prec][l];
-    if (prec == 0) {
-      MFNS_CUDA(cudaMemcpyAsync(w.x.get(), v0.data(), n * 8, cudaMemcpyHostToDevice, s));
-    } else {
-      std::vector<float> vf(v0.begin(), v0.end());
-      MFNS_CUDA(cudaMemcpyAsync(w.x.get(), vf.data(), n * 4, cudaMemcpyHostToDevice, s));
-      MFNS_CUDA(cudaStreamSynchronize(s));
-    }
-    double lam = 0.0;
-    double* d_out = p.scal.as<double>();
-    for (int it = 0; it < 20; ++it) {
-      oplevel_vmult(lv, prec, w.x.get(), w.t.get(), s);
-      double nv = 0, nw = 0;
-      if (prec == 0) {
-        vmul<double>(w.r.as<double>(), lv.dinv[0].as<double>(), w.t.as<double>(), n, s);
-        dot<double>(d_out, w.x.as<double>(), w.x.as<double>(), n, p.part.as<double>(), s);
-        dot<double>(d_out + 1, w.r.as<double>(), w.r.as<double>(), n, p.part.as<double>(), s);
-      } else {
-        vmul<float>(w.r.as<float>(), lv.dinv[1].as<float>(), w.t.as<float>(), n, s);
-        dot<float>(d_out, w.x.as<float>(), w.x.as<float>(), n, p.part.as<double>(), s);
-        dot<float>(d_out + 1, w.r.as<float>(), w.r.as<float>(), n, p.part.as<double>(), s);
-      }
-      double hv[2];
-      MFNS_CUDA(cudaMemcpyAsync(hv, d_out, 16, cudaMemcpyDeviceToHost, s));
-      MFNS_CUDA(cudaStreamSynchronize(s));
-      nv = std::sqrt(hv[0]);
-      nw = std::sqrt(hv[1]);
-      if (nv == 0 || nw == 0 || !std::isfinite(nw)) break;
-      lam = nw / nv;
-      if (prec == 0) {
-        vcopy<double>(w.x.as<double>(), w.r.as<double>(), n, s);
-        vscale<double>(w.x.as<double>(), 1.0 / nw, n, s);
-      } else {
-        vcopy<float>(w.x.as<float>(), w.r.as<float>(), n, s);
-        vscale<float>(w.x.as<float>(), (float)(1.0 / nw), n, s);
-      }
-    }
-    lv.lmax = 1.2 * lam;
+    lv.lmax = 1.2 * arnoldi_spectral_radius(p, lv, s);
   }
+}
+
+// Spectral radius of a small dense matrix H (m x m, row-major) by power iteration with
+// renormalisation: rho = lim (||H^k v|| / ||v||)^(1/k).
+static double small_spectral_radius(const std::vector<double>& H, int m) {
+  std::vector<double> v(m, 1.0), w(m);
+  for (int i = 0; i < m; ++i) v[i] = 1.0 + 0.01 * i;
+  double logsum = 0.0;
+  const int warm = 200, iters = 2000;
+  for (int it = 0; it < warm + iters; ++it) {
+    double nrm = 0.0;
+    for (int i = 0; i < m; ++i) {
+      double t = 0.0;
+      for (int j = 0; j < m; ++j) t += H[i * m + j] * v[j];
+      w[i] = t;
+      nrm += t * t;
+    }
+    nrm = std::sqrt(nrm);
+    if (nrm == 0.0 || !std::isfinite(nrm)) return 0.0;
+    if (it >= warm) logsum += std::log(nrm);
+    for (int i = 0; i < m; ++i) v[i] = w[i] / nrm;
+  }
+  return std::exp(logsum / iters);
+}
+
+double arnoldi_spectral_radius(Problem& p, OpLevel& lv, cudaStream_t s) {
+  const int64_t n = lv.n_dofs;
+  const int m = (int)std::min<int64_t>(std::min(p.restart, 30), std::max<int64_t>(n - 1, 1));
+  double* V = p.V.as<double>();
+  const int64_t stride = sys_of(p).n_dofs;  // V holds restart+1 vectors of the system length
+  const double** Vp = (const double**)p.ptrV.as<const double*>();
+  double* w = p.w.as<double>();
+  const double* dinv = lv.dinv[0].as<double>();
+  std::mt19937_64 rng(1);
+  std::uniform_real_distribution<double> U(-1.0, 1.0);
+  std::vector<double> v0(n);
+  for (auto& v : v0) v = U(rng);
+  MFNS_CUDA(cudaMemcpyAsync(V, v0.data(), n * 8, cudaMemcpyHostToDevice, s));
+  const double n0 = std::sqrt(host_dot(p, V, V, n, s));
+  vscale<double>(V, 1.0 / n0, n, s);
+  std::vector<double> H((size_t)(m + 1) * m, 0.0);
+  int mm = 0;
+  for (int j = 0; j < m; ++j) {
+    oplevel_vmult(lv, 0, V + (size_t)j * stride, p.tmp.get(), s);
+    vmul<double>(w, dinv, p.tmp.as<double>(), n, s);
+    double* hd = p.hvec.as<double>();
+    multidot(hd, nullptr, w, j + 1, n, p.part.as<double>(), Vp, s);
+    multi_axpy(w, Vp, hd, j + 1, n, s);
+    multidot(hd + kMaxDots, nullptr, w, j + 1, n, p.part.as<double>(), Vp, s);
+    multi_axpy(w, Vp, hd + kMaxDots, j + 1, n, s);
+    std::vector<double> hh(2 * kMaxDots);
+    MFNS_CUDA(cudaMemcpyAsync(hh.data(), hd, 2 * kMaxDots * 8, cudaMemcpyDeviceToHost, s));
+    const double hn = std::sqrt(host_dot(p, w, w, n, s));
+    for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = hh[i] + hh[kMaxDots + i];
+    mm = j + 1;
+    if (!(hn > 1e-14) || j + 1 == m) break;
+    H[(size_t)(j + 1) * m + j] = hn;
+    vcopy<double>(V + (size_t)(j + 1) * stride, w, n, s);
+    vscale<double>(V + (size_t)(j + 1) * stride, 1.0 / hn, n, s);
+  }
+  std::vector<double> Hm((size_t)mm * mm);
+  for (int i = 0; i < mm; ++i)
+    for (int j = 0; j < mm; ++j) Hm[(size_t)i * mm + j] = H[(size_t)i * m + j];
+  return small_spectral_radius(Hm, mm);
 }
 
 // Dense LU inverse with partial pivoting (host, in place).

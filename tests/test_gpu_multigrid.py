@@ -94,7 +94,7 @@ def test_transfers_match_oracle(ctx, case):
 @pytest.mark.parametrize("case", HIER[:2], ids=lambda c: f"{c[0]}-{c[1]}d")
 def test_smoother_matches_oracle(ctx, case, smoother):
     kind, dim, n, refine, k, phys = case
-    prob = _gpu_problem(ctx, kind, dim, n, refine, k, lambda_max=1.0, smoother=0 if smoother[0] == "chebyshev" else 1,
+    prob = _gpu_problem(ctx, kind, dim, n, refine, k, lambda_max=1.0, smoother=1 if smoother[0] == "chebyshev" else 2,
                         smoother_degree=smoother[1], **phys)
     levels = solvers.hierarchy(_forest(dim, n, refine), kind, k, nu=phys["nu"], dt=phys.get("dt") or np.inf)
     lv = levels[0]
@@ -118,7 +118,7 @@ def test_smoother_matches_oracle(ctx, case, smoother):
 @pytest.mark.parametrize("case", HIER, ids=lambda c: f"{c[0]}-{c[1]}d-k{c[4]}-{'ball' if c[3] else 'uni'}")
 def test_vcycle_matches_oracle(ctx, case):
     kind, dim, n, refine, k, phys = case
-    prob = _gpu_problem(ctx, kind, dim, n, refine, k, lambda_max=1.0, smoother_degree=3, **phys)
+    prob = _gpu_problem(ctx, kind, dim, n, refine, k, lambda_max=1.0, smoother=1, smoother_degree=3, **phys)
     levels = solvers.hierarchy(_forest(dim, n, refine), kind, k, nu=phys["nu"], dt=phys.get("dt") or np.inf)
     lmax = [1.2 * solvers.power_lmax(lv.A, lv.dinv, iterations=50) for lv in levels[:-1]]
     for l, lm in enumerate(lmax):
