@@ -218,6 +218,21 @@ int mfns_vcycle(mfns_problem* p, int precision, const void* b, void* x, void* st
  * pressure is only fixed up to a constant.  Returns MFNS_ERR_NOT_CONVERGED when maxit is hit. */
 int mfns_solve(mfns_problem* p, const void* b, void* x, mfns_solve_info* info, void* stream);
 
+/* ---- batched solves (continuous batching of many problems) ---------------------------------- */
+/* Start a solve as in mfns_solve (same FGMRES, same preconditioner), without iterating: the
+ * right-hand side is projected, x set to zero and the initial residual norm read back (one
+ * synchronisation).  All later device work of this solve runs on `stream`; give every problem
+ * of a batch its own stream so their work overlaps on the device. */
+int mfns_solve_begin(mfns_problem* p, const void* b, void* x, void* stream);
+/* One round: every listed problem whose solve is still running performs one FGMRES iteration
+ * (Section 3).  The device work of all of them is enqueued first, each on its own stream, then
+ * each is completed on the host (Givens rotation, and at the end of a restart cycle the update
+ * of x and the true residual).  running[i] (optional) is set to 1 while problem i iterates.
+ * Problems are independent: the result of each is the same alone and in any batch. */
+int mfns_batch_step(mfns_problem** problems, int n, int* running);
+/* Iterations, relative residual and convergence of the last (or current) solve of p. */
+int mfns_solve_status(const mfns_problem* p, mfns_solve_info* info);
+
 #ifdef __cplusplus
 }
 #endif

@@ -11,8 +11,10 @@ Readings of the paper (Section 2 and the configurations built here):
   2:1 closure refines every cell that touches (face, edge or vertex) a cell
   two or more levels finer, until no such cell remains.
 * A coarser global-coarsening level is obtained by replacing the cells of the
-  finest level by their parents; a uniform mesh with an even number of root
-  cells per direction coarsens to the uniform mesh with half as many.
+  finest level by their parents; a uniform mesh with n root cells per
+  direction coarsens to the uniform mesh with ceil(n/2) (nested for even n,
+  non-nested for odd n: Section 2 lists non-nested multigrid among the
+  supported hierarchies, and its transfer is the same interpolation).
 * Hanging nodes (Section 2, "resolution of (hanging-node) constraints"): a
   node that lies in the closure of a coarser active cell without being a node
   of that cell takes the value of the coarser cell's finite-element function
@@ -84,12 +86,12 @@ class Forest:
 
     def coarsen_finest(self):
         """One global-coarsening step: the finest-level cells are replaced by their parents;
-        a uniform forest with even n becomes the uniform forest with n/2 root cells."""
+        a uniform forest with n root cells becomes the uniform forest with ceil(n/2)."""
         L = self.max_level
         if L == 0:
-            if self.n % 2 != 0 or self.n < 2:
-                raise ValueError("cannot coarsen a uniform mesh with odd n")
-            return uniform(self.dim, self.n // 2)
+            if self.n < 2:
+                raise ValueError("cannot coarsen a single cell")
+            return uniform(self.dim, (self.n + 1) // 2)
         fine = self.cells[self.cells[:, 0] == L]
         keep = self.cells[self.cells[:, 0] != L]
         par = np.unique(np.concatenate([[[L - 1]] * len(fine), fine[:, 1:] // 2], axis=1), axis=0)

@@ -12,6 +12,8 @@ Readings of the paper (Sections 2, 3 and 5):
   lmin = lmax / 20.
 * Relaxation around point Jacobi (Section 5, Exp. 3): x <- x + w D^{-1} (b - A x)
   with w = 2 / (lmin + lmax).
+* Hierarchy: uniform meshes coarsen n -> ceil(n/2) while n > 2 (non-nested
+  for odd n, Section 2); the coarsest level is therefore tiny.
 * Coarse solver: direct (dense) solve; a pressure null space (constant
   pressure with all-Dirichlet velocity) is removed by adding e e^T, e the
   normalised indicator of the free pressure DoFs.
@@ -86,11 +88,11 @@ def cg_jacobi_fixed(M, dinv, b, iterations):
 # -- hierarchy -------------------------------------------------------------------
 def coarse_forests(forest, stop_n=2):
     """Global-coarsening sequence of meshes, finest first; uniform meshes are
-    coarsened while n is even and n > stop_n."""
+    coarsened to ceil(n/2) cells per direction while n > stop_n."""
     out = [forest]
     f = forest
     while True:
-        if f.max_level == 0 and (f.n % 2 != 0 or f.n <= stop_n):
+        if f.max_level == 0 and f.n <= stop_n:
             break
         f = f.coarsen_finest()
         out.append(f)

@@ -71,6 +71,9 @@ _SIGS = {
     "mfns_restrict": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
     "mfns_vcycle": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
     "mfns_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(SolveInfo), C.c_void_p]),
+    "mfns_solve_begin": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "mfns_batch_step": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.POINTER(C.c_int)]),
+    "mfns_solve_status": (C.c_int, [C.c_void_p, C.POINTER(SolveInfo)]),
 }
 
 EXPORTED = tuple(_SIGS)

@@ -185,6 +185,14 @@ class Problem:
             L.check(code)
         return si
 
+    def solve_begin(self, b, x, stream=None):
+        L.check(self.lib.mfns_solve_begin(self.h, _ptr(b), _ptr(x), _stream(stream)))
+
+    def solve_status(self):
+        si = L.SolveInfo()
+        L.check(self.lib.mfns_solve_status(self.h, C.byref(si)))
+        return si
+
     def close(self):
         if self.h:
             self.lib.mfns_problem_destroy(self.h)
@@ -195,3 +203,12 @@ class Problem:
             self.close()
         except Exception:
             pass
+
+
+def batch_step(problems):
+    """One FGMRES iteration for every running solve of `problems`; returns the running flags."""
+    n = len(problems)
+    arr = (C.c_void_p * n)(*[p.h for p in problems])
+    run = (C.c_int * n)()
+    L.check(L.load().mfns_batch_step(arr, n, run))
+    return [bool(v) for v in run]

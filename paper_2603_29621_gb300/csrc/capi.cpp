@@ -313,6 +313,45 @@ int mfns_solve(mfns_problem* p, const void* b, void* x, mfns_solve_info* info, v
   API_END
 }
 
+int mfns_solve_begin(mfns_problem* p, const void* b, void* x, void* stream) {
+  API_BEGIN
+  if (!p || !b || !x) return fail(MFNS_ERR_ARG, "bad arguments");
+  if (p->p->kind == MFNS_PMASS) return fail(MFNS_ERR_UNSUPPORTED, "no solver for the pressure mass problem");
+  MFNS_CUDA(cudaSetDevice(p->ctx->device));
+  krylov_begin(*p->p, (const double*)b, (double*)x, S(stream));
+  API_END
+}
+
+int mfns_batch_step(mfns_problem** ps, int n, int* running) {
+  API_BEGIN
+  if (!ps || n < 0) return fail(MFNS_ERR_ARG, "bad arguments");
+  for (int i = 0; i < n; ++i)
+    if (!ps[i]) return fail(MFNS_ERR_ARG, "null problem in batch");
+  if (n > 0) MFNS_CUDA(cudaSetDevice(ps[0]->ctx->device));
+  // enqueue the device work of every active solve (each on its own stream), then complete them
+  for (int i = 0; i < n; ++i) krylov_enqueue(*ps[i]->p);
+  for (int i = 0; i < n; ++i) {
+    Problem& P = *ps[i]->p;
+    bool run = false;
+    if (P.kry.active) {
+      MFNS_CUDA(cudaStreamSynchronize(P.kry.stream));
+      run = krylov_complete(P);
+    }
+    if (running) running[i] = run ? 1 : 0;
+  }
+  API_END
+}
+
+int mfns_solve_status(const mfns_problem* p, mfns_solve_info* info) {
+  if (!p || !info) return fail(MFNS_ERR_ARG, "bad arguments");
+  const Krylov& K = p->p->kry;
+  info->iterations = K.it;
+  info->rel_residual = K.relres;
+  info->seconds = 0.0;
+  info->converged = K.converged ? 1 : 0;
+  return MFNS_OK;
+}
+
 }  // extern "C"
 
 static bool op_supported_kind(int dim, int kind, int k) {

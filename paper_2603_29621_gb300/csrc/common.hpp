@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <mutex>
 #include <stdexcept>
 #include <string>
 #include <vector>
@@ -26,15 +27,21 @@ struct Error : std::runtime_error {
       throw ::mfns::Error(::mfns::kErrCuda, std::string(#expr) + ": " + cudaGetErrorString(e_)); \
   } while (0)
 
-// Per-context HBM accounting: every library allocation is charged against the budget.
+// Per-context HBM accounting: every library allocation is charged against the budget
+// (thread-safe: problems of one context may be created and destroyed from several threads).
 struct Budget {
   size_t limit = 0, used = 0, peak = 0;
+  std::mutex mu;
   void charge(size_t b) {
+    std::lock_guard<std::mutex> lock(mu);
     if (limit && used + b > limit) throw Error(kErrBudget, "HBM budget exceeded");
     used += b;
     if (used > peak) peak = used;
   }
-  void release(size_t b) { used -= b; }
+  void release(size_t b) {
+    std::lock_guard<std::mutex> lock(mu);
+    used -= b;
+  }
 };
 
 class DevBuf {

@@ -223,12 +223,12 @@ Forest forest_refine_ball(Forest f, const double centre[3], double radius, int l
 
 bool forest_can_coarsen(const Forest& f, int stop_n) {
   if (f.max_level() > 0) return true;
-  return f.n % 2 == 0 && f.n > stop_n;
+  return f.n > stop_n;
 }
 
 Forest forest_coarsen(const Forest& f) {
   int L = f.max_level();
-  if (L == 0) return forest_uniform(f.dim, f.n / 2);
+  if (L == 0) return forest_uniform(f.dim, (f.n + 1) / 2);  // non-nested when n is odd
   Forest g;
   g.dim = f.dim;
   g.n = f.n;

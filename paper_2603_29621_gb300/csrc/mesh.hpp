@@ -38,7 +38,7 @@ Forest forest_uniform(int dim, int n);
 Forest forest_refine(const Forest& f, const std::vector<char>& mask);
 Forest forest_balance(Forest f);  // 2:1 over faces, edges and vertices
 Forest forest_refine_ball(Forest f, const double centre[3], double radius, int levels);
-// one global-coarsening step (finest level -> parents; uniform even n -> n/2)
+// one global-coarsening step (finest level -> parents; uniform n -> ceil(n/2), non-nested for odd n)
 bool forest_can_coarsen(const Forest& f, int stop_n);
 Forest forest_coarsen(const Forest& f);
 

@@ -86,6 +86,16 @@ struct Workspace {
   DevBuf r, d, t, b, x;                 // per level, per precision
 };
 
+// FGMRES state of one solve (resumable: one Arnoldi step per round)
+struct Krylov {
+  bool active = false, converged = false;
+  int it = 0, j = 0;
+  double bnorm = 0.0, relres = 0.0;
+  std::vector<double> H, cs, sn, g;
+  double* x = nullptr;
+  cudaStream_t stream = nullptr;
+};
+
 struct Problem {
   int kind = 0, dim = 3, k = 2;
   Physics phys;
@@ -115,6 +125,8 @@ struct Problem {
   cudaGraphExec_t pc_graph = nullptr;
   cudaGraphExec_t vc_graph[2] = {nullptr, nullptr};
   DevBuf pc_in, pc_out, vc_in[2], vc_out[2];
+  Krylov kry;
+  double* hh_host = nullptr;            // pinned: Gram--Schmidt coefficients of the last step
   size_t bytes = 0;
   ~Problem();
 };
@@ -137,5 +149,10 @@ void setup_coarse(Problem& p, cudaStream_t s);
 void alloc_workspaces(Problem& p);
 // Solve (FP64 FGMRES); returns iterations, writes relres; throws on CUDA errors
 int fgmres_solve(Problem& p, const double* b, double* x, double* relres, bool* converged, cudaStream_t s);
+// Resumable FGMRES: begin (synchronises once), then per step enqueue (async) and complete (host,
+// after the stream is synchronised); complete returns false once the solve has finished.
+void krylov_begin(Problem& p, const double* b, double* x, cudaStream_t s);
+void krylov_enqueue(Problem& p);
+bool krylov_complete(Problem& p);
 
 }  // namespace mfns

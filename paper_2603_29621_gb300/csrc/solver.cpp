@@ -39,6 +39,7 @@ static int sys_op_of(int kind) {
 Problem::~Problem() {
   invalidate_graphs(*this);
   if (cap_stream) cudaStreamDestroy(cap_stream);
+  if (hh_host) cudaFreeHost(hh_host);
 }
 
 std::unique_ptr<Problem> build_problem(const Forest& f, int kind, int k, const Physics& ph, int mg_order,
@@ -140,6 +141,7 @@ void alloc_workspaces(Problem& p) {
   for (int j = 0; j < m; ++j) pz[j] = p.Z.as<double>() + (size_t)j * n;
   p.ptrV = upload(bud, pv);
   p.ptrZ = upload(bud, pz);
+  if (!p.hh_host) MFNS_CUDA(cudaMallocHost(&p.hh_host, (2 * kMaxDots + 2) * sizeof(double)));
   p.mg_b32.alloc(bud, n * 4);
   p.mg_x32.alloc(bud, n * 4);
   p.pc_in.alloc(bud, n * 8);
@@ -557,89 +559,152 @@ static void precondition_body(Problem& p, const double* v, double* z, cudaStream
   }
 }
 
-int fgmres_solve(Problem& p, const double* b_in, double* x, double* relres, bool* converged, cudaStream_t s) {
+// ---------------------------------------------------------------------- FGMRES as a state machine
+// One call of krylov_enqueue + krylov_complete performs one Arnoldi step (preconditioner, operator,
+// CGS2, Givens); a restart cycle ends with the update of x and a true residual.  Batched rounds
+// enqueue the device work of many problems (each on its own stream) before completing any.
+
+static void start_cycle(Problem& p, double beta) {
   OpLevel& S = sys_of(p);
+  Krylov& K = p.kry;
+  const int m = p.restart;
+  vcopy<double>(p.V.as<double>(), p.tmp.as<double>(), S.n_dofs, K.stream);
+  vscale<double>(p.V.as<double>(), 1.0 / beta, S.n_dofs, K.stream);
+  std::fill(K.g.begin(), K.g.end(), 0.0);
+  K.g[0] = beta;
+  K.j = 0;
+  (void)m;
+}
+
+void krylov_begin(Problem& p, const double* b_in, double* x, cudaStream_t s) {
+  OpLevel& S = sys_of(p);
+  Krylov& K = p.kry;
   const int64_t n = S.n_dofs;
   const int m = p.restart;
-  double* b = p.sys_r.as<double>();   // projected right-hand side
-  double* r = p.tmp.as<double>();
-  double* w = p.w.as<double>();
-  double* V = p.V.as<double>();
-  double* Z = p.Z.as<double>();
-  const double** Vp = (const double**)p.ptrV.as<const double*>();
-  const double** Zp = (const double**)p.ptrZ.as<const double*>();
+  K = Krylov();
+  K.stream = s;
+  K.x = x;
+  K.H.assign((size_t)(m + 1) * m, 0.0);
+  K.cs.assign(m, 0.0);
+  K.sn.assign(m, 0.0);
+  K.g.assign(m + 1, 0.0);
+  double* b = p.sys_r.as<double>();  // projected right-hand side
   vcopy<double>(b, b_in, n, s);
   project_pressure<double>(S, b, p.scal.as<double>(), p.part.as<double>(), s);
   vzero<double>(x, n, s);
-  const double bnorm = std::sqrt(host_dot(p, b, b, n, s));
-  *converged = true;
-  *relres = 0.0;
-  if (bnorm == 0.0) return 0;
-  vcopy<double>(r, b, n, s);
-  int it = 0;
-  std::vector<double> H((m + 1) * m), cs(m), sn(m), g(m + 1), h(m + 2);
-  while (true) {
-    const double beta = std::sqrt(host_dot(p, r, r, n, s));
-    *relres = beta / bnorm;
-    if (beta <= p.tol * bnorm) break;
-    if (it >= p.maxit) {
-      *converged = false;
-      break;
-    }
-    vcopy<double>(V, r, n, s);
-    vscale<double>(V, 1.0 / beta, n, s);
-    std::fill(g.begin(), g.end(), 0.0);
-    g[0] = beta;
-    int jdone = 0;
-    for (int j = 0; j < m; ++j) {
-      double* zj = Z + (size_t)j * n;
-      precondition(p, V + (size_t)j * n, zj, s);
-      project_pressure<double>(S, zj, p.scal.as<double>(), p.part.as<double>(), s);
-      oplevel_vmult(S, 0, zj, w, s);
-      // classical Gram--Schmidt, two passes
-      double* hd = p.hvec.as<double>();
-      multidot(hd, nullptr, w, j + 1, n, p.part.as<double>(), Vp, s);
-      multi_axpy(w, Vp, hd, j + 1, n, s);
-      multidot(hd + kMaxDots, nullptr, w, j + 1, n, p.part.as<double>(), Vp, s);
-      multi_axpy(w, Vp, hd + kMaxDots, j + 1, n, s);
-      std::vector<double> hh(2 * kMaxDots);
-      MFNS_CUDA(cudaMemcpyAsync(hh.data(), hd, 2 * kMaxDots * 8, cudaMemcpyDeviceToHost, s));
-      const double hn = std::sqrt(host_dot(p, w, w, n, s));
-      for (int i = 0; i <= j; ++i) H[i * m + j] = hh[i] + hh[kMaxDots + i];
-      H[(j + 1) * m + j] = hn;
-      if (hn > 0) {
-        vcopy<double>(V + (size_t)(j + 1) * n, w, n, s);
-        vscale<double>(V + (size_t)(j + 1) * n, 1.0 / hn, n, s);
-      }
-      for (int i = 0; i < j; ++i) {
-        const double t = cs[i] * H[i * m + j] + sn[i] * H[(i + 1) * m + j];
-        H[(i + 1) * m + j] = -sn[i] * H[i * m + j] + cs[i] * H[(i + 1) * m + j];
-        H[i * m + j] = t;
-      }
-      const double den = std::hypot(H[j * m + j], H[(j + 1) * m + j]);
-      cs[j] = H[j * m + j] / den;
-      sn[j] = H[(j + 1) * m + j] / den;
-      H[j * m + j] = den;
-      H[(j + 1) * m + j] = 0.0;
-      g[j + 1] = -sn[j] * g[j];
-      g[j] = cs[j] * g[j];
-      ++it;
-      jdone = j + 1;
-      if (std::fabs(g[j + 1]) <= p.tol * bnorm || it >= p.maxit) break;
-    }
-    std::vector<double> y(jdone);
-    for (int i = jdone - 1; i >= 0; --i) {
-      double sacc = g[i];
-      for (int k2 = i + 1; k2 < jdone; ++k2) sacc -= H[i * m + k2] * y[k2];
-      y[i] = sacc / H[i * m + i];
-    }
-    MFNS_CUDA(cudaMemcpyAsync(p.yvec.get(), y.data(), jdone * 8, cudaMemcpyHostToDevice, s));
-    multi_axpy_add(x, Zp, p.yvec.as<double>(), jdone, n, s);
-    MFNS_CUDA(cudaStreamSynchronize(s));
-    oplevel_vmult(S, 0, x, w, s);
-    vsub<double>(r, b, w, n, s);
+  vcopy<double>(p.tmp.as<double>(), b, n, s);  // r = b - A 0
+  K.bnorm = std::sqrt(host_dot(p, b, b, n, s));
+  K.relres = 0.0;
+  K.active = true;
+  if (K.bnorm == 0.0) {
+    K.active = false;
+    K.converged = true;
+    return;
   }
-  return it;
+  K.relres = 1.0;
+  start_cycle(p, K.bnorm);
+}
+
+// Device work of one Arnoldi step (asynchronous on the problem's stream).
+void krylov_enqueue(Problem& p) {
+  Krylov& K = p.kry;
+  if (!K.active) return;
+  OpLevel& S = sys_of(p);
+  const int64_t n = S.n_dofs;
+  cudaStream_t s = K.stream;
+  const int j = K.j;
+  double* V = p.V.as<double>();
+  double* zj = p.Z.as<double>() + (size_t)j * n;
+  const double** Vp = (const double**)p.ptrV.as<const double*>();
+  double* w = p.w.as<double>();
+  precondition(p, V + (size_t)j * n, zj, s);
+  project_pressure<double>(S, zj, p.scal.as<double>(), p.part.as<double>(), s);
+  oplevel_vmult(S, 0, zj, w, s);
+  double* hd = p.hvec.as<double>();
+  multidot(hd, nullptr, w, j + 1, n, p.part.as<double>(), Vp, s);
+  multi_axpy(w, Vp, hd, j + 1, n, s);
+  multidot(hd + kMaxDots, nullptr, w, j + 1, n, p.part.as<double>(), Vp, s);
+  multi_axpy(w, Vp, hd + kMaxDots, j + 1, n, s);
+  dot<double>(p.scal.as<double>() + 12, w, w, n, p.part.as<double>(), s);
+  MFNS_CUDA(cudaMemcpyAsync(p.hh_host, hd, 2 * kMaxDots * 8, cudaMemcpyDeviceToHost, s));
+  MFNS_CUDA(cudaMemcpyAsync(p.hh_host + 2 * kMaxDots, p.scal.as<double>() + 12, 8, cudaMemcpyDeviceToHost, s));
+}
+
+// Host part of the step (after the problem's stream has been synchronised); ends the restart
+// cycle when needed.  Returns true while the solve is still running.
+bool krylov_complete(Problem& p) {
+  Krylov& K = p.kry;
+  if (!K.active) return false;
+  OpLevel& S = sys_of(p);
+  const int64_t n = S.n_dofs;
+  const int m = p.restart;
+  cudaStream_t s = K.stream;
+  const int j = K.j;
+  double* V = p.V.as<double>();
+  std::vector<double>& H = K.H;
+  const double* hh = p.hh_host;
+  const double hn = std::sqrt(std::max(hh[2 * kMaxDots], 0.0));
+  for (int i = 0; i <= j; ++i) H[i * m + j] = hh[i] + hh[kMaxDots + i];
+  H[(j + 1) * m + j] = hn;
+  if (hn > 0) {
+    vcopy<double>(V + (size_t)(j + 1) * n, p.w.as<double>(), n, s);
+    vscale<double>(V + (size_t)(j + 1) * n, 1.0 / hn, n, s);
+  }
+  for (int i = 0; i < j; ++i) {
+    const double t = K.cs[i] * H[i * m + j] + K.sn[i] * H[(i + 1) * m + j];
+    H[(i + 1) * m + j] = -K.sn[i] * H[i * m + j] + K.cs[i] * H[(i + 1) * m + j];
+    H[i * m + j] = t;
+  }
+  const double den = std::hypot(H[j * m + j], H[(j + 1) * m + j]);
+  K.cs[j] = H[j * m + j] / den;
+  K.sn[j] = H[(j + 1) * m + j] / den;
+  H[j * m + j] = den;
+  H[(j + 1) * m + j] = 0.0;
+  K.g[j + 1] = -K.sn[j] * K.g[j];
+  K.g[j] = K.cs[j] * K.g[j];
+  ++K.it;
+  K.j = j + 1;
+  const bool cycle_end = std::fabs(K.g[j + 1]) <= p.tol * K.bnorm || K.it >= p.maxit || K.j == m;
+  if (!cycle_end) return true;
+  // end of the restart cycle: x += Z y, true residual r = b - A x
+  const int jd = K.j;
+  std::vector<double> y(jd);
+  for (int i = jd - 1; i >= 0; --i) {
+    double acc = K.g[i];
+    for (int k2 = i + 1; k2 < jd; ++k2) acc -= H[i * m + k2] * y[k2];
+    y[i] = acc / H[i * m + i];
+  }
+  MFNS_CUDA(cudaMemcpyAsync(p.yvec.get(), y.data(), jd * 8, cudaMemcpyHostToDevice, s));
+  multi_axpy_add(K.x, (const double**)p.ptrZ.as<const double*>(), p.yvec.as<double>(), jd, n, s);
+  oplevel_vmult(S, 0, K.x, p.w.get(), s);
+  vsub<double>(p.tmp.as<double>(), p.sys_r.as<double>(), p.w.as<double>(), n, s);
+  const double beta = std::sqrt(host_dot(p, p.tmp.as<double>(), p.tmp.as<double>(), n, s));
+  K.relres = beta / K.bnorm;
+  std::fill(H.begin(), H.end(), 0.0);
+  if (beta <= p.tol * K.bnorm) {
+    K.active = false;
+    K.converged = true;
+    return false;
+  }
+  if (K.it >= p.maxit) {
+    K.active = false;
+    K.converged = false;
+    return false;
+  }
+  start_cycle(p, beta);
+  return true;
+}
+
+int fgmres_solve(Problem& p, const double* b_in, double* x, double* relres, bool* converged, cudaStream_t s) {
+  krylov_begin(p, b_in, x, s);
+  while (p.kry.active) {
+    krylov_enqueue(p);
+    MFNS_CUDA(cudaStreamSynchronize(s));
+    krylov_complete(p);
+  }
+  *relres = p.kry.relres;
+  *converged = p.kry.converged;
+  return p.kry.it;
 }
 
 }  // namespace mfns

@@ -1,4 +1,5 @@
-// Separable transfers between uniform meshes (Eq. 4 on tensor-product grids).
+// Separable transfers between uniform meshes (Eq. 4 on tensor-product grids), nested
+// (n -> n/2) or non-nested (odd n -> (n+1)/2, Section 2) h-steps and p-steps.
 //
 // On a uniform mesh the Q_k space is the tensor product of 1D spaces, and the
 // interpolation P of Eq. 4 (coarse FE function evaluated at the fine nodes) is
@@ -108,7 +109,7 @@ void to_csr(const std::vector<double>& M, int64_t rows, int64_t cols, std::vecto
 bool build_separable(SepTransfer& t, const OpLevel& fine, const OpLevel& coarse, Budget* bud) {
   if (!fine.forest.uniform() || !coarse.forest.uniform() || !fine.L.structured || !coarse.L.structured) return false;
   const int nf = fine.forest.n, nc = coarse.forest.n, kf = fine.k, kc = coarse.k;
-  const bool h = kf == kc && nf == 2 * nc;
+  const bool h = kf == kc && nc == (nf + 1) / 2 && nc < nf;  // nested (even nf) or non-nested (odd nf)
   const bool p = nf == nc && kf > kc;
   if (!h && !p) return false;
   t.dim = fine.dim;
@@ -122,8 +123,16 @@ bool build_separable(SepTransfer& t, const OpLevel& fine, const OpLevel& coarse,
   for (int64_t g = 0; g < t.Mf; ++g) {
     int64_t cf = g / kf, s = g % kf;
     if (cf == nf) { cf = nf - 1; s = kf; }
-    int64_t cc = h ? cf / 2 : cf;
-    const double xi = h ? 0.5 * ((cf % 2) + xf[s]) : xf[s];
+    int64_t cc = cf;
+    double xi = xf[s];
+    if (h && nf == 2 * nc) {  // nested: child half of the parent cell
+      cc = cf / 2;
+      xi = 0.5 * ((cf % 2) + xf[s]);
+    } else if (h) {           // non-nested: locate the fine node in the coarse mesh
+      const double X = (double(cf) + xf[s]) * double(nc) / double(nf);
+      cc = std::min<int64_t>((int64_t)std::floor(X), nc - 1);
+      xi = X - double(cc);
+    }
     for (int m = 0; m <= kc; ++m) P1[g * t.Mc + (int64_t)kc * cc + m] = lagrange(xc, m, xi);
   }
   std::vector<double> P1T(t.Mc * t.Mf);

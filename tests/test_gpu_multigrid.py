@@ -59,6 +59,8 @@ def _from_gpu(t, perm):
 BALL = ((0.3, 0.3, 0.3), 0.3, 1)
 HIER = [
     ("stab_ns", 3, 4, None, 2, dict(nu=1e-2, dt=1e-2)),
+    ("stab_ns", 3, 5, None, 2, dict(nu=1e-2, dt=1e-2)),     # 5 -> 3 -> 2: non-nested h-steps
+    ("stokes_a", 2, 7, None, 3, dict(nu=1.0)),
     ("stokes_a", 3, 2, BALL, 2, dict(nu=1.0)),
     ("stokes_a", 2, 4, BALL, 3, dict(nu=1.0)),
     ("stab_ns", 2, 4, BALL, 2, dict(nu=1e-2, dt=1e-1)),
@@ -91,7 +93,7 @@ def test_transfers_match_oracle(ctx, case):
 
 
 @pytest.mark.parametrize("smoother", [("chebyshev", 3), ("chebyshev", 5), ("jacobi", 4)])
-@pytest.mark.parametrize("case", HIER[:2], ids=lambda c: f"{c[0]}-{c[1]}d")
+@pytest.mark.parametrize("case", [HIER[0], HIER[3]], ids=lambda c: f"{c[0]}-{c[1]}d")
 def test_smoother_matches_oracle(ctx, case, smoother):
     kind, dim, n, refine, k, phys = case
     prob = _gpu_problem(ctx, kind, dim, n, refine, k, lambda_max=1.0, smoother=1 if smoother[0] == "chebyshev" else 2,

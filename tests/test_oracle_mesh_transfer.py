@@ -39,6 +39,7 @@ def test_coarsening_sequence():
     seq = solvers.coarse_forests(f)
     assert [s.max_level for s in seq] == [2, 1, 0, 0, 0]
     assert [s.n for s in seq] == [8, 8, 8, 4, 2]
+    assert [s.n for s in solvers.coarse_forests(mesh.uniform(3, 47))] == [47, 24, 12, 6, 3, 2]
     assert all(mesh.is_balanced(s) for s in seq)
     assert seq[2].n_cells == 512
 
@@ -55,6 +56,28 @@ def _poly(dim, deg, seed=0, bubble=False):
             out = out * np.prod(x * (1 - x), axis=1)
         return out
     return f
+
+
+@pytest.mark.parametrize("kind,dim,n", [("stokes_a", 2, 5), ("stab_ns", 3, 3)])
+def test_non_nested_prolongation_reproduces_polynomials(kind, dim, n):
+    """Uniform n -> ceil(n/2) for odd n (non-nested meshes): P I_c(poly) = I_f(poly) still holds."""
+    fine_forest = mesh.uniform(dim, n)
+    coarse_forest = fine_forest.coarsen_finest()
+    assert coarse_forest.n == (n + 1) // 2
+    ncomp = dim if kind == "stokes_a" else dim + 1
+    for k in (1, 2):
+        pc = assemble.Problem(coarse_forest, kind, k)
+        pf = assemble.Problem(fine_forest, kind, k)
+        P = transfer.prolongation(pc, pf)
+        base = _poly(dim, max(k - 2, 0), bubble=True) if k >= 2 else (lambda x: 0 * x[:, 0])
+        pfun = _poly(dim, k, seed=4)
+        fun = lambda x: np.concatenate([np.stack([base(x)] * dim, 1), pfun(x)[:, None]], 1)[:, :ncomp]
+        y = P @ pc.dofs.interpolate(fun)
+        xf = pf.dofs.interpolate(fun)
+        free = pf.dofs.free
+        assert np.abs(y[free] - xf[free]).max() < 1e-12
+        # a non-nested P is not a plain injection: some fine nodes see several coarse nodes
+        assert (np.diff(P.tocsr().indptr) > 1).any()
 
 
 @pytest.mark.parametrize("kind,dim", [("stokes_a", 2), ("stab_ns", 3), ("stokes_a", 3)])
