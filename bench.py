@@ -29,7 +29,8 @@ sys.path.insert(0, ROOT)
 
 METRIC = "DoF/s stab-NS Q2 vmult; solves/s + p50/p99 latency, FP32-MG vs FP64 @1e-8"
 UNIT = "DoF/s"
-FLOP_PER_CELL = 22700.0          # algorithmic flops per Q2Q2 cell apply (frozen state recomputed)
+FLOP_PER_CELL = 17000.0          # algorithmic flops per Q2Q2 cell apply, frozen point values precomputed
+FQ_BYTES_PER_CELL_F32 = 16 * 27 * 4  # precomputed frozen point data read per cell (u, grad u, Rbar, tau)
 FP32_LANES, N_SM, SM_MHZ_MAX = 128, 152, 2070.0
 CPU_SAMPLE_N = 12                # oracle sample: 12^3 cells of the same operator
 
@@ -43,6 +44,8 @@ def parse():
     ap.add_argument("--n", type=int, default=64)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--vmult-only", action="store_true", help="time only the FP32 apply (profiling runs)")
+    ap.add_argument("--no-solves", action="store_true", help="skip the solve and serving sections")
+    ap.add_argument("--serve-requests", type=int, default=32, help="requests of the bounded serving stream")
     return ap.parse_args()
 
 
@@ -140,6 +143,95 @@ def cpu_baseline(seconds=10.0):
                        f"operator ({A.shape[0]} DoFs, {A.nnz} nnz), {reps} products in {dt:.1f} s; "
                        f"assembly {t_asm:.1f} s not timed"),
             "ms_per_step": 1e3 * dt / reps, "n_dofs": int(A.shape[0])}
+
+
+def solve_section(api, L, inputs, torch):
+    """Config 4 (stabilised NS 48^3 Q2Q2, three viscosities) and config 3 (Stokes Q2/Q1 on the
+    ball-refined 32^3 mesh): FGMRES in FP64 with FP64 or FP32 multigrid; iterations, solve time
+    and error against the manufactured discrete solution x* (smooth fields sampled at the
+    support points, b = A x*)."""
+    ctx = api.Context(torch.cuda.current_device())
+    out = {"stab_ns_48": [], "stokes_ball_32": []}
+
+    def one(kind, n, k, nu, dt, mgp, ball, tol):  # -> (record, solution with pressure mean removed)
+        m = api.Mesh(ctx, 3, n)
+        if ball:
+            m.refine_ball(*ball)
+        t0 = time.perf_counter()
+        p = api.Problem(ctx, m, kind=kind, degree=k, nu=nu, dt=dt, mg_precision=mgp, tol=tol, maxit=300)
+        setup = time.perf_counter() - t0
+        xyz, fld = p.support_points()
+        xs = torch.tensor(inputs.smooth_solution(xyz, fld, 3, nu if kind == L.STOKES else 1.0), device="cuda")
+        b = torch.empty_like(xs)
+        p.vmult(xs, b)
+        x = torch.zeros_like(xs)
+        p.solve(b, x, raise_on_nonconvergence=False)           # warm-up (graph capture)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        info = p.solve(b, x, raise_on_nonconvergence=False)
+        torch.cuda.synchronize()
+        dt_solve = time.perf_counter() - t0
+        ps = slice(p.info.n_velocity_dofs, None) if kind == L.STOKES else slice(3, None, 4)
+        d = x - xs
+        d[ps] -= d[ps].mean()
+        xr = xs.clone()
+        xr[ps] -= xr[ps].mean()
+        err = float(torch.linalg.norm(d) / torch.linalg.norm(xr))
+        r = {"mg": "fp32" if mgp else "fp64", "nu": nu, "dofs": p.info.n_dofs, "cells": p.info.n_cells,
+             "levels": p.info.n_levels, "iterations": info.iterations, "rel_residual": info.rel_residual,
+             "converged": bool(info.converged), "solve_s": dt_solve, "setup_s": setup, "error_vs_xstar": err}
+        xa = x.clone()
+        xa[ps] -= xa[ps].mean()
+        p.close()
+        m.close()
+        return r, xa
+
+    def pair(key, *a):
+        r64, x64 = one(*a[:5], L.FP64, *a[5:])
+        r32, x32 = one(*a[:5], L.FP32, *a[5:])
+        r32["rel_diff_vs_fp64_mg"] = float(torch.linalg.norm(x32 - x64) / torch.linalg.norm(x64))
+        out[key] += [r64, r32]
+
+    for nu in (1e-1, 1e-2, 1e-3):
+        pair("stab_ns_48", L.STAB_NS, 48, 2, nu, 1e-2, None, 1e-11)
+    pair("stokes_ball_32", L.STOKES, 32, 2, 1.0, 0.0, ((0.5, 0.5, 0.5), 0.25, 2), 1e-11)
+    for key in list(out):
+        r64 = [r for r in out[key] if r["mg"] == "fp64"]
+        r32 = [r for r in out[key] if r["mg"] == "fp32"]
+        out[key + "_fp32_speedup"] = sum(r["solve_s"] for r in r64) / max(sum(r["solve_s"] for r in r32), 1e-12)
+    ctx.close()
+    return out
+
+
+def serving_section(api, L, torch, count):
+    """Config 5, bounded: a seeded Poisson stream of `count` requests (n in 8..48, k in 1..3, nu
+    log-uniform in [1e-3, 1], Stokes / stabilised NS 50/50, b = A x*), offered at 0.8 x the measured
+    single-stream throughput, served with FP32 and with FP64 multigrid."""
+    from paper_2603_29621_gb300 import serve
+    ctx = api.Context(torch.cuda.current_device(), hbm_budget_bytes=150 * 1024 ** 3)
+    probe = serve.poisson_stream(6, rate=1.0, seed=3)
+    t0 = time.perf_counter()
+    for req in probe:
+        serve.solve_alone(ctx, req)
+    mu = len(probe) / (time.perf_counter() - t0)          # single-stream solves/s incl. set-up
+    rate = 0.8 * mu
+    reqs = serve.poisson_stream(count, rate=rate)
+    out = {"requests": count, "offered_rate_per_s": rate, "single_stream_solves_per_s": mu}
+    sols = {}
+    for name, mgp in (("fp64_mg", L.FP64), ("fp32_mg", L.FP32)):
+        srv = serve.Server(ctx, max_active=16, mg_precision=mgp)
+        recs, summary = srv.run(reqs, realtime=True, keep_solutions=True)
+        srv.close()
+        out[name] = summary
+        sols[name] = {r["rid"]: (r["x"], r["kind"], r["dofs"]) for r in recs if "x" in r}
+    diffs = []
+    for rid, (x32, kind, n) in sols["fp32_mg"].items():
+        x64 = sols["fp64_mg"][rid][0]
+        diffs.append(float(np.linalg.norm(x32 - x64) / np.linalg.norm(x64)))
+    out["fp32_vs_fp64_max_rel_diff"] = max(diffs) if diffs else None
+    out["fp32_vs_fp64_throughput"] = out["fp32_mg"]["solves_per_s"] / max(out["fp64_mg"]["solves_per_s"], 1e-12)
+    ctx.close()
+    return out
 
 
 def run_reference(args, world, rank):
@@ -299,6 +391,14 @@ def run_ours(args, world, rank, local):
         "chebyshev3_fp32": {"ms_per_sweep": ms_cheb, "dofs_per_s": world * ndof / (ms_cheb * 1e-3)},
         "vcycle_fp32": {"ms": ms_vc, "levels": prob.info.n_levels},
     }
+    if not args.no_solves:
+        prob.close()
+        m.close()
+        ctx.close()
+        t0 = time.perf_counter()
+        line["solves"] = solve_section(api, L, inputs, torch)
+        line["serving"] = serving_section(api, L, torch, args.serve_requests)
+        line["solves_serving_wall_s"] = time.perf_counter() - t0
     if world == 1 and not args.no_cpu_baseline:
         cb = cpu_baseline()
         cb.pop("ms_per_step", None)

@@ -25,3 +25,20 @@ def match_dofs(xa, fa, xb, fb, digits=9):
         raise ValueError("duplicate support points")
     perm = np.array([where[k] for k in key(xb, fb)], dtype=np.int64)
     return perm
+
+
+def smooth_solution(xyz, field, dim, pressure_scale=1.0):
+    """Smooth manufactured discrete solution x* sampled at support points (xyz, field):
+    velocity component c = (1 + c/2) sin(pi x) sin(pi y) [sin(pi z)] + c x y / 4,
+    pressure = pressure_scale * cos(pi x) cos(2 pi y) [cos(pi z)]."""
+    x, y = xyz[:, 0], xyz[:, 1]
+    z = xyz[:, 2] if dim == 3 else np.zeros_like(x)
+    sz = np.sin(np.pi * z) if dim == 3 else 1.0
+    cz = np.cos(np.pi * z) if dim == 3 else 1.0
+    out = np.empty(len(field))
+    for c in range(dim):
+        sel = field == c
+        out[sel] = ((1 + 0.5 * c) * np.sin(np.pi * x) * np.sin(np.pi * y) * sz + 0.25 * c * x * y)[sel]
+    sel = field == dim
+    out[sel] = (pressure_scale * np.cos(np.pi * x) * np.cos(2 * np.pi * y) * cz)[sel]
+    return out

@@ -71,8 +71,7 @@ def _degree(req):
 
 def _manufactured(prob, req):
     """x* ~ U(-1,1) (seeded per request); for Stokes the pressure entries are scaled by nu,
-    the pressure scale of nu (grad u, grad v) - (p, div v), so that velocity and pressure
-    errors weigh alike."""
+    the pressure scale of nu (grad u, grad v) - (p, div v)."""
     xstar = torch.tensor(inputs.uniform_vector(prob.info.n_dofs, seed=req.seed), device="cuda")
     if req.kind == L.STOKES:
         xstar[prob.info.n_velocity_dofs:] *= req.nu
@@ -184,7 +183,10 @@ class Server:
                                     "iterations": st.iterations, "rel_residual": st.rel_residual,
                                     "converged": bool(st.converged), "error": self._error(a)})
                     if keep_solutions:
-                        records[-1]["x"] = a.x.cpu().numpy()
+                        xs = a.x.clone()
+                        ps = _pressure_slice(a.prob, a.req)
+                        xs[ps] -= xs[ps].mean()      # the pressure is fixed up to a constant
+                        records[-1]["x"] = xs.cpu().numpy()
                     a.prob.close()
                     budget_blocked = False
                 active = keep
@@ -212,7 +214,8 @@ class Server:
 
 
 def solve_alone(ctx, req, mg_precision=L.FP32, tol=1e-12, dt=1e-2):
-    """The same request solved on its own with mfns_solve (reference for the mixed results)."""
+    """The same request solved on its own with mfns_solve (reference for the mixed results);
+    returns (solution with the pressure mean removed, solve info)."""
     m = api.Mesh(ctx, 3, req.n)
     prob = api.Problem(ctx, m, kind=req.kind, degree=_degree(req), nu=req.nu,
                        dt=dt if req.kind == L.STAB_NS else 0.0, mg_precision=mg_precision, tol=tol, maxit=300)
@@ -221,5 +224,7 @@ def solve_alone(ctx, req, mg_precision=L.FP32, tol=1e-12, dt=1e-2):
     prob.vmult(xstar, b)
     x = torch.zeros_like(xstar)
     info = prob.solve(b, x, raise_on_nonconvergence=False)
+    ps = _pressure_slice(prob, req)
+    x[ps] -= x[ps].mean()          # the pressure is fixed up to a constant (as in the records)
     torch.cuda.synchronize()
     return x, info

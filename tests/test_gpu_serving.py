@@ -62,7 +62,7 @@ def test_serving_results_same_alone_and_in_the_mix(ctx):
     # admission overlapped: more than one request was active in some rounds
     assert summary["rounds"] < sum(r["iterations"] for r in records)
     for req in reqs:
-        x_alone, info = serve.solve_alone(ctx, req, tol=1e-12)
+        x_alone, info = serve.solve_alone(ctx, req, tol=1e-12)   # pressure mean removed, like the records
         x_mix = byid[req.rid]["x"]
         xa = x_alone.cpu().numpy()
         assert info.iterations == byid[req.rid]["iterations"]
