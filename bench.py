@@ -366,7 +366,7 @@ def run_ours(args, world, rank, local):
     except (OSError, ValueError):
         pass
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
-    alg_bytes = 12 * (ndof // 4) * 4                               # src 4 + dst 4 + frozen 4 fields, fp32
+    alg_bytes = 8 * (ndof // 4) * 4 + ncell * FQ_BYTES_PER_CELL_F32  # src + dst (4 fields, fp32) + frozen point data
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms32, "higher_is_better": True, "scaling": "weak",

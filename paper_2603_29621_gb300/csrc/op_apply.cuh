@@ -19,6 +19,11 @@ struct Team {
     constexpr int w = sizeof(T) / 4, m = 32 / w;
     return NBUF * BUF + (((TPC - NBUF * BUF) % m) + m) % m;
   }
+  // Staged frozen blocks live in a second shared-memory region: per-team stride in bytes, a
+  // multiple of 16 (cp.async alignment) that is 48 mod 128 so consecutive teams start 12 banks apart.
+  __host__ __device__ static constexpr size_t stage_stride_bytes(size_t block_bytes) {
+    return block_bytes + (size_t)((((48 - (int)(block_bytes % 128)) % 128) + 128) % 128);
+  }
 };
 
 // Minimum resident blocks per SM for the register allocator (occupancy vs spills), per
@@ -58,6 +63,11 @@ __device__ __forceinline__ int64_t structured_node(int n, const int cc[3], int a
 template <int DIM>
 struct FrozenPoint {
   static constexpr int NFQ = DIM + DIM * DIM + DIM + 1;  // u, grad u, Rbar, tau
+  // one cell's block: [point l][value k][lane], padded to a multiple of 4 values (16 bytes in FP32)
+  template <typename T>
+  __host__ __device__ static constexpr int block(int q) {
+    return (ipow(q, DIM - 1) * q * NFQ + 3) / 4 * 4;
+  }
 };
 
 template <int DIM, int K, int OP, typename T, bool STRUCT, bool DIAG, int FQ = 0>
@@ -70,7 +80,6 @@ op_kernel(const OpArgs<T, K + 1, K + 1, (OP == OP_STOKES ? K : K + 1)> args) {
   constexpr int NB = ipow(N, DIM);
   constexpr int NBP = ipow(NP, DIM);
   constexpr int BUF = TM::BUF;
-  constexpr int NBUF = 3;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* smem = reinterpret_cast<T*>(smem_raw);
 
@@ -82,9 +91,15 @@ op_kernel(const OpArgs<T, K + 1, K + 1, (OP == OP_STOKES ? K : K + 1)> args) {
   if (!lane_active) team = TM::CPW;  // dummy team for the spare lanes
   const int ti = tid % Q;
   const int tj = DIM == 3 ? tid / Q : 0;
+  constexpr int FQB = (Tr::FROZEN && FQ == 1) ? FrozenPoint<DIM>::template block<T>(Q) : 0;
   T* buf0 = smem + (size_t)(warp * (TM::CPW + 1) + team) * TM::template stride<T>();
   T* buf1 = buf0 + BUF;
   T* buf2 = buf1 + BUF;
+  // staged frozen block (FQ == 1): [point][value][lane], 16-byte aligned (second region)
+  const size_t region1 = ((sizeof(T) * (size_t)(blockDim.x >> 5) * (TM::CPW + 1) * TM::template stride<T>() + 15) / 16) * 16;
+  // the spare lanes read team 0's block (same words as its lanes: broadcast, no bank conflict)
+  T* fqs = reinterpret_cast<T*>(smem_raw + region1 + (size_t)(warp * TM::CPW + (lane_active ? team : 0)) *
+                                                         TM::stage_stride_bytes(sizeof(T) * FQB));
 
   // ---- which cell
   int64_t cell;
@@ -227,35 +242,16 @@ op_kernel(const OpArgs<T, K + 1, K + 1, (OP == OP_STOKES ? K : K + 1)> args) {
   T Ub[DIM][Q], Gb[DIM][DIM][Q], Rb[DIM][Q], tau[Q];
   constexpr int NFQ = FrozenPoint<DIM>::NFQ;
   if constexpr (Tr::FROZEN && FQ == 1) {
-    const T* fp = args.fq + ((size_t)cellpos * TM::TPC + tid) * Q * NFQ;
-#pragma unroll
-    for (int l = 0; l < Q; ++l) {
-      T v[NFQ];
-      if constexpr (NFQ % 4 == 0 && sizeof(T) == 4) {
-#pragma unroll
-        for (int q4 = 0; q4 < NFQ / 4; ++q4) {
-          const float4 w = lane_active ? __ldg(reinterpret_cast<const float4*>(fp + l * NFQ) + q4) : make_float4(0, 0, 0, 0);
-          v[4 * q4] = w.x; v[4 * q4 + 1] = w.y; v[4 * q4 + 2] = w.z; v[4 * q4 + 3] = w.w;
-        }
-      } else if constexpr (NFQ % 2 == 0 && sizeof(T) == 8) {
-#pragma unroll
-        for (int q2 = 0; q2 < NFQ / 2; ++q2) {
-          const double2 w = lane_active ? __ldg(reinterpret_cast<const double2*>(fp + l * NFQ) + q2) : make_double2(0, 0);
-          v[2 * q2] = w.x; v[2 * q2 + 1] = w.y;
-        }
-      } else {
-#pragma unroll
-        for (int q = 0; q < NFQ; ++q) v[q] = lane_active ? fp[l * NFQ + q] : T(0);
-      }
-#pragma unroll
-      for (int i = 0; i < DIM; ++i) {
-        Ub[i][l] = v[i];
-#pragma unroll
-        for (int j = 0; j < DIM; ++j) Gb[i][j][l] = v[DIM + i * DIM + j];
-        Rb[i][l] = v[DIM + DIM * DIM + i];
-      }
-      tau[l] = v[NFQ - 1];
+    // the team copies its cell's block (contiguous in global memory) with 16-byte cp.async;
+    // the copy overlaps the interpolation of the trial fields and is awaited before first use
+    constexpr int CH = FQB * (int)sizeof(T) / 16;  // 16-byte chunks per cell
+    const char* gsrc = reinterpret_cast<const char*>(args.fq + (size_t)cellpos * FQB);
+    if (lane_active) {
+      const unsigned sdst = (unsigned)__cvta_generic_to_shared(fqs);
+      for (int c = tid; c < CH; c += TM::TPC)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sdst + 16 * c), "l"(gsrc + 16 * c) : "memory");
     }
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
   }
   if constexpr (Tr::FROZEN && FQ != 1) {
     T fz[DIM + 1][N];
@@ -317,17 +313,19 @@ op_kernel(const OpArgs<T, K + 1, K + 1, (OP == OP_STOKES ? K : K + 1)> args) {
     }
     if constexpr (FQ == 2) {
       if (valid) {
-        T* fp = args.fq + ((size_t)cellpos * TM::TPC + tid) * Q * NFQ;
+        constexpr int B = FrozenPoint<DIM>::template block<T>(Q);
+        T* fp = args.fq + (size_t)cellpos * B + tid;
+        auto at = [&](int l, int k) -> T& { return fp[(l * NFQ + k) * TM::TPC]; };
 #pragma unroll
         for (int l = 0; l < Q; ++l) {
 #pragma unroll
           for (int i = 0; i < DIM; ++i) {
-            fp[l * NFQ + i] = Ub[i][l];
+            at(l, i) = Ub[i][l];
 #pragma unroll
-            for (int j = 0; j < DIM; ++j) fp[l * NFQ + DIM + i * DIM + j] = Gb[i][j][l];
-            fp[l * NFQ + DIM + DIM * DIM + i] = Rb[i][l];
+            for (int j = 0; j < DIM; ++j) at(l, DIM + i * DIM + j) = Gb[i][j][l];
+            at(l, DIM + DIM * DIM + i) = Rb[i][l];
           }
-          fp[l * NFQ + NFQ - 1] = tau[l];
+          at(l, NFQ - 1) = tau[l];
         }
       }
       return;  // set-up pass: nothing else to do (no __syncwarp follows)
@@ -430,6 +428,28 @@ op_kernel(const OpArgs<T, K + 1, K + 1, (OP == OP_STOKES ? K : K + 1)> args) {
         integrate<DIM, Q, NP, true, false, T>(c0, cg, rp, buf1, buf2, ti, tj, tab.Sp, tab.D);
       }
     } else {  // OP_STAB_NS
+      // frozen point values: registers (FQ 0) or the staged shared-memory block (FQ 1)
+      // each lane waits for its own copies; the warp barrier then publishes every lane's chunks
+      if constexpr (FQ == 1) {
+        asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+        __syncwarp();
+      }
+      auto UB = [&](int d, int l) -> T {
+        if constexpr (FQ == 1) return fqs[(l * NFQ + d) * TM::TPC + tid];
+        else return Ub[d][l];
+      };
+      auto GB = [&](int i, int j, int l) -> T {
+        if constexpr (FQ == 1) return fqs[(l * NFQ + DIM + i * DIM + j) * TM::TPC + tid];
+        else return Gb[i][j][l];
+      };
+      auto RB = [&](int i, int l) -> T {
+        if constexpr (FQ == 1) return fqs[(l * NFQ + DIM + DIM * DIM + i) * TM::TPC + tid];
+        else return Rb[i][l];
+      };
+      auto TAU = [&](int l) -> T {
+        if constexpr (FQ == 1) return fqs[(l * NFQ + NFQ - 1) * TM::TPC + tid];
+        else return tau[l];
+      };
       const T cfm = args.cf[0], cfc = args.cf[1], cfn = args.cf[2], cfs = args.cf[3], cfsn = args.cf[4],
               cfp = args.cf[5], cfl = args.cf[6];
       const T cm = args.cm;
@@ -456,7 +476,7 @@ op_kernel(const OpArgs<T, K + 1, K + 1, (OP == OP_STOKES ? K : K + 1)> args) {
 #pragma unroll
           for (int d = 0; d < DIM; ++d) {
             g[d][l] *= inv_h;
-            ugu += Ub[d][l] * g[d][l];
+            ugu += UB(d, l) * g[d][l];
             lap += h2[d][l];
           }
           lap *= inv_h * inv_h;
@@ -465,10 +485,10 @@ op_kernel(const OpArgs<T, K + 1, K + 1, (OP == OP_STOKES ? K : K + 1)> args) {
           Rl[j][l] += gal - cfl * nu * lap;
 #pragma unroll
           for (int i = 0; i < DIM; ++i) {
-            const T nt = cfn * val[l] * Gb[i][j][l];   // (du . grad ub)_i from component j
+            const T nt = cfn * val[l] * GB(i, j, l);   // (du . grad ub)_i from component j
             vc[i][l] += nt;
             Rl[i][l] += nt;
-            gc[i][j][l] += cfsn * tau[l] * Rb[i][l] * val[l];  // tau Rbar_i (du . grad v_i)
+            gc[i][j][l] += cfsn * TAU(l) * RB(i, l) * val[l];  // tau Rbar_i (du . grad v_i)
           }
 #pragma unroll
           for (int d = 0; d < DIM; ++d) gc[j][d][l] += nu * g[d][l];
@@ -494,10 +514,10 @@ op_kernel(const OpArgs<T, K + 1, K + 1, (OP == OP_STOKES ? K : K + 1)> args) {
         T c0[Q], cg[DIM][Q];
 #pragma unroll
         for (int l = 0; l < Q; ++l) {
-          const T st = cfs * tau[l] * Rl[i][l];
+          const T st = cfs * TAU(l) * Rl[i][l];
           c0[l] = vc[i][l] * jxw[l];
 #pragma unroll
-          for (int d = 0; d < DIM; ++d) cg[d][l] = (gc[i][d][l] + st * Ub[d][l]) * jxw[l] * inv_h;
+          for (int d = 0; d < DIM; ++d) cg[d][l] = (gc[i][d][l] + st * UB(d, l)) * jxw[l] * inv_h;
         }
         integrate<DIM, Q, N, true, true, T>(c0, cg, r[i], buf1, buf2, ti, tj, tab.S, tab.D);
       }
@@ -507,7 +527,7 @@ op_kernel(const OpArgs<T, K + 1, K + 1, (OP == OP_STOKES ? K : K + 1)> args) {
         for (int l = 0; l < Q; ++l) {
           c0[l] = args.div_sign * dv[l] * jxw[l];
 #pragma unroll
-          for (int d = 0; d < DIM; ++d) cg[d][l] = cfp * tau[l] * Rl[d][l] * jxw[l] * inv_h;
+          for (int d = 0; d < DIM; ++d) cg[d][l] = cfp * TAU(l) * Rl[d][l] * jxw[l] * inv_h;
         }
         integrate<DIM, Q, N, true, true, T>(c0, cg, r[DIM], buf1, buf2, ti, tj, tab.S, tab.D);
       }
@@ -576,9 +596,12 @@ op_kernel(const OpArgs<T, K + 1, K + 1, (OP == OP_STOKES ? K : K + 1)> args) {
 }
 
 template <int DIM, int K, int OP, typename T>
-constexpr size_t op_smem_bytes(int warps = kOpWarps) {
+constexpr size_t op_smem_bytes(int warps = kOpWarps, bool staged_frozen = false) {
   using TM = Team<DIM, K + 1>;
-  return sizeof(T) * (size_t)warps * (TM::CPW + 1) * TM::template stride<T>();
+  const size_t region1 = ((sizeof(T) * (size_t)warps * (TM::CPW + 1) * TM::template stride<T>() + 15) / 16) * 16;
+  if (!staged_frozen) return region1;
+  const size_t block = sizeof(T) * FrozenPoint<DIM>::template block<T>(K + 1);
+  return region1 + (size_t)warps * TM::CPW * TM::stage_stride_bytes(block);
 }
 
 }  // namespace mfns

@@ -84,10 +84,11 @@ KernelTimer::~KernelTimer() {
 }
 
 int64_t frozen_point_values_per_cell(int dim, int k) {
+  // one cell's block [point][value][lane], padded to 16 bytes in FP32 and FP64 alike
   const int q = k + 1;
   const int64_t lanes = dim == 3 ? q * q : q;
   const int nfq = dim + dim * dim + dim + 1;
-  return lanes * q * nfq;
+  return ((lanes * q * nfq + 3) / 4) * 4;
 }
 
 void op_precompute_frozen(const OpLaunch& L, int prec, cudaStream_t s) {

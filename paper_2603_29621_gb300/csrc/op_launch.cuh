@@ -1,6 +1,8 @@
 // Templated launcher of the operator kernel; included by the per-operator
 // instantiation units (op_<kind>_<dim>d.cu).
 #pragma once
+#include <atomic>
+
 #include "common.hpp"
 #include "op_apply.cuh"
 #include "op_launch.hpp"
@@ -57,7 +59,26 @@ void op_launch(const OpLaunch& L, const T* src, T* dst, bool diag, cudaStream_t 
   using TM = Team<DIM, Q>;
   const int warps = L.warps[prec] > 0 ? L.warps[prec] : kOpWarps;
   const int cells_per_block = warps * TM::CPW;
-  const size_t smem = op_smem_bytes<DIM, K, OP, T>(warps);
+  const size_t smem = op_smem_bytes<DIM, K, OP, T>(warps, false);
+  const size_t smem_fq = op_smem_bytes<DIM, K, OP, T>(warps, true);
+  if constexpr (OP == OP_STAB_NS) {
+    // the staged-frozen kernels may need more than the default 48 KB of dynamic shared memory;
+    // the attribute is per device and set once for the largest block size
+    static std::atomic<uint64_t> attr_done{0};
+    int dev = 0;
+    MFNS_CUDA(cudaGetDevice(&dev));
+    const uint64_t bit = 1ull << (dev & 63);
+    if (fq == 1 && !(attr_done.load() & bit)) {
+      const int mx = (int)op_smem_bytes<DIM, K, OP, T>(kOpWarps, true);
+      MFNS_CUDA(cudaFuncSetAttribute(op_kernel<DIM, K, OP, T, true, false, 1>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+      MFNS_CUDA(cudaFuncSetAttribute(op_kernel<DIM, K, OP, T, false, true, 1>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+      MFNS_CUDA(cudaFuncSetAttribute(op_kernel<DIM, K, OP, T, false, false, 1>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+      attr_done.fetch_or(bit);
+    }
+  }
   const bool structured = L.structured && !diag;
   int64_t color_offset = 0;
   for (int c = 0; c < L.n_colors; ++c) {
@@ -84,11 +105,11 @@ void op_launch(const OpLaunch& L, const T* src, T* dst, bool diag, cudaStream_t 
           op_kernel<DIM, K, OP, T, false, false, 2><<<grid, warps * 32, smem, s>>>(a);
       } else if (fq == 1) {
         if (structured)
-          op_kernel<DIM, K, OP, T, true, false, 1><<<grid, warps * 32, smem, s>>>(a);
+          op_kernel<DIM, K, OP, T, true, false, 1><<<grid, warps * 32, smem_fq, s>>>(a);
         else if (diag)
-          op_kernel<DIM, K, OP, T, false, true, 1><<<grid, warps * 32, smem, s>>>(a);
+          op_kernel<DIM, K, OP, T, false, true, 1><<<grid, warps * 32, smem_fq, s>>>(a);
         else
-          op_kernel<DIM, K, OP, T, false, false, 1><<<grid, warps * 32, smem, s>>>(a);
+          op_kernel<DIM, K, OP, T, false, false, 1><<<grid, warps * 32, smem_fq, s>>>(a);
       } else {
         if (structured)
           op_kernel<DIM, K, OP, T, true, false, 0><<<grid, warps * 32, smem, s>>>(a);
