@@ -19,10 +19,14 @@ struct Team {
     constexpr int w = sizeof(T) / 4, m = 32 / w;
     return NBUF * BUF + (((TPC - NBUF * BUF) % m) + m) % m;
   }
-  // Staged frozen blocks live in a second shared-memory region: per-team stride in bytes, a
-  // multiple of 16 (cp.async alignment) that is 48 mod 128 so consecutive teams start 12 banks apart.
+  // Staged frozen blocks live in a second shared-memory region.  Per-team stride in bytes: the
+  // block rounded up so that consecutive teams start TPC values (rounded up to 8 bytes) apart
+  // modulo the 128-byte bank window; the lanes of the CPW teams then read disjoint banks
+  // whenever CPW * TPC values fit in 32 banks.  The stride is a multiple of 8 bytes (cp.async).
+  template <typename T>
   __host__ __device__ static constexpr size_t stage_stride_bytes(size_t block_bytes) {
-    return block_bytes + (size_t)((((48 - (int)(block_bytes % 128)) % 128) + 128) % 128);
+    constexpr size_t shift = ((TPC * sizeof(T) + 7) / 8 * 8) % 128;
+    return block_bytes + (shift + 128 - block_bytes % 128) % 128;
   }
 };
 
@@ -95,11 +99,11 @@ op_kernel(const OpArgs<T, K + 1, K + 1, (OP == OP_STOKES ? K : K + 1)> args) {
   T* buf0 = smem + (size_t)(warp * (TM::CPW + 1) + team) * TM::template stride<T>();
   T* buf1 = buf0 + BUF;
   T* buf2 = buf1 + BUF;
-  // staged frozen block (FQ == 1): [point][value][lane], 16-byte aligned (second region)
+  // staged frozen block (FQ == 1): [point][value][lane], 8-byte aligned (second region)
   const size_t region1 = ((sizeof(T) * (size_t)(blockDim.x >> 5) * (TM::CPW + 1) * TM::template stride<T>() + 15) / 16) * 16;
   // the spare lanes read team 0's block (same words as its lanes: broadcast, no bank conflict)
   T* fqs = reinterpret_cast<T*>(smem_raw + region1 + (size_t)(warp * TM::CPW + (lane_active ? team : 0)) *
-                                                         TM::stage_stride_bytes(sizeof(T) * FQB));
+                                                         TM::template stage_stride_bytes<T>(sizeof(T) * FQB));
 
   // ---- which cell
   int64_t cell;
@@ -242,14 +246,20 @@ op_kernel(const OpArgs<T, K + 1, K + 1, (OP == OP_STOKES ? K : K + 1)> args) {
   T Ub[DIM][Q], Gb[DIM][DIM][Q], Rb[DIM][Q], tau[Q];
   constexpr int NFQ = FrozenPoint<DIM>::NFQ;
   if constexpr (Tr::FROZEN && FQ == 1) {
-    // the team copies its cell's block (contiguous in global memory) with 16-byte cp.async;
-    // the copy overlaps the interpolation of the trial fields and is awaited before first use
-    constexpr int CH = FQB * (int)sizeof(T) / 16;  // 16-byte chunks per cell
+    // the team copies its cell's block (contiguous in global memory) with cp.async, in 16-byte
+    // chunks where the team's staging slot is 16-byte aligned and 8-byte chunks otherwise; the
+    // copy overlaps the interpolation of the trial fields and is awaited before first use
+    constexpr int CB = TM::template stage_stride_bytes<T>(sizeof(T) * FQB) % 16 == 0 ? 16 : 8;
+    constexpr int CH = FQB * (int)sizeof(T) / CB;  // chunks per cell
     const char* gsrc = reinterpret_cast<const char*>(args.fq + (size_t)cellpos * FQB);
     if (lane_active) {
       const unsigned sdst = (unsigned)__cvta_generic_to_shared(fqs);
-      for (int c = tid; c < CH; c += TM::TPC)
-        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sdst + 16 * c), "l"(gsrc + 16 * c) : "memory");
+      for (int c = tid; c < CH; c += TM::TPC) {
+        if constexpr (CB == 16)
+          asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sdst + 16 * c), "l"(gsrc + 16 * c) : "memory");
+        else
+          asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sdst + 8 * c), "l"(gsrc + 8 * c) : "memory");
+      }
     }
     asm volatile("cp.async.commit_group;\n" ::: "memory");
   }
@@ -601,7 +611,7 @@ constexpr size_t op_smem_bytes(int warps = kOpWarps, bool staged_frozen = false)
   const size_t region1 = ((sizeof(T) * (size_t)warps * (TM::CPW + 1) * TM::template stride<T>() + 15) / 16) * 16;
   if (!staged_frozen) return region1;
   const size_t block = sizeof(T) * FrozenPoint<DIM>::template block<T>(K + 1);
-  return region1 + (size_t)warps * TM::CPW * TM::stage_stride_bytes(block);
+  return region1 + (size_t)warps * TM::CPW * TM::template stage_stride_bytes<T>(block);
 }
 
 }  // namespace mfns

@@ -17,13 +17,26 @@ def uniform_vector(n, seed=SEED_SRC, low=-1.0, high=1.0):
 
 
 def match_dofs(xa, fa, xb, fb, digits=9):
-    """Permutation perm with (xa[perm[i]], fa[perm[i]]) == (xb[i], fb[i]) (coordinates rounded)."""
-    key = lambda x, f: [tuple(np.round(r, digits)) + (int(g),) for r, g in zip(x, f)]
-    ka = key(xa, fa)
-    where = {k: i for i, k in enumerate(ka)}
-    if len(where) != len(ka):
+    """Permutation perm with (xa[perm[i]], fa[perm[i]]) == (xb[i], fb[i]) (coordinates rounded to
+    `digits` decimals); both sides are sorted by the integer key (coordinates, field) and paired."""
+    xa, xb = np.asarray(xa, dtype=float), np.asarray(xb, dtype=float)
+
+    def keys(x, f):
+        q = np.rint(np.round(x, digits) * 10.0 ** digits).astype(np.int64)
+        return np.column_stack([q, np.asarray(f, dtype=np.int64)])
+
+    ka, kb = keys(xa, fa), keys(xb, fb)
+    if ka.shape != kb.shape:
+        raise ValueError("the two DoF sets differ in size")
+    oa = np.lexsort(ka.T[::-1])
+    ob = np.lexsort(kb.T[::-1])
+    sa, sb = ka[oa], kb[ob]
+    if len(sa) > 1 and np.any(np.all(sa[1:] == sa[:-1], axis=1)):
         raise ValueError("duplicate support points")
-    perm = np.array([where[k] for k in key(xb, fb)], dtype=np.int64)
+    if not np.array_equal(sa, sb):
+        raise ValueError("the two DoF sets have different support points")
+    perm = np.empty(len(kb), dtype=np.int64)
+    perm[ob] = oa
     return perm
 
 
