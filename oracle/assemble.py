@@ -22,8 +22,10 @@ class Problem:
     (Taylor--Green by default)."""
 
     def __init__(self, forest, kind, k, nu=1.0, dt=np.inf, terms=forms.TERMS_ALL,
-                 div_sign=None, frozen=None):
+                 div_sign=None, frozen=None, alpha=1.5):
         self.forest, self.kind, self.k, self.nu, self.dt, self.terms = forest, kind, k, nu, dt, terms
+        self.alpha = alpha
+        self.g_nodes = None
         dim = forest.dim
         self.dim = dim
         if kind == "stokes":
@@ -60,11 +62,56 @@ class Problem:
             return forms.vector_laplacian(dim, k, self.nu, h)
         if self.kind == "pmass":
             return forms.scalar_mass(dim, k, k + 1, h)
+        ub, pb, gl = self._state_local(cells)
+        return forms.stabilized_ns(dim, k, h, ub, pb, self.nu, self.dt, self.terms, self.div_sign,
+                                   self.alpha, gl)
+
+    # -- state of the stabilised NS problem (Section 5: Newton linearisation, BDF2) ----
+    def _state_local(self, cells, nodes_u=None):
         ns = self.dofs.nodesets[0]
         cn = ns.cell_nodes[cells]                                # (nc, nb)
-        ub = np.transpose(self.ub_nodes[cn], (0, 2, 1))          # (nc, dim, nb)
+        ubn = self.ub_nodes if nodes_u is None else nodes_u
+        ub = np.transpose(ubn[cn], (0, 2, 1))                    # (nc, dim, nb)
         pb = self.pb_nodes[cn]
-        return forms.stabilized_ns(dim, k, h, ub, pb, self.nu, self.dt, self.terms, self.div_sign)
+        gl = None if self.g_nodes is None else np.transpose(self.g_nodes[cn], (0, 2, 1))
+        return ub, pb, gl
+
+    def _split(self, U):
+        n = self.dofs.nodesets[0].n_nodes
+        U = np.asarray(U, dtype=float)
+        return U[: self.dim * n].reshape(self.dim, n).T.copy(), U[self.dim * n: (self.dim + 1) * n].copy()
+
+    def state_vector(self):
+        """The current state (u, p) as a vector in this problem's DoF order."""
+        return np.concatenate([self.ub_nodes.T.ravel(), self.pb_nodes])
+
+    def set_state(self, U, g=None):
+        """State (u, p) from a DoF vector (constrained entries included as given); g: DoF vector
+        whose velocity entries hold the explicit field g of ``forms.stabilized_ns_residual``."""
+        self.ub_nodes, self.pb_nodes = self._split(U)
+        self.g_nodes = None if g is None else self._split(g)[0]
+
+    def set_dt(self, dt, alpha):
+        self.dt, self.alpha = dt, alpha
+
+    def residual(self, tau_state=None, chunk=512):
+        """Nonlinear residual F(state) on the free rows (test functions C v), zero on constrained
+        rows; tau_state: DoF vector whose velocity fixes tau (default: the state)."""
+        d = self.dofs
+        Fall = np.zeros(d.n_dofs)
+        tu = None if tau_state is None else self._split(tau_state)[0]
+        nc = self.forest.n_cells
+        hh = self.forest.h()
+        for s0 in range(0, nc, chunk):
+            cells = np.arange(s0, min(nc, s0 + chunk))
+            ub, pb, gl = self._state_local(cells)
+            tl = None if tu is None else self._state_local(cells, tu)[0]
+            Fe = forms.stabilized_ns_residual(self.dim, self.k, hh[cells], ub, pb, self.nu, self.dt, gl,
+                                              self.div_sign, self.alpha, tl)
+            np.add.at(Fall, self.cell_dofs[cells], Fe)
+        F = np.zeros(d.n_dofs)
+        F[d.free_ids] = d.C.T @ Fall
+        return F
 
     # -- global matrices --------------------------------------------------------
     def assemble_K(self, chunk=512):

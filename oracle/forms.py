@@ -114,10 +114,13 @@ def frozen_at_qp(t, ub_loc, pb_loc):
     return U, G, LU, GP
 
 
-def stabilized_ns(dim, k, h, ub_loc, pb_loc, nu, dt, terms=TERMS_ALL, div_sign=1.0, alpha=1.5):
+def stabilized_ns(dim, k, h, ub_loc, pb_loc, nu, dt, terms=TERMS_ALL, div_sign=1.0, alpha=1.5, g_loc=None):
     """(nc, n, n) Newton-linearised SUPG/PSPG BDF2 element matrices on Q_k^dim Q_k, n = (dim+1) nb.
 
-    Local order: velocity components 0..dim-1 then pressure, each over the nb nodes."""
+    Local order: velocity components 0..dim-1 then pressure, each over the nb nodes.
+    g_loc (nc, dim, nb): nodal explicit part of the time derivative and forcing (see
+    ``stabilized_ns_residual``); it enters Rbar as c_m ub + g.  Without it the frozen state's
+    history equals the state, so the time derivative in Rbar vanishes."""
     t = CellTables(dim, k, k + 1, h)
     h = np.asarray(h, dtype=float).reshape(-1)
     nb = t.nb
@@ -134,6 +137,8 @@ def stabilized_ns(dim, k, h, ub_loc, pb_loc, nu, dt, terms=TERMS_ALL, div_sign=1
     U, G, LU, GP = frozen_at_qp(t, ub_loc, pb_loc)
     tau = tau_formula(np.linalg.norm(U, axis=2), h[:, None], nu, dt)      # (nc, nq)
     Rbar = np.einsum("cqj,cqij->cqi", U, G) + GP - nu * LU                # (nc, nq, dim)
+    if g_loc is not None:
+        Rbar = Rbar + cm * U + np.einsum("qb,cib->cqi", t.phi, g_loc)
     W = t.JxW
     phi, g, lap = t.phi, t.grad, t.lap
     Ug = np.einsum("cqd,cqbd->cqb", U, g)                                 # ub . grad phi_b
@@ -166,6 +171,50 @@ def stabilized_ns(dim, k, h, ub_loc, pb_loc, nu, dt, terms=TERMS_ALL, div_sign=1
         K[:, P:, j * nb:(j + 1) * nb] = blk
     K[:, P:, P:] = ps * np.einsum("cq,cqad,cqbd->cab", W * tau, g, g)
     return K
+
+
+def stabilized_ns_residual(dim, k, h, u_loc, p_loc, nu, dt, g_loc=None, div_sign=1.0, alpha=1.5, tau_u_loc=None):
+    """(nc, (dim+1) nb) element residual vectors of the SUPG/PSPG BDF discretisation of the
+    incompressible Navier--Stokes equations (Section 5) at the discrete state (u, p).
+
+    The time derivative at t^{n+1} is (alpha u + sum_j beta_j u^{n-j}) / dt; its explicit part
+    and the forcing are passed as one nodal field g = sum_j beta_j u^{n-j} / dt - f_h, so that the
+    strong momentum residual is R = c_m u + g + u.grad u + grad p - nu lap u, c_m = alpha / dt
+    (g absent: R without the time derivative, as for the frozen state).  Residual, per test
+    function (v, q):
+      (c_m u + g + u.grad u, v) + nu (grad u, grad v) - (p, div v) + (tau R, u.grad v)
+      + s (div u, q) + (tau R, grad q),
+    with tau (Tezduyar) from |u| at the point, or from the field tau_u_loc when given (tau frozen
+    at another state: the Jacobian of this residual at that state is the linearised operator)."""
+    t = CellTables(dim, k, k + 1, h)
+    h = np.asarray(h, dtype=float).reshape(-1)
+    nb = t.nb
+    nc = t.JxW.shape[0]
+    cm = alpha / dt if np.isfinite(dt) else 0.0
+    U, G, LU, GP = frozen_at_qp(t, u_loc, p_loc)
+    P = np.einsum("qb,cb->cq", t.phi, p_loc)
+    if g_loc is None:
+        Tt = np.zeros_like(U)
+    else:
+        Tt = cm * U + np.einsum("qb,cib->cqi", t.phi, g_loc)
+    conv = np.einsum("cqj,cqij->cqi", U, G)
+    R = Tt + conv + GP - nu * LU
+    Ut = U if tau_u_loc is None else np.einsum("qb,cib->cqi", t.phi, tau_u_loc)
+    tau = tau_formula(np.linalg.norm(Ut, axis=2), h[:, None], nu, dt)
+    W = t.JxW
+    phi, g = t.phi, t.grad
+    Ug = np.einsum("cqd,cqbd->cqb", U, g)                                 # u . grad phi_a
+    F = np.zeros((nc, (dim + 1) * nb))
+    for i in range(dim):
+        Fi = np.einsum("cq,cq,qa->ca", W, Tt[:, :, i] + conv[:, :, i], phi)
+        Fi += nu * np.einsum("cq,cqd,cqad->ca", W, G[:, :, i, :], g)
+        Fi -= np.einsum("cq,cq,cqa->ca", W, P, g[..., i])
+        Fi += np.einsum("cq,cq,cqa->ca", W * tau, R[:, :, i], Ug)
+        F[:, i * nb:(i + 1) * nb] = Fi
+    div = np.einsum("cqii->cq", G)
+    F[:, dim * nb:] = (div_sign * np.einsum("cq,cq,qa->ca", W, div, phi)
+                       + np.einsum("cq,cqd,cqad->ca", W * tau, R, g))
+    return F
 
 
 def taylor_green(dim):

@@ -260,6 +260,19 @@ class DofHandler:
         self.n_dofs = off
         self._build_constraints()
 
+    def set_hanging(self, x):
+        """Copy of x with every hanging (non-Dirichlet) entry replaced by the weighted sum of its
+        masters' entries (free and boundary masters alike)."""
+        y = np.array(x, dtype=float, copy=True)
+        for f, (nc, k, dbc) in enumerate(self.fields):
+            ns = self.nodesets[f]
+            for c in range(nc):
+                base = self.offsets[f] + c * ns.n_nodes
+                for g, masters in ns.hanging.items():
+                    if not self.dirichlet[base + g]:
+                        y[base + g] = sum(w * y[base + m] for m, w in masters)
+        return y
+
     def dof(self, f, comp, node):
         return self.offsets[f] + comp * self.nodesets[f].n_nodes + node
 
