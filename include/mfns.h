@@ -136,6 +136,25 @@ typedef struct {
   int converged;
 } mfns_solve_info;
 
+/* Newton step of a BDF time step (Section 5), see mfns_bdf_step. */
+typedef struct {
+  double dt;           /* time step dt_n = t_{n+1} - t_n (> 0) */
+  double omega;        /* step ratio dt_n / dt_{n-1}; 0 = BDF1 (implicit Euler), e.g. for the first step */
+  double rtol;         /* stop when ||F(u_k)|| <= max(atol, rtol ||F(u_0)||); 0 = 1e-8 */
+  double atol;
+  double lin_tol;      /* relative tolerance of each FGMRES solve (inexact Newton); 0 = 1e-4 */
+  int max_newton;      /* 0 = 10 */
+  int extrapolate;     /* 1: start from (1 + omega) u^n - omega u^{n-1} on the free entries */
+} mfns_newton_desc;
+
+typedef struct {
+  int newton_iterations;        /* Newton updates performed */
+  int linear_iterations;        /* FGMRES iterations over all Newton updates */
+  double residual0, residual;   /* ||F|| (l2, FP64) at the initial guess and at the result */
+  double seconds;
+  int converged;
+} mfns_newton_info;
+
 /* ---- context --------------------------------------------------------------------------- */
 /* device: CUDA ordinal; hbm_budget_bytes: 0 = unlimited.  Errors: ARG, CUDA. */
 int mfns_ctx_create(int device, size_t hbm_budget_bytes, mfns_ctx** out);
@@ -217,6 +236,40 @@ int mfns_vcycle(mfns_problem* p, int precision, const void* b, void* x, void* st
  * The pressure l2 mean of b and of every preconditioned vector is removed when the
  * pressure is only fixed up to a constant.  Returns MFNS_ERR_NOT_CONVERGED when maxit is hit. */
 int mfns_solve(mfns_problem* p, const void* b, void* x, mfns_solve_info* info, void* stream);
+
+/* ---- nonlinear and time-dependent stabilised Navier--Stokes (Section 5) ---------------------- */
+/* STAB_NS on uniform meshes: set the time step dt, the BDF coefficient alpha of u^{n+1} (3/2 for
+ * BDF2 with equal steps, 1 for BDF1) and the state at which the operator is linearised.
+ * `state` is an FP64 device vector in the system layout (velocity with its Dirichlet values, and
+ * pressure).  `explicit_field` (FP64 device, system layout, velocity entries used; may be NULL)
+ * holds g = (beta_n u^n + beta_{n-1} u^{n-1}) / dt - f_h, the explicit part of the BDF time
+ * derivative and the nodal forcing: the strong momentum residual becomes
+ * R = (alpha/dt) u + g + u.grad u + grad p - nu lap u.  Without it the time derivative in R is
+ * zero (as for the default Taylor--Green state).  The state and g are interpolated to every
+ * multigrid level (coarse-node evaluation of the fine FE function); each level's stored point
+ * values, diagonal and the coarse inverse are recomputed.  The call synchronises `stream`.
+ * Returns MFNS_ERR_UNSUPPORTED for other kinds or a hierarchy with refined meshes. */
+int mfns_set_state(mfns_problem* p, double dt, double alpha, const void* state, const void* explicit_field,
+                   void* stream);
+/* dst = F(state), the nonlinear residual of the SUPG/PSPG BDF discretisation at the state of the
+ * last mfns_set_state, on the free rows; constrained rows are set to 0.  With tau frozen at the
+ * state, mfns_vmult applies its Jacobian.  dst: device vector in `precision`, system layout. */
+int mfns_residual(mfns_problem* p, int precision, void* dst, void* stream);
+/* One variable-step BDF step for u^{n+1} (Section 5): Newton's method on F(u) = 0 with
+ * g = (beta_n u^n + beta_{n-1} u^{n-1}) / dt - forcing, each update solving J(u_k) d = -F(u_k) by
+ * FGMRES with the multigrid preconditioner at the current state (mg_precision of the problem).
+ * alpha = (1 + 2 w)/(1 + w), beta_n = -(1 + w), beta_{n-1} = w^2/(1 + w) for w = desc.omega > 0;
+ * w = 0: alpha = 1, beta_n = -1 (BDF1, u_nm1 unused).  u_n, u_nm1, forcing (may be NULL) and u
+ * are FP64 device vectors in the system layout; u holds the initial guess with the Dirichlet
+ * values at t_{n+1} on entry (the increments vanish on constrained entries) and the result on
+ * return.  The pressure is fixed up to a constant when the velocity is Dirichlet everywhere.
+ * Synchronises `stream`; returns MFNS_ERR_NOT_CONVERGED (result written) after max_newton
+ * updates.  Buffers for g, F and the increment are allocated on the first call. */
+int mfns_bdf_step(mfns_problem* p, const mfns_newton_desc* desc, const void* u_n, const void* u_nm1,
+                  const void* forcing, void* u, mfns_newton_info* info, void* stream);
+/* *umax (host) = max over velocity nodes of |u| for an FP64 device vector u in the system layout
+ * (time-step control by a CFL number: dt = CFL h / umax).  Synchronises `stream`. */
+int mfns_max_velocity(mfns_problem* p, const void* u, double* umax, void* stream);
 
 /* ---- batched solves (continuous batching of many problems) ---------------------------------- */
 /* Start a solve as in mfns_solve (same FGMRES, same preconditioner), without iterating: the

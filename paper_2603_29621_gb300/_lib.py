@@ -46,6 +46,16 @@ class SolveInfo(C.Structure):
                 ("converged", C.c_int)]
 
 
+class NewtonDesc(C.Structure):
+    _fields_ = [("dt", C.c_double), ("omega", C.c_double), ("rtol", C.c_double), ("atol", C.c_double),
+                ("lin_tol", C.c_double), ("max_newton", C.c_int), ("extrapolate", C.c_int)]
+
+
+class NewtonInfo(C.Structure):
+    _fields_ = [("newton_iterations", C.c_int), ("linear_iterations", C.c_int), ("residual0", C.c_double),
+                ("residual", C.c_double), ("seconds", C.c_double), ("converged", C.c_int)]
+
+
 _SIGS = {
     "mfns_ctx_create": (C.c_int, [C.c_int, C.c_size_t, C.POINTER(C.c_void_p)]),
     "mfns_ctx_destroy": (C.c_int, [C.c_void_p]),
@@ -71,6 +81,11 @@ _SIGS = {
     "mfns_restrict": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
     "mfns_vcycle": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
     "mfns_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(SolveInfo), C.c_void_p]),
+    "mfns_set_state": (C.c_int, [C.c_void_p, C.c_double, C.c_double, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "mfns_residual": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
+    "mfns_bdf_step": (C.c_int, [C.c_void_p, C.POINTER(NewtonDesc), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                C.POINTER(NewtonInfo), C.c_void_p]),
+    "mfns_max_velocity": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_double), C.c_void_p]),
     "mfns_solve_begin": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "mfns_batch_step": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.POINTER(C.c_int)]),
     "mfns_solve_status": (C.c_int, [C.c_void_p, C.POINTER(SolveInfo)]),

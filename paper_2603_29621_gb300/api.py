@@ -20,6 +20,12 @@ def _ptr(t):
     return C.c_void_p(t.data_ptr())
 
 
+def _f64(*ts):
+    for t in ts:
+        if t is not None and t.dtype != torch.float64:
+            raise ValueError("state, explicit field, forcing and solution vectors must be float64")
+
+
 def _stream(stream):
     s = torch.cuda.current_stream() if stream is None else stream
     return C.c_void_p(s.cuda_stream)
@@ -184,6 +190,38 @@ class Problem:
         if code != L.OK and (code != L.ERR_NOT_CONVERGED or raise_on_nonconvergence):
             L.check(code)
         return si
+
+    # -- nonlinear / time-dependent stabilised NS (Section 5) --------------------------------
+    def set_state(self, dt, alpha, state, explicit_field=None, stream=None):
+        """Linearisation state (FP64 system vector), dt, BDF coefficient alpha and the explicit field g."""
+        _f64(state, explicit_field)
+        g = None if explicit_field is None else _ptr(explicit_field)
+        L.check(self.lib.mfns_set_state(self.h, float(dt), float(alpha), _ptr(state), g, _stream(stream)))
+
+    def residual(self, dst, stream=None):
+        prec = L.FP64 if dst.dtype == torch.float64 else L.FP32
+        L.check(self.lib.mfns_residual(self.h, prec, _ptr(dst), _stream(stream)))
+        return dst
+
+    def bdf_step(self, u, u_n, u_nm1=None, forcing=None, dt=0.0, omega=1.0, rtol=1e-8, atol=0.0, lin_tol=1e-4,
+                 max_newton=10, extrapolate=False, stream=None, raise_on_nonconvergence=True):
+        """One BDF step (omega = dt_n / dt_{n-1}, 0: BDF1) by Newton-FGMRES; u: guess in, solution out."""
+        _f64(u, u_n, u_nm1, forcing)
+        desc = L.NewtonDesc(dt=float(dt), omega=float(omega), rtol=float(rtol), atol=float(atol),
+                            lin_tol=float(lin_tol), max_newton=int(max_newton), extrapolate=int(bool(extrapolate)))
+        info = L.NewtonInfo()
+        opt = lambda t: None if t is None else _ptr(t)
+        code = self.lib.mfns_bdf_step(self.h, C.byref(desc), _ptr(u_n), opt(u_nm1), opt(forcing), _ptr(u),
+                                      C.byref(info), _stream(stream))
+        if code != L.OK and (code != L.ERR_NOT_CONVERGED or raise_on_nonconvergence):
+            L.check(code)
+        return info
+
+    def max_velocity(self, u, stream=None):
+        _f64(u)
+        out = C.c_double()
+        L.check(self.lib.mfns_max_velocity(self.h, _ptr(u), C.byref(out), _stream(stream)))
+        return out.value
 
     def solve_begin(self, b, x, stream=None):
         L.check(self.lib.mfns_solve_begin(self.h, _ptr(b), _ptr(x), _stream(stream)))

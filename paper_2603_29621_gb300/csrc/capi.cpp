@@ -313,6 +313,61 @@ int mfns_solve(mfns_problem* p, const void* b, void* x, mfns_solve_info* info, v
   API_END
 }
 
+int mfns_set_state(mfns_problem* p, double dt, double alpha, const void* state, const void* explicit_field,
+                   void* stream) {
+  API_BEGIN
+  if (!p || !state) return fail(MFNS_ERR_ARG, "bad arguments");
+  MFNS_CUDA(cudaSetDevice(p->ctx->device));
+  set_state(*p->p, dt, alpha, (const double*)state, (const double*)explicit_field, S(stream));
+  API_END
+}
+
+int mfns_residual(mfns_problem* p, int precision, void* dst, void* stream) {
+  API_BEGIN
+  if (!p || !dst || (precision != MFNS_FP64 && precision != MFNS_FP32)) return fail(MFNS_ERR_ARG, "bad arguments");
+  MFNS_CUDA(cudaSetDevice(p->ctx->device));
+  residual(*p->p, precision, dst, S(stream));
+  API_END
+}
+
+int mfns_bdf_step(mfns_problem* p, const mfns_newton_desc* desc, const void* u_n, const void* u_nm1,
+                  const void* forcing, void* u, mfns_newton_info* info, void* stream) {
+  API_BEGIN
+  if (!p || !desc || !u_n || !u) return fail(MFNS_ERR_ARG, "bad arguments");
+  MFNS_CUDA(cudaSetDevice(p->ctx->device));
+  NewtonParams np;
+  np.dt = desc->dt;
+  np.omega = desc->omega;
+  np.rtol = desc->rtol > 0 ? desc->rtol : 1e-8;
+  np.atol = desc->atol > 0 ? desc->atol : 0.0;
+  np.lin_tol = desc->lin_tol > 0 ? desc->lin_tol : 1e-4;
+  np.max_newton = desc->max_newton > 0 ? desc->max_newton : 10;
+  np.extrapolate = desc->extrapolate != 0;
+  auto t0 = std::chrono::steady_clock::now();
+  NewtonResult r = bdf_step(*p->p, np, (const double*)u_n, (const double*)u_nm1, (const double*)forcing,
+                            (double*)u, S(stream));
+  MFNS_CUDA(cudaStreamSynchronize(S(stream)));
+  auto t1 = std::chrono::steady_clock::now();
+  if (info) {
+    info->newton_iterations = r.newton_iterations;
+    info->linear_iterations = r.linear_iterations;
+    info->residual0 = r.residual0;
+    info->residual = r.residual;
+    info->seconds = std::chrono::duration<double>(t1 - t0).count();
+    info->converged = r.converged ? 1 : 0;
+  }
+  if (!r.converged) return fail(MFNS_ERR_NOT_CONVERGED, "Newton reached max_newton");
+  API_END
+}
+
+int mfns_max_velocity(mfns_problem* p, const void* u, double* umax, void* stream) {
+  API_BEGIN
+  if (!p || !u || !umax) return fail(MFNS_ERR_ARG, "bad arguments");
+  MFNS_CUDA(cudaSetDevice(p->ctx->device));
+  *umax = max_velocity(*p->p, (const double*)u, S(stream));
+  API_END
+}
+
 int mfns_solve_begin(mfns_problem* p, const void* b, void* x, void* stream) {
   API_BEGIN
   if (!p || !b || !x) return fail(MFNS_ERR_ARG, "bad arguments");

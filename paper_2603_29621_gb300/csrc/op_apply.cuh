@@ -63,7 +63,8 @@ __device__ __forceinline__ int64_t structured_node(int n, const int cc[3], int a
 }
 
 // FQ: 0 = frozen state interpolated in the kernel, 1 = read the precomputed point values,
-// 2 = compute the point values, write them to args.fq and stop (set-up pass).
+// 2 = compute the point values, write them to args.fq and stop (set-up pass),
+// 3 = nonlinear residual at the frozen state (Section 5; src unused).
 template <int DIM>
 struct FrozenPoint {
   static constexpr int NFQ = DIM + DIM * DIM + DIM + 1;  // u, grad u, Rbar, tau
@@ -207,7 +208,7 @@ op_kernel(const OpArgs<T, K + 1, K + 1, (OP == OP_STOKES ? K : K + 1)> args) {
   T u0[NU][N];
   T pv0[NP];
   T d0[NU][N];
-  if (!DIAG) {
+  if (!DIAG && FQ != 2) {  // the set-up pass reads neither src nor dst
 #pragma unroll
     for (int c = 0; c < N; ++c) {
       if constexpr (NU == 4) {
@@ -242,8 +243,10 @@ op_kernel(const OpArgs<T, K + 1, K + 1, (OP == OP_STOKES ? K : K + 1)> args) {
     }
   }
 
-  // frozen state (stabilised NS) at the lane's Gauss points
+  // frozen state (stabilised NS) at the lane's Gauss points; pressure value, pressure gradient and
+  // velocity Laplacian are kept for the residual pass
   T Ub[DIM][Q], Gb[DIM][DIM][Q], Rb[DIM][Q], tau[Q];
+  T gp[DIM][Q], lb[DIM][Q], pb[Q];
   constexpr int NFQ = FrozenPoint<DIM>::NFQ;
   if constexpr (Tr::FROZEN && FQ == 1) {
     // the team copies its cell's block (contiguous in global memory) with cp.async, in 16-byte
@@ -281,7 +284,6 @@ op_kernel(const OpArgs<T, K + 1, K + 1, (OP == OP_STOKES ? K : K + 1)> args) {
         for (int f = 0; f <= DIM; ++f) fz[f][c] = own ? args.frozen[fnode[c] * NU + f] : T(0);
       }
     }
-    T gp[DIM][Q], lb[DIM][Q];
 #pragma unroll
     for (int f = 0; f <= DIM; ++f) {
       T val[Q], g[DIM][Q], h2[DIM][Q];
@@ -302,9 +304,29 @@ op_kernel(const OpArgs<T, K + 1, K + 1, (OP == OP_STOKES ? K : K + 1)> args) {
       } else {
         derivatives<DIM, Q, false, T>(val, g, h2, buf1, ti, tj, tab.D, tab.D2);
 #pragma unroll
-        for (int l = 0; l < Q; ++l)
+        for (int l = 0; l < Q; ++l) {
+          pb[l] = val[l];
 #pragma unroll
           for (int d = 0; d < DIM; ++d) gp[d][l] = g[d][l] * inv_h;
+        }
+      }
+    }
+    // time derivative in the strong residual: c_m u + g with the explicit field g (BDF history
+    // and forcing); without g the state's history equals the state and the term vanishes
+    T tq[DIM][Q];
+#pragma unroll
+    for (int i = 0; i < DIM; ++i)
+#pragma unroll
+      for (int l = 0; l < Q; ++l) tq[i][l] = 0;
+    if (args.gexp) {  // kernel parameter: uniform over the warp
+#pragma unroll
+      for (int i = 0; i < DIM; ++i) {
+        T gz[N], gv[Q];
+#pragma unroll
+        for (int c = 0; c < N; ++c) gz[c] = own ? args.gexp[fnode[c] * NU + i] : T(0);
+        values<DIM, Q, N, T>(gz, gv, buf0, ti, tj, tab.S);
+#pragma unroll
+        for (int l = 0; l < Q; ++l) tq[i][l] = args.cm * Ub[i][l] + gv[l];
       }
     }
 #pragma unroll
@@ -312,7 +334,7 @@ op_kernel(const OpArgs<T, K + 1, K + 1, (OP == OP_STOKES ? K : K + 1)> args) {
       T un2 = 0;
 #pragma unroll
       for (int i = 0; i < DIM; ++i) {
-        T s = gp[i][l] - nu * lb[i][l];
+        T s = tq[i][l] + gp[i][l] - nu * lb[i][l];
 #pragma unroll
         for (int j = 0; j < DIM; ++j) s += Ub[j][l] * Gb[i][j][l];
         Rb[i][l] = s;
@@ -436,6 +458,35 @@ op_kernel(const OpArgs<T, K + 1, K + 1, (OP == OP_STOKES ? K : K + 1)> args) {
 #pragma unroll
         for (int l = 0; l < Q; ++l) c0[l] = args.div_sign * div[l] * jxw[l];
         integrate<DIM, Q, NP, true, false, T>(c0, cg, rp, buf1, buf2, ti, tj, tab.Sp, tab.D);
+      }
+    } else if constexpr (FQ == 3) {  // OP_STAB_NS, nonlinear residual at the frozen state
+      // (c_m u + g + u.grad u, v) + nu (grad u, grad v) - (p, div v) + (tau R, u.grad v)
+      // + s (div u, q) + (tau R, grad q), with R the strong residual computed above
+#pragma unroll
+      for (int i = 0; i < DIM; ++i) {
+        T c0[Q], cg[DIM][Q];
+#pragma unroll
+        for (int l = 0; l < Q; ++l) {
+          c0[l] = (Rb[i][l] - gp[i][l] + nu * lb[i][l]) * jxw[l];  // c_m u + g + u.grad u
+          const T st = tau[l] * Rb[i][l];
+#pragma unroll
+          for (int d = 0; d < DIM; ++d)
+            cg[d][l] = (nu * Gb[i][d][l] - (d == i ? pb[l] : T(0)) + st * Ub[d][l]) * jxw[l] * inv_h;
+        }
+        integrate<DIM, Q, N, true, true, T>(c0, cg, r[i], buf1, buf2, ti, tj, tab.S, tab.D);
+      }
+      {
+        T c0[Q], cg[DIM][Q];
+#pragma unroll
+        for (int l = 0; l < Q; ++l) {
+          T dv = 0;
+#pragma unroll
+          for (int j = 0; j < DIM; ++j) dv += Gb[j][j][l];
+          c0[l] = args.div_sign * dv * jxw[l];
+#pragma unroll
+          for (int d = 0; d < DIM; ++d) cg[d][l] = tau[l] * Rb[d][l] * jxw[l] * inv_h;
+        }
+        integrate<DIM, Q, N, true, true, T>(c0, cg, r[DIM], buf1, buf2, ti, tj, tab.S, tab.D);
       }
     } else {  // OP_STAB_NS
       // frozen point values: registers (FQ 0) or the staged shared-memory block (FQ 1)

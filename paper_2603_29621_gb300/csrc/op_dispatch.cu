@@ -99,6 +99,14 @@ void op_precompute_frozen(const OpLaunch& L, int prec, cudaStream_t s) {
     dispatch<float>(L, nullptr, nullptr, false, s, 2);
 }
 
+void op_residual(const OpLaunch& L, int prec, void* dst, cudaStream_t s) {
+  if (L.op != OP_STAB_NS) throw Error(kErrArg, "residual: not a stabilised NS operator");
+  if (prec == 0)
+    dispatch<double>(L, nullptr, static_cast<double*>(dst), false, s, 3);
+  else
+    dispatch<float>(L, nullptr, static_cast<float*>(dst), false, s, 3);
+}
+
 int autotune_warps(OpLaunch& L, int prec, void* src, void* dst, int64_t n, cudaStream_t s) {
   static std::mutex mu;
   static std::map<std::tuple<int, int, int, int, bool>, int> cache;

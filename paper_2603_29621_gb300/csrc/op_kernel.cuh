@@ -52,6 +52,7 @@ struct OpArgs {
   const T* src;
   T* dst;
   const T* frozen;             // stabilised NS: frozen state, same layout as src
+  const T* gexp;               // stabilised NS: explicit BDF history + forcing g (velocity slots), or null
   const int32_t* cell_u;       // indexed: master node per slot, bit 31 = boundary node
   const int32_t* cell_p;       // indexed Taylor--Hood: pressure master per slot
   const int32_t* cell_f;       // indexed stabilised NS: true node per slot (frozen gather)
@@ -62,7 +63,7 @@ struct OpArgs {
   int32_t color;               // structured: parity bits of this colour
   int64_t p_offset;            // Taylor--Hood: first pressure entry
   T h;                         // structured: edge length
-  T nu, cm, dt_inv, div_sign;  // physics (cm = 3/(2 dt))
+  T nu, cm, dt_inv, div_sign;  // physics (cm = alpha / dt, alpha = 3/2 for BDF2 with equal steps)
   T cf[7];                     // term factors: mass conv newton supg supgN pspg strongvisc
   // diagonal mode: compute (C e_m)^T A_cell (C e_m) for every local slot m
   int diag;

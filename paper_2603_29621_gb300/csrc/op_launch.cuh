@@ -49,13 +49,17 @@ void op_launch(const OpLaunch& L, const T* src, T* dst, bool diag, cudaStream_t 
   a.nu = (T)L.nu;
   const double dt_inv = L.dt > 0 ? 1.0 / L.dt : 0.0;
   a.dt_inv = (T)dt_inv;
-  a.cm = (T)(1.5 * dt_inv);
+  a.cm = (T)(L.alpha * dt_inv);
   a.div_sign = (T)L.div_sign;
   for (int b = 0; b < 7; ++b) a.cf[b] = (L.terms >> b) & 1 ? T(1) : T(0);
   a.diag = diag;
   // frozen state: -1 = use the precomputed point data when present; 2 = write it (set-up pass)
   a.fq = reinterpret_cast<T*>(L.fq[prec]);
-  const int fq = OP != OP_STAB_NS ? 0 : fq_mode == 2 ? 2 : (a.fq ? 1 : 0);
+  a.gexp = reinterpret_cast<const T*>(L.gexp[prec]);
+  // 3 = residual pass: the state is read from the frozen buffer (src unused, pointed there)
+  const int fq = OP != OP_STAB_NS ? 0 : (fq_mode == 2 || fq_mode == 3) ? fq_mode : (a.fq ? 1 : 0);
+  if (fq == 3 && diag) throw Error(kErrArg, "residual pass in diagonal mode");
+  if (fq == 2 || fq == 3) a.src = a.frozen;
   using TM = Team<DIM, Q>;
   const int warps = L.warps[prec] > 0 ? L.warps[prec] : kOpWarps;
   const int cells_per_block = warps * TM::CPW;
@@ -103,6 +107,11 @@ void op_launch(const OpLaunch& L, const T* src, T* dst, bool diag, cudaStream_t 
           op_kernel<DIM, K, OP, T, true, false, 2><<<grid, warps * 32, smem, s>>>(a);
         else
           op_kernel<DIM, K, OP, T, false, false, 2><<<grid, warps * 32, smem, s>>>(a);
+      } else if (fq == 3) {
+        if (L.structured)
+          op_kernel<DIM, K, OP, T, true, false, 3><<<grid, warps * 32, smem, s>>>(a);
+        else
+          op_kernel<DIM, K, OP, T, false, false, 3><<<grid, warps * 32, smem, s>>>(a);
       } else if (fq == 1) {
         if (structured)
           op_kernel<DIM, K, OP, T, true, false, 1><<<grid, warps * 32, smem_fq, s>>>(a);

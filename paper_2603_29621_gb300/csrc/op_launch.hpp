@@ -35,6 +35,8 @@ struct OpLaunch {
   const void* frozen[2] = {nullptr, nullptr};    // fp64 / fp32 frozen state
   int64_t p_offset = 0;
   double nu = 1.0, dt = 0.0, div_sign = -1.0;    // dt <= 0: stationary
+  double alpha = 1.5;                            // BDF coefficient of u^{n+1}: c_m = alpha / dt
+  const void* gexp[2] = {nullptr, nullptr};      // stabilised NS: explicit field g (fp64 / fp32) or none
   int terms = 127;
   // 1D tables in double (converted to the kernel precision at launch)
   int Q = 3, N = 3, NP = 3;
@@ -53,6 +55,10 @@ int autotune_warps(OpLaunch& L, int prec, void* src, void* dst, int64_t n, cudaS
 int64_t frozen_point_values_per_cell(int dim, int k);
 // Fill L.fq[prec] (device buffer of n_cells * frozen_point_values_per_cell) from the frozen state.
 void op_precompute_frozen(const OpLaunch& L, int prec, cudaStream_t s);
+
+// Stabilised NS: dst = F(frozen state), the nonlinear residual on the free rows (dst zeroed by the
+// caller; constrained rows untouched).
+void op_residual(const OpLaunch& L, int prec, void* dst, cudaStream_t s);
 
 // Fill the 1D tables of `L` for its degree (needs L.dim, L.k, L.op).
 void fill_tables(OpLaunch& L);

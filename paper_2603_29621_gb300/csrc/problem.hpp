@@ -29,6 +29,7 @@ struct OpLevel {
   OpLaunch L;
   std::vector<int32_t> perm;            // colour-sorted position -> forest cell id
   DevBuf cell_u, cell_p, cell_f, mask, hcell[2], frozen[2], fq[2];
+  DevBuf gexp[2];                       // stabilised NS: explicit BDF field g (allocated on first use)
   std::vector<int32_t> constrained_host;
   DevBuf constrained;                   // identity rows
   int64_t n_hang = 0;
@@ -57,6 +58,7 @@ struct SepTransfer {
   int64_t Mf = 0, Mc = 0;               // 1D node counts
   DevBuf p_ptr, p_idx, p_w[2];          // rows = fine nodes
   DevBuf r_ptr, r_idx, r_w[2];          // rows = coarse nodes
+  DevBuf i_ptr, i_idx, i_w;             // fine-to-coarse interpolation, rows = coarse nodes (fp64)
   DevBuf tmp1[2], tmp2[2];              // intermediate grids per precision
 };
 
@@ -76,6 +78,8 @@ struct Transfer {
 void build_transfer(Transfer& t, const OpLevel& fine, const OpLevel& coarse, Budget* bud);
 bool build_separable(SepTransfer& t, const OpLevel& fine, const OpLevel& coarse, Budget* bud);
 void sep_restrict(const SepTransfer& t, int prec, const void* fine, void* coarse, cudaStream_t s);
+// coarse = the fine FE function evaluated at the coarse nodes (all components, no masking; fp64)
+void sep_interpolate(const SepTransfer& t, const double* fine, double* coarse, cudaStream_t s);
 void sep_prolongate_add(const SepTransfer& t, int prec, const void* coarse, void* fine, cudaStream_t s);
 void transfer_prolongate_add(const Transfer& t, const OpLevel& fine, const OpLevel& coarse, int prec,
                              const void* xc, void* xf, cudaStream_t s);
@@ -127,6 +131,10 @@ struct Problem {
   DevBuf pc_in, pc_out, vc_in[2], vc_out[2];
   Krylov kry;
   double* hh_host = nullptr;            // pinned: Gram--Schmidt coefficients of the last step
+  // Newton / BDF (stabilised NS; allocated on first use): explicit field, residual, increment
+  DevBuf nt_g, nt_F, nt_d;
+  double st_dt = -1.0, st_alpha = -1.0;  // dt, alpha and explicit-field use of the last set_state
+  bool st_g = false;
   size_t bytes = 0;
   ~Problem();
 };
@@ -146,6 +154,28 @@ void estimate_lambda(Problem& p, cudaStream_t s);
 // choose the cell kernel's block size for every operator of the problem (cached per process)
 void autotune(Problem& p, cudaStream_t s);
 void setup_coarse(Problem& p, cudaStream_t s);
+// Stabilised NS (Section 5): set dt, the BDF coefficient alpha, the frozen state U and the explicit
+// field g (null: none) on the finest level, carry them down the hierarchy by interpolation and
+// refresh every level's point data, diagonal and the coarse inverse.  Uniform meshes only.
+void set_state(Problem& p, double dt, double alpha, const double* U, const double* g, cudaStream_t s);
+// dst = F(state): the nonlinear residual on the free rows, zero on constrained rows
+void residual(Problem& p, int prec, void* dst, cudaStream_t s);
+struct NewtonParams {
+  double dt = 0.0, omega = 1.0, rtol = 1e-8, atol = 0.0, lin_tol = 1e-4;
+  int max_newton = 10;
+  bool extrapolate = false;
+};
+struct NewtonResult {
+  int newton_iterations = 0, linear_iterations = 0;
+  double residual0 = 0.0, residual = 0.0;
+  bool converged = false;
+};
+// One variable-step BDF step (omega = dt_n / dt_{n-1}; 0: BDF1) solved by Newton-FGMRES.
+// u: in = initial guess with the Dirichlet values at t_{n+1}, out = solution.
+NewtonResult bdf_step(Problem& p, const NewtonParams& np, const double* u_n, const double* u_nm1,
+                      const double* forcing, double* u, cudaStream_t s);
+// max over velocity nodes of |u| (host value)
+double max_velocity(Problem& p, const double* u, cudaStream_t s);
 void alloc_workspaces(Problem& p);
 // Solve (FP64 FGMRES); returns iterations, writes relres; throws on CUDA errors
 int fgmres_solve(Problem& p, const double* b, double* x, double* relres, bool* converged, cudaStream_t s);

@@ -167,8 +167,9 @@ void alloc_workspaces(Problem& p) {
 
 static void level_dinv(Problem& p, OpLevel& lv, cudaStream_t s) {
   const int64_t n = lv.n_dofs;
-  lv.dinv[0].alloc(p.bud, n * 8);
-  lv.dinv[1].alloc(p.bud, n * 4);
+  // kept across refreshes (captured graphs hold these pointers)
+  if (lv.dinv[0].bytes() != (size_t)n * 8) lv.dinv[0].alloc(p.bud, n * 8);
+  if (lv.dinv[1].bytes() != (size_t)n * 4) lv.dinv[1].alloc(p.bud, n * 4);
   // the diagonal in the multigrid precision (fp32 mode never evaluates fp64 cell kernels here)
   if (p.mg_precision == 1) {
     oplevel_diag(lv, 1, lv.dinv[1].get(), s);
@@ -343,9 +344,15 @@ void setup_coarse(Problem& p, cudaStream_t s) {
       for (int32_t j : cl.pres_host) A[(int64_t)i * n + j] += v;
   }
   if (!invert_dense(A, n)) throw Error(kErrArg, "singular coarse matrix");
-  p.coarse_inv[0] = upload(p.bud, A);
   std::vector<float> Af(A.begin(), A.end());
-  p.coarse_inv[1] = upload(p.bud, Af);
+  if (p.coarse_inv[0].bytes() == (size_t)n * n * 8) {  // refresh in place (graphs hold the pointers)
+    MFNS_CUDA(cudaMemcpyAsync(p.coarse_inv[0].get(), A.data(), n * n * 8, cudaMemcpyHostToDevice, s));
+    MFNS_CUDA(cudaMemcpyAsync(p.coarse_inv[1].get(), Af.data(), n * n * 4, cudaMemcpyHostToDevice, s));
+    MFNS_CUDA(cudaStreamSynchronize(s));
+  } else {
+    p.coarse_inv[0] = upload(p.bud, A);
+    p.coarse_inv[1] = upload(p.bud, Af);
+  }
 }
 
 // ---------------------------------------------------------------------- smoothing
@@ -705,6 +712,132 @@ int fgmres_solve(Problem& p, const double* b_in, double* x, double* relres, bool
   *relres = p.kry.relres;
   *converged = p.kry.converged;
   return p.kry.it;
+}
+
+// ---------------------------------------------------------------------- Newton / BDF (Section 5)
+void set_state(Problem& p, double dt, double alpha, const double* U, const double* g, cudaStream_t s) {
+  if (p.kind != 2) throw Error(kErrUnsupported, "set_state: stabilised NS problems only");
+  for (auto& t : p.transfers)
+    if (!t->separable) throw Error(kErrUnsupported, "set_state: the hierarchy must consist of uniform meshes");
+  if (!(dt > 0.0) || !(alpha > 0.0)) throw Error(kErrArg, "set_state: dt and alpha must be positive");
+  const bool has_g = g != nullptr;
+  for (auto& lvp : p.levels) {
+    OpLevel& lv = *lvp;
+    lv.L.dt = dt;
+    lv.L.alpha = alpha;
+    if (has_g && !lv.gexp[0].get()) {
+      lv.gexp[0].alloc(p.bud, lv.n_main_dofs * 8);
+      lv.gexp[1].alloc(p.bud, lv.n_main_dofs * 4);
+    }
+    lv.L.gexp[0] = has_g ? lv.gexp[0].get() : nullptr;
+    lv.L.gexp[1] = has_g ? lv.gexp[1].get() : nullptr;
+  }
+  // the state (and g) on the finest level, then interpolated level by level down the hierarchy
+  OpLevel& f0 = *p.levels[0];
+  MFNS_CUDA(cudaMemcpyAsync(f0.frozen[0].get(), U, f0.n_main_dofs * 8, cudaMemcpyDeviceToDevice, s));
+  if (has_g) MFNS_CUDA(cudaMemcpyAsync(f0.gexp[0].get(), g, f0.n_main_dofs * 8, cudaMemcpyDeviceToDevice, s));
+  for (size_t l = 0; l + 1 < p.levels.size(); ++l) {
+    const SepTransfer& t = p.transfers[l]->sep;
+    sep_interpolate(t, p.levels[l]->frozen[0].as<double>(), p.levels[l + 1]->frozen[0].as<double>(), s);
+    if (has_g) sep_interpolate(t, p.levels[l]->gexp[0].as<double>(), p.levels[l + 1]->gexp[0].as<double>(), s);
+  }
+  for (auto& lvp : p.levels) {
+    OpLevel& lv = *lvp;
+    vcast_d2f(lv.frozen[1].as<float>(), lv.frozen[0].as<double>(), lv.n_main_dofs, s);
+    if (has_g) vcast_d2f(lv.gexp[1].as<float>(), lv.gexp[0].as<double>(), lv.n_main_dofs, s);
+    for (int prec = 0; prec < 2; ++prec) op_precompute_frozen(lv.L, prec, s);
+  }
+  for (auto& lvp : p.levels) level_dinv(p, *lvp, s);
+  setup_coarse(p, s);  // synchronises
+  // captured graphs hold dt, alpha and the explicit-field pointer as launch parameters
+  if (dt != p.st_dt || alpha != p.st_alpha || has_g != p.st_g) invalidate_graphs(p);
+  p.st_dt = dt;
+  p.st_alpha = alpha;
+  p.st_g = has_g;
+  p.phys.dt = dt;
+}
+
+void residual(Problem& p, int prec, void* dst, cudaStream_t s) {
+  if (p.kind != 2) throw Error(kErrUnsupported, "residual: stabilised NS problems only");
+  OpLevel& lv = *p.levels[0];
+  MFNS_CUDA(cudaMemsetAsync(dst, 0, lv.n_dofs * esize(prec), s));
+  op_residual(lv.L, prec, dst, s);
+  const int64_t nc = (int64_t)lv.constrained_host.size();
+  if (prec == 0)
+    vset_idx<double>((double*)dst, 0.0, lv.constrained.as<int32_t>(), nc, s);
+  else
+    vset_idx<float>((float*)dst, 0.0f, lv.constrained.as<int32_t>(), nc, s);
+}
+
+double max_velocity(Problem& p, const double* u, cudaStream_t s) {
+  OpLevel& lv = *p.levels[0];
+  if (p.kind != 2) throw Error(kErrUnsupported, "max_velocity: stabilised NS problems only");
+  unsigned long long* d = reinterpret_cast<unsigned long long*>(p.scal.as<double>() + 14);
+  max_node_norm2(d, u, lv.nu.n_nodes, lv.NU, lv.dim, s);
+  unsigned long long bits = 0;
+  MFNS_CUDA(cudaMemcpyAsync(&bits, d, 8, cudaMemcpyDeviceToHost, s));
+  MFNS_CUDA(cudaStreamSynchronize(s));
+  double m2;
+  std::memcpy(&m2, &bits, 8);
+  return std::sqrt(m2);
+}
+
+NewtonResult bdf_step(Problem& p, const NewtonParams& np, const double* u_n, const double* u_nm1,
+                      const double* forcing, double* u, cudaStream_t s) {
+  if (p.kind != 2) throw Error(kErrUnsupported, "bdf_step: stabilised NS problems only");
+  if (!(np.dt > 0.0) || np.omega < 0.0) throw Error(kErrArg, "bdf_step: dt > 0 and omega >= 0 required");
+  if (np.omega > 0.0 && !u_nm1) throw Error(kErrArg, "bdf_step: BDF2 needs u^{n-1}");
+  OpLevel& lv = *p.levels[0];
+  const int64_t n = lv.n_dofs;
+  if (p.nt_g.bytes() != (size_t)n * 8) {
+    p.nt_g.alloc(p.bud, n * 8);
+    p.nt_F.alloc(p.bud, n * 8);
+    p.nt_d.alloc(p.bud, n * 8);
+  }
+  double* g = p.nt_g.as<double>();
+  double* F = p.nt_F.as<double>();
+  double* d = p.nt_d.as<double>();
+  // variable-step BDF2: alpha u^{n+1} + beta_n u^n + beta_nm1 u^{n-1}, omega = dt_n / dt_{n-1}
+  const double w = np.omega;
+  const double alpha = w == 0.0 ? 1.0 : (1.0 + 2.0 * w) / (1.0 + w);
+  const double bn = w == 0.0 ? -1.0 : -(1.0 + w);
+  const double bnm1 = w == 0.0 ? 0.0 : w * w / (1.0 + w);
+  vlincomb3(g, bn / np.dt, u_n, bnm1 / np.dt, w == 0.0 ? nullptr : u_nm1, -1.0, forcing, n, s);
+  const int64_t ncon = (int64_t)lv.constrained_host.size();
+  if (np.extrapolate) {  // free entries from (1 + w) u^n - w u^{n-1}; constrained entries kept from u
+    vlincomb3(d, 1.0 + w, u_n, -w, w == 0.0 ? nullptr : u_nm1, 0.0, nullptr, n, s);
+    vcopy_idx<double>(d, u, lv.constrained.as<int32_t>(), ncon, s);
+    MFNS_CUDA(cudaMemcpyAsync(u, d, n * 8, cudaMemcpyDeviceToDevice, s));
+  }
+  NewtonResult res;
+  const double tol_saved = p.tol;
+  for (int it = 0;; ++it) {
+    set_state(p, np.dt, alpha, u, g, s);
+    residual(p, 0, F, s);
+    const double r = std::sqrt(host_dot(p, F, F, n, s));
+    if (it == 0) res.residual0 = r;
+    res.residual = r;
+    res.newton_iterations = it;
+    if (r <= std::max(np.atol, np.rtol * res.residual0)) {
+      res.converged = true;
+      break;
+    }
+    if (it == np.max_newton || !std::isfinite(r)) break;
+    // J(u) d = -F by FGMRES with the multigrid preconditioner at the current state
+    vscale<double>(F, -1.0, n, s);
+    p.tol = np.lin_tol;
+    double rel = 0.0;
+    bool conv = false;
+    try {
+      res.linear_iterations += fgmres_solve(p, F, d, &rel, &conv, s);
+    } catch (...) {
+      p.tol = tol_saved;
+      throw;
+    }
+    p.tol = tol_saved;
+    vaxpy<double>(u, 1.0, d, n, s);
+  }
+  return res;
 }
 
 }  // namespace mfns

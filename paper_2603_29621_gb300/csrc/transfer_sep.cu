@@ -150,6 +150,21 @@ bool build_separable(SepTransfer& t, const OpLevel& fine, const OpLevel& coarse,
   t.r_idx = upload(bud, idx);
   t.r_w[0] = upload(bud, w);
   t.r_w[1] = upload(bud, std::vector<float>(w.begin(), w.end()));
+  // dense 1D interpolation I1 (Mc x Mf): fine basis at every coarse node (used to carry a fine
+  // FE function, e.g. a Newton state, down the hierarchy)
+  std::vector<double> I1(t.Mc * t.Mf, 0.0);
+  for (int64_t g = 0; g < t.Mc; ++g) {
+    int64_t cc = g / kc, s = g % kc;
+    if (cc == nc) { cc = nc - 1; s = kc; }
+    const double X = (double(cc) + xc[s]) * double(nf) / double(nc);  // position in fine cells
+    const int64_t cf = std::min<int64_t>((int64_t)std::floor(X), nf - 1);
+    const double xi = X - double(cf);
+    for (int m = 0; m <= kf; ++m) I1[g * t.Mf + (int64_t)kf * cf + m] = lagrange(xf, m, xi);
+  }
+  to_csr(I1, t.Mc, t.Mf, ptr, idx, w);
+  t.i_ptr = upload(bud, ptr);
+  t.i_idx = upload(bud, idx);
+  t.i_w = upload(bud, w);
   // intermediate grids: after the first pass and after the second (3D)
   const int64_t a = t.dim == 3 ? t.Mc * t.Mf * t.Mf : t.Mc * t.Mf;
   const int64_t b = t.dim == 3 ? t.Mc * t.Mc * t.Mf : 0;
@@ -206,6 +221,33 @@ static void sep_dispatch(const SepTransfer& t, int prec, const T* in, T* out, bo
 #undef C
   }
   throw Error(kErrUnsupported, "separable transfer: unsupported component count");
+}
+
+template <int NC>
+static void sep_interpolate_t(const SepTransfer& t, const double* fine, double* coarse, cudaStream_t s) {
+  const int64_t Mf = t.Mf, Mc = t.Mc;
+  double* t1 = t.tmp1[0].as<double>();
+  double* t2 = t.tmp2[0].as<double>();
+  if (t.dim == 3) {
+    const int64_t e0[3] = {Mf, Mf, Mf}, e1[3] = {Mc, Mf, Mf}, e2[3] = {Mc, Mc, Mf};
+    pass<double, NC>(fine, t1, 0, e0, Mc, t.i_ptr, t.i_idx, t.i_w, 0, false, false, false, s);
+    pass<double, NC>(t1, t2, 1, e1, Mc, t.i_ptr, t.i_idx, t.i_w, 0, false, false, false, s);
+    pass<double, NC>(t2, coarse, 2, e2, Mc, t.i_ptr, t.i_idx, t.i_w, 0, false, false, false, s);
+  } else {
+    const int64_t e0[3] = {Mf, Mf, 1}, e1[3] = {Mc, Mf, 1};
+    pass<double, NC>(fine, t1, 0, e0, Mc, t.i_ptr, t.i_idx, t.i_w, 0, false, false, false, s);
+    pass<double, NC>(t1, coarse, 1, e1, Mc, t.i_ptr, t.i_idx, t.i_w, 0, false, false, false, s);
+  }
+}
+
+void sep_interpolate(const SepTransfer& t, const double* fine, double* coarse, cudaStream_t s) {
+  switch (t.ncomp) {
+    case 1: return sep_interpolate_t<1>(t, fine, coarse, s);
+    case 2: return sep_interpolate_t<2>(t, fine, coarse, s);
+    case 3: return sep_interpolate_t<3>(t, fine, coarse, s);
+    case 4: return sep_interpolate_t<4>(t, fine, coarse, s);
+  }
+  throw Error(kErrUnsupported, "separable interpolation: unsupported component count");
 }
 
 void sep_restrict(const SepTransfer& t, int prec, const void* fine, void* coarse, cudaStream_t s) {

@@ -22,6 +22,30 @@ template <typename T> __global__ void k_axpby(T* y, T a, const T* x, T b, int64_
 template <typename T> __global__ void k_sub(T* r, const T* b, const T* ax, int64_t n) { GRID_STRIDE(i, n) r[i] = b[i] - ax[i]; }
 template <typename T> __global__ void k_scale(T* y, T a, int64_t n) { GRID_STRIDE(i, n) y[i] *= a; }
 __global__ void k_d2f(float* y, const double* x, int64_t n) { GRID_STRIDE(i, n) y[i] = (float)x[i]; }
+__global__ void k_lincomb3(double* y, double a, const double* x1, double b, const double* x2, double c,
+                           const double* x3, int64_t n) {
+  GRID_STRIDE(i, n) {
+    double v = a * x1[i];
+    if (x2) v += b * x2[i];
+    if (x3) v += c * x3[i];
+    y[i] = v;
+  }
+}
+// max over nodes of the squared Euclidean norm of the first `dim` entries of each node's record;
+// the maximum is order independent, and non-negative doubles order like their bit patterns
+__global__ void k_max_node_norm2(unsigned long long* out, const double* x, int64_t nodes, int stride, int dim) {
+  double m = 0.0;
+  GRID_STRIDE(i, nodes) {
+    double s = 0.0;
+    for (int d = 0; d < dim; ++d) {
+      const double v = x[i * stride + d];
+      s += v * v;
+    }
+    m = fmax(m, s);
+  }
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_down_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(out, (unsigned long long)__double_as_longlong(m));
+}
 __global__ void k_f2d(double* y, const float* x, int64_t n) { GRID_STRIDE(i, n) y[i] = (double)x[i]; }
 template <typename T> __global__ void k_copy_idx(T* y, const T* x, const int32_t* idx, int64_t n) {
   GRID_STRIDE(i, n) y[idx[i]] = x[idx[i]];
@@ -162,6 +186,14 @@ template <typename T> void vaxpby(T* y, T a, const T* x, T b, int64_t n, cudaStr
 template <typename T> void vsub(T* r, const T* b, const T* ax, int64_t n, cudaStream_t s) { LAUNCH(k_sub<T>, n, s, r, b, ax, n); }
 template <typename T> void vscale(T* y, T a, int64_t n, cudaStream_t s) { LAUNCH(k_scale<T>, n, s, y, a, n); }
 void vcast_d2f(float* y, const double* x, int64_t n, cudaStream_t s) { LAUNCH(k_d2f, n, s, y, x, n); }
+void vlincomb3(double* y, double a, const double* x1, double b, const double* x2, double c, const double* x3,
+               int64_t n, cudaStream_t s) {
+  LAUNCH(k_lincomb3, n, s, y, a, x1, b, x2, c, x3, n);
+}
+void max_node_norm2(unsigned long long* out, const double* x, int64_t nodes, int stride, int dim, cudaStream_t s) {
+  MFNS_CUDA(cudaMemsetAsync(out, 0, sizeof(unsigned long long), s));
+  LAUNCH(k_max_node_norm2, nodes, s, out, x, nodes, stride, dim);
+}
 void vcast_f2d(double* y, const float* x, int64_t n, cudaStream_t s) { LAUNCH(k_f2d, n, s, y, x, n); }
 template <typename T> void vcopy_idx(T* y, const T* x, const int32_t* idx, int64_t n, cudaStream_t s) {
   LAUNCH(k_copy_idx<T>, n, s, y, x, idx, n);
