@@ -234,6 +234,55 @@ def serving_section(api, L, torch, count):
     return out
 
 
+def transient_section(api, L, inputs, torch, n=48, steps=4, cfl=0.5, nu=1e-2):
+    """Time stepping of the stabilised NS problem on n^3 Q2Q2 cells (Section 5): Taylor--Green
+    initial state (its boundary values kept as Dirichlet data), one BDF1 step, then variable-step
+    BDF2 with dt = cfl h / max|u|; every step solved by Newton-FGMRES with the multigrid at the
+    current state (inexact Newton: FGMRES to 1e-4, Newton to a 1e-8 residual reduction)."""
+    ctx = api.Context(torch.cuda.current_device())
+    out = {"cells": n ** 3, "steps": steps, "cfl": cfl, "nu": nu}
+    finals = {}
+    for name, mgp in (("fp64_mg", L.FP64), ("fp32_mg", L.FP32)):
+        m = api.Mesh(ctx, 3, n)
+        t0 = time.perf_counter()
+        p = api.Problem(ctx, m, kind=L.STAB_NS, degree=2, nu=nu, dt=1e-2, mg_precision=mgp, maxit=200)
+        setup = time.perf_counter() - t0
+        xyz, fld = p.support_points()
+        u_n = torch.tensor(inputs.taylor_green_state(xyz, fld, 3), device="cuda")
+        u_nm1 = None
+        h = 1.0 / n
+        dt_old = None
+        recs = []
+        torch.cuda.synchronize()
+        t_all = time.perf_counter()
+        for s in range(steps):
+            dt = cfl * h / p.max_velocity(u_n)
+            om = 0.0 if dt_old is None else dt / dt_old
+            u = u_n.clone()
+            info = p.bdf_step(u, u_n, u_nm1, dt=dt, omega=om, rtol=1e-8, lin_tol=1e-4, max_newton=8,
+                              extrapolate=u_nm1 is not None, raise_on_nonconvergence=False)
+            recs.append({"dt": dt, "omega": om, "newton": info.newton_iterations, "fgmres": info.linear_iterations,
+                         "residual_reduction": info.residual / max(info.residual0, 1e-300),
+                         "converged": bool(info.converged), "seconds": info.seconds})
+            u_nm1, u_n, dt_old = u_n, u, dt
+        torch.cuda.synchronize()
+        total = time.perf_counter() - t_all
+        later = recs[1:] if len(recs) > 1 else recs
+        out[name] = {"dofs": p.info.n_dofs, "levels": p.info.n_levels, "setup_s": setup, "total_s": total,
+                     "s_per_step_after_first": sum(r["seconds"] for r in later) / len(later),
+                     "dof_steps_per_s": p.info.n_dofs * steps / total, "steps": recs}
+        xf = u_n.clone()
+        xf[3::4] -= xf[3::4].mean()
+        finals[name] = xf
+        p.close()
+        m.close()
+    out["fp32_mg_speedup"] = out["fp64_mg"]["total_s"] / max(out["fp32_mg"]["total_s"], 1e-12)
+    out["fp32_vs_fp64_final_state_rel_diff"] = float(torch.linalg.norm(finals["fp32_mg"] - finals["fp64_mg"])
+                                                     / torch.linalg.norm(finals["fp64_mg"]))
+    ctx.close()
+    return out
+
+
 def run_reference(args, world, rank):
     if rank != 0:
         return
@@ -397,6 +446,7 @@ def run_ours(args, world, rank, local):
         ctx.close()
         t0 = time.perf_counter()
         line["solves"] = solve_section(api, L, inputs, torch)
+        line["transient"] = transient_section(api, L, inputs, torch)
         line["serving"] = serving_section(api, L, torch, args.serve_requests)
         line["solves_serving_wall_s"] = time.perf_counter() - t0
     if world == 1 and not args.no_cpu_baseline:

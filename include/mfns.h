@@ -247,7 +247,9 @@ int mfns_solve(mfns_problem* p, const void* b, void* x, mfns_solve_info* info, v
  * R = (alpha/dt) u + g + u.grad u + grad p - nu lap u.  Without it the time derivative in R is
  * zero (as for the default Taylor--Green state).  The state and g are interpolated to every
  * multigrid level (coarse-node evaluation of the fine FE function); each level's stored point
- * values, diagonal and the coarse inverse are recomputed.  The call synchronises `stream`.
+ * values, smoother diagonal (evaluated in FP32 whatever the multigrid precision: it only scales
+ * the smoother's correction) and the coarse inverse are recomputed.  The call synchronises
+ * `stream`.
  * Returns MFNS_ERR_UNSUPPORTED for other kinds or a hierarchy with refined meshes. */
 int mfns_set_state(mfns_problem* p, double dt, double alpha, const void* state, const void* explicit_field,
                    void* stream);

@@ -114,6 +114,7 @@ struct Problem {
   bool coarse_dense = true;
   int64_t coarse_n = 0;
   DevBuf coarse_inv[2];
+  DevBuf coarse_cols;                   // set-up scratch: operator columns of the coarse level
   int coarse_cheby_degree = 30;
   // workspaces [precision][level]
   std::vector<Workspace> ws[2];
@@ -158,6 +159,10 @@ void setup_coarse(Problem& p, cudaStream_t s);
 // field g (null: none) on the finest level, carry them down the hierarchy by interpolation and
 // refresh every level's point data, diagonal and the coarse inverse.  Uniform meshes only.
 void set_state(Problem& p, double dt, double alpha, const double* U, const double* g, cudaStream_t s);
+// the two halves of set_state: the finest level only (enough for the residual and the Jacobian),
+// and the rest of the hierarchy with the diagonals and the coarse inverse
+void set_state_fine(Problem& p, double dt, double alpha, const double* U, const double* g, cudaStream_t s);
+void refresh_preconditioner(Problem& p, cudaStream_t s);
 // dst = F(state): the nonlinear residual on the free rows, zero on constrained rows
 void residual(Problem& p, int prec, void* dst, cudaStream_t s);
 struct NewtonParams {

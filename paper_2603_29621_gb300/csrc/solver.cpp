@@ -165,13 +165,15 @@ void alloc_workspaces(Problem& p) {
   }
 }
 
-static void level_dinv(Problem& p, OpLevel& lv, cudaStream_t s) {
+// fp32: evaluate the diagonal in FP32 whatever the multigrid precision (Newton refreshes: the
+// diagonal only scales the smoother's correction, and FP64 cell kernels run at 1/60 the rate)
+static void level_dinv(Problem& p, OpLevel& lv, cudaStream_t s, bool fp32 = false) {
   const int64_t n = lv.n_dofs;
   // kept across refreshes (captured graphs hold these pointers)
   if (lv.dinv[0].bytes() != (size_t)n * 8) lv.dinv[0].alloc(p.bud, n * 8);
   if (lv.dinv[1].bytes() != (size_t)n * 4) lv.dinv[1].alloc(p.bud, n * 4);
   // the diagonal in the multigrid precision (fp32 mode never evaluates fp64 cell kernels here)
-  if (p.mg_precision == 1) {
+  if (p.mg_precision == 1 || fp32) {
     oplevel_diag(lv, 1, lv.dinv[1].get(), s);
     vrecip<float>(lv.dinv[1].as<float>(), lv.dinv[1].as<float>(), n, s);
     vcast_f2d(lv.dinv[0].as<double>(), lv.dinv[1].as<float>(), n, s);
@@ -324,18 +326,21 @@ void setup_coarse(Problem& p, cudaStream_t s) {
   p.coarse_n = n;
   p.coarse_dense = n <= 4096;
   if (!p.coarse_dense) return;
-  // assemble the coarse matrix column by column with the fp64 operator
-  std::vector<double> A(n * n), col(n);
+  // assemble the coarse matrix with the fp64 operator, kCols unit-vector products per round trip
+  constexpr int64_t kCols = 64;
+  std::vector<double> A(n * n), cols(n * kCols);
   Workspace& w = p.ws[0].back();
-  std::vector<double> e(n, 0.0);
-  for (int64_t j = 0; j < n; ++j) {
-    e[j] = 1.0;
-    MFNS_CUDA(cudaMemcpyAsync(w.x.get(), e.data(), n * 8, cudaMemcpyHostToDevice, s));
-    oplevel_vmult(cl, 0, w.x.get(), w.t.get(), s);
-    MFNS_CUDA(cudaMemcpyAsync(col.data(), w.t.get(), n * 8, cudaMemcpyDeviceToHost, s));
+  if (p.coarse_cols.bytes() != (size_t)(n * kCols * 8)) p.coarse_cols.alloc(p.bud, n * kCols * 8);
+  for (int64_t j0 = 0; j0 < n; j0 += kCols) {
+    const int64_t nb = std::min<int64_t>(kCols, n - j0);
+    for (int64_t j = 0; j < nb; ++j) {
+      vunit(w.x.as<double>(), n, j0 + j, s);
+      oplevel_vmult(cl, 0, w.x.get(), p.coarse_cols.as<double>() + j * n, s);
+    }
+    MFNS_CUDA(cudaMemcpyAsync(cols.data(), p.coarse_cols.get(), nb * n * 8, cudaMemcpyDeviceToHost, s));
     MFNS_CUDA(cudaStreamSynchronize(s));
-    e[j] = 0.0;
-    for (int64_t i = 0; i < n; ++i) A[i * n + j] = col[i];
+    for (int64_t j = 0; j < nb; ++j)
+      for (int64_t i = 0; i < n; ++i) A[i * n + j0 + j] = cols[j * n + i];
   }
   // constant-pressure null space: add e e^T over the free pressure entries
   if (cl.n_pres > 0 && (cl.op == OP_STAB_NS || cl.op == OP_STOKES)) {
@@ -715,7 +720,7 @@ int fgmres_solve(Problem& p, const double* b_in, double* x, double* relres, bool
 }
 
 // ---------------------------------------------------------------------- Newton / BDF (Section 5)
-void set_state(Problem& p, double dt, double alpha, const double* U, const double* g, cudaStream_t s) {
+void set_state_fine(Problem& p, double dt, double alpha, const double* U, const double* g, cudaStream_t s) {
   if (p.kind != 2) throw Error(kErrUnsupported, "set_state: stabilised NS problems only");
   for (auto& t : p.transfers)
     if (!t->separable) throw Error(kErrUnsupported, "set_state: the hierarchy must consist of uniform meshes");
@@ -732,29 +737,43 @@ void set_state(Problem& p, double dt, double alpha, const double* U, const doubl
     lv.L.gexp[0] = has_g ? lv.gexp[0].get() : nullptr;
     lv.L.gexp[1] = has_g ? lv.gexp[1].get() : nullptr;
   }
-  // the state (and g) on the finest level, then interpolated level by level down the hierarchy
-  OpLevel& f0 = *p.levels[0];
-  MFNS_CUDA(cudaMemcpyAsync(f0.frozen[0].get(), U, f0.n_main_dofs * 8, cudaMemcpyDeviceToDevice, s));
-  if (has_g) MFNS_CUDA(cudaMemcpyAsync(f0.gexp[0].get(), g, f0.n_main_dofs * 8, cudaMemcpyDeviceToDevice, s));
-  for (size_t l = 0; l + 1 < p.levels.size(); ++l) {
-    const SepTransfer& t = p.transfers[l]->sep;
-    sep_interpolate(t, p.levels[l]->frozen[0].as<double>(), p.levels[l + 1]->frozen[0].as<double>(), s);
-    if (has_g) sep_interpolate(t, p.levels[l]->gexp[0].as<double>(), p.levels[l + 1]->gexp[0].as<double>(), s);
-  }
-  for (auto& lvp : p.levels) {
-    OpLevel& lv = *lvp;
-    vcast_d2f(lv.frozen[1].as<float>(), lv.frozen[0].as<double>(), lv.n_main_dofs, s);
-    if (has_g) vcast_d2f(lv.gexp[1].as<float>(), lv.gexp[0].as<double>(), lv.n_main_dofs, s);
-    for (int prec = 0; prec < 2; ++prec) op_precompute_frozen(lv.L, prec, s);
-  }
-  for (auto& lvp : p.levels) level_dinv(p, *lvp, s);
-  setup_coarse(p, s);  // synchronises
   // captured graphs hold dt, alpha and the explicit-field pointer as launch parameters
   if (dt != p.st_dt || alpha != p.st_alpha || has_g != p.st_g) invalidate_graphs(p);
   p.st_dt = dt;
   p.st_alpha = alpha;
   p.st_g = has_g;
   p.phys.dt = dt;
+  OpLevel& f0 = *p.levels[0];
+  MFNS_CUDA(cudaMemcpyAsync(f0.frozen[0].get(), U, f0.n_main_dofs * 8, cudaMemcpyDeviceToDevice, s));
+  vcast_d2f(f0.frozen[1].as<float>(), f0.frozen[0].as<double>(), f0.n_main_dofs, s);
+  if (has_g) {
+    MFNS_CUDA(cudaMemcpyAsync(f0.gexp[0].get(), g, f0.n_main_dofs * 8, cudaMemcpyDeviceToDevice, s));
+    vcast_d2f(f0.gexp[1].as<float>(), f0.gexp[0].as<double>(), f0.n_main_dofs, s);
+  }
+  for (int prec = 0; prec < 2; ++prec) op_precompute_frozen(f0.L, prec, s);
+}
+
+void refresh_preconditioner(Problem& p, cudaStream_t s) {
+  // the finest state (and g) interpolated level by level down the hierarchy
+  const bool has_g = p.st_g;
+  for (size_t l = 0; l + 1 < p.levels.size(); ++l) {
+    const SepTransfer& t = p.transfers[l]->sep;
+    OpLevel& c = *p.levels[l + 1];
+    sep_interpolate(t, p.levels[l]->frozen[0].as<double>(), c.frozen[0].as<double>(), s);
+    vcast_d2f(c.frozen[1].as<float>(), c.frozen[0].as<double>(), c.n_main_dofs, s);
+    if (has_g) {
+      sep_interpolate(t, p.levels[l]->gexp[0].as<double>(), c.gexp[0].as<double>(), s);
+      vcast_d2f(c.gexp[1].as<float>(), c.gexp[0].as<double>(), c.n_main_dofs, s);
+    }
+    for (int prec = 0; prec < 2; ++prec) op_precompute_frozen(c.L, prec, s);
+  }
+  for (auto& lvp : p.levels) level_dinv(p, *lvp, s, true);
+  setup_coarse(p, s);  // synchronises
+}
+
+void set_state(Problem& p, double dt, double alpha, const double* U, const double* g, cudaStream_t s) {
+  set_state_fine(p, dt, alpha, U, g, s);
+  refresh_preconditioner(p, s);
 }
 
 void residual(Problem& p, int prec, void* dst, cudaStream_t s) {
@@ -812,7 +831,9 @@ NewtonResult bdf_step(Problem& p, const NewtonParams& np, const double* u_n, con
   NewtonResult res;
   const double tol_saved = p.tol;
   for (int it = 0;; ++it) {
-    set_state(p, np.dt, alpha, u, g, s);
+    // the finest level's state suffices for the residual and the Jacobian; the multigrid levels,
+    // diagonals and the coarse inverse are refreshed only before a linear solve
+    set_state_fine(p, np.dt, alpha, u, g, s);
     residual(p, 0, F, s);
     const double r = std::sqrt(host_dot(p, F, F, n, s));
     if (it == 0) res.residual0 = r;
@@ -824,6 +845,7 @@ NewtonResult bdf_step(Problem& p, const NewtonParams& np, const double* u_n, con
     }
     if (it == np.max_newton || !std::isfinite(r)) break;
     // J(u) d = -F by FGMRES with the multigrid preconditioner at the current state
+    refresh_preconditioner(p, s);
     vscale<double>(F, -1.0, n, s);
     p.tol = np.lin_tol;
     double rel = 0.0;

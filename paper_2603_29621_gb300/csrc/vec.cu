@@ -22,6 +22,7 @@ template <typename T> __global__ void k_axpby(T* y, T a, const T* x, T b, int64_
 template <typename T> __global__ void k_sub(T* r, const T* b, const T* ax, int64_t n) { GRID_STRIDE(i, n) r[i] = b[i] - ax[i]; }
 template <typename T> __global__ void k_scale(T* y, T a, int64_t n) { GRID_STRIDE(i, n) y[i] *= a; }
 __global__ void k_d2f(float* y, const double* x, int64_t n) { GRID_STRIDE(i, n) y[i] = (float)x[i]; }
+__global__ void k_unit(double* x, int64_t n, int64_t j) { GRID_STRIDE(i, n) x[i] = i == j ? 1.0 : 0.0; }
 __global__ void k_lincomb3(double* y, double a, const double* x1, double b, const double* x2, double c,
                            const double* x3, int64_t n) {
   GRID_STRIDE(i, n) {
@@ -186,6 +187,7 @@ template <typename T> void vaxpby(T* y, T a, const T* x, T b, int64_t n, cudaStr
 template <typename T> void vsub(T* r, const T* b, const T* ax, int64_t n, cudaStream_t s) { LAUNCH(k_sub<T>, n, s, r, b, ax, n); }
 template <typename T> void vscale(T* y, T a, int64_t n, cudaStream_t s) { LAUNCH(k_scale<T>, n, s, y, a, n); }
 void vcast_d2f(float* y, const double* x, int64_t n, cudaStream_t s) { LAUNCH(k_d2f, n, s, y, x, n); }
+void vunit(double* x, int64_t n, int64_t j, cudaStream_t s) { LAUNCH(k_unit, n, s, x, n, j); }
 void vlincomb3(double* y, double a, const double* x1, double b, const double* x2, double c, const double* x3,
                int64_t n, cudaStream_t s) {
   LAUNCH(k_lincomb3, n, s, y, a, x1, b, x2, c, x3, n);

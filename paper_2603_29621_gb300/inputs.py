@@ -55,3 +55,22 @@ def smooth_solution(xyz, field, dim, pressure_scale=1.0):
     sel = field == dim
     out[sel] = (pressure_scale * np.cos(np.pi * x) * np.cos(2 * np.pi * y) * cz)[sel]
     return out
+
+
+def taylor_green_state(xyz, field, dim):
+    """Initial condition sampled at support points (xyz, field): the Taylor--Green field
+    u = (sin 2 pi x cos 2 pi y cos 2 pi z, -cos 2 pi x sin 2 pi y cos 2 pi z, 0),
+    p = (cos 4 pi x + cos 4 pi y)(cos 4 pi z + 2) / 16 (2D: without the z factors)."""
+    tp = 2.0 * np.pi
+    x, y = xyz[:, 0], xyz[:, 1]
+    cz = np.cos(tp * xyz[:, 2]) if dim == 3 else 1.0
+    pz = (np.cos(2 * tp * xyz[:, 2]) + 2.0) if dim == 3 else 1.0
+    vals = [np.sin(tp * x) * np.cos(tp * y) * cz, -np.cos(tp * x) * np.sin(tp * y) * cz]
+    if dim == 3:
+        vals.append(np.zeros_like(x))
+    vals.append((np.cos(2 * tp * x) + np.cos(2 * tp * y)) * pz / 16.0)
+    out = np.empty(len(field))
+    for c in range(dim + 1):
+        sel = field == c
+        out[sel] = vals[c][sel]
+    return out
