@@ -87,6 +87,8 @@ op_kernel(const OpArgs<T, K + 1, K + 1, (OP == OP_STOKES ? K : K + 1)> args) {
   constexpr int BUF = TM::BUF;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* smem = reinterpret_cast<T*>(smem_raw);
+  const T* srcp = args.src + (int64_t)blockIdx.y * args.col_stride;
+  T* dstp = args.dst + (int64_t)blockIdx.y * args.col_stride;
 
   const int lane = lane_id();
   const int warp = threadIdx.x >> 5;
@@ -213,22 +215,22 @@ op_kernel(const OpArgs<T, K + 1, K + 1, (OP == OP_STOKES ? K : K + 1)> args) {
     for (int c = 0; c < N; ++c) {
       if constexpr (NU == 4) {
         if constexpr (sizeof(T) == 4) {
-          const float4 v = own ? __ldg(reinterpret_cast<const float4*>(args.src + node[c] * 4)) : make_float4(0, 0, 0, 0);
+          const float4 v = own ? __ldg(reinterpret_cast<const float4*>(srcp + node[c] * 4)) : make_float4(0, 0, 0, 0);
           u0[0][c] = v.x; u0[1][c] = v.y; u0[2][c] = v.z; u0[3][c] = v.w;
-          const float4 w = (own && valid) ? *reinterpret_cast<const float4*>(args.dst + node[c] * 4) : make_float4(0, 0, 0, 0);
+          const float4 w = (own && valid) ? *reinterpret_cast<const float4*>(dstp + node[c] * 4) : make_float4(0, 0, 0, 0);
           d0[0][c] = w.x; d0[1][c] = w.y; d0[2][c] = w.z; d0[3][c] = w.w;
         } else {
-          const double2 v0 = own ? __ldg(reinterpret_cast<const double2*>(args.src + node[c] * 4)) : make_double2(0, 0);
-          const double2 v1 = own ? __ldg(reinterpret_cast<const double2*>(args.src + node[c] * 4 + 2)) : make_double2(0, 0);
+          const double2 v0 = own ? __ldg(reinterpret_cast<const double2*>(srcp + node[c] * 4)) : make_double2(0, 0);
+          const double2 v1 = own ? __ldg(reinterpret_cast<const double2*>(srcp + node[c] * 4 + 2)) : make_double2(0, 0);
           u0[0][c] = v0.x; u0[1][c] = v0.y; u0[2][c] = v1.x; u0[3][c] = v1.y;
-          const double2 w0 = (own && valid) ? *reinterpret_cast<const double2*>(args.dst + node[c] * 4) : make_double2(0, 0);
-          const double2 w1 = (own && valid) ? *reinterpret_cast<const double2*>(args.dst + node[c] * 4 + 2) : make_double2(0, 0);
+          const double2 w0 = (own && valid) ? *reinterpret_cast<const double2*>(dstp + node[c] * 4) : make_double2(0, 0);
+          const double2 w1 = (own && valid) ? *reinterpret_cast<const double2*>(dstp + node[c] * 4 + 2) : make_double2(0, 0);
           d0[0][c] = w0.x; d0[1][c] = w0.y; d0[2][c] = w1.x; d0[3][c] = w1.y;
         }
       } else {
 #pragma unroll
         for (int f = 0; f < NU; ++f) {
-          u0[f][c] = own ? args.src[node[c] * NU + f] : T(0);
+          u0[f][c] = own ? srcp[node[c] * NU + f] : T(0);
           d0[f][c] = 0;
         }
       }
@@ -239,7 +241,7 @@ op_kernel(const OpArgs<T, K + 1, K + 1, (OP == OP_STOKES ? K : K + 1)> args) {
     }
     if (Tr::SPLIT_P) {
 #pragma unroll
-      for (int c = 0; c < NP; ++c) pv0[c] = ownp ? args.src[args.p_offset + pnode[c]] : T(0);
+      for (int c = 0; c < NP; ++c) pv0[c] = ownp ? srcp[args.p_offset + pnode[c]] : T(0);
     }
   }
 
@@ -364,9 +366,15 @@ op_kernel(const OpArgs<T, K + 1, K + 1, (OP == OP_STOKES ? K : K + 1)> args) {
     }
   }
 
-  // the local loop: one pass for vmult, NLOC passes (unit vectors) for the diagonal
-  const int npass = DIAG ? NLOC : 1;
-  for (int pass = 0; pass < npass; ++pass) {
+  // the local loop: one pass for vmult, NLOC passes (unit vectors) for the diagonal; in diagonal
+  // mode blockIdx.y takes the passes [pass_begin, pass_end) (levels with few cells split them)
+  int pass_begin = 0, pass_end = 1;
+  if (DIAG) {
+    const int per = (NLOC + (int)gridDim.y - 1) / (int)gridDim.y;
+    pass_begin = (int)blockIdx.y * per;
+    pass_end = min(NLOC, pass_begin + per);
+  }
+  for (int pass = pass_begin; pass < pass_end; ++pass) {
     T u[NU][N];
     T pv[NP];
     if (!DIAG) {
@@ -620,7 +628,7 @@ op_kernel(const OpArgs<T, K + 1, K + 1, (OP == OP_STOKES ? K : K + 1)> args) {
       if (own) {
 #pragma unroll
         for (int c = 0; c < N; ++c) {
-          T* d = args.dst + node[c] * NU;
+          T* d = dstp + node[c] * NU;
           if constexpr (NU == 4) {
             // dst values were loaded with the gather (no other cell of this colour touches them)
             if constexpr (sizeof(T) == 4) {
@@ -638,20 +646,30 @@ op_kernel(const OpArgs<T, K + 1, K + 1, (OP == OP_STOKES ? K : K + 1)> args) {
       }
       if (Tr::SPLIT_P && ownp) {
 #pragma unroll
-        for (int c = 0; c < NP; ++c) args.dst[args.p_offset + pnode[c]] += rp[c];
+        for (int c = 0; c < NP; ++c) dstp[args.p_offset + pnode[c]] += rp[c];
       }
     }
   }
   if (DIAG && valid) {
+    // only the entries of this block's passes (another block of the same cell owns the others)
     if (own) {
 #pragma unroll
-      for (int c = 0; c < N; ++c)
+      for (int c = 0; c < N; ++c) {
+        const int slot = DIM == 3 ? (c * N + tj_n) * N + ti_n : c * N + ti_n;
 #pragma unroll
-        for (int f = 0; f < NU; ++f) args.dst[node[c] * NU + f] += dacc[f][c];
+        for (int f = 0; f < NU; ++f) {
+          const int ps = f * NB + slot;
+          if (ps >= pass_begin && ps < pass_end) dstp[node[c] * NU + f] += dacc[f][c];
+        }
+      }
     }
     if (Tr::SPLIT_P && ownp) {
 #pragma unroll
-      for (int c = 0; c < NP; ++c) args.dst[args.p_offset + pnode[c]] += daccp[c];
+      for (int c = 0; c < NP; ++c) {
+        const int slot = DIM == 3 ? (c * NP + tj_p) * NP + ti_p : c * NP + ti_p;
+        const int ps = NU * NB + slot;
+        if (ps >= pass_begin && ps < pass_end) dstp[args.p_offset + pnode[c]] += daccp[c];
+      }
     }
   }
 }

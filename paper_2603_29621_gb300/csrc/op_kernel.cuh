@@ -71,6 +71,9 @@ struct OpArgs {
   // point), laid out [cell position][lane][point][NFQ] with cell position = colour offset + index
   T* fq;
   int64_t color_offset;  // structured: cells of the colours before this one
+  // several right-hand sides in one launch: blockIdx.y selects src/dst + blockIdx.y * col_stride
+  // (0 in diagonal mode, where blockIdx.y splits the unit-vector passes instead)
+  int64_t col_stride;
 };
 
 // ------------------------------------------------------------ small helpers

@@ -29,7 +29,8 @@ static void build_tables(const OpLaunch& L, Tables<T, Q, N, NP>& t) {
 }
 
 template <int DIM, int K, int OP, typename T>
-void op_launch(const OpLaunch& L, const T* src, T* dst, bool diag, cudaStream_t s, int fq_mode) {
+void op_launch(const OpLaunch& L, const T* src, T* dst, bool diag, cudaStream_t s, int fq_mode, int ncols,
+               int64_t col_stride) {
   constexpr int Q = K + 1, N = K + 1, NP = OP == OP_STOKES ? K : K + 1;
   OpArgs<T, Q, N, NP> a{};
   if (L.Q != Q || L.N != N || L.NP != NP) throw Error(kErrArg, "operator tables do not match the degree");
@@ -53,6 +54,9 @@ void op_launch(const OpLaunch& L, const T* src, T* dst, bool diag, cudaStream_t 
   a.div_sign = (T)L.div_sign;
   for (int b = 0; b < 7; ++b) a.cf[b] = (L.terms >> b) & 1 ? T(1) : T(0);
   a.diag = diag;
+  if (ncols < 1 || (ncols > 1 && (diag || fq_mode == 2 || fq_mode == 3)))
+    throw Error(kErrArg, "several columns only for operator applications");
+  a.col_stride = ncols > 1 ? col_stride : 0;
   // frozen state: -1 = use the precomputed point data when present; 2 = write it (set-up pass)
   a.fq = reinterpret_cast<T*>(L.fq[prec]);
   a.gexp = reinterpret_cast<const T*>(L.gexp[prec]);
@@ -99,7 +103,17 @@ void op_launch(const OpLaunch& L, const T* src, T* dst, bool diag, cudaStream_t 
       ncell = a.cell_end - a.cell_begin;
     }
     if (ncell <= 0) continue;
-    const unsigned grid = (unsigned)((ncell + cells_per_block - 1) / cells_per_block);
+    const unsigned gx = (unsigned)((ncell + cells_per_block - 1) / cells_per_block);
+    // diagonal of a level with few cells: split the unit-vector passes over blockIdx.y (only on
+    // uniform meshes, where no two slots of a cell share a DoF, so the blocks write disjoint entries)
+    unsigned gy = (unsigned)ncols;
+    if (diag && L.structured) {
+      using Tr = OpTraits<OP, DIM>;
+      constexpr int NLOC = Tr::NU * ipow(N, DIM) + (Tr::SPLIT_P ? ipow(NP, DIM) : 0);
+      const unsigned want = 152u * 8u;
+      gy = gx >= want ? 1u : std::min<unsigned>((unsigned)NLOC, (want + gx - 1) / gx);
+    }
+    const dim3 grid(gx, gy);
     if (L.timer && L.timer->enabled) L.timer->record_pair_begin(s);
     if constexpr (OP == OP_STAB_NS) {
       if (fq == 2) {
@@ -141,7 +155,9 @@ void op_launch(const OpLaunch& L, const T* src, T* dst, bool diag, cudaStream_t 
 }
 
 #define MFNS_INSTANTIATE_OP(DIM, K, OP)                                                                        \
-  template void op_launch<DIM, K, OP, double>(const OpLaunch&, const double*, double*, bool, cudaStream_t, int); \
-  template void op_launch<DIM, K, OP, float>(const OpLaunch&, const float*, float*, bool, cudaStream_t, int);
+  template void op_launch<DIM, K, OP, double>(const OpLaunch&, const double*, double*, bool, cudaStream_t, int, int, \
+                                               int64_t);                                                           \
+  template void op_launch<DIM, K, OP, float>(const OpLaunch&, const float*, float*, bool, cudaStream_t, int, int,    \
+                                              int64_t);
 
 }  // namespace mfns

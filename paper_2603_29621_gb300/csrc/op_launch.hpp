@@ -65,10 +65,15 @@ void fill_tables(OpLaunch& L);
 
 // dst = A src on the free rows (dst must be zeroed by the caller); diag = true
 // accumulates the diagonal instead (src ignored).  Constrained rows untouched.
+// ncols > 1: ncols products at once, column j reading src + j col_stride and writing dst + j col_stride.
 template <int DIM, int K, int OP, typename T>
-void op_launch(const OpLaunch& L, const T* src, T* dst, bool diag, cudaStream_t s, int fq_mode = -1);
+void op_launch(const OpLaunch& L, const T* src, T* dst, bool diag, cudaStream_t s, int fq_mode = -1, int ncols = 1,
+               int64_t col_stride = 0);
 
 // Runtime dispatch over (dim, k, op, precision); prec 0 = fp64, 1 = fp32.
 void op_apply(const OpLaunch& L, int prec, const void* src, void* dst, bool diag, cudaStream_t s);
+// ncols applications at once (column j: src + j col_stride -> dst + j col_stride), dst zeroed by the caller
+void op_apply_cols(const OpLaunch& L, int prec, const void* src, void* dst, int ncols, int64_t col_stride,
+                   cudaStream_t s);
 
 }  // namespace mfns

@@ -217,6 +217,17 @@ void oplevel_vmult(const OpLevel& lv, int prec, const void* src, void* dst, cuda
     vcopy_idx<float>((float*)dst, (const float*)src, lv.constrained.as<int32_t>(), nc, s);
 }
 
+void oplevel_vmult_cols(const OpLevel& lv, int prec, const void* X, void* Y, int ncols, cudaStream_t s) {
+  const int64_t n = lv.n_dofs;
+  MFNS_CUDA(cudaMemsetAsync(Y, 0, (size_t)ncols * n * esize(prec), s));
+  op_apply_cols(lv.L, prec, X, Y, ncols, n, s);
+  const int64_t nc = (int64_t)lv.constrained_host.size();
+  if (prec == 0)
+    vcopy_idx_cols<double>((double*)Y, (const double*)X, lv.constrained.as<int32_t>(), nc, n, ncols, s);
+  else
+    vcopy_idx_cols<float>((float*)Y, (const float*)X, lv.constrained.as<int32_t>(), nc, n, ncols, s);
+}
+
 void oplevel_diag(const OpLevel& lv, int prec, void* diag, cudaStream_t s) {
   MFNS_CUDA(cudaMemsetAsync(diag, 0, lv.n_dofs * esize(prec), s));
   op_apply(lv.L, prec, nullptr, diag, true, s);

@@ -49,6 +49,8 @@ struct OpLevel {
 void build_oplevel(OpLevel& lv, const Forest& f, int op, int k, const Physics& ph, Budget* bud);
 void oplevel_vmult(const OpLevel& lv, int prec, const void* src, void* dst, cudaStream_t s);
 void oplevel_diag(const OpLevel& lv, int prec, void* diag, cudaStream_t s);
+// Y[:, j] = A X[:, j] for ncols columns of length n_dofs (column-major blocks)
+void oplevel_vmult_cols(const OpLevel& lv, int prec, const void* X, void* Y, int ncols, cudaStream_t s);
 void oplevel_distribute(const OpLevel& lv, int prec, void* x, cudaStream_t s);
 void oplevel_support(const OpLevel& lv, double* xyz, int* field);
 

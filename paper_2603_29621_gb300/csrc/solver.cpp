@@ -326,18 +326,19 @@ void setup_coarse(Problem& p, cudaStream_t s) {
   p.coarse_n = n;
   p.coarse_dense = n <= 4096;
   if (!p.coarse_dense) return;
-  // assemble the coarse matrix with the fp64 operator, kCols unit-vector products per round trip
-  constexpr int64_t kCols = 64;
+  // assemble the coarse matrix with the fp64 operator: blocks of kCols unit vectors, each block
+  // applied in one multi-column launch per colour
+  constexpr int64_t kCols = 128;
   std::vector<double> A(n * n), cols(n * kCols);
-  Workspace& w = p.ws[0].back();
-  if (p.coarse_cols.bytes() != (size_t)(n * kCols * 8)) p.coarse_cols.alloc(p.bud, n * kCols * 8);
+  const int64_t blk = std::min<int64_t>(kCols, n);
+  if (p.coarse_cols.bytes() != (size_t)(2 * n * blk * 8)) p.coarse_cols.alloc(p.bud, 2 * n * blk * 8);
+  double* X = p.coarse_cols.as<double>();
+  double* Y = X + n * blk;
   for (int64_t j0 = 0; j0 < n; j0 += kCols) {
     const int64_t nb = std::min<int64_t>(kCols, n - j0);
-    for (int64_t j = 0; j < nb; ++j) {
-      vunit(w.x.as<double>(), n, j0 + j, s);
-      oplevel_vmult(cl, 0, w.x.get(), p.coarse_cols.as<double>() + j * n, s);
-    }
-    MFNS_CUDA(cudaMemcpyAsync(cols.data(), p.coarse_cols.get(), nb * n * 8, cudaMemcpyDeviceToHost, s));
+    vunit_cols(X, n, j0, nb, s);
+    oplevel_vmult_cols(cl, 0, X, Y, (int)nb, s);
+    MFNS_CUDA(cudaMemcpyAsync(cols.data(), Y, nb * n * 8, cudaMemcpyDeviceToHost, s));
     MFNS_CUDA(cudaStreamSynchronize(s));
     for (int64_t j = 0; j < nb; ++j)
       for (int64_t i = 0; i < n; ++i) A[i * n + j0 + j] = cols[j * n + i];

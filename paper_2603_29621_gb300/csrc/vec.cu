@@ -22,7 +22,19 @@ template <typename T> __global__ void k_axpby(T* y, T a, const T* x, T b, int64_
 template <typename T> __global__ void k_sub(T* r, const T* b, const T* ax, int64_t n) { GRID_STRIDE(i, n) r[i] = b[i] - ax[i]; }
 template <typename T> __global__ void k_scale(T* y, T a, int64_t n) { GRID_STRIDE(i, n) y[i] *= a; }
 __global__ void k_d2f(float* y, const double* x, int64_t n) { GRID_STRIDE(i, n) y[i] = (float)x[i]; }
-__global__ void k_unit(double* x, int64_t n, int64_t j) { GRID_STRIDE(i, n) x[i] = i == j ? 1.0 : 0.0; }
+__global__ void k_unit_cols(double* X, int64_t n, int64_t j0, int64_t nb) {
+  GRID_STRIDE(t, n * nb) {
+    const int64_t j = t / n, i = t - j * n;
+    X[t] = i == j0 + j ? 1.0 : 0.0;
+  }
+}
+template <typename T>
+__global__ void k_copy_idx_cols(T* Y, const T* X, const int32_t* idx, int64_t m, int64_t n, int64_t nb) {
+  GRID_STRIDE(t, m * nb) {
+    const int64_t j = t / m, i = idx[t - j * m];
+    Y[j * n + i] = X[j * n + i];
+  }
+}
 __global__ void k_lincomb3(double* y, double a, const double* x1, double b, const double* x2, double c,
                            const double* x3, int64_t n) {
   GRID_STRIDE(i, n) {
@@ -187,7 +199,15 @@ template <typename T> void vaxpby(T* y, T a, const T* x, T b, int64_t n, cudaStr
 template <typename T> void vsub(T* r, const T* b, const T* ax, int64_t n, cudaStream_t s) { LAUNCH(k_sub<T>, n, s, r, b, ax, n); }
 template <typename T> void vscale(T* y, T a, int64_t n, cudaStream_t s) { LAUNCH(k_scale<T>, n, s, y, a, n); }
 void vcast_d2f(float* y, const double* x, int64_t n, cudaStream_t s) { LAUNCH(k_d2f, n, s, y, x, n); }
-void vunit(double* x, int64_t n, int64_t j, cudaStream_t s) { LAUNCH(k_unit, n, s, x, n, j); }
+void vunit_cols(double* X, int64_t n, int64_t j0, int64_t nb, cudaStream_t s) {
+  LAUNCH(k_unit_cols, n * nb, s, X, n, j0, nb);
+}
+template <typename T>
+void vcopy_idx_cols(T* Y, const T* X, const int32_t* idx, int64_t m, int64_t n, int64_t nb, cudaStream_t s) {
+  LAUNCH(k_copy_idx_cols<T>, m * nb, s, Y, X, idx, m, n, nb);
+}
+template void vcopy_idx_cols<double>(double*, const double*, const int32_t*, int64_t, int64_t, int64_t, cudaStream_t);
+template void vcopy_idx_cols<float>(float*, const float*, const int32_t*, int64_t, int64_t, int64_t, cudaStream_t);
 void vlincomb3(double* y, double a, const double* x1, double b, const double* x2, double c, const double* x3,
                int64_t n, cudaStream_t s) {
   LAUNCH(k_lincomb3, n, s, y, a, x1, b, x2, c, x3, n);

@@ -19,8 +19,11 @@ template <typename T> void vaxpby(T* y, T a, const T* x, T b, int64_t n, cudaStr
 template <typename T> void vsub(T* r, const T* b, const T* ax, int64_t n, cudaStream_t s);   // r = b - ax
 template <typename T> void vscale(T* y, T a, int64_t n, cudaStream_t s);
 void vcast_d2f(float* y, const double* x, int64_t n, cudaStream_t s);
-// x = e_j (unit vector)
-void vunit(double* x, int64_t n, int64_t j, cudaStream_t s);
+// X (n x nb, column-major) = columns j0 .. j0+nb-1 of the identity
+void vunit_cols(double* X, int64_t n, int64_t j0, int64_t nb, cudaStream_t s);
+// Y[:, j][idx] = X[:, j][idx] for the nb columns of length n
+template <typename T>
+void vcopy_idx_cols(T* Y, const T* X, const int32_t* idx, int64_t m, int64_t n, int64_t nb, cudaStream_t s);
 // y = a x1 + b x2 + c x3 (x2, x3 may be null: their terms are left out)
 void vlincomb3(double* y, double a, const double* x1, double b, const double* x2, double c, const double* x3,
                int64_t n, cudaStream_t s);
