@@ -113,6 +113,11 @@ typedef struct {
   int recompute_frozen; /* STAB_NS: 1 = interpolate the frozen state inside every apply; 0 (default) =
                            store its point values (u, grad u, Rbar, tau) once per level (more HBM,
                            fewer shared-memory contractions per apply) */
+  int fused_smoother;   /* 1: on uniform levels the Chebyshev / Jacobi update and the V-cycle residual
+                           are applied by the cell kernel to each node in the colour that completes
+                           its product (no separate vector pass); 0 (default): the product is
+                           written out and a streaming kernel applies the update (faster on GB300:
+                           the cell kernel is latency-bound) */
 } mfns_problem_desc;
 
 typedef struct {

@@ -29,6 +29,7 @@ class ProblemDesc(C.Structure):
         ("coarse_stop_n", C.c_int), ("fgmres_restart", C.c_int), ("tol", C.c_double),
         ("maxit", C.c_int), ("cg_iterations", C.c_int), ("lambda_max", C.c_double),
         ("recompute_frozen", C.c_int),
+        ("fused_smoother", C.c_int),
     ]
 
 

@@ -126,6 +126,7 @@ int mfns_problem_create(mfns_ctx* ctx, const mfns_mesh* mesh, const mfns_problem
   p->tol = desc->tol > 0 ? desc->tol : 1e-8;
   p->maxit = desc->maxit > 0 ? desc->maxit : 500;
   p->cg_iterations = desc->cg_iterations > 0 ? desc->cg_iterations : 10;
+  p->fused_smoother = desc->fused_smoother != 0;
   if (desc->lambda_max > 0)
     for (auto& lv : p->levels) lv->lmax = desc->lambda_max;
   alloc_workspaces(*p);

@@ -75,7 +75,8 @@ struct FrozenPoint {
   }
 };
 
-template <int DIM, int K, int OP, typename T, bool STRUCT, bool DIAG, int FQ = 0>
+// EPI: the fused smoother / residual epilogue is compiled in (structured launches only).
+template <int DIM, int K, int OP, typename T, bool STRUCT, bool DIAG, int FQ = 0, bool EPI = false>
 __global__ void __launch_bounds__(kOpWarps * 32, OpMinBlocks<DIM, K, OP, T>::value)
 op_kernel(const OpArgs<T, K + 1, K + 1, (OP == OP_STOKES ? K : K + 1)> args) {
   constexpr int Q = K + 1, N = K + 1, NP = OP == OP_STOKES ? K : K + 1;
@@ -629,6 +630,48 @@ op_kernel(const OpArgs<T, K + 1, K + 1, (OP == OP_STOKES ? K : K + 1)> args) {
 #pragma unroll
         for (int c = 0; c < N; ++c) {
           T* d = dstp + node[c] * NU;
+          if (EPI && args.lastc[node[c]] == (uint8_t)args.color) {
+            // fused epilogue: this colour completes (A src) at the node
+            const int64_t o = node[c] * NU;
+            const bool cbnd = OP != OP_PMASS && bnd[c];  // velocity entries are identity rows
+            if constexpr (NU == 4 && sizeof(T) == 4) {
+              const float4 b4 = *reinterpret_cast<const float4*>(args.eb + o);
+              const float ax[4] = {d0[0][c] + r[0][c], d0[1][c] + r[1][c], d0[2][c] + r[2][c], d0[3][c] + r[3][c]};
+              const float bb[4] = {b4.x, b4.y, b4.z, b4.w};
+              float xo[4];
+              if (args.epi == 1) {
+                const float4 q4 = *reinterpret_cast<const float4*>(args.edinv + o);
+                const float4 e4 = *reinterpret_cast<const float4*>(args.ed + o);
+                const float qq[4] = {q4.x, q4.y, q4.z, q4.w}, ee[4] = {e4.x, e4.y, e4.z, e4.w};
+                float dn[4];
+#pragma unroll
+                for (int f = 0; f < 4; ++f) {
+                  const bool keep = cbnd && f < DIM;
+                  dn[f] = keep ? ee[f] : args.ec1 * ee[f] + args.ec2 * qq[f] * (bb[f] - ax[f]);
+                  xo[f] = u0[f][c] + dn[f];
+                }
+                *reinterpret_cast<float4*>(args.ed + o) = make_float4(dn[0], dn[1], dn[2], dn[3]);
+              } else {
+#pragma unroll
+                for (int f = 0; f < 4; ++f) xo[f] = bb[f] - ax[f];
+              }
+              *reinterpret_cast<float4*>(args.exout + o) = make_float4(xo[0], xo[1], xo[2], xo[3]);
+            } else {
+#pragma unroll
+              for (int f = 0; f < NU; ++f) {
+                if (cbnd && f < DIM) continue;
+                const T ax = (NU == 4 ? d0[f][c] : d[f]) + r[f][c];
+                if (args.epi == 1) {
+                  const T dn = args.ec1 * args.ed[o + f] + args.ec2 * args.edinv[o + f] * (args.eb[o + f] - ax);
+                  args.ed[o + f] = dn;
+                  args.exout[o + f] = u0[f][c] + dn;
+                } else {
+                  args.exout[o + f] = args.eb[o + f] - ax;
+                }
+              }
+            }
+            continue;
+          }
           if constexpr (NU == 4) {
             // dst values were loaded with the gather (no other cell of this colour touches them)
             if constexpr (sizeof(T) == 4) {

@@ -15,9 +15,9 @@ constexpr int kOpWarpsDefault = 4;
 
 #define MFNS_DECL(DIM, K, OP)                                                                                  \
   extern template void op_launch<DIM, K, OP, double>(const OpLaunch&, const double*, double*, bool, cudaStream_t, \
-                                                     int, int, int64_t);                                         \
+                                                     int, int, int64_t, const OpEpilogue*);                      \
   extern template void op_launch<DIM, K, OP, float>(const OpLaunch&, const float*, float*, bool, cudaStream_t, int, \
-                                                    int, int64_t);
+                                                    int, int64_t, const OpEpilogue*);
 
 MFNS_DECL(3, 1, OP_STAB_NS) MFNS_DECL(3, 2, OP_STAB_NS) MFNS_DECL(3, 3, OP_STAB_NS)
 MFNS_DECL(2, 1, OP_STAB_NS) MFNS_DECL(2, 2, OP_STAB_NS) MFNS_DECL(2, 3, OP_STAB_NS) MFNS_DECL(2, 4, OP_STAB_NS)
@@ -41,10 +41,10 @@ bool op_supported(int dim, int k, int op) {
 
 template <typename T>
 static void dispatch(const OpLaunch& L, const T* s, T* d, bool diag, cudaStream_t st, int fq_mode = -1,
-                     int ncols = 1, int64_t col_stride = 0) {
+                     int ncols = 1, int64_t col_stride = 0, const OpEpilogue* epi = nullptr) {
 #define MFNS_CASE(DIM, K, OP)                   \
   if (L.dim == DIM && L.k == K && L.op == OP) \
-    return op_launch<DIM, K, OP, T>(L, s, d, diag, st, fq_mode, ncols, col_stride);
+    return op_launch<DIM, K, OP, T>(L, s, d, diag, st, fq_mode, ncols, col_stride, epi);
   MFNS_CASE(3, 1, OP_STAB_NS) MFNS_CASE(3, 2, OP_STAB_NS) MFNS_CASE(3, 3, OP_STAB_NS)
   MFNS_CASE(2, 1, OP_STAB_NS) MFNS_CASE(2, 2, OP_STAB_NS) MFNS_CASE(2, 3, OP_STAB_NS) MFNS_CASE(2, 4, OP_STAB_NS)
   MFNS_CASE(3, 2, OP_STOKES) MFNS_CASE(3, 3, OP_STOKES) MFNS_CASE(3, 4, OP_STOKES)
@@ -156,6 +156,13 @@ void op_apply(const OpLaunch& L, int prec, const void* src, void* dst, bool diag
     dispatch<double>(L, static_cast<const double*>(src), static_cast<double*>(dst), diag, s);
   else
     dispatch<float>(L, static_cast<const float*>(src), static_cast<float*>(dst), diag, s);
+}
+
+void op_apply_epi(const OpLaunch& L, int prec, const void* src, void* dst, const OpEpilogue& epi, cudaStream_t s) {
+  if (prec == 0)
+    dispatch<double>(L, static_cast<const double*>(src), static_cast<double*>(dst), false, s, -1, 1, 0, &epi);
+  else
+    dispatch<float>(L, static_cast<const float*>(src), static_cast<float*>(dst), false, s, -1, 1, 0, &epi);
 }
 
 void op_apply_cols(const OpLaunch& L, int prec, const void* src, void* dst, int ncols, int64_t col_stride,

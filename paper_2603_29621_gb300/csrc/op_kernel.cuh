@@ -74,6 +74,17 @@ struct OpArgs {
   // several right-hand sides in one launch: blockIdx.y selects src/dst + blockIdx.y * col_stride
   // (0 in diagonal mode, where blockIdx.y splits the unit-vector passes instead)
   int64_t col_stride;
+  // fused epilogue, applied to a node by the colour that completes its product (lastc[node] ==
+  // colour); dst then only carries partial sums.  epi 1: Chebyshev / Jacobi step
+  // ed = ec1 ed + ec2 edinv (eb - A src), exout = src + ed;  epi 2: residual exout = eb - A src.
+  // Constrained rows are left to a separate pass (identity rows).
+  int epi;
+  const uint8_t* lastc;
+  const T* eb;
+  const T* edinv;
+  T* ed;
+  T* exout;
+  T ec1, ec2;
 };
 
 // ------------------------------------------------------------ small helpers

@@ -30,7 +30,7 @@ static void build_tables(const OpLaunch& L, Tables<T, Q, N, NP>& t) {
 
 template <int DIM, int K, int OP, typename T>
 void op_launch(const OpLaunch& L, const T* src, T* dst, bool diag, cudaStream_t s, int fq_mode, int ncols,
-               int64_t col_stride) {
+               int64_t col_stride, const OpEpilogue* epi) {
   constexpr int Q = K + 1, N = K + 1, NP = OP == OP_STOKES ? K : K + 1;
   OpArgs<T, Q, N, NP> a{};
   if (L.Q != Q || L.N != N || L.NP != NP) throw Error(kErrArg, "operator tables do not match the degree");
@@ -57,6 +57,20 @@ void op_launch(const OpLaunch& L, const T* src, T* dst, bool diag, cudaStream_t 
   if (ncols < 1 || (ncols > 1 && (diag || fq_mode == 2 || fq_mode == 3)))
     throw Error(kErrArg, "several columns only for operator applications");
   a.col_stride = ncols > 1 ? col_stride : 0;
+  const bool fused = epi && epi->mode;
+  if (fused) {
+    if (diag || ncols > 1 || fq_mode == 2 || fq_mode == 3 || OpTraits<OP, DIM>::SPLIT_P || !L.lastc ||
+        !L.structured)
+      throw Error(kErrArg, "fused epilogue: single-column application on a uniform mesh, main-node operator");
+    a.epi = epi->mode;
+    a.lastc = L.lastc;
+    a.eb = static_cast<const T*>(epi->b);
+    a.edinv = static_cast<const T*>(epi->dinv);
+    a.ed = static_cast<T*>(epi->d);
+    a.exout = static_cast<T*>(epi->xout);
+    a.ec1 = (T)epi->c1;
+    a.ec2 = (T)epi->c2;
+  }
   // frozen state: -1 = use the precomputed point data when present; 2 = write it (set-up pass)
   a.fq = reinterpret_cast<T*>(L.fq[prec]);
   a.gexp = reinterpret_cast<const T*>(L.gexp[prec]);
@@ -84,6 +98,8 @@ void op_launch(const OpLaunch& L, const T* src, T* dst, bool diag, cudaStream_t 
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
       MFNS_CUDA(cudaFuncSetAttribute(op_kernel<DIM, K, OP, T, false, false, 1>,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+      MFNS_CUDA(cudaFuncSetAttribute(op_kernel<DIM, K, OP, T, true, false, 1, true>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
       attr_done.fetch_or(bit);
     }
   }
@@ -98,6 +114,7 @@ void op_launch(const OpLaunch& L, const T* src, T* dst, bool diag, cudaStream_t 
       for (int d = 0; d < DIM; ++d) ncell *= (L.n - ((c >> d) & 1) + 1) / 2;
       color_offset += ncell;
     } else {
+      a.color = c;
       a.cell_begin = L.color_ptr[c];
       a.cell_end = L.color_ptr[c + 1];
       ncell = a.cell_end - a.cell_begin;
@@ -127,14 +144,18 @@ void op_launch(const OpLaunch& L, const T* src, T* dst, bool diag, cudaStream_t 
         else
           op_kernel<DIM, K, OP, T, false, false, 3><<<grid, warps * 32, smem, s>>>(a);
       } else if (fq == 1) {
-        if (structured)
+        if (structured && fused)
+          op_kernel<DIM, K, OP, T, true, false, 1, true><<<grid, warps * 32, smem_fq, s>>>(a);
+        else if (structured)
           op_kernel<DIM, K, OP, T, true, false, 1><<<grid, warps * 32, smem_fq, s>>>(a);
         else if (diag)
           op_kernel<DIM, K, OP, T, false, true, 1><<<grid, warps * 32, smem_fq, s>>>(a);
         else
           op_kernel<DIM, K, OP, T, false, false, 1><<<grid, warps * 32, smem_fq, s>>>(a);
       } else {
-        if (structured)
+        if (structured && fused)
+          op_kernel<DIM, K, OP, T, true, false, 0, true><<<grid, warps * 32, smem, s>>>(a);
+        else if (structured)
           op_kernel<DIM, K, OP, T, true, false, 0><<<grid, warps * 32, smem, s>>>(a);
         else if (diag)
           op_kernel<DIM, K, OP, T, false, true, 0><<<grid, warps * 32, smem, s>>>(a);
@@ -142,7 +163,9 @@ void op_launch(const OpLaunch& L, const T* src, T* dst, bool diag, cudaStream_t 
           op_kernel<DIM, K, OP, T, false, false, 0><<<grid, warps * 32, smem, s>>>(a);
       }
     } else {
-      if (structured)
+      if (structured && fused)
+        op_kernel<DIM, K, OP, T, true, false, 0, true><<<grid, warps * 32, smem, s>>>(a);
+      else if (structured)
         op_kernel<DIM, K, OP, T, true, false><<<grid, warps * 32, smem, s>>>(a);
       else if (diag)
         op_kernel<DIM, K, OP, T, false, true><<<grid, warps * 32, smem, s>>>(a);
@@ -156,8 +179,8 @@ void op_launch(const OpLaunch& L, const T* src, T* dst, bool diag, cudaStream_t 
 
 #define MFNS_INSTANTIATE_OP(DIM, K, OP)                                                                        \
   template void op_launch<DIM, K, OP, double>(const OpLaunch&, const double*, double*, bool, cudaStream_t, int, int, \
-                                               int64_t);                                                           \
+                                               int64_t, const OpEpilogue*);                                        \
   template void op_launch<DIM, K, OP, float>(const OpLaunch&, const float*, float*, bool, cudaStream_t, int, int,    \
-                                              int64_t);
+                                              int64_t, const OpEpilogue*);
 
 }  // namespace mfns

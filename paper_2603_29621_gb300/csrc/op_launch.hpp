@@ -19,6 +19,17 @@ struct KernelTimer {
   ~KernelTimer();
 };
 
+// Fused epilogue of an operator application (see OpArgs): mode 1 = Chebyshev / Jacobi step,
+// mode 2 = residual; pointers in the launch precision.
+struct OpEpilogue {
+  int mode = 0;
+  const void* b = nullptr;
+  const void* dinv = nullptr;
+  void* d = nullptr;
+  void* xout = nullptr;
+  double c1 = 0.0, c2 = 0.0;
+};
+
 struct OpLaunch {
   int dim = 3, k = 2, op = 0;        // main-field degree k, op = OpKind
   bool structured = false;          // uniform mesh with lexicographic numbering
@@ -44,6 +55,7 @@ struct OpLaunch {
   KernelTimer* timer = nullptr;     // optional per-launch timing
   void* fq[2] = {nullptr, nullptr}; // stabilised NS: precomputed frozen point data (fp64 / fp32)
   int warps[2] = {0, 0};            // warps per block per precision (0 = not tuned yet: use 4)
+  const uint8_t* lastc = nullptr;   // per main node: index of the last colour whose cells touch it
 };
 
 // Autotuner: pick the warps per block (1, 2 or 4) of the cell kernel for this operator and
@@ -68,10 +80,12 @@ void fill_tables(OpLaunch& L);
 // ncols > 1: ncols products at once, column j reading src + j col_stride and writing dst + j col_stride.
 template <int DIM, int K, int OP, typename T>
 void op_launch(const OpLaunch& L, const T* src, T* dst, bool diag, cudaStream_t s, int fq_mode = -1, int ncols = 1,
-               int64_t col_stride = 0);
+               int64_t col_stride = 0, const OpEpilogue* epi = nullptr);
 
 // Runtime dispatch over (dim, k, op, precision); prec 0 = fp64, 1 = fp32.
 void op_apply(const OpLaunch& L, int prec, const void* src, void* dst, bool diag, cudaStream_t s);
+// dst (zeroed by the caller) receives partial sums; the epilogue writes the fused result
+void op_apply_epi(const OpLaunch& L, int prec, const void* src, void* dst, const OpEpilogue& epi, cudaStream_t s);
 // ncols applications at once (column j: src + j col_stride -> dst + j col_stride), dst zeroed by the caller
 void op_apply_cols(const OpLaunch& L, int prec, const void* src, void* dst, int ncols, int64_t col_stride,
                    cudaStream_t s);

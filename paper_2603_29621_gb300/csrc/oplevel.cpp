@@ -110,6 +110,36 @@ void build_oplevel(OpLevel& lv, const Forest& f, int op, int k, const Physics& p
     for (size_t i = 0; i < nc; ++i)
       for (int b = 0; b < nbp; ++b) cp[i * nbp + b] = lv.np.cell_master[(size_t)lv.perm[i] * nbp + b];
   }
+  // last colour touching each main node (fused smoother / residual epilogue): colours run in
+  // index order, so it is the largest colour index among the cells whose slots name the node
+  if (op != OP_STOKES) {
+    std::vector<uint8_t> lc(lv.nu.n_nodes, 0);
+    if (L.structured) {  // the structured launch's colour = parity bits of the cell coordinates
+      const int n = f.n;
+      const int64_t M = (int64_t)k * n + 1;
+      for (int64_t g = 0; g < lv.nu.n_nodes; ++g) {
+        int64_t idx[3] = {g % M, (g / M) % M, dim == 3 ? g / (M * M) : 0};
+        int col = 0;
+        for (int d = 0; d < dim; ++d) {
+          // cells touching the node along d: i/k, and i/k - 1 when the node lies on a cell face
+          const int64_t i = idx[d];
+          int bit = 0;
+          const int64_t c0 = i / k;
+          if (c0 < n && (c0 & 1)) bit = 1;
+          if (i % k == 0 && c0 - 1 >= 0 && ((c0 - 1) & 1)) bit = 1;
+          col |= bit << d;
+        }
+        lc[g] = (uint8_t)col;
+      }
+    } else {
+      if (ncol > 255) throw Error(kErrUnsupported, "more than 255 cell colours");
+      for (int c = 0; c < ncol; ++c)
+        for (int32_t i = L.color_ptr[c]; i < L.color_ptr[c + 1]; ++i)
+          for (int b = 0; b < nb; ++b) lc[cu[(size_t)i * nb + b] & 0x7fffffff] = (uint8_t)c;
+    }
+    lv.lastc = upload(bud, lc);
+    L.lastc = lv.lastc.as<uint8_t>();
+  }
   lv.cell_u = upload(bud, cu);
   lv.cell_p = upload(bud, cp);
   lv.cell_f = upload(bud, cf);
@@ -226,6 +256,42 @@ void oplevel_vmult_cols(const OpLevel& lv, int prec, const void* X, void* Y, int
     vcopy_idx_cols<double>((double*)Y, (const double*)X, lv.constrained.as<int32_t>(), nc, n, ncols, s);
   else
     vcopy_idx_cols<float>((float*)Y, (const float*)X, lv.constrained.as<int32_t>(), nc, n, ncols, s);
+}
+
+void oplevel_smooth_step(const OpLevel& lv, int prec, const void* x, void* xout, void* d, const void* b,
+                         const void* dinv, void* t, double c1, double c2, cudaStream_t s) {
+  MFNS_CUDA(cudaMemsetAsync(t, 0, lv.n_dofs * esize(prec), s));
+  OpEpilogue e;
+  e.mode = 1;
+  e.b = b;
+  e.dinv = dinv;
+  e.d = d;
+  e.xout = xout;
+  e.c1 = c1;
+  e.c2 = c2;
+  op_apply_epi(lv.L, prec, x, t, e, s);
+  const int64_t nc = (int64_t)lv.constrained_host.size();
+  if (prec == 0)
+    vcheby_idx<double>((const double*)x, (double*)xout, (double*)d, (const double*)b, (const double*)dinv, c1, c2,
+                       lv.constrained.as<int32_t>(), nc, s);
+  else
+    vcheby_idx<float>((const float*)x, (float*)xout, (float*)d, (const float*)b, (const float*)dinv, (float)c1,
+                      (float)c2, lv.constrained.as<int32_t>(), nc, s);
+}
+
+void oplevel_residual_fused(const OpLevel& lv, int prec, const void* x, const void* b, void* r, void* t,
+                            cudaStream_t s) {
+  MFNS_CUDA(cudaMemsetAsync(t, 0, lv.n_dofs * esize(prec), s));
+  OpEpilogue e;
+  e.mode = 2;
+  e.b = b;
+  e.xout = r;
+  op_apply_epi(lv.L, prec, x, t, e, s);
+  const int64_t nc = (int64_t)lv.constrained_host.size();
+  if (prec == 0)
+    vsub_idx<double>((double*)r, (const double*)b, (const double*)x, lv.constrained.as<int32_t>(), nc, s);
+  else
+    vsub_idx<float>((float*)r, (const float*)b, (const float*)x, lv.constrained.as<int32_t>(), nc, s);
 }
 
 void oplevel_diag(const OpLevel& lv, int prec, void* diag, cudaStream_t s) {

@@ -30,6 +30,7 @@ struct OpLevel {
   std::vector<int32_t> perm;            // colour-sorted position -> forest cell id
   DevBuf cell_u, cell_p, cell_f, mask, hcell[2], frozen[2], fq[2];
   DevBuf gexp[2];                       // stabilised NS: explicit BDF field g (allocated on first use)
+  DevBuf lastc;                         // per main node: last colour touching it (fused epilogues)
   std::vector<int32_t> constrained_host;
   DevBuf constrained;                   // identity rows
   int64_t n_hang = 0;
@@ -49,6 +50,13 @@ struct OpLevel {
 void build_oplevel(OpLevel& lv, const Forest& f, int op, int k, const Physics& ph, Budget* bud);
 void oplevel_vmult(const OpLevel& lv, int prec, const void* src, void* dst, cudaStream_t s);
 void oplevel_diag(const OpLevel& lv, int prec, void* diag, cudaStream_t s);
+// One smoothing step with the update fused into the operator application (t: scratch):
+// d = c1 d + c2 dinv (b - A x), xout = x + d  (xout must not alias x)
+void oplevel_smooth_step(const OpLevel& lv, int prec, const void* x, void* xout, void* d, const void* b,
+                         const void* dinv, void* t, double c1, double c2, cudaStream_t s);
+// r = b - A x with the subtraction fused into the operator application (t: scratch)
+void oplevel_residual_fused(const OpLevel& lv, int prec, const void* x, const void* b, void* r, void* t,
+                            cudaStream_t s);
 // Y[:, j] = A X[:, j] for ncols columns of length n_dofs (column-major blocks)
 void oplevel_vmult_cols(const OpLevel& lv, int prec, const void* X, void* Y, int ncols, cudaStream_t s);
 void oplevel_distribute(const OpLevel& lv, int prec, void* x, cudaStream_t s);
@@ -106,6 +114,7 @@ struct Problem {
   int kind = 0, dim = 3, k = 2;
   Physics phys;
   int smoother = 0, smoother_degree = 5, mg_precision = 0, restart = 30, maxit = 500, cg_iterations = 10;
+  bool fused_smoother = false;          // fuse smoother update / V-cycle residual into the cell kernel
   double tol = 1e-8;
   Budget* bud = nullptr;
   std::unique_ptr<OpLevel> system;      // the problem's operator on the finest mesh

@@ -370,33 +370,45 @@ static void smooth_t(Problem& p, int level, int prec, const T* b, T* x, bool x_i
   const T* dinv = lv.dinv[prec].as<T>();
   T* d = w.d.as<T>();
   T* t = w.t.as<T>();
+  // with p.fused_smoother on a uniform level, steps with an operator application fuse the update
+  // into the cell kernel's last-colour scatter; the new iterate then goes to the other of two
+  // buffers (x and the level's residual vector, free while smoothing).  Otherwise the product
+  // is written out and a streaming kernel applies the update.
+  const bool fused = p.fused_smoother && lv.L.structured && lv.L.lastc;
+  T* cur = x;
+  auto step = [&](double c1, double c2) {
+    if (!fused) {
+      oplevel_vmult(lv, prec, x, t, s);
+      vcheby<T>(x, d, b, t, dinv, (T)c1, (T)c2, n, s);
+      return;
+    }
+    T* out = cur == x ? w.r.as<T>() : x;
+    oplevel_smooth_step(lv, prec, cur, out, d, b, dinv, t, c1, c2, s);
+    cur = out;
+  };
   const double lmax = lv.lmax, lmin = lmax / 20.0;
   if (p.smoother == 1) {  // Jacobi relaxation
     const T omega = (T)(2.0 / (lmin + lmax));
     for (int it = 0; it < degree; ++it) {
-      if (it == 0 && x_is_zero) {
+      if (it == 0 && x_is_zero)
         vcheby0<T>(x, d, b, dinv, omega, n, s);
-      } else {
-        oplevel_vmult(lv, prec, x, t, s);
-        vcheby<T>(x, d, b, t, dinv, T(0), omega, n, s);
-      }
+      else
+        step(0.0, (double)omega);
     }
-    return;
-  }
-  const double theta = 0.5 * (lmax + lmin), delta = 0.5 * (lmax - lmin), sigma = theta / delta;
-  double rho_old = 1.0 / sigma;
-  if (x_is_zero) {
-    vcheby0<T>(x, d, b, dinv, (T)(1.0 / theta), n, s);
   } else {
-    oplevel_vmult(lv, prec, x, t, s);
-    vcheby<T>(x, d, b, t, dinv, T(0), (T)(1.0 / theta), n, s);
+    const double theta = 0.5 * (lmax + lmin), delta = 0.5 * (lmax - lmin), sigma = theta / delta;
+    double rho_old = 1.0 / sigma;
+    if (x_is_zero)
+      vcheby0<T>(x, d, b, dinv, (T)(1.0 / theta), n, s);
+    else
+      step(0.0, 1.0 / theta);
+    for (int j = 1; j < degree; ++j) {
+      const double rho = 1.0 / (2.0 * sigma - rho_old);
+      step(rho * rho_old, 2.0 * rho / delta);
+      rho_old = rho;
+    }
   }
-  for (int j = 1; j < degree; ++j) {
-    oplevel_vmult(lv, prec, x, t, s);
-    const double rho = 1.0 / (2.0 * sigma - rho_old);
-    vcheby<T>(x, d, b, t, dinv, (T)(rho * rho_old), (T)(2.0 * rho / delta), n, s);
-    rho_old = rho;
-  }
+  if (cur != x) vcopy<T>(x, cur, n, s);
 }
 
 void smooth(Problem& p, int level, int prec, const void* b, void* x, bool x_is_zero, cudaStream_t s) {
@@ -428,8 +440,12 @@ static void vcycle_level(Problem& p, int prec, int l, const T* b, T* x, cudaStre
   Workspace& wc = p.ws[prec][l + 1];
   const int64_t n = lv.n_dofs;
   smooth_t<T>(p, l, prec, b, x, true, p.smoother_degree, s);
-  oplevel_vmult(lv, prec, x, w.t.get(), s);
-  vsub<T>(w.r.as<T>(), b, w.t.as<T>(), n, s);
+  if (p.fused_smoother && lv.L.structured && lv.L.lastc) {
+    oplevel_residual_fused(lv, prec, x, b, w.r.get(), w.t.get(), s);  // r = b - A x, fused
+  } else {
+    oplevel_vmult(lv, prec, x, w.t.get(), s);
+    vsub<T>(w.r.as<T>(), b, w.t.as<T>(), n, s);
+  }
   transfer_restrict(*p.transfers[l], lv, *p.levels[l + 1], prec, w.r.get(), wc.b.get(), s);
   vcycle_level<T>(p, prec, l + 1, wc.b.as<T>(), wc.x.as<T>(), s);
   transfer_prolongate_add(*p.transfers[l], lv, *p.levels[l + 1], prec, wc.x.get(), x, s);

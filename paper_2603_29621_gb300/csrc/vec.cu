@@ -29,6 +29,23 @@ __global__ void k_unit_cols(double* X, int64_t n, int64_t j0, int64_t nb) {
   }
 }
 template <typename T>
+__global__ void k_cheby_idx(const T* x, T* xout, T* d, const T* b, const T* dinv, T c1, T c2, const int32_t* idx,
+                            int64_t m) {
+  GRID_STRIDE(t, m) {
+    const int32_t i = idx[t];
+    const T di = c1 * d[i] + c2 * dinv[i] * (b[i] - x[i]);  // identity row: (A x)_i = x_i
+    d[i] = di;
+    xout[i] = x[i] + di;
+  }
+}
+template <typename T>
+__global__ void k_sub_idx(T* r, const T* b, const T* x, const int32_t* idx, int64_t m) {
+  GRID_STRIDE(t, m) {
+    const int32_t i = idx[t];
+    r[i] = b[i] - x[i];
+  }
+}
+template <typename T>
 __global__ void k_copy_idx_cols(T* Y, const T* X, const int32_t* idx, int64_t m, int64_t n, int64_t nb) {
   GRID_STRIDE(t, m * nb) {
     const int64_t j = t / m, i = idx[t - j * m];
@@ -206,6 +223,21 @@ template <typename T>
 void vcopy_idx_cols(T* Y, const T* X, const int32_t* idx, int64_t m, int64_t n, int64_t nb, cudaStream_t s) {
   LAUNCH(k_copy_idx_cols<T>, m * nb, s, Y, X, idx, m, n, nb);
 }
+template <typename T>
+void vcheby_idx(const T* x, T* xout, T* d, const T* b, const T* dinv, T c1, T c2, const int32_t* idx, int64_t m,
+                cudaStream_t s) {
+  LAUNCH(k_cheby_idx<T>, m, s, x, xout, d, b, dinv, c1, c2, idx, m);
+}
+template <typename T>
+void vsub_idx(T* r, const T* b, const T* x, const int32_t* idx, int64_t m, cudaStream_t s) {
+  LAUNCH(k_sub_idx<T>, m, s, r, b, x, idx, m);
+}
+template void vcheby_idx<double>(const double*, double*, double*, const double*, const double*, double, double,
+                                 const int32_t*, int64_t, cudaStream_t);
+template void vcheby_idx<float>(const float*, float*, float*, const float*, const float*, float, float,
+                                const int32_t*, int64_t, cudaStream_t);
+template void vsub_idx<double>(double*, const double*, const double*, const int32_t*, int64_t, cudaStream_t);
+template void vsub_idx<float>(float*, const float*, const float*, const int32_t*, int64_t, cudaStream_t);
 template void vcopy_idx_cols<double>(double*, const double*, const int32_t*, int64_t, int64_t, int64_t, cudaStream_t);
 template void vcopy_idx_cols<float>(float*, const float*, const int32_t*, int64_t, int64_t, int64_t, cudaStream_t);
 void vlincomb3(double* y, double a, const double* x1, double b, const double* x2, double c, const double* x3,

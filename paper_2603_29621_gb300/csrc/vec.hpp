@@ -21,6 +21,12 @@ template <typename T> void vscale(T* y, T a, int64_t n, cudaStream_t s);
 void vcast_d2f(float* y, const double* x, int64_t n, cudaStream_t s);
 // X (n x nb, column-major) = columns j0 .. j0+nb-1 of the identity
 void vunit_cols(double* X, int64_t n, int64_t j0, int64_t nb, cudaStream_t s);
+// constrained (identity) rows of a fused smoothing step / residual
+template <typename T>
+void vcheby_idx(const T* x, T* xout, T* d, const T* b, const T* dinv, T c1, T c2, const int32_t* idx, int64_t m,
+                cudaStream_t s);
+template <typename T>
+void vsub_idx(T* r, const T* b, const T* x, const int32_t* idx, int64_t m, cudaStream_t s);
 // Y[:, j][idx] = X[:, j][idx] for the nb columns of length n
 template <typename T>
 void vcopy_idx_cols(T* Y, const T* X, const int32_t* idx, int64_t m, int64_t n, int64_t nb, cudaStream_t s);

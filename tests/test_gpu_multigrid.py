@@ -92,12 +92,13 @@ def test_transfers_match_oracle(ctx, case):
         assert np.abs(got - exp).max() <= 1e-12 * np.abs(exp).max(), (l, np.abs(got - exp).max())
 
 
+@pytest.mark.parametrize("fused", [0, 1], ids=["separate", "fused"])
 @pytest.mark.parametrize("smoother", [("chebyshev", 3), ("chebyshev", 5), ("jacobi", 4)])
-@pytest.mark.parametrize("case", [HIER[0], HIER[3]], ids=lambda c: f"{c[0]}-{c[1]}d")
-def test_smoother_matches_oracle(ctx, case, smoother):
+@pytest.mark.parametrize("case", [HIER[0], HIER[3], HIER[2]], ids=lambda c: f"{c[0]}-{c[1]}d-{'ball' if c[3] else 'uni'}")
+def test_smoother_matches_oracle(ctx, case, smoother, fused):
     kind, dim, n, refine, k, phys = case
     prob = _gpu_problem(ctx, kind, dim, n, refine, k, lambda_max=1.0, smoother=1 if smoother[0] == "chebyshev" else 2,
-                        smoother_degree=smoother[1], **phys)
+                        smoother_degree=smoother[1], fused_smoother=fused, **phys)
     levels = solvers.hierarchy(_forest(dim, n, refine), kind, k, nu=phys["nu"], dt=phys.get("dt") or np.inf)
     lv = levels[0]
     lmax = 1.2 * solvers.power_lmax(lv.A, lv.dinv, iterations=50)
@@ -117,10 +118,12 @@ def test_smoother_matches_oracle(ctx, case, smoother):
         assert np.abs(got - exp).max() <= 1e-11 * np.abs(exp).max(), np.abs(got - exp).max()
 
 
+@pytest.mark.parametrize("fused", [0, 1], ids=["separate", "fused"])
 @pytest.mark.parametrize("case", HIER, ids=lambda c: f"{c[0]}-{c[1]}d-k{c[4]}-{'ball' if c[3] else 'uni'}")
-def test_vcycle_matches_oracle(ctx, case):
+def test_vcycle_matches_oracle(ctx, case, fused):
     kind, dim, n, refine, k, phys = case
-    prob = _gpu_problem(ctx, kind, dim, n, refine, k, lambda_max=1.0, smoother=1, smoother_degree=3, **phys)
+    prob = _gpu_problem(ctx, kind, dim, n, refine, k, lambda_max=1.0, smoother=1, smoother_degree=3,
+                        fused_smoother=fused, **phys)
     levels = solvers.hierarchy(_forest(dim, n, refine), kind, k, nu=phys["nu"], dt=phys.get("dt") or np.inf)
     lmax = [1.2 * solvers.power_lmax(lv.A, lv.dinv, iterations=50) for lv in levels[:-1]]
     for l, lm in enumerate(lmax):
