@@ -287,9 +287,22 @@ int mfns_solve_begin(mfns_problem* p, const void* b, void* x, void* stream);
 /* One round: every listed problem whose solve is still running performs one FGMRES iteration
  * (Section 3).  The device work of all of them is enqueued first, each on its own stream, then
  * each is completed on the host (Givens rotation, and at the end of a restart cycle the update
- * of x and the true residual).  running[i] (optional) is set to 1 while problem i iterates.
- * Problems are independent: the result of each is the same alone and in any batch. */
+ * of x and the true residual).  The preconditioners of the running STAB_NS / STOKES_A problems
+ * on uniform meshes (two or more) run as one batched V-cycle (see mfns_batch_vcycle) replayed
+ * from a CUDA graph that is captured when the set of such problems changes.  running[i]
+ * (optional) is set to 1 while problem i iterates.  Problems are independent: the result of
+ * each is the same alone and in any batch. */
 int mfns_batch_step(mfns_problem** problems, int n, int* running);
+/* One V-cycle (zero initial guess) for each of n problems of one context, batched: the
+ * operator applications of all problems whose current multigrid levels share dimension, degree,
+ * operator, precision and smoother run as one launch per level and colour over the cells of all
+ * of them, each block reading its problem from a descriptor table (uneven sizes share launches).
+ * Results equal n separate mfns_vcycle calls (bitwise: the per-cell arithmetic and its order are
+ * those of a single-problem launch).  b[i], x[i]: device vectors of problem i in `precision`.
+ * Problems: STAB_NS or STOKES_A on uniform meshes, fused_smoother = 0 (else
+ * MFNS_ERR_UNSUPPORTED).  mfns_batch_step uses the same batching, captured into a CUDA graph, for
+ * the preconditioners of such problems.  Synchronises `stream`. */
+int mfns_batch_vcycle(mfns_problem** problems, int n, int precision, void* const* b, void* const* x, void* stream);
 /* Iterations, relative residual and convergence of the last (or current) solve of p. */
 int mfns_solve_status(const mfns_problem* p, mfns_solve_info* info);
 

@@ -90,6 +90,8 @@ _SIGS = {
     "mfns_solve_begin": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "mfns_batch_step": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.POINTER(C.c_int)]),
     "mfns_solve_status": (C.c_int, [C.c_void_p, C.POINTER(SolveInfo)]),
+    "mfns_batch_vcycle": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.c_int, C.POINTER(C.c_void_p),
+                                    C.POINTER(C.c_void_p), C.c_void_p]),
 }
 
 EXPORTED = tuple(_SIGS)

@@ -250,3 +250,14 @@ def batch_step(problems):
     run = (C.c_int * n)()
     L.check(L.load().mfns_batch_step(arr, n, run))
     return [bool(v) for v in run]
+
+
+def batch_vcycle(problems, bs, xs, stream=None):
+    """One batched V-cycle (zero start) per problem: x_i = V-cycle_i(b_i), shared launches per level."""
+    n = len(problems)
+    prec = L.FP64 if bs[0].dtype == torch.float64 else L.FP32
+    arr = (C.c_void_p * n)(*[p.h for p in problems])
+    bp = (C.c_void_p * n)(*[_ptr(b).value for b in bs])
+    xp = (C.c_void_p * n)(*[_ptr(x).value for x in xs])
+    L.check(L.load().mfns_batch_vcycle(arr, n, prec, bp, xp, _stream(stream)))
+    return xs

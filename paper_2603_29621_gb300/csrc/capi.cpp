@@ -1,6 +1,7 @@
 // C ABI (include/mfns.h): argument checking, error translation, dispatch.
 #include "../../include/mfns.h"
 
+#include <algorithm>
 #include <chrono>
 #include <cstring>
 #include <string>
@@ -26,7 +27,12 @@ namespace mfns {
 int capi_fail(int code, const char* msg) { return fail(code, msg); }
 }  // namespace mfns
 
-#define API_BEGIN try {
+// Every entry first consumes a runtime error left pending in this thread by another component of
+// the process (the runtime is shared, e.g. with PyTorch): the library checks each of its own calls
+// when it fails, and the post-launch checks must not report someone else's error.
+#define API_BEGIN \
+  try {           \
+    (void)cudaGetLastError();
 #define API_END                                                      \
   }                                                                  \
   catch (const Error& e) { return fail(e.code, e.what()); }          \
@@ -35,6 +41,24 @@ int capi_fail(int code, const char* msg) { return fail(code, msg); }
   return MFNS_OK;
 
 static cudaStream_t S(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+BatchRound* batch_round(mfns_ctx* ctx, const std::vector<Problem*>& ps) {
+  std::vector<std::pair<uint64_t, uint64_t>> key;
+  for (Problem* p : ps) key.push_back({p->uid, p->graph_epoch});
+  if (!ctx->round) {
+    ctx->round = std::make_unique<BatchRound>();
+    MFNS_CUDA(cudaStreamCreateWithFlags(&ctx->round->stream, cudaStreamNonBlocking));
+    MFNS_CUDA(cudaEventCreateWithFlags(&ctx->round->done, cudaEventDisableTiming));
+  }
+  BatchRound& r = *ctx->round;
+  if (!r.plan || r.key != key) {
+    MFNS_CUDA(cudaStreamSynchronize(r.stream));
+    r.plan.reset();
+    r.plan = make_batch_precond(ps);
+    r.key = key;
+  }
+  return &r;
+}
 
 static bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
@@ -384,8 +408,29 @@ int mfns_batch_step(mfns_problem** ps, int n, int* running) {
   for (int i = 0; i < n; ++i)
     if (!ps[i]) return fail(MFNS_ERR_ARG, "null problem in batch");
   if (n > 0) MFNS_CUDA(cudaSetDevice(ps[0]->ctx->device));
-  // enqueue the device work of every active solve (each on its own stream), then complete them
-  for (int i = 0; i < n; ++i) krylov_enqueue(*ps[i]->p);
+  // the preconditioners of the active problems that use one V-cycle on uniform levels run as one
+  // batched, graph-captured V-cycle (operator applications of all of them in shared launches per
+  // level and colour); every other problem, and all the rest of each step, on its own stream
+  std::vector<Problem*> bat;
+  for (int i = 0; i < n; ++i) {
+    Problem& P = *ps[i]->p;
+    if (P.kry.active && batchable(P) && ps[i]->ctx == ps[0]->ctx) bat.push_back(&P);
+  }
+  if (bat.size() < 2) bat.clear();
+  BatchRound* br = bat.empty() ? nullptr : batch_round(ps[0]->ctx, bat);
+  for (int i = 0; i < n; ++i) {
+    Problem& P = *ps[i]->p;
+    if (br && P.kry.active && std::find(bat.begin(), bat.end(), &P) != bat.end())
+      krylov_enqueue_pre(P);
+    else
+      krylov_enqueue(P);
+  }
+  if (br) {
+    for (Problem* P : bat) MFNS_CUDA(cudaStreamWaitEvent(br->stream, P->ev_step, 0));
+    batch_precond_launch(*br->plan, br->stream);
+    MFNS_CUDA(cudaEventRecord(br->done, br->stream));
+    for (Problem* P : bat) krylov_enqueue_post(*P, br->done);
+  }
   for (int i = 0; i < n; ++i) {
     Problem& P = *ps[i]->p;
     bool run = false;
@@ -395,6 +440,29 @@ int mfns_batch_step(mfns_problem** ps, int n, int* running) {
     }
     if (running) running[i] = run ? 1 : 0;
   }
+  API_END
+}
+
+int mfns_batch_vcycle(mfns_problem** ps, int n, int precision, void* const* b, void* const* x, void* stream) {
+  API_BEGIN
+  if (!ps || n <= 0 || !b || !x || (precision != MFNS_FP64 && precision != MFNS_FP32))
+    return fail(MFNS_ERR_ARG, "bad arguments");
+  std::vector<Problem*> pp;
+  std::vector<const void*> bb;
+  std::vector<void*> xx;
+  for (int i = 0; i < n; ++i) {
+    if (!ps[i] || !b[i] || !x[i]) return fail(MFNS_ERR_ARG, "null problem or vector in batch");
+    if (ps[i]->ctx != ps[0]->ctx) return fail(MFNS_ERR_ARG, "problems of different contexts");
+    if (!batchable(*ps[i]->p))
+      return fail(MFNS_ERR_UNSUPPORTED, "batched V-cycle: one-V-cycle problems on uniform levels only");
+    pp.push_back(ps[i]->p.get());
+    bb.push_back(b[i]);
+    xx.push_back(x[i]);
+  }
+  MFNS_CUDA(cudaSetDevice(ps[0]->ctx->device));
+  BatchVcyclePtr B = make_batch_vcycle(pp, precision, bb, xx, nullptr);
+  batch_vcycle(*B, S(stream));
+  MFNS_CUDA(cudaStreamSynchronize(S(stream)));  // the plan's tables are freed on return
   API_END
 }
 

@@ -1,14 +1,34 @@
 // Definitions of the opaque C-ABI handles (shared by the C-ABI translation units).
 #pragma once
 #include <memory>
+#include <utility>
+#include <vector>
 
 #include "../../include/mfns.h"
 #include "problem.hpp"
 
+// The batched preconditioner of the last batched round and its stream; rebuilt when the set
+// of batched problems (or one of their captured graphs) changes.
+struct BatchRound {
+  std::vector<std::pair<uint64_t, uint64_t>> key;  // (uid, graph epoch) of the members, in order
+  mfns::BatchPrecondPtr plan;
+  cudaStream_t stream = nullptr;
+  cudaEvent_t done = nullptr;
+  ~BatchRound() {
+    plan.reset();
+    if (done) cudaEventDestroy(done);
+    if (stream) cudaStreamDestroy(stream);
+  }
+};
+
 struct mfns_ctx {
   int device = 0;
   mfns::Budget budget;
+  std::unique_ptr<BatchRound> round;
 };
+
+// plan of a batched round over `ps` (cached in the context while the set is unchanged)
+BatchRound* batch_round(mfns_ctx* ctx, const std::vector<mfns::Problem*>& ps);
 struct mfns_mesh {
   mfns_ctx* ctx = nullptr;
   mfns::Forest forest;

@@ -20,11 +20,17 @@ struct Error : std::runtime_error {
   Error(int c, const std::string& m) : std::runtime_error(m), code(c) {}
 };
 
-#define MFNS_CUDA(expr)                                                                      \
-  do {                                                                                       \
-    cudaError_t e_ = (expr);                                                                 \
-    if (e_ != cudaSuccess)                                                                   \
-      throw ::mfns::Error(::mfns::kErrCuda, std::string(#expr) + ": " + cudaGetErrorString(e_)); \
+#ifdef __FILE_NAME__
+#define MFNS_SRC_FILE __FILE_NAME__
+#else
+#define MFNS_SRC_FILE __FILE__
+#endif
+#define MFNS_CUDA(expr)                                                                                   \
+  do {                                                                                                    \
+    cudaError_t e_ = (expr);                                                                              \
+    if (e_ != cudaSuccess)                                                                                \
+      throw ::mfns::Error(::mfns::kErrCuda, std::string(MFNS_SRC_FILE ":") + std::to_string(__LINE__) + \
+                                                " " #expr ": " + cudaGetErrorString(e_));                 \
   } while (0)
 
 // Per-context HBM accounting: every library allocation is charged against the budget

@@ -75,6 +75,7 @@ extern "C" int mfns_smooth_noalloc(mfns_problem* p, int level, int precision, co
                                    void* stream) {
   using namespace mfns;
   try {
+    (void)cudaGetLastError();  // a pending error of another component of the process is not ours
     if (!p || level < 0 || level >= (int)p->p->levels.size() || !b || !x || (precision != 0 && precision != 1))
       return capi_fail(kErrArg, "bad arguments");
     const int64_t n = p->p->levels[level]->n_dofs;

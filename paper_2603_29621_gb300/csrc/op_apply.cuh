@@ -76,7 +76,10 @@ struct FrozenPoint {
 };
 
 // EPI: the fused smoother / residual epilogue is compiled in (structured launches only).
-template <int DIM, int K, int OP, typename T, bool STRUCT, bool DIAG, int FQ = 0, bool EPI = false>
+// MULTI: one launch over the cells of several problems (structured, plain products); each block
+// reads its problem's fields from args.probs.
+template <int DIM, int K, int OP, typename T, bool STRUCT, bool DIAG, int FQ = 0, bool EPI = false,
+          bool MULTI = false>
 __global__ void __launch_bounds__(kOpWarps * 32, OpMinBlocks<DIM, K, OP, T>::value)
 op_kernel(const OpArgs<T, K + 1, K + 1, (OP == OP_STOKES ? K : K + 1)> args) {
   constexpr int Q = K + 1, N = K + 1, NP = OP == OP_STOKES ? K : K + 1;
@@ -88,8 +91,51 @@ op_kernel(const OpArgs<T, K + 1, K + 1, (OP == OP_STOKES ? K : K + 1)> args) {
   constexpr int BUF = TM::BUF;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* smem = reinterpret_cast<T*>(smem_raw);
-  const T* srcp = args.src + (int64_t)blockIdx.y * args.col_stride;
-  T* dstp = args.dst + (int64_t)blockIdx.y * args.col_stride;
+  // per-problem fields: kernel parameters, or the descriptor of the problem owning this block
+  const T* srcp;
+  T* dstp;
+  const T *frozen, *gexp;
+  T* fqd;
+  int nmesh;
+  int64_t color_offset, p_offset, bx;
+  T hs, nu_, cm_, dt_inv_, div_sign_, cf_[7];
+  if constexpr (MULTI) {
+    static_assert(STRUCT && !DIAG && !EPI, "multi-problem launches: structured products only");
+    const ProbArgs<T>* pa = args.probs + args.block_pid[blockIdx.x];
+    srcp = pa->src;
+    dstp = pa->dst;
+    frozen = pa->frozen;
+    gexp = pa->gexp;
+    fqd = pa->fq;
+    nmesh = pa->n;
+    color_offset = pa->color_offset;
+    p_offset = pa->p_offset;
+    bx = (int64_t)blockIdx.x - pa->first_block;
+    hs = pa->h;
+    nu_ = pa->nu;
+    cm_ = pa->cm;
+    dt_inv_ = pa->dt_inv;
+    div_sign_ = pa->div_sign;
+#pragma unroll
+    for (int i = 0; i < 7; ++i) cf_[i] = pa->cf[i];
+  } else {
+    srcp = args.src + (int64_t)blockIdx.y * args.col_stride;
+    dstp = args.dst + (int64_t)blockIdx.y * args.col_stride;
+    frozen = args.frozen;
+    gexp = args.gexp;
+    fqd = args.fq;
+    nmesh = args.n;
+    color_offset = args.color_offset;
+    p_offset = args.p_offset;
+    bx = (int64_t)blockIdx.x;
+    hs = args.h;
+    nu_ = args.nu;
+    cm_ = args.cm;
+    dt_inv_ = args.dt_inv;
+    div_sign_ = args.div_sign;
+#pragma unroll
+    for (int i = 0; i < 7; ++i) cf_[i] = args.cf[i];
+  }
 
   const int lane = lane_id();
   const int warp = threadIdx.x >> 5;
@@ -115,9 +161,9 @@ op_kernel(const OpArgs<T, K + 1, K + 1, (OP == OP_STOKES ? K : K + 1)> args) {
   int cc[3] = {0, 0, 0};
   int64_t cellpos;  // position in the colour-major enumeration (precomputed frozen data)
   {
-    const int64_t t = (int64_t)blockIdx.x * ((blockDim.x >> 5) * TM::CPW) + warp * TM::CPW + (lane_active ? team : 0);
+    const int64_t t = bx * ((blockDim.x >> 5) * TM::CPW) + warp * TM::CPW + (lane_active ? team : 0);
     if (STRUCT) {
-      const int n = args.n;
+      const int n = nmesh;
       int m[3], bits[3];
       int64_t total = 1;
       for (int d = 0; d < 3; ++d) {
@@ -131,7 +177,7 @@ op_kernel(const OpArgs<T, K + 1, K + 1, (OP == OP_STOKES ? K : K + 1)> args) {
       cc[1] = 2 * (int)((tt / m[0]) % m[1]) + bits[1];
       cc[2] = DIM == 3 ? 2 * (int)(tt / ((int64_t)m[0] * m[1])) + bits[2] : 0;
       cell = cc[0] + (int64_t)n * (cc[1] + (int64_t)n * cc[2]);
-      cellpos = args.color_offset + tt;
+      cellpos = color_offset + tt;
     } else {
       const int64_t c = args.cell_begin + t;
       valid = lane_active && c < args.cell_end;
@@ -139,7 +185,7 @@ op_kernel(const OpArgs<T, K + 1, K + 1, (OP == OP_STOKES ? K : K + 1)> args) {
       cellpos = cell;
     }
   }
-  const T h = STRUCT ? args.h : args.hcell[cell];
+  const T h = STRUCT ? hs : args.hcell[cell];
   const uint32_t mask = STRUCT ? 0u : args.mask[cell];
   // warp-uniform: every team of the warp takes the constraint path if one needs it
   // (a team with mask 0 leaves its values unchanged), so all __syncwarp calls match
@@ -162,8 +208,8 @@ op_kernel(const OpArgs<T, K + 1, K + 1, (OP == OP_STOKES ? K : K + 1)> args) {
   for (int c = 0; c < N; ++c) {
     const int slot = DIM == 3 ? (c * N + tj_n) * N + ti_n : c * N + ti_n;
     if (STRUCT) {
-      node[c] = DIM == 3 ? structured_node<DIM, K>(args.n, cc, ti_n, tj_n, c, bnd[c])
-                         : structured_node<DIM, K>(args.n, cc, ti_n, c, 0, bnd[c]);
+      node[c] = DIM == 3 ? structured_node<DIM, K>(nmesh, cc, ti_n, tj_n, c, bnd[c])
+                         : structured_node<DIM, K>(nmesh, cc, ti_n, c, 0, bnd[c]);
       fnode[c] = node[c];
     } else {
       const int32_t v = args.cell_u[cell * NB + slot];
@@ -179,8 +225,8 @@ op_kernel(const OpArgs<T, K + 1, K + 1, (OP == OP_STOKES ? K : K + 1)> args) {
       const int slot = DIM == 3 ? (c * NP + tj_p) * NP + ti_p : c * NP + ti_p;
       if (STRUCT) {
         bool dummy;
-        pnode[c] = DIM == 3 ? structured_node<DIM, K - 1>(args.n, cc, ti_p, tj_p, c, dummy)
-                            : structured_node<DIM, K - 1>(args.n, cc, ti_p, c, 0, dummy);
+        pnode[c] = DIM == 3 ? structured_node<DIM, K - 1>(nmesh, cc, ti_p, tj_p, c, dummy)
+                            : structured_node<DIM, K - 1>(nmesh, cc, ti_p, c, 0, dummy);
       } else {
         pnode[c] = args.cell_p[cell * NBP + slot];
       }
@@ -188,7 +234,7 @@ op_kernel(const OpArgs<T, K + 1, K + 1, (OP == OP_STOKES ? K : K + 1)> args) {
   }
 
   const auto& tab = args.tab;
-  const T nu = args.nu;
+  const T nu = nu_;
 
   // weights of the lane's column
   T jxw[Q];
@@ -242,7 +288,7 @@ op_kernel(const OpArgs<T, K + 1, K + 1, (OP == OP_STOKES ? K : K + 1)> args) {
     }
     if (Tr::SPLIT_P) {
 #pragma unroll
-      for (int c = 0; c < NP; ++c) pv0[c] = ownp ? srcp[args.p_offset + pnode[c]] : T(0);
+      for (int c = 0; c < NP; ++c) pv0[c] = ownp ? srcp[p_offset + pnode[c]] : T(0);
     }
   }
 
@@ -257,7 +303,7 @@ op_kernel(const OpArgs<T, K + 1, K + 1, (OP == OP_STOKES ? K : K + 1)> args) {
     // copy overlaps the interpolation of the trial fields and is awaited before first use
     constexpr int CB = TM::template stage_stride_bytes<T>(sizeof(T) * FQB) % 16 == 0 ? 16 : 8;
     constexpr int CH = FQB * (int)sizeof(T) / CB;  // chunks per cell
-    const char* gsrc = reinterpret_cast<const char*>(args.fq + (size_t)cellpos * FQB);
+    const char* gsrc = reinterpret_cast<const char*>(fqd + (size_t)cellpos * FQB);
     if (lane_active) {
       const unsigned sdst = (unsigned)__cvta_generic_to_shared(fqs);
       for (int c = tid; c < CH; c += TM::TPC) {
@@ -275,16 +321,16 @@ op_kernel(const OpArgs<T, K + 1, K + 1, (OP == OP_STOKES ? K : K + 1)> args) {
     for (int c = 0; c < N; ++c) {
       if constexpr (NU == 4) {
         if constexpr (sizeof(T) == 4) {
-          const float4 v = own ? *reinterpret_cast<const float4*>(args.frozen + fnode[c] * 4) : make_float4(0, 0, 0, 0);
+          const float4 v = own ? *reinterpret_cast<const float4*>(frozen + fnode[c] * 4) : make_float4(0, 0, 0, 0);
           fz[0][c] = v.x; fz[1][c] = v.y; fz[2][c] = v.z; fz[3][c] = v.w;
         } else {
-          const double2 v0 = own ? *reinterpret_cast<const double2*>(args.frozen + fnode[c] * 4) : make_double2(0, 0);
-          const double2 v1 = own ? *reinterpret_cast<const double2*>(args.frozen + fnode[c] * 4 + 2) : make_double2(0, 0);
+          const double2 v0 = own ? *reinterpret_cast<const double2*>(frozen + fnode[c] * 4) : make_double2(0, 0);
+          const double2 v1 = own ? *reinterpret_cast<const double2*>(frozen + fnode[c] * 4 + 2) : make_double2(0, 0);
           fz[0][c] = v0.x; fz[1][c] = v0.y; fz[2][c] = v1.x; fz[3][c] = v1.y;
         }
       } else {
 #pragma unroll
-        for (int f = 0; f <= DIM; ++f) fz[f][c] = own ? args.frozen[fnode[c] * NU + f] : T(0);
+        for (int f = 0; f <= DIM; ++f) fz[f][c] = own ? frozen[fnode[c] * NU + f] : T(0);
       }
     }
 #pragma unroll
@@ -321,15 +367,15 @@ op_kernel(const OpArgs<T, K + 1, K + 1, (OP == OP_STOKES ? K : K + 1)> args) {
     for (int i = 0; i < DIM; ++i)
 #pragma unroll
       for (int l = 0; l < Q; ++l) tq[i][l] = 0;
-    if (args.gexp) {  // kernel parameter: uniform over the warp
+    if (gexp) {  // kernel parameter: uniform over the warp
 #pragma unroll
       for (int i = 0; i < DIM; ++i) {
         T gz[N], gv[Q];
 #pragma unroll
-        for (int c = 0; c < N; ++c) gz[c] = own ? args.gexp[fnode[c] * NU + i] : T(0);
+        for (int c = 0; c < N; ++c) gz[c] = own ? gexp[fnode[c] * NU + i] : T(0);
         values<DIM, Q, N, T>(gz, gv, buf0, ti, tj, tab.S);
 #pragma unroll
-        for (int l = 0; l < Q; ++l) tq[i][l] = args.cm * Ub[i][l] + gv[l];
+        for (int l = 0; l < Q; ++l) tq[i][l] = cm_ * Ub[i][l] + gv[l];
       }
     }
 #pragma unroll
@@ -343,13 +389,13 @@ op_kernel(const OpArgs<T, K + 1, K + 1, (OP == OP_STOKES ? K : K + 1)> args) {
         Rb[i][l] = s;
         un2 += Ub[i][l] * Ub[i][l];
       }
-      const T a = T(2) * args.dt_inv, b2 = T(4) * un2 * inv_h * inv_h, c = T(12) * nu * inv_h * inv_h;
+      const T a = T(2) * dt_inv_, b2 = T(4) * un2 * inv_h * inv_h, c = T(12) * nu * inv_h * inv_h;
       tau[l] = T(1) / sqrt(a * a + b2 + c * c);
     }
     if constexpr (FQ == 2) {
       if (valid) {
         constexpr int B = FrozenPoint<DIM>::template block<T>(Q);
-        T* fp = args.fq + (size_t)cellpos * B + tid;
+        T* fp = fqd + (size_t)cellpos * B + tid;
         auto at = [&](int l, int k) -> T& { return fp[(l * NFQ + k) * TM::TPC]; };
 #pragma unroll
         for (int l = 0; l < Q; ++l) {
@@ -465,7 +511,7 @@ op_kernel(const OpArgs<T, K + 1, K + 1, (OP == OP_STOKES ? K : K + 1)> args) {
       {
         T c0[Q], cg[DIM][Q];
 #pragma unroll
-        for (int l = 0; l < Q; ++l) c0[l] = args.div_sign * div[l] * jxw[l];
+        for (int l = 0; l < Q; ++l) c0[l] = div_sign_ * div[l] * jxw[l];
         integrate<DIM, Q, NP, true, false, T>(c0, cg, rp, buf1, buf2, ti, tj, tab.Sp, tab.D);
       }
     } else if constexpr (FQ == 3) {  // OP_STAB_NS, nonlinear residual at the frozen state
@@ -491,7 +537,7 @@ op_kernel(const OpArgs<T, K + 1, K + 1, (OP == OP_STOKES ? K : K + 1)> args) {
           T dv = 0;
 #pragma unroll
           for (int j = 0; j < DIM; ++j) dv += Gb[j][j][l];
-          c0[l] = args.div_sign * dv * jxw[l];
+          c0[l] = div_sign_ * dv * jxw[l];
 #pragma unroll
           for (int d = 0; d < DIM; ++d) cg[d][l] = tau[l] * Rb[d][l] * jxw[l] * inv_h;
         }
@@ -520,9 +566,9 @@ op_kernel(const OpArgs<T, K + 1, K + 1, (OP == OP_STOKES ? K : K + 1)> args) {
         if constexpr (FQ == 1) return fqs[(l * NFQ + NFQ - 1) * TM::TPC + tid];
         else return tau[l];
       };
-      const T cfm = args.cf[0], cfc = args.cf[1], cfn = args.cf[2], cfs = args.cf[3], cfsn = args.cf[4],
-              cfp = args.cf[5], cfl = args.cf[6];
-      const T cm = args.cm;
+      const T cfm = cf_[0], cfc = cf_[1], cfn = cf_[2], cfs = cf_[3], cfsn = cf_[4],
+              cfp = cf_[5], cfl = cf_[6];
+      const T cm = cm_;
       T Rl[DIM][Q], vc[DIM][Q], gc[DIM][DIM][Q], dv[Q];
 #pragma unroll
       for (int l = 0; l < Q; ++l) {
@@ -595,7 +641,7 @@ op_kernel(const OpArgs<T, K + 1, K + 1, (OP == OP_STOKES ? K : K + 1)> args) {
         T c0[Q], cg[DIM][Q];
 #pragma unroll
         for (int l = 0; l < Q; ++l) {
-          c0[l] = args.div_sign * dv[l] * jxw[l];
+          c0[l] = div_sign_ * dv[l] * jxw[l];
 #pragma unroll
           for (int d = 0; d < DIM; ++d) cg[d][l] = cfp * TAU(l) * Rl[d][l] * jxw[l] * inv_h;
         }
@@ -689,7 +735,7 @@ op_kernel(const OpArgs<T, K + 1, K + 1, (OP == OP_STOKES ? K : K + 1)> args) {
       }
       if (Tr::SPLIT_P && ownp) {
 #pragma unroll
-        for (int c = 0; c < NP; ++c) dstp[args.p_offset + pnode[c]] += rp[c];
+        for (int c = 0; c < NP; ++c) dstp[p_offset + pnode[c]] += rp[c];
       }
     }
   }
@@ -711,7 +757,7 @@ op_kernel(const OpArgs<T, K + 1, K + 1, (OP == OP_STOKES ? K : K + 1)> args) {
       for (int c = 0; c < NP; ++c) {
         const int slot = DIM == 3 ? (c * NP + tj_p) * NP + ti_p : c * NP + ti_p;
         const int ps = NU * NB + slot;
-        if (ps >= pass_begin && ps < pass_end) dstp[args.p_offset + pnode[c]] += daccp[c];
+        if (ps >= pass_begin && ps < pass_end) dstp[p_offset + pnode[c]] += daccp[c];
       }
     }
   }

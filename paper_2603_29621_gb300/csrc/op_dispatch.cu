@@ -17,7 +17,9 @@ constexpr int kOpWarpsDefault = 4;
   extern template void op_launch<DIM, K, OP, double>(const OpLaunch&, const double*, double*, bool, cudaStream_t, \
                                                      int, int, int64_t, const OpEpilogue*);                      \
   extern template void op_launch<DIM, K, OP, float>(const OpLaunch&, const float*, float*, bool, cudaStream_t, int, \
-                                                    int, int64_t, const OpEpilogue*);
+                                                    int, int64_t, const OpEpilogue*);                            \
+  extern template void op_launch_multi<DIM, K, OP, double>(const OpLaunch&, int, const MultiColour&, cudaStream_t); \
+  extern template void op_launch_multi<DIM, K, OP, float>(const OpLaunch&, int, const MultiColour&, cudaStream_t);
 
 MFNS_DECL(3, 1, OP_STAB_NS) MFNS_DECL(3, 2, OP_STAB_NS) MFNS_DECL(3, 3, OP_STAB_NS)
 MFNS_DECL(2, 1, OP_STAB_NS) MFNS_DECL(2, 2, OP_STAB_NS) MFNS_DECL(2, 3, OP_STAB_NS) MFNS_DECL(2, 4, OP_STAB_NS)
@@ -156,6 +158,22 @@ void op_apply(const OpLaunch& L, int prec, const void* src, void* dst, bool diag
     dispatch<double>(L, static_cast<const double*>(src), static_cast<double*>(dst), diag, s);
   else
     dispatch<float>(L, static_cast<const float*>(src), static_cast<float*>(dst), diag, s);
+}
+
+void op_apply_multi(const OpLaunch& L, int prec, int color, const MultiColour& mc, cudaStream_t s) {
+#define MFNS_CASE(DIM, K, OP)                                           \
+  if (L.dim == DIM && L.k == K && L.op == OP) {                         \
+    if (prec == 0) return op_launch_multi<DIM, K, OP, double>(L, color, mc, s); \
+    return op_launch_multi<DIM, K, OP, float>(L, color, mc, s);         \
+  }
+  MFNS_CASE(3, 1, OP_STAB_NS) MFNS_CASE(3, 2, OP_STAB_NS) MFNS_CASE(3, 3, OP_STAB_NS)
+  MFNS_CASE(2, 1, OP_STAB_NS) MFNS_CASE(2, 2, OP_STAB_NS) MFNS_CASE(2, 3, OP_STAB_NS) MFNS_CASE(2, 4, OP_STAB_NS)
+  MFNS_CASE(3, 1, OP_STOKES_A) MFNS_CASE(3, 2, OP_STOKES_A) MFNS_CASE(3, 3, OP_STOKES_A) MFNS_CASE(3, 4, OP_STOKES_A)
+  MFNS_CASE(2, 1, OP_STOKES_A) MFNS_CASE(2, 2, OP_STOKES_A) MFNS_CASE(2, 3, OP_STOKES_A) MFNS_CASE(2, 4, OP_STOKES_A)
+  MFNS_CASE(2, 1, OP_PMASS) MFNS_CASE(2, 2, OP_PMASS) MFNS_CASE(2, 3, OP_PMASS)
+  MFNS_CASE(3, 1, OP_PMASS) MFNS_CASE(3, 2, OP_PMASS) MFNS_CASE(3, 3, OP_PMASS)
+#undef MFNS_CASE
+  throw Error(kErrUnsupported, "multi-problem launch: unsupported (dim, degree, operator)");
 }
 
 void op_apply_epi(const OpLaunch& L, int prec, const void* src, void* dst, const OpEpilogue& epi, cudaStream_t s) {

@@ -46,6 +46,23 @@ struct Tables {
   T Pp[2][NP][NP];  // same for the pressure degree
 };
 
+// Per-problem fields of one colour launch over several problems (structured cells): the
+// descriptor table of a multi-problem launch (blocks [first_block, next problem's first_block)).
+template <typename T>
+struct ProbArgs {
+  const T* src;
+  T* dst;
+  const T* frozen;
+  const T* gexp;
+  T* fq;
+  int64_t color_offset;  // cells of this problem's earlier colours
+  int64_t p_offset;
+  int64_t first_block;
+  int32_t n;
+  T h, nu, cm, dt_inv, div_sign;
+  T cf[7];
+};
+
 template <typename T, int Q, int N, int NP>
 struct OpArgs {
   Tables<T, Q, N, NP> tab;
@@ -85,6 +102,9 @@ struct OpArgs {
   T* ed;
   T* exout;
   T ec1, ec2;
+  // multi-problem launch: descriptor of the problem owning each block
+  const ProbArgs<T>* probs;
+  const int32_t* block_pid;
 };
 
 // ------------------------------------------------------------ small helpers

@@ -177,10 +177,54 @@ void op_launch(const OpLaunch& L, const T* src, T* dst, bool diag, cudaStream_t 
   }
 }
 
+template <int DIM, int K, int OP, typename T>
+void op_launch_multi(const OpLaunch& L, int color, const MultiColour& mc, cudaStream_t s) {
+  constexpr int Q = K + 1, N = K + 1, NP = OP == OP_STOKES ? K : K + 1;
+  if constexpr (OpTraits<OP, DIM>::SPLIT_P) {
+    throw Error(kErrArg, "multi-problem launch: Taylor--Hood system operator");
+  } else {
+    if (!L.structured) throw Error(kErrArg, "multi-problem launch: non-uniform level");
+    if (mc.nblocks == 0) return;
+    OpArgs<T, Q, N, NP> a{};
+    if (L.Q != Q || L.N != N || L.NP != NP) throw Error(kErrArg, "operator tables do not match the degree");
+    build_tables(L, a.tab);
+    const int prec = sizeof(T) == 8 ? 0 : 1;
+    a.color = color;
+    a.probs = static_cast<const ProbArgs<T>*>(mc.probs);
+    a.block_pid = mc.block_pid;
+    const int warps = L.warps[prec] > 0 ? L.warps[prec] : kOpWarps;
+    bool staged = false;
+    if constexpr (OP == OP_STAB_NS) staged = L.fq[prec] != nullptr;
+    if (staged) {
+      static std::atomic<uint64_t> attr_done{0};
+      int dev = 0;
+      MFNS_CUDA(cudaGetDevice(&dev));
+      const uint64_t bit = 1ull << (dev & 63);
+      if constexpr (OP == OP_STAB_NS) {
+        if (!(attr_done.load() & bit)) {
+          MFNS_CUDA(cudaFuncSetAttribute(op_kernel<DIM, K, OP, T, true, false, 1, false, true>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)op_smem_bytes<DIM, K, OP, T>(kOpWarps, true)));
+          attr_done.fetch_or(bit);
+        }
+      }
+      if constexpr (OP == OP_STAB_NS)
+        op_kernel<DIM, K, OP, T, true, false, 1, false, true>
+            <<<mc.nblocks, warps * 32, op_smem_bytes<DIM, K, OP, T>(warps, true), s>>>(a);
+    } else {
+      op_kernel<DIM, K, OP, T, true, false, 0, false, true>
+          <<<mc.nblocks, warps * 32, op_smem_bytes<DIM, K, OP, T>(warps, false), s>>>(a);
+    }
+    MFNS_CUDA(cudaGetLastError());
+  }
+}
+
 #define MFNS_INSTANTIATE_OP(DIM, K, OP)                                                                        \
   template void op_launch<DIM, K, OP, double>(const OpLaunch&, const double*, double*, bool, cudaStream_t, int, int, \
                                                int64_t, const OpEpilogue*);                                        \
   template void op_launch<DIM, K, OP, float>(const OpLaunch&, const float*, float*, bool, cudaStream_t, int, int,    \
-                                              int64_t, const OpEpilogue*);
+                                              int64_t, const OpEpilogue*);                                         \
+  template void op_launch_multi<DIM, K, OP, double>(const OpLaunch&, int, const MultiColour&, cudaStream_t);       \
+  template void op_launch_multi<DIM, K, OP, float>(const OpLaunch&, int, const MultiColour&, cudaStream_t);
 
 }  // namespace mfns

@@ -82,6 +82,19 @@ template <int DIM, int K, int OP, typename T>
 void op_launch(const OpLaunch& L, const T* src, T* dst, bool diag, cudaStream_t s, int fq_mode = -1, int ncols = 1,
                int64_t col_stride = 0, const OpEpilogue* epi = nullptr);
 
+// One colour of a multi-problem launch (structured cells, plain products): `probs` is the device
+// descriptor table (one ProbArgs of the launch precision per problem), `block_pid` the problem of
+// every block, `nblocks` the blocks of all problems.  `L` (any member) provides the 1D tables and
+// the block size; all members share (dim, k, op, precision) and the frozen-data mode.
+struct MultiColour {
+  const void* probs = nullptr;
+  const int32_t* block_pid = nullptr;
+  unsigned nblocks = 0;
+};
+template <int DIM, int K, int OP, typename T>
+void op_launch_multi(const OpLaunch& L, int color, const MultiColour& mc, cudaStream_t s);
+void op_apply_multi(const OpLaunch& L, int prec, int color, const MultiColour& mc, cudaStream_t s);
+
 // Runtime dispatch over (dim, k, op, precision); prec 0 = fp64, 1 = fp32.
 void op_apply(const OpLaunch& L, int prec, const void* src, void* dst, bool diag, cudaStream_t s);
 // dst (zeroed by the caller) receives partial sums; the epilogue writes the fused result

@@ -110,7 +110,22 @@ struct Krylov {
   cudaStream_t stream = nullptr;
 };
 
+// Multi-problem operator application (batch.cu): one launch per colour over several problems'
+// structured levels sharing (dim, degree, operator, precision, frozen-data mode, block size).
+struct MultiOp;
+MultiOp* multi_op_create(const std::vector<const OpLevel*>& lv, const std::vector<const void*>& src,
+                         const std::vector<void*>& dst, int prec, Budget* bud);
+void multi_op_destroy(MultiOp* m);
+// dst_i = A_i src_i for every member (constrained rows dst = src)
+void multi_vmult(const MultiOp& m, cudaStream_t s);
+struct MultiOpDel {
+  void operator()(MultiOp* m) const { multi_op_destroy(m); }
+};
+using MultiOpPtr = std::unique_ptr<MultiOp, MultiOpDel>;
+
 struct Problem {
+  uint64_t uid = 0;                     // process-unique id (batch plans are keyed by it)
+  uint64_t graph_epoch = 0;             // incremented whenever the captured graphs are dropped
   int kind = 0, dim = 3, k = 2;
   Physics phys;
   int smoother = 0, smoother_degree = 5, mg_precision = 0, restart = 30, maxit = 500, cg_iterations = 10;
@@ -145,6 +160,7 @@ struct Problem {
   double* hh_host = nullptr;            // pinned: Gram--Schmidt coefficients of the last step
   // Newton / BDF (stabilised NS; allocated on first use): explicit field, residual, increment
   DevBuf nt_g, nt_F, nt_d;
+  cudaEvent_t ev_step = nullptr;        // batched rounds: the step's input is in pc_in
   double st_dt = -1.0, st_alpha = -1.0;  // dt, alpha and explicit-field use of the last set_state
   bool st_g = false;
   size_t bytes = 0;
@@ -200,5 +216,33 @@ int fgmres_solve(Problem& p, const double* b, double* x, double* relres, bool* c
 void krylov_begin(Problem& p, const double* b, double* x, cudaStream_t s);
 void krylov_enqueue(Problem& p);
 bool krylov_complete(Problem& p);
+// The same step split around its preconditioner application, for rounds in which the
+// preconditioners of several problems run as one batched, graph-captured V-cycle (D6):
+// pre = the step's vector into p.pc_in (event p.ev_step recorded), post = the rest of the step,
+// ordered after `ready` (recorded once the batched preconditioner has written p.pc_out).
+void krylov_enqueue_pre(Problem& p);
+void krylov_enqueue_post(Problem& p, cudaEvent_t ready);
+// Problems whose preconditioner is one V-cycle on uniform levels (batched rounds)
+bool batchable(const Problem& p);
+// One V-cycle for each of several problems, in lock-step over the levels: at every level, the
+// operator applications of all problems whose levels share (dim, degree, operator, precision,
+// smoother) run as one launch per colour.  Results equal those of the problems' own V-cycles.
+struct BatchVcycle;
+struct BatchVcycleDel {
+  void operator()(BatchVcycle* b) const;
+};
+using BatchVcyclePtr = std::unique_ptr<BatchVcycle, BatchVcycleDel>;
+BatchVcyclePtr make_batch_vcycle(const std::vector<Problem*>& ps, int prec, const std::vector<const void*>& b,
+                                 const std::vector<void*>& x, Budget* bud);
+void batch_vcycle(BatchVcycle& B, cudaStream_t s);
+// The preconditioners of the listed (batchable) problems in one captured CUDA graph: input
+// p.pc_in, output p.pc_out of every problem.
+struct BatchPrecond;
+struct BatchPrecondDel {
+  void operator()(BatchPrecond* b) const;
+};
+using BatchPrecondPtr = std::unique_ptr<BatchPrecond, BatchPrecondDel>;
+BatchPrecondPtr make_batch_precond(const std::vector<Problem*>& ps);
+void batch_precond_launch(BatchPrecond& B, cudaStream_t s);
 
 }  // namespace mfns

@@ -9,6 +9,10 @@
 // coarse system is larger than 4096 unknowns.  FGMRES(m) with classical
 // Gram--Schmidt applied twice (Section 3 "We solve the Stokes system with FGMRES").
 #include <algorithm>
+#include <atomic>
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -40,11 +44,15 @@ Problem::~Problem() {
   invalidate_graphs(*this);
   if (cap_stream) cudaStreamDestroy(cap_stream);
   if (hh_host) cudaFreeHost(hh_host);
+  if (ev_step) cudaEventDestroy(ev_step);
 }
+
+static std::atomic<uint64_t> g_problem_uid{0};
 
 std::unique_ptr<Problem> build_problem(const Forest& f, int kind, int k, const Physics& ph, int mg_order,
                                        int coarse_stop_n, Budget* bud) {
   auto p = std::make_unique<Problem>();
+  p->uid = ++g_problem_uid;
   p->kind = kind;
   p->dim = f.dim;
   p->k = k;
@@ -543,6 +551,7 @@ static void precondition(Problem& p, const double* v, double* z, cudaStream_t s)
 }
 
 void invalidate_graphs(Problem& p) {
+  ++p.graph_epoch;
   if (p.pc_graph) cudaGraphExecDestroy(p.pc_graph);
   p.pc_graph = nullptr;
   for (int i = 0; i < 2; ++i) {
@@ -634,6 +643,29 @@ void krylov_begin(Problem& p, const double* b_in, double* x, cudaStream_t s) {
   start_cycle(p, K.bnorm);
 }
 
+// Device work of one Arnoldi step split around the preconditioner (batched rounds).
+void krylov_enqueue_pre(Problem& p) {
+  Krylov& K = p.kry;
+  if (!K.active) return;
+  const int64_t n = sys_of(p).n_dofs;
+  MFNS_CUDA(cudaMemcpyAsync(p.pc_in.get(), p.V.as<double>() + (size_t)K.j * n, n * 8, cudaMemcpyDeviceToDevice,
+                            K.stream));
+  if (!p.ev_step) MFNS_CUDA(cudaEventCreateWithFlags(&p.ev_step, cudaEventDisableTiming));
+  MFNS_CUDA(cudaEventRecord(p.ev_step, K.stream));
+}
+
+static void krylov_after_precondition(Problem& p, double* zj);
+
+void krylov_enqueue_post(Problem& p, cudaEvent_t ready) {
+  Krylov& K = p.kry;
+  if (!K.active) return;
+  const int64_t n = sys_of(p).n_dofs;
+  double* zj = p.Z.as<double>() + (size_t)K.j * n;
+  MFNS_CUDA(cudaStreamWaitEvent(K.stream, ready, 0));
+  MFNS_CUDA(cudaMemcpyAsync(zj, p.pc_out.get(), n * 8, cudaMemcpyDeviceToDevice, K.stream));
+  krylov_after_precondition(p, zj);
+}
+
 // Device work of one Arnoldi step (asynchronous on the problem's stream).
 void krylov_enqueue(Problem& p) {
   Krylov& K = p.kry;
@@ -644,9 +676,18 @@ void krylov_enqueue(Problem& p) {
   const int j = K.j;
   double* V = p.V.as<double>();
   double* zj = p.Z.as<double>() + (size_t)j * n;
+  precondition(p, V + (size_t)j * n, zj, s);
+  krylov_after_precondition(p, zj);
+}
+
+static void krylov_after_precondition(Problem& p, double* zj) {
+  Krylov& K = p.kry;
+  OpLevel& S = sys_of(p);
+  const int64_t n = S.n_dofs;
+  cudaStream_t s = K.stream;
+  const int j = K.j;
   const double** Vp = (const double**)p.ptrV.as<const double*>();
   double* w = p.w.as<double>();
-  precondition(p, V + (size_t)j * n, zj, s);
   project_pressure<double>(S, zj, p.scal.as<double>(), p.part.as<double>(), s);
   oplevel_vmult(S, 0, zj, w, s);
   double* hd = p.hvec.as<double>();
@@ -878,5 +919,225 @@ NewtonResult bdf_step(Problem& p, const NewtonParams& np, const double* u_n, con
   }
   return res;
 }
+
+// ---------------------------------------------------------------------- batched V-cycles (D6)
+bool batchable(const Problem& p) {
+  if ((p.kind != 1 && p.kind != 2) || p.fused_smoother || !p.use_graphs) return false;
+  for (auto& l : p.levels)
+    if (!l->L.structured) return false;
+  return true;
+}
+
+struct BatchGroup {
+  std::vector<int> mem;  // problem indices
+  MultiOpPtr op;         // x -> t at this level for every member
+};
+
+struct BatchVcycle {
+  int prec = 1;
+  std::vector<Problem*> ps;
+  std::vector<const void*> b0;
+  std::vector<void*> x0;
+  int steps = 0;                               // max levels over the problems
+  std::vector<std::vector<BatchGroup>> groups;  // [level][group]
+};
+
+void BatchVcycleDel::operator()(BatchVcycle* b) const { delete b; }
+
+BatchVcyclePtr make_batch_vcycle(const std::vector<Problem*>& ps, int prec, const std::vector<const void*>& b,
+                                 const std::vector<void*>& x, Budget* bud) {
+  BatchVcyclePtr B(new BatchVcycle);
+  B->prec = prec;
+  B->ps = ps;
+  B->b0 = b;
+  B->x0 = x;
+  for (Problem* p : ps) {
+    if (!batchable(*p)) throw Error(kErrArg, "batched V-cycle: unsupported problem");
+    B->steps = std::max<int>(B->steps, (int)p->levels.size());
+  }
+  B->groups.resize(B->steps);
+  for (int t = 0; t < B->steps; ++t) {
+    // members: problems for which level t is not the coarse level; grouped by what one launch shares
+    std::map<std::tuple<int, int, int, bool, int, int, int>, std::vector<int>> key;
+    for (int i = 0; i < (int)ps.size(); ++i) {
+      const Problem& p = *ps[i];
+      if (t >= (int)p.levels.size() - 1) continue;
+      const OpLaunch& L = p.levels[t]->L;
+      key[{L.dim, L.k, L.op, L.fq[prec] != nullptr, L.warps[prec], p.smoother, p.smoother_degree}].push_back(i);
+    }
+    for (auto& kv : key) {
+      BatchGroup g;
+      g.mem = kv.second;
+      std::vector<const OpLevel*> lv;
+      std::vector<const void*> src;
+      std::vector<void*> dst;
+      for (int i : g.mem) {
+        Problem& p = *ps[i];
+        lv.push_back(p.levels[t].get());
+        src.push_back(t == 0 ? x[i] : p.ws[prec][t].x.get());
+        dst.push_back(p.ws[prec][t].t.get());
+      }
+      g.op = MultiOpPtr(multi_op_create(lv, src, dst, prec, bud));
+      B->groups[t].push_back(std::move(g));
+    }
+  }
+  return B;
+}
+
+// One smoothing sweep of every member of a group: the same steps as smooth_t (without fusion),
+// the operator applications of all members in one multi-problem launch per colour.
+template <typename T>
+static void batch_smooth(BatchVcycle& B, int t, BatchGroup& G, bool x_is_zero, cudaStream_t s) {
+  const int prec = B.prec;
+  const Problem& p0 = *B.ps[G.mem[0]];
+  const int degree = p0.smoother_degree;
+  struct M {
+    T *x, *d, *t;
+    const T *b, *dinv;
+    int64_t n;
+    double theta, delta, sigma, rho_old;
+    T omega;
+  };
+  std::vector<M> ms;
+  for (int i : G.mem) {
+    Problem& p = *B.ps[i];
+    OpLevel& lv = *p.levels[t];
+    Workspace& w = p.ws[prec][t];
+    M m;
+    m.x = t == 0 ? (T*)B.x0[i] : w.x.as<T>();
+    m.b = t == 0 ? (const T*)B.b0[i] : w.b.as<T>();
+    m.d = w.d.as<T>();
+    m.t = w.t.as<T>();
+    m.dinv = lv.dinv[prec].as<T>();
+    m.n = lv.n_dofs;
+    const double lmax = lv.lmax, lmin = lmax / 20.0;
+    m.omega = (T)(2.0 / (lmin + lmax));
+    m.theta = 0.5 * (lmax + lmin);
+    m.delta = 0.5 * (lmax - lmin);
+    m.sigma = m.theta / m.delta;
+    m.rho_old = 1.0 / m.sigma;
+    ms.push_back(m);
+  }
+  if (p0.smoother == 1) {  // Jacobi relaxation
+    for (int it = 0; it < degree; ++it) {
+      if (it == 0 && x_is_zero) {
+        for (M& m : ms) vcheby0<T>(m.x, m.d, m.b, m.dinv, m.omega, m.n, s);
+      } else {
+        multi_vmult(*G.op, s);
+        for (M& m : ms) vcheby<T>(m.x, m.d, m.b, m.t, m.dinv, T(0), (T)(double)m.omega, m.n, s);
+      }
+    }
+    return;
+  }
+  if (x_is_zero) {
+    for (M& m : ms) vcheby0<T>(m.x, m.d, m.b, m.dinv, (T)(1.0 / m.theta), m.n, s);
+  } else {
+    multi_vmult(*G.op, s);
+    for (M& m : ms) vcheby<T>(m.x, m.d, m.b, m.t, m.dinv, T(0), (T)(1.0 / m.theta), m.n, s);
+  }
+  for (int j = 1; j < degree; ++j) {
+    multi_vmult(*G.op, s);
+    for (M& m : ms) {
+      const double rho = 1.0 / (2.0 * m.sigma - m.rho_old);
+      vcheby<T>(m.x, m.d, m.b, m.t, m.dinv, (T)(rho * m.rho_old), (T)(2.0 * rho / m.delta), m.n, s);
+      m.rho_old = rho;
+    }
+  }
+}
+
+template <typename T>
+static void batch_vcycle_t(BatchVcycle& B, cudaStream_t s) {
+  const int prec = B.prec;
+  const int np = (int)B.ps.size();
+  auto bv = [&](int i, int l) -> T* { return l == 0 ? (T*)B.b0[i] : B.ps[i]->ws[prec][l].b.as<T>(); };
+  auto xv = [&](int i, int l) -> T* { return l == 0 ? (T*)B.x0[i] : B.ps[i]->ws[prec][l].x.as<T>(); };
+  auto nl = [&](int i) { return (int)B.ps[i]->levels.size(); };
+  // descent: pre-smoothing, residual and restriction per level; coarse solves where a hierarchy ends
+  for (int t = 0; t < B.steps; ++t) {
+    for (int i = 0; i < np; ++i)
+      if (t == nl(i) - 1) coarse_solve<T>(*B.ps[i], prec, bv(i, t), xv(i, t), s);
+    for (BatchGroup& g : B.groups[t]) batch_smooth<T>(B, t, g, true, s);
+    for (BatchGroup& g : B.groups[t]) {
+      multi_vmult(*g.op, s);
+      for (int i : g.mem) {
+        Problem& p = *B.ps[i];
+        Workspace& w = p.ws[prec][t];
+        vsub<T>(w.r.as<T>(), bv(i, t), w.t.as<T>(), p.levels[t]->n_dofs, s);
+        transfer_restrict(*p.transfers[t], *p.levels[t], *p.levels[t + 1], prec, w.r.get(),
+                          p.ws[prec][t + 1].b.get(), s);
+      }
+    }
+  }
+  // ascent: prolongation and post-smoothing
+  for (int t = B.steps - 2; t >= 0; --t) {
+    for (BatchGroup& g : B.groups[t]) {
+      for (int i : g.mem) {
+        Problem& p = *B.ps[i];
+        transfer_prolongate_add(*p.transfers[t], *p.levels[t], *p.levels[t + 1], prec, p.ws[prec][t + 1].x.get(),
+                                xv(i, t), s);
+      }
+      batch_smooth<T>(B, t, g, false, s);
+    }
+  }
+}
+
+void batch_vcycle(BatchVcycle& B, cudaStream_t s) {
+  if (B.prec == 0)
+    batch_vcycle_t<double>(B, s);
+  else
+    batch_vcycle_t<float>(B, s);
+}
+
+struct BatchPrecond {
+  std::vector<Problem*> ps;
+  BatchVcyclePtr vc[2];
+  cudaStream_t cap = nullptr;
+  cudaGraphExec_t graph = nullptr;
+  ~BatchPrecond() {
+    if (graph) cudaGraphExecDestroy(graph);
+    if (cap) cudaStreamDestroy(cap);
+  }
+};
+
+void BatchPrecondDel::operator()(BatchPrecond* b) const { delete b; }
+
+// the preconditioners of precondition_body for every member, the V-cycles batched per precision
+static void batch_precond_body(BatchPrecond& B, cudaStream_t s) {
+  for (Problem* p : B.ps)
+    if (p->mg_precision == 1) vcast_d2f(p->mg_b32.as<float>(), p->pc_in.as<double>(), sys_of(*p).n_dofs, s);
+  for (int prec = 0; prec < 2; ++prec)
+    if (B.vc[prec]) batch_vcycle(*B.vc[prec], s);
+  for (Problem* p : B.ps)
+    if (p->mg_precision == 1) vcast_f2d(p->pc_out.as<double>(), p->mg_x32.as<float>(), sys_of(*p).n_dofs, s);
+}
+
+BatchPrecondPtr make_batch_precond(const std::vector<Problem*>& ps) {
+  BatchPrecondPtr B(new BatchPrecond);
+  B->ps = ps;
+  for (int prec = 0; prec < 2; ++prec) {
+    std::vector<Problem*> mem;
+    std::vector<const void*> b;
+    std::vector<void*> x;
+    for (Problem* p : ps) {
+      if (p->mg_precision != prec) continue;
+      mem.push_back(p);
+      b.push_back(prec == 1 ? p->mg_b32.get() : p->pc_in.get());
+      x.push_back(prec == 1 ? p->mg_x32.get() : p->pc_out.get());
+    }
+    if (!mem.empty()) B->vc[prec] = make_batch_vcycle(mem, prec, b, x, nullptr);
+  }
+  MFNS_CUDA(cudaStreamCreateWithFlags(&B->cap, cudaStreamNonBlocking));
+  std::vector<std::unique_ptr<TimerPause>> pause;
+  for (Problem* p : ps) pause.push_back(std::make_unique<TimerPause>(*p));
+  MFNS_CUDA(cudaStreamBeginCapture(B->cap, cudaStreamCaptureModeThreadLocal));
+  batch_precond_body(*B, B->cap);
+  cudaGraph_t g;
+  MFNS_CUDA(cudaStreamEndCapture(B->cap, &g));
+  MFNS_CUDA(cudaGraphInstantiate(&B->graph, g, 0));
+  MFNS_CUDA(cudaGraphDestroy(g));
+  return B;
+}
+
+void batch_precond_launch(BatchPrecond& B, cudaStream_t s) { MFNS_CUDA(cudaGraphLaunch(B.graph, s)); }
 
 }  // namespace mfns
