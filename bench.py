@@ -230,6 +230,17 @@ def serving_section(api, L, torch, count):
         diffs.append(float(np.linalg.norm(x32 - x64) / np.linalg.norm(x64)))
     out["fp32_vs_fp64_max_rel_diff"] = max(diffs) if diffs else None
     out["fp32_vs_fp64_throughput"] = out["fp32_mg"]["solves_per_s"] / max(out["fp64_mg"]["solves_per_s"], 1e-12)
+    # saturated burst (all requests at once, n in 8..32): batched preconditioners (one V-cycle launch
+    # per level and colour over all active problems) against every problem on its own stream
+    burst = serve.poisson_stream(max(8, count // 2), rate=1e4, seed=4, n_range=(8, 32))
+    for name, on in (("burst_fp32_batched", True), ("burst_fp32_per_problem", False)):
+        ctx.set_batching(on)
+        srv = serve.Server(ctx, max_active=16, mg_precision=L.FP32)
+        out[name] = srv.run(burst, realtime=True)[1]
+        srv.close()
+    ctx.set_batching(True)
+    out["burst_batched_speedup"] = (out["burst_fp32_batched"]["solves_per_s"]
+                                    / max(out["burst_fp32_per_problem"]["solves_per_s"], 1e-12))
     ctx.close()
     return out
 

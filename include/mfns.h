@@ -163,6 +163,9 @@ typedef struct {
 /* ---- context --------------------------------------------------------------------------- */
 /* device: CUDA ordinal; hbm_budget_bytes: 0 = unlimited.  Errors: ARG, CUDA. */
 int mfns_ctx_create(int device, size_t hbm_budget_bytes, mfns_ctx** out);
+/* 1 (default): mfns_batch_step runs the preconditioners of eligible problems as one batched
+ * V-cycle; 0: every problem's preconditioner on its own stream (for comparison). */
+int mfns_ctx_set_batching(mfns_ctx* ctx, int enable);
 int mfns_ctx_destroy(mfns_ctx* ctx);
 /* bytes currently charged to the context */
 int mfns_ctx_memory(const mfns_ctx* ctx, size_t* used, size_t* peak);

@@ -60,6 +60,7 @@ class NewtonInfo(C.Structure):
 _SIGS = {
     "mfns_ctx_create": (C.c_int, [C.c_int, C.c_size_t, C.POINTER(C.c_void_p)]),
     "mfns_ctx_destroy": (C.c_int, [C.c_void_p]),
+    "mfns_ctx_set_batching": (C.c_int, [C.c_void_p, C.c_int]),
     "mfns_ctx_memory": (C.c_int, [C.c_void_p, C.POINTER(C.c_size_t), C.POINTER(C.c_size_t)]),
     "mfns_last_error": (C.c_char_p, []),
     "mfns_mesh_uniform": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.POINTER(C.c_void_p)]),

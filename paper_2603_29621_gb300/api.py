@@ -43,6 +43,10 @@ class Context:
         self.h = h
         self.device = device
 
+    def set_batching(self, enable):
+        """Batched preconditioners in mfns_batch_step (default on)."""
+        L.check(self.lib.mfns_ctx_set_batching(self.h, int(bool(enable))))
+
     def memory(self):
         u, p = C.c_size_t(), C.c_size_t()
         L.check(self.lib.mfns_ctx_memory(self.h, C.byref(u), C.byref(p)))

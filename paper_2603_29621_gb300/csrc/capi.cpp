@@ -80,6 +80,12 @@ int mfns_ctx_create(int device, size_t hbm_budget_bytes, mfns_ctx** out) {
   API_END
 }
 
+int mfns_ctx_set_batching(mfns_ctx* ctx, int enable) {
+  if (!ctx) return fail(MFNS_ERR_ARG, "ctx is null");
+  ctx->batching = enable != 0;
+  return MFNS_OK;
+}
+
 int mfns_ctx_destroy(mfns_ctx* ctx) {
   delete ctx;
   return MFNS_OK;
@@ -416,7 +422,7 @@ int mfns_batch_step(mfns_problem** ps, int n, int* running) {
     Problem& P = *ps[i]->p;
     if (P.kry.active && batchable(P) && ps[i]->ctx == ps[0]->ctx) bat.push_back(&P);
   }
-  if (bat.size() < 2) bat.clear();
+  if (bat.size() < 2 || !ps[0]->ctx->batching) bat.clear();
   BatchRound* br = bat.empty() ? nullptr : batch_round(ps[0]->ctx, bat);
   for (int i = 0; i < n; ++i) {
     Problem& P = *ps[i]->p;

@@ -24,6 +24,7 @@ struct BatchRound {
 struct mfns_ctx {
   int device = 0;
   mfns::Budget budget;
+  bool batching = true;  // mfns_batch_step batches eligible preconditioners
   std::unique_ptr<BatchRound> round;
 };
 
