@@ -257,8 +257,9 @@ int mfns_solve(mfns_problem* p, const void* b, void* x, mfns_solve_info* info, v
  * multigrid level (coarse-node evaluation of the fine FE function); each level's stored point
  * values, smoother diagonal (evaluated in FP32 whatever the multigrid precision: it only scales
  * the smoother's correction) and the coarse inverse are recomputed.  The call synchronises
- * `stream`.
- * Returns MFNS_ERR_UNSUPPORTED for other kinds or a hierarchy with refined meshes. */
+ * `stream`.  On refined meshes the hanging-node entries of the state and of g are set from their
+ * masters first; a coarse level receives the fine function evaluated at its nodes cell by cell
+ * (through the children of each coarse cell).  Returns MFNS_ERR_UNSUPPORTED for other kinds. */
 int mfns_set_state(mfns_problem* p, double dt, double alpha, const void* state, const void* explicit_field,
                    void* stream);
 /* dst = F(state), the nonlinear residual of the SUPG/PSPG BDF discretisation at the state of the

@@ -84,12 +84,17 @@ struct Transfer {
   DevBuf child_code;                    // per child: child bits, or 8 = same cell
   std::vector<double> E;                // h: P_half[2][NF][NC]; p: S[NF][NC]
   std::vector<double> Pc;               // coarse hanging interpolation P[2][NC][NC]
+  DevBuf own_c;                         // state interpolation: owner flag per coarse (cell, slot)
 };
 void build_transfer(Transfer& t, const OpLevel& fine, const OpLevel& coarse, Budget* bud);
 bool build_separable(SepTransfer& t, const OpLevel& fine, const OpLevel& coarse, Budget* bud);
 void sep_restrict(const SepTransfer& t, int prec, const void* fine, void* coarse, cudaStream_t s);
 // coarse = the fine FE function evaluated at the coarse nodes (all components, no masking; fp64)
 void sep_interpolate(const SepTransfer& t, const double* fine, double* coarse, cudaStream_t s);
+// the same for any transfer (separable passes, or per coarse cell through its children); the fine
+// values must have consistent hanging-node entries; coarse hanging entries are left to the caller
+void cell_interpolate(Transfer& t, const OpLevel& fine, const OpLevel& coarse, const double* uf, double* uc,
+                      Budget* bud, cudaStream_t s);
 void sep_prolongate_add(const SepTransfer& t, int prec, const void* coarse, void* fine, cudaStream_t s);
 void transfer_prolongate_add(const Transfer& t, const OpLevel& fine, const OpLevel& coarse, int prec,
                              const void* xc, void* xf, cudaStream_t s);
@@ -184,7 +189,7 @@ void autotune(Problem& p, cudaStream_t s);
 void setup_coarse(Problem& p, cudaStream_t s);
 // Stabilised NS (Section 5): set dt, the BDF coefficient alpha, the frozen state U and the explicit
 // field g (null: none) on the finest level, carry them down the hierarchy by interpolation and
-// refresh every level's point data, diagonal and the coarse inverse.  Uniform meshes only.
+// refresh every level's point data, diagonal and the coarse inverse (uniform and refined meshes).
 void set_state(Problem& p, double dt, double alpha, const double* U, const double* g, cudaStream_t s);
 // the two halves of set_state: the finest level only (enough for the residual and the Jacobian),
 // and the rest of the hierarchy with the diagonals and the coarse inverse

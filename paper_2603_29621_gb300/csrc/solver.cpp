@@ -223,11 +223,15 @@ void estimate_lambda(Problem& p, cudaStream_t s) {
   }
   // lambda_max of D^{-1} A per level: Arnoldi (classical Gram--Schmidt twice) in FP64 from a
   // seeded random start; the estimate is the spectral radius of the m x m Hessenberg matrix
-  // (its Ritz values), times 1.2.
+  // (its Ritz values), times 1.2 for the Chebyshev smoother.  The relaxation smoother takes
+  // twice the spectral radius: the stabilised operator's D^{-1} A has complex eigenvalues near
+  // its spectral radius, where omega = 2 / (lmin + 1.2 rho) over-relaxes (Q1Q1 with viscosity-
+  // dominated tau stagnated, in the oracle as on the GPU); 2 rho makes omega ~ 0.95 / rho.
+  const double factor = p.smoother == 1 ? 2.0 : 1.2;
   for (size_t l = 0; l < p.levels.size(); ++l) {
     OpLevel& lv = *p.levels[l];
     if (lv.lmax > 0) continue;
-    lv.lmax = 1.2 * arnoldi_spectral_radius(p, lv, s);
+    lv.lmax = factor * arnoldi_spectral_radius(p, lv, s);
   }
 }
 
@@ -780,8 +784,6 @@ int fgmres_solve(Problem& p, const double* b_in, double* x, double* relres, bool
 // ---------------------------------------------------------------------- Newton / BDF (Section 5)
 void set_state_fine(Problem& p, double dt, double alpha, const double* U, const double* g, cudaStream_t s) {
   if (p.kind != 2) throw Error(kErrUnsupported, "set_state: stabilised NS problems only");
-  for (auto& t : p.transfers)
-    if (!t->separable) throw Error(kErrUnsupported, "set_state: the hierarchy must consist of uniform meshes");
   if (!(dt > 0.0) || !(alpha > 0.0)) throw Error(kErrArg, "set_state: dt and alpha must be positive");
   const bool has_g = g != nullptr;
   for (auto& lvp : p.levels) {
@@ -802,10 +804,14 @@ void set_state_fine(Problem& p, double dt, double alpha, const double* U, const 
   p.st_g = has_g;
   p.phys.dt = dt;
   OpLevel& f0 = *p.levels[0];
+  // hanging-node entries of the state follow their masters (the kernels read the state at the true
+  // nodes of every cell)
   MFNS_CUDA(cudaMemcpyAsync(f0.frozen[0].get(), U, f0.n_main_dofs * 8, cudaMemcpyDeviceToDevice, s));
+  oplevel_distribute(f0, 0, f0.frozen[0].get(), s);
   vcast_d2f(f0.frozen[1].as<float>(), f0.frozen[0].as<double>(), f0.n_main_dofs, s);
   if (has_g) {
     MFNS_CUDA(cudaMemcpyAsync(f0.gexp[0].get(), g, f0.n_main_dofs * 8, cudaMemcpyDeviceToDevice, s));
+    oplevel_distribute(f0, 0, f0.gexp[0].get(), s);
     vcast_d2f(f0.gexp[1].as<float>(), f0.gexp[0].as<double>(), f0.n_main_dofs, s);
   }
   for (int prec = 0; prec < 2; ++prec) op_precompute_frozen(f0.L, prec, s);
@@ -815,12 +821,15 @@ void refresh_preconditioner(Problem& p, cudaStream_t s) {
   // the finest state (and g) interpolated level by level down the hierarchy
   const bool has_g = p.st_g;
   for (size_t l = 0; l + 1 < p.levels.size(); ++l) {
-    const SepTransfer& t = p.transfers[l]->sep;
+    Transfer& t = *p.transfers[l];
+    OpLevel& f = *p.levels[l];
     OpLevel& c = *p.levels[l + 1];
-    sep_interpolate(t, p.levels[l]->frozen[0].as<double>(), c.frozen[0].as<double>(), s);
+    cell_interpolate(t, f, c, f.frozen[0].as<double>(), c.frozen[0].as<double>(), p.bud, s);
+    oplevel_distribute(c, 0, c.frozen[0].get(), s);
     vcast_d2f(c.frozen[1].as<float>(), c.frozen[0].as<double>(), c.n_main_dofs, s);
     if (has_g) {
-      sep_interpolate(t, p.levels[l]->gexp[0].as<double>(), c.gexp[0].as<double>(), s);
+      cell_interpolate(t, f, c, f.gexp[0].as<double>(), c.gexp[0].as<double>(), p.bud, s);
+      oplevel_distribute(c, 0, c.gexp[0].get(), s);
       vcast_d2f(c.gexp[1].as<float>(), c.gexp[0].as<double>(), c.n_main_dofs, s);
     }
     for (int prec = 0; prec < 2; ++prec) op_precompute_frozen(c.L, prec, s);
@@ -886,6 +895,7 @@ NewtonResult bdf_step(Problem& p, const NewtonParams& np, const double* u_n, con
     vcopy_idx<double>(d, u, lv.constrained.as<int32_t>(), ncon, s);
     MFNS_CUDA(cudaMemcpyAsync(u, d, n * 8, cudaMemcpyDeviceToDevice, s));
   }
+  oplevel_distribute(lv, 0, u, s);  // hanging entries of the start follow their masters
   NewtonResult res;
   const double tol_saved = p.tol;
   for (int it = 0;; ++it) {
@@ -916,6 +926,7 @@ NewtonResult bdf_step(Problem& p, const NewtonParams& np, const double* u_n, con
     }
     p.tol = tol_saved;
     vaxpy<double>(u, 1.0, d, n, s);
+    oplevel_distribute(lv, 0, u, s);  // hanging entries follow their masters
   }
   return res;
 }

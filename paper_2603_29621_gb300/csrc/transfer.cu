@@ -392,6 +392,97 @@ static void dispatch_transfer(const Transfer& t, const OpLevel& fine, const OpLe
   throw Error(kErrUnsupported, "transfer not instantiated for this (dim, degrees, components)");
 }
 
+// ---- coarse nodal values of a fine finite-element function (Newton states on refined meshes)
+struct GllPair {
+  double xf[8], xc[8];
+};
+
+__device__ __forceinline__ double lagrange_at(const double* x, int n, int m, double e) {
+  double v = 1.0;
+  for (int j = 0; j < n; ++j)
+    if (j != m) v *= (e - x[j]) / (x[m] - x[j]);
+  return v;
+}
+
+// One thread per (coarse cell, coarse slot), coarse colour order.  The slot's reference point is
+// located in a child of the coarse cell (or the same cell: p-steps, cells kept), the fine function
+// is evaluated there from the child's nodal values, and the owner slot of the coarse node writes.
+__global__ void k_cell_interpolate(const double* __restrict__ uf, double* __restrict__ uc, int64_t ncc, int dim,
+                                   int nf, int ncn, int ncomp, const int32_t* __restrict__ child,
+                                   const uint8_t* __restrict__ code, const int32_t* __restrict__ fnodes,
+                                   const int32_t* __restrict__ cnodes, int32_t cmask,
+                                   const uint8_t* __restrict__ own, GllPair tab) {
+  const int nbc = dim == 3 ? ncn * ncn * ncn : ncn * ncn;
+  const int nbf = dim == 3 ? nf * nf * nf : nf * nf;
+  const int nch = 1 << dim;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < ncc * nbc; t += (int64_t)gridDim.x * blockDim.x) {
+    if (!own[t]) continue;
+    const int64_t i = t / nbc;
+    const int slot = (int)(t - i * nbc);
+    const int idx[3] = {slot % ncn, (slot / ncn) % ncn, dim == 3 ? slot / (ncn * ncn) : 0};
+    double eta[3] = {0.0, 0.0, 0.0};
+    int32_t fcell;
+    if (code[i * nch] == 8) {
+      fcell = child[i * nch];
+      for (int d = 0; d < dim; ++d) eta[d] = tab.xc[idx[d]];
+    } else {
+      int ch = 0;
+      for (int d = 0; d < dim; ++d) {
+        const double xi = tab.xc[idx[d]];
+        const int h = xi > 0.5 ? 1 : 0;  // a node on the mid-plane lies in both halves: take the first
+        ch |= h << d;
+        eta[d] = 2.0 * xi - h;
+      }
+      fcell = child[i * nch + ch];
+    }
+    double phi[3][8];
+    for (int d = 0; d < 3; ++d)
+      for (int m = 0; m < nf; ++m) phi[d][m] = d < dim ? lagrange_at(tab.xf, nf, m, eta[d]) : (m == 0 ? 1.0 : 0.0);
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int fs = 0; fs < nbf; ++fs) {
+      const int a = fs % nf, b = (fs / nf) % nf, c = dim == 3 ? fs / (nf * nf) : 0;
+      const double w = phi[0][a] * phi[1][b] * phi[2][c];
+      const int64_t g = fnodes[(int64_t)fcell * nbf + fs] & 0x3fffffff;
+      for (int q = 0; q < ncomp; ++q) acc[q] += w * uf[g * ncomp + q];
+    }
+    const int64_t gc = cnodes[t] & cmask;
+    for (int q = 0; q < ncomp; ++q) uc[gc * ncomp + q] = acc[q];
+  }
+}
+
+void cell_interpolate(Transfer& t, const OpLevel& fine, const OpLevel& coarse, const double* uf, double* uc,
+                      Budget* bud, cudaStream_t s) {
+  if (t.separable) return sep_interpolate(t.sep, uf, uc, s);
+  const int dim = t.dim, nf = t.kf + 1, ncn = t.kc + 1;
+  if (nf > 8 || ncn > 8 || t.ncomp > 4) throw Error(kErrUnsupported, "state interpolation: degree or components");
+  const int nbc = coarse.nu.nb;
+  const int64_t ncc = (int64_t)coarse.forest.n_cells();
+  const bool coarse_f = coarse.cell_f.get() != nullptr;
+  if (!t.own_c.get()) {  // owner slot of every coarse node (first occurrence in colour order)
+    std::vector<uint8_t> own((size_t)ncc * nbc, 0);
+    std::vector<char> seen(coarse.nu.n_nodes, 0);
+    for (int64_t i = 0; i < ncc; ++i)
+      for (int b = 0; b < nbc; ++b) {
+        const int32_t g = coarse.nu.cell_nodes[(size_t)coarse.perm[i] * nbc + b];
+        if (!seen[g]) own[(size_t)i * nbc + b] = 1;
+        seen[g] = 1;
+      }
+    t.own_c = upload(bud, own);
+  }
+  GllPair tab{};
+  const std::vector<double> xf = gll_nodes(t.kf), xc = gll_nodes(t.kc);
+  for (int m = 0; m < nf; ++m) tab.xf[m] = xf[m];
+  for (int m = 0; m < ncn; ++m) tab.xc[m] = xc[m];
+  const int64_t work = ncc * nbc;
+  const unsigned grid = (unsigned)std::min<int64_t>((work + 255) / 256, 152 * 32);
+  if (work > 0)
+    k_cell_interpolate<<<grid, 256, 0, s>>>(uf, uc, ncc, dim, nf, ncn, t.ncomp, t.child_cell.as<int32_t>(),
+                                            t.child_code.as<uint8_t>(), fine.tnodes.as<int32_t>(),
+                                            coarse_f ? coarse.cell_f.as<int32_t>() : coarse.cell_u.as<int32_t>(),
+                                            coarse_f ? int32_t(-1) : int32_t(0x7fffffff), t.own_c.as<uint8_t>(), tab);
+  MFNS_CUDA(cudaGetLastError());
+}
+
 void transfer_prolongate_add(const Transfer& t, const OpLevel& fine, const OpLevel& coarse, int prec, const void* xc,
                              void* xf, cudaStream_t s) {
   if (t.separable) return sep_prolongate_add(t.sep, prec, xc, xf, s);

@@ -207,6 +207,12 @@ class Server:
                    "max_error": max(r["error"] for r in records) if records else None,
                    "all_converged": all(r["converged"] for r in records), "rounds": rounds,
                    "makespan_s": span}
+        conv = sorted(r["error"] for r in records if r["converged"])
+        summary["not_converged"] = [{k: r[k] for k in ("rid", "kind", "n", "k", "nu") if k in r}
+                                    for r in records if not r["converged"]]
+        summary["error_converged_p50"] = float(np.percentile(conv, 50)) if conv else None
+        summary["error_converged_p99"] = float(np.percentile(conv, 99)) if conv else None
+        summary["error_converged_max"] = conv[-1] if conv else None
         return records, summary
 
     def close(self):

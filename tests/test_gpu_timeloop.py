@@ -217,12 +217,104 @@ def test_max_velocity(ctx):
     assert prob.max_velocity(_to_lib(U, perm)) == pytest.approx(ref, rel=1e-15)
 
 
-def test_set_state_rejects_refined_meshes(ctx):
+BALL2 = ((0.3, 0.3, 0.3), 0.3, 1)
+
+
+def _pair_ball(ctx, dim, n, k, nu, dt, alpha=1.5, mg_precision=1):
     from paper_2603_29621_gb300 import _lib as L, api
-    m = api.Mesh(ctx, 2, 2)
-    m.refine_ball((0.3, 0.3, 0.3), 0.3, 1)
-    prob = api.Problem(ctx, m, kind=L.STAB_NS, degree=2, nu=0.1, dt=0.1, lambda_max=2.0)
-    u = torch.zeros(prob.info.n_dofs, device="cuda", dtype=torch.float64)
-    with pytest.raises(L.MfnsError) as e:
-        prob.set_state(0.1, 1.5, u)
-    assert e.value.code == L.ERR_UNSUPPORTED
+    m = api.Mesh(ctx, dim, n)
+    m.refine_ball(*BALL2)
+    prob = api.Problem(ctx, m, kind=L.STAB_NS, degree=k, nu=nu, dt=dt, mg_precision=mg_precision)
+    f = mesh.refine_ball(mesh.uniform(dim, n), *BALL2)
+    op = assemble.Problem(f, "stab_ns", k, nu=nu, dt=dt, alpha=alpha)
+    xg, fg = prob.support_points()
+    xo, fo = op.dofs.support_points()
+    return prob, op, inputs.match_dofs(xg, fg, xo, fo), m, f
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("case", [(2, 2, 3), (3, 2, 2)], ids=lambda c: f"{c[0]}d-n{c[1]}-k{c[2]}-ball")
+def test_residual_and_jacobian_on_refined_meshes(ctx, case, prec):
+    dim, n, k = case
+    nu, dt, alpha = 2e-2, 0.05, 1.5
+    prob, op, perm, _, _ = _pair_ball(ctx, dim, n, k, nu, dt, alpha)
+    d = op.dofs
+    assert len(d.nodesets[0].hanging) > 0
+    rng = np.random.default_rng(12)
+    U = d.set_hanging(op.state_vector() + 0.3 * rng.uniform(-1, 1, d.n_dofs))
+    g = d.set_hanging(rng.uniform(-1, 1, d.n_dofs))
+    op.set_state(U, g)
+    Fo = op.residual()
+    A = op.assemble()
+    prob.set_state(dt, alpha, _to_lib(U, perm), _to_lib(g, perm))
+    dt_ = torch.float64 if prec == 0 else torch.float32
+    F = torch.full((len(perm),), 7.0, device="cuda", dtype=dt_)
+    prob.residual(F)
+    Fg = _from_lib(F, perm)
+    assert np.linalg.norm(Fg - Fo) <= TOL[prec] * np.linalg.norm(Fo)
+    x = inputs.uniform_vector(len(perm))
+    y = torch.empty(len(perm), device="cuda", dtype=dt_)
+    prob.vmult(_to_lib(x, perm, dt_), y)
+    yo = A @ x
+    assert np.linalg.norm(_from_lib(y, perm) - yo) <= TOL[prec] * np.linalg.norm(yo)
+
+
+@pytest.mark.parametrize("case", [(3, 2, 2), (2, 3, 3)], ids=lambda c: f"{c[0]}d-n{c[1]}-k{c[2]}-ball")
+def test_state_reaches_every_level_of_a_refined_hierarchy(ctx, case):
+    """Q1 state and explicit field (exact on every level): after mfns_set_state every level's
+    operator equals the oracle's at that state, through refined h-steps (children evaluated per
+    coarse cell), uniform h-steps and p-steps."""
+    from oracle import solvers
+    dim, n, k = case
+    nu, dt, alpha = 5e-2, 0.1, 1.5
+    prob, op, perm, _, f = _pair_ball(ctx, dim, n, k, nu, dt, alpha, mg_precision=0)
+    C, U, g = _q1_state(op, 6)
+    prob.set_state(dt, alpha, _to_lib(U, perm), _to_lib(g, perm))
+    levels = solvers.hierarchy(f, "stab_ns", k, nu=nu, dt=dt)
+    info = prob.get_info()
+    assert info.n_levels == len(levels) >= 3
+    refined_steps = 0
+    for lvl, lv in enumerate(levels):
+        ol = lv.problem
+        refined_steps += int(ol.forest.max_level > 0)
+        xo = ol.dofs.nodesets[0].x
+        ol.set_dt(dt, alpha)
+        ol.set_state(np.concatenate([_q1_field(xo, C[0, c]) for c in range(dim + 1)]),
+                     np.concatenate([_q1_field(xo, C[1, c]) for c in range(dim + 1)]))
+        xg, fg = prob.support_points(lvl)
+        xs, fs = ol.dofs.support_points()
+        pl = inputs.match_dofs(xg, fg, xs, fs)
+        x = inputs.uniform_vector(len(pl), seed=lvl)
+        y = torch.empty(len(pl), device="cuda", dtype=torch.float64)
+        prob.vmult(_to_lib(x, pl), y, which=lvl)
+        yo = ol.assemble() @ x
+        assert np.linalg.norm(_from_lib(y, pl) - yo) <= 1e-12 * np.linalg.norm(yo), lvl
+    assert refined_steps >= 1
+
+
+@pytest.mark.parametrize("case", [(2, 3, 2), (3, 2, 2)], ids=lambda c: f"{c[0]}d-n{c[1]}-k{c[2]}-ball")
+def test_bdf_step_exact_on_refined_meshes(ctx, case):
+    dim, n, k = case
+    prob, op, perm, _, _ = _pair_ball(ctx, dim, n, k, 0.05, 0.1, mg_precision=1)
+    fields = _linear_flow(dim, 3)
+    ts = [0.0, 0.1, 0.22, 0.3]
+    dirich = op.dofs.dirichlet
+    u_nm1 = _to_lib(fields(op, ts[0])[0], perm)
+    u_n = _to_lib(fields(op, ts[1])[0], perm)
+    for j in range(2, len(ts)):
+        dt = ts[j] - ts[j - 1]
+        om = dt / (ts[j - 1] - ts[j - 2])
+        Uex, fo = fields(op, ts[j])
+        guess = np.zeros_like(Uex)
+        guess[dirich] = Uex[dirich]
+        u = _to_lib(guess, perm)
+        info = prob.bdf_step(u, u_n, u_nm1, forcing=_to_lib(fo, perm), dt=dt, omega=om, rtol=1e-12,
+                             lin_tol=1e-8, max_newton=12, extrapolate=True)
+        assert info.converged
+        # the pressure is fixed up to a constant: remove the offset of the free pressure entries
+        # from every pressure entry (hanging ones included)
+        d = _from_lib(u, perm) - Uex
+        P = op.dofs.offsets[1]
+        d[P:] -= d[op.pressure_dofs()].mean()
+        assert np.linalg.norm(d) <= 1e-9 * np.linalg.norm(Uex)
+        u_nm1, u_n = u_n, u
