@@ -180,6 +180,19 @@ def solve_section(api, L, inputs, torch, tol_ns=1e-13, tol_stokes=1e-14):
         r = {"mg": "fp32" if mgp else "fp64", "nu": nu, "dofs": p.info.n_dofs, "cells": p.info.n_cells,
              "levels": p.info.n_levels, "iterations": info.iterations, "rel_residual": info.rel_residual,
              "converged": bool(info.converged), "solve_s": dt_solve, "setup_s": setup, "error_vs_xstar": err}
+        if mgp == L.FP32:  # the system operator's apply (indexed cells, hanging nodes on refined meshes)
+            for prec, vec in (("fp64", xs), ("fp32", xs.float())):
+                out_v = torch.empty_like(vec)
+                for _ in range(3):
+                    p.vmult(vec, out_v)
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                for _ in range(10):
+                    p.vmult(vec, out_v)
+                e1.record()
+                e1.synchronize()
+                r[f"vmult_{prec}_dofs_per_s_l2_warm"] = p.info.n_dofs / (e0.elapsed_time(e1) / 10 * 1e-3)
         xa = x.clone()
         xa[ps] -= xa[ps].mean()
         p.close()
