@@ -3,7 +3,7 @@
 Each case builds the same mesh on both sides, maps the library's DoF order to
 the oracle's by (support point, field), applies the matrix-free operator to a
 seeded U(-1,1) vector and compares with the oracle's assembled A = C^T K C (+) I
-element by element: relative l2 error <= 1e-12 in FP64 (spec bound) and
+element by element: relative l2 error <= 1e-12 in FP64 (the accuracy target of the path) and
 <= 2e-5 in FP32 (single-precision round-off of a ~10^3-term sum per entry)."""
 import numpy as np
 import pytest
