@@ -64,6 +64,8 @@ HIER = [
     ("stokes_a", 3, 2, BALL, 2, dict(nu=1.0)),
     ("stokes_a", 2, 4, BALL, 3, dict(nu=1.0)),
     ("stab_ns", 2, 4, BALL, 2, dict(nu=1e-2, dt=1e-1)),
+    ("stab_ns", 3, 4, None, 1, dict(nu=0.4, dt=1e-2)),      # Q1Q1, viscosity-dominated tau
+    ("stab_ns", 2, 5, None, 1, dict(nu=1e-2, dt=1e-2)),     # Q1Q1, 5 -> 3 -> 2 non-nested
 ]
 
 
@@ -94,7 +96,8 @@ def test_transfers_match_oracle(ctx, case):
 
 @pytest.mark.parametrize("fused", [0, 1], ids=["separate", "fused"])
 @pytest.mark.parametrize("smoother", [("chebyshev", 3), ("chebyshev", 5), ("jacobi", 4)])
-@pytest.mark.parametrize("case", [HIER[0], HIER[3], HIER[2]], ids=lambda c: f"{c[0]}-{c[1]}d-{'ball' if c[3] else 'uni'}")
+@pytest.mark.parametrize("case", [HIER[0], HIER[3], HIER[2], HIER[6]],
+                         ids=lambda c: f"{c[0]}-{c[1]}d-k{c[4]}-{'ball' if c[3] else 'uni'}")
 def test_smoother_matches_oracle(ctx, case, smoother, fused):
     kind, dim, n, refine, k, phys = case
     prob = _gpu_problem(ctx, kind, dim, n, refine, k, lambda_max=1.0, smoother=1 if smoother[0] == "chebyshev" else 2,
