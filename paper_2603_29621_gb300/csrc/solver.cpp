@@ -19,6 +19,7 @@
 #include <random>
 
 #include "problem.hpp"
+#include "ritz.hpp"
 #include "vec.hpp"
 
 namespace mfns {
@@ -97,7 +98,8 @@ std::unique_ptr<Problem> build_problem(const Forest& f, int kind, int k, const P
 
 static OpLevel& sys_of(Problem& p) { return p.system ? *p.system : *p.levels[0]; }
 static double host_dot(Problem& p, const double* a, const double* b, int64_t n, cudaStream_t s);
-double arnoldi_spectral_radius(Problem& p, OpLevel& lv, cudaStream_t s);
+double arnoldi_spectral_radius(Problem& p, OpLevel& lv, cudaStream_t s,
+                               std::vector<std::complex<double>>* ritz = nullptr);
 
 // Timers record events on the launching stream; they are paused while a graph is captured.
 struct TimerPause {
@@ -222,16 +224,24 @@ void estimate_lambda(Problem& p, cudaStream_t s) {
     vcast_d2f(pm.dinv[1].as<float>(), pm.dinv[0].as<double>(), pm.n_dofs, s);
   }
   // lambda_max of D^{-1} A per level: Arnoldi (classical Gram--Schmidt twice) in FP64 from a
-  // seeded random start; the estimate is the spectral radius of the m x m Hessenberg matrix
-  // (its Ritz values), times 1.2 for the Chebyshev smoother.  The relaxation smoother takes
-  // twice the spectral radius: the stabilised operator's D^{-1} A has complex eigenvalues near
-  // its spectral radius, where omega = 2 / (lmin + 1.2 rho) over-relaxes (Q1Q1 with viscosity-
-  // dominated tau stagnated, in the oracle as on the GPU); 2 rho makes omega ~ 0.95 / rho.
-  const double factor = p.smoother == 1 ? 2.0 : 1.2;
+  // seeded random start; the estimate is the spectral radius rho of the m x m Hessenberg matrix
+  // (the modulus of its largest Ritz value), times 1.2 for the Chebyshev smoother.  The
+  // relaxation smoother's weight omega minimises max |1 - omega theta| over the Ritz values
+  // theta in the upper half of the spectrum (|theta| >= rho / 2): the stabilised operator's
+  // D^{-1} A has complex eigenvalues there, and a weight from rho alone over-relaxed them (Q1Q1
+  // with viscosity-dominated tau stagnated, in the oracle as on the GPU).  lmax is stored so that
+  // the smoother's omega = 2 / (lmax / 20 + lmax) equals that weight.
   for (size_t l = 0; l < p.levels.size(); ++l) {
     OpLevel& lv = *p.levels[l];
     if (lv.lmax > 0) continue;
-    lv.lmax = factor * arnoldi_spectral_radius(p, lv, s);
+    std::vector<std::complex<double>> ritz;
+    const double rho = arnoldi_spectral_radius(p, lv, s, &ritz);
+    if (p.smoother == 1) {
+      const double w = relaxation_weight(ritz);
+      lv.lmax = (w > 0.0 && std::isfinite(w)) ? 2.0 / (1.05 * w) : 2.0 * rho;
+    } else {
+      lv.lmax = 1.2 * rho;
+    }
   }
 }
 
@@ -258,7 +268,8 @@ static double small_spectral_radius(const std::vector<double>& H, int m) {
   return std::exp(logsum / iters);
 }
 
-double arnoldi_spectral_radius(Problem& p, OpLevel& lv, cudaStream_t s) {
+double arnoldi_spectral_radius(Problem& p, OpLevel& lv, cudaStream_t s,
+                               std::vector<std::complex<double>>* ritz) {
   const int64_t n = lv.n_dofs;
   const int m = (int)std::min<int64_t>(std::min(p.restart, 30), std::max<int64_t>(n - 1, 1));
   double* V = p.V.as<double>();
@@ -296,6 +307,7 @@ double arnoldi_spectral_radius(Problem& p, OpLevel& lv, cudaStream_t s) {
   std::vector<double> Hm((size_t)mm * mm);
   for (int i = 0; i < mm; ++i)
     for (int j = 0; j < mm; ++j) Hm[(size_t)i * mm + j] = H[(size_t)i * m + j];
+  if (ritz) *ritz = hessenberg_eigenvalues(Hm, mm);
   return small_spectral_radius(Hm, mm);
 }
 
