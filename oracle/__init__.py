@@ -25,6 +25,9 @@ assembly, no sum factorisation):
 * ``solvers``   -- Chebyshev--Jacobi and Jacobi smoothing, the V-cycle, FGMRES
                    with classical Gram--Schmidt (two passes) and the
                    block-triangular Stokes preconditioner (Eq. 5).
+* ``ls``        -- local-smoothing multigrid (Section 2): level spaces on the
+                   refined parts of the mesh with Dirichlet conditions on the
+                   refinement edge, as a multiplicative subspace correction.
 
 Parity status: every function here is pinned by tests against closed forms,
 textbook values, invariants or brute force (see ``tests/test_oracle_*.py``);

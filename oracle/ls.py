@@ -1,0 +1,187 @@
+"""Local-smoothing (LS) multigrid on locally refined meshes (Section 2).
+
+Oracle (test infrastructure only), float64, assembled sparse matrices.
+
+Section 2 contrasts two ways of building the levels of a geometric hierarchy
+on a locally refined mesh.  Global coarsening smooths on the whole domain and
+resolves hanging nodes on every level (``solvers.hierarchy``).  Local
+smoothing takes as level l the cells of refinement level l only -- the part
+Omega_l of the domain refined at least l times -- smooths there with
+homogeneous Dirichlet conditions on the internal boundary of Omega_l (the
+refinement edge), and goes on to the next coarser part.
+
+Written here as what that method is: a multiplicative subspace correction
+over the level spaces
+    V_l = { level-l finite-element functions on Omega_l that vanish on the
+            refinement edge and on the Dirichlet boundary },   l = L, ..., 1,
+and V_0, the finite-element space of the unrefined base mesh.  Every V_l lies
+in the fine (hanging-node conforming) space V; ``level_prolongation`` gives
+its embedding P_l (nodal interpolation at the free fine DoFs).  One cycle:
+  pre-smoothing  l = L .. 1 : x_l = S_l(P_l^T r) from zero,  x += P_l x_l,
+  level 0                   : one global-coarsening V-cycle of the base
+                              hierarchy on P_0^T r,           x += P_0 x_0,
+  post-smoothing l = 1 .. L : d_l = S_l(P_l^T r) from zero,  x += P_l d_l,
+with r = b - A x updated after every correction and S_l the level smoother
+(Chebyshev or relaxation around point Jacobi, ``solvers``) on
+A_l = P_l^T A P_l, extended by identity rows on the level's edge and boundary
+nodes.  For the vector Laplacian the Galerkin product equals the operator
+assembled on the level mesh with Dirichlet conditions on the refinement edge
+(same bilinear form, exact quadrature); the tests pin that.
+
+Readings: the paper does not say which levels carry the polynomial
+coarsening.  Here the refined levels keep the fine degree k and the base
+level is the first level of the base mesh's own global hierarchy (which
+coarsens p and h in the order of Section 3 or 5).  LS levels exist for the
+vector Laplacian (the Stokes A block) only: on the stabilised operator the
+level operators would not be Galerkin products (tau depends on the cell size).
+"""
+import numpy as np
+import scipy.sparse as sp
+
+from . import assemble, fe, mesh, solvers, transfer
+
+
+def level_cells(forest, l):
+    """(m, dim) integer coordinates of the cells of refinement level l: the active cells of
+    level l and the level-l ancestors of finer active cells."""
+    c = forest.cells
+    sel = c[:, 0] >= l
+    crd = c[sel, 1:] >> (c[sel, 0] - l)[:, None]
+    return np.unique(crd, axis=0)
+
+
+class LevelSpace:
+    """Q_k nodes of the level-l cells, numbered by their integer node index k * cell + slot.
+
+    Attributes: ``cells`` (m, dim), ``idx`` (Nn, dim) node indices, ``x`` (Nn, dim) support
+    points, ``cell_nodes`` (m, (k+1)^dim), ``edge`` (node on the refinement edge), ``boundary``
+    (node on the domain boundary), ``interior`` (neither)."""
+
+    def __init__(self, forest, l, k):
+        dim = forest.dim
+        self.dim, self.k, self.l = dim, k, l
+        self.N = forest.n * 2 ** l                       # level-l cells per direction
+        self.cells = level_cells(forest, l)
+        loc = fe.tensor_index(dim, k + 1)
+        keys = (k * self.cells[:, None, :] + loc[None, :, :]).reshape(-1, dim)
+        uniq, inv = np.unique(keys, axis=0, return_inverse=True)
+        self.idx = uniq
+        self.cell_nodes = inv.reshape(len(self.cells), -1)
+        self.n_nodes = len(uniq)
+        xi = fe.gll_points(k)
+        cell, slot = uniq // k, uniq % k
+        top = cell == self.N                             # the last node of a line: slot k of N-1
+        cell = np.where(top, self.N - 1, cell)
+        slot = np.where(top, k, slot)
+        self.x = (cell + xi[slot]) / self.N
+        self.boundary = ((uniq == 0) | (uniq == k * self.N)).any(axis=1)
+        # refinement edge: some level-l cell inside the domain whose closure holds the node is
+        # not a cell of this level
+        present = {tuple(c) for c in self.cells.tolist()}
+        self.edge = np.zeros(self.n_nodes, dtype=bool)
+        for g in range(self.n_nodes):
+            choices = []
+            for d in range(dim):
+                i = int(uniq[g, d])
+                choices.append((i // k - 1, i // k) if i % k == 0 else (i // k,))
+            for cand in np.array(np.meshgrid(*choices, indexing="ij")).reshape(dim, -1).T:
+                if ((cand >= 0) & (cand < self.N)).all() and tuple(cand.tolist()) not in present:
+                    self.edge[g] = True
+                    break
+        self.interior = ~(self.edge | self.boundary)
+        self._cell_of = {tuple(c): i for i, c in enumerate(self.cells.tolist())}
+
+    def locate(self, x):
+        """Id of a level cell whose closed box contains each point (npts, dim), -1 if none."""
+        t = x * self.N
+        lo = np.floor(t - 1e-9).astype(np.int64)
+        hi = np.floor(t + 1e-9).astype(np.int64)
+        out = -np.ones(len(x), dtype=np.int64)
+        for sel in fe.tensor_index(self.dim, 2):
+            cand = np.where(sel[None, :] == 0, lo, hi)
+            for i in np.nonzero(out < 0)[0]:
+                out[i] = self._cell_of.get(tuple(cand[i].tolist()), -1)
+        return out
+
+
+def level_prolongation(problem, space):
+    """P_l: level vector (ncomp * Nn, component-major) -> fine DoF vector.  Column (c, g) is the
+    level basis function of interior node g in component c, evaluated at every free fine DoF of
+    component c (zero at constrained fine DoFs and for non-interior level nodes)."""
+    d = problem.dofs
+    ncomp, k, _ = d.fields[0]
+    ns = d.nodesets[0]
+    cells = space.locate(ns.x)
+    inside = cells >= 0
+    xi = ns.x[inside] * space.N - space.cells[cells[inside]]
+    phi = fe.eval_basis_at(space.dim, k, np.clip(xi, 0.0, 1.0))    # (n_in, nb)
+    lnodes = space.cell_nodes[cells[inside]]                          # (n_in, nb)
+    keep = (np.abs(phi) > 1e-14) & space.interior[lnodes]
+    fine_nodes = np.nonzero(inside)[0]
+    rows, cols, vals = [], [], []
+    for c in range(ncomp):
+        rf = d.dof(0, c, fine_nodes)
+        rows.append(np.repeat(rf[:, None], phi.shape[1], axis=1)[keep])
+        cols.append((c * space.n_nodes + lnodes)[keep])
+        vals.append(phi[keep])
+    P = sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
+                      shape=(d.n_dofs, ncomp * space.n_nodes))
+    P = sp.diags(d.free.astype(float)) @ P
+    P = P.tocsr()
+    P.eliminate_zeros()
+    return P
+
+
+class LsLevel:
+    def __init__(self, problem, A, l):
+        self.space = LevelSpace(problem.forest, l, problem.k)
+        self.P = level_prolongation(problem, self.space)
+        ncomp = problem.dofs.fields[0][0]
+        inner = np.tile(self.space.interior, ncomp)
+        self.A = (self.P.T @ A @ self.P + sp.diags((~inner).astype(float))).tocsr()
+        self.dinv = 1.0 / self.A.diagonal()
+        self.lmax = None
+
+
+class LocalSmoothing:
+    """The LS V-cycle of a 'stokes_a' problem on a locally refined forest.
+
+    ``lmax_ls[l - 1]`` is the smoother bound of level l (l = 1..L); the base level's
+    global-coarsening hierarchy gets ``lmax_base`` (one per level but its coarsest)."""
+
+    def __init__(self, problem, lmax_ls, lmax_base, smoother=("chebyshev", 5), stop_n=2, order="p_then_h"):
+        assert problem.kind == "stokes_a"
+        self.problem = problem
+        self.A = problem.assemble()
+        forest = problem.forest
+        self.L = forest.max_level
+        self.levels = [LsLevel(problem, self.A, l) for l in range(1, self.L + 1)]
+        for lv, lm in zip(self.levels, lmax_ls):
+            lv.lmax = lm
+        self.smoother = smoother
+        base = mesh.uniform(forest.dim, forest.n)
+        self.base_levels = solvers.hierarchy(base, "stokes_a", problem.k, order=order, stop_n=stop_n,
+                                             nu=problem.nu)
+        self.base = solvers.VCycle(self.base_levels, lmax_base, smoother)
+        self.P0 = transfer.prolongation(self.base_levels[0].problem, problem)
+
+    def _smooth(self, lv, b):
+        kind, deg = self.smoother
+        x0 = np.zeros_like(b)
+        if kind == "chebyshev":
+            return solvers.chebyshev(lv.A, lv.dinv, b, x0, deg, lv.lmax, x_is_zero=True)
+        return solvers.jacobi_relaxation(lv.A, lv.dinv, b, x0, deg, lv.lmax)
+
+    def __call__(self, b):
+        A = self.A
+        x = np.zeros_like(b)
+        r = b.copy()
+        for lv in reversed(self.levels):                  # pre-smoothing, finest part first
+            x = x + lv.P @ self._smooth(lv, lv.P.T @ r)
+            r = b - A @ x
+        x = x + self.P0 @ self.base(self.P0.T @ r)       # the base mesh's V-cycle
+        r = b - A @ x
+        for lv in self.levels:                            # post-smoothing, coarsest part first
+            x = x + lv.P @ self._smooth(lv, lv.P.T @ r)
+            r = b - A @ x
+        return x
