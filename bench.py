@@ -151,14 +151,15 @@ def solve_section(api, L, inputs, torch, tol_ns=1e-13, tol_stokes=1e-14):
     and error against the manufactured discrete solution x* (smooth fields sampled at the
     support points, b = A x*)."""
     ctx = api.Context(torch.cuda.current_device())
-    out = {"stab_ns_48": [], "stokes_ball_32": []}
+    out = {"stab_ns_48": [], "stokes_ball_32": [], "stokes_ball_32_ls": []}
 
-    def one(kind, n, k, nu, dt, mgp, ball, tol):  # -> (record, solution with pressure mean removed)
+    def one(kind, n, k, nu, dt, mgp, ball, tol, hierarchy=0):  # -> (record, solution, pressure mean removed)
         m = api.Mesh(ctx, 3, n)
         if ball:
             m.refine_ball(*ball)
         t0 = time.perf_counter()
-        p = api.Problem(ctx, m, kind=kind, degree=k, nu=nu, dt=dt, mg_precision=mgp, tol=tol, maxit=300)
+        p = api.Problem(ctx, m, kind=kind, degree=k, nu=nu, dt=dt, mg_precision=mgp, tol=tol, maxit=300,
+                        hierarchy=hierarchy)
         setup = time.perf_counter() - t0
         xyz, fld = p.support_points()
         xs = torch.tensor(inputs.smooth_solution(xyz, fld, 3, nu if kind == L.STOKES else 1.0), device="cuda")
@@ -177,10 +178,11 @@ def solve_section(api, L, inputs, torch, tol_ns=1e-13, tol_stokes=1e-14):
         xr = xs.clone()
         xr[ps] -= xr[ps].mean()
         err = float(torch.linalg.norm(d) / torch.linalg.norm(xr))
-        r = {"mg": "fp32" if mgp else "fp64", "nu": nu, "dofs": p.info.n_dofs, "cells": p.info.n_cells,
+        r = {"mg": "fp32" if mgp else "fp64", "hierarchy": "local_smoothing" if hierarchy else "global_coarsening",
+             "nu": nu, "dofs": p.info.n_dofs, "cells": p.info.n_cells,
              "levels": p.info.n_levels, "iterations": info.iterations, "rel_residual": info.rel_residual,
              "converged": bool(info.converged), "solve_s": dt_solve, "setup_s": setup, "error_vs_xstar": err}
-        if mgp == L.FP32:  # the system operator's apply (indexed cells, hanging nodes on refined meshes)
+        if mgp == L.FP32 and not hierarchy:  # the system operator's apply (indexed cells, hanging nodes)
             for prec, vec in (("fp64", xs), ("fp32", xs.float())):
                 out_v = torch.empty_like(vec)
                 for _ in range(3):
@@ -199,16 +201,27 @@ def solve_section(api, L, inputs, torch, tol_ns=1e-13, tol_stokes=1e-14):
         m.close()
         return r, xa
 
-    def pair(key, *a):
-        r64, x64 = one(*a[:5], L.FP64, *a[5:])
-        r32, x32 = one(*a[:5], L.FP32, *a[5:])
+    def pair(key, *a, hierarchy=0):
+        r64, x64 = one(*a[:5], L.FP64, *a[5:], hierarchy=hierarchy)
+        r32, x32 = one(*a[:5], L.FP32, *a[5:], hierarchy=hierarchy)
         r32["rel_diff_vs_fp64_mg"] = float(torch.linalg.norm(x32 - x64) / torch.linalg.norm(x64))
         out[key] += [r64, r32]
+        return x64
 
     for nu in (1e-1, 1e-2, 1e-3):
         pair("stab_ns_48", L.STAB_NS, 48, 2, nu, 1e-2, None, tol_ns)
-    pair("stokes_ball_32", L.STOKES, 32, 2, 1.0, 0.0, ((0.5, 0.5, 0.5), 0.25, 2), tol_stokes)
-    for key in list(out):
+    ball = ((0.5, 0.5, 0.5), 0.25, 2)
+    x_gc = pair("stokes_ball_32", L.STOKES, 32, 2, 1.0, 0.0, ball, tol_stokes)
+    # Section 2: local smoothing (levels = refinement levels, Dirichlet conditions on the refinement
+    # edge) against global coarsening on the same problem
+    x_ls = pair("stokes_ball_32_ls", L.STOKES, 32, 2, 1.0, 0.0, ball, tol_stokes, hierarchy=L.LOCAL_SMOOTHING)
+    out["stokes_ball_32_ls"][0]["rel_diff_vs_global_coarsening"] = float(
+        torch.linalg.norm(x_ls - x_gc) / torch.linalg.norm(x_gc))
+    gc, lsr = out["stokes_ball_32"], out["stokes_ball_32_ls"]
+    out["stokes_ball_32_ls_vs_gc"] = {
+        r["mg"]: {"iterations_gc": g["iterations"], "iterations_ls": r["iterations"],
+                  "solve_s_gc": g["solve_s"], "solve_s_ls": r["solve_s"]} for g, r in zip(gc, lsr)}
+    for key in [k for k in out if isinstance(out[k], list)]:
         r64 = [r for r in out[key] if r["mg"] == "fp64"]
         r32 = [r for r in out[key] if r["mg"] == "fp32"]
         out[key + "_fp32_speedup"] = sum(r["solve_s"] for r in r64) / max(sum(r["solve_s"] for r in r32), 1e-12)

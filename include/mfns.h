@@ -118,6 +118,17 @@ typedef struct {
                            its product (no separate vector pass); 0 (default): the product is
                            written out and a streaming kernel applies the update (faster on GB300:
                            the cell kernel is latency-bound) */
+  int hierarchy;        /* multigrid levels on a locally refined mesh (Section 2): 0 (default) global
+                           coarsening -- every level covers the whole domain, hanging nodes resolved
+                           on each; 1 local smoothing (MFNS_STOKES and MFNS_STOKES_A only) -- level
+                           l is the set of cells of refinement level l with homogeneous Dirichlet
+                           conditions on its refinement edge, level 0 the unrefined base mesh with
+                           its own global-coarsening hierarchy.  The levels reported by
+                           mfns_problem_info and addressed by mfns_set_lambda_max are then the
+                           refined levels (finest first) followed by the base hierarchy;
+                           mfns_smooth, mfns_prolongate_add and mfns_restrict address global-
+                           coarsening levels only and return MFNS_ERR_UNSUPPORTED or
+                           MFNS_ERR_ARG.  On an unrefined mesh 1 is the same as 0. */
 } mfns_problem_desc;
 
 typedef struct {

@@ -19,6 +19,7 @@ FP64, FP32 = 0, 1
 OP_SYSTEM, OP_PMASS = -1, -2
 TERM_MASS, TERM_CONV, TERM_NEWTON, TERM_SUPG = 1, 2, 4, 8
 TERM_SUPG_NEWTON, TERM_PSPG, TERM_STRONG_VISC, TERMS_ALL = 16, 32, 64, 127
+GLOBAL_COARSENING, LOCAL_SMOOTHING = 0, 1   # mfns_problem_desc.hierarchy
 
 
 class ProblemDesc(C.Structure):
@@ -30,6 +31,7 @@ class ProblemDesc(C.Structure):
         ("maxit", C.c_int), ("cg_iterations", C.c_int), ("lambda_max", C.c_double),
         ("recompute_frozen", C.c_int),
         ("fused_smoother", C.c_int),
+        ("hierarchy", C.c_int),
     ]
 
 

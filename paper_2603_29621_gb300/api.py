@@ -96,10 +96,10 @@ class Mesh:
 
 def make_desc(kind, degree, nu=1.0, dt=0.0, terms=0, div_sign=0.0, smoother=0, smoother_degree=0,
               mg_order=0, mg_precision=L.FP64, coarse_stop_n=0, fgmres_restart=0, tol=0.0, maxit=0,
-              cg_iterations=0, lambda_max=0.0, recompute_frozen=0, fused_smoother=0):
+              cg_iterations=0, lambda_max=0.0, recompute_frozen=0, fused_smoother=0, hierarchy=0):
     return L.ProblemDesc(kind, degree, nu, dt, terms, div_sign, smoother, smoother_degree, mg_order,
                          mg_precision, coarse_stop_n, fgmres_restart, tol, maxit, cg_iterations, lambda_max,
-                         recompute_frozen, int(bool(fused_smoother)))
+                         recompute_frozen, int(bool(fused_smoother)), int(hierarchy))
 
 
 class Problem:

@@ -144,8 +144,12 @@ int mfns_problem_create(mfns_ctx* ctx, const mfns_mesh* mesh, const mfns_problem
   ph.div_sign = desc->div_sign != 0 ? desc->div_sign : (desc->kind == MFNS_STAB_NS ? 1.0 : -1.0);
   ph.precompute_frozen = desc->recompute_frozen == 0;
   const size_t used0 = ctx->budget.used;
+  if (desc->hierarchy != 0 && desc->hierarchy != 1) return fail(MFNS_ERR_ARG, "hierarchy must be 0 or 1");
+  if (desc->hierarchy == 1 && desc->kind != MFNS_STOKES && desc->kind != MFNS_STOKES_A)
+    return fail(MFNS_ERR_UNSUPPORTED, "local smoothing is built for MFNS_STOKES and MFNS_STOKES_A");
   std::unique_ptr<Problem> p = build_problem(mesh->forest, desc->kind, k, ph, desc->mg_order,
-                                             desc->coarse_stop_n > 0 ? desc->coarse_stop_n : 2, &ctx->budget);
+                                             desc->coarse_stop_n > 0 ? desc->coarse_stop_n : 2, &ctx->budget,
+                                             desc->hierarchy);
   if (desc->smoother < 0 || desc->smoother > 2) return fail(MFNS_ERR_ARG, "smoother must be 0, 1 or 2");
   // internal: 0 = Chebyshev, 1 = Jacobi relaxation
   p->smoother = desc->smoother == 0 ? (desc->kind == MFNS_STAB_NS ? 1 : 0) : desc->smoother - 1;
@@ -158,7 +162,7 @@ int mfns_problem_create(mfns_ctx* ctx, const mfns_mesh* mesh, const mfns_problem
   p->cg_iterations = desc->cg_iterations > 0 ? desc->cg_iterations : 10;
   p->fused_smoother = desc->fused_smoother != 0;
   if (desc->lambda_max > 0)
-    for (auto& lv : p->levels) lv->lmax = desc->lambda_max;
+    for (int l = 0; l < mg_level_count(*p); ++l) mg_level(*p, l).lmax = desc->lambda_max;
   alloc_workspaces(*p);
   cudaStream_t s = 0;
   autotune(*p, s);
@@ -196,16 +200,18 @@ int mfns_problem_info(const mfns_problem* pc, mfns_info* out) {
   out->dim = P.dim;
   out->degree = P.k;
   out->kind = P.kind;
-  out->n_levels = (int)P.levels.size();
+  const int nl = mg_level_count(P);
+  out->n_levels = nl;
   out->n_dofs = S.n_dofs;
   out->n_velocity_dofs = S.n_main_dofs;
   out->n_cells = (int64_t)S.forest.n_cells();
   out->n_colors = S.L.n_colors;
-  for (size_t l = 0; l < P.levels.size() && l < 32; ++l) {
-    out->level_dofs[l] = P.levels[l]->n_dofs;
-    out->level_degree[l] = P.levels[l]->k;
-    out->level_cells[l] = (int64_t)P.levels[l]->forest.n_cells();
-    out->lambda_max[l] = P.levels[l]->lmax;
+  for (int l = 0; l < nl && l < 32; ++l) {
+    OpLevel& lv = mg_level(P, l);
+    out->level_dofs[l] = lv.n_dofs;
+    out->level_degree[l] = lv.k;
+    out->level_cells[l] = (int64_t)lv.forest.n_cells();
+    out->lambda_max[l] = lv.lmax;
   }
   out->device_bytes = P.bytes;
   return MFNS_OK;
@@ -230,8 +236,8 @@ int mfns_constrained_dofs(const mfns_problem* pc, int which, int64_t* idx, int64
 }
 
 int mfns_set_lambda_max(mfns_problem* p, int level, double lmax) {
-  if (!p || level < 0 || level >= (int)p->p->levels.size() || !(lmax > 0)) return fail(MFNS_ERR_ARG, "bad level");
-  p->p->levels[level]->lmax = lmax;
+  if (!p || level < 0 || level >= mg_level_count(*p->p) || !(lmax > 0)) return fail(MFNS_ERR_ARG, "bad level");
+  mg_level(*p->p, level).lmax = lmax;
   invalidate_graphs(*p->p);
   return MFNS_OK;
 }
@@ -287,6 +293,7 @@ int mfns_smooth(mfns_problem* p, int level, int prec, const void* b, void* x, in
   API_BEGIN
   if (!p || level < 0 || level >= (int)p->p->levels.size() || !b || !x || (prec != 0 && prec != 1))
     return fail(MFNS_ERR_ARG, "bad arguments");
+  if (p->p->ls) return fail(MFNS_ERR_UNSUPPORTED, "single-level smoothing is not exposed for local smoothing");
   MFNS_CUDA(cudaSetDevice(p->ctx->device));
   smooth(*p->p, level, prec, b, x, x_is_zero != 0, S(stream));
   API_END

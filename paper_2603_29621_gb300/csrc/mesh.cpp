@@ -171,9 +171,117 @@ Lattice make_lattice(const Forest& f) {
         for (int i = 0; i < s; ++i)
           lat.cell[(size_t)(x0 + i) + N * ((size_t)(y0 + j) + N * (size_t)(z0 + k))] = (int32_t)c;
   }
-  for (int32_t v : lat.cell)
-    if (v < 0) throw std::runtime_error("forest does not cover the domain");
+  if (!f.partial)
+    for (int32_t v : lat.cell)
+      if (v < 0) throw std::runtime_error("forest does not cover the domain");
   return lat;
+}
+
+Forest forest_level(const Forest& f, int l) {
+  Forest out;
+  out.dim = f.dim;
+  out.n = f.n;
+  out.partial = true;
+  std::vector<std::array<int32_t, 3>> cells;
+  for (size_t c = 0; c < f.n_cells(); ++c) {
+    const int sh = f.lev[c] - l;
+    if (sh < 0) continue;
+    cells.push_back({f.crd[3 * c] >> sh, f.crd[3 * c + 1] >> sh, f.crd[3 * c + 2] >> sh});
+  }
+  std::sort(cells.begin(), cells.end());
+  cells.erase(std::unique(cells.begin(), cells.end()), cells.end());
+  for (auto& c : cells) {
+    out.lev.push_back(l);
+    for (int d = 0; d < 3; ++d) out.crd.push_back(c[d]);
+  }
+  out.sort();
+  return out;
+}
+
+bool ls_owned_nodes(const Forest& fine, const NodeSpace& fns, const Forest& lf, const NodeSpace& lns,
+                    const std::vector<uint8_t>& edge, int l, std::vector<int32_t>& owner,
+                    std::vector<int32_t>& cf, std::vector<int32_t>& cl, std::string* err) {
+  const int nb = fns.nb;
+  if (lns.nb != nb || (int64_t)owner.size() != fns.n_nodes || (int64_t)edge.size() != lns.n_nodes) {
+    if (err) *err = "inconsistent node spaces";
+    return false;
+  }
+  std::vector<char> hang(fns.n_nodes, 0);
+  for (int32_t g : fns.hang_node) hang[g] = 1;
+  std::vector<std::pair<std::array<int32_t, 3>, int32_t>> at(lf.n_cells());
+  for (size_t c = 0; c < lf.n_cells(); ++c) at[c] = {{lf.crd[3 * c], lf.crd[3 * c + 1], lf.crd[3 * c + 2]}, (int32_t)c};
+  std::sort(at.begin(), at.end());
+  for (size_t c = 0; c < fine.n_cells(); ++c) {
+    if (fine.lev[c] != l) continue;
+    const std::array<int32_t, 3> key = {fine.crd[3 * c], fine.crd[3 * c + 1], fine.crd[3 * c + 2]};
+    auto it = std::lower_bound(at.begin(), at.end(), std::make_pair(key, int32_t(-1)));
+    if (it == at.end() || it->first != key) {
+      if (err) *err = "active cell missing from its level";
+      return false;
+    }
+    for (int b = 0; b < nb; ++b) {
+      const int32_t gf = fns.cell_nodes[c * nb + b];
+      if (fns.cell_master[c * nb + b] != gf || hang[gf] || fns.boundary[gf]) continue;  // hanging or Dirichlet
+      const int32_t gl = lns.cell_nodes[(size_t)it->second * nb + b];
+      if (edge[gl]) continue;
+      if (owner[gf] == l) continue;  // already listed from a neighbouring cell of this level
+      if (owner[gf] >= 0) {
+        if (err) *err = "a fine DoF owned by two levels";
+        return false;
+      }
+      owner[gf] = l;
+      cf.push_back(gf);
+      cl.push_back(gl);
+    }
+  }
+  return true;
+}
+
+bool ls_all_owned(const NodeSpace& fns, const std::vector<int32_t>& owner) {
+  std::vector<char> hang(fns.n_nodes, 0);
+  for (int32_t g : fns.hang_node) hang[g] = 1;
+  for (int64_t g = 0; g < fns.n_nodes; ++g)
+    if (!hang[g] && !fns.boundary[g] && owner[g] < 0) return false;
+  return true;
+}
+
+std::vector<uint8_t> refinement_edge(const Forest& f, const NodeSpace& ns) {
+  std::vector<uint8_t> edge(ns.n_nodes, 0);
+  const size_t nc = f.n_cells();
+  if (nc == 0) return edge;
+  const int dim = f.dim, k = ns.k, np = k + 1, l = f.lev[0];
+  const int64_t N = (int64_t)f.n << l;
+  auto key = [&](const int64_t c[3]) { return c[0] + N * (c[1] + N * c[2]); };
+  std::vector<int64_t> present(nc);
+  for (size_t c = 0; c < nc; ++c) {
+    if (f.lev[c] != l) throw std::runtime_error("refinement_edge: cells of different levels");
+    const int64_t cc[3] = {f.crd[3 * c], f.crd[3 * c + 1], f.crd[3 * c + 2]};
+    present[c] = key(cc);
+  }
+  std::sort(present.begin(), present.end());
+  auto has = [&](const int64_t c[3]) { return std::binary_search(present.begin(), present.end(), key(c)); };
+  for (size_t c = 0; c < nc; ++c)
+    for (int b = 0; b < ns.nb; ++b) {
+      const int s[3] = {b % np, (b / np) % np, dim == 3 ? b / (np * np) : 0};
+      // the level cells whose closure holds the node: one or two per direction
+      int64_t lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+      for (int d = 0; d < dim; ++d) {
+        const int64_t cd = f.crd[3 * c + d];
+        lo[d] = s[d] == 0 ? cd - 1 : cd;
+        hi[d] = s[d] == k ? cd + 1 : cd;
+      }
+      bool on_edge = false;
+      for (int64_t z = lo[2]; z <= hi[2] && !on_edge; ++z)
+        for (int64_t y = lo[1]; y <= hi[1] && !on_edge; ++y)
+          for (int64_t x = lo[0]; x <= hi[0] && !on_edge; ++x) {
+            const int64_t cand[3] = {x, y, z};
+            bool inside = true;
+            for (int d = 0; d < dim; ++d) inside = inside && cand[d] >= 0 && cand[d] < N;
+            if (inside && !has(cand)) on_edge = true;
+          }
+      if (on_edge) edge[ns.cell_nodes[c * ns.nb + b]] = 1;
+    }
+  return edge;
 }
 
 Forest forest_balance(Forest f) {
@@ -267,7 +375,8 @@ std::vector<uint32_t> constraint_masks(const Forest& f, const Lattice& lat) {
     auto level_at = [&](const int p[3]) -> int {
       for (int d = 0; d < dim; ++d)
         if (p[d] < 0 || p[d] >= N) return 1 << 20;
-      return f.lev[lat.at(p[0], p[1], dim == 3 ? p[2] : 0)];
+      const int32_t id = lat.at(p[0], p[1], dim == 3 ? p[2] : 0);
+      return id < 0 ? 1 << 20 : f.lev[id];  // a hole of a partial forest has no cell to hang from
     };
     uint32_t m = 0;
     for (int d = 0; d < dim; ++d)

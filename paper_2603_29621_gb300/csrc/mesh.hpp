@@ -25,6 +25,7 @@ constexpr uint32_t kChildShift = 24;
 struct Forest {
   int dim = 3;
   int n = 1;                      // root cells per direction
+  bool partial = false;           // the cells need not cover the domain (a local-smoothing level)
   std::vector<int32_t> lev;       // level of every active cell
   std::vector<int32_t> crd;       // 3 integer coordinates per cell (at its level)
   size_t n_cells() const { return lev.size(); }
@@ -38,6 +39,9 @@ Forest forest_uniform(int dim, int n);
 Forest forest_refine(const Forest& f, const std::vector<char>& mask);
 Forest forest_balance(Forest f);  // 2:1 over faces, edges and vertices
 Forest forest_refine_ball(Forest f, const double centre[3], double radius, int levels);
+// Local smoothing (Section 2): the cells of refinement level l -- the active cells of level l
+// and the level-l ancestors of finer ones -- as a partial forest
+Forest forest_level(const Forest& f, int l);
 // one global-coarsening step (finest level -> parents; uniform n -> ceil(n/2), non-nested for odd n)
 bool forest_can_coarsen(const Forest& f, int stop_n);
 Forest forest_coarsen(const Forest& f);
@@ -70,6 +74,21 @@ struct NodeSpace {
 };
 NodeSpace make_nodes(const Forest& f, const Lattice& lat, const std::vector<uint32_t>& masks, int k,
                      std::string* err);
+
+// Nodes of a single-level partial forest on its refinement edge: some cell of that level inside
+// the domain whose closure holds the node is not one of the forest's cells.
+std::vector<uint8_t> refinement_edge(const Forest& f, const NodeSpace& ns);
+
+// Local smoothing: the DoFs a level owns.  For the active cells of the fine forest at refinement
+// level l, every slot whose fine node is free (not hanging, not on the boundary) and whose level
+// node (same cell of the level forest `lf`, same slot) is not on the refinement edge appends the
+// pair (fine node, level node) to (cf, cl) and records owner[fine node] = l.  A node listed by
+// two levels, or an active cell missing from `lf`, is an error (false, message in err).
+bool ls_owned_nodes(const Forest& fine, const NodeSpace& fns, const Forest& lf, const NodeSpace& lns,
+                    const std::vector<uint8_t>& edge, int l, std::vector<int32_t>& owner,
+                    std::vector<int32_t>& cf, std::vector<int32_t>& cl, std::string* err);
+// every free node of the fine space has an owner
+bool ls_all_owned(const NodeSpace& fns, const std::vector<int32_t>& owner);
 
 // 1D helpers shared by the host code (GLL nodes, Gauss rule, Lagrange values).
 std::vector<double> gll_nodes(int k);

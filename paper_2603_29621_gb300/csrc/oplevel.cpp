@@ -38,7 +38,7 @@ static DevBuf upload_as(Budget* bud, const std::vector<double>& v) {
   return upload(bud, t);
 }
 
-void build_oplevel(OpLevel& lv, const Forest& f, int op, int k, const Physics& ph, Budget* bud) {
+void build_oplevel(OpLevel& lv, const Forest& f, int op, int k, const Physics& ph, Budget* bud, bool edge_dirichlet) {
   lv.op = op;
   lv.dim = f.dim;
   lv.k = k;
@@ -53,6 +53,12 @@ void build_oplevel(OpLevel& lv, const Forest& f, int op, int k, const Physics& p
   if (op == OP_STOKES) {
     lv.np = make_nodes(f, lat, masks, k - 1, &err);
     if (!err.empty()) throw Error(kErrArg, err);
+  }
+  if (edge_dirichlet) {  // local smoothing: homogeneous Dirichlet conditions on the refinement edge
+    if (!f.partial || op != OP_STOKES_A) throw Error(kErrUnsupported, "refinement-edge conditions need a level forest");
+    const std::vector<uint8_t> e = refinement_edge(f, lv.nu);
+    for (int64_t g = 0; g < lv.nu.n_nodes; ++g)
+      if (e[g]) lv.nu.boundary[g] = 1;
   }
   lv.n_main_dofs = lv.nu.n_nodes * lv.NU;
   lv.n_dofs = lv.n_main_dofs + (op == OP_STOKES ? lv.np.n_nodes : 0);

@@ -47,7 +47,10 @@ struct OpLevel {
   size_t bytes() const;
 };
 
-void build_oplevel(OpLevel& lv, const Forest& f, int op, int k, const Physics& ph, Budget* bud);
+// edge_dirichlet (level forests of local smoothing): nodes on the refinement edge are constrained
+// like Dirichlet nodes (identity rows, zero in the operator's input)
+void build_oplevel(OpLevel& lv, const Forest& f, int op, int k, const Physics& ph, Budget* bud,
+                   bool edge_dirichlet = false);
 void oplevel_vmult(const OpLevel& lv, int prec, const void* src, void* dst, cudaStream_t s);
 void oplevel_diag(const OpLevel& lv, int prec, void* diag, cudaStream_t s);
 // One smoothing step with the update fused into the operator application (t: scratch):
@@ -86,7 +89,9 @@ struct Transfer {
   std::vector<double> Pc;               // coarse hanging interpolation P[2][NC][NC]
   DevBuf own_c;                         // state interpolation: owner flag per coarse (cell, slot)
 };
-void build_transfer(Transfer& t, const OpLevel& fine, const OpLevel& coarse, Budget* bud);
+// allow_unrefined (local smoothing): coarse cells without children in the fine level are skipped
+void build_transfer(Transfer& t, const OpLevel& fine, const OpLevel& coarse, Budget* bud,
+                    bool allow_unrefined = false);
 bool build_separable(SepTransfer& t, const OpLevel& fine, const OpLevel& coarse, Budget* bud);
 void sep_restrict(const SepTransfer& t, int prec, const void* fine, void* coarse, cudaStream_t s);
 // coarse = the fine FE function evaluated at the coarse nodes (all components, no masking; fp64)
@@ -128,6 +133,8 @@ struct MultiOpDel {
 };
 using MultiOpPtr = std::unique_ptr<MultiOp, MultiOpDel>;
 
+struct LocalSmoothing;
+
 struct Problem {
   uint64_t uid = 0;                     // process-unique id (batch plans are keyed by it)
   uint64_t graph_epoch = 0;             // incremented whenever the captured graphs are dropped
@@ -168,13 +175,46 @@ struct Problem {
   cudaEvent_t ev_step = nullptr;        // batched rounds: the step's input is in pc_in
   double st_dt = -1.0, st_alpha = -1.0;  // dt, alpha and explicit-field use of the last set_state
   bool st_g = false;
+  // local-smoothing hierarchy (null: global coarsening over `levels`)
+  std::unique_ptr<LocalSmoothing> ls;
   size_t bytes = 0;
   ~Problem();
 };
 
+// Local smoothing (Section 2) for the vector Laplacian on a locally refined mesh.  Level l >= 1 is
+// the set of cells of refinement level l (a partial forest), smoothed with homogeneous Dirichlet
+// conditions on its refinement edge; level 0 is the unrefined base mesh, whose own
+// global-coarsening hierarchy (p and h) completes the cycle.  Every free DoF of the fine mesh is
+// owned by exactly one level: the coarsest level among the active cells holding it, where it is
+// not on the refinement edge.
+struct LsLevel {
+  std::unique_ptr<OpLevel> op;          // refinement edge and boundary constrained: the smoother's operator
+  std::unique_ptr<OpLevel> full;        // boundary constrained only: residual rows on the edge, transfers
+  Transfer down;                        // this level (fine) <-> the next coarser level
+  DevBuf copy_fine, copy_lvl;           // owned DoFs: fine node id, level node id
+  int64_t n_copy = 0;
+  Workspace ws[2];                      // b defect, x iterate, r residual, t product, d smoother direction
+  DevBuf z[2], c[2];                    // smoother right-hand side; restricted contribution / correction
+};
+struct LocalSmoothing {
+  std::unique_ptr<Problem> base;        // level 0 and below: the base mesh's global-coarsening hierarchy
+  std::vector<std::unique_ptr<LsLevel>> lv;  // lv[l - 1]: refinement level l
+  DevBuf copy_fine, copy_lvl;           // DoFs owned by level 0
+  int64_t n_copy = 0;
+  DevBuf b[2], x[2], c[2];              // level-0 defect, iterate, restricted contribution
+};
+// Multigrid levels as seen by the API (information, smoother bounds): global coarsening: `levels`;
+// local smoothing: the refined levels finest first, then the base hierarchy.
+int mg_level_count(const Problem& p);
+OpLevel& mg_level(Problem& p, int i);
+
 // Build everything for a mesh and a description; throws Error.
+// hierarchy: 0 global coarsening, 1 local smoothing (vector Laplacian and the Stokes A block on a
+// locally refined mesh; an unrefined mesh needs none and gets global coarsening)
 std::unique_ptr<Problem> build_problem(const Forest& f, int kind, int k, const Physics& ph, int mg_order,
-                                       int coarse_stop_n, Budget* bud);
+                                       int coarse_stop_n, Budget* bud, int hierarchy = 0);
+// the level workspaces alone (r, d, t, b, x per level and precision)
+void alloc_level_workspaces(Problem& p);
 
 // Multigrid
 void smooth(Problem& p, int level, int prec, const void* b, void* x, bool x_is_zero, cudaStream_t s);

@@ -9,6 +9,7 @@
 // coarse system is larger than 4096 unknowns.  FGMRES(m) with classical
 // Gram--Schmidt applied twice (Section 3 "We solve the Stokes system with FGMRES").
 #include <algorithm>
+#include <array>
 #include <atomic>
 #include <map>
 #include <mutex>
@@ -49,9 +50,13 @@ Problem::~Problem() {
 }
 
 static std::atomic<uint64_t> g_problem_uid{0};
+static int64_t sys_of_n(const Problem& p) { return p.system ? p.system->n_dofs : p.levels[0]->n_dofs; }
+
+static void build_local_smoothing(Problem& p, const Forest& f, int k, const Physics& ph, int mg_order,
+                                  int coarse_stop_n, Budget* bud);
 
 std::unique_ptr<Problem> build_problem(const Forest& f, int kind, int k, const Physics& ph, int mg_order,
-                                       int coarse_stop_n, Budget* bud) {
+                                       int coarse_stop_n, Budget* bud, int hierarchy) {
   auto p = std::make_unique<Problem>();
   p->uid = ++g_problem_uid;
   p->kind = kind;
@@ -63,8 +68,11 @@ std::unique_ptr<Problem> build_problem(const Forest& f, int kind, int k, const P
   if (mg_order == 0) mg_order = kind == 2 ? 2 : 1;
   // (forest, degree) sequence of the hierarchy, finest first
   std::vector<std::pair<Forest, int>> seq;
-  if (kind == 3) {
-    seq.push_back({f, k});
+  const bool local = hierarchy == 1 && f.max_level() > 0;
+  if (hierarchy == 1 && mop != OP_STOKES_A)
+    throw Error(kErrUnsupported, "local smoothing is built for the vector Laplacian and the Stokes A block");
+  if (kind == 3 || local) {
+    seq.push_back({f, k});  // local smoothing: the fine operator only; the levels live in p->ls
   } else {
     std::vector<Forest> fs{f};
     while (forest_can_coarsen(fs.back(), coarse_stop_n)) fs.push_back(forest_coarsen(fs.back()));
@@ -93,7 +101,89 @@ std::unique_ptr<Problem> build_problem(const Forest& f, int kind, int k, const P
     p->pmass = std::make_unique<OpLevel>();
     build_oplevel(*p->pmass, f, OP_PMASS, k - 1, ph, bud);
   }
+  if (local) build_local_smoothing(*p, f, k, ph, mg_order, coarse_stop_n, bud);
   return p;
+}
+
+static void level_copy_list(const OpLevel& fine, const OpLevel& lvl, int l, const std::vector<uint8_t>& edge,
+                            std::vector<int32_t>& owner, std::vector<int32_t>& cf, std::vector<int32_t>& cl) {
+  std::string err;
+  if (!ls_owned_nodes(fine.forest, fine.nu, lvl.forest, lvl.nu, edge, l, owner, cf, cl, &err))
+    throw Error(kErrArg, "local smoothing: " + err);
+}
+
+static void build_local_smoothing(Problem& p, const Forest& f, int k, const Physics& ph, int mg_order,
+                                  int coarse_stop_n, Budget* bud) {
+  auto S = std::make_unique<LocalSmoothing>();
+  const OpLevel& fine = *p.levels[0];
+  const int L = f.max_level();
+  // level 0 and below: the base mesh with its own global-coarsening hierarchy (vector Laplacian)
+  Forest base = forest_uniform(f.dim, f.n);
+  S->base = build_problem(base, 1, k, ph, mg_order, coarse_stop_n, bud, 0);
+  std::vector<int32_t> owner(fine.nu.n_nodes, -1);
+  std::vector<int32_t> cf, cl;
+  {
+    const OpLevel& b0 = *S->base->levels[0];
+    level_copy_list(fine, b0, 0, std::vector<uint8_t>(b0.nu.n_nodes, 0), owner, cf, cl);
+    S->n_copy = (int64_t)cf.size();
+    S->copy_fine = upload(bud, cf);
+    S->copy_lvl = upload(bud, cl);
+  }
+  const int64_t cap = sys_of_n(p);
+  for (int l = 1; l <= L; ++l) {
+    auto lv = std::make_unique<LsLevel>();
+    const Forest lf = forest_level(f, l);
+    lv->op = std::make_unique<OpLevel>();
+    build_oplevel(*lv->op, lf, OP_STOKES_A, k, ph, bud, true);
+    lv->full = std::make_unique<OpLevel>();
+    build_oplevel(*lv->full, lf, OP_STOKES_A, k, ph, bud, false);
+    if (lv->op->n_dofs != lv->full->n_dofs || lv->op->perm != lv->full->perm)
+      throw Error(kErrArg, "local smoothing: level operators disagree on the numbering");
+    if (lv->op->n_dofs > cap) throw Error(kErrUnsupported, "local smoothing: level larger than the fine system");
+    const OpLevel& coarse = l == 1 ? *S->base->levels[0] : *S->lv.back()->full;
+    build_transfer(lv->down, *lv->full, coarse, bud, true);
+    const std::vector<uint8_t> edge = refinement_edge(lf, lv->full->nu);
+    cf.clear();
+    cl.clear();
+    level_copy_list(fine, *lv->full, l, edge, owner, cf, cl);
+    lv->n_copy = (int64_t)cf.size();
+    lv->copy_fine = upload(bud, cf);
+    lv->copy_lvl = upload(bud, cl);
+    for (int prec = 0; prec < 2; ++prec) {
+      const size_t b = lv->op->n_dofs * esize(prec);
+      Workspace& w = lv->ws[prec];
+      w.r.alloc(bud, b);
+      w.d.alloc(bud, b);
+      w.t.alloc(bud, b);
+      w.b.alloc(bud, b);
+      w.x.alloc(bud, b);
+      lv->z[prec].alloc(bud, b);
+      lv->c[prec].alloc(bud, b);
+    }
+    S->lv.push_back(std::move(lv));
+  }
+  // every free fine node has exactly one owner
+  if (!ls_all_owned(fine.nu, owner)) throw Error(kErrArg, "local smoothing: a free fine DoF is owned by no level");
+  for (int prec = 0; prec < 2; ++prec) {
+    const size_t b = S->base->levels[0]->n_dofs * esize(prec);
+    S->b[prec].alloc(bud, b);
+    S->x[prec].alloc(bud, b);
+    S->c[prec].alloc(bud, b);
+  }
+  alloc_level_workspaces(*S->base);
+  p.ls = std::move(S);
+}
+
+int mg_level_count(const Problem& p) {
+  if (!p.ls) return (int)p.levels.size();
+  return (int)(p.ls->lv.size() + p.ls->base->levels.size());
+}
+
+OpLevel& mg_level(Problem& p, int i) {
+  if (!p.ls) return *p.levels.at(i);
+  const int nl = (int)p.ls->lv.size();
+  if (i < nl) return *p.ls->lv[nl - 1 - i]->op;
+  return *p.ls->base->levels.at(i - nl);
 }
 
 static OpLevel& sys_of(Problem& p) { return p.system ? *p.system : *p.levels[0]; }
@@ -118,7 +208,7 @@ struct TimerPause {
   }
 };
 
-void alloc_workspaces(Problem& p) {
+void alloc_level_workspaces(Problem& p) {
   Budget* bud = p.bud;
   for (int prec = 0; prec < 2; ++prec) {
     p.ws[prec].clear();
@@ -133,6 +223,11 @@ void alloc_workspaces(Problem& p) {
       w.x.alloc(bud, b);
     }
   }
+}
+
+void alloc_workspaces(Problem& p) {
+  Budget* bud = p.bud;
+  alloc_level_workspaces(p);
   OpLevel& S = sys_of(p);
   const int64_t n = S.n_dofs;
   const int m = p.restart;
@@ -202,6 +297,16 @@ void autotune(Problem& p, cudaStream_t s) {
       MFNS_CUDA(cudaMemsetAsync(w.x.get(), 0, p.levels[l]->n_dofs * esize(prec), s));
       autotune_warps(p.levels[l]->L, prec, w.x.get(), w.t.get(), p.levels[l]->n_dofs, s);
     }
+  if (p.ls) {
+    for (auto& lv : p.ls->lv)
+      for (int prec = 0; prec < 2; ++prec) {
+        Workspace& w = lv->ws[prec];
+        MFNS_CUDA(cudaMemsetAsync(w.x.get(), 0, lv->op->n_dofs * esize(prec), s));
+        autotune_warps(lv->op->L, prec, w.x.get(), w.t.get(), lv->op->n_dofs, s);
+        autotune_warps(lv->full->L, prec, w.x.get(), w.t.get(), lv->full->n_dofs, s);
+      }
+    autotune(*p.ls->base, s);
+  }
   for (OpLevel* lv : {p.system.get(), p.pmass.get()}) {
     if (!lv) continue;
     for (int prec = 0; prec < 2; ++prec) {
@@ -214,7 +319,31 @@ void autotune(Problem& p, cudaStream_t s) {
   }
 }
 
+static void sync_ls_settings(Problem& p) {
+  Problem& B = *p.ls->base;
+  B.smoother = p.smoother;
+  B.smoother_degree = p.smoother_degree;
+  B.mg_precision = p.mg_precision;
+  B.fused_smoother = p.fused_smoother;
+  B.coarse_cheby_degree = p.coarse_cheby_degree;
+}
+
 void estimate_lambda(Problem& p, cudaStream_t s) {
+  if (p.ls) {  // the levels the cycle smooths on: refined levels and the base hierarchy
+    sync_ls_settings(p);
+    const int nl = mg_level_count(p);
+    for (int i = 0; i < nl; ++i) level_dinv(p, mg_level(p, i), s);
+    for (int i = 0; i < nl; ++i) {
+      OpLevel& lv = mg_level(p, i);
+      if (lv.lmax > 0) continue;
+      if (lv.n_dofs > sys_of(p).n_dofs) throw Error(kErrUnsupported, "multigrid level larger than the system");
+      std::vector<std::complex<double>> ritz;
+      const double rho = arnoldi_spectral_radius(p, lv, s, &ritz);
+      const double w = p.smoother == 1 ? relaxation_weight(ritz) : 0.0;
+      lv.lmax = p.smoother != 1 ? 1.2 * rho : (w > 0.0 && std::isfinite(w)) ? 2.0 / (1.05 * w) : 2.0 * rho;
+    }
+    return;
+  }
   // diagonals, then the Arnoldi estimate of lambda_max(D^{-1} A) per level
   for (auto& lv : p.levels) level_dinv(p, *lv, s);
   if (p.kind == 0) {
@@ -345,6 +474,7 @@ static bool invert_dense(std::vector<double>& A, int64_t n) {
 }
 
 void setup_coarse(Problem& p, cudaStream_t s) {
+  if (p.ls) return setup_coarse(*p.ls->base, s);
   OpLevel& cl = *p.levels.back();
   const int64_t n = cl.n_dofs;
   p.coarse_n = n;
@@ -387,9 +517,8 @@ void setup_coarse(Problem& p, cudaStream_t s) {
 
 // ---------------------------------------------------------------------- smoothing
 template <typename T>
-static void smooth_t(Problem& p, int level, int prec, const T* b, T* x, bool x_is_zero, int degree, cudaStream_t s) {
-  OpLevel& lv = *p.levels[level];
-  Workspace& w = p.ws[prec][level];
+static void smooth_op(const Problem& p, OpLevel& lv, Workspace& w, int prec, const T* b, T* x, bool x_is_zero,
+                      int degree, cudaStream_t s) {
   const int64_t n = lv.n_dofs;
   const T* dinv = lv.dinv[prec].as<T>();
   T* d = w.d.as<T>();
@@ -435,6 +564,11 @@ static void smooth_t(Problem& p, int level, int prec, const T* b, T* x, bool x_i
   if (cur != x) vcopy<T>(x, cur, n, s);
 }
 
+template <typename T>
+static void smooth_t(Problem& p, int level, int prec, const T* b, T* x, bool x_is_zero, int degree, cudaStream_t s) {
+  smooth_op<T>(p, *p.levels[level], p.ws[prec][level], prec, b, x, x_is_zero, degree, s);
+}
+
 void smooth(Problem& p, int level, int prec, const void* b, void* x, bool x_is_zero, cudaStream_t s) {
   if (prec == 0)
     smooth_t<double>(p, level, 0, (const double*)b, (double*)x, x_is_zero, p.smoother_degree, s);
@@ -476,11 +610,80 @@ static void vcycle_level(Problem& p, int prec, int l, const T* b, T* x, cudaStre
   smooth_t<T>(p, l, prec, b, x, false, p.smoother_degree, s);
 }
 
+// Local-smoothing cycle (Section 2).  The fine defect b is copied to the level that owns each
+// DoF.  Down the levels: smooth from zero on the level's cells with the refinement edge held at
+// zero, form the level residual with the unconstrained-edge operator (its edge rows carry the
+// correction's effect on the coarser level), restrict it and add it to the coarser defect.  Level 0
+// runs the base hierarchy's V-cycle.  Up the levels: prolongate the coarser iterate (which sets
+// the edge values), form the residual with those edge values, smooth the correction from zero and
+// add it.  The fine result is copied back from the owning levels; constrained entries stay zero.
+template <typename T>
+static void ls_vcycle(Problem& p, int prec, const T* b, T* x, cudaStream_t s) {
+  LocalSmoothing& S = *p.ls;
+  sync_ls_settings(p);
+  const int nc = p.levels[0]->NU;
+  const int L = (int)S.lv.size();
+  Problem& B = *S.base;
+  const OpLevel& b0 = *B.levels[0];
+  T* bl0 = S.b[prec].as<T>();
+  MFNS_CUDA(cudaMemsetAsync(bl0, 0, b0.n_dofs * sizeof(T), s));
+  vcopy_map<T>(bl0, S.copy_lvl.as<int32_t>(), b, S.copy_fine.as<int32_t>(), S.n_copy, nc, s);
+  for (auto& lv : S.lv) {
+    T* bl = lv->ws[prec].b.as<T>();
+    MFNS_CUDA(cudaMemsetAsync(bl, 0, lv->op->n_dofs * sizeof(T), s));
+    vcopy_map<T>(bl, lv->copy_lvl.as<int32_t>(), b, lv->copy_fine.as<int32_t>(), lv->n_copy, nc, s);
+  }
+  for (int l = L; l >= 1; --l) {
+    LsLevel& lv = *S.lv[l - 1];
+    Workspace& w = lv.ws[prec];
+    const int64_t n = lv.op->n_dofs;
+    T* z = lv.z[prec].as<T>();
+    vcopy<T>(z, w.b.as<T>(), n, s);
+    vset_idx<T>(z, T(0), lv.op->constrained.as<int32_t>(), (int64_t)lv.op->constrained_host.size(), s);
+    smooth_op<T>(p, *lv.op, w, prec, z, w.x.as<T>(), true, p.smoother_degree, s);
+    oplevel_vmult(*lv.full, prec, w.x.get(), w.t.get(), s);
+    vsub<T>(w.r.as<T>(), w.b.as<T>(), w.t.as<T>(), n, s);
+    const OpLevel& coarse = l == 1 ? b0 : *S.lv[l - 2]->full;
+    T* cb = l == 1 ? bl0 : S.lv[l - 2]->ws[prec].b.as<T>();
+    T* cc = l == 1 ? S.c[prec].as<T>() : S.lv[l - 2]->c[prec].as<T>();
+    transfer_restrict(lv.down, *lv.full, coarse, prec, w.r.get(), cc, s);
+    vaxpy<T>(cb, T(1), cc, coarse.n_dofs, s);
+  }
+  vcycle_level<T>(B, prec, 0, bl0, S.x[prec].as<T>(), s);
+  for (int l = 1; l <= L; ++l) {
+    LsLevel& lv = *S.lv[l - 1];
+    Workspace& w = lv.ws[prec];
+    const int64_t n = lv.op->n_dofs;
+    const OpLevel& coarse = l == 1 ? b0 : *S.lv[l - 2]->full;
+    const void* xc = l == 1 ? S.x[prec].get() : S.lv[l - 2]->ws[prec].x.get();
+    transfer_prolongate_add(lv.down, *lv.full, coarse, prec, xc, w.x.get(), s);
+    oplevel_vmult(*lv.full, prec, w.x.get(), w.t.get(), s);
+    vsub<T>(w.r.as<T>(), w.b.as<T>(), w.t.as<T>(), n, s);
+    vset_idx<T>(w.r.as<T>(), T(0), lv.op->constrained.as<int32_t>(), (int64_t)lv.op->constrained_host.size(), s);
+    T* dlt = lv.c[prec].as<T>();
+    smooth_op<T>(p, *lv.op, w, prec, w.r.as<T>(), dlt, true, p.smoother_degree, s);
+    vaxpy<T>(w.x.as<T>(), T(1), dlt, n, s);
+  }
+  MFNS_CUDA(cudaMemsetAsync(x, 0, p.levels[0]->n_dofs * sizeof(T), s));
+  vcopy_map<T>(x, S.copy_fine.as<int32_t>(), S.x[prec].as<T>(), S.copy_lvl.as<int32_t>(), S.n_copy, nc, s);
+  for (auto& lv : S.lv)
+    vcopy_map<T>(x, lv->copy_fine.as<int32_t>(), lv->ws[prec].x.as<T>(), lv->copy_lvl.as<int32_t>(), lv->n_copy, nc, s);
+}
+
+// one multigrid cycle on the problem's hierarchy (global coarsening or local smoothing)
+template <typename T>
+static void mg_cycle(Problem& p, int prec, const T* b, T* x, cudaStream_t s) {
+  if (p.ls)
+    ls_vcycle<T>(p, prec, b, x, s);
+  else
+    vcycle_level<T>(p, prec, 0, b, x, s);
+}
+
 void vcycle(Problem& p, int prec, const void* b, void* x, cudaStream_t s) {
   if (prec == 0)
-    vcycle_level<double>(p, 0, 0, (const double*)b, (double*)x, s);
+    mg_cycle<double>(p, 0, (const double*)b, (double*)x, s);
   else
-    vcycle_level<float>(p, 1, 0, (const float*)b, (float*)x, s);
+    mg_cycle<float>(p, 1, (const float*)b, (float*)x, s);
 }
 
 // ---------------------------------------------------------------------- FGMRES
@@ -540,7 +743,7 @@ static void stokes_block(Problem& p, int prec, const T* r, T* z, cudaStream_t s)
   oplevel_vmult(S, prec, full, Bz, s);
   // velocity rhs r_u - B z_p, then one V-cycle on the A block
   vsub<T>(Bz, r, Bz, nu, s);
-  vcycle_level<T>(p, prec, 0, Bz, z, s);
+  mg_cycle<T>(p, prec, Bz, z, s);
 }
 
 static void precondition_body(Problem& p, const double* v, double* z, cudaStream_t s);
@@ -602,13 +805,13 @@ static void precondition_body(Problem& p, const double* v, double* z, cudaStream
     if (p.kind == 0)
       stokes_block<double>(p, 0, v, z, s);
     else
-      vcycle_level<double>(p, 0, 0, v, z, s);
+      mg_cycle<double>(p, 0, v, z, s);
   } else {
     vcast_d2f(p.mg_b32.as<float>(), v, n, s);
     if (p.kind == 0)
       stokes_block<float>(p, 1, p.mg_b32.as<float>(), p.mg_x32.as<float>(), s);
     else
-      vcycle_level<float>(p, 1, 0, p.mg_b32.as<float>(), p.mg_x32.as<float>(), s);
+      mg_cycle<float>(p, 1, p.mg_b32.as<float>(), p.mg_x32.as<float>(), s);
     vcast_f2d(z, p.mg_x32.as<float>(), n, s);
   }
 }
@@ -945,7 +1148,7 @@ NewtonResult bdf_step(Problem& p, const NewtonParams& np, const double* u_n, con
 
 // ---------------------------------------------------------------------- batched V-cycles (D6)
 bool batchable(const Problem& p) {
-  if ((p.kind != 1 && p.kind != 2) || p.fused_smoother || !p.use_graphs) return false;
+  if ((p.kind != 1 && p.kind != 2) || p.fused_smoother || !p.use_graphs || p.ls) return false;
   for (auto& l : p.levels)
     if (!l->L.structured) return false;
   return true;

@@ -231,9 +231,9 @@ __global__ void __launch_bounds__(128) transfer_kernel(const TransferArgs<T, NF,
 }
 
 // ------------------------------------------------------------------------ host side
-void build_transfer(Transfer& t, const OpLevel& fine, const OpLevel& coarse, Budget* bud) {
+void build_transfer(Transfer& t, const OpLevel& fine, const OpLevel& coarse, Budget* bud, bool allow_unrefined) {
   const int dim = fine.dim;
-  if (build_separable(t.sep, fine, coarse, bud)) {  // uniform -> uniform: tensor-product stencils
+  if (!allow_unrefined && build_separable(t.sep, fine, coarse, bud)) {  // uniform -> uniform: tensor-product stencils
     t.separable = true;
     t.dim = dim;
     t.kf = fine.k;
@@ -288,6 +288,7 @@ void build_transfer(Transfer& t, const OpLevel& fine, const OpLevel& coarse, Bud
       for (int ch = 0; ch < nch; ++ch) {
         const int64_t cx = 2 * x + (ch & 1), cy = 2 * y + ((ch >> 1) & 1), cz = dim == 3 ? 2 * z + ((ch >> 2) & 1) : 0;
         auto it = fmap.find(key(uniform_step ? 0 : l + 1, cx, cy, cz));
+        if (it == fmap.end() && allow_unrefined && ch == 0) break;  // not refined: no children (-1)
         if (it == fmap.end()) throw Error(kErrArg, "h-transfer: coarse cell neither kept nor refined once");
         child[i * nch + ch] = fpos[it->second];
         code[i * nch + ch] = (uint8_t)ch;
