@@ -187,7 +187,7 @@ static OpLevel* select_op(mfns_problem* p, int which) {
   Problem& P = *p->p;
   if (which == MFNS_OP_SYSTEM) return P.system ? P.system.get() : P.levels[0].get();
   if (which == MFNS_OP_PMASS) return P.pmass ? P.pmass.get() : nullptr;
-  if (which >= 0 && which < (int)P.levels.size()) return P.levels[which].get();
+  if (which >= 0 && which < mg_level_count(P)) return &mg_level(P, which);
   return nullptr;
 }
 

@@ -329,6 +329,12 @@ static void sync_ls_settings(Problem& p) {
 }
 
 void estimate_lambda(Problem& p, cudaStream_t s) {
+  if (p.kind == 0) {  // Stokes: the pressure mass diagonal of the Schur-complement CG
+    OpLevel& pm = *p.pmass;
+    oplevel_diag(pm, 0, pm.dinv[0].get(), s);
+    vrecip<double>(pm.dinv[0].as<double>(), pm.dinv[0].as<double>(), pm.n_dofs, s);
+    vcast_d2f(pm.dinv[1].as<float>(), pm.dinv[0].as<double>(), pm.n_dofs, s);
+  }
   if (p.ls) {  // the levels the cycle smooths on: refined levels and the base hierarchy
     sync_ls_settings(p);
     const int nl = mg_level_count(p);
@@ -346,12 +352,6 @@ void estimate_lambda(Problem& p, cudaStream_t s) {
   }
   // diagonals, then the Arnoldi estimate of lambda_max(D^{-1} A) per level
   for (auto& lv : p.levels) level_dinv(p, *lv, s);
-  if (p.kind == 0) {
-    OpLevel& pm = *p.pmass;
-    oplevel_diag(pm, 0, pm.dinv[0].get(), s);
-    vrecip<double>(pm.dinv[0].as<double>(), pm.dinv[0].as<double>(), pm.n_dofs, s);
-    vcast_d2f(pm.dinv[1].as<float>(), pm.dinv[0].as<double>(), pm.n_dofs, s);
-  }
   // lambda_max of D^{-1} A per level: Arnoldi (classical Gram--Schmidt twice) in FP64 from a
   // seeded random start; the estimate is the spectral radius rho of the m x m Hessenberg matrix
   // (the modulus of its largest Ritz value), times 1.2 for the Chebyshev smoother.  The

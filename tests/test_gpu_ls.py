@@ -81,7 +81,7 @@ def test_ls_cycle_matches_oracle(ctx, case, smoother):
     info = prob.info
     for i in range(len(lm_ls)):           # the refined levels are the oracle's level cell sets
         assert info.level_cells[i] == len(orc.levels[len(lm_ls) - 1 - i].space.cells)
-    perm = _perm(prob, 0, op)
+    perm = _perm(prob, L.OP_SYSTEM, op)          # the fine operator (level indices name cycle levels)
     b = inputs.uniform_vector(op.dofs.n_dofs, seed=7) * op.dofs.free
     x = torch.zeros(len(b), dtype=torch.float64, device="cuda")
     prob.vcycle(_to_gpu(b, perm), x)
