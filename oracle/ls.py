@@ -24,7 +24,9 @@ its embedding P_l (nodal interpolation at the free fine DoFs).  One cycle:
 with r = b - A x updated after every correction and S_l the level smoother
 (Chebyshev or relaxation around point Jacobi, ``solvers``) on
 A_l = P_l^T A P_l, extended by identity rows on the level's edge and boundary
-nodes.  For the vector Laplacian the Galerkin product equals the operator
+nodes.  The constrained (Dirichlet and hanging) rows of A are identity rows
+and lie outside every level space: the cycle inverts them exactly, x = b on
+those rows.  For the vector Laplacian the Galerkin product equals the operator
 assembled on the level mesh with Dirichlet conditions on the refinement edge
 (same bilinear form, exact quadrature); the tests pin that.
 
@@ -184,4 +186,6 @@ class LocalSmoothing:
         for lv in self.levels:                            # post-smoothing, coarsest part first
             x = x + lv.P @ self._smooth(lv, lv.P.T @ r)
             r = b - A @ x
+        con = self.problem.dofs.constrained               # identity rows of A
+        x[con] = b[con]
         return x

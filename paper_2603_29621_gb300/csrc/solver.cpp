@@ -668,6 +668,9 @@ static void ls_vcycle(Problem& p, int prec, const T* b, T* x, cudaStream_t s) {
   vcopy_map<T>(x, S.copy_fine.as<int32_t>(), S.x[prec].as<T>(), S.copy_lvl.as<int32_t>(), S.n_copy, nc, s);
   for (auto& lv : S.lv)
     vcopy_map<T>(x, lv->copy_fine.as<int32_t>(), lv->ws[prec].x.as<T>(), lv->copy_lvl.as<int32_t>(), lv->n_copy, nc, s);
+  // the constrained (Dirichlet, hanging) rows are identity rows outside every level: inverted exactly
+  const OpLevel& f0 = *p.levels[0];
+  vcopy_idx<T>(x, b, f0.constrained.as<int32_t>(), (int64_t)f0.constrained_host.size(), s);
 }
 
 // one multigrid cycle on the problem's hierarchy (global coarsening or local smoothing)
