@@ -28,6 +28,10 @@ assembly, no sum factorisation):
 * ``ls``        -- local-smoothing multigrid (Section 2): level spaces on the
                    refined parts of the mesh with Dirichlet conditions on the
                    refinement edge, as a multiplicative subspace correction.
+* ``hp``        -- hp-adaptive continuous spaces (a degree per cell, h- and
+                   p-hanging constraints), the vector Laplacian and Taylor--Hood
+                   Stokes on them, hp transfers and the hp-multigrid hierarchy
+                   (degrees lowered one by one, then h; Section 3).
 
 Parity status: every function here is pinned by tests against closed forms,
 textbook values, invariants or brute force (see ``tests/test_oracle_*.py``);

@@ -1,0 +1,201 @@
+"""Pins of the oracle's hp-adaptive spaces and hp-multigrid (Section 3).
+
+* With one degree everywhere the hp space, its constraints and its operator are the oracle's
+  standard ones.
+* Conformity, checked independently of the constraint construction: for random free values, the
+  traces of the two cells on every shared face piece agree (h- and p-interfaces, 2D and 3D).
+* Dimension: the number of free DoFs equals the dimension of the conforming space computed by brute
+  force (rank of the continuity and boundary conditions on the broken space).
+* The interpolant of a polynomial of the lowest degree present lies in the space, and its energy is
+  the closed-form nu * int |grad u|^2.
+* hp transfers are exact for polynomials of the coarse space.
+* hp-multigrid (degrees lowered one by one, then h) as an FGMRES preconditioner converges.
+* The configuration the construction does not cover is rejected.
+"""
+import numpy as np
+import pytest
+
+from oracle import assemble, fe, hp, mesh, solvers
+
+
+def _ball(dim, n, levels):
+    return mesh.refine_ball(mesh.uniform(dim, n), (0.3, 0.35, 0.4), 0.3, levels)
+
+
+def _degrees(f, base, vary=True):
+    """base + refinement level (+ parity of the root cell's x index): finer cells never have a lower
+    degree than a coarser neighbour, and same-level neighbours may differ by one."""
+    lev = f.cells[:, 0]
+    root_x = f.cells[:, 1] >> lev
+    return base + lev + ((root_x % 2) if vary else 0)
+
+
+def _face_pieces(f):
+    """(A, B, points) for every pair of cells sharing a piece of a face: GLL points of degree 5 on
+    the piece (enough to identify traces of degree <= 5)."""
+    N, cell_at = f.lattice()
+    dim = f.dim
+    h = f.h()
+    org = f.origin()
+    out = []
+    x5 = fe.gll_points(5)
+    for a in range(f.n_cells):
+        for d in range(dim):
+            for side in (0, 1):
+                plane = org[a, d] + side * h[a]
+                if plane <= 1e-12 or plane >= 1 - 1e-12:
+                    continue
+                # lattice cells just across the face
+                lo = np.rint(org[a] * N).astype(int)
+                hi = np.rint((org[a] + h[a]) * N).astype(int)
+                sl = [slice(lo[j], hi[j]) for j in range(dim)]
+                q = int(round(plane * N))
+                sl[d] = slice(q, q + 1) if side else slice(q - 1, q)
+                for b in np.unique(cell_at[tuple(sl)]):
+                    # shared piece: intersection of the two face boxes
+                    lo_s = np.maximum(org[a], org[b])
+                    hi_s = np.minimum(org[a] + h[a], org[b] + h[b])
+                    tang = [j for j in range(dim) if j != d]
+                    grids = np.meshgrid(*[lo_s[j] + (hi_s[j] - lo_s[j]) * x5 for j in tang], indexing="ij")
+                    pts = np.zeros((grids[0].size, dim))
+                    for j, g in zip(tang, grids):
+                        pts[:, j] = g.ravel()
+                    pts[:, d] = plane
+                    out.append((a, int(b), pts))
+    return out
+
+
+def test_uniform_degree_is_the_standard_space():
+    for dim, n, levels, k in [(2, 3, 2, 2), (2, 2, 1, 3), (3, 2, 1, 2)]:
+        f = _ball(dim, n, levels)
+        H = hp.HpProblem(f, np.full(f.n_cells, k), "stokes_a", nu=0.6)
+        S = assemble.Problem(f, "stokes_a", k, nu=0.6)
+        xh, fh = H.dofs.support_points()
+        xs, fs = S.dofs.support_points()
+        key = {(tuple(np.rint(x * 2 ** 30).astype(np.int64)), c): i for i, (x, c) in enumerate(zip(xs, fs))}
+        perm = np.array([key[(tuple(np.rint(x * 2 ** 30).astype(np.int64)), c)] for x, c in zip(xh, fh)])
+        assert len(perm) == len(xs) and len(set(perm.tolist())) == len(perm)
+        assert np.array_equal(H.dofs.constrained, S.dofs.constrained[perm])
+        Ah, As = H.assemble(), S.assemble()[perm][:, perm]
+        assert abs(Ah - As).max() <= 1e-13 * abs(As).max()
+
+
+@pytest.mark.parametrize("dim,n,levels,base", [(2, 3, 2, 1), (2, 4, 1, 2), (3, 2, 1, 1), (3, 3, 1, 2)])
+def test_traces_agree_on_every_interface(dim, n, levels, base):
+    f = _ball(dim, n, levels)
+    deg = _degrees(f, base)
+    assert len(np.unique(deg)) >= 2
+    P = hp.HpProblem(f, deg, "stokes_a")
+    d = P.dofs
+    assert d.hanging.any()
+    rng = np.random.default_rng(1)
+    x = d.distribute(rng.uniform(-1, 1, d.n_dofs))
+    pieces = _face_pieces(f)
+    p_faces = sum(1 for a, b, _ in pieces if deg[a] != deg[b] and f.cells[a, 0] == f.cells[b, 0])
+    h_faces = sum(1 for a, b, _ in pieces if f.cells[a, 0] != f.cells[b, 0])
+    assert p_faces > 0 and h_faces > 0
+    worst = 0.0
+    for a, b, pts in pieces:
+        for comp in range(dim):
+            ua = P.evaluate_in(x, pts, np.full(len(pts), a), 0, comp)
+            ub = P.evaluate_in(x, pts, np.full(len(pts), b), 0, comp)
+            worst = max(worst, np.abs(ua - ub).max())
+    assert worst <= 1e-12
+
+
+@pytest.mark.parametrize("dim,n,levels,base", [(2, 2, 1, 1), (2, 3, 1, 2), (3, 2, 1, 1)])
+def test_dimension_equals_brute_force_rank(dim, n, levels, base):
+    f = _ball(dim, n, levels)
+    deg = _degrees(f, base)
+    ns = hp.HpNodeSet(f, deg)
+    free = ~ns.boundary
+    free[list(ns.hanging)] = False
+    # broken space: every cell's own nodal values; continuity on every shared face piece and zero
+    # boundary traces as linear conditions
+    offs = np.cumsum([0] + [(int(k) + 1) ** dim for k in deg])
+    rows = []
+    h, org = f.h(), f.origin()
+
+    def basis(c, pts):
+        xi = np.clip((pts - org[c]) / h[c], 0.0, 1.0)
+        return fe.eval_basis_at(dim, int(deg[c]), xi)
+
+    for a, b, pts in _face_pieces(f):
+        G = np.zeros((len(pts), offs[-1]))
+        G[:, offs[a]:offs[a + 1]] = basis(a, pts)
+        G[:, offs[b]:offs[b + 1]] -= basis(b, pts)
+        rows.append(G)
+    for c in range(f.n_cells):                       # boundary nodes of every cell vanish
+        loc = fe.tensor_index(dim, int(deg[c]) + 1)
+        on = ((loc == 0) & (org[c] <= 1e-12)[None]) | ((loc == deg[c]) & (org[c] + h[c] >= 1 - 1e-12)[None])
+        for i in np.nonzero(on.any(axis=1))[0]:
+            r = np.zeros((1, offs[-1]))
+            r[0, offs[c] + i] = 1.0
+            rows.append(r)
+    G = np.concatenate(rows)
+    dim_space = offs[-1] - np.linalg.matrix_rank(G, tol=1e-9)
+    assert dim_space == int(free.sum())
+
+
+@pytest.mark.parametrize("dim,n,levels", [(2, 3, 1), (3, 2, 1)])
+def test_polynomial_energy(dim, n, levels):
+    f = _ball(dim, n, levels)
+    deg = _degrees(f, 2)                             # lowest degree 2: x(1-x) y(1-y) ... is in the space
+    nu = 0.7
+    P = hp.HpProblem(f, deg, "stokes_a", nu=nu)
+
+    def u(x):
+        phi = np.prod(x * (1 - x), axis=1)
+        return np.stack([(c + 1) * phi for c in range(dim)], axis=1)
+
+    xv = P.dofs.interpolate(u)
+    assert np.abs(P.dofs.distribute(xv) - xv).max() <= 1e-14
+    energy = xv @ (P.assemble_K() @ xv)              # = x_free^T (C^T K C) x_free
+    free = P.dofs.free_ids
+    A = P.assemble()
+    assert abs(xv[free] @ (A[free][:, free] @ xv[free]) - energy) <= 1e-12 * energy
+    one_d = {2: 1.0 / 90.0 * 2, 3: 3 * (1.0 / 3.0) * (1.0 / 30.0) ** 2}[dim]   # int |grad phi|^2
+    exact = nu * one_d * sum((c + 1) ** 2 for c in range(dim))
+    assert abs(energy - exact) <= 1e-12 * exact
+
+
+def test_transfers_exact_for_coarse_polynomials():
+    f = _ball(2, 3, 1)
+    deg = _degrees(f, 3)                             # degrees 3..5 -> 2..4 on the next level
+    levels = hp.hierarchy(f, deg)
+    fine, coarse = levels[0].problem, levels[1].problem
+    assert (coarse.degrees == np.maximum(deg - 1, 1)).all()
+
+    def u(x):
+        phi = np.prod(x * (1 - x), axis=1)
+        return np.stack([phi, -2.0 * phi], axis=1)     # degree 2: in the coarse space (degrees >= 2)
+
+    got = levels[0].P @ coarse.dofs.interpolate(u)
+    exp = fine.dofs.interpolate(u) * fine.dofs.free
+    assert np.abs(got - exp).max() <= 1e-13
+    # restriction is the transpose
+    assert (levels[0].P.T - levels[0].P.T.tocsr()).nnz == 0
+
+
+@pytest.mark.parametrize("dim,n,levels,base", [(2, 4, 1, 2), (3, 2, 1, 2)])
+def test_hp_multigrid_preconditioner_converges(dim, n, levels, base):
+    f = _ball(dim, n, levels)
+    deg = _degrees(f, base)
+    lv = hp.hierarchy(f, deg)
+    assert lv[0].problem.degrees.max() >= 3 and lv[-1].problem.forest.n <= 2
+    lmax = [1.2 * solvers.power_lmax(l.A, l.dinv, iterations=60) for l in lv[:-1]]
+    V = solvers.VCycle(lv, lmax, ("chebyshev", 5))
+    A = lv[0].A
+    rng = np.random.default_rng(2)
+    d = lv[0].problem.dofs
+    xs = rng.uniform(-1, 1, d.n_dofs) * d.free
+    x, its, res = solvers.fgmres(A, A @ xs, V, tol=1e-10)
+    assert res <= 1e-10 and its <= 30
+    assert np.abs(x - xs).max() <= 1e-7
+
+
+def test_coarse_higher_degree_across_a_hanging_face_is_rejected():
+    f = _ball(2, 3, 1)
+    deg = 3 - f.cells[:, 0]                          # coarse cells 3, refined cells 2
+    with pytest.raises(NotImplementedError):
+        hp.HpNodeSet(f, deg)
