@@ -1,0 +1,37 @@
+// Host construction of hp-adaptive node spaces (Section 3): every cell of a forest carries its own
+// degree; nodes are identified exactly; the constraints of h- and p-adaptivity are resolved to
+// free masters.
+//
+// Constraint rule: a node is constrained when a cell whose closed box holds it does not have it
+// as a node and dominates every cell that does (it is coarser, or of the same level and of lower
+// degree); the node then takes that cell's finite-element function at its position.  Chains (a
+// master that is itself constrained) are resolved transitively, so every listed master is free
+// of hanging constraints.  This is a conforming space unless a hanging face has a coarse cell of
+// higher degree than a fine cell on it; that configuration is rejected.
+#pragma once
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "mesh.hpp"
+
+namespace mfns {
+
+struct HpSpace {
+  int dim = 3;
+  int64_t n_nodes = 0;
+  std::vector<int32_t> degree;       // per cell
+  std::vector<int64_t> cell_ptr;     // per cell: offset of its (k_c+1)^dim slots in cell_nodes
+  std::vector<int32_t> cell_nodes;   // node id of every slot (lexicographic, x fastest)
+  std::vector<double> x;             // n_nodes * dim support points
+  std::vector<uint8_t> boundary;     // node on the domain boundary
+  // constrained nodes: value = sum over j in [hang_ptr[i], hang_ptr[i+1]) of hang_w[j] * value of
+  // hang_master[j]; hang_node ascending
+  std::vector<int32_t> hang_node, hang_ptr, hang_master;
+  std::vector<double> hang_w;
+};
+
+// Builds the space; false with a message in err for an unsupported configuration or bad input.
+bool make_hp_space(const Forest& f, const std::vector<int32_t>& degree, HpSpace& out, std::string* err);
+
+}  // namespace mfns
