@@ -189,6 +189,10 @@ int mfns_mesh_uniform(mfns_ctx* ctx, int dim, int n, mfns_mesh** out);
  * then 2:1 closure over faces, edges and vertices.  centre[2] is ignored in 2D. */
 int mfns_mesh_refine_ball(mfns_mesh* mesh, const double centre[3], double radius, int levels);
 int mfns_mesh_info(const mfns_mesh* mesh, int64_t* n_cells, int* max_level);
+/* The active cells in the mesh's canonical order (the order of mfns_problem_create_hp's degree
+ * array): 4 int32 per cell -- level and the integer coordinates x, y, z at that level (z = 0 in
+ * 2D); writes up to cap cells to cells_host (may be NULL), the count to *n. */
+int mfns_mesh_cells(const mfns_mesh* mesh, int32_t* cells_host, int64_t cap, int64_t* n);
 int mfns_mesh_destroy(mfns_mesh* mesh);
 
 /* ---- problems ------------------------------------------------------------------------------ */
@@ -196,6 +200,17 @@ int mfns_mesh_destroy(mfns_mesh* mesh);
  * the dense coarse inverse and all workspaces.  The mesh may be destroyed afterwards. */
 int mfns_problem_create(mfns_ctx* ctx, const mfns_mesh* mesh, const mfns_problem_desc* desc,
                         mfns_problem** out);
+/* hp-adaptive vector Laplacian (Section 3): cell_degree[c] (1..4; host array of n_cells entries in
+ * the order of mfns_mesh_cells) is the degree of cell c.  A node is constrained when a cell whose
+ * closed box holds it does not have it as a node and dominates every cell that does (coarser, or
+ * same level and lower degree); it takes that cell's finite-element function at its position.
+ * The multigrid hierarchy lowers every degree by one per level until all cells are linear, then
+ * coarsens globally.  desc->kind must be MFNS_STOKES_A and desc->hierarchy 0
+ * (MFNS_ERR_UNSUPPORTED otherwise); a mesh on which a hanging face has a coarse cell of higher
+ * degree than a fine cell returns MFNS_ERR_UNSUPPORTED; one degree everywhere is the same as
+ * mfns_problem_create. */
+int mfns_problem_create_hp(mfns_ctx* ctx, const mfns_mesh* mesh, const mfns_problem_desc* desc,
+                           const int32_t* cell_degree, int64_t n_cells, mfns_problem** out);
 int mfns_problem_info(const mfns_problem* p, mfns_info* out);
 /* Support point (xyz_host[3*i..], z = 0 in 2D) and field (0..dim-1 velocity component,
  * dim pressure) of every entry of the vector of `which` (MFNS_OP_SYSTEM, MFNS_OP_PMASS

@@ -70,6 +70,9 @@ _SIGS = {
     "mfns_mesh_info": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int)]),
     "mfns_mesh_destroy": (C.c_int, [C.c_void_p]),
     "mfns_problem_create": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(ProblemDesc), C.POINTER(C.c_void_p)]),
+    "mfns_problem_create_hp": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(ProblemDesc), C.c_void_p, C.c_int64,
+                                         C.POINTER(C.c_void_p)]),
+    "mfns_mesh_cells": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.POINTER(C.c_int64)]),
     "mfns_problem_info": (C.c_int, [C.c_void_p, C.POINTER(Info)]),
     "mfns_dof_support_points": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
     "mfns_constrained_dofs": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int64, C.POINTER(C.c_int64)]),

@@ -82,6 +82,14 @@ class Mesh:
         L.check(self.lib.mfns_mesh_info(self.h, C.byref(n), C.byref(l)))
         return n.value, l.value
 
+    def cells(self):
+        """(n_cells, 4) int32: level, x, y, z of every active cell in the canonical order."""
+        n = C.c_int64()
+        L.check(self.lib.mfns_mesh_cells(self.h, None, 0, C.byref(n)))
+        out = np.zeros((n.value, 4), dtype=np.int32)
+        L.check(self.lib.mfns_mesh_cells(self.h, out.ctypes.data_as(C.c_void_p), n.value, C.byref(n)))
+        return out
+
     def close(self):
         if self.h:
             self.lib.mfns_mesh_destroy(self.h)
@@ -103,12 +111,18 @@ def make_desc(kind, degree, nu=1.0, dt=0.0, terms=0, div_sign=0.0, smoother=0, s
 
 
 class Problem:
-    def __init__(self, ctx, mesh, **desc):
+    def __init__(self, ctx, mesh, degrees=None, **desc):
+        """degrees: optional per-cell degree (order of Mesh.cells()) for an hp problem."""
         self.ctx = ctx
         self.lib = ctx.lib
         self.desc = make_desc(**desc)
         h = C.c_void_p()
-        L.check(self.lib.mfns_problem_create(ctx.h, mesh.h, C.byref(self.desc), C.byref(h)))
+        if degrees is None:
+            L.check(self.lib.mfns_problem_create(ctx.h, mesh.h, C.byref(self.desc), C.byref(h)))
+        else:
+            deg = np.ascontiguousarray(degrees, dtype=np.int32)
+            L.check(self.lib.mfns_problem_create_hp(ctx.h, mesh.h, C.byref(self.desc),
+                                                    deg.ctypes.data_as(C.c_void_p), len(deg), C.byref(h)))
         self.h = h
         self.info = self.get_info()
 

@@ -128,6 +128,9 @@ int mfns_mesh_destroy(mfns_mesh* mesh) {
   return MFNS_OK;
 }
 
+static int finish_problem(mfns_ctx* ctx, const mfns_problem_desc* desc, std::unique_ptr<Problem> p, size_t used0,
+                          mfns_problem** out);
+
 int mfns_problem_create(mfns_ctx* ctx, const mfns_mesh* mesh, const mfns_problem_desc* desc, mfns_problem** out) {
   API_BEGIN
   if (!ctx || !mesh || !desc || !out) return fail(MFNS_ERR_ARG, "null argument");
@@ -150,6 +153,13 @@ int mfns_problem_create(mfns_ctx* ctx, const mfns_mesh* mesh, const mfns_problem
   std::unique_ptr<Problem> p = build_problem(mesh->forest, desc->kind, k, ph, desc->mg_order,
                                              desc->coarse_stop_n > 0 ? desc->coarse_stop_n : 2, &ctx->budget,
                                              desc->hierarchy);
+  return finish_problem(ctx, desc, std::move(p), used0, out);
+  API_END
+}
+
+// settings, workspaces, autotuning, smoother bounds and the coarse solver of a built problem
+static int finish_problem(mfns_ctx* ctx, const mfns_problem_desc* desc, std::unique_ptr<Problem> p, size_t used0,
+                          mfns_problem** out) {
   if (desc->smoother < 0 || desc->smoother > 2) return fail(MFNS_ERR_ARG, "smoother must be 0, 1 or 2");
   // internal: 0 = Chebyshev, 1 = Jacobi relaxation
   p->smoother = desc->smoother == 0 ? (desc->kind == MFNS_STAB_NS ? 1 : 0) : desc->smoother - 1;
@@ -174,7 +184,43 @@ int mfns_problem_create(mfns_ctx* ctx, const mfns_mesh* mesh, const mfns_problem
   w->ctx = ctx;
   w->p = std::move(p);
   *out = w;
+  return MFNS_OK;
+}
+
+int mfns_problem_create_hp(mfns_ctx* ctx, const mfns_mesh* mesh, const mfns_problem_desc* desc,
+                           const int32_t* cell_degree, int64_t n_cells, mfns_problem** out) {
+  API_BEGIN
+  if (!ctx || !mesh || !desc || !cell_degree || !out) return fail(MFNS_ERR_ARG, "null argument");
+  if (n_cells != (int64_t)mesh->forest.n_cells()) return fail(MFNS_ERR_ARG, "one degree per mesh cell expected");
+  if (desc->kind != MFNS_STOKES_A) return fail(MFNS_ERR_UNSUPPORTED, "hp problems are built for MFNS_STOKES_A");
+  if (desc->hierarchy != 0) return fail(MFNS_ERR_UNSUPPORTED, "hp problems use global coarsening");
+  if (!(desc->nu > 0)) return fail(MFNS_ERR_ARG, "nu must be positive");
+  if (desc->mg_precision != MFNS_FP64 && desc->mg_precision != MFNS_FP32) return fail(MFNS_ERR_ARG, "bad precision");
+  const int dim = mesh->forest.dim;
+  std::vector<int32_t> degree(cell_degree, cell_degree + n_cells);
+  for (int32_t k : degree)
+    if (!op_supported_kind(dim, MFNS_STOKES_A, k)) return fail(MFNS_ERR_UNSUPPORTED, "unsupported cell degree");
+  MFNS_CUDA(cudaSetDevice(ctx->device));
+  Physics ph;
+  ph.nu = desc->nu;
+  ph.div_sign = -1.0;
+  const size_t used0 = ctx->budget.used;
+  std::unique_ptr<Problem> p = build_problem_hp(mesh->forest, degree, ph,
+                                                desc->coarse_stop_n > 0 ? desc->coarse_stop_n : 2, &ctx->budget);
+  return finish_problem(ctx, desc, std::move(p), used0, out);
   API_END
+}
+
+int mfns_mesh_cells(const mfns_mesh* mesh, int32_t* cells, int64_t cap, int64_t* n) {
+  if (!mesh || !n) return fail(MFNS_ERR_ARG, "null argument");
+  const Forest& f = mesh->forest;
+  *n = (int64_t)f.n_cells();
+  if (cells)
+    for (int64_t c = 0; c < *n && c < cap; ++c) {
+      cells[4 * c] = f.lev[c];
+      for (int d = 0; d < 3; ++d) cells[4 * c + 1 + d] = f.crd[3 * c + d];
+    }
+  return MFNS_OK;
 }
 
 int mfns_problem_destroy(mfns_problem* p) {

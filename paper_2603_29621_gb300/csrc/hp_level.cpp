@@ -1,0 +1,291 @@
+// hp levels (Section 3): the operator of a mesh whose cells carry different degrees.
+//
+// The cells of each degree form a group that the degree's cell kernel applies on its own node ids
+// (no constraint masks).  The constraints of h- and p-adaptivity act around the cell kernels: the
+// input is copied and its constrained entries completed from their masters, every group adds its
+// products, the products on constrained entries are folded into their masters with the same
+// weights (C^T), and constrained rows are identity rows: A = C^T K C on the free DoFs.  The exact
+// diagonal is probed: free DoFs that share no cell once the constraints are resolved are set to
+// one together and read back from one product.
+#include <algorithm>
+#include <map>
+#include <numeric>
+#include <set>
+
+#include "problem.hpp"
+#include "vec.hpp"
+
+namespace mfns {
+
+template <typename T>
+static DevBuf upload_as(Budget* bud, const std::vector<double>& v) {
+  std::vector<T> t(v.begin(), v.end());
+  return upload(bud, t);
+}
+
+// greedy colouring of a subset of cells so that no two cells of a colour share a node
+static int color_subset(const HpSpace& sp, const std::vector<int32_t>& cells, std::vector<int32_t>& color) {
+  std::map<int32_t, std::vector<int32_t>> node_cells;
+  for (int32_t i = 0; i < (int32_t)cells.size(); ++i) {
+    const int32_t c = cells[i];
+    for (int64_t j = sp.cell_ptr[c]; j < sp.cell_ptr[c + 1]; ++j) node_cells[sp.cell_nodes[j]].push_back(i);
+  }
+  color.assign(cells.size(), -1);
+  int ncol = 0;
+  for (int32_t i = 0; i < (int32_t)cells.size(); ++i) {
+    std::set<int> used;
+    const int32_t c = cells[i];
+    for (int64_t j = sp.cell_ptr[c]; j < sp.cell_ptr[c + 1]; ++j)
+      for (int32_t o : node_cells[sp.cell_nodes[j]])
+        if (color[o] >= 0) used.insert(color[o]);
+    int col = 0;
+    while (used.count(col)) ++col;
+    color[i] = col;
+    ncol = std::max(ncol, col + 1);
+  }
+  return ncol;
+}
+
+void build_hp_oplevel(OpLevel& lv, const Forest& f, const std::vector<int32_t>& degree, const Physics& ph,
+                      Budget* bud) {
+  const int dim = f.dim;
+  auto hp = std::make_unique<HpData>();
+  std::string err;
+  if (!make_hp_space(f, degree, hp->space, &err))
+    throw Error(err.rfind("unsupported", 0) == 0 ? kErrUnsupported : kErrArg, err);
+  const HpSpace& sp = hp->space;
+  lv.op = OP_STOKES_A;
+  lv.dim = dim;
+  lv.k = *std::max_element(degree.begin(), degree.end());
+  lv.forest = f;
+  lv.NU = dim;
+  lv.nu = NodeSpace();
+  lv.nu.dim = dim;
+  lv.nu.n_nodes = sp.n_nodes;
+  lv.nu.x = sp.x;
+  lv.nu.boundary = sp.boundary;
+  lv.n_main_dofs = lv.n_dofs = sp.n_nodes * dim;
+  if (lv.n_dofs >= (int64_t(1) << 31) - 1) throw Error(kErrUnsupported, "more than 2^31 DoFs per level");
+  // groups of one degree: colour-sorted cell tables with node ids and the Dirichlet bit
+  for (int k = 1; k <= lv.k; ++k) {
+    std::vector<int32_t> cells;
+    for (size_t c = 0; c < f.n_cells(); ++c)
+      if (degree[c] == k) cells.push_back((int32_t)c);
+    if (cells.empty()) continue;
+    auto g = std::make_unique<HpGroup>();
+    g->k = k;
+    std::vector<int32_t> color;
+    const int ncol = color_subset(sp, cells, color);
+    std::vector<int32_t> order(cells.size());
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return color[a] < color[b]; });
+    const int nb = (int)(sp.cell_ptr[cells[0] + 1] - sp.cell_ptr[cells[0]]);
+    std::vector<int32_t> cu(cells.size() * nb);
+    std::vector<uint32_t> mk(cells.size(), 0u);
+    std::vector<double> hc(cells.size());
+    OpLaunch& L = g->L;
+    L.dim = dim;
+    L.k = k;
+    L.op = OP_STOKES_A;
+    L.structured = false;
+    L.n = f.n;
+    L.h = 1.0 / f.n;
+    L.n_cells = (int64_t)cells.size();
+    L.n_colors = ncol;
+    L.color_ptr.assign(ncol + 1, 0);
+    for (size_t i = 0; i < cells.size(); ++i) {
+      const int32_t c = cells[order[i]];
+      g->cells.push_back(c);
+      L.color_ptr[color[order[i]] + 1]++;
+      hc[i] = f.h(c);
+      for (int b = 0; b < nb; ++b) {
+        const int32_t node = sp.cell_nodes[sp.cell_ptr[c] + b];
+        cu[i * nb + b] = node | (sp.boundary[node] ? int32_t(0x80000000u) : 0);
+      }
+    }
+    for (int c = 0; c < ncol; ++c) L.color_ptr[c + 1] += L.color_ptr[c];
+    L.nu = ph.nu;
+    L.dt = ph.dt;
+    L.div_sign = ph.div_sign;
+    L.terms = ph.terms;
+    fill_tables(L);
+    g->cell_u = upload(bud, cu);
+    g->mask = upload(bud, mk);
+    g->hcell[0] = upload_as<double>(bud, hc);
+    g->hcell[1] = upload_as<float>(bud, hc);
+    L.cell_u = g->cell_u.as<int32_t>();
+    L.mask = g->mask.as<uint32_t>();
+    L.hcell[0] = g->hcell[0].get();
+    L.hcell[1] = g->hcell[1].get();
+    L.p_offset = lv.n_main_dofs;
+    L.timer = g->timer.get();
+    hp->groups.push_back(std::move(g));
+  }
+  // the level's own launch description stays empty: hp levels run through their groups
+  lv.L = OpLaunch();
+  lv.L.dim = dim;
+  lv.L.k = lv.k;
+  lv.L.op = OP_STOKES_A;
+  // constrained rows; constraint lists without Dirichlet slaves or masters (every component is a
+  // velocity component with Dirichlet conditions)
+  std::vector<char> hang(sp.n_nodes, 0);
+  for (int32_t g : sp.hang_node) hang[g] = 1;
+  for (int64_t g = 0; g < sp.n_nodes; ++g)
+    if (sp.boundary[g] || hang[g])
+      for (int c = 0; c < dim; ++c) lv.constrained_host.push_back((int32_t)(g * dim + c));
+  std::sort(lv.constrained_host.begin(), lv.constrained_host.end());
+  lv.constrained = upload(bud, lv.constrained_host);
+  std::vector<int32_t> hd, hptr(1, 0), hs;
+  std::vector<double> hw;
+  std::map<int32_t, std::vector<std::pair<int32_t, double>>> transpose;  // master dof -> (slave dof, w)
+  for (size_t i = 0; i < sp.hang_node.size(); ++i) {
+    const int32_t g = sp.hang_node[i];
+    if (sp.boundary[g]) continue;
+    for (int c = 0; c < dim; ++c) {
+      const int32_t sd = (int32_t)(g * dim + c);
+      hd.push_back(sd);
+      for (int32_t j = sp.hang_ptr[i]; j < sp.hang_ptr[i + 1]; ++j) {
+        const int32_t m = sp.hang_master[j];
+        if (sp.boundary[m]) continue;
+        const int32_t md = (int32_t)(m * dim + c);
+        hs.push_back(md);
+        hw.push_back(sp.hang_w[j]);
+        transpose[md].push_back({sd, sp.hang_w[j]});
+      }
+      hptr.push_back((int32_t)hs.size());
+    }
+  }
+  lv.n_hang = (int64_t)hd.size();
+  lv.hang_dof = upload(bud, hd);
+  lv.hang_ptr = upload(bud, hptr);
+  lv.hang_src = upload(bud, hs);
+  lv.hang_w[0] = upload_as<double>(bud, hw);
+  lv.hang_w[1] = upload_as<float>(bud, hw);
+  std::vector<int32_t> cm, cp(1, 0), cs;
+  std::vector<double> cw;
+  for (auto& kv : transpose) {
+    cm.push_back(kv.first);
+    for (auto& sw : kv.second) {
+      cs.push_back(sw.first);
+      cw.push_back(sw.second);
+    }
+    cp.push_back((int32_t)cs.size());
+  }
+  hp->n_ct = (int64_t)cm.size();
+  hp->ct_master = upload(bud, cm);
+  hp->ct_ptr = upload(bud, cp);
+  hp->ct_slave = upload(bud, cs);
+  hp->ct_w[0] = upload_as<double>(bud, cw);
+  hp->ct_w[1] = upload_as<float>(bud, cw);
+  // probing groups for the diagonal: free nodes m, n may share a group only if no cell holds a
+  // node of S(m) = {m} + its slaves and one of S(n)
+  std::vector<std::vector<int32_t>> masters_of(sp.n_nodes);  // free node -> itself; hanging -> masters
+  for (int64_t g = 0; g < sp.n_nodes; ++g)
+    if (!sp.boundary[g] && !hang[g]) masters_of[g].push_back((int32_t)g);
+  for (size_t i = 0; i < sp.hang_node.size(); ++i) {
+    const int32_t g = sp.hang_node[i];
+    if (sp.boundary[g]) continue;
+    for (int32_t j = sp.hang_ptr[i]; j < sp.hang_ptr[i + 1]; ++j)
+      if (!sp.boundary[sp.hang_master[j]]) masters_of[g].push_back(sp.hang_master[j]);
+  }
+  std::vector<std::vector<int32_t>> node_cells(sp.n_nodes);
+  for (size_t c = 0; c < f.n_cells(); ++c)
+    for (int64_t j = sp.cell_ptr[c]; j < sp.cell_ptr[c + 1]; ++j) node_cells[sp.cell_nodes[j]].push_back((int32_t)c);
+  std::vector<std::vector<int32_t>> cell_masters(f.n_cells());  // free masters reached by each cell
+  for (size_t c = 0; c < f.n_cells(); ++c) {
+    auto& v = cell_masters[c];
+    for (int64_t j = sp.cell_ptr[c]; j < sp.cell_ptr[c + 1]; ++j)
+      for (int32_t m : masters_of[sp.cell_nodes[j]]) v.push_back(m);
+    std::sort(v.begin(), v.end());
+    v.erase(std::unique(v.begin(), v.end()), v.end());
+  }
+  std::vector<std::vector<int32_t>> master_cells(sp.n_nodes);
+  for (size_t c = 0; c < f.n_cells(); ++c)
+    for (int32_t m : cell_masters[c]) master_cells[m].push_back((int32_t)c);
+  std::vector<int32_t> pcol(sp.n_nodes, -1);
+  int npc = 0;
+  for (int64_t m = 0; m < sp.n_nodes; ++m) {
+    if (sp.boundary[m] || hang[m]) continue;
+    std::set<int> used;
+    for (int32_t c : master_cells[m])
+      for (int32_t o : cell_masters[c])
+        if (pcol[o] >= 0) used.insert(pcol[o]);
+    int col = 0;
+    while (used.count(col)) ++col;
+    pcol[m] = col;
+    npc = std::max(npc, col + 1);
+  }
+  std::vector<int32_t> pd;
+  hp->probe_ptr.assign(1, 0);
+  for (int col = 0; col < npc; ++col)
+    for (int c = 0; c < dim; ++c) {
+      for (int64_t m = 0; m < sp.n_nodes; ++m)
+        if (pcol[m] == col) pd.push_back((int32_t)(m * dim + c));
+      hp->probe_ptr.push_back((int64_t)pd.size());
+    }
+  hp->probe_dofs = upload(bud, pd);
+  for (int prec = 0; prec < 2; ++prec) {
+    hp->tmp[prec].alloc(bud, lv.n_dofs * esize(prec));
+    hp->probe_e[prec].alloc(bud, lv.n_dofs * esize(prec));
+    hp->probe_y[prec].alloc(bud, lv.n_dofs * esize(prec));
+  }
+  lv.hp = std::move(hp);
+}
+
+void hp_distribute(const OpLevel& lv, int prec, void* x, cudaStream_t s) { oplevel_distribute(lv, prec, x, s); }
+
+void hp_condense(const OpLevel& lv, int prec, void* y, cudaStream_t s) {
+  const HpData& H = *lv.hp;
+  if (prec == 0)
+    vcondense<double>((double*)y, H.ct_master.as<int32_t>(), H.ct_ptr.as<int32_t>(), H.ct_slave.as<int32_t>(),
+                      H.ct_w[0].as<double>(), H.n_ct, s);
+  else
+    vcondense<float>((float*)y, H.ct_master.as<int32_t>(), H.ct_ptr.as<int32_t>(), H.ct_slave.as<int32_t>(),
+                     H.ct_w[1].as<float>(), H.n_ct, s);
+}
+
+void hp_vmult(const OpLevel& lv, int prec, const void* src, void* dst, cudaStream_t s) {
+  const HpData& H = *lv.hp;
+  const int64_t n = lv.n_dofs;
+  void* t = H.tmp[prec].get();
+  MFNS_CUDA(cudaMemcpyAsync(t, src, n * esize(prec), cudaMemcpyDeviceToDevice, s));
+  hp_distribute(lv, prec, t, s);
+  MFNS_CUDA(cudaMemsetAsync(dst, 0, n * esize(prec), s));
+  for (auto& g : H.groups) op_apply(g->L, prec, t, dst, false, s);
+  hp_condense(lv, prec, dst, s);
+  const int64_t nc = (int64_t)lv.constrained_host.size();
+  if (prec == 0)
+    vcopy_idx<double>((double*)dst, (const double*)src, lv.constrained.as<int32_t>(), nc, s);
+  else
+    vcopy_idx<float>((float*)dst, (const float*)src, lv.constrained.as<int32_t>(), nc, s);
+}
+
+void hp_diag(const OpLevel& lv, int prec, void* diag, cudaStream_t s) {
+  const HpData& H = *lv.hp;
+  const int64_t n = lv.n_dofs;
+  void* e = H.probe_e[prec].get();
+  void* y = H.probe_y[prec].get();
+  MFNS_CUDA(cudaMemsetAsync(diag, 0, n * esize(prec), s));
+  const int32_t* pd = H.probe_dofs.as<int32_t>();
+  for (size_t p = 0; p + 1 < H.probe_ptr.size(); ++p) {
+    const int64_t a = H.probe_ptr[p], m = H.probe_ptr[p + 1] - H.probe_ptr[p];
+    if (m == 0) continue;
+    MFNS_CUDA(cudaMemsetAsync(e, 0, n * esize(prec), s));
+    if (prec == 0)
+      vset_idx<double>((double*)e, 1.0, pd + a, m, s);
+    else
+      vset_idx<float>((float*)e, 1.0f, pd + a, m, s);
+    hp_vmult(lv, prec, e, y, s);
+    if (prec == 0)
+      vcopy_idx<double>((double*)diag, (const double*)y, pd + a, m, s);
+    else
+      vcopy_idx<float>((float*)diag, (const float*)y, pd + a, m, s);
+  }
+  const int64_t nc = (int64_t)lv.constrained_host.size();
+  if (prec == 0)
+    vset_idx<double>((double*)diag, 1.0, lv.constrained.as<int32_t>(), nc, s);
+  else
+    vset_idx<float>((float*)diag, 1.0f, lv.constrained.as<int32_t>(), nc, s);
+}
+
+}  // namespace mfns

@@ -244,6 +244,7 @@ void build_oplevel(OpLevel& lv, const Forest& f, int op, int k, const Physics& p
 }
 
 void oplevel_vmult(const OpLevel& lv, int prec, const void* src, void* dst, cudaStream_t s) {
+  if (lv.hp) return hp_vmult(lv, prec, src, dst, s);
   MFNS_CUDA(cudaMemsetAsync(dst, 0, lv.n_dofs * esize(prec), s));
   op_apply(lv.L, prec, src, dst, false, s);
   const int64_t nc = (int64_t)lv.constrained_host.size();
@@ -254,6 +255,7 @@ void oplevel_vmult(const OpLevel& lv, int prec, const void* src, void* dst, cuda
 }
 
 void oplevel_vmult_cols(const OpLevel& lv, int prec, const void* X, void* Y, int ncols, cudaStream_t s) {
+  if (lv.hp) throw Error(kErrUnsupported, "multi-column products of hp levels");
   const int64_t n = lv.n_dofs;
   MFNS_CUDA(cudaMemsetAsync(Y, 0, (size_t)ncols * n * esize(prec), s));
   op_apply_cols(lv.L, prec, X, Y, ncols, n, s);
@@ -301,6 +303,7 @@ void oplevel_residual_fused(const OpLevel& lv, int prec, const void* x, const vo
 }
 
 void oplevel_diag(const OpLevel& lv, int prec, void* diag, cudaStream_t s) {
+  if (lv.hp) return hp_diag(lv, prec, diag, s);
   MFNS_CUDA(cudaMemsetAsync(diag, 0, lv.n_dofs * esize(prec), s));
   op_apply(lv.L, prec, nullptr, diag, true, s);
   const int64_t nc = (int64_t)lv.constrained_host.size();

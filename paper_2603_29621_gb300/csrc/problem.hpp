@@ -8,11 +8,15 @@
 #include <vector>
 
 #include "common.hpp"
+#include "hp_space.hpp"
 #include "mesh.hpp"
 #include "opkind.hpp"
 #include "op_launch.hpp"
 
 namespace mfns {
+
+struct HpData;
+struct HpTransfer;
 
 struct Physics {
   double nu = 1.0, dt = 0.0, div_sign = -1.0;
@@ -44,8 +48,43 @@ struct OpLevel {
   DevBuf dinv[2];
   double lmax = 0.0;
   std::unique_ptr<KernelTimer> timer = std::make_unique<KernelTimer>();
+  // hp level (cells of several degrees): operator, diagonal and support points come from here
+  std::unique_ptr<HpData> hp;
   size_t bytes() const;
 };
+
+// hp levels (Section 3).  The cells of one degree form a group applied by that degree's cell
+// kernel with their own node ids (no constraint masks).  The constraints of h- and
+// p-adaptivity are applied around the cell kernels: the input's constrained entries are first
+// completed from their masters (distribute), the products on constrained entries are then folded
+// into the masters with the same weights (the transpose), and constrained rows are identity rows.
+struct HpGroup {
+  int k = 1;
+  OpLaunch L;
+  std::vector<int32_t> cells;           // forest cell ids, colour order
+  DevBuf cell_u, mask, hcell[2];
+  std::unique_ptr<KernelTimer> timer = std::make_unique<KernelTimer>();
+};
+struct HpData {
+  HpSpace space;
+  std::vector<std::unique_ptr<HpGroup>> groups;
+  DevBuf tmp[2], probe_e[2], probe_y[2];  // distributed input; probing vectors of the diagonal
+  // transpose of the constraints: for master dof ct_master[i], slaves ct_slave[j] with weights
+  // ct_w[j], j in [ct_ptr[i], ct_ptr[i+1])
+  DevBuf ct_master, ct_ptr, ct_slave, ct_w[2];
+  int64_t n_ct = 0;
+  // exact diagonal by probing: free dofs in groups that share no cell after the constraints
+  std::vector<int64_t> probe_ptr;
+  DevBuf probe_dofs;
+};
+void build_hp_oplevel(OpLevel& lv, const Forest& f, const std::vector<int32_t>& degree, const Physics& ph,
+                      Budget* bud);
+void hp_vmult(const OpLevel& lv, int prec, const void* src, void* dst, cudaStream_t s);
+void hp_diag(const OpLevel& lv, int prec, void* diag, cudaStream_t s);
+// y[m] += sum of w * y[slave] over the slaves of every master m (hp levels)
+void hp_condense(const OpLevel& lv, int prec, void* y, cudaStream_t s);
+// x[slave] = sum of w * x[master] for every constrained (non-Dirichlet) entry
+void hp_distribute(const OpLevel& lv, int prec, void* x, cudaStream_t s);
 
 // edge_dirichlet (level forests of local smoothing): nodes on the refinement edge are constrained
 // like Dirichlet nodes (identity rows, zero in the operator's input)
@@ -88,6 +127,17 @@ struct Transfer {
   std::vector<double> E;                // h: P_half[2][NF][NC]; p: S[NF][NC]
   std::vector<double> Pc;               // coarse hanging interpolation P[2][NC][NC]
   DevBuf own_c;                         // state interpolation: owner flag per coarse (cell, slot)
+  std::unique_ptr<HpTransfer> hp;       // p-step from an hp level (groups of degree pairs)
+};
+// p-transfer from an hp level to the level with every degree lowered by one (hp or uniform)
+void build_hp_transfer(Transfer& t, const OpLevel& fine, const OpLevel& coarse, Budget* bud);
+// one (fine degree, coarse degree) pair of an hp p-transfer: the same cells on both levels
+struct HpTGroup {
+  Transfer t;                           // degree change (or identity) per cell, coarse colours
+  OpLevel fine_view, coarse_view;       // fine owner table (tnodes); coarse cell table and masks
+};
+struct HpTransfer {
+  std::vector<std::unique_ptr<HpTGroup>> groups;
 };
 // allow_unrefined (local smoothing): coarse cells without children in the fine level are skipped
 void build_transfer(Transfer& t, const OpLevel& fine, const OpLevel& coarse, Budget* bud,
@@ -209,6 +259,10 @@ int mg_level_count(const Problem& p);
 OpLevel& mg_level(Problem& p, int i);
 
 // Build everything for a mesh and a description; throws Error.
+// hp-adaptive vector Laplacian (Section 3): degree[c] per forest cell; hierarchy: every degree
+// lowered by one per level until all are linear, then global coarsening
+std::unique_ptr<Problem> build_problem_hp(const Forest& f, const std::vector<int32_t>& degree, const Physics& ph,
+                                          int coarse_stop_n, Budget* bud);
 // hierarchy: 0 global coarsening, 1 local smoothing (vector Laplacian and the Stokes A block on a
 // locally refined mesh; an unrefined mesh needs none and gets global coarsening)
 std::unique_ptr<Problem> build_problem(const Forest& f, int kind, int k, const Physics& ph, int mg_order,

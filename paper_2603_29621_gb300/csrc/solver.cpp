@@ -174,6 +174,53 @@ static void build_local_smoothing(Problem& p, const Forest& f, int k, const Phys
   p.ls = std::move(S);
 }
 
+std::unique_ptr<Problem> build_problem_hp(const Forest& f, const std::vector<int32_t>& degree, const Physics& ph,
+                                          int coarse_stop_n, Budget* bud) {
+  if (degree.size() != f.n_cells()) throw Error(kErrArg, "one degree per cell expected");
+  auto uniform = [](const std::vector<int32_t>& d) {
+    return std::all_of(d.begin(), d.end(), [&](int32_t k) { return k == d[0]; });
+  };
+  if (uniform(degree)) return build_problem(f, 1, degree[0], ph, 1, coarse_stop_n, bud, 0);
+  auto p = std::make_unique<Problem>();
+  p->uid = ++g_problem_uid;
+  p->kind = 1;
+  p->dim = f.dim;
+  p->k = *std::max_element(degree.begin(), degree.end());
+  p->phys = ph;
+  p->bud = bud;
+  // Section 3: every cell's degree lowered by one per level until all cells are linear ...
+  std::vector<int32_t> d = degree;
+  while (!uniform(d)) {
+    auto lv = std::make_unique<OpLevel>();
+    build_hp_oplevel(*lv, f, d, ph, bud);
+    p->levels.push_back(std::move(lv));
+    for (auto& k : d) k = std::max(k - 1, 1);
+  }
+  for (int kk = d[0]; kk >= 1; --kk) {  // (all linear after the loop; kept general)
+    auto lv = std::make_unique<OpLevel>();
+    build_oplevel(*lv, f, OP_STOKES_A, kk, ph, bud);
+    p->levels.push_back(std::move(lv));
+  }
+  // ... then global coarsening with linear elements
+  Forest fc = f;
+  while (forest_can_coarsen(fc, coarse_stop_n)) {
+    fc = forest_coarsen(fc);
+    auto lv = std::make_unique<OpLevel>();
+    build_oplevel(*lv, fc, OP_STOKES_A, 1, ph, bud);
+    p->levels.push_back(std::move(lv));
+  }
+  if (p->levels.size() > 32) throw Error(kErrUnsupported, "more than 32 multigrid levels");
+  for (size_t l = 0; l + 1 < p->levels.size(); ++l) {
+    auto t = std::make_unique<Transfer>();
+    if (p->levels[l]->hp)
+      build_hp_transfer(*t, *p->levels[l], *p->levels[l + 1], bud);
+    else
+      build_transfer(*t, *p->levels[l], *p->levels[l + 1], bud);
+    p->transfers.push_back(std::move(t));
+  }
+  return p;
+}
+
 int mg_level_count(const Problem& p) {
   if (!p.ls) return (int)p.levels.size();
   return (int)(p.ls->lv.size() + p.ls->base->levels.size());
@@ -294,8 +341,13 @@ void autotune(Problem& p, cudaStream_t s) {
   for (int prec = 0; prec < 2; ++prec)
     for (size_t l = 0; l < p.levels.size(); ++l) {
       Workspace& w = p.ws[prec][l];
-      MFNS_CUDA(cudaMemsetAsync(w.x.get(), 0, p.levels[l]->n_dofs * esize(prec), s));
-      autotune_warps(p.levels[l]->L, prec, w.x.get(), w.t.get(), p.levels[l]->n_dofs, s);
+      OpLevel& lv = *p.levels[l];
+      MFNS_CUDA(cudaMemsetAsync(w.x.get(), 0, lv.n_dofs * esize(prec), s));
+      if (lv.hp) {  // hp levels: every degree group on its own
+        for (auto& g : lv.hp->groups) autotune_warps(g->L, prec, w.x.get(), w.t.get(), lv.n_dofs, s);
+      } else {
+        autotune_warps(lv.L, prec, w.x.get(), w.t.get(), lv.n_dofs, s);
+      }
     }
   if (p.ls) {
     for (auto& lv : p.ls->lv)

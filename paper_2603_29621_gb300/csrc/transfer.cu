@@ -11,6 +11,8 @@
 // transpose; its scatter into the coarse vector follows the coarse colours.
 #include <algorithm>
 #include <cstdlib>
+#include <map>
+#include <numeric>
 #include <cstring>
 #include <unordered_map>
 
@@ -484,8 +486,150 @@ void cell_interpolate(Transfer& t, const OpLevel& fine, const OpLevel& coarse, c
   MFNS_CUDA(cudaGetLastError());
 }
 
+// ---- hp p-transfers: groups of cells with one (fine degree, coarse degree) pair
+void build_hp_transfer(Transfer& t, const OpLevel& fine, const OpLevel& coarse, Budget* bud) {
+  if (!fine.hp) throw Error(kErrArg, "hp transfer needs an hp fine level");
+  const HpSpace& fs = fine.hp->space;
+  const Forest& ff = fine.forest;
+  const Forest& fc = coarse.forest;
+  if (ff.n_cells() != fc.n_cells() || ff.lev != fc.lev || ff.crd != fc.crd)
+    throw Error(kErrArg, "hp p-transfer needs the same cells on both levels");
+  const int dim = fine.dim, NU = fine.NU, nch = 1 << dim;
+  const size_t nc = ff.n_cells();
+  // coarse: degree, slot values (node | Dirichlet bit) and constraint masks per cell
+  std::vector<int> kc(nc);
+  std::vector<uint32_t> cmask(nc, 0u);
+  if (coarse.hp) {
+    for (size_t c = 0; c < nc; ++c) kc[c] = coarse.hp->space.degree[c];
+  } else {
+    for (size_t c = 0; c < nc; ++c) kc[c] = coarse.k;
+    const Lattice lat = make_lattice(fc);
+    cmask = constraint_masks(fc, lat);
+  }
+  auto coarse_slot = [&](size_t c, int b) -> int32_t {
+    int32_t node;
+    bool bnd;
+    if (coarse.hp) {
+      const HpSpace& cs = coarse.hp->space;
+      node = cs.cell_nodes[cs.cell_ptr[c] + b];
+      bnd = cs.boundary[node];
+    } else {
+      node = coarse.nu.cell_master[c * coarse.nu.nb + b];
+      bnd = coarse.nu.boundary[node];
+    }
+    return node | (bnd ? int32_t(0x80000000u) : 0);
+  };
+  // fine owner flags over all cells: bit 31 not the owner or hanging, bit 30 Dirichlet
+  std::vector<char> hangf(fs.n_nodes, 0), seen(fs.n_nodes, 0);
+  for (int32_t g : fs.hang_node) hangf[g] = 1;
+  std::vector<int32_t> fval(fs.cell_nodes.size());
+  for (size_t c = 0; c < nc; ++c)
+    for (int64_t j = fs.cell_ptr[c]; j < fs.cell_ptr[c + 1]; ++j) {
+      const int32_t g = fs.cell_nodes[j];
+      int32_t v = g;
+      if (fs.boundary[g]) v |= 0x40000000;
+      if (seen[g] || hangf[g]) v |= int32_t(0x80000000u);
+      seen[g] = 1;
+      fval[j] = v;
+    }
+  std::map<std::pair<int, int>, std::vector<int32_t>> pairs;
+  for (size_t c = 0; c < nc; ++c) pairs[{fs.degree[c], kc[c]}].push_back((int32_t)c);
+  auto H = std::make_unique<HpTransfer>();
+  for (auto& kv : pairs) {
+    const int kf = kv.first.first, kcg = kv.first.second;
+    const std::vector<int32_t>& cells = kv.second;
+    const int NF = kf + 1, NC = kcg + 1;
+    const int NBF = dim == 3 ? NF * NF * NF : NF * NF, NBC = dim == 3 ? NC * NC * NC : NC * NC;
+    // colours of the coarse scatter: no two cells of a colour write the same coarse entry
+    std::map<int32_t, std::vector<int32_t>> node_cells;
+    for (int32_t i = 0; i < (int32_t)cells.size(); ++i)
+      for (int b = 0; b < NBC; ++b) node_cells[coarse_slot(cells[i], b) & 0x7fffffff].push_back(i);
+    std::vector<int32_t> color(cells.size(), -1);
+    int ncol = 0;
+    for (int32_t i = 0; i < (int32_t)cells.size(); ++i) {
+      std::vector<char> used(ncol + 1, 0);
+      for (int b = 0; b < NBC; ++b)
+        for (int32_t o : node_cells[coarse_slot(cells[i], b) & 0x7fffffff])
+          if (color[o] >= 0) used[color[o]] = 1;
+      int col = 0;
+      while (used[col]) ++col;
+      color[i] = col;
+      ncol = std::max(ncol, col + 1);
+    }
+    std::vector<int32_t> order(cells.size());
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return color[a] < color[b]; });
+    auto G = std::make_unique<HpTGroup>();
+    Transfer& tt = G->t;
+    tt.dim = dim;
+    tt.kf = kf;
+    tt.kc = kcg;
+    tt.ncomp = NU;
+    tt.hkind = kf == kcg;  // same degree: identity (code 8 with the h tables)
+    tt.n_coarse_cells = (int64_t)cells.size();
+    tt.color_ptr.assign(ncol + 1, 0);
+    std::vector<int32_t> cu(cells.size() * NBC), fn(cells.size() * NBF), child(cells.size() * nch, -1);
+    std::vector<uint32_t> mk(cells.size());
+    std::vector<uint8_t> code(cells.size() * nch, 0);
+    for (size_t i = 0; i < cells.size(); ++i) {
+      const int32_t c = cells[order[i]];
+      tt.color_ptr[color[order[i]] + 1]++;
+      for (int b = 0; b < NBC; ++b) cu[i * NBC + b] = coarse_slot(c, b);
+      for (int b = 0; b < NBF; ++b) fn[i * NBF + b] = fval[fs.cell_ptr[c] + b];
+      mk[i] = cmask[c];
+      child[i * nch] = (int32_t)i;
+      code[i * nch] = 8;
+    }
+    for (int c = 0; c < ncol; ++c) tt.color_ptr[c + 1] += tt.color_ptr[c];
+    tt.child_cell = upload(bud, child);
+    tt.child_code = upload(bud, code);
+    const std::vector<double> xf = gll_nodes(kf), xc = gll_nodes(kcg);
+    tt.E.assign(2 * NF * NC, 0.0);
+    for (int h = 0; h < 2; ++h)
+      for (int r = 0; r < NF; ++r)
+        for (int m = 0; m < NC; ++m)
+          tt.E[(h * NF + r) * NC + m] = tt.hkind ? lagrange(xc, m, 0.5 * (h + xf[r])) : lagrange(xc, m, xf[r]);
+    tt.Pc.assign(2 * NC * NC, 0.0);
+    for (int h = 0; h < 2; ++h)
+      for (int r = 0; r < NC; ++r)
+        for (int m = 0; m < NC; ++m) tt.Pc[(h * NC + r) * NC + m] = lagrange(xc, m, 0.5 * (h + xc[r]));
+    for (OpLevel* v : {&G->fine_view, &G->coarse_view}) {
+      v->op = OP_STOKES_A;
+      v->dim = dim;
+      v->NU = NU;
+    }
+    G->fine_view.k = kf;
+    G->coarse_view.k = kcg;
+    G->fine_view.tnodes = upload(bud, fn);
+    G->coarse_view.cell_u = upload(bud, cu);
+    G->coarse_view.mask = upload(bud, mk);
+    H->groups.push_back(std::move(G));
+  }
+  t.dim = dim;
+  t.kf = fine.k;
+  t.kc = coarse.k;
+  t.ncomp = NU;
+  t.hkind = false;
+  t.hp = std::move(H);
+}
+
 void transfer_prolongate_add(const Transfer& t, const OpLevel& fine, const OpLevel& coarse, int prec, const void* xc,
                              void* xf, cudaStream_t s) {
+  if (t.hp) {
+    const void* src = xc;
+    if (coarse.hp) {  // the coarse function at every slot: complete its constrained entries first
+      void* tmp = coarse.hp->tmp[prec].get();
+      MFNS_CUDA(cudaMemcpyAsync(tmp, xc, coarse.n_dofs * esize(prec), cudaMemcpyDeviceToDevice, s));
+      hp_distribute(coarse, prec, tmp, s);
+      src = tmp;
+    }
+    for (auto& g : t.hp->groups)
+      if (prec == 0)
+        dispatch_transfer<double>(g->t, g->fine_view, g->coarse_view, (const double*)src, (double*)xf, false, s);
+      else
+        dispatch_transfer<float>(g->t, g->fine_view, g->coarse_view, (const float*)src, (float*)xf, false, s);
+    return;
+  }
   if (t.separable) return sep_prolongate_add(t.sep, prec, xc, xf, s);
   if (prec == 0)
     dispatch_transfer<double>(t, fine, coarse, (const double*)xc, (double*)xf, false, s);
@@ -495,7 +639,15 @@ void transfer_prolongate_add(const Transfer& t, const OpLevel& fine, const OpLev
 
 void transfer_restrict(const Transfer& t, const OpLevel& fine, const OpLevel& coarse, int prec, const void* rf,
                        void* rc, cudaStream_t s) {
-  if (t.separable) {
+  if (t.hp) {
+    MFNS_CUDA(cudaMemsetAsync(rc, 0, coarse.n_dofs * esize(prec), s));
+    for (auto& g : t.hp->groups)
+      if (prec == 0)
+        dispatch_transfer<double>(g->t, g->fine_view, g->coarse_view, (const double*)rf, (double*)rc, true, s);
+      else
+        dispatch_transfer<float>(g->t, g->fine_view, g->coarse_view, (const float*)rf, (float*)rc, true, s);
+    if (coarse.hp) hp_condense(coarse, prec, rc, s);  // contributions of constrained entries to masters
+  } else if (t.separable) {
     sep_restrict(t.sep, prec, rf, rc, s);
   } else {
     MFNS_CUDA(cudaMemsetAsync(rc, 0, coarse.n_dofs * esize(prec), s));

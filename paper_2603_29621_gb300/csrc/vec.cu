@@ -82,6 +82,14 @@ template <typename T> __global__ void k_copy_idx(T* y, const T* x, const int32_t
 }
 template <typename T> __global__ void k_set_idx(T* y, T v, const int32_t* idx, int64_t n) { GRID_STRIDE(i, n) y[idx[i]] = v; }
 template <typename T>
+__global__ void k_condense(T* y, const int32_t* mdof, const int32_t* ptr, const int32_t* sdof, const T* w, int64_t n) {
+  GRID_STRIDE(i, n) {
+    T acc = T(0);
+    for (int32_t j = ptr[i]; j < ptr[i + 1]; ++j) acc += w[j] * y[sdof[j]];
+    y[mdof[i]] += acc;
+  }
+}
+template <typename T>
 __global__ void k_copy_map(T* y, const int32_t* ymap, const T* x, const int32_t* xmap, int64_t n, int nc) {
   GRID_STRIDE(t, n * nc) {
     const int64_t i = t / nc, c = t - i * nc;
@@ -263,6 +271,10 @@ template <typename T> void vset_idx(T* y, T v, const int32_t* idx, int64_t n, cu
   LAUNCH(k_set_idx<T>, n, s, y, v, idx, n);
 }
 template <typename T>
+void vcondense(T* y, const int32_t* mdof, const int32_t* ptr, const int32_t* sdof, const T* w, int64_t n, cudaStream_t s) {
+  LAUNCH(k_condense<T>, n, s, y, mdof, ptr, sdof, w, n);
+}
+template <typename T>
 void vcopy_map(T* y, const int32_t* ymap, const T* x, const int32_t* xmap, int64_t n, int nc, cudaStream_t s) {
   LAUNCH(k_copy_map<T>, n * nc, s, y, ymap, x, xmap, n, nc);
 }
@@ -335,6 +347,7 @@ void cg_step_p(T* p, const T* z, const double* num, const double* den, int64_t n
   template void vcopy_idx<T>(T*, const T*, const int32_t*, int64_t, cudaStream_t);                  \
   template void vset_idx<T>(T*, T, const int32_t*, int64_t, cudaStream_t);                          \
   template void vcopy_map<T>(T*, const int32_t*, const T*, const int32_t*, int64_t, int, cudaStream_t); \
+  template void vcondense<T>(T*, const int32_t*, const int32_t*, const int32_t*, const T*, int64_t, cudaStream_t); \
   template void vdistribute<T>(T*, const int32_t*, const int32_t*, const int32_t*, const T*, int64_t, cudaStream_t); \
   template void vcheby<T>(T*, T*, const T*, const T*, const T*, T, T, int64_t, cudaStream_t);       \
   template void vcheby0<T>(T*, T*, const T*, const T*, T, int64_t, cudaStream_t);                   \

@@ -40,6 +40,11 @@ void vcast_f2d(double* y, const float* x, int64_t n, cudaStream_t s);
 template <typename T> void vcopy_idx(T* y, const T* x, const int32_t* idx, int64_t n, cudaStream_t s);
 // y[idx[i]] = v
 template <typename T> void vset_idx(T* y, T v, const int32_t* idx, int64_t n, cudaStream_t s);
+// transpose of a constraint distribution: y[mdof[i]] += sum_{j in ptr[i]..ptr[i+1]} w[j] y[sdof[j]]
+// (every mdof distinct and never an sdof)
+template <typename T>
+void vcondense(T* y, const int32_t* mdof, const int32_t* ptr, const int32_t* sdof, const T* w, int64_t n,
+               cudaStream_t s);
 // node-interleaved blocks of nc entries: y[ymap[i] * nc + c] = x[xmap[i] * nc + c], i < n, c < nc
 template <typename T>
 void vcopy_map(T* y, const int32_t* ymap, const T* x, const int32_t* xmap, int64_t n, int nc, cudaStream_t s);
