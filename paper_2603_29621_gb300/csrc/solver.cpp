@@ -159,6 +159,7 @@ static void build_local_smoothing(Problem& p, const Forest& f, int k, const Phys
       w.x.alloc(bud, b);
       lv->z[prec].alloc(bud, b);
       lv->c[prec].alloc(bud, b);
+      for (DevBuf* v : {&w.r, &w.d, &w.t, &w.b, &w.x, &lv->z[prec], &lv->c[prec]}) MFNS_CUDA(cudaMemset(v->get(), 0, b));
     }
     S->lv.push_back(std::move(lv));
   }
@@ -268,6 +269,9 @@ void alloc_level_workspaces(Problem& p) {
       w.t.alloc(bud, b);
       w.b.alloc(bud, b);
       w.x.alloc(bud, b);
+      // defined contents: a smoothing step with coefficient 0 on the previous direction (the fused
+      // epilogue multiplies it) must not meet NaN bit patterns left in recycled device memory
+      for (DevBuf* v : {&w.r, &w.d, &w.t, &w.b, &w.x}) MFNS_CUDA(cudaMemset(v->get(), 0, b));
     }
   }
 }

@@ -33,7 +33,8 @@ __global__ void k_cheby_idx(const T* x, T* xout, T* d, const T* b, const T* dinv
                             int64_t m) {
   GRID_STRIDE(t, m) {
     const int32_t i = idx[t];
-    const T di = c1 * d[i] + c2 * dinv[i] * (b[i] - x[i]);  // identity row: (A x)_i = x_i
+    // identity row: (A x)_i = x_i; c1 = 0 (a first step) does not read d, which may be unset
+    const T di = (c1 != T(0) ? c1 * d[i] : T(0)) + c2 * dinv[i] * (b[i] - x[i]);
     d[i] = di;
     xout[i] = x[i] + di;
   }
@@ -107,7 +108,7 @@ __global__ void k_distribute(T* x, const int32_t* dof, const int32_t* ptr, const
 template <typename T>
 __global__ void k_cheby(T* x, T* d, const T* b, const T* ax, const T* dinv, T c1, T c2, int64_t n) {
   GRID_STRIDE(i, n) {
-    const T di = c1 * d[i] + c2 * dinv[i] * (b[i] - ax[i]);
+    const T di = (c1 != T(0) ? c1 * d[i] : T(0)) + c2 * dinv[i] * (b[i] - ax[i]);  // c1 = 0: d not read
     d[i] = di;
     x[i] += di;
   }
