@@ -4,8 +4,6 @@
 #include <algorithm>
 #include <array>
 #include <cmath>
-#include <map>
-#include <stdexcept>
 #include <utility>
 
 namespace mfns {
@@ -83,19 +81,30 @@ bool make_hp_space(const Forest& f, const std::vector<int32_t>& degree, HpSpace&
       out.x[g * dim + d] = lat[g * dim + d] / double(N);
       if (lat[g * dim + d] <= 1e-12 || lat[g * dim + d] >= double(N) - 1e-12) out.boundary[g] = 1;
     }
-  // owners of every node and the dominating (level, degree) among them
-  std::vector<std::vector<int32_t>> owners(nn);
-  for (int64_t g = 0; g < nslots; ++g) {
-    auto& o = owners[out.cell_nodes[g]];
-    if (o.empty() || o.back() != slot_cell[g]) o.push_back(slot_cell[g]);
+  // owners of every node (compressed rows) and the dominating (level, degree) among them
+  std::vector<int64_t> own_ptr(nn + 1, 0);
+  for (int64_t j = 0; j < nslots; ++j) own_ptr[out.cell_nodes[j] + 1]++;
+  for (int64_t g = 0; g < nn; ++g) own_ptr[g + 1] += own_ptr[g];
+  std::vector<int32_t> own(nslots);
+  {
+    std::vector<int64_t> fill(own_ptr.begin(), own_ptr.end() - 1);
+    for (int64_t j = 0; j < nslots; ++j) own[fill[out.cell_nodes[j]]++] = slot_cell[j];
   }
-  std::vector<std::pair<int, int>> dom(nn, {1 << 30, 1 << 30});
-  for (int64_t g = 0; g < nn; ++g)
-    for (int32_t c : owners[g]) dom[g] = std::min(dom[g], std::make_pair((int)f.lev[c], (int)degree[c]));
+  auto dom_key = [&](int32_t c) { return std::make_pair((int)f.lev[c], (int)degree[c]); };
   const Lattice latt = make_lattice(f);
-  // direct constraints
-  std::map<int32_t, std::vector<std::pair<int32_t, double>>> direct;
+  // direct constraints, in ascending node order: index of the node's row (-1: free)
+  std::vector<int32_t> row_of(nn, -1);
+  std::vector<int32_t> d_node, d_ptr(1, 0), d_master;
+  std::vector<double> d_w;
   for (int64_t g = 0; g < nn; ++g) {
+    const int32_t* ob = own.data() + own_ptr[g];
+    const int32_t* oe = own.data() + own_ptr[g + 1];
+    std::pair<int, int> dom = {1 << 30, 1 << 30};
+    int kmin_owner = 1 << 30;
+    for (const int32_t* o = ob; o != oe; ++o) {
+      dom = std::min(dom, dom_key(*o));
+      kmin_owner = std::min<int>(kmin_owner, degree[*o]);
+    }
     int64_t lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
     for (int d = 0; d < dim; ++d) {
       const double t = lat[g * dim + d];
@@ -108,64 +117,87 @@ bool make_hp_space(const Forest& f, const std::vector<int32_t>& degree, HpSpace&
       for (int64_t y = lo[1]; y <= hi[1]; ++y)
         for (int64_t xx = lo[0]; xx <= hi[0]; ++xx) {
           const int32_t c = latt.at((int)xx, (int)y, (int)z);
-          if (std::find(owners[g].begin(), owners[g].end(), c) != owners[g].end()) continue;
-          const std::pair<int, int> key = {f.lev[c], degree[c]};
-          if (key < dom[g] && (best < 0 || key < best_key || (key == best_key && c < best))) {
+          if (std::find(ob, oe, c) != oe) continue;
+          const std::pair<int, int> key = dom_key(c);
+          if (key < dom && (best < 0 || key < best_key || (key == best_key && c < best))) {
             best_key = key;
             best = c;
           }
         }
     if (best < 0) continue;
-    if (best_key.first < dom[g].first) {  // hanging on a coarser cell: no fine owner of lower degree
-      int kmin = 1 << 30;
-      for (int32_t c : owners[g]) kmin = std::min<int>(kmin, degree[c]);
-      if (best_key.second > kmin) return fail("unsupported: a hanging face whose coarse cell has a higher degree than a fine cell");
-    }
+    // hanging on a coarser cell: no fine owner of lower degree
+    if (best_key.first < dom.first && best_key.second > kmin_owner)
+      return fail("unsupported: a hanging face whose coarse cell has a higher degree than a fine cell");
     // the dominating cell's finite-element function at the node
     const int k = degree[best], np = k + 1;
     const double s = double(int64_t(1) << (L - f.lev[best]));
     double xi[3] = {0, 0, 0};
     for (int d = 0; d < dim; ++d) xi[d] = std::min(1.0, std::max(0.0, (lat[g * dim + d] - f.crd[3 * best + d] * s) / s));
-    std::vector<std::pair<int32_t, double>> w;
+    double l1[3][9];
+    for (int d = 0; d < dim; ++d)
+      for (int a = 0; a < np; ++a) l1[d][a] = lagrange(gll[k], a, xi[d]);
+    row_of[g] = (int32_t)d_node.size();
+    d_node.push_back((int32_t)g);
     for (int64_t i = 0; i < out.cell_ptr[best + 1] - out.cell_ptr[best]; ++i) {
       const int a[3] = {int(i % np), int((i / np) % np), dim == 3 ? int(i / (np * np)) : 0};
       double v = 1.0;
-      for (int d = 0; d < dim; ++d) v *= lagrange(gll[k], a[d], xi[d]);
-      if (std::fabs(v) > 1e-13) w.push_back({out.cell_nodes[out.cell_ptr[best] + i], v});
+      for (int d = 0; d < dim; ++d) v *= l1[d][a[d]];
+      if (std::fabs(v) > 1e-13) {
+        d_master.push_back(out.cell_nodes[out.cell_ptr[best] + i]);
+        d_w.push_back(v);
+      }
     }
-    direct[(int32_t)g] = std::move(w);
+    d_ptr.push_back((int32_t)d_master.size());
   }
-  // resolve chains to free masters
-  std::map<int32_t, std::vector<std::pair<int32_t, double>>> resolved;
-  auto resolve = [&](int32_t g, auto&& self, int depth) -> const std::vector<std::pair<int32_t, double>>& {
-    auto it = resolved.find(g);
-    if (it != resolved.end()) return it->second;
-    if (depth > 64) throw std::runtime_error("constraint cycle");
-    std::map<int32_t, double> acc;
-    for (auto& mw : direct[g]) {
-      if (direct.count(mw.first)) {
-        for (auto& mm : self(mw.first, self, depth + 1)) acc[mm.first] += mw.second * mm.second;
-      } else {
-        acc[mw.first] += mw.second;
+  // resolve chains to free masters (rows in ascending node order; a row's masters may be rows)
+  std::vector<char> state(d_node.size(), 0);  // 0 open, 1 in progress, 2 resolved
+  std::vector<std::vector<std::pair<int32_t, double>>> res(d_node.size());
+  std::vector<std::pair<int32_t, int>> stack;
+  for (size_t r0 = 0; r0 < d_node.size(); ++r0) {
+    if (state[r0] == 2) continue;
+    stack.assign(1, {(int32_t)r0, 0});
+    state[r0] = 1;
+    while (!stack.empty()) {
+      const int32_t r = stack.back().first;
+      bool pushed = false;
+      for (int32_t j = d_ptr[r]; j < d_ptr[r + 1] && !pushed; ++j) {
+        const int32_t q = row_of[d_master[j]];
+        if (q < 0 || state[q] == 2) continue;
+        if (state[q] == 1) return fail("constraint cycle");
+        state[q] = 1;
+        stack.push_back({q, 0});
+        pushed = true;
       }
+      if (pushed) continue;
+      std::vector<std::pair<int32_t, double>> acc;
+      for (int32_t j = d_ptr[r]; j < d_ptr[r + 1]; ++j) {
+        const int32_t m = d_master[j], q = row_of[m];
+        if (q < 0) {
+          acc.push_back({m, d_w[j]});
+        } else {
+          for (auto& mw : res[q]) acc.push_back({mw.first, d_w[j] * mw.second});
+        }
+      }
+      std::sort(acc.begin(), acc.end(), [](const auto& x, const auto& y) { return x.first < y.first; });
+      auto& out_r = res[r];
+      for (auto& mw : acc) {
+        if (!out_r.empty() && out_r.back().first == mw.first)
+          out_r.back().second += mw.second;
+        else
+          out_r.push_back(mw);
+      }
+      state[r] = 2;
+      stack.pop_back();
     }
-    auto& r = resolved[g];
-    for (auto& kv : acc) r.push_back(kv);
-    return r;
-  };
+  }
   out.hang_ptr.assign(1, 0);
-  try {
-    for (auto& kv : direct) {
-      const auto& r = resolve(kv.first, resolve, 0);
-      out.hang_node.push_back(kv.first);
-      for (auto& mw : r) {
-        out.hang_master.push_back(mw.first);
-        out.hang_w.push_back(mw.second);
-      }
-      out.hang_ptr.push_back((int32_t)out.hang_master.size());
+  for (size_t r = 0; r < d_node.size(); ++r) {
+    out.hang_node.push_back(d_node[r]);
+    for (auto& mw : res[r]) {
+      out.hang_master.push_back(mw.first);
+      out.hang_w.push_back(mw.second);
     }
-  } catch (const std::exception& e) {
-    return fail(e.what());
+    out.hang_ptr.push_back((int32_t)out.hang_master.size());
   }
   return true;
 }
