@@ -199,3 +199,45 @@ def test_coarse_higher_degree_across_a_hanging_face_is_rejected():
     deg = 3 - f.cells[:, 0]                          # coarse cells 3, refined cells 2
     with pytest.raises(NotImplementedError):
         hp.HpNodeSet(f, deg)
+
+
+def test_taylor_hood_uniform_degree_is_the_standard_operator():
+    f = _ball(2, 3, 1)
+    H = hp.HpProblem(f, np.full(f.n_cells, 3), "stokes", nu=0.8)
+    S = assemble.Problem(f, "stokes", 3, nu=0.8)
+    xh, fh = H.dofs.support_points()
+    xs, fs = S.dofs.support_points()
+    key = {(tuple(np.rint(x * 2 ** 30).astype(np.int64)), c): i for i, (x, c) in enumerate(zip(xs, fs))}
+    perm = np.array([key[(tuple(np.rint(x * 2 ** 30).astype(np.int64)), c)] for x, c in zip(xh, fh)])
+    assert np.array_equal(H.dofs.constrained, S.dofs.constrained[perm])
+    Ah, As = H.assemble(), S.assemble()[perm][:, perm]
+    assert abs(Ah - As).max() <= 1e-13 * abs(As).max()
+
+
+def test_taylor_hood_hp_energy_closed_form():
+    """u = (phi, 2 phi), phi = x(1-x)y(1-y), p = x - 1/2 on an hp mesh with velocity degrees 2..4
+    (pressure 1..3): x^T A x = nu int |grad u|^2 - 2 int p div u = nu / 9 + 1/18."""
+    f = _ball(2, 3, 1)
+    deg = _degrees(f, 2)
+    nu = 0.6
+    P = hp.HpProblem(f, deg, "stokes", nu=nu)
+    d = P.dofs
+
+    def fields(x):
+        phi = np.prod(x * (1 - x), axis=1)
+        return np.stack([phi, 2 * phi, x[:, 0] - 0.5], axis=1)
+
+    xv = d.interpolate(fields)
+    assert np.abs(d.distribute(xv) - xv).max() <= 1e-14
+    energy = xv @ (P.assemble_K() @ xv)
+    exact = nu / 9.0 + 1.0 / 18.0
+    assert abs(energy - exact) <= 1e-12 * exact
+    # the pressure space is conforming across every interface too
+    rng = np.random.default_rng(5)
+    x = d.distribute(rng.uniform(-1, 1, d.n_dofs))
+    worst = 0.0
+    for a, b, pts in _face_pieces(f):
+        pa = P.evaluate_in(x, pts, np.full(len(pts), a), 1, 0)
+        pb = P.evaluate_in(x, pts, np.full(len(pts), b), 1, 0)
+        worst = max(worst, np.abs(pa - pb).max())
+    assert worst <= 1e-12
