@@ -229,6 +229,55 @@ def solve_section(api, L, inputs, torch, tol_ns=1e-13, tol_stokes=1e-14):
     return out
 
 
+def hp_section(api, L, inputs, torch):
+    """Section 3 (hp-adaptivity): the vector Laplacian on the ball-refined 16^3 mesh with a degree per
+    cell (2 + refinement level + parity of the root cell's x index: 2..4, never lower on the fine side
+    of a hanging face), hp-multigrid (every degree lowered by one per level, then h) in FP32 inside
+    FP64 FGMRES, beside the same mesh with degree 2 everywhere.  Errors are recorded, not raised:
+    this section runs last."""
+    out = {}
+    ctx = None
+    try:
+        ctx = api.Context(torch.cuda.current_device())
+        for name, use_hp in (("hp_degrees_2_to_4", True), ("uniform_degree_2", False)):
+            m = api.Mesh(ctx, 3, 16)
+            m.refine_ball((0.5, 0.5, 0.5), 0.25, 1)
+            cells = m.cells()
+            deg = (2 + cells[:, 0] + ((cells[:, 1] >> cells[:, 0]) % 2)).astype(np.int32)
+            desc = dict(kind=L.STOKES_A, nu=1.0, tol=1e-10, mg_precision=L.FP32, maxit=200)
+            t0 = time.perf_counter()
+            if use_hp:
+                p = api.Problem(ctx, m, degrees=deg, degree=int(deg.max()), **desc)
+            else:
+                p = api.Problem(ctx, m, degree=2, **desc)
+            setup = time.perf_counter() - t0
+            xyz, fld = p.support_points()
+            xs = torch.tensor(inputs.smooth_solution(xyz, fld, 3), device="cuda")
+            b = torch.empty_like(xs)
+            p.vmult(xs, b)
+            x = torch.zeros_like(xs)
+            p.solve(b, x, raise_on_nonconvergence=False)            # warm-up (graph capture)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            info = p.solve(b, x, raise_on_nonconvergence=False)
+            torch.cuda.synchronize()
+            out[name] = {"dofs": p.info.n_dofs, "cells": p.info.n_cells, "levels": p.info.n_levels,
+                         "degrees": [int(deg.min()), int(deg.max())] if use_hp else [2, 2],
+                         "iterations": info.iterations, "converged": bool(info.converged),
+                         "rel_residual": info.rel_residual, "solve_s": time.perf_counter() - t0, "setup_s": setup,
+                         "error_vs_xstar": float(torch.linalg.norm(x - xs) / torch.linalg.norm(xs))}
+            p.close()
+            m.close()
+    except Exception as e:  # noqa: BLE001 -- reported in the JSON line
+        out["error"] = f"{type(e).__name__}: {e}"
+    try:
+        if ctx is not None:
+            ctx.close()
+    except Exception as e:  # noqa: BLE001
+        out.setdefault("error", f"{type(e).__name__}: {e}")
+    return out
+
+
 def serving_section(api, L, torch, count):
     """Config 5, bounded: a seeded Poisson stream of `count` requests (n in 8..48, k in 1..3, nu
     log-uniform in [1e-3, 1], Stokes / stabilised NS 50/50, b = A x*), offered at 0.8 x the measured
@@ -504,6 +553,7 @@ def run_ours(args, world, rank, local):
         line["transient"] = transient_section(api, L, inputs, torch)
         line["serving"] = serving_section(api, L, torch, args.serve_requests)
         line["solves_serving_wall_s"] = time.perf_counter() - t0
+        line["hp"] = hp_section(api, L, inputs, torch)
     if world == 1 and not args.no_cpu_baseline:
         cb = cpu_baseline()
         cb.pop("ms_per_step", None)
