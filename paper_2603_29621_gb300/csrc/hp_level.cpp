@@ -10,7 +10,6 @@
 #include <algorithm>
 #include <map>
 #include <numeric>
-#include <set>
 
 #include "problem.hpp"
 #include "vec.hpp"
@@ -21,29 +20,6 @@ template <typename T>
 static DevBuf upload_as(Budget* bud, const std::vector<double>& v) {
   std::vector<T> t(v.begin(), v.end());
   return upload(bud, t);
-}
-
-// greedy colouring of a subset of cells so that no two cells of a colour share a node
-static int color_subset(const HpSpace& sp, const std::vector<int32_t>& cells, std::vector<int32_t>& color) {
-  std::map<int32_t, std::vector<int32_t>> node_cells;
-  for (int32_t i = 0; i < (int32_t)cells.size(); ++i) {
-    const int32_t c = cells[i];
-    for (int64_t j = sp.cell_ptr[c]; j < sp.cell_ptr[c + 1]; ++j) node_cells[sp.cell_nodes[j]].push_back(i);
-  }
-  color.assign(cells.size(), -1);
-  int ncol = 0;
-  for (int32_t i = 0; i < (int32_t)cells.size(); ++i) {
-    std::set<int> used;
-    const int32_t c = cells[i];
-    for (int64_t j = sp.cell_ptr[c]; j < sp.cell_ptr[c + 1]; ++j)
-      for (int32_t o : node_cells[sp.cell_nodes[j]])
-        if (color[o] >= 0) used.insert(color[o]);
-    int col = 0;
-    while (used.count(col)) ++col;
-    color[i] = col;
-    ncol = std::max(ncol, col + 1);
-  }
-  return ncol;
 }
 
 void build_hp_oplevel(OpLevel& lv, const Forest& f, const std::vector<int32_t>& degree, const Physics& ph,
@@ -75,7 +51,7 @@ void build_hp_oplevel(OpLevel& lv, const Forest& f, const std::vector<int32_t>& 
     auto g = std::make_unique<HpGroup>();
     g->k = k;
     std::vector<int32_t> color;
-    const int ncol = color_subset(sp, cells, color);
+    const int ncol = hp_color_cells(sp, cells, color);
     std::vector<int32_t> order(cells.size());
     std::iota(order.begin(), order.end(), 0);
     std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return color[a] < color[b]; });
@@ -177,50 +153,19 @@ void build_hp_oplevel(OpLevel& lv, const Forest& f, const std::vector<int32_t>& 
   hp->ct_slave = upload(bud, cs);
   hp->ct_w[0] = upload_as<double>(bud, cw);
   hp->ct_w[1] = upload_as<float>(bud, cw);
-  // probing groups for the diagonal: free nodes m, n may share a group only if no cell holds a
-  // node of S(m) = {m} + its slaves and one of S(n)
-  std::vector<std::vector<int32_t>> masters_of(sp.n_nodes);  // free node -> itself; hanging -> masters
-  for (int64_t g = 0; g < sp.n_nodes; ++g)
-    if (!sp.boundary[g] && !hang[g]) masters_of[g].push_back((int32_t)g);
-  for (size_t i = 0; i < sp.hang_node.size(); ++i) {
-    const int32_t g = sp.hang_node[i];
-    if (sp.boundary[g]) continue;
-    for (int32_t j = sp.hang_ptr[i]; j < sp.hang_ptr[i + 1]; ++j)
-      if (!sp.boundary[sp.hang_master[j]]) masters_of[g].push_back(sp.hang_master[j]);
-  }
-  std::vector<std::vector<int32_t>> node_cells(sp.n_nodes);
-  for (size_t c = 0; c < f.n_cells(); ++c)
-    for (int64_t j = sp.cell_ptr[c]; j < sp.cell_ptr[c + 1]; ++j) node_cells[sp.cell_nodes[j]].push_back((int32_t)c);
-  std::vector<std::vector<int32_t>> cell_masters(f.n_cells());  // free masters reached by each cell
-  for (size_t c = 0; c < f.n_cells(); ++c) {
-    auto& v = cell_masters[c];
-    for (int64_t j = sp.cell_ptr[c]; j < sp.cell_ptr[c + 1]; ++j)
-      for (int32_t m : masters_of[sp.cell_nodes[j]]) v.push_back(m);
-    std::sort(v.begin(), v.end());
-    v.erase(std::unique(v.begin(), v.end()), v.end());
-  }
-  std::vector<std::vector<int32_t>> master_cells(sp.n_nodes);
-  for (size_t c = 0; c < f.n_cells(); ++c)
-    for (int32_t m : cell_masters[c]) master_cells[m].push_back((int32_t)c);
-  std::vector<int32_t> pcol(sp.n_nodes, -1);
-  int npc = 0;
-  for (int64_t m = 0; m < sp.n_nodes; ++m) {
-    if (sp.boundary[m] || hang[m]) continue;
-    std::set<int> used;
-    for (int32_t c : master_cells[m])
-      for (int32_t o : cell_masters[c])
-        if (pcol[o] >= 0) used.insert(pcol[o]);
-    int col = 0;
-    while (used.count(col)) ++col;
-    pcol[m] = col;
-    npc = std::max(npc, col + 1);
-  }
+  // probing groups for the diagonal: free nodes that no cell reaches together
+  std::vector<char> free_node(sp.n_nodes, 0);
+  for (int64_t g = 0; g < sp.n_nodes; ++g) free_node[g] = !sp.boundary[g] && !hang[g];
+  std::vector<int32_t> pcol;
+  const int npc = hp_probe_groups(sp, free_node, pcol);
+  std::vector<std::vector<int32_t>> bucket(npc);  // free nodes of every group, ascending
+  for (int64_t m = 0; m < sp.n_nodes; ++m)
+    if (pcol[m] >= 0) bucket[pcol[m]].push_back((int32_t)m);
   std::vector<int32_t> pd;
   hp->probe_ptr.assign(1, 0);
   for (int col = 0; col < npc; ++col)
     for (int c = 0; c < dim; ++c) {
-      for (int64_t m = 0; m < sp.n_nodes; ++m)
-        if (pcol[m] == col) pd.push_back((int32_t)(m * dim + c));
+      for (int32_t m : bucket[col]) pd.push_back((int32_t)(m * dim + c));
       hp->probe_ptr.push_back((int64_t)pd.size());
     }
   hp->probe_dofs = upload(bud, pd);

@@ -202,4 +202,96 @@ bool make_hp_space(const Forest& f, const std::vector<int32_t>& degree, HpSpace&
   return true;
 }
 
+int hp_color_cells(const HpSpace& sp, const std::vector<int32_t>& cells, std::vector<int32_t>& color) {
+  // node -> subset positions (compressed rows)
+  std::vector<int64_t> ptr(sp.n_nodes + 1, 0);
+  for (int32_t c : cells)
+    for (int64_t j = sp.cell_ptr[c]; j < sp.cell_ptr[c + 1]; ++j) ptr[sp.cell_nodes[j] + 1]++;
+  for (int64_t g = 0; g < sp.n_nodes; ++g) ptr[g + 1] += ptr[g];
+  std::vector<int32_t> idx(ptr[sp.n_nodes]);
+  {
+    std::vector<int64_t> fill(ptr.begin(), ptr.end() - 1);
+    for (int32_t i = 0; i < (int32_t)cells.size(); ++i)
+      for (int64_t j = sp.cell_ptr[cells[i]]; j < sp.cell_ptr[cells[i] + 1]; ++j) idx[fill[sp.cell_nodes[j]]++] = i;
+  }
+  color.assign(cells.size(), -1);
+  std::vector<int32_t> stamp;  // stamp[col] == i: colour col is taken by a neighbour of cell i
+  int ncol = 0;
+  for (int32_t i = 0; i < (int32_t)cells.size(); ++i) {
+    for (int64_t j = sp.cell_ptr[cells[i]]; j < sp.cell_ptr[cells[i] + 1]; ++j) {
+      const int32_t g = sp.cell_nodes[j];
+      for (int64_t q = ptr[g]; q < ptr[g + 1]; ++q) {
+        const int32_t o = idx[q];
+        if (color[o] >= 0) {
+          if ((size_t)color[o] >= stamp.size()) stamp.resize(color[o] + 1, -1);
+          stamp[color[o]] = i;
+        }
+      }
+    }
+    int col = 0;
+    while ((size_t)col < stamp.size() && stamp[col] == i) ++col;
+    color[i] = col;
+    ncol = std::max(ncol, col + 1);
+  }
+  return ncol;
+}
+
+int hp_probe_groups(const HpSpace& sp, const std::vector<char>& free_node, std::vector<int32_t>& group) {
+  const int64_t nn = sp.n_nodes;
+  const size_t nc = sp.cell_ptr.size() - 1;
+  // free masters reached by every node: itself when free, its free masters when constrained
+  std::vector<int64_t> mptr(nn + 1, 0);
+  std::vector<int32_t> hrow(nn, -1);
+  for (size_t i = 0; i < sp.hang_node.size(); ++i) hrow[sp.hang_node[i]] = (int32_t)i;
+  auto for_masters = [&](int32_t g, auto&& fn) {
+    if (free_node[g]) {
+      fn(g);
+    } else if (hrow[g] >= 0 && !sp.boundary[g]) {  // Dirichlet entries do not couple
+      for (int32_t j = sp.hang_ptr[hrow[g]]; j < sp.hang_ptr[hrow[g] + 1]; ++j)
+        if (free_node[sp.hang_master[j]]) fn(sp.hang_master[j]);
+    }
+  };
+  // cell -> its free masters (compressed, duplicates removed)
+  std::vector<int64_t> cptr(nc + 1, 0);
+  std::vector<int32_t> cidx;
+  for (size_t c = 0; c < nc; ++c) {
+    const size_t start = cidx.size();
+    for (int64_t j = sp.cell_ptr[c]; j < sp.cell_ptr[c + 1]; ++j) for_masters(sp.cell_nodes[j], [&](int32_t m) { cidx.push_back(m); });
+    std::sort(cidx.begin() + start, cidx.end());
+    cidx.erase(std::unique(cidx.begin() + start, cidx.end()), cidx.end());
+    cptr[c + 1] = (int64_t)cidx.size();
+  }
+  // master -> cells (compressed)
+  std::vector<int64_t> optr(nn + 1, 0);
+  for (int32_t m : cidx) optr[m + 1]++;
+  for (int64_t g = 0; g < nn; ++g) optr[g + 1] += optr[g];
+  std::vector<int32_t> oidx(optr[nn]);
+  {
+    std::vector<int64_t> fill(optr.begin(), optr.end() - 1);
+    for (size_t c = 0; c < nc; ++c)
+      for (int64_t q = cptr[c]; q < cptr[c + 1]; ++q) oidx[fill[cidx[q]]++] = (int32_t)c;
+  }
+  group.assign(nn, -1);
+  std::vector<int64_t> stamp;
+  int ng = 0;
+  for (int64_t m = 0; m < nn; ++m) {
+    if (!free_node[m]) continue;
+    for (int64_t q = optr[m]; q < optr[m + 1]; ++q) {
+      const int32_t c = oidx[q];
+      for (int64_t r = cptr[c]; r < cptr[c + 1]; ++r) {
+        const int32_t o = group[cidx[r]];
+        if (o >= 0) {
+          if ((size_t)o >= stamp.size()) stamp.resize(o + 1, -1);
+          stamp[o] = m;
+        }
+      }
+    }
+    int col = 0;
+    while ((size_t)col < stamp.size() && stamp[col] == m) ++col;
+    group[m] = col;
+    ng = std::max(ng, col + 1);
+  }
+  return ng;
+}
+
 }  // namespace mfns

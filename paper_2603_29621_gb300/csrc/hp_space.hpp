@@ -34,4 +34,14 @@ struct HpSpace {
 // Builds the space; false with a message in err for an unsupported configuration or bad input.
 bool make_hp_space(const Forest& f, const std::vector<int32_t>& degree, HpSpace& out, std::string* err);
 
+// Greedy colouring of a subset of cells: no two cells of one colour share a node.  color[i] is the
+// colour of cells[i]; returns the number of colours.
+int hp_color_cells(const HpSpace& sp, const std::vector<int32_t>& cells, std::vector<int32_t>& color);
+
+// Groups of free nodes for probing the diagonal of C^T K C: two free nodes share a group only if no
+// cell holds a node whose free masters include both (a free node is its own master).  `free_node`
+// marks the free nodes; masters of constrained nodes are hang_master entries that are free.
+// group[g] is the group of free node g (-1 otherwise); returns the number of groups.
+int hp_probe_groups(const HpSpace& sp, const std::vector<char>& free_node, std::vector<int32_t>& group);
+
 }  // namespace mfns
