@@ -28,6 +28,9 @@ assembly, no sum factorisation):
 * ``ls``        -- local-smoothing multigrid (Section 2): level spaces on the
                    refined parts of the mesh with Dirichlet conditions on the
                    refinement edge, as a multiplicative subspace correction.
+* ``spacetime`` -- space-time finite elements for transient Stokes (Section 4):
+                   DG(r) in time on right Radau points, the stage-major
+                   Kronecker operator G_Q (x) M + tau I_Q (x) A, time transfers.
 * ``hp``        -- hp-adaptive continuous spaces (a degree per cell, h- and
                    p-hanging constraints), the vector Laplacian and Taylor--Hood
                    Stokes on them, hp transfers and the hp-multigrid hierarchy

@@ -1,0 +1,101 @@
+"""Pins of the oracle's space-time discretisation (Section 4).
+
+* Right Gauss--Radau points in closed form (Q = 1, 2, 3).
+* DG(r) in time on a scalar ODE y' = lambda y: the one-slab amplification is the (r, r+1) Pade
+  approximant of exp (the Radau IIA stability function), for r = 0..3.
+* DG(r) reproduces solutions that are polynomials of degree <= r in time.
+* With r = 0 the Kronecker operator is backward Euler, M + tau A.
+* One slab of the transient Stokes problem reproduces a manufactured discrete solution
+  c(t) (U, P), c a polynomial of degree <= r (pressure up to one constant per stage), on a mesh with
+  hanging nodes.
+* Time transfers are exact for polynomials of the coarse temporal degree.
+"""
+from math import factorial
+
+import numpy as np
+import pytest
+
+from oracle import mesh, spacetime
+
+
+def test_radau_points_closed_form():
+    assert np.allclose(spacetime.radau_right(1), [1.0], atol=0, rtol=0)
+    assert np.allclose(spacetime.radau_right(2), [1 / 3, 1.0], atol=1e-15)
+    s6 = np.sqrt(6.0)
+    assert np.allclose(spacetime.radau_right(3), [(4 - s6) / 10, (4 + s6) / 10, 1.0], atol=1e-15)
+
+
+def _pade(k, m, w):
+    num = sum(factorial(k + m - j) * factorial(k) / (factorial(k + m) * factorial(j) * factorial(k - j)) * w ** j
+              for j in range(k + 1))
+    den = sum(factorial(k + m - j) * factorial(m) / (factorial(k + m) * factorial(j) * factorial(m - j)) * (-w) ** j
+              for j in range(m + 1))
+    return num / den
+
+
+@pytest.mark.parametrize("r", [0, 1, 2, 3])
+def test_amplification_is_the_radau_pade_approximant(r):
+    t, M, A, m = spacetime.temporal_matrices(r)
+    for w in (-0.3, -1.0, -4.0, -25.0, 0.4):
+        y = np.linalg.solve(A - w * M, m)            # y' = lambda y, w = lambda tau, y(t_{n-1}) = 1
+        assert abs(y[-1] - _pade(r, r + 1, w)) <= 1e-13 * max(1.0, abs(y[-1]))
+
+
+@pytest.mark.parametrize("r", [0, 1, 2, 3])
+def test_polynomials_of_degree_r_in_time_are_exact(r):
+    t, M, A, m = spacetime.temporal_matrices(r)
+    rng = np.random.default_rng(r)
+    a = rng.uniform(-1, 1, r + 1)                    # y(s) = sum a_j s^j on the reference slab
+    lam, tau = -2.5, 0.7
+    y = lambda s: sum(a[j] * s ** j for j in range(r + 1))
+    dy = lambda s: sum(j * a[j] * s ** (j - 1) for j in range(1, r + 1))
+    # y' = lam y + f  on [0, tau], with s = t / tau:  f(t) = dy/tau - lam y
+    from oracle import fe
+    xg, wg = fe.gauss(r + 3)
+    phi = np.array([[fe.lagrange_value(t, j, s) for s in xg] for j in range(r + 1)])
+    F = tau * (phi * wg[None, :]) @ np.array([dy(s) / tau - lam * y(s) for s in xg])
+    stages = np.linalg.solve(A - lam * tau * M, F + m * y(0.0))
+    assert np.abs(stages - np.array([y(s) for s in t])).max() <= 1e-13
+
+
+def test_dg0_kronecker_operator_is_backward_euler():
+    st = spacetime.SpaceTimeStokes(mesh.uniform(2, 3), 2, 0, nu=0.7, tau=0.3)
+    assert np.allclose(st.G_Q, [[1.0]])
+    K = st.operator()
+    assert abs(K - (st.M + 0.3 * st.A)).max() <= 1e-15
+
+
+@pytest.mark.parametrize("r", [0, 1, 2])
+def test_slab_reproduces_a_manufactured_solution(r):
+    f = mesh.refine_ball(mesh.uniform(2, 3), (0.3, 0.35, 0.4), 0.3, 1)
+    tau, t0 = 0.25, 0.4
+    st = spacetime.SpaceTimeStokes(f, 2, r, nu=0.8, tau=tau)
+    d = st.space.dofs
+    assert d.hanging.any()
+    rng = np.random.default_rng(7 + r)
+    X = d.distribute(rng.uniform(-1, 1, d.n_dofs))   # a discrete (U, P) with consistent hanging entries
+    a = rng.uniform(-1, 1, r + 1)
+    c = lambda t: sum(a[j] * (t - t0) ** j for j in range(r + 1))
+    dc = lambda t: sum(j * a[j] * (t - t0) ** (j - 1) for j in range(1, r + 1))
+    MX, AX = st.M @ X, st.A @ X
+    load = lambda t: dc(t) * MX + c(t) * AX          # M u' + A x = f on the free rows
+    b = st.rhs(load, c(t0) * X, t0)
+    stage_t = t0 + st.nodes * tau
+    b = st.set_constrained(b, [c(t) * X for t in stage_t])
+    K = st.operator().toarray()
+    x = np.linalg.lstsq(K, b, rcond=None)[0].reshape(st.Q, st.n)
+    pres = st.space.pressure_dofs()
+    for q, t in enumerate(stage_t):
+        e = x[q] - c(t) * X
+        e[pres] -= e[pres].mean()
+        assert np.abs(e).max() <= 1e-10 * np.abs(X).max(), (q, np.abs(e).max())
+
+
+@pytest.mark.parametrize("rc,rf", [(0, 1), (1, 2), (1, 3), (2, 3)])
+def test_time_transfer_exact_for_coarse_polynomials(rc, rf):
+    P = spacetime.time_prolongation(rc, rf)
+    tc, tf = spacetime.radau_right(rc + 1), spacetime.radau_right(rf + 1)
+    rng = np.random.default_rng(rc * 10 + rf)
+    a = rng.uniform(-1, 1, rc + 1)
+    poly = lambda s: sum(a[j] * s ** j for j in range(rc + 1))
+    assert np.abs(P @ poly(tc) - poly(tf)).max() <= 1e-14
