@@ -144,3 +144,140 @@ class SpaceTimeStokes:
         for q in range(self.Q):
             bb[q, con] = self.tau * stage_values[q][con]
         return bb.ravel()
+
+
+# -- space-time multigrid (hp-STMG, Section 4) ----------------------------------------------------
+class StLevel:
+    """One level: the slab operator, the transfer from the next coarser level, and the patches of the
+    space-time Schwarz smoother over all stages of the slab -- 'cell': one spatial cell (its free
+    velocity and pressure DoFs); 'vertex': the cells around one mesh vertex (the free DoFs whose
+    node lies inside that star, i.e. every cell holding the node is in the star)."""
+
+    def __init__(self, forest, k, r, nu, tau, patch="vertex"):
+        self.k, self.r = k, r
+        self.st = SpaceTimeStokes(forest, k, r, nu=nu, tau=tau)
+        self.K = self.st.operator()
+        self.P = None
+        st = self.st
+        d = st.space.dofs
+        cd = st.space.cell_dofs                                  # (nc, n_local)
+        n, Q = st.n, st.Q
+        self.patches, self.inv = [], []
+        mult = np.zeros(Q * n)
+        Kd = self.K.tocsr()
+        for loc in _patch_dofs(st.space, patch):
+            idx = (np.arange(Q)[:, None] * n + loc[None, :]).ravel()
+            Kp = Kd[idx][:, idx].toarray()
+            self.patches.append(idx)
+            try:
+                self.inv.append(np.linalg.inv(Kp))
+            except np.linalg.LinAlgError:      # a patch holding every pressure DoF: constant pressure null
+                self.inv.append(np.linalg.pinv(Kp))
+            mult[idx] += 1.0
+        self.weight = np.where(mult > 0, 1.0 / np.maximum(mult, 1.0), 0.0)
+        con = np.zeros((Q, n), dtype=bool)
+        con[:, d.constrained] = True
+        self.con = con.ravel()
+
+    def schwarz(self, r):
+        """Weighted additive Schwarz: sum of the patch solves, each entry divided by the number of
+        patches that hold it; constrained rows (tau times identity) solved exactly."""
+        z = np.zeros_like(r)
+        for idx, Ki in zip(self.patches, self.inv):
+            z[idx] += Ki @ r[idx]
+        z *= self.weight
+        z[self.con] = r[self.con] / self.st.tau
+        return z
+
+
+def _patch_dofs(problem, patch):
+    """Free DoFs of every smoother patch (arrays of spatial DoF indices)."""
+    d = problem.dofs
+    cd = problem.cell_dofs
+    if patch == "cell":
+        return [np.unique(cd[c][d.free[cd[c]]]) for c in range(cd.shape[0])]
+    # vertex stars: cells holding each vertex of the mesh (vertices = nodes of the Q1 space)
+    f = problem.forest
+    dim = f.dim
+    corners = fe.tensor_index(dim, 2)
+    h, org = f.h(), f.origin()
+    key = lambda x: tuple(np.rint(np.asarray(x) * 2 ** 30).astype(np.int64))
+    star = {}
+    for c in range(f.n_cells):
+        for cr in corners:
+            star.setdefault(key(org[c] + cr * h[c]), []).append(c)
+    # cells holding each DoF's node (its closed box contains the node)
+    xs, _ = d.support_points()
+    holders = [set() for _ in range(d.n_dofs)]
+    for c in range(f.n_cells):
+        for g in cd[c]:
+            holders[g].add(c)
+    out = []
+    for cells in star.values():
+        cs = set(cells)
+        loc = sorted({g for c in cells for g in cd[c] if d.free[g] and holders[g] <= cs})
+        if loc:
+            out.append(np.array(loc))
+    return out
+
+
+def stmg_levels(forest, k, r, nu=1.0, tau=0.1, stop_n=2, patch="vertex"):
+    """Levels finest first: spatial degree halved (Taylor--Hood keeps k >= 2), then the temporal
+    degree halved (DG(r) -> DG(r // 2)), then global h-coarsening in space; no geometric coarsening
+    in time (time-marching)."""
+    from . import solvers, transfer
+    seq = [(forest, k, r)]
+    while seq[-1][1] > 2:
+        seq.append((forest, max(2, seq[-1][1] // 2), seq[-1][2]))
+    while seq[-1][2] > 0:
+        seq.append((forest, seq[-1][1], seq[-1][2] // 2))
+    for fc in solvers.coarse_forests(forest, stop_n)[1:]:
+        seq.append((fc, seq[-1][1], seq[-1][2]))
+    levels = [StLevel(f, kk, rr, nu, tau, patch) for f, kk, rr in seq]
+    for l in range(len(levels) - 1):
+        fine, coarse = levels[l], levels[l + 1]
+        if fine.r != coarse.r:                                   # temporal p-step: P_tau (x) I
+            Pt = time_prolongation(coarse.r, fine.r)
+            fine.P = sp.kron(sp.csr_matrix(Pt), sp.identity(fine.st.n)).tocsr()
+        else:                                                     # spatial step: I_Q (x) P_h
+            Ph = transfer.prolongation(coarse.st.space, fine.st.space)
+            fine.P = sp.kron(sp.identity(fine.st.Q), Ph).tocsr()
+    return levels
+
+
+class STMG:
+    """One V-cycle of space-time multigrid: `nu_s` damped weighted Schwarz steps (damping omega)
+    before and after the coarse correction, a direct solve on the coarsest level (least squares: the
+    pressure constant of every stage is a null direction).
+
+    Readings (the paper gives neither the damping nor the number of steps): omega = 0.7, nu_s = 4,
+    vertex-star patches.  Undamped, the weighted additive Schwarz iteration has spectral radius
+    about 1.8 on Taylor--Hood; with Taylor--Hood's continuous pressure, cell patches (the paper's
+    choice for a discontinuous pressure) need omega <= 0.5 and give iteration counts that grow
+    under refinement, vertex stars do far less so."""
+
+    def __init__(self, levels, nu_s=4, omega=0.7):
+        self.levels, self.nu_s, self.omega = levels, nu_s, omega
+        self.coarse = np.linalg.pinv(levels[-1].K.toarray())
+
+    def __call__(self, b, l=0):
+        lv = self.levels[l]
+        if l == len(self.levels) - 1:
+            return self.coarse @ b
+        x = np.zeros_like(b)
+        for _ in range(self.nu_s):
+            x = x + self.omega * lv.schwarz(b - lv.K @ x)
+        xc = self(lv.P.T @ (b - lv.K @ x), l + 1)
+        x = x + lv.P @ xc
+        for _ in range(self.nu_s):
+            x = x + self.omega * lv.schwarz(b - lv.K @ x)
+        return x
+
+    def project(self, v):
+        """Zero pressure mean in every stage (the null space of K and K^T)."""
+        lv = self.levels[0]
+        pres = lv.st.space.pressure_dofs()
+        out = np.array(v, dtype=float, copy=True).reshape(lv.st.Q, lv.st.n)
+        for q in range(lv.st.Q):
+            out[q, pres] -= out[q, pres].mean()
+        return out.ravel()

@@ -99,3 +99,43 @@ def test_time_transfer_exact_for_coarse_polynomials(rc, rf):
     a = rng.uniform(-1, 1, rc + 1)
     poly = lambda s: sum(a[j] * s ** j for j in range(rc + 1))
     assert np.abs(P @ poly(tc) - poly(tf)).max() <= 1e-14
+
+
+def test_stmg_level_sequence_follows_the_coarsening_rules():
+    """Polynomial before geometric (spatial degree halved, Taylor--Hood keeping k >= 2, then the
+    temporal degree), then h in space only (time-marching: no coarsening of tau)."""
+    lv = spacetime.stmg_levels(mesh.uniform(2, 4), 4, 3, tau=0.1)
+    seq = [(l.k, l.r, l.st.space.forest.n) for l in lv]
+    assert seq == [(4, 3, 4), (2, 3, 4), (2, 1, 4), (2, 0, 4), (2, 0, 2)]
+    assert all(l.st.tau == 0.1 for l in lv)
+
+
+@pytest.mark.parametrize("patch,omega", [("vertex", 0.7), ("cell", 0.5)])
+def test_damped_schwarz_contracts_except_the_pressure_constants(patch, omega):
+    """I - omega S K on the free entries: one eigenvalue 1 per stage (the constant pressure, a null
+    direction of K) and every other eigenvalue inside the unit disc.  (Cell patches on Taylor--Hood
+    need the stronger damping: with omega = 0.7 their iteration is slightly expansive.)"""
+    lv = spacetime.StLevel(mesh.uniform(2, 3), 2, 1, 1.0, 0.05, patch=patch)
+    K = lv.K.toarray()
+    N = K.shape[0]
+    S = np.stack([lv.schwarz(e) for e in np.eye(N)], axis=1)
+    free = ~lv.con
+    E = (np.eye(N) - omega * S @ K)[np.ix_(free, free)]
+    ev = np.sort(np.abs(np.linalg.eigvals(E)))[::-1]
+    Q = lv.st.Q
+    assert np.all(np.abs(ev[:Q] - 1.0) <= 1e-8)
+    assert ev[Q] < 0.999
+
+
+@pytest.mark.parametrize("n,k,r", [(8, 2, 1), (4, 3, 2), (8, 2, 0)])
+def test_stmg_preconditioned_fgmres_converges(n, k, r):
+    from oracle import solvers
+    lv = spacetime.stmg_levels(mesh.uniform(2, n), k, r, nu=1.0, tau=0.05)
+    V = spacetime.STMG(lv)
+    K = lv[0].K
+    d = lv[0].st.space.dofs
+    rng = np.random.default_rng(1)
+    xs = V.project(np.tile(d.distribute(rng.uniform(-1, 1, d.n_dofs)), lv[0].st.Q))
+    x, its, res = solvers.fgmres(K, K @ xs, V, tol=1e-10, maxit=200, project=V.project)
+    assert res <= 1e-10 and its <= 40, its
+    assert np.abs(V.project(x - xs)).max() <= 1e-7 * np.abs(xs).max()
