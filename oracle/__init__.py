@@ -31,6 +31,8 @@ assembly, no sum factorisation):
 * ``spacetime`` -- space-time finite elements for transient Stokes (Section 4):
                    DG(r) in time on right Radau points, the stage-major
                    Kronecker operator G_Q (x) M + tau I_Q (x) A, time transfers.
+* ``pdisc``     -- Stokes with a discontinuous pressure, Q_k / P^disc_{k-1}
+                   (the spatial pair of Section 4), with its transfers.
 * ``hp``        -- hp-adaptive continuous spaces (a degree per cell, h- and
                    p-hanging constraints), the vector Laplacian and Taylor--Hood
                    Stokes on them, hp transfers and the hp-multigrid hierarchy

@@ -82,14 +82,28 @@ class SpaceTimeStokes:
     """One slab of the transient Stokes equations: Taylor--Hood Q_k/Q_{k-1} on a forest, DG(r) in
     time.  Vectors are stage-major: Q blocks of the spatial Stokes vector."""
 
-    def __init__(self, forest, k, r, nu=1.0, tau=0.1):
-        self.space = assemble.Problem(forest, "stokes", k, nu=nu)
+    def __init__(self, forest, k, r, nu=1.0, tau=0.1, pressure="continuous"):
+        """pressure: 'continuous' (Taylor--Hood Q_k/Q_{k-1}) or 'disc' (Q_k/P^disc_{k-1})."""
+        from . import pdisc
+        self.pressure = pressure
+        if pressure == "disc":
+            self.space = pdisc.StokesPdisc(forest, k, nu=nu)
+        else:
+            self.space = assemble.Problem(forest, "stokes", k, nu=nu)
         self.r, self.Q, self.tau, self.nu = r, r + 1, tau, nu
         self.nodes, self.M_Q, self.A_Q, self.m_Q = temporal_matrices(r)
         self.G_Q = np.linalg.solve(self.M_Q, self.A_Q)
         self.A = self.space.assemble()                    # Stokes operator, identity constrained rows
-        self.M = self._velocity_mass()
+        self.M = self.space.velocity_mass() if pressure == "disc" else self._velocity_mass()
         self.n = self.A.shape[0]
+
+    def pressure_null(self):
+        """The constant pressure of one stage (null direction of A with all-Dirichlet velocity)."""
+        if self.pressure == "disc":
+            return self.space.pressure_null()
+        e = np.zeros(self.n)
+        e[self.space.pressure_dofs()] = 1.0
+        return e
 
     def _velocity_mass(self):
         """Stokes block mass: the velocity mass on the free velocity rows, zero elsewhere."""
@@ -153,9 +167,9 @@ class StLevel:
     velocity and pressure DoFs); 'vertex': the cells around one mesh vertex (the free DoFs whose
     node lies inside that star, i.e. every cell holding the node is in the star)."""
 
-    def __init__(self, forest, k, r, nu, tau, patch="vertex"):
+    def __init__(self, forest, k, r, nu, tau, patch="vertex", pressure="continuous"):
         self.k, self.r = k, r
-        self.st = SpaceTimeStokes(forest, k, r, nu=nu, tau=tau)
+        self.st = SpaceTimeStokes(forest, k, r, nu=nu, tau=tau, pressure=pressure)
         self.K = self.st.operator()
         self.P = None
         st = self.st
@@ -206,8 +220,7 @@ def _patch_dofs(problem, patch):
     for c in range(f.n_cells):
         for cr in corners:
             star.setdefault(key(org[c] + cr * h[c]), []).append(c)
-    # cells holding each DoF's node (its closed box contains the node)
-    xs, _ = d.support_points()
+    # cells holding each DoF
     holders = [set() for _ in range(d.n_dofs)]
     for c in range(f.n_cells):
         for g in cd[c]:
@@ -221,10 +234,15 @@ def _patch_dofs(problem, patch):
     return out
 
 
-def stmg_levels(forest, k, r, nu=1.0, tau=0.1, stop_n=2, patch="vertex"):
-    """Levels finest first: spatial degree halved (Taylor--Hood keeps k >= 2), then the temporal
-    degree halved (DG(r) -> DG(r // 2)), then global h-coarsening in space; no geometric coarsening
-    in time (time-marching)."""
+def stmg_levels(forest, k, r, nu=1.0, tau=0.1, stop_n=2, patch=None, pressure="disc"):
+    """Levels finest first: spatial degree halved (k >= 2 kept: Q2 is the lowest stable velocity for
+    both pairs), then the temporal degree halved (DG(r) -> DG(r // 2)), then global h-coarsening in
+    space; no geometric coarsening in time (time-marching).  Patches: one cell for the discontinuous
+    pressure (the paper's pair: every pressure DoF belongs to one cell), vertex stars for the
+    continuous one (a cell patch would cut the pressure coupling; a vertex star of a discontinuous
+    pressure holds a pressure constant as a local null mode)."""
+    if patch is None:
+        patch = "cell" if pressure == "disc" else "vertex"
     from . import solvers, transfer
     seq = [(forest, k, r)]
     while seq[-1][1] > 2:
@@ -233,14 +251,18 @@ def stmg_levels(forest, k, r, nu=1.0, tau=0.1, stop_n=2, patch="vertex"):
         seq.append((forest, seq[-1][1], seq[-1][2] // 2))
     for fc in solvers.coarse_forests(forest, stop_n)[1:]:
         seq.append((fc, seq[-1][1], seq[-1][2]))
-    levels = [StLevel(f, kk, rr, nu, tau, patch) for f, kk, rr in seq]
+    levels = [StLevel(f, kk, rr, nu, tau, patch, pressure) for f, kk, rr in seq]
     for l in range(len(levels) - 1):
         fine, coarse = levels[l], levels[l + 1]
         if fine.r != coarse.r:                                   # temporal p-step: P_tau (x) I
             Pt = time_prolongation(coarse.r, fine.r)
             fine.P = sp.kron(sp.csr_matrix(Pt), sp.identity(fine.st.n)).tocsr()
         else:                                                     # spatial step: I_Q (x) P_h
-            Ph = transfer.prolongation(coarse.st.space, fine.st.space)
+            if pressure == "disc":
+                from . import pdisc
+                Ph = pdisc.prolongation(coarse.st.space, fine.st.space)
+            else:
+                Ph = transfer.prolongation(coarse.st.space, fine.st.space)
             fine.P = sp.kron(sp.identity(fine.st.Q), Ph).tocsr()
     return levels
 
@@ -250,8 +272,8 @@ class STMG:
     before and after the coarse correction, a direct solve on the coarsest level (least squares: the
     pressure constant of every stage is a null direction).
 
-    Readings (the paper gives neither the damping nor the number of steps): omega = 0.7, nu_s = 4,
-    vertex-star patches.  Undamped, the weighted additive Schwarz iteration has spectral radius
+    Readings (the paper gives neither the damping nor the number of steps): omega = 0.7, nu_s = 4;
+    patches as chosen by ``stmg_levels``.  Undamped, the weighted additive Schwarz iteration has spectral radius
     about 1.8 on Taylor--Hood; with Taylor--Hood's continuous pressure, cell patches (the paper's
     choice for a discontinuous pressure) need omega <= 0.5 and give iteration counts that grow
     under refinement, vertex stars do far less so."""
@@ -274,10 +296,10 @@ class STMG:
         return x
 
     def project(self, v):
-        """Zero pressure mean in every stage (the null space of K and K^T)."""
+        """Remove the constant pressure of every stage (the null space of K and K^T)."""
         lv = self.levels[0]
-        pres = lv.st.space.pressure_dofs()
+        e = lv.st.pressure_null()
         out = np.array(v, dtype=float, copy=True).reshape(lv.st.Q, lv.st.n)
         for q in range(lv.st.Q):
-            out[q, pres] -= out[q, pres].mean()
+            out[q] -= (out[q] @ e) / (e @ e) * e
         return out.ravel()

@@ -59,17 +59,18 @@ def test_polynomials_of_degree_r_in_time_are_exact(r):
 
 
 def test_dg0_kronecker_operator_is_backward_euler():
-    st = spacetime.SpaceTimeStokes(mesh.uniform(2, 3), 2, 0, nu=0.7, tau=0.3)
+    st = spacetime.SpaceTimeStokes(mesh.uniform(2, 3), 2, 0, nu=0.7, tau=0.3, pressure="continuous")
     assert np.allclose(st.G_Q, [[1.0]])
     K = st.operator()
     assert abs(K - (st.M + 0.3 * st.A)).max() <= 1e-15
 
 
+@pytest.mark.parametrize("pressure", ["continuous", "disc"])
 @pytest.mark.parametrize("r", [0, 1, 2])
-def test_slab_reproduces_a_manufactured_solution(r):
+def test_slab_reproduces_a_manufactured_solution(r, pressure):
     f = mesh.refine_ball(mesh.uniform(2, 3), (0.3, 0.35, 0.4), 0.3, 1)
     tau, t0 = 0.25, 0.4
-    st = spacetime.SpaceTimeStokes(f, 2, r, nu=0.8, tau=tau)
+    st = spacetime.SpaceTimeStokes(f, 2, r, nu=0.8, tau=tau, pressure=pressure)
     d = st.space.dofs
     assert d.hanging.any()
     rng = np.random.default_rng(7 + r)
@@ -84,10 +85,10 @@ def test_slab_reproduces_a_manufactured_solution(r):
     b = st.set_constrained(b, [c(t) * X for t in stage_t])
     K = st.operator().toarray()
     x = np.linalg.lstsq(K, b, rcond=None)[0].reshape(st.Q, st.n)
-    pres = st.space.pressure_dofs()
+    en = st.pressure_null()
     for q, t in enumerate(stage_t):
         e = x[q] - c(t) * X
-        e[pres] -= e[pres].mean()
+        e -= (e @ en) / (en @ en) * en                 # the stage's pressure constant is free
         assert np.abs(e).max() <= 1e-10 * np.abs(X).max(), (q, np.abs(e).max())
 
 
@@ -102,20 +103,21 @@ def test_time_transfer_exact_for_coarse_polynomials(rc, rf):
 
 
 def test_stmg_level_sequence_follows_the_coarsening_rules():
-    """Polynomial before geometric (spatial degree halved, Taylor--Hood keeping k >= 2, then the
-    temporal degree), then h in space only (time-marching: no coarsening of tau)."""
+    """Polynomial before geometric (spatial degree halved, k >= 2 kept, then the temporal degree),
+    then h in space only (time-marching: no coarsening of tau)."""
     lv = spacetime.stmg_levels(mesh.uniform(2, 4), 4, 3, tau=0.1)
     seq = [(l.k, l.r, l.st.space.forest.n) for l in lv]
     assert seq == [(4, 3, 4), (2, 3, 4), (2, 1, 4), (2, 0, 4), (2, 0, 2)]
     assert all(l.st.tau == 0.1 for l in lv)
 
 
-@pytest.mark.parametrize("patch,omega", [("vertex", 0.7), ("cell", 0.5)])
-def test_damped_schwarz_contracts_except_the_pressure_constants(patch, omega):
+@pytest.mark.parametrize("pressure,patch,omega", [("continuous", "vertex", 0.7), ("continuous", "cell", 0.5),
+                                                   ("disc", "cell", 0.7)])
+def test_damped_schwarz_contracts_except_the_pressure_constants(pressure, patch, omega):
     """I - omega S K on the free entries: one eigenvalue 1 per stage (the constant pressure, a null
     direction of K) and every other eigenvalue inside the unit disc.  (Cell patches on Taylor--Hood
     need the stronger damping: with omega = 0.7 their iteration is slightly expansive.)"""
-    lv = spacetime.StLevel(mesh.uniform(2, 3), 2, 1, 1.0, 0.05, patch=patch)
+    lv = spacetime.StLevel(mesh.uniform(2, 3), 2, 1, 1.0, 0.05, patch=patch, pressure=pressure)
     K = lv.K.toarray()
     N = K.shape[0]
     S = np.stack([lv.schwarz(e) for e in np.eye(N)], axis=1)
@@ -127,10 +129,11 @@ def test_damped_schwarz_contracts_except_the_pressure_constants(patch, omega):
     assert ev[Q] < 0.999
 
 
+@pytest.mark.parametrize("pressure", ["disc", "continuous"])
 @pytest.mark.parametrize("n,k,r", [(8, 2, 1), (4, 3, 2), (8, 2, 0)])
-def test_stmg_preconditioned_fgmres_converges(n, k, r):
+def test_stmg_preconditioned_fgmres_converges(n, k, r, pressure):
     from oracle import solvers
-    lv = spacetime.stmg_levels(mesh.uniform(2, n), k, r, nu=1.0, tau=0.05)
+    lv = spacetime.stmg_levels(mesh.uniform(2, n), k, r, nu=1.0, tau=0.05, pressure=pressure)
     V = spacetime.STMG(lv)
     K = lv[0].K
     d = lv[0].st.space.dofs
