@@ -189,3 +189,128 @@ class LocalSmoothing:
         con = self.problem.dofs.constrained               # identity rows of A
         x[con] = b[con]
         return x
+
+
+# -- the level recursion with rediscretised level operators ---------------------------------------
+class _RLevel:
+    """Level l >= 1 in the numbering of the uniform level-l mesh: its operator assembled on the
+    level-l cells only, with the domain boundary (velocity) constrained ('full') and with the
+    refinement edge constrained too, every component ('op'); identity rows outside Omega_l."""
+
+    def __init__(self, forest, l, kind, k, params):
+        dim = forest.dim
+        self.U = assemble.Problem(mesh.uniform(dim, forest.n * 2 ** l), kind, k, **params)
+        U = self.U
+        sp_ = LevelSpace(forest, l, k)
+        nsU = U.dofs.nodesets[0]
+        key = {tuple(np.rint(x * 2 ** 30).astype(np.int64)): g for g, x in enumerate(nsU.x)}
+        inside = np.zeros(nsU.n_nodes, dtype=bool)
+        edge = np.zeros(nsU.n_nodes, dtype=bool)
+        for x, e in zip(sp_.x, sp_.edge):
+            g = key[tuple(np.rint(x * 2 ** 30).astype(np.int64))]
+            inside[g] = True
+            edge[g] |= e
+        present = {tuple(c) for c in sp_.cells.tolist()}
+        cells = np.array([i for i, c in enumerate(U.forest.cells[:, 1:].tolist()) if tuple(c) in present])
+        Ke = U.element_matrices(cells)
+        cd = U.cell_dofs[cells]
+        n = U.dofs.n_dofs
+        K = sp.csr_matrix((Ke.ravel(), (np.repeat(cd[:, :, None], cd.shape[1], 2).ravel(),
+                                        np.repeat(cd[:, None, :], cd.shape[1], 1).ravel())), shape=(n, n))
+        d = U.dofs
+        node_of = np.concatenate([np.arange(d.nodesets[f].n_nodes) for f, (nc, _, _) in enumerate(d.fields)
+                                  for _ in range(nc)])
+        outside = ~inside[node_of]
+        self.inside = ~outside
+        full_c = d.dirichlet | outside
+        op_c = full_c | edge[node_of]
+
+        def constrain(c):
+            D = sp.diags((~c).astype(float))
+            return (D @ K @ D + sp.diags(c.astype(float))).tocsr()
+
+        self.full, self.op = constrain(full_c), constrain(op_c)
+        self.op_c, self.full_c = op_c, full_c
+        self.dinv = 1.0 / self.op.diagonal()
+        self.lmax = None
+        self.P = None                                 # from the next coarser uniform level
+
+
+class LocalSmoothingLevels:
+    """The local-smoothing cycle as a level recursion with rediscretised level operators (the form a
+    stabilised operator needs: tau depends on the cell size, so level operators are not Galerkin
+    products).  For 'stokes_a' it equals ``LocalSmoothing`` (pinned).  Each free fine DoF is owned by
+    the coarsest level among the active cells holding it; its defect is copied there, and the result
+    is copied back from there; constrained fine rows return b.  Level 0 is the base mesh's
+    global-coarsening hierarchy (``solvers.hierarchy``, the kind's default order)."""
+
+    def __init__(self, problem, lmax_ls, lmax_base, smoother=("chebyshev", 5), stop_n=2, **params):
+        from . import transfer
+        self.problem = problem
+        f, kind, k = problem.forest, problem.kind, problem.k
+        self.L = f.max_level
+        self.levels = [_RLevel(f, l, kind, k, params) for l in range(1, self.L + 1)]
+        for lv, lm in zip(self.levels, lmax_ls):
+            lv.lmax = lm
+        self.smoother = smoother
+        self.base_levels = solvers.hierarchy(mesh.uniform(f.dim, f.n), kind, k, stop_n=stop_n, **params)
+        self.base = solvers.VCycle(self.base_levels, lmax_base, smoother)
+        uni = [self.base_levels[0].problem] + [lv.U for lv in self.levels]
+        for l, lv in enumerate(self.levels):
+            lv.P = transfer.prolongation(uni[l], uni[l + 1])
+        # owners: fine free DoF -> (level, DoF of that level's uniform numbering)
+        d = problem.dofs
+        xs, fid = d.support_points()
+        ns = d.nodesets[0]
+        owner_node = ns.owner_level
+        node_of = np.concatenate([np.arange(d.nodesets[f_].n_nodes) for f_, (nc, _, _) in enumerate(d.fields)
+                                  for _ in range(nc)])
+        self.copies = []
+        for l in range(self.L + 1):
+            Ud = uni[l].dofs
+            xu, fu = Ud.support_points()
+            key = {(tuple(np.rint(x * 2 ** 30).astype(np.int64)), c): i for i, (x, c) in enumerate(zip(xu, fu))}
+            pairs = [(g, key[(tuple(np.rint(xs[g] * 2 ** 30).astype(np.int64)), fid[g])])
+                     for g in np.nonzero(d.free)[0] if owner_node[node_of[g]] == l]
+            self.copies.append(np.array(pairs, dtype=np.int64).reshape(-1, 2))
+
+    def _smooth(self, lv, b):
+        kind, deg = self.smoother
+        x0 = np.zeros_like(b)
+        if kind == "chebyshev":
+            return solvers.chebyshev(lv.op, lv.dinv, b, x0, deg, lv.lmax, x_is_zero=True)
+        return solvers.jacobi_relaxation(lv.op, lv.dinv, b, x0, deg, lv.lmax)
+
+    def __call__(self, b):
+        uni_n = [self.base_levels[0].A.shape[0]] + [lv.U.dofs.n_dofs for lv in self.levels]
+        B = []
+        for l in range(self.L + 1):
+            v = np.zeros(uni_n[l])
+            c = self.copies[l]
+            v[c[:, 1]] = b[c[:, 0]]
+            B.append(v)
+        X = [None] * (self.L + 1)
+        for l in range(self.L, 0, -1):                  # down: smooth, residual with edge rows, restrict
+            lv = self.levels[l - 1]
+            z = B[l].copy()
+            z[lv.op_c] = 0.0
+            X[l] = self._smooth(lv, z)
+            r = (B[l] - lv.full @ X[l]) * lv.inside
+            cst = lv.P.T @ r
+            below_c = self.levels[l - 2].full_c if l >= 2 else self.base_levels[0].problem.dofs.constrained
+            cst[below_c] = 0.0
+            B[l - 1] = B[l - 1] + cst
+        X[0] = self.base(B[0])
+        for l in range(1, self.L + 1):                  # up: prolongate, residual, smooth the correction
+            lv = self.levels[l - 1]
+            X[l] = X[l] + (lv.P @ X[l - 1]) * lv.inside
+            r = B[l] - lv.full @ X[l]
+            r[lv.op_c] = 0.0
+            X[l] = X[l] + self._smooth(lv, r)
+        x = np.zeros_like(b)
+        for l in range(self.L + 1):
+            c = self.copies[l]
+            x[c[:, 0]] = X[l][c[:, 1]]
+        con = self.problem.dofs.constrained
+        x[con] = b[con]
+        return x
