@@ -120,9 +120,12 @@ typedef struct {
                            the cell kernel is latency-bound) */
   int hierarchy;        /* multigrid levels on a locally refined mesh (Section 2): 0 (default) global
                            coarsening -- every level covers the whole domain, hanging nodes resolved
-                           on each; 1 local smoothing (MFNS_STOKES and MFNS_STOKES_A only) -- level
+                           on each; 1 local smoothing (MFNS_STOKES, MFNS_STOKES_A and
+                           MFNS_STAB_NS; for MFNS_STAB_NS with the frozen Taylor--Green state:
+                           mfns_set_state / mfns_bdf_step return MFNS_ERR_UNSUPPORTED) -- level
                            l is the set of cells of refinement level l with homogeneous Dirichlet
-                           conditions on its refinement edge, level 0 the unrefined base mesh with
+                           conditions on its refinement edge (velocity, and pressure for
+                           MFNS_STAB_NS), level 0 the unrefined base mesh with
                            its own global-coarsening hierarchy.  The levels reported by
                            mfns_problem_info and addressed by mfns_set_lambda_max are then the
                            refined levels (finest first) followed by the base hierarchy;

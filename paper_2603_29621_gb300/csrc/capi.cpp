@@ -148,8 +148,8 @@ int mfns_problem_create(mfns_ctx* ctx, const mfns_mesh* mesh, const mfns_problem
   ph.precompute_frozen = desc->recompute_frozen == 0;
   const size_t used0 = ctx->budget.used;
   if (desc->hierarchy != 0 && desc->hierarchy != 1) return fail(MFNS_ERR_ARG, "hierarchy must be 0 or 1");
-  if (desc->hierarchy == 1 && desc->kind != MFNS_STOKES && desc->kind != MFNS_STOKES_A)
-    return fail(MFNS_ERR_UNSUPPORTED, "local smoothing is built for MFNS_STOKES and MFNS_STOKES_A");
+  if (desc->hierarchy == 1 && desc->kind == MFNS_PMASS)
+    return fail(MFNS_ERR_UNSUPPORTED, "local smoothing is built for MFNS_STOKES, MFNS_STOKES_A and MFNS_STAB_NS");
   std::unique_ptr<Problem> p = build_problem(mesh->forest, desc->kind, k, ph, desc->mg_order,
                                              desc->coarse_stop_n > 0 ? desc->coarse_stop_n : 2, &ctx->budget,
                                              desc->hierarchy);

@@ -54,11 +54,16 @@ void build_oplevel(OpLevel& lv, const Forest& f, int op, int k, const Physics& p
     lv.np = make_nodes(f, lat, masks, k - 1, &err);
     if (!err.empty()) throw Error(kErrArg, err);
   }
-  if (edge_dirichlet) {  // local smoothing: homogeneous Dirichlet conditions on the refinement edge
-    if (!f.partial || op != OP_STOKES_A) throw Error(kErrUnsupported, "refinement-edge conditions need a level forest");
+  // local smoothing: homogeneous Dirichlet conditions on the refinement edge, for the velocity
+  // (the boundary flag) and, for the stabilised operator, the pressure too (constrained rows)
+  std::vector<uint8_t> edge_p;
+  if (edge_dirichlet) {
+    if (!f.partial || (op != OP_STOKES_A && op != OP_STAB_NS))
+      throw Error(kErrUnsupported, "refinement-edge conditions need a level forest of the vector Laplacian or stabilised NS");
     const std::vector<uint8_t> e = refinement_edge(f, lv.nu);
     for (int64_t g = 0; g < lv.nu.n_nodes; ++g)
       if (e[g]) lv.nu.boundary[g] = 1;
+    if (op == OP_STAB_NS) edge_p = e;
   }
   lv.n_main_dofs = lv.nu.n_nodes * lv.NU;
   lv.n_dofs = lv.n_main_dofs + (op == OP_STOKES ? lv.np.n_nodes : 0);
@@ -194,8 +199,9 @@ void build_oplevel(OpLevel& lv, const Forest& f, int op, int k, const Physics& p
   std::vector<double> hw;
   for (int64_t g = 0; g < lv.nu.n_nodes; ++g) {
     const bool bnd = has_dir && lv.nu.boundary[g];
+    const bool pedge = !edge_p.empty() && edge_p[g];
     for (int c = 0; c < lv.NU; ++c) {
-      const bool dir = bnd && c < nvel;
+      const bool dir = (bnd && c < nvel) || (pedge && c == dim);
       if (dir || hang[g]) lv.constrained_host.push_back((int32_t)(g * lv.NU + c));
     }
   }
@@ -229,7 +235,7 @@ void build_oplevel(OpLevel& lv, const Forest& f, int op, int k, const Physics& p
       if (!hangp[g]) lv.pres_host.push_back((int32_t)(lv.n_main_dofs + g));
   } else if (op == OP_STAB_NS) {
     for (int64_t g = 0; g < lv.nu.n_nodes; ++g)
-      if (!hang[g]) lv.pres_host.push_back((int32_t)(g * lv.NU + dim));
+      if (!hang[g] && (edge_p.empty() || !edge_p[g])) lv.pres_host.push_back((int32_t)(g * lv.NU + dim));
   }
   std::sort(lv.constrained_host.begin(), lv.constrained_host.end());
   lv.constrained = upload(bud, lv.constrained_host);

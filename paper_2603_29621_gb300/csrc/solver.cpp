@@ -69,8 +69,8 @@ std::unique_ptr<Problem> build_problem(const Forest& f, int kind, int k, const P
   // (forest, degree) sequence of the hierarchy, finest first
   std::vector<std::pair<Forest, int>> seq;
   const bool local = hierarchy == 1 && f.max_level() > 0;
-  if (hierarchy == 1 && mop != OP_STOKES_A)
-    throw Error(kErrUnsupported, "local smoothing is built for the vector Laplacian and the Stokes A block");
+  if (hierarchy == 1 && mop != OP_STOKES_A && mop != OP_STAB_NS)
+    throw Error(kErrUnsupported, "local smoothing is built for the vector Laplacian, the Stokes A block and stabilised NS");
   if (kind == 3 || local) {
     seq.push_back({f, k});  // local smoothing: the fine operator only; the levels live in p->ls
   } else {
@@ -119,7 +119,8 @@ static void build_local_smoothing(Problem& p, const Forest& f, int k, const Phys
   const int L = f.max_level();
   // level 0 and below: the base mesh with its own global-coarsening hierarchy (vector Laplacian)
   Forest base = forest_uniform(f.dim, f.n);
-  S->base = build_problem(base, 1, k, ph, mg_order, coarse_stop_n, bud, 0);
+  const int mop = fine.op;  // OP_STOKES_A (vector Laplacian, Stokes A block) or OP_STAB_NS
+  S->base = build_problem(base, mop == OP_STAB_NS ? 2 : 1, k, ph, mg_order, coarse_stop_n, bud, 0);
   std::vector<int32_t> owner(fine.nu.n_nodes, -1);
   std::vector<int32_t> cf, cl;
   {
@@ -134,9 +135,9 @@ static void build_local_smoothing(Problem& p, const Forest& f, int k, const Phys
     auto lv = std::make_unique<LsLevel>();
     const Forest lf = forest_level(f, l);
     lv->op = std::make_unique<OpLevel>();
-    build_oplevel(*lv->op, lf, OP_STOKES_A, k, ph, bud, true);
+    build_oplevel(*lv->op, lf, mop, k, ph, bud, true);
     lv->full = std::make_unique<OpLevel>();
-    build_oplevel(*lv->full, lf, OP_STOKES_A, k, ph, bud, false);
+    build_oplevel(*lv->full, lf, mop, k, ph, bud, false);
     if (lv->op->n_dofs != lv->full->n_dofs || lv->op->perm != lv->full->perm)
       throw Error(kErrArg, "local smoothing: level operators disagree on the numbering");
     if (lv->op->n_dofs > cap) throw Error(kErrUnsupported, "local smoothing: level larger than the fine system");
@@ -1092,6 +1093,7 @@ void set_state_fine(Problem& p, double dt, double alpha, const double* U, const 
 }
 
 void refresh_preconditioner(Problem& p, cudaStream_t s) {
+  if (p.ls) throw Error(kErrUnsupported, "Newton states are carried to global-coarsening levels only");
   // the finest state (and g) interpolated level by level down the hierarchy
   const bool has_g = p.st_g;
   for (size_t l = 0; l + 1 < p.levels.size(); ++l) {

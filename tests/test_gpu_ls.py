@@ -125,7 +125,7 @@ def test_ls_stokes_solve_matches_global_coarsening(ctx, mg_precision):
 def test_ls_rejects_unsupported(ctx):
     from paper_2603_29621_gb300 import _lib as L
     with pytest.raises(L.MfnsError) as e:
-        _gpu(ctx, L.STAB_NS, 3, 2, 1, 2, nu=1e-2, dt=1e-2)
+        _gpu(ctx, L.PMASS, 3, 2, 1, 2, nu=1.0)
     assert e.value.code == L.ERR_UNSUPPORTED
     prob = _gpu(ctx, L.STOKES_A, 2, 4, 1, 2, nu=1.0)
     b = torch.zeros(prob.info.n_dofs, dtype=torch.float64, device="cuda")
