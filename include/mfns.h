@@ -203,12 +203,13 @@ int mfns_mesh_destroy(mfns_mesh* mesh);
  * the dense coarse inverse and all workspaces.  The mesh may be destroyed afterwards. */
 int mfns_problem_create(mfns_ctx* ctx, const mfns_mesh* mesh, const mfns_problem_desc* desc,
                         mfns_problem** out);
-/* hp-adaptive vector Laplacian (Section 3): cell_degree[c] (1..4; host array of n_cells entries in
+/* hp-adaptive problems (Section 3): cell_degree[c] (1..4; host array of n_cells entries in
  * the order of mfns_mesh_cells) is the degree of cell c.  A node is constrained when a cell whose
  * closed box holds it does not have it as a node and dominates every cell that does (coarser, or
  * same level and lower degree); it takes that cell's finite-element function at its position.
  * The multigrid hierarchy lowers every degree by one per level until all cells are linear, then
- * coarsens globally.  desc->kind must be MFNS_STOKES_A and desc->hierarchy 0
+ * coarsens globally.  desc->kind must be MFNS_STOKES_A or MFNS_STOKES (Taylor--Hood: velocity
+ * degree per cell >= 2, pressure one lower, the A block on the hp hierarchy) and desc->hierarchy 0
  * (MFNS_ERR_UNSUPPORTED otherwise); a mesh on which a hanging face has a coarse cell of higher
  * degree than a fine cell returns MFNS_ERR_UNSUPPORTED; one degree everywhere is the same as
  * mfns_problem_create. */

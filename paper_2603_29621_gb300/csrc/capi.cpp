@@ -192,21 +192,23 @@ int mfns_problem_create_hp(mfns_ctx* ctx, const mfns_mesh* mesh, const mfns_prob
   API_BEGIN
   if (!ctx || !mesh || !desc || !cell_degree || !out) return fail(MFNS_ERR_ARG, "null argument");
   if (n_cells != (int64_t)mesh->forest.n_cells()) return fail(MFNS_ERR_ARG, "one degree per mesh cell expected");
-  if (desc->kind != MFNS_STOKES_A) return fail(MFNS_ERR_UNSUPPORTED, "hp problems are built for MFNS_STOKES_A");
+  if (desc->kind != MFNS_STOKES_A && desc->kind != MFNS_STOKES)
+    return fail(MFNS_ERR_UNSUPPORTED, "hp problems are built for MFNS_STOKES_A and MFNS_STOKES");
   if (desc->hierarchy != 0) return fail(MFNS_ERR_UNSUPPORTED, "hp problems use global coarsening");
   if (!(desc->nu > 0)) return fail(MFNS_ERR_ARG, "nu must be positive");
   if (desc->mg_precision != MFNS_FP64 && desc->mg_precision != MFNS_FP32) return fail(MFNS_ERR_ARG, "bad precision");
   const int dim = mesh->forest.dim;
   std::vector<int32_t> degree(cell_degree, cell_degree + n_cells);
   for (int32_t k : degree)
-    if (!op_supported_kind(dim, MFNS_STOKES_A, k)) return fail(MFNS_ERR_UNSUPPORTED, "unsupported cell degree");
+    if (!op_supported_kind(dim, desc->kind, k)) return fail(MFNS_ERR_UNSUPPORTED, "unsupported cell degree");
   MFNS_CUDA(cudaSetDevice(ctx->device));
   Physics ph;
   ph.nu = desc->nu;
   ph.div_sign = -1.0;
   const size_t used0 = ctx->budget.used;
   std::unique_ptr<Problem> p = build_problem_hp(mesh->forest, degree, ph,
-                                                desc->coarse_stop_n > 0 ? desc->coarse_stop_n : 2, &ctx->budget);
+                                                desc->coarse_stop_n > 0 ? desc->coarse_stop_n : 2, &ctx->budget,
+                                                desc->kind == MFNS_STOKES ? 0 : 1);
   return finish_problem(ctx, desc, std::move(p), used0, out);
   API_END
 }

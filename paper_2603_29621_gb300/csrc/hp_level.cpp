@@ -23,26 +23,47 @@ static DevBuf upload_as(Budget* bud, const std::vector<double>& v) {
 }
 
 void build_hp_oplevel(OpLevel& lv, const Forest& f, const std::vector<int32_t>& degree, const Physics& ph,
-                      Budget* bud) {
+                      Budget* bud, int op) {
+  if (op != OP_STOKES_A && op != OP_STOKES && op != OP_PMASS) throw Error(kErrUnsupported, "hp level of this operator");
   const int dim = f.dim;
   auto hp = std::make_unique<HpData>();
   std::string err;
   if (!make_hp_space(f, degree, hp->space, &err))
     throw Error(err.rfind("unsupported", 0) == 0 ? kErrUnsupported : kErrArg, err);
   const HpSpace& sp = hp->space;
-  lv.op = OP_STOKES_A;
+  // Taylor--Hood: the pressure space has degree k - 1 on every cell
+  HpSpace psp;
+  if (op == OP_STOKES) {
+    std::vector<int32_t> dp(degree);
+    for (auto& k : dp) {
+      if (k < 2) throw Error(kErrUnsupported, "Taylor--Hood needs velocity degrees >= 2");
+      k -= 1;
+    }
+    if (!make_hp_space(f, dp, psp, &err)) throw Error(err.rfind("unsupported", 0) == 0 ? kErrUnsupported : kErrArg, err);
+  }
+  const bool dirichlet = op != OP_PMASS;
+  lv.op = op;
   lv.dim = dim;
   lv.k = *std::max_element(degree.begin(), degree.end());
   lv.forest = f;
-  lv.NU = dim;
+  lv.NU = op == OP_PMASS ? 1 : dim;
   lv.nu = NodeSpace();
   lv.nu.dim = dim;
   lv.nu.n_nodes = sp.n_nodes;
   lv.nu.x = sp.x;
   lv.nu.boundary = sp.boundary;
-  lv.n_main_dofs = lv.n_dofs = sp.n_nodes * dim;
+  lv.n_main_dofs = sp.n_nodes * lv.NU;
+  lv.n_dofs = lv.n_main_dofs + (op == OP_STOKES ? psp.n_nodes : 0);
+  if (op == OP_STOKES) {
+    lv.np = NodeSpace();
+    lv.np.dim = dim;
+    lv.np.n_nodes = psp.n_nodes;
+    lv.np.x = psp.x;
+    lv.np.boundary = psp.boundary;
+  }
   if (lv.n_dofs >= (int64_t(1) << 31) - 1) throw Error(kErrUnsupported, "more than 2^31 DoFs per level");
-  // groups of one degree: colour-sorted cell tables with node ids and the Dirichlet bit
+  // groups of one degree: colour-sorted cell tables with node ids and the Dirichlet bit (two
+  // cells sharing a pressure node share a velocity node too: the velocity colouring suffices)
   for (int k = 1; k <= lv.k; ++k) {
     std::vector<int32_t> cells;
     for (size_t c = 0; c < f.n_cells(); ++c)
@@ -56,13 +77,14 @@ void build_hp_oplevel(OpLevel& lv, const Forest& f, const std::vector<int32_t>& 
     std::iota(order.begin(), order.end(), 0);
     std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return color[a] < color[b]; });
     const int nb = (int)(sp.cell_ptr[cells[0] + 1] - sp.cell_ptr[cells[0]]);
-    std::vector<int32_t> cu(cells.size() * nb);
+    const int nbp = op == OP_STOKES ? (int)(psp.cell_ptr[cells[0] + 1] - psp.cell_ptr[cells[0]]) : 0;
+    std::vector<int32_t> cu(cells.size() * nb), cp(cells.size() * nbp);
     std::vector<uint32_t> mk(cells.size(), 0u);
     std::vector<double> hc(cells.size());
     OpLaunch& L = g->L;
     L.dim = dim;
     L.k = k;
-    L.op = OP_STOKES_A;
+    L.op = op;
     L.structured = false;
     L.n = f.n;
     L.h = 1.0 / f.n;
@@ -76,8 +98,9 @@ void build_hp_oplevel(OpLevel& lv, const Forest& f, const std::vector<int32_t>& 
       hc[i] = f.h(c);
       for (int b = 0; b < nb; ++b) {
         const int32_t node = sp.cell_nodes[sp.cell_ptr[c] + b];
-        cu[i * nb + b] = node | (sp.boundary[node] ? int32_t(0x80000000u) : 0);
+        cu[i * nb + b] = node | (dirichlet && sp.boundary[node] ? int32_t(0x80000000u) : 0);
       }
+      for (int b = 0; b < nbp; ++b) cp[i * nbp + b] = psp.cell_nodes[psp.cell_ptr[c] + b];
     }
     for (int c = 0; c < ncol; ++c) L.color_ptr[c + 1] += L.color_ptr[c];
     L.nu = ph.nu;
@@ -86,10 +109,12 @@ void build_hp_oplevel(OpLevel& lv, const Forest& f, const std::vector<int32_t>& 
     L.terms = ph.terms;
     fill_tables(L);
     g->cell_u = upload(bud, cu);
+    g->cell_p = upload(bud, cp);
     g->mask = upload(bud, mk);
     g->hcell[0] = upload_as<double>(bud, hc);
     g->hcell[1] = upload_as<float>(bud, hc);
     L.cell_u = g->cell_u.as<int32_t>();
+    L.cell_p = op == OP_STOKES ? g->cell_p.as<int32_t>() : nullptr;
     L.mask = g->mask.as<uint32_t>();
     L.hcell[0] = g->hcell[0].get();
     L.hcell[1] = g->hcell[1].get();
@@ -101,43 +126,62 @@ void build_hp_oplevel(OpLevel& lv, const Forest& f, const std::vector<int32_t>& 
   lv.L = OpLaunch();
   lv.L.dim = dim;
   lv.L.k = lv.k;
-  lv.L.op = OP_STOKES_A;
-  // constrained rows; constraint lists without Dirichlet slaves or masters (every component is a
-  // velocity component with Dirichlet conditions)
-  std::vector<char> hang(sp.n_nodes, 0);
-  for (int32_t g : sp.hang_node) hang[g] = 1;
-  for (int64_t g = 0; g < sp.n_nodes; ++g)
-    if (sp.boundary[g] || hang[g])
-      for (int c = 0; c < dim; ++c) lv.constrained_host.push_back((int32_t)(g * dim + c));
-  std::sort(lv.constrained_host.begin(), lv.constrained_host.end());
-  lv.constrained = upload(bud, lv.constrained_host);
+  lv.L.op = op;
+  // constrained rows and constraint lists (no Dirichlet slaves or masters in a Dirichlet field);
+  // fields: the main one (NU components per node), then for Taylor--Hood the pressure block
+  struct Field {
+    const HpSpace* sp;
+    int ncomp;
+    bool dirichlet;
+    int64_t offset;
+  };
+  std::vector<Field> fields = {{&sp, lv.NU, dirichlet, 0}};
+  if (op == OP_STOKES) fields.push_back({&psp, 1, false, lv.n_main_dofs});
   std::vector<int32_t> hd, hptr(1, 0), hs;
   std::vector<double> hw;
   std::map<int32_t, std::vector<std::pair<int32_t, double>>> transpose;  // master dof -> (slave dof, w)
-  for (size_t i = 0; i < sp.hang_node.size(); ++i) {
-    const int32_t g = sp.hang_node[i];
-    if (sp.boundary[g]) continue;
-    for (int c = 0; c < dim; ++c) {
-      const int32_t sd = (int32_t)(g * dim + c);
-      hd.push_back(sd);
-      for (int32_t j = sp.hang_ptr[i]; j < sp.hang_ptr[i + 1]; ++j) {
-        const int32_t m = sp.hang_master[j];
-        if (sp.boundary[m]) continue;
-        const int32_t md = (int32_t)(m * dim + c);
-        hs.push_back(md);
-        hw.push_back(sp.hang_w[j]);
-        transpose[md].push_back({sd, sp.hang_w[j]});
+  std::vector<std::vector<char>> hangs;
+  for (const Field& F : fields) {
+    const HpSpace& S = *F.sp;
+    std::vector<char> hang(S.n_nodes, 0);
+    for (int32_t g : S.hang_node) hang[g] = 1;
+    for (int64_t g = 0; g < S.n_nodes; ++g)
+      if ((F.dirichlet && S.boundary[g]) || hang[g])
+        for (int c = 0; c < F.ncomp; ++c) lv.constrained_host.push_back((int32_t)(F.offset + g * F.ncomp + c));
+    for (size_t i = 0; i < S.hang_node.size(); ++i) {
+      const int32_t g = S.hang_node[i];
+      if (F.dirichlet && S.boundary[g]) continue;
+      for (int c = 0; c < F.ncomp; ++c) {
+        const int32_t sd = (int32_t)(F.offset + g * F.ncomp + c);
+        hd.push_back(sd);
+        for (int32_t j = S.hang_ptr[i]; j < S.hang_ptr[i + 1]; ++j) {
+          const int32_t m = S.hang_master[j];
+          if (F.dirichlet && S.boundary[m]) continue;
+          const int32_t md = (int32_t)(F.offset + m * F.ncomp + c);
+          hs.push_back(md);
+          hw.push_back(S.hang_w[j]);
+          transpose[md].push_back({sd, S.hang_w[j]});
+        }
+        hptr.push_back((int32_t)hs.size());
       }
-      hptr.push_back((int32_t)hs.size());
     }
+    hangs.push_back(std::move(hang));
   }
+  std::sort(lv.constrained_host.begin(), lv.constrained_host.end());
+  lv.constrained = upload(bud, lv.constrained_host);
   lv.n_hang = (int64_t)hd.size();
   lv.hang_dof = upload(bud, hd);
   lv.hang_ptr = upload(bud, hptr);
   lv.hang_src = upload(bud, hs);
   lv.hang_w[0] = upload_as<double>(bud, hw);
   lv.hang_w[1] = upload_as<float>(bud, hw);
-  std::vector<int32_t> cm, cp(1, 0), cs;
+  if (op == OP_STOKES) {  // free pressure entries: the constant-pressure null space
+    for (int64_t g = 0; g < psp.n_nodes; ++g)
+      if (!hangs[1][g]) lv.pres_host.push_back((int32_t)(lv.n_main_dofs + g));
+    lv.n_pres = (int64_t)lv.pres_host.size();
+    lv.pres = upload(bud, lv.pres_host);
+  }
+  std::vector<int32_t> cm, cpt(1, 0), cs;
   std::vector<double> cw;
   for (auto& kv : transpose) {
     cm.push_back(kv.first);
@@ -145,35 +189,40 @@ void build_hp_oplevel(OpLevel& lv, const Forest& f, const std::vector<int32_t>& 
       cs.push_back(sw.first);
       cw.push_back(sw.second);
     }
-    cp.push_back((int32_t)cs.size());
+    cpt.push_back((int32_t)cs.size());
   }
   hp->n_ct = (int64_t)cm.size();
   hp->ct_master = upload(bud, cm);
-  hp->ct_ptr = upload(bud, cp);
+  hp->ct_ptr = upload(bud, cpt);
   hp->ct_slave = upload(bud, cs);
   hp->ct_w[0] = upload_as<double>(bud, cw);
   hp->ct_w[1] = upload_as<float>(bud, cw);
-  // probing groups for the diagonal: free nodes that no cell reaches together
-  std::vector<char> free_node(sp.n_nodes, 0);
-  for (int64_t g = 0; g < sp.n_nodes; ++g) free_node[g] = !sp.boundary[g] && !hang[g];
-  std::vector<int32_t> pcol;
-  const int npc = hp_probe_groups(sp, free_node, pcol);
-  std::vector<std::vector<int32_t>> bucket(npc);  // free nodes of every group, ascending
-  for (int64_t m = 0; m < sp.n_nodes; ++m)
-    if (pcol[m] >= 0) bucket[pcol[m]].push_back((int32_t)m);
+  // probing groups for the diagonal, field by field: free nodes that no cell reaches together
   std::vector<int32_t> pd;
   hp->probe_ptr.assign(1, 0);
-  for (int col = 0; col < npc; ++col)
-    for (int c = 0; c < dim; ++c) {
-      for (int32_t m : bucket[col]) pd.push_back((int32_t)(m * dim + c));
-      hp->probe_ptr.push_back((int64_t)pd.size());
-    }
+  for (size_t fi = 0; fi < fields.size(); ++fi) {
+    const Field& F = fields[fi];
+    const HpSpace& S = *F.sp;
+    std::vector<char> free_node(S.n_nodes, 0);
+    for (int64_t g = 0; g < S.n_nodes; ++g) free_node[g] = !(F.dirichlet && S.boundary[g]) && !hangs[fi][g];
+    std::vector<int32_t> pcol;
+    const int npc = hp_probe_groups(S, free_node, pcol);
+    std::vector<std::vector<int32_t>> bucket(npc);  // free nodes of every group, ascending
+    for (int64_t m = 0; m < S.n_nodes; ++m)
+      if (pcol[m] >= 0) bucket[pcol[m]].push_back((int32_t)m);
+    for (int col = 0; col < npc; ++col)
+      for (int c = 0; c < F.ncomp; ++c) {
+        for (int32_t m : bucket[col]) pd.push_back((int32_t)(F.offset + m * F.ncomp + c));
+        hp->probe_ptr.push_back((int64_t)pd.size());
+      }
+  }
   hp->probe_dofs = upload(bud, pd);
   for (int prec = 0; prec < 2; ++prec) {
     hp->tmp[prec].alloc(bud, lv.n_dofs * esize(prec));
     hp->probe_e[prec].alloc(bud, lv.n_dofs * esize(prec));
     hp->probe_y[prec].alloc(bud, lv.n_dofs * esize(prec));
   }
+  if (op == OP_STOKES) hp->pspace = std::move(psp);
   lv.hp = std::move(hp);
 }
 

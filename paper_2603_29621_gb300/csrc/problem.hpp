@@ -62,11 +62,12 @@ struct HpGroup {
   int k = 1;
   OpLaunch L;
   std::vector<int32_t> cells;           // forest cell ids, colour order
-  DevBuf cell_u, mask, hcell[2];
+  DevBuf cell_u, cell_p, mask, hcell[2];
   std::unique_ptr<KernelTimer> timer = std::make_unique<KernelTimer>();
 };
 struct HpData {
-  HpSpace space;
+  HpSpace space;                        // the main field's nodes (velocity, or the scalar field)
+  HpSpace pspace;                       // Taylor--Hood: the pressure nodes (degrees k - 1)
   std::vector<std::unique_ptr<HpGroup>> groups;
   DevBuf tmp[2], probe_e[2], probe_y[2];  // distributed input; probing vectors of the diagonal
   // transpose of the constraints: for master dof ct_master[i], slaves ct_slave[j] with weights
@@ -77,8 +78,10 @@ struct HpData {
   std::vector<int64_t> probe_ptr;
   DevBuf probe_dofs;
 };
+// op: OP_STOKES_A (vector Laplacian, degree per cell), OP_STOKES (Taylor--Hood: velocity degree per
+// cell, pressure one lower) or OP_PMASS (scalar mass, degree per cell)
 void build_hp_oplevel(OpLevel& lv, const Forest& f, const std::vector<int32_t>& degree, const Physics& ph,
-                      Budget* bud);
+                      Budget* bud, int op = OP_STOKES_A);
 void hp_vmult(const OpLevel& lv, int prec, const void* src, void* dst, cudaStream_t s);
 void hp_diag(const OpLevel& lv, int prec, void* diag, cudaStream_t s);
 // y[m] += sum of w * y[slave] over the slaves of every master m (hp levels)
@@ -261,8 +264,10 @@ OpLevel& mg_level(Problem& p, int i);
 // Build everything for a mesh and a description; throws Error.
 // hp-adaptive vector Laplacian (Section 3): degree[c] per forest cell; hierarchy: every degree
 // lowered by one per level until all are linear, then global coarsening
+// kind 1: the vector Laplacian; kind 0: Taylor--Hood Stokes (system and pressure mass on hp spaces,
+// the A block on the hp hierarchy)
 std::unique_ptr<Problem> build_problem_hp(const Forest& f, const std::vector<int32_t>& degree, const Physics& ph,
-                                          int coarse_stop_n, Budget* bud);
+                                          int coarse_stop_n, Budget* bud, int kind = 1);
 // hierarchy: 0 global coarsening, 1 local smoothing (vector Laplacian and the Stokes A block on a
 // locally refined mesh; an unrefined mesh needs none and gets global coarsening)
 std::unique_ptr<Problem> build_problem(const Forest& f, int kind, int k, const Physics& ph, int mg_order,

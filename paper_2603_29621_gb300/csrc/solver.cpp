@@ -177,15 +177,16 @@ static void build_local_smoothing(Problem& p, const Forest& f, int k, const Phys
 }
 
 std::unique_ptr<Problem> build_problem_hp(const Forest& f, const std::vector<int32_t>& degree, const Physics& ph,
-                                          int coarse_stop_n, Budget* bud) {
+                                          int coarse_stop_n, Budget* bud, int kind) {
   if (degree.size() != f.n_cells()) throw Error(kErrArg, "one degree per cell expected");
+  if (kind != 0 && kind != 1) throw Error(kErrUnsupported, "hp problems: Stokes or its A block");
   auto uniform = [](const std::vector<int32_t>& d) {
     return std::all_of(d.begin(), d.end(), [&](int32_t k) { return k == d[0]; });
   };
-  if (uniform(degree)) return build_problem(f, 1, degree[0], ph, 1, coarse_stop_n, bud, 0);
+  if (uniform(degree)) return build_problem(f, kind, degree[0], ph, 1, coarse_stop_n, bud, 0);
   auto p = std::make_unique<Problem>();
   p->uid = ++g_problem_uid;
-  p->kind = 1;
+  p->kind = kind;
   p->dim = f.dim;
   p->k = *std::max_element(degree.begin(), degree.end());
   p->phys = ph;
@@ -219,6 +220,14 @@ std::unique_ptr<Problem> build_problem_hp(const Forest& f, const std::vector<int
     else
       build_transfer(*t, *p->levels[l], *p->levels[l + 1], bud);
     p->transfers.push_back(std::move(t));
+  }
+  if (kind == 0) {  // Taylor--Hood system and the pressure mass of the Schur complement (Eq. 5)
+    p->system = std::make_unique<OpLevel>();
+    build_hp_oplevel(*p->system, f, degree, ph, bud, OP_STOKES);
+    std::vector<int32_t> dp(degree);
+    for (auto& k : dp) k -= 1;
+    p->pmass = std::make_unique<OpLevel>();
+    build_hp_oplevel(*p->pmass, f, dp, ph, bud, OP_PMASS);
   }
   return p;
 }
@@ -371,7 +380,11 @@ void autotune(Problem& p, cudaStream_t s) {
       void* b = prec == 0 ? p.tmp.get() : p.mg_x32.get();
       if ((int64_t)lv->n_dofs > (int64_t)sys_of(p).n_dofs) continue;
       MFNS_CUDA(cudaMemsetAsync(a, 0, lv->n_dofs * esize(prec), s));
-      autotune_warps(lv->L, prec, a, b, lv->n_dofs, s);
+      if (lv->hp) {  // hp operators: every degree group on its own (the level's own launch is empty)
+        for (auto& g : lv->hp->groups) autotune_warps(g->L, prec, a, b, lv->n_dofs, s);
+      } else {
+        autotune_warps(lv->L, prec, a, b, lv->n_dofs, s);
+      }
     }
   }
 }
