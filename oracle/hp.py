@@ -16,9 +16,17 @@ Readings of the paper:
   its own nodes); chains are resolved transitively; Dirichlet nodes are fixed to zero and take
   precedence.  This gives a conforming space whenever no hanging face has a coarse neighbour of
   higher degree than the fine cells on it (the tests check continuity across every interface and
-  the dimension against a brute-force rank).  The opposite configuration -- the face where the
-  paper's Jacobi+ASM smoother places its blocks -- needs both sides constrained to the lower
-  degree and is rejected here (NotImplementedError).
+  the dimension against a brute-force rank).  The opposite configuration -- the combined h+p face
+  where the paper's Jacobi+ASM smoother places its blocks -- needs both sides constrained to the
+  lower degree; the local rule rejects it (NotImplementedError).
+* The same space by elimination (rule 'elimination'), for every configuration including the
+  combined face: the continuity conditions on every shared face piece, as linear equations in the
+  non-boundary node values, brought to reduced row echelon form with the columns ordered from the
+  least to the most preferred node (coarser, then lower degree, then node id), so that the slaves
+  are the least preferred nodes.  Where the local rule applies it gives the same interior slaves
+  and the same weights on the free masters.  With combined faces the Jacobi-preconditioned A block
+  has a much larger largest eigenvalue (the ill-conditioned relations between the remaining
+  unknowns that Section 3 gives as the reason for the ASM blend).
 * Degrees: cell-wise k_c in 1..4 for the vector Laplacian; Taylor--Hood needs k_c >= 2 (pressure
   k_c - 1 >= 1).  Quadrature per cell: Gauss with k_c + 1 points per direction.
 * p-coarsening ("decreased one by one until ... all linear elements"): k_c -> max(k_c - 1, 1) on
@@ -39,9 +47,15 @@ class HpNodeSet:
     ``cell_nodes`` list of node-id arrays (one per cell, (k_c+1)^dim, lexicographic),
     ``boundary`` (Nn,), ``hanging`` dict node -> [(master, weight)] (masters unconstrained)."""
 
-    def __init__(self, forest, degrees):
+    def __init__(self, forest, degrees, rule="dominance"):
+        """rule: 'dominance' (the local rule of the module docstring) or 'elimination' (every
+        configuration, including a hanging face whose coarse cell has the higher degree: continuity
+        on every shared face piece and zero boundary values as linear conditions, eliminated in the
+        preference order coarser -> lower degree -> node id; the least preferred nodes become the
+        slaves)."""
         dim = forest.dim
         self.forest, self.dim = forest, dim
+        self.rule = rule
         self.degrees = np.asarray(degrees, dtype=np.int64)
         assert self.degrees.shape == (forest.n_cells,) and self.degrees.min() >= 1
         L = forest.max_level
@@ -83,7 +97,10 @@ class HpNodeSet:
         for g, c in zip(inv, own_c):
             self.owners[g].append(int(c))
         self.dom = [min((int(lev[c]), int(self.degrees[c])) for c in cs) for cs in self.owners]
-        self._find_constraints()
+        if rule == "elimination":
+            self._eliminate()
+        else:
+            self._find_constraints()
 
     def _touching(self):
         """(Nn, 2^dim) ids of the cells whose closed box holds each node."""
@@ -144,19 +161,105 @@ class HpNodeSet:
         self.hanging = {g: resolve(g) for g in direct}
 
 
+    def _face_pieces(self):
+        """(A, B, points) for every pair of cells sharing a piece of a face, with GLL points of
+        degree kmax + 1 on the piece (enough to identify the traces)."""
+        f = self.forest
+        N, cell_at = f.lattice()
+        dim, h, org = self.dim, f.h(), f.origin()
+        xs = fe.gll_points(int(self.degrees.max()) + 1)
+        out = []
+        for a in range(f.n_cells):
+            for d in range(dim):
+                for side in (0, 1):
+                    plane = org[a, d] + side * h[a]
+                    if plane <= 1e-12 or plane >= 1 - 1e-12:
+                        continue
+                    lo = np.rint(org[a] * N).astype(int)
+                    hi = np.rint((org[a] + h[a]) * N).astype(int)
+                    sl = [slice(lo[j], hi[j]) for j in range(dim)]
+                    q = int(round(plane * N))
+                    sl[d] = slice(q, q + 1) if side else slice(q - 1, q)
+                    for b in np.unique(cell_at[tuple(sl)]):
+                        if b < a and f.cells[b, 0] == f.cells[a, 0]:
+                            continue                     # same-level pairs once
+                        lo_s = np.maximum(org[a], org[b])
+                        hi_s = np.minimum(org[a] + h[a], org[b] + h[b])
+                        tang = [j for j in range(dim) if j != d]
+                        grids = np.meshgrid(*[lo_s[j] + (hi_s[j] - lo_s[j]) * xs for j in tang], indexing="ij")
+                        pts = np.zeros((grids[0].size, dim))
+                        for j, g in zip(tang, grids):
+                            pts[:, j] = g.ravel()
+                        pts[:, d] = plane
+                        out.append((a, int(b), pts))
+        return out
+
+    def _eliminate(self):
+        """Constraints by elimination (rule 'elimination'): the continuity conditions G u = 0 on the
+        non-boundary nodes, reduced to row echelon form with the columns in reverse preference order,
+        so that every pivot (slave) is as little preferred as possible; slave = -sum of its row's
+        free entries.  Boundary nodes are fixed to zero and are not variables."""
+        f, dim = self.forest, self.dim
+        lev = f.cells[:, 0]
+        h, org = f.h(), f.origin()
+        var = np.nonzero(~self.boundary)[0]
+        col_of = -np.ones(self.n_nodes, dtype=np.int64)
+        pref = sorted(var.tolist(), key=lambda g: (self.dom[g][0], self.dom[g][1], g))
+        order = pref[::-1]                                 # least preferred first: pivots land there
+        for j, g in enumerate(order):
+            col_of[g] = j
+        rows = []
+        for a, b, pts in self._face_pieces():
+            G = np.zeros((len(pts), len(order)))
+            for c, sgn in ((a, 1.0), (b, -1.0)):
+                xi = np.clip((pts - org[c]) / h[c], 0.0, 1.0)
+                phi = fe.eval_basis_at(dim, int(self.degrees[c]), xi)
+                for bb, g in enumerate(self.cell_nodes[c]):
+                    if col_of[g] >= 0:
+                        G[:, col_of[g]] += sgn * phi[:, bb]
+            rows.append(G)
+        G = np.concatenate(rows) if rows else np.zeros((0, len(order)))
+        # reduced row echelon form (Gauss--Jordan, largest entry in the pivot column)
+        R = G.copy()
+        piv_cols, r = [], 0
+        tol = 1e-10 * max(1.0, np.abs(R).max() if R.size else 1.0)
+        for j in range(R.shape[1]):
+            if r >= R.shape[0]:
+                break
+            i = r + int(np.argmax(np.abs(R[r:, j])))
+            if abs(R[i, j]) <= tol:
+                continue
+            R[[r, i]] = R[[i, r]]
+            R[r] /= R[r, j]
+            others = np.nonzero(np.abs(R[:, j]) > 0)[0]
+            for i2 in others:
+                if i2 != r:
+                    R[i2] -= R[i2, j] * R[r]
+            piv_cols.append(j)
+            r += 1
+        R = R[:r]
+        R[np.abs(R) < 1e-13] = 0.0
+        pivots = set(piv_cols)
+        self.hanging = {}
+        for i, j in enumerate(piv_cols):
+            g = order[j]
+            masters = [(order[q], -float(R[i, q])) for q in np.nonzero(R[i])[0] if q not in pivots]
+            self.hanging[int(g)] = sorted((int(m), w) for m, w in masters)
+
+
 class HpDofHandler:
     """DoFs of fields on an hp forest: ``fields`` = [(n_components, degree_shift, dirichlet)], the
     field's degree on cell c being degrees[c] - degree_shift.  Numbering: field by field, component
     by component, node by node (as ``mesh.DofHandler``)."""
 
-    def __init__(self, forest, degrees, fields):
+    def __init__(self, forest, degrees, fields, rule="dominance"):
         self.forest, self.dim = forest, forest.dim
         self.degrees = np.asarray(degrees, dtype=np.int64)
         self.fields = fields
         self.nodesets, self.offsets = [], []
         off = 0
         for nc, shift, _ in fields:
-            ns = HpNodeSet(forest, self.degrees - shift)
+            ns = HpNodeSet(forest, self.degrees - shift, rule)
             self.nodesets.append(ns)
             self.offsets.append(off)
             off += nc * ns.n_nodes
@@ -228,7 +331,7 @@ class HpProblem:
     """Operator on an hp forest: kind 'stokes_a' (vector Laplacian nu (grad u, grad v)) or 'stokes'
     (Taylor--Hood, symmetric form of Eq. 5)."""
 
-    def __init__(self, forest, degrees, kind, nu=1.0):
+    def __init__(self, forest, degrees, kind, nu=1.0, rule="dominance"):
         dim = forest.dim
         self.forest, self.kind, self.nu, self.dim = forest, kind, nu, dim
         self.degrees = np.asarray(degrees, dtype=np.int64)
@@ -239,7 +342,7 @@ class HpProblem:
             fields = [(dim, 0, True), (1, 1, False)]
         else:
             raise ValueError(kind)
-        self.dofs = HpDofHandler(forest, self.degrees, fields)
+        self.dofs = HpDofHandler(forest, self.degrees, fields, rule)
 
     def assemble_K(self):
         d = self.dofs

@@ -241,3 +241,100 @@ def test_taylor_hood_hp_energy_closed_form():
         pb = P.evaluate_in(x, pts, np.full(len(pts), b), 1, 0)
         worst = max(worst, np.abs(pa - pb).max())
     assert worst <= 1e-12
+
+
+# -- the elimination rule: every configuration, including the combined h+p face ----------------------
+@pytest.mark.parametrize("dim,n,levels,base", [(2, 3, 1, 1), (2, 3, 2, 1), (2, 2, 1, 2), (3, 2, 1, 1)])
+def test_elimination_reproduces_the_dominance_rule(dim, n, levels, base):
+    """Two independent constructions of the same space: local dominance and global elimination in
+    the preference order (coarser, lower degree, node id) give the same slaves and the same weights
+    on the free masters."""
+    f = _ball(dim, n, levels)
+    deg = _degrees(f, base)
+    a = hp.HpNodeSet(f, deg)
+    b = hp.HpNodeSet(f, deg, "elimination")
+    # elimination keeps boundary nodes out of the unknowns (they are zero): compare interior slaves
+    # and their free masters
+    assert {g for g in a.hanging if not a.boundary[g]} == set(b.hanging)
+    for g, masters in b.hanging.items():
+        ref = {m: w for m, w in a.hanging[g] if not a.boundary[m]}
+        got = dict(masters)
+        assert not any(b.boundary[m] for m in got)
+        assert max(abs(ref.get(m, 0.0) - got.get(m, 0.0)) for m in set(ref) | set(got)) <= 1e-12
+
+
+def _combined(f, kind):
+    lev = f.cells[:, 0]
+    return {"3-2": 3 - lev, "4-2": 4 - 2 * lev}[kind]
+
+
+@pytest.mark.parametrize("dim,n,kind", [(2, 3, "3-2"), (2, 4, "4-2"), (3, 2, "3-2")])
+def test_combined_faces_conforming_with_the_right_dimension(dim, n, kind):
+    """A hanging face whose coarse cell has the higher degree: traces agree on every interface and
+    the number of free DoFs is the brute-force dimension of the conforming space."""
+    f = _ball(dim, n, 1)
+    deg = _combined(f, kind)
+    with pytest.raises(NotImplementedError):
+        hp.HpNodeSet(f, deg)
+    P = hp.HpProblem(f, deg, "stokes_a", rule="elimination")
+    d = P.dofs
+    x = d.distribute(np.random.default_rng(2).uniform(-1, 1, d.n_dofs))
+    worst = 0.0
+    for a, b, pts in _face_pieces(f):
+        ua = P.evaluate_in(x, pts, np.full(len(pts), a), 0, 0)
+        ub = P.evaluate_in(x, pts, np.full(len(pts), b), 0, 0)
+        worst = max(worst, np.abs(ua - ub).max())
+    assert worst <= 1e-10
+    if dim == 2:
+        ns = d.nodesets[0]
+        free = ~ns.boundary
+        free[list(ns.hanging)] = False
+        offs = np.cumsum([0] + [(int(k) + 1) ** dim for k in deg])
+        h, org = f.h(), f.origin()
+        rows = []
+        for a, b, pts in _face_pieces(f):
+            G = np.zeros((len(pts), offs[-1]))
+            for c, sgn in ((a, 1.0), (b, -1.0)):
+                G[:, offs[c]:offs[c + 1]] += sgn * fe.eval_basis_at(dim, int(deg[c]), np.clip((pts - org[c]) / h[c], 0, 1))
+            rows.append(G)
+        for c in range(f.n_cells):
+            loc = fe.tensor_index(dim, int(deg[c]) + 1)
+            on = ((loc == 0) & (org[c] <= 1e-12)[None]) | ((loc == deg[c]) & (org[c] + h[c] >= 1 - 1e-12)[None])
+            for i in np.nonzero(on.any(axis=1))[0]:
+                r = np.zeros((1, offs[-1]))
+                r[0, offs[c] + i] = 1.0
+                rows.append(r)
+        G = np.concatenate(rows)
+        assert offs[-1] - np.linalg.matrix_rank(G, tol=1e-9) == int(free.sum())
+
+
+def test_combined_faces_energy_closed_form():
+    f = _ball(2, 3, 1)
+    nu = 0.7
+    P = hp.HpProblem(f, _combined(f, "3-2"), "stokes_a", nu=nu, rule="elimination")
+
+    def u(x):
+        phi = np.prod(x * (1 - x), axis=1)
+        return np.stack([phi, 2 * phi], axis=1)
+
+    xv = P.dofs.interpolate(u)
+    assert np.abs(P.dofs.distribute(xv) - xv).max() <= 1e-12
+    energy = xv @ (P.assemble_K() @ xv)
+    exact = nu * (1.0 / 45.0) * 5
+    assert abs(energy - exact) <= 1e-11 * exact
+
+
+def test_combined_faces_raise_the_jacobi_eigenvalue():
+    """Section 3: eliminating the constrained unknowns of a combined h+p face leaves ill-conditioned
+    relations between the remaining ones, visible in the eigenvalue estimate of the Jacobi-
+    preconditioned A block (Fig. 3): lambda_max(D^-1 A) well above its value without such faces."""
+    def lmax(f, deg, rule):
+        P = hp.HpProblem(f, deg, "stokes_a", rule=rule)
+        A = P.assemble()
+        d = P.dofs.free
+        Af = A[d][:, d].toarray()
+        return np.abs(np.linalg.eigvals(Af / np.diag(Af)[:, None])).max()
+    f = _ball(2, 5, 1)
+    plain = lmax(f, 2 + f.cells[:, 0], "dominance")
+    combined = lmax(f, 3 - f.cells[:, 0], "elimination")
+    assert plain < 2.0 and combined > 2.5 * plain
