@@ -47,15 +47,18 @@ class HpNodeSet:
     ``cell_nodes`` list of node-id arrays (one per cell, (k_c+1)^dim, lexicographic),
     ``boundary`` (Nn,), ``hanging`` dict node -> [(master, weight)] (masters unconstrained)."""
 
-    def __init__(self, forest, degrees, rule="dominance"):
+    def __init__(self, forest, degrees, rule="dominance", dirichlet=True):
         """rule: 'dominance' (the local rule of the module docstring) or 'elimination' (every
         configuration, including a hanging face whose coarse cell has the higher degree: continuity
-        on every shared face piece and zero boundary values as linear conditions, eliminated in the
-        preference order coarser -> lower degree -> node id; the least preferred nodes become the
-        slaves)."""
+        on every shared face piece as linear conditions, eliminated in the preference order
+        coarser -> lower degree -> node id; the least preferred nodes become the slaves).
+        dirichlet (elimination only): boundary values are fixed to zero and are not unknowns;
+        without it (a field with no boundary condition, the Taylor--Hood pressure) every node is
+        an unknown."""
         dim = forest.dim
         self.forest, self.dim = forest, dim
         self.rule = rule
+        self.fixed_boundary = dirichlet
         self.degrees = np.asarray(degrees, dtype=np.int64)
         assert self.degrees.shape == (forest.n_cells,) and self.degrees.min() >= 1
         L = forest.max_level
@@ -196,13 +199,13 @@ class HpNodeSet:
 
     def _eliminate(self):
         """Constraints by elimination (rule 'elimination'): the continuity conditions G u = 0 on the
-        non-boundary nodes, reduced to row echelon form with the columns in reverse preference order,
+        unknown node values, reduced to row echelon form with the columns in reverse preference order,
         so that every pivot (slave) is as little preferred as possible; slave = -sum of its row's
-        free entries.  Boundary nodes are fixed to zero and are not variables."""
+        free entries.  With fixed_boundary the boundary nodes are zero and are not unknowns."""
         f, dim = self.forest, self.dim
         lev = f.cells[:, 0]
         h, org = f.h(), f.origin()
-        var = np.nonzero(~self.boundary)[0]
+        var = np.nonzero(~self.boundary)[0] if self.fixed_boundary else np.arange(self.n_nodes)
         col_of = -np.ones(self.n_nodes, dtype=np.int64)
         pref = sorted(var.tolist(), key=lambda g: (self.dom[g][0], self.dom[g][1], g))
         order = pref[::-1]                                 # least preferred first: pivots land there
@@ -258,8 +261,8 @@ class HpDofHandler:
         self.fields = fields
         self.nodesets, self.offsets = [], []
         off = 0
-        for nc, shift, _ in fields:
-            ns = HpNodeSet(forest, self.degrees - shift, rule)
+        for nc, shift, dbc in fields:
+            ns = HpNodeSet(forest, self.degrees - shift, rule, dirichlet=dbc)
             self.nodesets.append(ns)
             self.offsets.append(off)
             off += nc * ns.n_nodes

@@ -268,6 +268,22 @@ def _combined(f, kind):
     return {"3-2": 3 - lev, "4-2": 4 - 2 * lev}[kind]
 
 
+@pytest.mark.parametrize("dim,n,levels,base", [(2, 3, 1, 1), (2, 3, 2, 2), (3, 2, 1, 1)])
+def test_elimination_without_dirichlet_reproduces_every_constraint(dim, n, levels, base):
+    """A field without boundary conditions (the Taylor--Hood pressure): every node is an unknown,
+    and elimination gives every slave of the local rule, boundary ones included, with all weights."""
+    f = _ball(dim, n, levels)
+    deg = _degrees(f, base)
+    a = hp.HpNodeSet(f, deg)
+    b = hp.HpNodeSet(f, deg, "elimination", dirichlet=False)
+    assert set(a.hanging) == set(b.hanging)
+    if dim == 3:
+        assert any(a.boundary[g] for g in a.hanging)     # the ball reaches the boundary there
+    for g, masters in b.hanging.items():
+        ref, got = dict(a.hanging[g]), dict(masters)     # the local rule may list zero weights
+        assert max(abs(ref.get(m, 0.0) - got.get(m, 0.0)) for m in set(ref) | set(got)) <= 1e-12
+
+
 @pytest.mark.parametrize("dim,n,kind", [(2, 3, "3-2"), (2, 4, "4-2"), (3, 2, "3-2")])
 def test_combined_faces_conforming_with_the_right_dimension(dim, n, kind):
     """A hanging face whose coarse cell has the higher degree: traces agree on every interface and
@@ -338,3 +354,32 @@ def test_combined_faces_raise_the_jacobi_eigenvalue():
     plain = lmax(f, 2 + f.cells[:, 0], "dominance")
     combined = lmax(f, 3 - f.cells[:, 0], "elimination")
     assert plain < 2.0 and combined > 2.5 * plain
+
+
+def test_taylor_hood_on_combined_faces():
+    """Velocity degree 3 on the coarse cells and 2 on the refined ones (pressure 2 and 1): both fields
+    conforming across every interface, and the energy of u = (phi, 2 phi), p = x - 1/2 is
+    nu / 9 + 1/18 as on any conforming space that holds them."""
+    f = _ball(2, 3, 1)
+    deg = _combined(f, "3-2")
+    nu = 0.6
+    P = hp.HpProblem(f, deg, "stokes", nu=nu, rule="elimination")
+    d = P.dofs
+
+    def fields(x):
+        phi = np.prod(x * (1 - x), axis=1)
+        return np.stack([phi, 2 * phi, x[:, 0] - 0.5], axis=1)
+
+    xv = d.interpolate(fields)
+    assert np.abs(d.distribute(xv) - xv).max() <= 1e-12
+    energy = xv @ (P.assemble_K() @ xv)
+    exact = nu / 9.0 + 1.0 / 18.0
+    assert abs(energy - exact) <= 1e-11 * exact
+    x = d.distribute(np.random.default_rng(6).uniform(-1, 1, d.n_dofs))
+    worst = 0.0
+    for a, b, pts in _face_pieces(f):
+        for field in (0, 1):
+            va = P.evaluate_in(x, pts, np.full(len(pts), a), field, 0)
+            vb = P.evaluate_in(x, pts, np.full(len(pts), b), field, 0)
+            worst = max(worst, np.abs(va - vb).max())
+    assert worst <= 1e-10
