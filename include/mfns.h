@@ -207,12 +207,15 @@ int mfns_problem_create(mfns_ctx* ctx, const mfns_mesh* mesh, const mfns_problem
  * the order of mfns_mesh_cells) is the degree of cell c.  A node is constrained when a cell whose
  * closed box holds it does not have it as a node and dominates every cell that does (coarser, or
  * same level and lower degree); it takes that cell's finite-element function at its position.
+ * Where a hanging face has a coarse cell of higher degree than a fine cell (the combined h+p
+ * face), that rule does not give a conforming space; the constraints of the whole space then
+ * come from eliminating the continuity conditions of every face piece, the least preferred nodes
+ * (finer, then higher degree, then face before edge before vertex, then higher node id) becoming
+ * the constrained ones; every constrained node is expressed in nodes of its own face or edge.
  * The multigrid hierarchy lowers every degree by one per level until all cells are linear, then
  * coarsens globally.  desc->kind must be MFNS_STOKES_A or MFNS_STOKES (Taylor--Hood: velocity
  * degree per cell >= 2, pressure one lower, the A block on the hp hierarchy) and desc->hierarchy 0
- * (MFNS_ERR_UNSUPPORTED otherwise); a mesh on which a hanging face has a coarse cell of higher
- * degree than a fine cell returns MFNS_ERR_UNSUPPORTED; one degree everywhere is the same as
- * mfns_problem_create. */
+ * (MFNS_ERR_UNSUPPORTED otherwise); one degree everywhere is the same as mfns_problem_create. */
 int mfns_problem_create_hp(mfns_ctx* ctx, const mfns_mesh* mesh, const mfns_problem_desc* desc,
                            const int32_t* cell_degree, int64_t n_cells, mfns_problem** out);
 int mfns_problem_info(const mfns_problem* p, mfns_info* out);

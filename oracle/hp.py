@@ -21,12 +21,15 @@ Readings of the paper:
   lower degree; the local rule rejects it (NotImplementedError).
 * The same space by elimination (rule 'elimination'), for every configuration including the
   combined face: the continuity conditions on every shared face piece, as linear equations in the
-  non-boundary node values, brought to reduced row echelon form with the columns ordered from the
-  least to the most preferred node (coarser, then lower degree, then node id), so that the slaves
-  are the least preferred nodes.  Where the local rule applies it gives the same interior slaves
-  and the same weights on the free masters.  With combined faces the Jacobi-preconditioned A block
-  has a much larger largest eigenvalue (the ill-conditioned relations between the remaining
-  unknowns that Section 3 gives as the reason for the ASM blend).
+  unknown node values, brought to reduced row echelon form with the columns ordered from the least
+  to the most preferred node (coarser, then lower degree, then vertices before edge, face and cell
+  interiors, then node id), so that the slaves are the least preferred nodes.  The entity order
+  is what the standard construction does face by face (the vertex and edge values of the coarse
+  face are kept): without it, ties broken by node id alone let a shared vertex become a slave and
+  the constraints chain along the whole refinement interface.  Where the local rule applies it
+  gives the same interior slaves and the same weights on the free masters.  With combined faces
+  the Jacobi-preconditioned A block has a larger largest eigenvalue (the ill-conditioned relations
+  between the remaining unknowns that Section 3 gives as the reason for the ASM blend).
 * Degrees: cell-wise k_c in 1..4 for the vector Laplacian; Taylor--Hood needs k_c >= 2 (pressure
   k_c - 1 >= 1).  Quadrature per cell: Gauss with k_c + 1 points per direction.
 * p-coarsening ("decreased one by one until ... all linear elements"): k_c -> max(k_c - 1, 1) on
@@ -51,7 +54,8 @@ class HpNodeSet:
         """rule: 'dominance' (the local rule of the module docstring) or 'elimination' (every
         configuration, including a hanging face whose coarse cell has the higher degree: continuity
         on every shared face piece as linear conditions, eliminated in the preference order
-        coarser -> lower degree -> node id; the least preferred nodes become the slaves).
+        coarser -> lower degree -> lower entity dimension -> node id; the least preferred nodes
+        become the slaves).
         dirichlet (elimination only): boundary values are fixed to zero and are not unknowns;
         without it (a field with no boundary condition, the Taylor--Hood pressure) every node is
         an unknown."""
@@ -197,6 +201,18 @@ class HpNodeSet:
                         out.append((a, int(b), pts))
         return out
 
+    def _entity(self, g):
+        """Dimension of the entity a node is interior to in a dominating owner cell: 0 vertex, 1
+        edge, 2 face, 3 cell (the number of local coordinates strictly between 0 and k)."""
+        lev = self.forest.cells[:, 0]
+        for c in self.owners[g]:
+            if (int(lev[c]), int(self.degrees[c])) == self.dom[g]:
+                k = int(self.degrees[c])
+                i = int(np.nonzero(self.cell_nodes[c] == g)[0][0])
+                a = [(i // (k + 1) ** d) % (k + 1) for d in range(self.dim)]
+                return sum(1 for v in a if 0 < v < k)
+        raise AssertionError("node without a dominating owner")
+
     def _eliminate(self):
         """Constraints by elimination (rule 'elimination'): the continuity conditions G u = 0 on the
         unknown node values, reduced to row echelon form with the columns in reverse preference order,
@@ -207,7 +223,7 @@ class HpNodeSet:
         h, org = f.h(), f.origin()
         var = np.nonzero(~self.boundary)[0] if self.fixed_boundary else np.arange(self.n_nodes)
         col_of = -np.ones(self.n_nodes, dtype=np.int64)
-        pref = sorted(var.tolist(), key=lambda g: (self.dom[g][0], self.dom[g][1], g))
+        pref = sorted(var.tolist(), key=lambda g: (self.dom[g][0], self.dom[g][1], self._entity(g), g))
         order = pref[::-1]                                 # least preferred first: pivots land there
         for j, g in enumerate(order):
             col_of[g] = j
@@ -331,8 +347,10 @@ class HpDofHandler:
 
 
 class HpProblem:
-    """Operator on an hp forest: kind 'stokes_a' (vector Laplacian nu (grad u, grad v)) or 'stokes'
-    (Taylor--Hood, symmetric form of Eq. 5)."""
+    """Operator on an hp forest: kind 'stokes_a' (vector Laplacian nu (grad u, grad v)), 'stokes'
+    (Taylor--Hood, symmetric form of Eq. 5) or 'pmass' (the mass matrix of the Taylor--Hood pressure
+    space, degree k_c - 1 per cell, no boundary conditions: the Schur-complement approximation of
+    Eq. 5 up to the factor 1/nu).  ``degrees`` are the velocity degrees in every case."""
 
     def __init__(self, forest, degrees, kind, nu=1.0, rule="dominance"):
         dim = forest.dim
@@ -343,6 +361,9 @@ class HpProblem:
         elif kind == "stokes":
             assert self.degrees.min() >= 2, "Taylor--Hood needs velocity degree >= 2"
             fields = [(dim, 0, True), (1, 1, False)]
+        elif kind == "pmass":
+            assert self.degrees.min() >= 2, "Taylor--Hood needs velocity degree >= 2"
+            fields = [(1, 1, False)]
         else:
             raise ValueError(kind)
         self.dofs = HpDofHandler(forest, self.degrees, fields, rule)
@@ -355,6 +376,8 @@ class HpProblem:
             cells = np.nonzero(self.degrees == k)[0]
             if self.kind == "stokes_a":
                 Ke = forms.vector_laplacian(self.dim, int(k), self.nu, h[cells])
+            elif self.kind == "pmass":
+                Ke = forms.scalar_mass(self.dim, int(k) - 1, int(k), h[cells])
             else:
                 Ke = forms.stokes_taylor_hood(self.dim, int(k), self.nu, h[cells], -1.0)
             cd = np.stack([d.cell_dofs(c) for c in cells])
@@ -447,16 +470,17 @@ class Level:
         self.lmax = None
 
 
-def hierarchy(forest, degrees, nu=1.0, stop_n=2):
+def hierarchy(forest, degrees, nu=1.0, stop_n=2, rule="dominance"):
     """hp-multigrid levels of the A block (finest first): every cell's degree lowered by one per
-    level until all cells are linear, then global coarsening with linear elements."""
+    level until all cells are linear, then global coarsening with linear elements.  rule: the
+    constraint construction of every level (``HpNodeSet``)."""
     degrees = np.asarray(degrees, dtype=np.int64)
     seq = [(forest, degrees)]
     while seq[-1][1].max() > 1:
         seq.append((forest, np.maximum(seq[-1][1] - 1, 1)))
     for f in solvers.coarse_forests(forest, stop_n)[1:]:
         seq.append((f, np.ones(f.n_cells, dtype=np.int64)))
-    levels = [Level(HpProblem(f, d, "stokes_a", nu)) for f, d in seq]
+    levels = [Level(HpProblem(f, d, "stokes_a", nu, rule=rule)) for f, d in seq]
     for l in range(len(levels) - 1):
         levels[l].P = prolongation(levels[l + 1].problem, levels[l].problem)
     return levels

@@ -28,7 +28,9 @@ void build_hp_oplevel(OpLevel& lv, const Forest& f, const std::vector<int32_t>& 
   const int dim = f.dim;
   auto hp = std::make_unique<HpData>();
   std::string err;
-  if (!make_hp_space(f, degree, hp->space, &err))
+  // constraints: the local rule, elimination where a combined h+p face needs it; the main field has
+  // Dirichlet conditions unless it is the pressure mass's
+  if (!make_hp_space(f, degree, hp->space, &err, HpRule::kAuto, op != OP_PMASS))
     throw Error(err.rfind("unsupported", 0) == 0 ? kErrUnsupported : kErrArg, err);
   const HpSpace& sp = hp->space;
   // Taylor--Hood: the pressure space has degree k - 1 on every cell
@@ -39,7 +41,7 @@ void build_hp_oplevel(OpLevel& lv, const Forest& f, const std::vector<int32_t>& 
       if (k < 2) throw Error(kErrUnsupported, "Taylor--Hood needs velocity degrees >= 2");
       k -= 1;
     }
-    if (!make_hp_space(f, dp, psp, &err)) throw Error(err.rfind("unsupported", 0) == 0 ? kErrUnsupported : kErrArg, err);
+    if (!make_hp_space(f, dp, psp, &err, HpRule::kAuto, false)) throw Error(err.rfind("unsupported", 0) == 0 ? kErrUnsupported : kErrArg, err);
   }
   const bool dirichlet = op != OP_PMASS;
   lv.op = op;
@@ -206,7 +208,7 @@ void build_hp_oplevel(OpLevel& lv, const Forest& f, const std::vector<int32_t>& 
     std::vector<char> free_node(S.n_nodes, 0);
     for (int64_t g = 0; g < S.n_nodes; ++g) free_node[g] = !(F.dirichlet && S.boundary[g]) && !hangs[fi][g];
     std::vector<int32_t> pcol;
-    const int npc = hp_probe_groups(S, free_node, pcol);
+    const int npc = hp_probe_groups(S, free_node, pcol, F.dirichlet);
     std::vector<std::vector<int32_t>> bucket(npc);  // free nodes of every group, ascending
     for (int64_t m = 0; m < S.n_nodes; ++m)
       if (pcol[m] >= 0) bucket[pcol[m]].push_back((int32_t)m);

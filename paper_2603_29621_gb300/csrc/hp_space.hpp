@@ -2,12 +2,19 @@
 // degree; nodes are identified exactly; the constraints of h- and p-adaptivity are resolved to
 // free masters.
 //
-// Constraint rule: a node is constrained when a cell whose closed box holds it does not have it
-// as a node and dominates every cell that does (it is coarser, or of the same level and of lower
-// degree); the node then takes that cell's finite-element function at its position.  Chains (a
-// master that is itself constrained) are resolved transitively, so every listed master is free
-// of hanging constraints.  This is a conforming space unless a hanging face has a coarse cell of
-// higher degree than a fine cell on it; that configuration is rejected.
+// Constraint rules.  Local (dominance): a node is constrained when a cell whose closed box holds it
+// does not have it as a node and dominates every cell that does (it is coarser, or of the same
+// level and of lower degree); the node then takes that cell's finite-element function at its
+// position.  Chains (a master that is itself constrained) are resolved transitively, so every
+// listed master is free of hanging constraints.  This is a conforming space unless a hanging face
+// has a coarse cell of higher degree than a fine cell on it (the combined h+p face).
+// Elimination: the continuity conditions on every shared face piece, in reduced row echelon form
+// with the columns ordered from the least to the most preferred node (coarser, then lower degree,
+// then vertices before edge, face and cell interiors, then node id); the pivots are the
+// constrained nodes, each expressed in nodes of its own face or edge.  It covers every configuration, including
+// the combined face, and gives the local rule's constraints where that applies (boundary handling
+// aside: with Dirichlet conditions boundary nodes are not unknowns and are neither constrained
+// nor masters).
 #pragma once
 #include <cstdint>
 #include <string>
@@ -31,8 +38,17 @@ struct HpSpace {
   std::vector<double> hang_w;
 };
 
+enum class HpRule {
+  kAuto = 0,         // the local rule, elimination where a combined h+p face makes it inapplicable
+  kDominance = 1,    // the local rule only (fails on a combined face)
+  kElimination = 2,  // elimination everywhere
+};
+
 // Builds the space; false with a message in err for an unsupported configuration or bad input.
-bool make_hp_space(const Forest& f, const std::vector<int32_t>& degree, HpSpace& out, std::string* err);
+// dirichlet: the field has homogeneous Dirichlet conditions on the domain boundary (used by the
+// elimination rule, which then takes boundary nodes as zero rather than as unknowns).
+bool make_hp_space(const Forest& f, const std::vector<int32_t>& degree, HpSpace& out, std::string* err,
+                   HpRule rule = HpRule::kAuto, bool dirichlet = true);
 
 // Greedy colouring of a subset of cells: no two cells of one colour share a node.  color[i] is the
 // colour of cells[i]; returns the number of colours.
@@ -40,8 +56,11 @@ int hp_color_cells(const HpSpace& sp, const std::vector<int32_t>& cells, std::ve
 
 // Groups of free nodes for probing the diagonal of C^T K C: two free nodes share a group only if no
 // cell holds a node whose free masters include both (a free node is its own master).  `free_node`
-// marks the free nodes; masters of constrained nodes are hang_master entries that are free.
+// marks the free nodes; masters of constrained nodes are hang_master entries that are free.  With
+// `dirichlet` boundary nodes are zero and couple nothing; without it (a field with no boundary
+// condition) a constrained boundary node couples its masters like any other.
 // group[g] is the group of free node g (-1 otherwise); returns the number of groups.
-int hp_probe_groups(const HpSpace& sp, const std::vector<char>& free_node, std::vector<int32_t>& group);
+int hp_probe_groups(const HpSpace& sp, const std::vector<char>& free_node, std::vector<int32_t>& group,
+                    bool dirichlet = true);
 
 }  // namespace mfns

@@ -24,8 +24,8 @@ HARNESS = r"""
 #include "hp_space.hpp"
 using namespace mfns;
 int main() {
-  int dim, n, nc;
-  if (std::scanf("%d %d %d", &dim, &n, &nc) != 3) return 1;
+  int dim, n, nc, rule, dbc;
+  if (std::scanf("%d %d %d %d %d", &dim, &n, &nc, &rule, &dbc) != 5) return 1;
   Forest f;
   f.dim = dim;
   f.n = n;
@@ -39,7 +39,7 @@ int main() {
   }
   HpSpace sp;
   std::string err;
-  if (!make_hp_space(f, deg, sp, &err)) { std::printf("FAIL %s\n", err.c_str()); return 0; }
+  if (!make_hp_space(f, deg, sp, &err, (HpRule)rule, dbc != 0)) { std::printf("FAIL %s\n", err.c_str()); return 0; }
   for (int32_t g : sp.cell_nodes) if (g < 0 || g >= sp.n_nodes) { std::printf("FAIL index\n"); return 0; }
   std::printf("NODES %lld\n", (long long)sp.n_nodes);
   for (int64_t g = 0; g < sp.n_nodes; ++g) {
@@ -69,9 +69,9 @@ int main() {
     }
     std::vector<char> freen(sp.n_nodes, 1), hang(sp.n_nodes, 0);
     for (int32_t g : sp.hang_node) hang[g] = 1;
-    for (int64_t g = 0; g < sp.n_nodes; ++g) freen[g] = !sp.boundary[g] && !hang[g];
+    for (int64_t g = 0; g < sp.n_nodes; ++g) freen[g] = !(dbc && sp.boundary[g]) && !hang[g];
     std::vector<int32_t> group;
-    const int ng = hp_probe_groups(sp, freen, group);
+    const int ng = hp_probe_groups(sp, freen, group, dbc != 0);
     std::vector<int32_t> hrow(sp.n_nodes, -1);
     for (size_t i = 0; i < sp.hang_node.size(); ++i) hrow[sp.hang_node[i]] = (int32_t)i;
     for (int c = 0; c < nc; ++c) {
@@ -79,7 +79,7 @@ int main() {
       for (int64_t j = sp.cell_ptr[c]; j < sp.cell_ptr[c + 1]; ++j) {
         const int32_t g = sp.cell_nodes[j];
         if (freen[g]) ms.push_back(g);
-        else if (hrow[g] >= 0 && !sp.boundary[g])
+        else if (hrow[g] >= 0 && !(dbc && sp.boundary[g]))
           for (int32_t q = sp.hang_ptr[hrow[g]]; q < sp.hang_ptr[hrow[g] + 1]; ++q)
             if (freen[sp.hang_master[q]]) ms.push_back(sp.hang_master[q]);
       }
@@ -114,9 +114,10 @@ def harness(tmp_path_factory):
     subprocess.run(["g++", "-O1", "-std=c++17", "-I", CSRC, str(src), os.path.join(CSRC, "mesh.cpp"),
                     os.path.join(CSRC, "hp_space.cpp"), "-o", str(exe)], check=True)
 
-    def run(forest, deg):
+    def run(forest, deg, rule=0, dirichlet=True):
+        """rule: 0 auto, 1 the local rule only, 2 elimination everywhere."""
         rows = [f"{c[0]} {c[1]} {c[2]} {c[3] if forest.dim == 3 else 0} {k}" for c, k in zip(forest.cells, deg)]
-        inp = f"{forest.dim} {forest.n} {len(rows)}\n" + "\n".join(rows) + "\n"
+        inp = f"{forest.dim} {forest.n} {len(rows)} {rule} {int(dirichlet)}\n" + "\n".join(rows) + "\n"
         out = subprocess.run([str(exe)], input=inp, capture_output=True, text=True, check=True).stdout.split("\n")
         if out[0].startswith("FAIL"):
             return out[0]
@@ -166,7 +167,62 @@ def test_hp_space_matches_the_oracle(harness, dim, n, levels, base):
         assert max(abs(mine[q] - ref[q]) for q in ref) <= 1e-12
 
 
-def test_coarse_higher_degree_across_a_hanging_face_is_rejected(harness):
+def _compare(got, ns):
+    """Library space against an oracle node set: same nodes, boundary flags, constrained nodes and
+    weights (a master of weight zero may be listed on one side only)."""
+    assert not isinstance(got, str), got
+    x, bnd, hang = got
+    assert len(x) == ns.n_nodes
+    idx = dict(zip(_key(ns.x), range(ns.n_nodes)))
+    m = np.array([idx[k] for k in _key(x)])
+    assert len(set(m.tolist())) == len(m)
+    assert np.array_equal(bnd, ns.boundary[m])
+    assert set(m[list(hang)].tolist()) == set(ns.hanging)
+    for g, masters in hang.items():
+        ref = dict(ns.hanging[m[g]])
+        mine = {int(m[q]): w for q, w in masters}
+        assert max(abs(mine.get(q, 0.0) - ref.get(q, 0.0)) for q in set(ref) | set(mine)) <= 1e-12
+    return len(hang)
+
+
+def _combined(f, kind):
+    lev = f.cells[:, 0]
+    return {"3-2": 3 - lev, "4-2": 4 - 2 * lev, "4-3": 4 - lev}[kind]
+
+
+def test_coarse_higher_degree_across_a_hanging_face_is_rejected_by_the_local_rule(harness):
     f = mesh.refine_ball(mesh.uniform(2, 3), (0.3, 0.35, 0.4), 0.3, 1)
-    out = harness(f, 3 - f.cells[:, 0])
+    out = harness(f, 3 - f.cells[:, 0], rule=1)
     assert isinstance(out, str) and "unsupported" in out
+
+
+@pytest.mark.parametrize("dirichlet", [True, False])
+@pytest.mark.parametrize("dim,n,levels,base", [(2, 3, 2, 1), (2, 2, 2, 2), (3, 2, 1, 1), (3, 3, 1, 2)])
+def test_elimination_matches_the_oracle_where_the_local_rule_applies(harness, dim, n, levels, base, dirichlet):
+    """Forced elimination against the oracle's elimination (dense reduced row echelon form over
+    other sample points): the reduced form is unique, so slaves and weights agree."""
+    f = mesh.refine_ball(mesh.uniform(dim, n), (0.3, 0.35, 0.4), 0.3, levels)
+    deg = _degrees(f, base)
+    ns = hp.HpNodeSet(f, deg, "elimination", dirichlet=dirichlet)
+    assert _compare(harness(f, deg, rule=2, dirichlet=dirichlet), ns) > 0
+
+
+@pytest.mark.parametrize("dirichlet", [True, False])
+@pytest.mark.parametrize("dim,n,kind", [(2, 3, "3-2"), (2, 4, "4-2"), (2, 3, "4-3"), (3, 2, "3-2"),
+                                        (3, 3, "3-2")])
+def test_combined_faces_by_elimination_match_the_oracle(harness, dim, n, kind, dirichlet):
+    """Coarse cells of higher degree than the refined ones: the automatic rule switches to
+    elimination and gives the oracle's constraints."""
+    f = mesh.refine_ball(mesh.uniform(dim, n), (0.3, 0.35, 0.4), 0.3, 1)
+    deg = _combined(f, kind)
+    ns = hp.HpNodeSet(f, deg, "elimination", dirichlet=dirichlet)
+    assert _compare(harness(f, deg, rule=0, dirichlet=dirichlet), ns) > 0
+
+
+def test_the_local_rule_stays_in_use_where_it_applies(harness):
+    """With no combined face the automatic rule is the local one: boundary constrained nodes are
+    listed (the local rule does not know the field's boundary condition)."""
+    f = mesh.refine_ball(mesh.uniform(3, 2), (0.3, 0.35, 0.4), 0.3, 1)
+    deg = _degrees(f, 1)
+    x, bnd, hang = harness(f, deg, rule=0)
+    assert any(bnd[g] for g in hang)

@@ -343,17 +343,36 @@ def test_combined_faces_energy_closed_form():
 def test_combined_faces_raise_the_jacobi_eigenvalue():
     """Section 3: eliminating the constrained unknowns of a combined h+p face leaves ill-conditioned
     relations between the remaining ones, visible in the eigenvalue estimate of the Jacobi-
-    preconditioned A block (Fig. 3): lambda_max(D^-1 A) well above its value without such faces."""
+    preconditioned A block (Fig. 3): lambda_max(D^-1 A) clearly above its value on the same mesh
+    without combined faces.  The constraints being local, the rise does not grow with the mesh."""
     def lmax(f, deg, rule):
         P = hp.HpProblem(f, deg, "stokes_a", rule=rule)
         A = P.assemble()
         d = P.dofs.free
         Af = A[d][:, d].toarray()
         return np.abs(np.linalg.eigvals(Af / np.diag(Af)[:, None])).max()
-    f = _ball(2, 5, 1)
-    plain = lmax(f, 2 + f.cells[:, 0], "dominance")
-    combined = lmax(f, 3 - f.cells[:, 0], "elimination")
-    assert plain < 2.0 and combined > 2.5 * plain
+    ratios = []
+    for n in (3, 5):
+        f = _ball(2, n, 1)
+        plain = lmax(f, 2 + f.cells[:, 0], "dominance")
+        combined = lmax(f, 3 - f.cells[:, 0], "elimination")
+        assert plain < 2.0
+        ratios.append(combined / plain)
+    assert min(ratios) > 1.2 and abs(ratios[1] - ratios[0]) < 0.05
+
+
+@pytest.mark.parametrize("dim,n,kind", [(2, 8, "3-2"), (2, 6, "4-2"), (3, 3, "3-2")])
+def test_elimination_constraints_are_local(dim, n, kind):
+    """Within equal (level, degree) the preference takes vertices before edge, then face interiors,
+    so a slave's masters lie in the coarse cell of its face: bounded in number and in distance,
+    whatever the size of the refined region."""
+    f = _ball(dim, n, 1)
+    ns = hp.HpNodeSet(f, _combined(f, kind), "elimination")
+    h0 = 1.0 / n
+    for g, masters in ns.hanging.items():
+        assert len(masters) <= (4 if dim == 2 else 16)
+        assert max(np.abs(ns.x[m] - ns.x[g]).max() for m, _ in masters) <= h0 + 1e-12
+        assert max(abs(w) for _, w in masters) <= 2.0
 
 
 def test_taylor_hood_on_combined_faces():
@@ -383,3 +402,33 @@ def test_taylor_hood_on_combined_faces():
             vb = P.evaluate_in(x, pts, np.full(len(pts), b), field, 0)
             worst = max(worst, np.abs(va - vb).max())
     assert worst <= 1e-10
+
+
+def test_pressure_mass_uniform_degree_is_the_standard_one():
+    f = _ball(2, 3, 1)
+    H = hp.HpProblem(f, np.full(f.n_cells, 3), "pmass")
+    S = assemble.Problem(f, "pmass", 2)
+    xh, _ = H.dofs.support_points()
+    xs, _ = S.dofs.support_points()
+    key = {tuple(np.rint(x * 2 ** 30).astype(np.int64)): i for i, x in enumerate(xs)}
+    perm = np.array([key[tuple(np.rint(x * 2 ** 30).astype(np.int64))] for x in xh])
+    assert np.array_equal(H.dofs.constrained, S.dofs.constrained[perm])
+    Ah, As = H.assemble(), S.assemble()[perm][:, perm]
+    assert abs(Ah - As).max() <= 1e-15 * abs(As).max()
+
+
+@pytest.mark.parametrize("rule,degf", [("dominance", lambda f: _degrees(f, 2)),
+                                       ("elimination", lambda f: _combined(f, "3-2"))])
+@pytest.mark.parametrize("dim", [2, 3])
+def test_pressure_mass_closed_forms(dim, rule, degf):
+    """Pressure degrees 1..3 (or combined faces): int 1 = 1 and int (x - 1/2)^2 = 1/12 over the
+    unit square/cube, both functions being in every pressure space."""
+    f = _ball(dim, 3 if dim == 2 else 2, 1)
+    P = hp.HpProblem(f, degf(f), "pmass", rule=rule)
+    M = P.assemble_K()
+    one = P.dofs.interpolate(lambda x: np.ones((len(x), 1)))
+    lin = P.dofs.interpolate(lambda x: (x[:, :1] - 0.5))
+    for v in (one, lin):
+        assert np.abs(P.dofs.distribute(v) - v).max() <= 1e-12
+    assert abs(one @ M @ one - 1.0) <= 1e-13
+    assert abs(lin @ M @ lin - 1.0 / 12.0) <= 1e-13
