@@ -127,10 +127,12 @@ def test_hp_solve_converges(ctx, mg_precision):
 
 
 def test_hp_rejects_unsupported(ctx):
+    """hp problems use global coarsening (local smoothing of hp levels is not built)."""
     from paper_2603_29621_gb300 import _lib as L, api
     m = api.Mesh(ctx, 2, 3)
     m.refine_ball(CENTRE, 0.3, 1)
     cells = m.cells()
     with pytest.raises(L.MfnsError) as e:
-        api.Problem(ctx, m, degrees=(3 - cells[:, 0]).astype(np.int32), kind=L.STOKES_A, degree=3)
+        api.Problem(ctx, m, degrees=(2 + cells[:, 0]).astype(np.int32), kind=L.STOKES_A, degree=3,
+                    hierarchy=L.LOCAL_SMOOTHING)
     assert e.value.code == L.ERR_UNSUPPORTED
