@@ -90,6 +90,7 @@ extern "C" {
 typedef struct mfns_ctx mfns_ctx;
 typedef struct mfns_mesh mfns_mesh;
 typedef struct mfns_problem mfns_problem;
+typedef struct mfns_spacetime mfns_spacetime;
 
 typedef struct {
   int kind;             /* MFNS_STOKES, MFNS_STOKES_A, MFNS_STAB_NS, MFNS_PMASS */
@@ -342,6 +343,34 @@ int mfns_batch_step(mfns_problem** problems, int n, int* running);
 int mfns_batch_vcycle(mfns_problem** problems, int n, int precision, void* const* b, void* const* x, void* stream);
 /* Iterations, relative residual and convergence of the last (or current) solve of p. */
 int mfns_solve_status(const mfns_problem* p, mfns_solve_info* info);
+
+/* ---- space-time slabs (Section 4) ----------------------------------------------------------- */
+/* One time slab of the transient Stokes equations on the Taylor--Hood space of `stokes` (an
+ * MFNS_STOKES problem built by mfns_problem_create; hp problems: MFNS_ERR_UNSUPPORTED), with
+ * DG(r) in time, 0 <= r <= 7: Q = r + 1 stages, the Lagrange basis at the Q right Gauss--Radau
+ * points of the slab (the last stage is the slab's end value; this is the Q-stage Radau IIA
+ * method), slab length tau > 0.  Vectors are stage-major: Q blocks of the problem's system vector
+ * (length Q * n, n = mfns_dof_support_points' length for MFNS_OP_SYSTEM).  The slab operator of
+ * Eq. 6 after mass scaling with M_Q^{-1}:
+ *     K = G_Q (x) M + tau I_Q (x) A,   G_Q = M_Q^{-1} A_Q,
+ * with reference-slab matrices M_Q[j][i] = int phi_i phi_j and A_Q[j][i] = int phi_i' phi_j +
+ * phi_i(0) phi_j(0), M the velocity mass (zero pressure rows, zero constrained rows) and A the
+ * problem's Stokes operator (identity rows on constrained entries), so constrained rows of K are
+ * tau times identity rows.  The problem must outlive the slab.  Errors: ARG, UNSUPPORTED, OOM,
+ * BUDGET, CUDA. */
+int mfns_spacetime_create(mfns_problem* stokes, int r, double tau, mfns_spacetime** out);
+/* Stage count, spatial vector length and (host arrays, may be NULL) the Q temporal nodes on
+ * [0, 1] and G_Q (Q x Q, row-major). */
+int mfns_spacetime_info(const mfns_spacetime* st, int* stages, int64_t* n_stage, double* nodes_host,
+                        double* g_host);
+/* y = K x (device vectors of length Q * n in `precision`; x and y must not overlap). */
+int mfns_spacetime_vmult(mfns_spacetime* st, int precision, const void* x, void* y, void* stream);
+int mfns_spacetime_destroy(mfns_spacetime* st);
+/* The DG(r) reference-slab matrices on the host, no device needed (any pointer may be NULL):
+ * nodes (Q), m_Q (Q, m_Q[j] = phi_j(0)), M_Q, A_Q and G_Q (Q x Q, row-major [j][i]).  Error: ARG
+ * for r outside 0..7. */
+int mfns_spacetime_temporal(int r, double* nodes_host, double* m_host, double* mq_host, double* aq_host,
+                            double* g_host);
 
 #ifdef __cplusplus
 }

@@ -98,6 +98,12 @@ _SIGS = {
     "mfns_solve_status": (C.c_int, [C.c_void_p, C.POINTER(SolveInfo)]),
     "mfns_batch_vcycle": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.c_int, C.POINTER(C.c_void_p),
                                     C.POINTER(C.c_void_p), C.c_void_p]),
+    "mfns_spacetime_create": (C.c_int, [C.c_void_p, C.c_int, C.c_double, C.POINTER(C.c_void_p)]),
+    "mfns_spacetime_info": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int64), C.c_void_p,
+                                      C.c_void_p]),
+    "mfns_spacetime_vmult": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "mfns_spacetime_destroy": (C.c_int, [C.c_void_p]),
+    "mfns_spacetime_temporal": (C.c_int, [C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
 }
 
 EXPORTED = tuple(_SIGS)

@@ -277,5 +277,48 @@ def batch_vcycle(problems, bs, xs, stream=None):
     arr = (C.c_void_p * n)(*[p.h for p in problems])
     bp = (C.c_void_p * n)(*[_ptr(b).value for b in bs])
     xp = (C.c_void_p * n)(*[_ptr(x).value for x in xs])
+    prec = L.FP64 if bs[0].dtype == torch.float64 else L.FP32
     L.check(L.load().mfns_batch_vcycle(arr, n, prec, bp, xp, _stream(stream)))
     return xs
+
+
+def temporal_matrices(r):
+    """DG(r) reference-slab matrices (host, no device): (nodes, m_Q, M_Q, A_Q, G_Q)."""
+    Q = r + 1
+    out = [np.zeros(Q), np.zeros(Q), np.zeros((Q, Q)), np.zeros((Q, Q)), np.zeros((Q, Q))]
+    L.check(L.load().mfns_spacetime_temporal(r, *[a.ctypes.data_as(C.c_void_p) for a in out]))
+    return tuple(out)
+
+
+class SpaceTime:
+    """One time slab (Section 4) on the Taylor--Hood space of a Stokes problem: DG(r) in time,
+    stage-major vectors of length Q * n."""
+
+    def __init__(self, problem, r, tau):
+        self.problem = problem                       # kept alive: the slab refers to it
+        self.lib = problem.lib
+        h = C.c_void_p()
+        L.check(self.lib.mfns_spacetime_create(problem.h, r, tau, C.byref(h)))
+        self.h = h
+        Q, n = C.c_int(), C.c_int64()
+        self.nodes = np.zeros(r + 1)
+        self.G = np.zeros((r + 1, r + 1))
+        L.check(self.lib.mfns_spacetime_info(h, C.byref(Q), C.byref(n), self.nodes.ctypes.data_as(C.c_void_p),
+                                             self.G.ctypes.data_as(C.c_void_p)))
+        self.Q, self.n = Q.value, n.value
+
+    def vmult(self, src, dst, stream=None):
+        prec = L.FP64 if src.dtype == torch.float64 else L.FP32
+        L.check(self.lib.mfns_spacetime_vmult(self.h, prec, _ptr(src), _ptr(dst), _stream(stream)))
+        return dst
+
+    def close(self):
+        if self.h:
+            self.lib.mfns_spacetime_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

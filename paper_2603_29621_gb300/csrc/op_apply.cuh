@@ -478,6 +478,15 @@ op_kernel(const OpArgs<T, K + 1, K + 1, (OP == OP_STOKES ? K : K + 1)> args) {
 #pragma unroll
       for (int l = 0; l < Q; ++l) c0[l] = val[l] * jxw[l];
       integrate<DIM, Q, N, true, false, T>(c0, g, r[0], buf1, buf2, ti, tj, tab.S, tab.D);
+    } else if constexpr (OP == OP_VMASS) {
+#pragma unroll
+      for (int f = 0; f < NU; ++f) {
+        T val[Q], c0[Q], g[DIM][Q];
+        values<DIM, Q, N, T>(u[f], val, buf0, ti, tj, tab.S);
+#pragma unroll
+        for (int l = 0; l < Q; ++l) c0[l] = val[l] * jxw[l];
+        integrate<DIM, Q, N, true, false, T>(c0, g, r[f], buf1, buf2, ti, tj, tab.S, tab.D);
+      }
     } else if constexpr (OP == OP_STOKES) {
       T gu[DIM][DIM][Q];
       T div[Q];

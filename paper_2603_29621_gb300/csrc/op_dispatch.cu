@@ -29,6 +29,8 @@ MFNS_DECL(3, 1, OP_STOKES_A) MFNS_DECL(3, 2, OP_STOKES_A) MFNS_DECL(3, 3, OP_STO
 MFNS_DECL(2, 1, OP_STOKES_A) MFNS_DECL(2, 2, OP_STOKES_A) MFNS_DECL(2, 3, OP_STOKES_A) MFNS_DECL(2, 4, OP_STOKES_A)
 MFNS_DECL(2, 1, OP_PMASS) MFNS_DECL(2, 2, OP_PMASS) MFNS_DECL(2, 3, OP_PMASS)
 MFNS_DECL(3, 1, OP_PMASS) MFNS_DECL(3, 2, OP_PMASS) MFNS_DECL(3, 3, OP_PMASS)
+MFNS_DECL(2, 2, OP_VMASS) MFNS_DECL(2, 3, OP_VMASS) MFNS_DECL(2, 4, OP_VMASS)
+MFNS_DECL(3, 2, OP_VMASS) MFNS_DECL(3, 3, OP_VMASS) MFNS_DECL(3, 4, OP_VMASS)
 
 bool op_supported(int dim, int k, int op) {
   if (dim != 2 && dim != 3) return false;
@@ -37,6 +39,7 @@ bool op_supported(int dim, int k, int op) {
     case OP_STOKES: return k >= 2 && k <= 4;
     case OP_STOKES_A: return k >= 1 && k <= 4;
     case OP_PMASS: return k >= 1 && k <= 3;
+    case OP_VMASS: return k >= 2 && k <= 4;  // the Taylor--Hood velocity degrees
   }
   return false;
 }
@@ -55,6 +58,8 @@ static void dispatch(const OpLaunch& L, const T* s, T* d, bool diag, cudaStream_
   MFNS_CASE(2, 1, OP_STOKES_A) MFNS_CASE(2, 2, OP_STOKES_A) MFNS_CASE(2, 3, OP_STOKES_A) MFNS_CASE(2, 4, OP_STOKES_A)
   MFNS_CASE(2, 1, OP_PMASS) MFNS_CASE(2, 2, OP_PMASS) MFNS_CASE(2, 3, OP_PMASS)
   MFNS_CASE(3, 1, OP_PMASS) MFNS_CASE(3, 2, OP_PMASS) MFNS_CASE(3, 3, OP_PMASS)
+  MFNS_CASE(2, 2, OP_VMASS) MFNS_CASE(2, 3, OP_VMASS) MFNS_CASE(2, 4, OP_VMASS)
+  MFNS_CASE(3, 2, OP_VMASS) MFNS_CASE(3, 3, OP_VMASS) MFNS_CASE(3, 4, OP_VMASS)
 #undef MFNS_CASE
   throw Error(kErrUnsupported, "unsupported (dim, degree, operator) combination");
 }

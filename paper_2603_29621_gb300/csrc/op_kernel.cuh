@@ -28,7 +28,7 @@ __host__ __device__ constexpr int ipow(int b, int e) { return e == 0 ? 1 : b * i
 
 template <int OP, int DIM>
 struct OpTraits {
-  static constexpr int NC = OP == OP_STOKES_A ? DIM : OP == OP_PMASS ? 1 : DIM + 1;  // components
+  static constexpr int NC = (OP == OP_STOKES_A || OP == OP_VMASS) ? DIM : OP == OP_PMASS ? 1 : DIM + 1;  // components
   static constexpr bool SPLIT_P = OP == OP_STOKES;   // pressure of lower degree in its own block
   static constexpr bool FROZEN = OP == OP_STAB_NS;
   static constexpr int NU = OP == OP_STOKES ? DIM : NC;  // components carried by the main nodes

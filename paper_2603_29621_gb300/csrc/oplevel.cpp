@@ -44,7 +44,7 @@ void build_oplevel(OpLevel& lv, const Forest& f, int op, int k, const Physics& p
   lv.k = k;
   lv.forest = f;
   const int dim = f.dim;
-  lv.NU = op == OP_STOKES_A ? dim : op == OP_PMASS ? 1 : op == OP_STOKES ? dim : dim + 1;
+  lv.NU = (op == OP_STOKES_A || op == OP_VMASS) ? dim : op == OP_PMASS ? 1 : op == OP_STOKES ? dim : dim + 1;
   Lattice lat = make_lattice(f);
   std::vector<uint32_t> masks = constraint_masks(f, lat);
   std::string err;

@@ -1,0 +1,37 @@
+// Space-time finite elements for one time slab of the transient Stokes equations (Section 4).
+//
+// The slab I_n = (t_{n-1}, t_n], tau = t_n - t_{n-1}, carries a DG(r) discretisation in time with
+// Q = r + 1 stages: the Lagrange basis phi_i at the Q right Gauss--Radau points of the slab (the
+// last point is the slab's end, so the value passed on to the next slab is the last stage).  On
+// the reference slab [0, 1]
+//   M_Q[j][i] = int phi_i phi_j,   A_Q[j][i] = int phi_i' phi_j + phi_i(0) phi_j(0),   m_Q[j] = phi_j(0)
+// (time derivative, upwind jump at the slab's start, previous end value); this is the Q-stage
+// Radau IIA method.  Stage values of the spatial vector are stored stage-major, and after mass
+// scaling with M_Q^{-1} the slab operator of Eq. 6 is
+//   K = G_Q (x) M + tau I_Q (x) A,   G_Q = M_Q^{-1} A_Q,
+// with M the velocity mass of the spatial Stokes space (zero pressure rows, zero constrained
+// rows) and A the spatial Stokes operator (identity rows on constrained entries), so the
+// constrained rows of K are tau times identity rows.
+#pragma once
+#include <string>
+#include <vector>
+
+namespace mfns {
+
+// The Q right Gauss--Radau points on [0, 1], ascending; the last one is 1.
+std::vector<double> radau_right(int Q);
+
+struct TemporalMatrices {
+  int Q = 0;
+  std::vector<double> t;        // Q nodes
+  std::vector<double> M, A, G;  // Q x Q, row-major: M[j * Q + i]
+  std::vector<double> m;        // Q
+};
+
+// DG(r) matrices on the reference slab, r in 0..7; false with a message otherwise.
+bool temporal_matrices(int r, TemporalMatrices& out, std::string* err);
+
+// P_tau (Q_f x Q_c, row-major): the coarse DG(rc) temporal polynomial at the fine DG(rf) nodes.
+std::vector<double> time_prolongation(int rc, int rf);
+
+}  // namespace mfns
