@@ -13,8 +13,11 @@
 // rows) and A the spatial Stokes operator (identity rows on constrained entries), so the
 // constrained rows of K are tau times identity rows.
 #pragma once
+#include <cstdint>
 #include <string>
 #include <vector>
+
+#include "mesh.hpp"
 
 namespace mfns {
 
@@ -33,5 +36,22 @@ bool temporal_matrices(int r, TemporalMatrices& out, std::string* err);
 
 // P_tau (Q_f x Q_c, row-major): the coarse DG(rc) temporal polynomial at the fine DG(rf) nodes.
 std::vector<double> time_prolongation(int rc, int rf);
+
+// Levels of the space-time multigrid, finest first: the spatial degree halved while above 2
+// (k >= 2 is kept: Q2 is the lowest Taylor--Hood velocity), then the temporal degree halved
+// (DG(r) -> DG(r / 2)) down to 0, then the coarser forests of global coarsening (index 1, 2, ...
+// of the forest sequence, forest 0 being the fine mesh); no coarsening of the slab length
+// (time-marching).
+struct StLevelSpec {
+  int k = 2, r = 0, forest = 0;
+};
+std::vector<StLevelSpec> stmg_sequence(int k, int r, int n_forests);
+
+// Patches of the space-time Schwarz smoother on a Taylor--Hood space (velocity entries g * dim + c
+// over the nodes of nu, then pressure entries n_main + g over the nodes of np): for every vertex
+// of the mesh, the cells having it as a corner form a star, and the patch is the set of free
+// entries (not Dirichlet, not hanging) every holding cell of which lies in the star.  Entries
+// ascending; stars in lattice order; empty patches dropped.
+std::vector<std::vector<int32_t>> vertex_star_patches(const Forest& f, const NodeSpace& nu, const NodeSpace& np);
 
 }  // namespace mfns

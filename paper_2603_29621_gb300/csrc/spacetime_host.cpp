@@ -1,5 +1,8 @@
 // Temporal matrices of DG(r) on right Gauss--Radau points (see spacetime.hpp).
+#include <algorithm>
+#include <array>
 #include <cmath>
+#include <map>
 
 #include "mesh.hpp"
 #include "spacetime.hpp"
@@ -123,6 +126,98 @@ std::vector<double> time_prolongation(int rc, int rf) {
   for (int i = 0; i <= rf; ++i)
     for (int j = 0; j <= rc; ++j) P[(size_t)i * (rc + 1) + j] = lagrange(tc, j, tf[i]);
   return P;
+}
+
+std::vector<StLevelSpec> stmg_sequence(int k, int r, int n_forests) {
+  std::vector<StLevelSpec> seq;
+  StLevelSpec s;
+  s.k = k;
+  s.r = r;
+  s.forest = 0;
+  seq.push_back(s);
+  while (seq.back().k > 2) {
+    s = seq.back();
+    s.k = std::max(2, s.k / 2);
+    seq.push_back(s);
+  }
+  while (seq.back().r > 0) {
+    s = seq.back();
+    s.r = s.r / 2;
+    seq.push_back(s);
+  }
+  for (int i = 1; i < n_forests; ++i) {
+    s = seq.back();
+    s.forest = i;
+    seq.push_back(s);
+  }
+  return seq;
+}
+
+std::vector<std::vector<int32_t>> vertex_star_patches(const Forest& f, const NodeSpace& nu, const NodeSpace& np) {
+  const int dim = f.dim;
+  const size_t nc = f.n_cells();
+  const int L = f.max_level();
+  const int64_t n_main = nu.n_nodes * dim;
+  // holding cells of every node (compressed rows), one table per field
+  auto holders = [&](const NodeSpace& ns, std::vector<int64_t>& ptr, std::vector<int32_t>& idx) {
+    ptr.assign(ns.n_nodes + 1, 0);
+    for (size_t c = 0; c < nc; ++c)
+      for (int b = 0; b < ns.nb; ++b) ptr[ns.cell_nodes[c * ns.nb + b] + 1]++;
+    for (int64_t g = 0; g < ns.n_nodes; ++g) ptr[g + 1] += ptr[g];
+    idx.assign(ptr[ns.n_nodes], 0);
+    std::vector<int64_t> fill(ptr.begin(), ptr.end() - 1);
+    for (size_t c = 0; c < nc; ++c)
+      for (int b = 0; b < ns.nb; ++b) idx[fill[ns.cell_nodes[c * ns.nb + b]]++] = (int32_t)c;
+  };
+  std::vector<int64_t> pu, pp;
+  std::vector<int32_t> iu, ip;
+  holders(nu, pu, iu);
+  holders(np, pp, ip);
+  std::vector<char> hang_u(nu.n_nodes, 0), hang_p(np.n_nodes, 0);
+  for (int32_t g : nu.hang_node) hang_u[g] = 1;
+  for (int32_t g : np.hang_node) hang_p[g] = 1;
+  // stars: corner position (finest-lattice units) -> cells
+  std::map<std::array<int64_t, 3>, std::vector<int32_t>> stars;
+  for (size_t c = 0; c < nc; ++c) {
+    const int64_t s = int64_t(1) << (L - f.lev[c]);
+    for (int a = 0; a < (1 << dim); ++a) {
+      std::array<int64_t, 3> key = {0, 0, 0};
+      for (int d = 0; d < dim; ++d) key[d] = (f.crd[3 * c + d] + ((a >> d) & 1)) * s;
+      stars[key].push_back((int32_t)c);
+    }
+  }
+  std::vector<std::vector<int32_t>> out;
+  std::vector<char> in_star(nc, 0);
+  for (auto& kv : stars) {
+    const std::vector<int32_t>& cells = kv.second;
+    for (int32_t c : cells) in_star[c] = 1;
+    std::vector<int32_t> patch;
+    auto inside = [&](const std::vector<int64_t>& ptr, const std::vector<int32_t>& idx, int32_t g) {
+      for (int64_t j = ptr[g]; j < ptr[g + 1]; ++j)
+        if (!in_star[idx[j]]) return false;
+      return true;
+    };
+    std::vector<int32_t> nodes_u, nodes_p;
+    for (int32_t c : cells) {
+      for (int b = 0; b < nu.nb; ++b) nodes_u.push_back(nu.cell_nodes[(size_t)c * nu.nb + b]);
+      for (int b = 0; b < np.nb; ++b) nodes_p.push_back(np.cell_nodes[(size_t)c * np.nb + b]);
+    }
+    std::sort(nodes_u.begin(), nodes_u.end());
+    nodes_u.erase(std::unique(nodes_u.begin(), nodes_u.end()), nodes_u.end());
+    std::sort(nodes_p.begin(), nodes_p.end());
+    nodes_p.erase(std::unique(nodes_p.begin(), nodes_p.end()), nodes_p.end());
+    for (int32_t g : nodes_u)
+      if (!nu.boundary[g] && !hang_u[g] && inside(pu, iu, g))
+        for (int c = 0; c < dim; ++c) patch.push_back((int32_t)(g * dim + c));
+    for (int32_t g : nodes_p)
+      if (!hang_p[g] && inside(pp, ip, g)) patch.push_back((int32_t)(n_main + g));
+    for (int32_t c : cells) in_star[c] = 0;
+    if (!patch.empty()) {
+      std::sort(patch.begin(), patch.end());
+      out.push_back(std::move(patch));
+    }
+  }
+  return out;
 }
 
 }  // namespace mfns

@@ -1,0 +1,135 @@
+"""Host set-up of the space-time multigrid (csrc/spacetime_host.cpp, compiled with g++) against the
+oracle (Section 4): the level sequence (spatial degree, then temporal degree, then h) and the vertex
+stars of the Schwarz smoother on Taylor--Hood spaces -- every patch, as a set of free entries
+identified by support point and field, equals one of the oracle's, on uniform meshes and on
+ball-refined meshes with hanging nodes, 2D and 3D."""
+import os
+import shutil
+import subprocess
+
+import numpy as np
+import pytest
+
+from oracle import assemble, mesh, solvers, spacetime
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+CSRC = os.path.join(ROOT, "paper_2603_29621_gb300", "csrc")
+CENTRE = (0.3, 0.35, 0.4)
+
+HARNESS = r"""
+#include <cstdio>
+#include <string>
+#include "spacetime.hpp"
+using namespace mfns;
+int main() {
+  int dim, n, nc, k, r, nf;
+  if (std::scanf("%d %d %d %d %d %d", &dim, &n, &nc, &k, &r, &nf) != 6) return 1;
+  Forest f;
+  f.dim = dim;
+  f.n = n;
+  for (int c = 0; c < nc; ++c) {
+    int l, x, y, z;
+    if (std::scanf("%d %d %d %d", &l, &x, &y, &z) != 4) return 1;
+    f.lev.push_back(l);
+    f.crd.push_back(x); f.crd.push_back(y); f.crd.push_back(z);
+  }
+  for (auto& s : stmg_sequence(k, r, nf)) std::printf("%d %d %d;", s.k, s.r, s.forest);
+  std::printf("\n");
+  Lattice lat = make_lattice(f);
+  std::vector<uint32_t> masks = constraint_masks(f, lat);
+  std::string err;
+  NodeSpace nu = make_nodes(f, lat, masks, k, &err);
+  NodeSpace np = make_nodes(f, lat, masks, k - 1, &err);
+  if (!err.empty()) { std::printf("FAIL %s\n", err.c_str()); return 0; }
+  std::printf("%lld %lld\n", (long long)nu.n_nodes, (long long)np.n_nodes);
+  for (double v : nu.x) std::printf("%.17g ", v);
+  std::printf("\n");
+  for (double v : np.x) std::printf("%.17g ", v);
+  std::printf("\n");
+  auto patches = vertex_star_patches(f, nu, np);
+  std::printf("%zu\n", patches.size());
+  for (auto& p : patches) {
+    for (int32_t i : p) std::printf("%d ", i);
+    std::printf("\n");
+  }
+  return 0;
+}
+"""
+
+
+@pytest.fixture(scope="module")
+def harness(tmp_path_factory):
+    if shutil.which("g++") is None:
+        pytest.skip("g++ not available")
+    d = tmp_path_factory.mktemp("stmghost")
+    src = d / "h.cpp"
+    src.write_text(HARNESS)
+    exe = d / "h"
+    subprocess.run(["g++", "-O1", "-std=c++17", "-I", CSRC, str(src), os.path.join(CSRC, "mesh.cpp"),
+                    os.path.join(CSRC, "spacetime_host.cpp"), "-o", str(exe)], check=True)
+
+    def run(forest, k, r, nf):
+        rows = [f"{c[0]} {c[1]} {c[2]} {c[3] if forest.dim == 3 else 0}" for c in forest.cells]
+        inp = f"{forest.dim} {forest.n} {len(rows)} {k} {r} {nf}\n" + "\n".join(rows) + "\n"
+        out = subprocess.run([str(exe)], input=inp, capture_output=True, text=True, check=True).stdout.split("\n")
+        seq = [tuple(int(v) for v in t.split()) for t in out[0].split(";") if t.strip()]
+        assert not out[1].startswith("FAIL"), out[1]
+        nnu, nnp = (int(v) for v in out[1].split())
+        dim = forest.dim
+        xu = np.array([float(v) for v in out[2].split()]).reshape(nnu, dim)
+        xp = np.array([float(v) for v in out[3].split()]).reshape(nnp, dim)
+        npatch = int(out[4])
+        patches = [[int(v) for v in out[5 + i].split()] for i in range(npatch)]
+        return seq, xu, xp, patches
+    return run
+
+
+def _forest(dim, n, ball):
+    f = mesh.uniform(dim, n)
+    return mesh.refine_ball(f, CENTRE, 0.3, 1) if ball else f
+
+
+@pytest.mark.parametrize("k,r", [(2, 0), (2, 3), (4, 1), (3, 2), (4, 3)])
+def test_level_sequence_matches_the_oracle(harness, k, r):
+    f = mesh.uniform(2, 8)
+    nf = len(solvers.coarse_forests(f, 2))
+    seq = harness(f, k, r, nf)[0]
+    lv = spacetime.stmg_levels(f, k, r, tau=0.1, pressure="continuous") if k <= 3 and r <= 2 else None
+    exp = []
+    kk, rr = k, r
+    exp.append((kk, rr, 0))
+    while kk > 2:
+        kk = max(2, kk // 2)
+        exp.append((kk, rr, 0))
+    while rr > 0:
+        rr //= 2
+        exp.append((kk, rr, 0))
+    for i in range(1, nf):
+        exp.append((kk, rr, i))
+    assert seq == exp
+    if lv is not None:
+        assert [(l.k, l.r) for l in lv] == [(a, b) for a, b, _ in seq]
+
+
+@pytest.mark.parametrize("dim,n,ball,k", [(2, 4, False, 2), (2, 3, True, 2), (2, 3, False, 3), (3, 2, False, 2),
+                                          (3, 2, True, 2)])
+def test_vertex_star_patches_match_the_oracle(harness, dim, n, ball, k):
+    f = _forest(dim, n, ball)
+    _, xu, xp, patches = harness(f, k, 0, 1)
+    prob = assemble.Problem(f, "stokes", k)
+    xo, fo = prob.dofs.support_points()
+    key = {(tuple(np.rint(x * 2 ** 30).astype(np.int64)), int(c)): i for i, (x, c) in enumerate(zip(xo, fo))}
+    n_main = len(xu) * dim
+
+    def oracle_index(i):
+        if i < n_main:
+            g, c = divmod(i, dim)
+            return key[(tuple(np.rint(xu[g] * 2 ** 30).astype(np.int64)), c)]
+        return key[(tuple(np.rint(xp[i - n_main] * 2 ** 30).astype(np.int64)), dim)]
+
+    mine = {frozenset(oracle_index(i) for i in p) for p in patches}
+    ref_list = spacetime._patch_dofs(prob, "vertex")
+    ref = {frozenset(p.tolist()) for p in ref_list}
+    assert mine == ref
+    # the same multiplicities (they set the Schwarz weights): no patch repeated on either side
+    assert len(patches) == len(mine) and len(ref_list) == len(ref)
