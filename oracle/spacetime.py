@@ -280,7 +280,10 @@ class STMG:
 
     def __init__(self, levels, nu_s=4, omega=0.7):
         self.levels, self.nu_s, self.omega = levels, nu_s, omega
-        self.coarse = np.linalg.pinv(levels[-1].K.toarray())
+        # pseudo-inverse with an explicit cutoff: the null singular values (one constant pressure per
+        # stage) come out of the SVD at 1e-19..1e-15 relative, above numpy's default cutoff in some
+        # builds, while the smallest non-null ones sit near 1e-5 relative
+        self.coarse = np.linalg.pinv(levels[-1].K.toarray(), rcond=1e-10)
 
     def __call__(self, b, l=0):
         lv = self.levels[l]
