@@ -366,6 +366,32 @@ int mfns_spacetime_info(const mfns_spacetime* st, int* stages, int64_t* n_stage,
 /* y = K x (device vectors of length Q * n in `precision`; x and y must not overlap). */
 int mfns_spacetime_vmult(mfns_spacetime* st, int precision, const void* x, void* y, void* stream);
 int mfns_spacetime_destroy(mfns_spacetime* st);
+/* Space-time multigrid for the slab (Section 4), FP64, uniform meshes (MFNS_ERR_UNSUPPORTED
+ * otherwise).  Levels, finest first: the spatial degree halved while above 2, then the temporal
+ * degree halved down to DG(0), then global coarsening in space down to 2 cells per direction; no
+ * coarsening of tau.  Transfers: P_tau (x) I for a temporal step (the coarse temporal polynomial
+ * at the fine nodes), I_Q (x) P_h for a spatial one (Eq. 4 for velocity and pressure); restriction
+ * is the transpose.  Smoother: nu_s steps x += omega S (b - K x) before and after the coarse
+ * correction, S the additive Schwarz method over vertex stars (for every mesh vertex, the free
+ * entries all of whose cells contain it, all stages together, each block solved exactly), each
+ * entry weighted by the inverse number of patches holding it, constrained rows solved exactly;
+ * the coarsest level is solved directly (pseudo-inverse: the constant pressure of every stage is
+ * a null direction).  The set-up probes the spatial operators on the device, inverts the patch
+ * blocks on the host and synchronises `stream`. */
+int mfns_spacetime_mg_build(mfns_spacetime* st, int nu_s, double omega, void* stream);
+/* Number of levels; for 0 <= level < *n_levels also its spatial degree, temporal degree and
+ * spatial vector length (level -1: the count only).  ARG if the multigrid is not built. */
+int mfns_spacetime_mg_level(const mfns_spacetime* st, int level, int* n_levels, int* k, int* r, int64_t* n_stage);
+/* Support point and field of every spatial entry of a level (host arrays of n_stage entries;
+ * xyz 3 per entry, z = 0 in 2D; field < dim velocity, dim pressure). */
+int mfns_spacetime_mg_support_points(const mfns_spacetime* st, int level, double* xyz_host, int* field_host);
+/* One piece of the cycle on device FP64 vectors (stage-major): what = 0: out = K_l in; 1: out =
+ * S_l in (Schwarz; not on the coarsest level); 2: out += P_l in (in on level l+1, out on level l);
+ * 3: out = P_l^T in (in on level l, out on level l+1).  in and out must not overlap. */
+int mfns_spacetime_mg_apply(mfns_spacetime* st, int level, int what, const void* in, void* out, void* stream);
+/* x = one V-cycle of the space-time multigrid applied to b (zero initial guess; FP64, length
+ * Q * n of the finest level). */
+int mfns_spacetime_vcycle(mfns_spacetime* st, const void* b, void* x, void* stream);
 /* The DG(r) reference-slab matrices on the host, no device needed (any pointer may be NULL):
  * nodes (Q), m_Q (Q, m_Q[j] = phi_j(0)), M_Q, A_Q and G_Q (Q x Q, row-major [j][i]).  Error: ARG
  * for r outside 0..7. */

@@ -312,6 +312,35 @@ class SpaceTime:
         L.check(self.lib.mfns_spacetime_vmult(self.h, prec, _ptr(src), _ptr(dst), _stream(stream)))
         return dst
 
+    # -- space-time multigrid (FP64) ------------------------------------------------------------
+    def mg_build(self, nu_s=4, omega=0.7, stream=None):
+        L.check(self.lib.mfns_spacetime_mg_build(self.h, nu_s, omega, _stream(stream)))
+        nl = C.c_int()
+        L.check(self.lib.mfns_spacetime_mg_level(self.h, -1, C.byref(nl), None, None, None))
+        self.mg_levels = []
+        for l in range(nl.value):
+            k, r, n = C.c_int(), C.c_int(), C.c_int64()
+            L.check(self.lib.mfns_spacetime_mg_level(self.h, l, None, C.byref(k), C.byref(r), C.byref(n)))
+            self.mg_levels.append((k.value, r.value, n.value))
+        return self.mg_levels
+
+    def mg_support_points(self, level):
+        n = self.mg_levels[level][2]
+        xyz = np.zeros((n, 3))
+        fld = np.zeros(n, dtype=np.int32)
+        L.check(self.lib.mfns_spacetime_mg_support_points(self.h, level, xyz.ctypes.data_as(C.c_void_p),
+                                                          fld.ctypes.data_as(C.c_void_p)))
+        return xyz, fld
+
+    def mg_apply(self, level, what, src, dst, stream=None):
+        """what: 0 operator, 1 Schwarz smoother, 2 prolongate-add (src coarse), 3 restrict (dst coarse)."""
+        L.check(self.lib.mfns_spacetime_mg_apply(self.h, level, what, _ptr(src), _ptr(dst), _stream(stream)))
+        return dst
+
+    def vcycle(self, b, x, stream=None):
+        L.check(self.lib.mfns_spacetime_vcycle(self.h, _ptr(b), _ptr(x), _stream(stream)))
+        return x
+
     def close(self):
         if self.h:
             self.lib.mfns_spacetime_destroy(self.h)

@@ -34,7 +34,127 @@ __global__ void k_stage_mix(T* __restrict__ y, const T* __restrict__ mx, StageMa
   }
 }
 
+
+// fine[q n + i] += sum_j P[q][j] coarse[j n + i]  (P: Qf x Qc)
+__global__ void k_time_prolong_add(double* __restrict__ fine, const double* __restrict__ coarse, StageMatrix P,
+                                   int Qf, int Qc, int64_t n) {
+  const int64_t total = (int64_t)Qf * n;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int q = (int)(idx / n);
+    const int64_t i = idx - (int64_t)q * n;
+    double v = fine[idx];
+    for (int j = 0; j < Qc; ++j) v += P.g[q][j] * coarse[(int64_t)j * n + i];
+    fine[idx] = v;
+  }
+}
+
+// coarse[j n + i] = sum_q P[q][j] fine[q n + i]
+__global__ void k_time_restrict(double* __restrict__ coarse, const double* __restrict__ fine, StageMatrix P, int Qf,
+                                int Qc, int64_t n) {
+  const int64_t total = (int64_t)Qc * n;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int j = (int)(idx / n);
+    const int64_t i = idx - (int64_t)j * n;
+    double v = 0.0;
+    for (int q = 0; q < Qf; ++q) v += P.g[q][j] * fine[(int64_t)q * n + i];
+    coarse[idx] = v;
+  }
+}
+
+// Patch solves of the Schwarz smoother, one block per patch: the patch's entries of all stages
+// (stage-major, Q m values) gathered into shared memory, times the patch's inverse (row-major),
+// written to the patch's slice of zloc (offset Q * p_ptr[p]).
+__global__ void k_patch_solve(const double* __restrict__ r, double* __restrict__ zloc, const int64_t* __restrict__ p_ptr,
+                              const int32_t* __restrict__ p_idx, const int64_t* __restrict__ k_ptr,
+                              const double* __restrict__ kinv, int Q, int64_t n) {
+  extern __shared__ double rl[];
+  const int64_t p = blockIdx.x;
+  const int64_t b0 = p_ptr[p];
+  const int m = (int)(p_ptr[p + 1] - b0);
+  const int mq = Q * m;
+  for (int t = threadIdx.x; t < mq; t += blockDim.x) {
+    const int q = t / m, a = t - q * m;
+    rl[t] = r[(int64_t)q * n + p_idx[b0 + a]];
+  }
+  __syncthreads();
+  const double* Kp = kinv + k_ptr[p];
+  double* out = zloc + (int64_t)Q * b0;
+  for (int row = threadIdx.x; row < mq; row += blockDim.x) {
+    const double* kr = Kp + (int64_t)row * mq;
+    double v = 0.0;
+    for (int j = 0; j < mq; ++j) v += kr[j] * rl[j];
+    out[row] = v;
+  }
+}
+
+// z[q n + i] = w[i] sum over the patches holding i of their result for (q, i), in a fixed order
+// (occurrence o: zloc index e_base[o] + q * e_np[o]).
+__global__ void k_patch_gather(double* __restrict__ z, const double* __restrict__ zloc, const int64_t* __restrict__ e_ptr,
+                               const int64_t* __restrict__ e_base, const int32_t* __restrict__ e_np,
+                               const double* __restrict__ w, int Q, int64_t n) {
+  const int64_t total = (int64_t)Q * n;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int q = (int)(idx / n);
+    const int64_t i = idx - (int64_t)q * n;
+    double v = 0.0;
+    for (int64_t o = e_ptr[i]; o < e_ptr[i + 1]; ++o) v += zloc[e_base[o] + (int64_t)q * e_np[o]];
+    z[idx] = w[i] * v;
+  }
+}
+
+// constrained rows of the slab operator are tau times identity rows: z = r / tau there
+__global__ void k_constrained_scale(double* __restrict__ z, const double* __restrict__ r, const int32_t* __restrict__ con,
+                                    int64_t ncon, int Q, int64_t n, double inv_tau) {
+  const int64_t total = (int64_t)Q * ncon;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+    const int q = (int)(t / ncon);
+    const int64_t i = (int64_t)q * n + con[t - (int64_t)q * ncon];
+    z[i] = r[i] * inv_tau;
+  }
+}
+
+unsigned stream_grid(int64_t total) {
+  return (unsigned)std::max<int64_t>(1, std::min<int64_t>((total + 255) / 256, 152 * 16));
+}
+
 }  // namespace
+
+namespace mfns {
+
+// One level of the space-time multigrid (finest first).
+struct StmgLevel {
+  int k = 2, r = 0, Q = 1;
+  std::unique_ptr<OpLevel> A, M, P;  // Taylor--Hood system, velocity mass, pressure space (transfers)
+  TemporalMatrices T;
+  int64_t n = 0;
+  // transfer to the next coarser level: 0 none (coarsest), 1 temporal, 2 spatial
+  int tkind = 0;
+  StageMatrix Pt{};  // temporal: Q x Qc
+  int Qc = 1;
+  std::unique_ptr<Transfer> tv, tp;  // spatial: velocity, pressure
+  // Schwarz smoother
+  int64_t n_patch = 0, max_patch = 0;
+  DevBuf p_ptr, p_idx, k_ptr, kinv, e_ptr, e_base, e_np, w, con;
+  int64_t n_con = 0;
+  // FP64 work vectors of Q n entries, and the patch results
+  DevBuf vx, vb, vr, vt, vz, vmx, zloc;
+};
+
+struct Stmg {
+  std::vector<std::unique_ptr<StmgLevel>> lv;
+  int nu_s = 4;
+  double omega = 0.7, tau = 0.1;
+  DevBuf cinv;      // coarsest: inverse of K + sum_q E_q E_q^T, (Q n)^2
+  int64_t cn = 0;   // Q n of the coarsest level
+  DevBuf pres;      // coarsest: free pressure entries (spatial)
+  int64_t n_pres = 0;
+  DevBuf part, scal;
+};
+
+}  // namespace mfns
 
 struct mfns_spacetime {
   mfns_problem* problem = nullptr;  // not owned; outlives the slab
@@ -44,38 +164,334 @@ struct mfns_spacetime {
   std::unique_ptr<mfns::OpLevel> mass;  // velocity mass on the problem's velocity nodes
   mfns::DevBuf mx[2];                   // Q x n: M applied to every stage (FP64, FP32)
   int64_t n = 0;                        // spatial vector length (the Stokes system's)
+  std::unique_ptr<mfns::Stmg> mg;       // space-time multigrid (built on request)
 };
 
 namespace mfns {
 
-static void st_vmult(mfns_spacetime& st, int prec, const void* x, void* y, cudaStream_t s) {
-  OpLevel& A = *st.problem->p->system;
-  const int64_t n = st.n;
+// y = (G (x) M + tau I (x) A) x on Q stages of length n; mx: Q * n scratch of the precision.
+static void slab_vmult(const OpLevel& A, const OpLevel& M, const std::vector<double>& Gq, int Q, double tau,
+                       int64_t n, void* mx, int prec, const void* x, void* y, cudaStream_t s) {
   const size_t es = esize(prec);
-  // tau A on every stage (identity rows on constrained entries)
-  oplevel_vmult_cols(A, prec, x, y, st.Q, s);
+  // A on every stage (identity rows on constrained entries)
+  oplevel_vmult_cols(A, prec, x, y, Q, s);
   // M on every stage: the velocity block of each stage (its first n_main entries); pressure rows
   // and constrained velocity rows of M are zero
-  void* mx = st.mx[prec].get();
-  MFNS_CUDA(cudaMemsetAsync(mx, 0, (size_t)st.Q * n * es, s));
-  op_apply_cols(st.mass->L, prec, x, mx, st.Q, n, s);
-  const int64_t nc = (int64_t)st.mass->constrained_host.size();
-  for (int q = 0; q < st.Q; ++q) {
+  MFNS_CUDA(cudaMemsetAsync(mx, 0, (size_t)Q * n * es, s));
+  op_apply_cols(M.L, prec, x, mx, Q, n, s);
+  const int64_t nc = (int64_t)M.constrained_host.size();
+  for (int q = 0; q < Q; ++q) {
     if (prec == 0)
-      vset_idx<double>((double*)mx + (int64_t)q * n, 0.0, st.mass->constrained.as<int32_t>(), nc, s);
+      vset_idx<double>((double*)mx + (int64_t)q * n, 0.0, M.constrained.as<int32_t>(), nc, s);
     else
-      vset_idx<float>((float*)mx + (int64_t)q * n, 0.0f, st.mass->constrained.as<int32_t>(), nc, s);
+      vset_idx<float>((float*)mx + (int64_t)q * n, 0.0f, M.constrained.as<int32_t>(), nc, s);
   }
   StageMatrix G{};
-  for (int q = 0; q < st.Q; ++q)
-    for (int j = 0; j < st.Q; ++j) G.g[q][j] = st.T.G[q * st.Q + j];
-  const int64_t total = (int64_t)st.Q * n;
+  for (int q = 0; q < Q; ++q)
+    for (int j = 0; j < Q; ++j) G.g[q][j] = Gq[q * Q + j];
+  const int64_t total = (int64_t)Q * n;
   const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>((total + 255) / 256, 152 * 16));
   if (prec == 0)
-    k_stage_mix<double><<<grid, 256, 0, s>>>((double*)y, (const double*)mx, G, st.Q, n, st.tau);
+    k_stage_mix<double><<<grid, 256, 0, s>>>((double*)y, (const double*)mx, G, Q, n, tau);
   else
-    k_stage_mix<float><<<grid, 256, 0, s>>>((float*)y, (const float*)mx, G, st.Q, n, (float)st.tau);
+    k_stage_mix<float><<<grid, 256, 0, s>>>((float*)y, (const float*)mx, G, Q, n, (float)tau);
   MFNS_CUDA(cudaGetLastError());
+}
+
+static void st_vmult(mfns_spacetime& st, int prec, const void* x, void* y, cudaStream_t s) {
+  slab_vmult(*st.problem->p->system, *st.mass, st.T.G, st.Q, st.tau, st.n, st.mx[prec].get(), prec, x, y, s);
+}
+
+// ---------------------------------------------------------------- space-time multigrid (FP64)
+static void level_vmult(Stmg& mg, StmgLevel& L, const double* x, double* y, cudaStream_t s) {
+  slab_vmult(*L.A, *L.M, L.T.G, L.Q, mg.tau, L.n, L.vmx.get(), 0, x, y, s);
+}
+
+// Schwarz patches of level L: spatial blocks of A and M by probing, the space-time block
+// G (x) M_pp + tau I (x) A_pp of every patch inverted on the host.
+static void build_schwarz(Stmg& mg, StmgLevel& L, Budget* bud, cudaStream_t s) {
+  const OpLevel& A = *L.A;
+  const int64_t n = L.n;
+  const int Q = L.Q;
+  const std::vector<std::vector<int32_t>> patches = vertex_star_patches(A.forest, A.nu, A.np);
+  std::vector<int32_t> colour;
+  const int ncol = colour_patches_for_probing(A.forest, A.nu, A.np, patches, colour);
+  std::vector<std::vector<int32_t>> members(ncol);
+  for (size_t p = 0; p < patches.size(); ++p) members[colour[p]].push_back((int32_t)p);
+  std::vector<std::pair<int, int>> cols;  // (colour, local index)
+  for (int c = 0; c < ncol; ++c) {
+    size_t len = 0;
+    for (int32_t p : members[c]) len = std::max(len, patches[p].size());
+    for (size_t m = 0; m < len; ++m) cols.push_back({c, (int)m});
+  }
+  std::vector<std::vector<double>> App(patches.size()), Mpp(patches.size());
+  for (size_t p = 0; p < patches.size(); ++p) {
+    App[p].assign(patches[p].size() * patches[p].size(), 0.0);
+    Mpp[p].assign(patches[p].size() * patches[p].size(), 0.0);
+  }
+  const int B = 32;
+  DevBuf X, YA, YM;
+  X.alloc(bud, (size_t)n * B * 8);
+  YA.alloc(bud, (size_t)n * B * 8);
+  YM.alloc(bud, (size_t)n * B * 8);
+  std::vector<double> Xh((size_t)n * B), Ya((size_t)n * B), Ym((size_t)n * B);
+  for (size_t c0 = 0; c0 < cols.size(); c0 += B) {
+    const int nb = (int)std::min<size_t>(B, cols.size() - c0);
+    std::fill(Xh.begin(), Xh.begin() + (size_t)n * nb, 0.0);
+    for (int j = 0; j < nb; ++j) {
+      const int c = cols[c0 + j].first, m = cols[c0 + j].second;
+      for (int32_t p : members[c])
+        if ((size_t)m < patches[p].size()) Xh[(size_t)j * n + patches[p][m]] = 1.0;
+    }
+    MFNS_CUDA(cudaMemcpyAsync(X.get(), Xh.data(), (size_t)n * nb * 8, cudaMemcpyHostToDevice, s));
+    oplevel_vmult_cols(A, 0, X.get(), YA.get(), nb, s);
+    MFNS_CUDA(cudaMemsetAsync(YM.get(), 0, (size_t)n * nb * 8, s));
+    op_apply_cols(L.M->L, 0, X.get(), YM.get(), nb, n, s);
+    MFNS_CUDA(cudaMemcpyAsync(Ya.data(), YA.get(), (size_t)n * nb * 8, cudaMemcpyDeviceToHost, s));
+    MFNS_CUDA(cudaMemcpyAsync(Ym.data(), YM.get(), (size_t)n * nb * 8, cudaMemcpyDeviceToHost, s));
+    MFNS_CUDA(cudaStreamSynchronize(s));
+    for (int j = 0; j < nb; ++j) {
+      const int c = cols[c0 + j].first, m = cols[c0 + j].second;
+      for (int32_t p : members[c]) {
+        const size_t np = patches[p].size();
+        if ((size_t)m >= np) continue;
+        for (size_t a = 0; a < np; ++a) {
+          App[p][a * np + m] = Ya[(size_t)j * n + patches[p][a]];
+          Mpp[p][a * np + m] = Ym[(size_t)j * n + patches[p][a]];
+        }
+      }
+    }
+  }
+  // space-time blocks, inverted; flattened tables
+  std::vector<int64_t> p_ptr(1, 0), k_ptr(1, 0);
+  std::vector<int32_t> p_idx;
+  std::vector<double> kinv;
+  int64_t max_patch = 0;
+  for (size_t p = 0; p < patches.size(); ++p) {
+    const int64_t m = (int64_t)patches[p].size(), mq = Q * m;
+    std::vector<double> K((size_t)mq * mq, 0.0);
+    for (int q = 0; q < Q; ++q)
+      for (int j = 0; j < Q; ++j) {
+        const double g = L.T.G[q * Q + j];
+        for (int64_t a = 0; a < m; ++a)
+          for (int64_t b = 0; b < m; ++b) {
+            double v = g * Mpp[p][a * m + b];
+            if (q == j) v += mg.tau * App[p][a * m + b];
+            K[(size_t)(q * m + a) * mq + (j * m + b)] = v;
+          }
+      }
+    if (!invert_dense_rel(K, mq, 1e-14)) throw Error(kErrUnsupported, "space-time multigrid: singular Schwarz patch");
+    p_idx.insert(p_idx.end(), patches[p].begin(), patches[p].end());
+    p_ptr.push_back((int64_t)p_idx.size());
+    kinv.insert(kinv.end(), K.begin(), K.end());
+    k_ptr.push_back((int64_t)kinv.size());
+    max_patch = std::max(max_patch, m);
+  }
+  if ((size_t)Q * max_patch * 8 > 48 * 1024) throw Error(kErrUnsupported, "space-time multigrid: patch too large");
+  // occurrences of every spatial entry (patch results to add) and the weights 1 / multiplicity
+  std::vector<int64_t> cnt(n + 1, 0);
+  for (auto& pt : patches)
+    for (int32_t i : pt) cnt[i + 1]++;
+  for (int64_t i = 0; i < n; ++i) cnt[i + 1] += cnt[i];
+  std::vector<int64_t> e_base(cnt[n]);
+  std::vector<int32_t> e_np(cnt[n]);
+  {
+    std::vector<int64_t> fill(cnt.begin(), cnt.end() - 1);
+    for (size_t p = 0; p < patches.size(); ++p)
+      for (size_t a = 0; a < patches[p].size(); ++a) {
+        const int32_t i = patches[p][a];
+        e_base[fill[i]] = (int64_t)Q * p_ptr[p] + (int64_t)a;
+        e_np[fill[i]] = (int32_t)patches[p].size();
+        fill[i]++;
+      }
+  }
+  std::vector<double> w(n, 0.0);
+  for (int64_t i = 0; i < n; ++i)
+    if (cnt[i + 1] > cnt[i]) w[i] = 1.0 / double(cnt[i + 1] - cnt[i]);
+  L.n_patch = (int64_t)patches.size();
+  L.max_patch = max_patch;
+  L.p_ptr = upload(bud, p_ptr);
+  L.p_idx = upload(bud, p_idx);
+  L.k_ptr = upload(bud, k_ptr);
+  L.kinv = upload(bud, kinv);
+  L.e_ptr = upload(bud, cnt);
+  L.e_base = upload(bud, e_base);
+  L.e_np = upload(bud, e_np);
+  L.w = upload(bud, w);
+  L.con = upload(bud, A.constrained_host);
+  L.n_con = (int64_t)A.constrained_host.size();
+  L.zloc.alloc(bud, (size_t)std::max<int64_t>(1, (int64_t)Q * p_ptr.back()) * 8);
+}
+
+// z = S r on level L (weighted additive Schwarz; constrained rows solved exactly)
+static void schwarz(Stmg& mg, StmgLevel& L, const double* r, double* z, cudaStream_t s) {
+  const int64_t total = (int64_t)L.Q * L.n;
+  if (L.n_patch > 0)
+    k_patch_solve<<<(unsigned)L.n_patch, 128, (size_t)L.Q * L.max_patch * 8, s>>>(
+        r, L.zloc.as<double>(), L.p_ptr.as<int64_t>(), L.p_idx.as<int32_t>(), L.k_ptr.as<int64_t>(),
+        L.kinv.as<double>(), L.Q, L.n);
+  k_patch_gather<<<stream_grid(total), 256, 0, s>>>(z, L.zloc.as<double>(), L.e_ptr.as<int64_t>(),
+                                                     L.e_base.as<int64_t>(), L.e_np.as<int32_t>(), L.w.as<double>(),
+                                                     L.Q, L.n);
+  if (L.n_con > 0)
+    k_constrained_scale<<<stream_grid((int64_t)L.Q * L.n_con), 256, 0, s>>>(z, r, L.con.as<int32_t>(), L.n_con, L.Q,
+                                                                              L.n, 1.0 / mg.tau);
+  MFNS_CUDA(cudaGetLastError());
+}
+
+static void level_prolongate_add(StmgLevel& F, StmgLevel& C, const double* xc, double* xf, cudaStream_t s) {
+  if (F.tkind == 1) {
+    k_time_prolong_add<<<stream_grid((int64_t)F.Q * F.n), 256, 0, s>>>(xf, xc, F.Pt, F.Q, F.Qc, F.n);
+    MFNS_CUDA(cudaGetLastError());
+    return;
+  }
+  for (int q = 0; q < F.Q; ++q) {
+    const double* c = xc + (int64_t)q * C.n;
+    double* f = xf + (int64_t)q * F.n;
+    transfer_prolongate_add(*F.tv, *F.A, *C.A, 0, c, f, s);
+    transfer_prolongate_add(*F.tp, *F.P, *C.P, 0, c + C.A->n_main_dofs, f + F.A->n_main_dofs, s);
+  }
+}
+
+static void level_restrict(StmgLevel& F, StmgLevel& C, const double* rf, double* rc, cudaStream_t s) {
+  if (F.tkind == 1) {
+    k_time_restrict<<<stream_grid((int64_t)F.Qc * F.n), 256, 0, s>>>(rc, rf, F.Pt, F.Q, F.Qc, F.n);
+    MFNS_CUDA(cudaGetLastError());
+    return;
+  }
+  for (int q = 0; q < F.Q; ++q) {
+    const double* f = rf + (int64_t)q * F.n;
+    double* c = rc + (int64_t)q * C.n;
+    // velocity first: it clears the whole coarse vector of the stage; the pressure block follows
+    transfer_restrict(*F.tv, *F.A, *C.A, 0, f, c, s);
+    transfer_restrict(*F.tp, *F.P, *C.P, 0, f + F.A->n_main_dofs, c + C.A->n_main_dofs, s);
+  }
+}
+
+static void coarse_solve(Stmg& mg, StmgLevel& C, cudaStream_t s) {
+  // x = (K + sum_q E_q E_q^T)^{-1} P b, P the projection removing every stage's constant pressure:
+  // the pseudo-inverse solution (K and K^T have the constant pressures as their null space)
+  double* t = C.vt.as<double>();
+  MFNS_CUDA(cudaMemcpyAsync(t, C.vb.get(), (size_t)C.Q * C.n * 8, cudaMemcpyDeviceToDevice, s));
+  for (int q = 0; q < C.Q; ++q) {
+    double* tq = t + (int64_t)q * C.n;
+    sum_idx<double>(mg.scal.as<double>(), tq, mg.pres.as<int32_t>(), mg.n_pres, mg.part.as<double>(), s);
+    sub_mean_idx<double>(tq, mg.pres.as<int32_t>(), mg.n_pres, mg.scal.as<double>(), s);
+  }
+  vgemv<double>(C.vx.as<double>(), mg.cinv.as<double>(), t, mg.cn, s);
+}
+
+static void stmg_smooth(Stmg& mg, StmgLevel& L, cudaStream_t s) {
+  const int64_t total = (int64_t)L.Q * L.n;
+  for (int it = 0; it < mg.nu_s; ++it) {
+    level_vmult(mg, L, L.vx.as<double>(), L.vt.as<double>(), s);
+    vsub<double>(L.vr.as<double>(), L.vb.as<double>(), L.vt.as<double>(), total, s);
+    schwarz(mg, L, L.vr.as<double>(), L.vz.as<double>(), s);
+    vaxpy<double>(L.vx.as<double>(), mg.omega, L.vz.as<double>(), total, s);
+  }
+}
+
+// L.vx = V-cycle(L.vb) from a zero start (Section 4: nu_s damped Schwarz steps before and after the
+// coarse correction, a direct solve on the coarsest level)
+static void stmg_cycle(Stmg& mg, size_t l, cudaStream_t s) {
+  StmgLevel& L = *mg.lv[l];
+  if (l + 1 == mg.lv.size()) return coarse_solve(mg, L, s);
+  StmgLevel& C = *mg.lv[l + 1];
+  const int64_t total = (int64_t)L.Q * L.n;
+  vzero<double>(L.vx.as<double>(), total, s);
+  stmg_smooth(mg, L, s);
+  level_vmult(mg, L, L.vx.as<double>(), L.vt.as<double>(), s);
+  vsub<double>(L.vr.as<double>(), L.vb.as<double>(), L.vt.as<double>(), total, s);
+  level_restrict(L, C, L.vr.as<double>(), C.vb.as<double>(), s);
+  stmg_cycle(mg, l + 1, s);
+  level_prolongate_add(L, C, C.vx.as<double>(), L.vx.as<double>(), s);
+  stmg_smooth(mg, L, s);
+}
+
+static void build_stmg(mfns_spacetime& st, int nu_s, double omega, cudaStream_t s) {
+  Problem& P = *st.problem->p;
+  const OpLevel& A0 = *P.system;
+  if (!A0.forest.uniform()) throw Error(kErrUnsupported, "space-time multigrid: uniform meshes only");
+  if (nu_s < 1 || !(omega > 0.0)) throw Error(kErrArg, "space-time multigrid: nu_s >= 1 and omega > 0");
+  std::vector<Forest> fs{A0.forest};
+  while (forest_can_coarsen(fs.back(), 2)) fs.push_back(forest_coarsen(fs.back()));
+  const std::vector<StLevelSpec> seq = stmg_sequence(A0.k, st.r, (int)fs.size());
+  auto mg = std::make_unique<Stmg>();
+  mg->nu_s = nu_s;
+  mg->omega = omega;
+  mg->tau = st.tau;
+  for (const StLevelSpec& sp : seq) {
+    auto L = std::make_unique<StmgLevel>();
+    L->k = sp.k;
+    L->r = sp.r;
+    L->Q = sp.r + 1;
+    std::string err;
+    if (!temporal_matrices(sp.r, L->T, &err)) throw Error(kErrArg, err);
+    L->A = std::make_unique<OpLevel>();
+    build_oplevel(*L->A, fs[sp.forest], OP_STOKES, sp.k, P.phys, P.bud);
+    L->M = std::make_unique<OpLevel>();
+    build_oplevel(*L->M, fs[sp.forest], OP_VMASS, sp.k, P.phys, P.bud);
+    L->n = L->A->n_dofs;
+    const size_t qn = (size_t)L->Q * L->n * 8;
+    for (DevBuf* v : {&L->vx, &L->vb, &L->vr, &L->vt, &L->vz, &L->vmx}) {
+      v->alloc(P.bud, qn);
+      MFNS_CUDA(cudaMemsetAsync(v->get(), 0, qn, s));
+    }
+    mg->lv.push_back(std::move(L));
+  }
+  for (size_t l = 0; l + 1 < mg->lv.size(); ++l) {
+    StmgLevel& F = *mg->lv[l];
+    StmgLevel& C = *mg->lv[l + 1];
+    if (F.r != C.r) {
+      F.tkind = 1;
+      F.Qc = C.Q;
+      const std::vector<double> Pt = time_prolongation(C.r, F.r);
+      for (int q = 0; q < F.Q; ++q)
+        for (int j = 0; j < C.Q; ++j) F.Pt.g[q][j] = Pt[(size_t)q * C.Q + j];
+    } else {
+      F.tkind = 2;
+      F.tv = std::make_unique<Transfer>();
+      build_transfer(*F.tv, *F.A, *C.A, P.bud);
+      for (StmgLevel* X : {&F, &C})
+        if (!X->P) {
+          X->P = std::make_unique<OpLevel>();
+          build_oplevel(*X->P, X->A->forest, OP_PMASS, X->k - 1, P.phys, P.bud);
+        }
+      F.tp = std::make_unique<Transfer>();
+      build_transfer(*F.tp, *F.P, *C.P, P.bud);
+    }
+    build_schwarz(*mg, F, P.bud, s);
+  }
+  // coarsest level: dense operator by unit vectors, plus the constant pressures of every stage
+  StmgLevel& C = *mg->lv.back();
+  const int64_t N = (int64_t)C.Q * C.n;
+  if (N > 8192) throw Error(kErrUnsupported, "space-time multigrid: coarsest level too large for a dense solve");
+  std::vector<double> K((size_t)N * N), col(N);
+  for (int64_t j = 0; j < N; ++j) {
+    MFNS_CUDA(cudaMemsetAsync(C.vz.get(), 0, (size_t)N * 8, s));
+    const double one = 1.0;
+    MFNS_CUDA(cudaMemcpyAsync(C.vz.as<double>() + j, &one, 8, cudaMemcpyHostToDevice, s));
+    level_vmult(*mg, C, C.vz.as<double>(), C.vt.as<double>(), s);
+    MFNS_CUDA(cudaMemcpyAsync(col.data(), C.vt.get(), (size_t)N * 8, cudaMemcpyDeviceToHost, s));
+    MFNS_CUDA(cudaStreamSynchronize(s));
+    for (int64_t i = 0; i < N; ++i) K[(size_t)i * N + j] = col[i];
+  }
+  const std::vector<int32_t>& pres = C.A->pres_host;
+  if (!pres.empty()) {
+    const double v = 1.0 / double(pres.size());
+    for (int q = 0; q < C.Q; ++q)
+      for (int32_t a : pres)
+        for (int32_t b : pres) K[(size_t)(q * C.n + a) * N + (q * C.n + b)] += v;
+  }
+  if (!invert_dense_rel(K, N, 1e-15)) throw Error(kErrArg, "space-time multigrid: singular coarse matrix");
+  mg->cinv = upload(P.bud, K);
+  mg->cn = N;
+  mg->pres = upload(P.bud, pres);
+  mg->n_pres = (int64_t)pres.size();
+  mg->part.alloc(P.bud, (size_t)kRedBlocks * kMaxDots * 8);
+  mg->scal.alloc(P.bud, 64);
+  MFNS_CUDA(cudaStreamSynchronize(s));
+  st.mg = std::move(mg);
 }
 
 }  // namespace mfns
@@ -155,4 +571,87 @@ extern "C" int mfns_spacetime_temporal(int r, double* nodes_host, double* m_host
   if (aq_host) std::copy(T.A.begin(), T.A.end(), aq_host);
   if (g_host) std::copy(T.G.begin(), T.G.end(), g_host);
   return MFNS_OK;
+}
+
+#define ST_BEGIN \
+  using namespace mfns; \
+  try {                 \
+    (void)cudaGetLastError();
+#define ST_END                                                  \
+  }                                                             \
+  catch (const Error& e) { return capi_fail(e.code, e.what()); } \
+  catch (const std::exception& e) { return capi_fail(kErrArg, e.what()); } \
+  return MFNS_OK;
+
+extern "C" int mfns_spacetime_mg_build(mfns_spacetime* st, int nu_s, double omega, void* stream) {
+  ST_BEGIN
+  if (!st) return capi_fail(kErrArg, "bad arguments");
+  MFNS_CUDA(cudaSetDevice(st->problem->ctx->device));
+  st->mg.reset();
+  build_stmg(*st, nu_s, omega, reinterpret_cast<cudaStream_t>(stream));
+  ST_END
+}
+
+extern "C" int mfns_spacetime_mg_level(const mfns_spacetime* st, int level, int* n_levels, int* k, int* r,
+                                       int64_t* n_stage) {
+  if (!st || !st->mg) return mfns::capi_fail(mfns::kErrArg, "no space-time multigrid (mfns_spacetime_mg_build)");
+  const int nl = (int)st->mg->lv.size();
+  if (n_levels) *n_levels = nl;
+  if (level < 0 || level >= nl) return level == -1 ? MFNS_OK : mfns::capi_fail(mfns::kErrArg, "level out of range");
+  const mfns::StmgLevel& L = *st->mg->lv[level];
+  if (k) *k = L.k;
+  if (r) *r = L.r;
+  if (n_stage) *n_stage = L.n;
+  return MFNS_OK;
+}
+
+extern "C" int mfns_spacetime_mg_support_points(const mfns_spacetime* st, int level, double* xyz_host, int* field_host) {
+  ST_BEGIN
+  if (!st || !st->mg || level < 0 || level >= (int)st->mg->lv.size() || !xyz_host || !field_host)
+    return capi_fail(kErrArg, "bad arguments");
+  oplevel_support(*st->mg->lv[level]->A, xyz_host, field_host);
+  ST_END
+}
+
+extern "C" int mfns_spacetime_mg_apply(mfns_spacetime* st, int level, int what, const void* in, void* out,
+                                       void* stream) {
+  ST_BEGIN
+  if (!st || !st->mg || !in || !out || in == out || level < 0 || level >= (int)st->mg->lv.size())
+    return capi_fail(kErrArg, "bad arguments");
+  Stmg& mg = *st->mg;
+  StmgLevel& L = *mg.lv[level];
+  const bool has_coarse = level + 1 < (int)mg.lv.size();
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  MFNS_CUDA(cudaSetDevice(st->problem->ctx->device));
+  switch (what) {
+    case 0: level_vmult(mg, L, (const double*)in, (double*)out, s); break;
+    case 1:
+      if (!has_coarse) return capi_fail(kErrArg, "the coarsest level has no smoother");
+      schwarz(mg, L, (const double*)in, (double*)out, s);
+      break;
+    case 2:
+      if (!has_coarse) return capi_fail(kErrArg, "the coarsest level has no coarser level");
+      level_prolongate_add(L, *mg.lv[level + 1], (const double*)in, (double*)out, s);
+      break;
+    case 3:
+      if (!has_coarse) return capi_fail(kErrArg, "the coarsest level has no coarser level");
+      level_restrict(L, *mg.lv[level + 1], (const double*)in, (double*)out, s);
+      break;
+    default: return capi_fail(kErrArg, "what: 0 operator, 1 Schwarz, 2 prolongate-add, 3 restrict");
+  }
+  ST_END
+}
+
+extern "C" int mfns_spacetime_vcycle(mfns_spacetime* st, const void* b, void* x, void* stream) {
+  ST_BEGIN
+  if (!st || !st->mg || !b || !x || b == x) return capi_fail(kErrArg, "bad arguments");
+  Stmg& mg = *st->mg;
+  StmgLevel& L = *mg.lv[0];
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  MFNS_CUDA(cudaSetDevice(st->problem->ctx->device));
+  const size_t bytes = (size_t)L.Q * L.n * 8;
+  MFNS_CUDA(cudaMemcpyAsync(L.vb.get(), b, bytes, cudaMemcpyDeviceToDevice, s));
+  stmg_cycle(mg, 0, s);
+  MFNS_CUDA(cudaMemcpyAsync(x, L.vx.get(), bytes, cudaMemcpyDeviceToDevice, s));
+  ST_END
 }

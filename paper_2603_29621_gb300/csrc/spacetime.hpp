@@ -54,4 +54,16 @@ std::vector<StLevelSpec> stmg_sequence(int k, int r, int n_forests);
 // ascending; stars in lattice order; empty patches dropped.
 std::vector<std::vector<int32_t>> vertex_star_patches(const Forest& f, const NodeSpace& nu, const NodeSpace& np);
 
+// Colours of the patches for probing the patch blocks of a spatial operator on that space: two
+// patches of one colour have no entry pair (row of one, column of the other) that any cell couples,
+// a cell coupling the entries of every node it holds and the masters of the hanging nodes it
+// holds.  colour[p] for every patch; returns the number of colours.
+// In-place inverse of a dense n x n matrix (row-major) by Gauss--Jordan elimination with partial
+// pivoting; false when a pivot falls below rel_tol times the largest entry (singular to that
+// tolerance).
+bool invert_dense_rel(std::vector<double>& A, int64_t n, double rel_tol);
+
+int colour_patches_for_probing(const Forest& f, const NodeSpace& nu, const NodeSpace& np,
+                               const std::vector<std::vector<int32_t>>& patches, std::vector<int32_t>& colour);
+
 }  // namespace mfns

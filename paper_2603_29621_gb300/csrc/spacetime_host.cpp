@@ -220,4 +220,103 @@ std::vector<std::vector<int32_t>> vertex_star_patches(const Forest& f, const Nod
   return out;
 }
 
+bool invert_dense_rel(std::vector<double>& A, int64_t n, double rel_tol) {
+  double amax = 0.0;
+  for (double v : A) amax = std::max(amax, std::fabs(v));
+  if (amax == 0.0) return false;
+  std::vector<double> I((size_t)n * n, 0.0);
+  for (int64_t i = 0; i < n; ++i) I[i * n + i] = 1.0;
+  for (int64_t c = 0; c < n; ++c) {
+    int64_t piv = c;
+    for (int64_t r = c + 1; r < n; ++r)
+      if (std::fabs(A[r * n + c]) > std::fabs(A[piv * n + c])) piv = r;
+    if (std::fabs(A[piv * n + c]) <= rel_tol * amax) return false;
+    if (piv != c)
+      for (int64_t j = 0; j < n; ++j) {
+        std::swap(A[c * n + j], A[piv * n + j]);
+        std::swap(I[c * n + j], I[piv * n + j]);
+      }
+    const double inv = 1.0 / A[c * n + c];
+    for (int64_t j = 0; j < n; ++j) {
+      A[c * n + j] *= inv;
+      I[c * n + j] *= inv;
+    }
+    for (int64_t r = 0; r < n; ++r) {
+      if (r == c) continue;
+      const double f = A[r * n + c];
+      if (f == 0.0) continue;
+      for (int64_t j = 0; j < n; ++j) {
+        A[r * n + j] -= f * A[c * n + j];
+        I[r * n + j] -= f * I[c * n + j];
+      }
+    }
+  }
+  A.swap(I);
+  return true;
+}
+
+int colour_patches_for_probing(const Forest& f, const NodeSpace& nu, const NodeSpace& np,
+                               const std::vector<std::vector<int32_t>>& patches, std::vector<int32_t>& colour) {
+  const int dim = f.dim;
+  const size_t nc = f.n_cells();
+  const int64_t n_main = nu.n_nodes * dim;
+  // cells reached by a node of a field: cells holding it, and cells holding a hanging node of
+  // which it is a master (compressed rows)
+  auto reach_table = [&](const NodeSpace& ns, std::vector<int64_t>& ptr, std::vector<int32_t>& idx) {
+    std::vector<std::vector<int32_t>> hang_of(ns.n_nodes);  // master -> hanging nodes
+    for (size_t i = 0; i < ns.hang_node.size(); ++i)
+      for (int32_t j = ns.hang_ptr[i]; j < ns.hang_ptr[i + 1]; ++j) hang_of[ns.hang_master[j]].push_back(ns.hang_node[i]);
+    std::vector<std::vector<int32_t>> held(ns.n_nodes);
+    for (size_t c = 0; c < nc; ++c)
+      for (int b = 0; b < ns.nb; ++b) held[ns.cell_nodes[c * ns.nb + b]].push_back((int32_t)c);
+    ptr.assign(ns.n_nodes + 1, 0);
+    idx.clear();
+    for (int64_t g = 0; g < ns.n_nodes; ++g) {
+      std::vector<int32_t> cs = held[g];
+      for (int32_t h : hang_of[g]) cs.insert(cs.end(), held[h].begin(), held[h].end());
+      std::sort(cs.begin(), cs.end());
+      cs.erase(std::unique(cs.begin(), cs.end()), cs.end());
+      idx.insert(idx.end(), cs.begin(), cs.end());
+      ptr[g + 1] = (int64_t)idx.size();
+    }
+  };
+  std::vector<int64_t> pu, pp;
+  std::vector<int32_t> iu, ip;
+  reach_table(nu, pu, iu);
+  reach_table(np, pp, ip);
+  // cells reached by every patch
+  std::vector<std::vector<int32_t>> reach(patches.size());
+  for (size_t p = 0; p < patches.size(); ++p) {
+    std::vector<int32_t>& R = reach[p];
+    for (int32_t e : patches[p]) {
+      if (e < n_main) {
+        const int32_t g = e / dim;
+        R.insert(R.end(), iu.begin() + pu[g], iu.begin() + pu[g + 1]);
+      } else {
+        const int32_t g = (int32_t)(e - n_main);
+        R.insert(R.end(), ip.begin() + pp[g], ip.begin() + pp[g + 1]);
+      }
+    }
+    std::sort(R.begin(), R.end());
+    R.erase(std::unique(R.begin(), R.end()), R.end());
+  }
+  // greedy: a patch takes the lowest colour not used by a patch reaching one of its cells (two
+  // patches couple an entry pair only through a cell both reach)
+  std::vector<std::vector<int32_t>> cell_colours(nc);
+  colour.assign(patches.size(), -1);
+  int ncol = 0;
+  std::vector<char> used;
+  for (size_t p = 0; p < patches.size(); ++p) {
+    used.assign(ncol + 1, 0);
+    for (int32_t c : reach[p])
+      for (int32_t col : cell_colours[c]) used[col] = 1;
+    int col = 0;
+    while (used[col]) ++col;
+    colour[p] = col;
+    ncol = std::max(ncol, col + 1);
+    for (int32_t c : reach[p]) cell_colours[c].push_back(col);
+  }
+  return ncol;
+}
+
 }  // namespace mfns

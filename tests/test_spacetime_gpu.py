@@ -70,3 +70,72 @@ def test_slab_rejects_other_problems(ctx):
     with pytest.raises(L.MfnsError) as e:
         api.SpaceTime(prob, 1, 0.1)
     assert e.value.code == L.ERR_UNSUPPORTED
+
+
+STMG_CASES = [(2, 8, 2, 1), (2, 4, 3, 2), (3, 4, 2, 1)]
+
+
+@pytest.mark.parametrize("case", STMG_CASES, ids=lambda c: f"{c[0]}d-n{c[1]}-k{c[2]}-r{c[3]}")
+def test_space_time_multigrid_matches_oracle(ctx, case):
+    """Every level's slab operator (1e-12), Schwarz smoother (1e-10) and transfers (1e-12), and one
+    V-cycle (1e-9) of the space-time multigrid against the oracle's (vertex stars, nu_s = 4,
+    omega = 0.7, uniform meshes)."""
+    from paper_2603_29621_gb300 import _lib as L, api
+    dim, n, k, r = case
+    nu, tau = 1.0, 0.05
+    f = mesh.uniform(dim, n)
+    m = api.Mesh(ctx, dim, n)
+    prob = api.Problem(ctx, m, kind=L.STOKES, degree=k, nu=nu, lambda_max=1.0)
+    st = api.SpaceTime(prob, r, tau)
+    levels = st.mg_build(nu_s=4, omega=0.7)
+    lv = spacetime.stmg_levels(f, k, r, nu=nu, tau=tau, pressure="continuous")
+    assert [(a, b) for a, b, _ in levels] == [(l.k, l.r) for l in lv]
+    full = []
+    for l, olv in enumerate(lv):
+        xg, fg = st.mg_support_points(l)
+        xo, fo = olv.st.space.dofs.support_points()
+        perm = inputs.match_dofs(xg[:, :dim], fg, xo, fo)
+        assert levels[l][2] == olv.st.n
+        full.append((np.arange(olv.st.Q)[:, None] * olv.st.n + perm[None, :]).ravel())
+
+    def to_gpu(x, l):
+        xd = np.empty_like(x)
+        xd[full[l]] = x
+        return torch.tensor(xd, device="cuda")
+
+    def from_gpu(t, l):
+        torch.cuda.synchronize()
+        return t.cpu().numpy()[full[l]]
+
+    rng = np.random.default_rng(3)
+    for l, olv in enumerate(lv):
+        N = olv.K.shape[0]
+        x = rng.uniform(-1, 1, N)
+        y = torch.zeros(N, dtype=torch.float64, device="cuda")
+        exp = olv.K @ x
+        assert np.abs(from_gpu(st.mg_apply(l, 0, to_gpu(x, l), y), l) - exp).max() <= 1e-12 * np.abs(exp).max(), l
+        if l == len(lv) - 1:
+            break
+        exp = olv.schwarz(x)
+        got = from_gpu(st.mg_apply(l, 1, to_gpu(x, l), y), l)
+        assert np.abs(got - exp).max() <= 1e-10 * np.abs(exp).max(), l
+        Nc = lv[l + 1].K.shape[0]
+        xc = rng.uniform(-1, 1, Nc)
+        xf0 = rng.uniform(-1, 1, N)
+        fine = to_gpu(xf0, l)
+        st.mg_apply(l, 2, to_gpu(xc, l + 1), fine)
+        exp = xf0 + olv.P @ xc
+        assert np.abs(from_gpu(fine, l) - exp).max() <= 1e-12 * np.abs(exp).max(), l
+        coarse = torch.zeros(Nc, dtype=torch.float64, device="cuda")
+        st.mg_apply(l, 3, to_gpu(xf0, l), coarse)
+        exp = olv.P.T @ xf0
+        assert np.abs(from_gpu(coarse, l + 1) - exp).max() <= 1e-12 * np.abs(exp).max(), l
+    V = spacetime.STMG(lv, nu_s=4, omega=0.7)
+    # a right-hand side in the range of K (consistent hanging entries, no constant pressures)
+    d = lv[0].st.space.dofs
+    xs = V.project(np.tile(d.distribute(rng.uniform(-1, 1, d.n_dofs)), lv[0].st.Q))
+    b = lv[0].K @ xs
+    x = torch.zeros(len(b), dtype=torch.float64, device="cuda")
+    st.vcycle(to_gpu(b, 0), x)
+    exp = V(b)
+    assert np.abs(from_gpu(x, 0) - exp).max() <= 1e-9 * np.abs(exp).max()

@@ -52,6 +52,10 @@ int main() {
     for (int32_t i : p) std::printf("%d ", i);
     std::printf("\n");
   }
+  std::vector<int32_t> colour;
+  colour_patches_for_probing(f, nu, np, patches, colour);
+  for (int32_t c : colour) std::printf("%d ", c);
+  std::printf("\n");
   return 0;
 }
 """
@@ -80,6 +84,7 @@ def harness(tmp_path_factory):
         xp = np.array([float(v) for v in out[3].split()]).reshape(nnp, dim)
         npatch = int(out[4])
         patches = [[int(v) for v in out[5 + i].split()] for i in range(npatch)]
+        run.colours = np.array([int(v) for v in out[5 + npatch].split()])
         return seq, xu, xp, patches
     return run
 
@@ -128,6 +133,23 @@ def test_vertex_star_patches_match_the_oracle(harness, dim, n, ball, k):
         return key[(tuple(np.rint(xp[i - n_main] * 2 ** 30).astype(np.int64)), dim)]
 
     mine = {frozenset(oracle_index(i) for i in p) for p in patches}
+    # probing colours: within a colour class no operator entry couples two different patches
+    A = abs(prob.assemble()).tocsr()
+    Mv = abs(spacetime.SpaceTimeStokes(f, k, 0, pressure="continuous").M).tocsr()
+    colours = harness.colours
+    assert len(colours) == len(patches) and colours.max() < 64
+    idx = [np.array([oracle_index(i) for i in p]) for p in patches]
+    for col in range(colours.max() + 1):
+        members = np.nonzero(colours == col)[0]
+        owner = -np.ones(A.shape[0], dtype=np.int64)
+        for pi in members:
+            assert np.all(owner[idx[pi]] < 0)              # patches of one colour are disjoint
+            owner[idx[pi]] = pi
+        for pi in members:
+            for Mat in (A, Mv):
+                cols = Mat[idx[pi]].nonzero()[1]
+                hit = owner[cols]
+                assert np.all((hit < 0) | (hit == pi)), (col, pi)
     ref_list = spacetime._patch_dofs(prob, "vertex")
     ref = {frozenset(p.tolist()) for p in ref_list}
     assert mine == ref
