@@ -392,6 +392,13 @@ int mfns_spacetime_mg_apply(mfns_spacetime* st, int level, int what, const void*
 /* x = one V-cycle of the space-time multigrid applied to b (zero initial guess; FP64, length
  * Q * n of the finest level). */
 int mfns_spacetime_vcycle(mfns_spacetime* st, const void* b, void* x, void* stream);
+/* K x = b on the slab by FGMRES(30) in FP64 (classical Gram--Schmidt twice), right-preconditioned
+ * by one space-time V-cycle; the constant pressure of every stage (the null space of K) is removed
+ * from b and from every preconditioned vector, so x has none.  Stops when ||b - K x|| <= tol ||b||
+ * or after maxit iterations (then MFNS_ERR_NOT_CONVERGED, x the last iterate).  iterations,
+ * relres, converged: host outputs (may be NULL).  Synchronises `stream` once per iteration. */
+int mfns_spacetime_solve(mfns_spacetime* st, const void* b, void* x, double tol, int maxit, int* iterations,
+                         double* relres, int* converged, void* stream);
 /* The DG(r) reference-slab matrices on the host, no device needed (any pointer may be NULL):
  * nodes (Q), m_Q (Q, m_Q[j] = phi_j(0)), M_Q, A_Q and G_Q (Q x Q, row-major [j][i]).  Error: ARG
  * for r outside 0..7. */

@@ -341,6 +341,15 @@ class SpaceTime:
         L.check(self.lib.mfns_spacetime_vcycle(self.h, _ptr(b), _ptr(x), _stream(stream)))
         return x
 
+    def solve(self, b, x, tol=1e-10, maxit=200, stream=None, raise_on_nonconvergence=True):
+        """FGMRES preconditioned by the space-time V-cycle; returns (iterations, relres)."""
+        its, rel, conv = C.c_int(), C.c_double(), C.c_int()
+        code = self.lib.mfns_spacetime_solve(self.h, _ptr(b), _ptr(x), tol, maxit, C.byref(its), C.byref(rel),
+                                             C.byref(conv), _stream(stream))
+        if code != L.OK and (code != L.ERR_NOT_CONVERGED or raise_on_nonconvergence):
+            L.check(code)
+        return its.value, rel.value
+
     def close(self):
         if self.h:
             self.lib.mfns_spacetime_destroy(self.h)

@@ -6,6 +6,7 @@
 // nodes, constrained velocity rows cleared), then one streaming pass y_q = tau (A x)_q +
 // sum_j G[q][j] (M x)_j.
 #include <algorithm>
+#include <cmath>
 #include <memory>
 #include <string>
 
@@ -145,6 +146,10 @@ struct StmgLevel {
 
 struct Stmg {
   std::vector<std::unique_ptr<StmgLevel>> lv;
+  // FGMRES on the finest level (allocated on first use): basis V (m + 1 vectors), Z (m), work
+  int restart = 30;
+  DevBuf V, Z, w, bp, pres0;
+  int64_t n_pres0 = 0;
   int nu_s = 4;
   double omega = 0.7, tau = 0.1;
   DevBuf cinv;      // coarsest: inverse of K + sum_q E_q E_q^T, (Q n)^2
@@ -408,6 +413,121 @@ static void stmg_cycle(Stmg& mg, size_t l, cudaStream_t s) {
   stmg_smooth(mg, L, s);
 }
 
+// every stage's constant pressure removed from a finest-level vector (its component along the
+// null space of K and K^T)
+static void project_constants(Stmg& mg, double* v, cudaStream_t s) {
+  StmgLevel& L = *mg.lv[0];
+  if (mg.n_pres0 == 0) return;
+  for (int q = 0; q < L.Q; ++q) {
+    double* vq = v + (int64_t)q * L.n;
+    sum_idx<double>(mg.scal.as<double>(), vq, mg.pres0.as<int32_t>(), mg.n_pres0, mg.part.as<double>(), s);
+    sub_mean_idx<double>(vq, mg.pres0.as<int32_t>(), mg.n_pres0, mg.scal.as<double>(), s);
+  }
+}
+
+static double dev_dot(Stmg& mg, const double* a, const double* b, int64_t n, cudaStream_t s) {
+  dot<double>(mg.scal.as<double>() + 1, a, b, n, mg.part.as<double>(), s);
+  double h;
+  MFNS_CUDA(cudaMemcpyAsync(&h, mg.scal.as<double>() + 1, 8, cudaMemcpyDeviceToHost, s));
+  MFNS_CUDA(cudaStreamSynchronize(s));
+  return h;
+}
+
+// FGMRES(m) in FP64 on the slab operator, right-preconditioned by one space-time V-cycle
+// (classical Gram--Schmidt applied twice, Givens rotations); the constant pressures of every
+// stage are removed from b and from every preconditioned vector, so x is the solution without
+// them.  Returns the iterations; relres = ||b - K x|| / ||b|| of the projected b.
+static int stmg_fgmres(mfns_spacetime& st, const double* b, double* x, double tol, int maxit, double* relres,
+                       bool* converged, cudaStream_t s) {
+  Stmg& mg = *st.mg;
+  StmgLevel& L = *mg.lv[0];
+  const int64_t N = (int64_t)L.Q * L.n;
+  const int m = mg.restart;
+  if (!mg.V.get()) {
+    Budget* bud = st.problem->p->bud;
+    mg.V.alloc(bud, (size_t)(m + 1) * N * 8);
+    mg.Z.alloc(bud, (size_t)m * N * 8);
+    mg.w.alloc(bud, (size_t)N * 8);
+    mg.bp.alloc(bud, (size_t)N * 8);
+  }
+  double* V = mg.V.as<double>();
+  double* Z = mg.Z.as<double>();
+  double* w = mg.w.as<double>();
+  double* bp = mg.bp.as<double>();
+  MFNS_CUDA(cudaMemcpyAsync(bp, b, (size_t)N * 8, cudaMemcpyDeviceToDevice, s));
+  project_constants(mg, bp, s);
+  vzero<double>(x, N, s);
+  const double bnorm = std::sqrt(dev_dot(mg, bp, bp, N, s));
+  *converged = false;
+  if (bnorm == 0.0) {
+    *relres = 0.0;
+    *converged = true;
+    return 0;
+  }
+  int it = 0;
+  double beta = bnorm;
+  MFNS_CUDA(cudaMemcpyAsync(V, bp, (size_t)N * 8, cudaMemcpyDeviceToDevice, s));  // r = b (x = 0)
+  std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), y(m), h(m + 1), h2(m + 1);
+  while (true) {
+    if (beta <= tol * bnorm) {
+      *converged = true;
+      break;
+    }
+    if (it >= maxit) break;
+    vscale<double>(V, 1.0 / beta, N, s);
+    std::fill(g.begin(), g.end(), 0.0);
+    g[0] = beta;
+    int j_done = 0;
+    for (int j = 0; j < m && it < maxit; ++j) {
+      double* Vj = V + (int64_t)j * N;
+      double* Zj = Z + (int64_t)j * N;
+      MFNS_CUDA(cudaMemcpyAsync(L.vb.get(), Vj, (size_t)N * 8, cudaMemcpyDeviceToDevice, s));
+      stmg_cycle(mg, 0, s);
+      MFNS_CUDA(cudaMemcpyAsync(Zj, L.vx.get(), (size_t)N * 8, cudaMemcpyDeviceToDevice, s));
+      project_constants(mg, Zj, s);
+      level_vmult(mg, L, Zj, w, s);
+      for (int i = 0; i <= j; ++i) h[i] = dev_dot(mg, V + (int64_t)i * N, w, N, s);
+      for (int i = 0; i <= j; ++i) vaxpy<double>(w, -h[i], V + (int64_t)i * N, N, s);
+      for (int i = 0; i <= j; ++i) h2[i] = dev_dot(mg, V + (int64_t)i * N, w, N, s);
+      for (int i = 0; i <= j; ++i) vaxpy<double>(w, -h2[i], V + (int64_t)i * N, N, s);
+      for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = h[i] + h2[i];
+      const double hn = std::sqrt(dev_dot(mg, w, w, N, s));
+      H[(size_t)(j + 1) * m + j] = hn;
+      if (hn > 0.0) {
+        MFNS_CUDA(cudaMemcpyAsync(V + (int64_t)(j + 1) * N, w, (size_t)N * 8, cudaMemcpyDeviceToDevice, s));
+        vscale<double>(V + (int64_t)(j + 1) * N, 1.0 / hn, N, s);
+      }
+      for (int i = 0; i < j; ++i) {  // earlier rotations
+        const double a = H[(size_t)i * m + j], c = H[(size_t)(i + 1) * m + j];
+        H[(size_t)i * m + j] = cs[i] * a + sn[i] * c;
+        H[(size_t)(i + 1) * m + j] = -sn[i] * a + cs[i] * c;
+      }
+      const double a = H[(size_t)j * m + j], c = H[(size_t)(j + 1) * m + j];
+      const double rr = std::hypot(a, c);
+      cs[j] = rr > 0.0 ? a / rr : 1.0;
+      sn[j] = rr > 0.0 ? c / rr : 0.0;
+      H[(size_t)j * m + j] = rr;
+      H[(size_t)(j + 1) * m + j] = 0.0;
+      g[j + 1] = -sn[j] * g[j];
+      g[j] = cs[j] * g[j];
+      ++it;
+      j_done = j + 1;
+      if (std::fabs(g[j + 1]) <= tol * bnorm || hn == 0.0) break;
+    }
+    for (int i = j_done - 1; i >= 0; --i) {  // H y = g (upper triangular)
+      double v = g[i];
+      for (int k = i + 1; k < j_done; ++k) v -= H[(size_t)i * m + k] * y[k];
+      y[i] = v / H[(size_t)i * m + i];
+    }
+    for (int i = 0; i < j_done; ++i) vaxpy<double>(x, y[i], Z + (int64_t)i * N, N, s);
+    level_vmult(mg, L, x, w, s);  // true residual, into the first basis vector
+    vsub<double>(V, bp, w, N, s);
+    beta = std::sqrt(dev_dot(mg, V, V, N, s));
+  }
+  *relres = beta / bnorm;
+  return it;
+}
+
 static void build_stmg(mfns_spacetime& st, int nu_s, double omega, cudaStream_t s) {
   Problem& P = *st.problem->p;
   const OpLevel& A0 = *P.system;
@@ -490,6 +610,8 @@ static void build_stmg(mfns_spacetime& st, int nu_s, double omega, cudaStream_t 
   mg->n_pres = (int64_t)pres.size();
   mg->part.alloc(P.bud, (size_t)kRedBlocks * kMaxDots * 8);
   mg->scal.alloc(P.bud, 64);
+  mg->pres0 = upload(P.bud, mg->lv[0]->A->pres_host);
+  mg->n_pres0 = (int64_t)mg->lv[0]->A->pres_host.size();
   MFNS_CUDA(cudaStreamSynchronize(s));
   st.mg = std::move(mg);
 }
@@ -653,5 +775,21 @@ extern "C" int mfns_spacetime_vcycle(mfns_spacetime* st, const void* b, void* x,
   MFNS_CUDA(cudaMemcpyAsync(L.vb.get(), b, bytes, cudaMemcpyDeviceToDevice, s));
   stmg_cycle(mg, 0, s);
   MFNS_CUDA(cudaMemcpyAsync(x, L.vx.get(), bytes, cudaMemcpyDeviceToDevice, s));
+  ST_END
+}
+
+extern "C" int mfns_spacetime_solve(mfns_spacetime* st, const void* b, void* x, double tol, int maxit,
+                                    int* iterations, double* relres, int* converged, void* stream) {
+  ST_BEGIN
+  if (!st || !st->mg || !b || !x || b == x || !(tol > 0.0) || maxit < 1) return capi_fail(kErrArg, "bad arguments");
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  MFNS_CUDA(cudaSetDevice(st->problem->ctx->device));
+  double rel = 0.0;
+  bool conv = false;
+  const int its = stmg_fgmres(*st, (const double*)b, (double*)x, tol, maxit, &rel, &conv, s);
+  if (iterations) *iterations = its;
+  if (relres) *relres = rel;
+  if (converged) *converged = conv ? 1 : 0;
+  if (!conv) return capi_fail(MFNS_ERR_NOT_CONVERGED, "space-time FGMRES did not reach the tolerance");
   ST_END
 }

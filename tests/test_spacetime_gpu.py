@@ -139,3 +139,37 @@ def test_space_time_multigrid_matches_oracle(ctx, case):
     st.vcycle(to_gpu(b, 0), x)
     exp = V(b)
     assert np.abs(from_gpu(x, 0) - exp).max() <= 1e-9 * np.abs(exp).max()
+
+
+@pytest.mark.parametrize("case", [(2, 8, 2, 1), (3, 4, 2, 1)], ids=lambda c: f"{c[0]}d-n{c[1]}-k{c[2]}-r{c[3]}")
+def test_space_time_solve_converges(ctx, case):
+    """FGMRES with the space-time V-cycle: the manufactured slab solution (no constant pressures) is
+    recovered, in about the oracle's number of iterations."""
+    from oracle import solvers
+    from paper_2603_29621_gb300 import _lib as L, api
+    dim, n, k, r = case
+    nu, tau = 1.0, 0.05
+    f = mesh.uniform(dim, n)
+    m = api.Mesh(ctx, dim, n)
+    prob = api.Problem(ctx, m, kind=L.STOKES, degree=k, nu=nu, lambda_max=1.0)
+    st = api.SpaceTime(prob, r, tau)
+    st.mg_build(nu_s=4, omega=0.7)
+    lv = spacetime.stmg_levels(f, k, r, nu=nu, tau=tau, pressure="continuous")
+    V = spacetime.STMG(lv)
+    K = lv[0].K
+    d = lv[0].st.space.dofs
+    xs = V.project(np.tile(d.distribute(np.random.default_rng(1).uniform(-1, 1, d.n_dofs)), lv[0].st.Q))
+    b = K @ xs
+    _, its_o, _ = solvers.fgmres(K, b, V, tol=1e-10, maxit=200, project=V.project)
+    xg, fg = prob.support_points()
+    xo, fo = d.support_points()
+    perm = inputs.match_dofs(xg, fg, xo, fo)
+    full = (np.arange(st.Q)[:, None] * st.n + perm[None, :]).ravel()
+    bd = np.empty_like(b)
+    bd[full] = b
+    x = torch.zeros(len(b), dtype=torch.float64, device="cuda")
+    its, rel = st.solve(torch.tensor(bd, device="cuda"), x, tol=1e-10, maxit=200)
+    torch.cuda.synchronize()
+    got = x.cpu().numpy()[full]
+    assert rel <= 1e-10 and abs(its - its_o) <= 3, (its, its_o)
+    assert np.abs(V.project(got) - xs).max() <= 1e-6 * np.abs(xs).max()
