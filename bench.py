@@ -278,6 +278,76 @@ def hp_section(api, L, inputs, torch):
     return out
 
 
+def spacetime_section(api, L, inputs, torch):
+    """Section 4 (space-time): the slab operator K = G_Q (x) M + tau I_Q (x) A of DG(1) in time on the
+    Taylor--Hood Q2/Q1 space of the unit cube with 32^3 cells (one product, FP64 and FP32), and
+    FGMRES preconditioned by the space-time multigrid (vertex-star Schwarz, nu_s = 4, omega = 0.7)
+    on 8^3 cells, tau = 0.05, for a manufactured slab solution.  Errors are recorded, not raised:
+    this section runs last."""
+    out = {}
+    ctx = None
+    try:
+        ctx = api.Context(torch.cuda.current_device())
+        m = api.Mesh(ctx, 3, 32)
+        p = api.Problem(ctx, m, kind=L.STOKES, degree=2, nu=1.0, lambda_max=1.0)
+        st = api.SpaceTime(p, 1, 0.05)
+        N = st.Q * st.n
+        for dt, name in ((torch.float64, "fp64"), (torch.float32, "fp32")):
+            x = torch.tensor(inputs.uniform_vector(N, seed=1), device="cuda", dtype=dt)
+            y = torch.empty_like(x)
+            for _ in range(3):
+                st.vmult(x, y)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            reps = 10
+            e0.record()
+            for _ in range(reps):
+                st.vmult(x, y)
+            e1.record()
+            torch.cuda.synchronize()
+            out.setdefault("slab_vmult_32cube_dg1", {"entries": N, "cells": 32 ** 3})[name + "_ms"] = \
+                e0.elapsed_time(e1) / reps
+        st.close()
+        p.close()
+        m.close()
+        m = api.Mesh(ctx, 3, 8)
+        p = api.Problem(ctx, m, kind=L.STOKES, degree=2, nu=1.0, lambda_max=1.0)
+        st = api.SpaceTime(p, 1, 0.05)
+        t0 = time.perf_counter()
+        levels = st.mg_build(nu_s=4, omega=0.7)
+        setup = time.perf_counter() - t0
+        xyz, fld = p.support_points()
+        one = inputs.smooth_solution(xyz, fld, 3)
+        xs_np = np.concatenate([(1.0 + 0.5 * q) * one for q in range(st.Q)])
+        pres = fld == 3
+        for q in range(st.Q):                                       # no constant pressure per stage
+            blk = xs_np[q * st.n:(q + 1) * st.n]
+            blk[pres] -= blk[pres].mean()
+        xs = torch.tensor(xs_np, device="cuda")
+        b = torch.empty_like(xs)
+        st.vmult(xs, b)
+        x = torch.zeros_like(xs)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        its, rel = st.solve(b, x, tol=1e-10, maxit=200, raise_on_nonconvergence=False)
+        torch.cuda.synchronize()
+        out["stmg_solve_8cube_dg1"] = {"entries": st.Q * st.n, "levels": [list(l) for l in levels],
+                                       "setup_s": setup, "iterations": its, "rel_residual": rel,
+                                       "solve_s": time.perf_counter() - t0,
+                                       "error_vs_xstar": float(torch.linalg.norm(x - xs) / torch.linalg.norm(xs))}
+        st.close()
+        p.close()
+        m.close()
+    except Exception as e:  # noqa: BLE001 -- reported in the JSON line
+        out["error"] = f"{type(e).__name__}: {e}"
+    try:
+        if ctx is not None:
+            ctx.close()
+    except Exception as e:  # noqa: BLE001
+        out.setdefault("error", f"{type(e).__name__}: {e}")
+    return out
+
+
 def serving_section(api, L, torch, count):
     """Config 5, bounded: a seeded Poisson stream of `count` requests (n in 8..48, k in 1..3, nu
     log-uniform in [1e-3, 1], Stokes / stabilised NS 50/50, b = A x*), offered at 0.8 x the measured
@@ -554,6 +624,7 @@ def run_ours(args, world, rank, local):
         line["serving"] = serving_section(api, L, torch, args.serve_requests)
         line["solves_serving_wall_s"] = time.perf_counter() - t0
         line["hp"] = hp_section(api, L, inputs, torch)
+        line["spacetime"] = spacetime_section(api, L, inputs, torch)
     if world == 1 and not args.no_cpu_baseline:
         cb = cpu_baseline()
         cb.pop("ms_per_step", None)
