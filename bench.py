@@ -278,6 +278,80 @@ def hp_section(api, L, inputs, torch):
     return out
 
 
+def _guarded_solve(api, L, inputs, torch, ctx, build, pslice):
+    """Set up with build(), solve a manufactured discrete solution twice (warm-up, timed) and report
+    iterations, time and the error against x* with the pressure mean removed (pslice)."""
+    t0 = time.perf_counter()
+    p, m = build()
+    setup = time.perf_counter() - t0
+    xyz, fld = p.support_points()
+    xs = torch.tensor(inputs.smooth_solution(xyz, fld, 3), device="cuda")
+    b = torch.empty_like(xs)
+    p.vmult(xs, b)
+    x = torch.zeros_like(xs)
+    p.solve(b, x, raise_on_nonconvergence=False)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    info = p.solve(b, x, raise_on_nonconvergence=False)
+    torch.cuda.synchronize()
+    dt_solve = time.perf_counter() - t0
+    ps = pslice(p)
+    d = x - xs
+    d[ps] -= d[ps].mean()
+    xr = xs.clone()
+    xr[ps] -= xr[ps].mean()
+    r = {"dofs": p.info.n_dofs, "cells": p.info.n_cells, "levels": p.info.n_levels, "iterations": info.iterations,
+         "rel_residual": info.rel_residual, "converged": bool(info.converged), "solve_s": dt_solve,
+         "setup_s": setup, "error_vs_xstar": float(torch.linalg.norm(d) / torch.linalg.norm(xr))}
+    p.close()
+    m.close()
+    return r
+
+
+def next_rows_section(api, L, inputs, torch):
+    """Section 2's local smoothing for Section 5's stabilised operator (Q2Q2, nu = 1e-2, dt = 1e-2) on
+    the ball-refined 24^3 mesh (two levels) beside global coarsening, and Section 3's hp Taylor--Hood Stokes
+    (velocity degrees 2..4 per cell, pressure one lower) on the ball-refined 16^3 mesh; FP32
+    multigrid inside FP64 FGMRES.  Errors are recorded per row, not raised: this section runs last."""
+    out = {}
+    ctx = None
+    try:
+        ctx = api.Context(torch.cuda.current_device())
+    except Exception as e:  # noqa: BLE001
+        return {"error": f"{type(e).__name__}: {e}"}
+    for name, hierarchy in (("global_coarsening", L.GLOBAL_COARSENING), ("local_smoothing", L.LOCAL_SMOOTHING)):
+        def build(h=hierarchy):
+            m = api.Mesh(ctx, 3, 24)
+            m.refine_ball((0.5, 0.5, 0.5), 0.25, 2)
+            p = api.Problem(ctx, m, kind=L.STAB_NS, degree=2, nu=1e-2, dt=1e-2, mg_precision=L.FP32, tol=1e-10,
+                            maxit=300, hierarchy=h)
+            return p, m
+        try:
+            out["stab_ns_ball_24_" + name] = _guarded_solve(api, L, inputs, torch, ctx, build,
+                                                             lambda p: slice(3, None, 4))
+        except Exception as e:  # noqa: BLE001
+            out["stab_ns_ball_24_" + name] = {"error": f"{type(e).__name__}: {e}"}
+
+    def build_hp():
+        m = api.Mesh(ctx, 3, 16)
+        m.refine_ball((0.5, 0.5, 0.5), 0.25, 1)
+        cells = m.cells()
+        deg = (2 + cells[:, 0] + ((cells[:, 1] >> cells[:, 0]) % 2)).astype(np.int32)
+        p = api.Problem(ctx, m, degrees=deg, kind=L.STOKES, degree=int(deg.max()), nu=1.0, mg_precision=L.FP32,
+                        tol=1e-10, maxit=300)
+        return p, m
+    try:
+        out["hp_taylor_hood_ball_16"] = _guarded_solve(api, L, inputs, torch, ctx, build_hp,
+                                                       lambda p: slice(p.info.n_velocity_dofs, None))
+    except Exception as e:  # noqa: BLE001
+        out["hp_taylor_hood_ball_16"] = {"error": f"{type(e).__name__}: {e}"}
+    try:
+        ctx.close()
+    except Exception as e:  # noqa: BLE001
+        out.setdefault("error", f"{type(e).__name__}: {e}")
+    return out
+
+
 def spacetime_section(api, L, inputs, torch):
     """Section 4 (space-time): the slab operator K = G_Q (x) M + tau I_Q (x) A of DG(1) in time on the
     Taylor--Hood Q2/Q1 space of the unit cube with 32^3 cells (one product, FP64 and FP32), and
@@ -625,6 +699,7 @@ def run_ours(args, world, rank, local):
         line["solves_serving_wall_s"] = time.perf_counter() - t0
         line["hp"] = hp_section(api, L, inputs, torch)
         line["spacetime"] = spacetime_section(api, L, inputs, torch)
+        line["next_rows"] = next_rows_section(api, L, inputs, torch)
     if world == 1 and not args.no_cpu_baseline:
         cb = cpu_baseline()
         cb.pop("ms_per_step", None)
