@@ -470,10 +470,75 @@ class Level:
         self.lmax = None
 
 
-def hierarchy(forest, degrees, nu=1.0, stop_n=2, rule="dominance"):
+def combined_faces(problem):
+    """(coarse cell, axis, side) of every cell face whose neighbours across it are finer and of lower
+    degree: the faces, h-refined on one side and p-refined on the other, where Section 3 places the
+    blocks of its additive Schwarz smoother."""
+    f = problem.forest
+    deg = problem.degrees
+    lev = f.cells[:, 0]
+    h, org = f.h(), f.origin()
+    out = set()
+    for a, b, pts in problem.dofs.nodesets[0]._face_pieces():
+        if lev[a] == lev[b]:
+            continue
+        c, fc = (a, b) if lev[a] < lev[b] else (b, a)
+        if deg[c] <= deg[fc]:
+            continue
+        for ax in range(f.dim):
+            if np.all(np.abs(pts[:, ax] - pts[0, ax]) <= 1e-12):
+                out.add((int(c), ax, int(round((pts[0, ax] - org[c, ax]) / h[c]))))
+    return sorted(out)
+
+
+def asm_blocks(problem):
+    """Blocks of the additive Schwarz part of Section 3's smoother: for every combined face, the free
+    velocity unknowns (all components together) whose node lies on the closed face of its coarse
+    cell.  Ascending DoF indices; faces without free unknowns give no block."""
+    d = problem.dofs
+    ns = d.nodesets[0]
+    f = problem.forest
+    h, org = f.h(), f.origin()
+    blocks = []
+    for c, ax, side in combined_faces(problem):
+        plane = org[c, ax] + side * h[c]
+        on = (np.abs(ns.x[:, ax] - plane) <= 1e-12) & np.all(
+            (ns.x >= org[c] - 1e-12) & (ns.x <= org[c] + h[c] + 1e-12), axis=1)
+        nodes = np.nonzero(on)[0]
+        idx = np.array([d.offsets[0] + comp * ns.n_nodes + g for comp in range(f.dim) for g in nodes], dtype=np.int64)
+        idx = np.sort(idx[d.free[idx]])
+        if len(idx):
+            blocks.append(idx)
+    return blocks
+
+
+class JacobiASM:
+    """The smoother's preconditioner blending additive Schwarz and point Jacobi (Section 3):
+    P^{-1} r = sum over blocks B of R_B^T A_BB^{-1} R_B r (summed where blocks overlap) plus
+    r_i / A_ii on the unknowns in no block."""
+
+    def __init__(self, A, blocks):
+        A = A.tocsr()
+        self.blocks = blocks
+        self.dinv = 1.0 / A.diagonal()
+        self.in_block = np.zeros(A.shape[0], dtype=bool)
+        self.inv = []
+        for B in blocks:
+            self.in_block[B] = True
+            self.inv.append(np.linalg.inv(A[B][:, B].toarray()))
+
+    def __call__(self, r):
+        z = np.where(self.in_block, 0.0, self.dinv * r)
+        for B, Bi in zip(self.blocks, self.inv):
+            z[B] += Bi @ r[B]
+        return z
+
+
+def hierarchy(forest, degrees, nu=1.0, stop_n=2, rule="dominance", smoother="jacobi"):
     """hp-multigrid levels of the A block (finest first): every cell's degree lowered by one per
     level until all cells are linear, then global coarsening with linear elements.  rule: the
-    constraint construction of every level (``HpNodeSet``)."""
+    constraint construction of every level (``HpNodeSet``).  smoother: 'jacobi' (every level's
+    ``dinv`` is the diagonal inverse) or 'asm' (levels with combined faces get ``JacobiASM``)."""
     degrees = np.asarray(degrees, dtype=np.int64)
     seq = [(forest, degrees)]
     while seq[-1][1].max() > 1:
@@ -483,6 +548,11 @@ def hierarchy(forest, degrees, nu=1.0, stop_n=2, rule="dominance"):
     levels = [Level(HpProblem(f, d, "stokes_a", nu, rule=rule)) for f, d in seq]
     for l in range(len(levels) - 1):
         levels[l].P = prolongation(levels[l + 1].problem, levels[l].problem)
+    if smoother == "asm":
+        for lv in levels[:-1]:
+            blocks = asm_blocks(lv.problem)
+            if blocks:
+                lv.dinv = JacobiASM(lv.A, blocks)
     return levels
 
 

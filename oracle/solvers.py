@@ -36,31 +36,38 @@ from . import assemble, mesh, transfer
 
 
 # -- smoothers -------------------------------------------------------------------
+def _prec(dinv):
+    """The smoother's preconditioner: a diagonal inverse (array, applied pointwise) or a callable."""
+    return dinv if callable(dinv) else (lambda r: dinv * r)
+
+
 def chebyshev(A, dinv, b, x, degree, lmax, lmin=None, x_is_zero=False):
+    P = _prec(dinv)
     lmin = lmax / 20.0 if lmin is None else lmin
     theta = 0.5 * (lmax + lmin)
     delta = 0.5 * (lmax - lmin)
     sigma = theta / delta
     x = np.array(x, dtype=float, copy=True)
     r = b.copy() if x_is_zero else b - A @ x
-    d = dinv * r / theta
+    d = P(r) / theta
     x += d
     rho_old = 1.0 / sigma
     for _ in range(1, degree):
         r = b - A @ x
         rho = 1.0 / (2.0 * sigma - rho_old)
-        d = rho * rho_old * d + (2.0 * rho / delta) * dinv * r
+        d = rho * rho_old * d + (2.0 * rho / delta) * P(r)
         x += d
         rho_old = rho
     return x
 
 
 def jacobi_relaxation(A, dinv, b, x, iterations, lmax, lmin=None):
+    P = _prec(dinv)
     lmin = lmax / 20.0 if lmin is None else lmin
     omega = 2.0 / (lmin + lmax)
     x = np.array(x, dtype=float, copy=True)
     for _ in range(iterations):
-        x += omega * dinv * (b - A @ x)
+        x += omega * P(b - A @ x)
     return x
 
 
@@ -248,12 +255,14 @@ class StokesBlockPreconditioner:
 
 
 def power_lmax(A, dinv, iterations=200, seed=1):
-    """Largest eigenvalue magnitude of D^{-1} A by power iteration (for oracle self-tests)."""
+    """Largest eigenvalue magnitude of P^{-1} A by power iteration (P^{-1} a diagonal inverse or a
+    callable; for oracle self-tests)."""
+    P = _prec(dinv)
     rng = np.random.default_rng(seed)
     v = rng.uniform(-1, 1, A.shape[0])
     lam = 0.0
     for _ in range(iterations):
-        w = dinv * (A @ v)
+        w = P(A @ v)
         lam = np.linalg.norm(w) / np.linalg.norm(v)
         v = w / np.linalg.norm(w)
     return lam

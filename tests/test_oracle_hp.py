@@ -432,3 +432,63 @@ def test_pressure_mass_closed_forms(dim, rule, degf):
         assert np.abs(P.dofs.distribute(v) - v).max() <= 1e-12
     assert abs(one @ M @ one - 1.0) <= 1e-13
     assert abs(lin @ M @ lin - 1.0 / 12.0) <= 1e-13
+
+
+# -- Section 3's blended smoother: point Jacobi with additive Schwarz blocks on combined faces -------
+def test_asm_without_combined_faces_is_point_jacobi():
+    f = _ball(2, 4, 1)
+    deg = 2 + f.cells[:, 0]
+    P = hp.HpProblem(f, deg, "stokes_a")
+    assert hp.combined_faces(P) == [] and hp.asm_blocks(P) == []
+    lv = hp.hierarchy(f, deg, smoother="asm")
+    assert all(isinstance(l.dinv, np.ndarray) for l in lv)
+
+
+def test_asm_blocks_lie_on_combined_faces():
+    f = _ball(2, 4, 1)
+    deg = _combined(f, "3-2")
+    P = hp.HpProblem(f, deg, "stokes_a", rule="elimination")
+    faces = hp.combined_faces(P)
+    blocks = hp.asm_blocks(P)
+    assert len(faces) > 0 and len(blocks) == len(faces)
+    d = P.dofs
+    ns = d.nodesets[0]
+    h, org = f.h(), f.origin()
+    for (c, ax, side), B in zip(faces, blocks):
+        assert f.cells[c, 0] == 0 and deg[c] == 3                  # the coarse, higher-degree side
+        assert np.all(d.free[B])
+        g = (B - d.offsets[0]) % ns.n_nodes
+        assert np.all(np.abs(ns.x[g, ax] - (org[c, ax] + side * h[c])) <= 1e-12)
+        # every component of every node of the block
+        assert len(B) == 2 * len(np.unique(g))
+
+
+def test_asm_preconditioner_is_spd_and_exact_on_one_block():
+    f = _ball(2, 3, 1)
+    P = hp.HpProblem(f, _combined(f, "3-2"), "stokes_a", rule="elimination")
+    A = P.assemble()
+    free = np.nonzero(P.dofs.free)[0]
+    J = hp.JacobiASM(A, hp.asm_blocks(P))
+    E = np.eye(A.shape[0])[:, free]
+    Pm = np.stack([J(e) for e in E.T], axis=1)[free]
+    assert np.abs(Pm - Pm.T).max() <= 1e-12 * np.abs(Pm).max()
+    assert np.linalg.eigvalsh(0.5 * (Pm + Pm.T)).min() > 0
+    whole = hp.JacobiASM(A, [free])
+    Af = A[free][:, free].toarray()
+    r = np.random.default_rng(0).uniform(-1, 1, A.shape[0])
+    assert np.abs(whole(r)[free] - np.linalg.solve(Af, r[free])).max() <= 1e-12 * np.abs(r).max() * np.linalg.cond(Af)
+
+
+@pytest.mark.parametrize("dim,n,kind", [(2, 8, "3-2"), (3, 2, "3-2")])
+def test_hp_multigrid_with_jacobi_asm_converges(dim, n, kind):
+    f = _ball(dim, n, 1)
+    lv = hp.hierarchy(f, _combined(f, kind), rule="elimination", smoother="asm")
+    assert any(isinstance(l.dinv, hp.JacobiASM) for l in lv)
+    lmax = [1.2 * solvers.power_lmax(l.A, l.dinv, iterations=60) for l in lv[:-1]]
+    V = solvers.VCycle(lv, lmax, ("chebyshev", 5))
+    A = lv[0].A
+    d = lv[0].problem.dofs
+    xs = np.random.default_rng(2).uniform(-1, 1, d.n_dofs) * d.free
+    x, its, res = solvers.fgmres(A, A @ xs, V, tol=1e-10)
+    assert res <= 1e-10 and its <= 12
+    assert np.abs(x - xs).max() <= 1e-7
