@@ -367,9 +367,11 @@ int mfns_spacetime_info(const mfns_spacetime* st, int* stages, int64_t* n_stage,
 int mfns_spacetime_vmult(mfns_spacetime* st, int precision, const void* x, void* y, void* stream);
 int mfns_spacetime_destroy(mfns_spacetime* st);
 /* Space-time multigrid for the slab (Section 4), FP64, uniform meshes (MFNS_ERR_UNSUPPORTED
- * otherwise).  Levels, finest first: the spatial degree halved while above 2, then the temporal
- * degree halved down to DG(0), then global coarsening in space down to 2 cells per direction; no
- * coarsening of tau.  Transfers: P_tau (x) I for a temporal step (the coarse temporal polynomial
+ * otherwise).  Levels, finest first (space before time, polynomial before geometric): the spatial
+ * degree halved while above 2, then global coarsening in space while the mesh has more than
+ * coarse_n (>= 2) cells per direction, then the temporal degree halved down to DG(0) on that
+ * coarsest mesh -- left out when one vertex star there holds every cell (its patch would be
+ * singular; the coarsest level is then solved at the fine temporal degree); no coarsening of tau.  Transfers: P_tau (x) I for a temporal step (the coarse temporal polynomial
  * at the fine nodes), I_Q (x) P_h for a spatial one (Eq. 4 for velocity and pressure); restriction
  * is the transpose.  Smoother: nu_s steps x += omega S (b - K x) before and after the coarse
  * correction, S the additive Schwarz method over vertex stars (for every mesh vertex, the free
@@ -378,7 +380,7 @@ int mfns_spacetime_destroy(mfns_spacetime* st);
  * the coarsest level is solved directly (pseudo-inverse: the constant pressure of every stage is
  * a null direction).  The set-up probes the spatial operators on the device, inverts the patch
  * blocks on the host and synchronises `stream`. */
-int mfns_spacetime_mg_build(mfns_spacetime* st, int nu_s, double omega, void* stream);
+int mfns_spacetime_mg_build(mfns_spacetime* st, int nu_s, double omega, int coarse_n, void* stream);
 /* Number of levels; for 0 <= level < *n_levels also its spatial degree, temporal degree and
  * spatial vector length (level -1: the count only).  ARG if the multigrid is not built. */
 int mfns_spacetime_mg_level(const mfns_spacetime* st, int level, int* n_levels, int* k, int* r, int64_t* n_stage);

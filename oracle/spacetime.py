@@ -234,23 +234,41 @@ def _patch_dofs(problem, patch):
     return out
 
 
+def _star_covers_all(forest):
+    """Whether some vertex star (the cells having one vertex as a corner) holds every cell."""
+    corners = fe.tensor_index(forest.dim, 2)
+    h, org = forest.h(), forest.origin()
+    count = {}
+    for c in range(forest.n_cells):
+        for cr in corners:
+            key = tuple(np.rint((org[c] + cr * h[c]) * 2 ** 30).astype(np.int64))
+            count[key] = count.get(key, 0) + 1
+    return max(count.values()) == forest.n_cells
+
+
 def stmg_levels(forest, k, r, nu=1.0, tau=0.1, stop_n=2, patch=None, pressure="disc"):
-    """Levels finest first: spatial degree halved (k >= 2 kept: Q2 is the lowest stable velocity for
-    both pairs), then the temporal degree halved (DG(r) -> DG(r // 2)), then global h-coarsening in
-    space; no geometric coarsening in time (time-marching).  Patches: one cell for the discontinuous
-    pressure (the paper's pair: every pressure DoF belongs to one cell), vertex stars for the
-    continuous one (a cell patch would cut the pressure coupling; a vertex star of a discontinuous
-    pressure holds a pressure constant as a local null mode)."""
+    """Levels finest first.  Section 4's rules -- coarsen in space before time (R1), and in each of
+    them polynomially before geometrically (R2: p before h, the temporal degree before tau) -- give:
+    the spatial degree halved (k >= 2 kept: Q2 is the lowest stable velocity for both pairs), then
+    global h-coarsening in space down to stop_n, then the temporal degree halved (DG(r) ->
+    DG(r // 2)) on the coarsest mesh; no geometric coarsening in time (time-marching).  Temporal
+    steps are left out when a vertex star of the coarsest mesh holds every cell (with vertex-star
+    patches that patch would hold every unknown and be singular); the coarsest level is then solved
+    at the fine temporal degree.  Patches: one cell for the discontinuous pressure (the paper's pair:
+    every pressure DoF belongs to one cell), vertex stars for the continuous one (a cell patch would
+    cut the pressure coupling; a vertex star of a discontinuous pressure holds a pressure constant as
+    a local null mode)."""
     if patch is None:
         patch = "cell" if pressure == "disc" else "vertex"
     from . import solvers, transfer
     seq = [(forest, k, r)]
     while seq[-1][1] > 2:
         seq.append((forest, max(2, seq[-1][1] // 2), seq[-1][2]))
-    while seq[-1][2] > 0:
-        seq.append((forest, seq[-1][1], seq[-1][2] // 2))
     for fc in solvers.coarse_forests(forest, stop_n)[1:]:
         seq.append((fc, seq[-1][1], seq[-1][2]))
+    if not (patch == "vertex" and _star_covers_all(seq[-1][0])):
+        while seq[-1][2] > 0:
+            seq.append((seq[-1][0], seq[-1][1], seq[-1][2] // 2))
     levels = [StLevel(f, kk, rr, nu, tau, patch, pressure) for f, kk, rr in seq]
     for l in range(len(levels) - 1):
         fine, coarse = levels[l], levels[l + 1]

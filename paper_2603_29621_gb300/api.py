@@ -313,8 +313,8 @@ class SpaceTime:
         return dst
 
     # -- space-time multigrid (FP64) ------------------------------------------------------------
-    def mg_build(self, nu_s=4, omega=0.7, stream=None):
-        L.check(self.lib.mfns_spacetime_mg_build(self.h, nu_s, omega, _stream(stream)))
+    def mg_build(self, nu_s=4, omega=0.7, coarse_n=2, stream=None):
+        L.check(self.lib.mfns_spacetime_mg_build(self.h, nu_s, omega, coarse_n, _stream(stream)))
         nl = C.c_int()
         L.check(self.lib.mfns_spacetime_mg_level(self.h, -1, C.byref(nl), None, None, None))
         self.mg_levels = []

@@ -528,14 +528,17 @@ static int stmg_fgmres(mfns_spacetime& st, const double* b, double* x, double to
   return it;
 }
 
-static void build_stmg(mfns_spacetime& st, int nu_s, double omega, cudaStream_t s) {
+static void build_stmg(mfns_spacetime& st, int nu_s, double omega, int coarse_n, cudaStream_t s) {
   Problem& P = *st.problem->p;
   const OpLevel& A0 = *P.system;
   if (!A0.forest.uniform()) throw Error(kErrUnsupported, "space-time multigrid: uniform meshes only");
-  if (nu_s < 1 || !(omega > 0.0)) throw Error(kErrArg, "space-time multigrid: nu_s >= 1 and omega > 0");
+  if (nu_s < 1 || !(omega > 0.0) || coarse_n < 2)
+    throw Error(kErrArg, "space-time multigrid: nu_s >= 1, omega > 0 and coarse_n >= 2");
   std::vector<Forest> fs{A0.forest};
-  while (forest_can_coarsen(fs.back(), 2)) fs.push_back(forest_coarsen(fs.back()));
-  const std::vector<StLevelSpec> seq = stmg_sequence(A0.k, st.r, (int)fs.size());
+  while (forest_can_coarsen(fs.back(), coarse_n)) fs.push_back(forest_coarsen(fs.back()));
+  // temporal steps on the coarsest mesh unless a vertex star there holds every cell
+  const std::vector<StLevelSpec> seq =
+      stmg_sequence(A0.k, st.r, (int)fs.size(), !vertex_star_covers_all(fs.back()));
   auto mg = std::make_unique<Stmg>();
   mg->nu_s = nu_s;
   mg->omega = omega;
@@ -705,12 +708,12 @@ extern "C" int mfns_spacetime_temporal(int r, double* nodes_host, double* m_host
   catch (const std::exception& e) { return capi_fail(kErrArg, e.what()); } \
   return MFNS_OK;
 
-extern "C" int mfns_spacetime_mg_build(mfns_spacetime* st, int nu_s, double omega, void* stream) {
+extern "C" int mfns_spacetime_mg_build(mfns_spacetime* st, int nu_s, double omega, int coarse_n, void* stream) {
   ST_BEGIN
   if (!st) return capi_fail(kErrArg, "bad arguments");
   MFNS_CUDA(cudaSetDevice(st->problem->ctx->device));
   st->mg.reset();
-  build_stmg(*st, nu_s, omega, reinterpret_cast<cudaStream_t>(stream));
+  build_stmg(*st, nu_s, omega, coarse_n, reinterpret_cast<cudaStream_t>(stream));
   ST_END
 }
 

@@ -37,15 +37,20 @@ bool temporal_matrices(int r, TemporalMatrices& out, std::string* err);
 // P_tau (Q_f x Q_c, row-major): the coarse DG(rc) temporal polynomial at the fine DG(rf) nodes.
 std::vector<double> time_prolongation(int rc, int rf);
 
-// Levels of the space-time multigrid, finest first: the spatial degree halved while above 2
-// (k >= 2 is kept: Q2 is the lowest Taylor--Hood velocity), then the temporal degree halved
-// (DG(r) -> DG(r / 2)) down to 0, then the coarser forests of global coarsening (index 1, 2, ...
-// of the forest sequence, forest 0 being the fine mesh); no coarsening of the slab length
-// (time-marching).
+// Levels of the space-time multigrid, finest first, by Section 4's rules -- space before time, and
+// in each polynomially before geometrically: the spatial degree halved while above 2 (k >= 2 is
+// kept: Q2 is the lowest Taylor--Hood velocity), then the coarser forests of global coarsening
+// (index 1, 2, ... of the forest sequence, forest 0 being the fine mesh), then, when time_steps,
+// the temporal degree halved (DG(r) -> DG(r / 2)) down to 0 on the coarsest forest; no coarsening
+// of the slab length (time-marching).
 struct StLevelSpec {
   int k = 2, r = 0, forest = 0;
 };
-std::vector<StLevelSpec> stmg_sequence(int k, int r, int n_forests);
+std::vector<StLevelSpec> stmg_sequence(int k, int r, int n_forests, bool time_steps);
+
+// Whether some vertex star (the cells having one vertex as a corner) holds every cell of f: its
+// vertex-star patch would then hold every unknown and be singular.
+bool vertex_star_covers_all(const Forest& f);
 
 // Patches of the space-time Schwarz smoother on a Taylor--Hood space (velocity entries g * dim + c
 // over the nodes of nu, then pressure entries n_main + g over the nodes of np): for every vertex

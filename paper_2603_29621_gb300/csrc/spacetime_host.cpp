@@ -128,7 +128,7 @@ std::vector<double> time_prolongation(int rc, int rf) {
   return P;
 }
 
-std::vector<StLevelSpec> stmg_sequence(int k, int r, int n_forests) {
+std::vector<StLevelSpec> stmg_sequence(int k, int r, int n_forests, bool time_steps) {
   std::vector<StLevelSpec> seq;
   StLevelSpec s;
   s.k = k;
@@ -140,17 +140,33 @@ std::vector<StLevelSpec> stmg_sequence(int k, int r, int n_forests) {
     s.k = std::max(2, s.k / 2);
     seq.push_back(s);
   }
-  while (seq.back().r > 0) {
-    s = seq.back();
-    s.r = s.r / 2;
-    seq.push_back(s);
-  }
   for (int i = 1; i < n_forests; ++i) {
     s = seq.back();
     s.forest = i;
     seq.push_back(s);
   }
+  while (time_steps && seq.back().r > 0) {
+    s = seq.back();
+    s.r = s.r / 2;
+    seq.push_back(s);
+  }
   return seq;
+}
+
+bool vertex_star_covers_all(const Forest& f) {
+  const int dim = f.dim;
+  const int L = f.max_level();
+  std::map<std::array<int64_t, 3>, int64_t> count;
+  int64_t best = 0;
+  for (size_t c = 0; c < f.n_cells(); ++c) {
+    const int64_t s = int64_t(1) << (L - f.lev[c]);
+    for (int a = 0; a < (1 << dim); ++a) {
+      std::array<int64_t, 3> key = {0, 0, 0};
+      for (int d = 0; d < dim; ++d) key[d] = (f.crd[3 * c + d] + ((a >> d) & 1)) * s;
+      best = std::max(best, ++count[key]);
+    }
+  }
+  return best == (int64_t)f.n_cells();
 }
 
 std::vector<std::vector<int32_t>> vertex_star_patches(const Forest& f, const NodeSpace& nu, const NodeSpace& np) {

@@ -72,10 +72,12 @@ def test_slab_rejects_other_problems(ctx):
     assert e.value.code == L.ERR_UNSUPPORTED
 
 
-STMG_CASES = [(2, 8, 2, 1), (2, 4, 3, 2), (3, 4, 2, 1)]
+# (dim, n, k, r, coarse_n): with coarse_n = 4 the coarsest mesh has no star holding every cell, so
+# the temporal levels (and their transfers) follow the spatial ones
+STMG_CASES = [(2, 8, 2, 1, 2), (2, 4, 3, 2, 2), (3, 4, 2, 1, 2), (2, 8, 2, 1, 4), (2, 8, 3, 2, 4)]
 
 
-@pytest.mark.parametrize("case", STMG_CASES, ids=lambda c: f"{c[0]}d-n{c[1]}-k{c[2]}-r{c[3]}")
+@pytest.mark.parametrize("case", STMG_CASES, ids=lambda c: f"{c[0]}d-n{c[1]}-k{c[2]}-r{c[3]}-c{c[4]}")
 def test_space_time_multigrid_matches_oracle(ctx, case):
     """Every level's slab operator (1e-12), Schwarz smoother and transfers (1e-12), and one V-cycle
     of the space-time multigrid against the oracle's (vertex stars, nu_s = 4, omega = 0.7, uniform
@@ -84,15 +86,17 @@ def test_space_time_multigrid_matches_oracle(ctx, case):
     about cond * eps * (block size), hence 1e-9 for the smoother and 1e-8 for the cycle (eight
     smoothing steps and a coarse solve of condition up to 2e4)."""
     from paper_2603_29621_gb300 import _lib as L, api
-    dim, n, k, r = case
+    dim, n, k, r, coarse_n = case
     nu, tau = 1.0, 0.05
     f = mesh.uniform(dim, n)
     m = api.Mesh(ctx, dim, n)
     prob = api.Problem(ctx, m, kind=L.STOKES, degree=k, nu=nu, lambda_max=1.0)
     st = api.SpaceTime(prob, r, tau)
-    levels = st.mg_build(nu_s=4, omega=0.7)
-    lv = spacetime.stmg_levels(f, k, r, nu=nu, tau=tau, pressure="continuous")
+    levels = st.mg_build(nu_s=4, omega=0.7, coarse_n=coarse_n)
+    lv = spacetime.stmg_levels(f, k, r, nu=nu, tau=tau, pressure="continuous", stop_n=coarse_n)
     assert [(a, b) for a, b, _ in levels] == [(l.k, l.r) for l in lv]
+    if coarse_n == 4:
+        assert any(lv[l].r != lv[l + 1].r for l in range(len(lv) - 1))
     full = []
     for l, olv in enumerate(lv):
         xg, fg = st.mg_support_points(l)

@@ -22,8 +22,8 @@ HARNESS = r"""
 #include "spacetime.hpp"
 using namespace mfns;
 int main() {
-  int dim, n, nc, k, r, nf;
-  if (std::scanf("%d %d %d %d %d %d", &dim, &n, &nc, &k, &r, &nf) != 6) return 1;
+  int dim, n, nc, k, r, nf, ts;
+  if (std::scanf("%d %d %d %d %d %d %d", &dim, &n, &nc, &k, &r, &nf, &ts) != 7) return 1;
   Forest f;
   f.dim = dim;
   f.n = n;
@@ -33,8 +33,8 @@ int main() {
     f.lev.push_back(l);
     f.crd.push_back(x); f.crd.push_back(y); f.crd.push_back(z);
   }
-  for (auto& s : stmg_sequence(k, r, nf)) std::printf("%d %d %d;", s.k, s.r, s.forest);
-  std::printf("\n");
+  for (auto& s : stmg_sequence(k, r, nf, ts != 0)) std::printf("%d %d %d;", s.k, s.r, s.forest);
+  std::printf("%d\n", (int)vertex_star_covers_all(f));
   Lattice lat = make_lattice(f);
   std::vector<uint32_t> masks = constraint_masks(f, lat);
   std::string err;
@@ -72,11 +72,13 @@ def harness(tmp_path_factory):
     subprocess.run(["g++", "-O1", "-std=c++17", "-I", CSRC, str(src), os.path.join(CSRC, "mesh.cpp"),
                     os.path.join(CSRC, "spacetime_host.cpp"), "-o", str(exe)], check=True)
 
-    def run(forest, k, r, nf):
+    def run(forest, k, r, nf, ts=True):
         rows = [f"{c[0]} {c[1]} {c[2]} {c[3] if forest.dim == 3 else 0}" for c in forest.cells]
-        inp = f"{forest.dim} {forest.n} {len(rows)} {k} {r} {nf}\n" + "\n".join(rows) + "\n"
+        inp = f"{forest.dim} {forest.n} {len(rows)} {k} {r} {nf} {int(ts)}\n" + "\n".join(rows) + "\n"
         out = subprocess.run([str(exe)], input=inp, capture_output=True, text=True, check=True).stdout.split("\n")
-        seq = [tuple(int(v) for v in t.split()) for t in out[0].split(";") if t.strip()]
+        parts = out[0].split(";")
+        run.covers_all = bool(int(parts[-1]))
+        seq = [tuple(int(v) for v in t.split()) for t in parts[:-1] if t.strip()]
         assert not out[1].startswith("FAIL"), out[1]
         nnu, nnp = (int(v) for v in out[1].split())
         dim = forest.dim
@@ -94,26 +96,25 @@ def _forest(dim, n, ball):
     return mesh.refine_ball(f, CENTRE, 0.3, 1) if ball else f
 
 
-@pytest.mark.parametrize("k,r", [(2, 0), (2, 3), (4, 1), (3, 2), (4, 3)])
-def test_level_sequence_matches_the_oracle(harness, k, r):
-    f = mesh.uniform(2, 8)
-    nf = len(solvers.coarse_forests(f, 2))
-    seq = harness(f, k, r, nf)[0]
-    lv = spacetime.stmg_levels(f, k, r, tau=0.1, pressure="continuous") if k <= 3 and r <= 2 else None
-    exp = []
-    kk, rr = k, r
-    exp.append((kk, rr, 0))
-    while kk > 2:
-        kk = max(2, kk // 2)
-        exp.append((kk, rr, 0))
-    while rr > 0:
-        rr //= 2
-        exp.append((kk, rr, 0))
-    for i in range(1, nf):
-        exp.append((kk, rr, i))
-    assert seq == exp
-    if lv is not None:
-        assert [(l.k, l.r) for l in lv] == [(a, b) for a, b, _ in seq]
+@pytest.mark.parametrize("n,stop_n", [(8, 2), (8, 4), (6, 3)])
+@pytest.mark.parametrize("k,r", [(2, 0), (2, 3), (4, 1), (3, 2)])
+def test_level_sequence_matches_the_oracle(harness, k, r, n, stop_n):
+    """Spatial degree, then h down to stop_n, then the temporal degree on the coarsest mesh unless a
+    vertex star there holds every cell -- the oracle's sequence for vertex-star patches."""
+    f = mesh.uniform(2, n)
+    fs = solvers.coarse_forests(f, stop_n)
+    ts = not spacetime._star_covers_all(fs[-1])
+    seq = harness(f, k, r, len(fs), ts)[0]
+    lv = spacetime.stmg_levels(f, k, r, tau=0.1, stop_n=stop_n, pressure="continuous")
+    assert [(a, b) for a, b, _ in seq] == [(l.k, l.r) for l in lv]
+    assert [fs[i].n for _, _, i in seq] == [l.st.space.forest.n for l in lv]
+
+
+@pytest.mark.parametrize("dim,n,ball", [(2, 2, False), (2, 3, False), (3, 2, False), (2, 4, True), (3, 2, True)])
+def test_vertex_star_covering_matches_the_oracle(harness, dim, n, ball):
+    f = _forest(dim, n, ball)
+    harness(f, 2, 0, 1)
+    assert harness.covers_all == spacetime._star_covers_all(f)
 
 
 @pytest.mark.parametrize("dim,n,ball,k", [(2, 4, False, 2), (2, 3, True, 2), (2, 3, False, 3), (3, 2, False, 2),
