@@ -415,6 +415,28 @@ def spacetime_section(api, L, inputs, torch):
     except Exception as e:  # noqa: BLE001 -- reported in the JSON line
         out["error"] = f"{type(e).__name__}: {e}"
     try:
+        # the paper's pair Q2/P1^disc with DG(1), cell patches, on 8^3 cells
+        m = api.Mesh(ctx, 3, 8)
+        st = api.SpaceTime.pdisc(ctx, m, 2, 1.0, 1, 0.05)
+        t0 = time.perf_counter()
+        levels = st.mg_build(nu_s=4, omega=0.7)
+        setup = time.perf_counter() - t0
+        xs = torch.tensor(inputs.uniform_vector(st.Q * st.n, seed=4), device="cuda")
+        b = torch.empty_like(xs)
+        st.vmult(xs, b)
+        x = torch.zeros_like(xs)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        its, rel = st.solve(b, x, tol=1e-10, maxit=200, raise_on_nonconvergence=False)
+        torch.cuda.synchronize()
+        out["stmg_solve_pdisc_8cube_dg1"] = {"entries": st.Q * st.n, "levels": [list(l) for l in levels],
+                                             "setup_s": setup, "iterations": its, "rel_residual": rel,
+                                             "solve_s": time.perf_counter() - t0}
+        st.close()
+        m.close()
+    except Exception as e:  # noqa: BLE001
+        out["pdisc_error"] = f"{type(e).__name__}: {e}"
+    try:
         if ctx is not None:
             ctx.close()
     except Exception as e:  # noqa: BLE001

@@ -359,6 +359,19 @@ int mfns_solve_status(const mfns_problem* p, mfns_solve_info* info);
  * tau times identity rows.  The problem must outlive the slab.  Errors: ARG, UNSUPPORTED, OOM,
  * BUDGET, CUDA. */
 int mfns_spacetime_create(mfns_problem* stokes, int r, double tau, mfns_spacetime** out);
+/* The same slab on the paper's spatial pair Q_k^dim / P^disc_{k-1} (Section 4): velocity of degree
+ * k (2..4) with homogeneous Dirichlet conditions, pressure of total degree k - 1 per cell in the
+ * monomials of the cell's centred, scaled coordinates (graded order), no continuity; the symmetric
+ * form nu (grad u, grad v) - (p, div v) - (div u, q).  Uniform meshes only (MFNS_ERR_UNSUPPORTED
+ * otherwise), FP64 only.  Spatial vector: the velocity block (nodes of the (k n + 1)^dim grid,
+ * lexicographic, dim interleaved components) then npc coefficients per cell (lexicographic cells).
+ * The slab owns its spatial operators; the mesh may be destroyed afterwards. */
+int mfns_spacetime_create_pdisc(mfns_ctx* ctx, const mfns_mesh* mesh, int k, double nu, int r, double tau,
+                                mfns_spacetime** out);
+/* Support point and field of every spatial entry of the slab (host arrays of n_stage entries, xyz 3
+ * per entry, z = 0 in 2D): field < dim velocity, dim pressure (Taylor--Hood), dim + a the
+ * coefficient a of the cell's pressure polynomial at the cell centre (P^disc). */
+int mfns_spacetime_support_points(const mfns_spacetime* st, double* xyz_host, int* field_host);
 /* Stage count, spatial vector length and (host arrays, may be NULL) the Q temporal nodes on
  * [0, 1] and G_Q (Q x Q, row-major). */
 int mfns_spacetime_info(const mfns_spacetime* st, int* stages, int64_t* n_stage, double* nodes_host,

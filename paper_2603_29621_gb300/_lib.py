@@ -99,6 +99,9 @@ _SIGS = {
     "mfns_batch_vcycle": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.c_int, C.POINTER(C.c_void_p),
                                     C.POINTER(C.c_void_p), C.c_void_p]),
     "mfns_spacetime_create": (C.c_int, [C.c_void_p, C.c_int, C.c_double, C.POINTER(C.c_void_p)]),
+    "mfns_spacetime_create_pdisc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_double, C.c_int, C.c_double,
+                                              C.POINTER(C.c_void_p)]),
+    "mfns_spacetime_support_points": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "mfns_spacetime_info": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int64), C.c_void_p,
                                       C.c_void_p]),
     "mfns_spacetime_vmult": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),

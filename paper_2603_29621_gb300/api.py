@@ -294,11 +294,14 @@ class SpaceTime:
     """One time slab (Section 4) on the Taylor--Hood space of a Stokes problem: DG(r) in time,
     stage-major vectors of length Q * n."""
 
-    def __init__(self, problem, r, tau):
+    def __init__(self, problem, r, tau, _handle=None, _lib=None):
         self.problem = problem                       # kept alive: the slab refers to it
-        self.lib = problem.lib
+        self.lib = problem.lib if problem is not None else _lib
         h = C.c_void_p()
-        L.check(self.lib.mfns_spacetime_create(problem.h, r, tau, C.byref(h)))
+        if _handle is None:
+            L.check(self.lib.mfns_spacetime_create(problem.h, r, tau, C.byref(h)))
+        else:
+            h = _handle
         self.h = h
         Q, n = C.c_int(), C.c_int64()
         self.nodes = np.zeros(r + 1)
@@ -306,6 +309,20 @@ class SpaceTime:
         L.check(self.lib.mfns_spacetime_info(h, C.byref(Q), C.byref(n), self.nodes.ctypes.data_as(C.c_void_p),
                                              self.G.ctypes.data_as(C.c_void_p)))
         self.Q, self.n = Q.value, n.value
+
+    @classmethod
+    def pdisc(cls, ctx, mesh, k, nu, r, tau):
+        """A slab on the Q_k / P^disc_{k-1} pair (uniform meshes, FP64); owns its spatial operators."""
+        h = C.c_void_p()
+        L.check(ctx.lib.mfns_spacetime_create_pdisc(ctx.h, mesh.h, k, nu, r, tau, C.byref(h)))
+        return cls(None, r, tau, _handle=h, _lib=ctx.lib)
+
+    def support_points(self):
+        xyz = np.zeros((self.n, 3))
+        fld = np.zeros(self.n, dtype=np.int32)
+        L.check(self.lib.mfns_spacetime_support_points(self.h, xyz.ctypes.data_as(C.c_void_p),
+                                                       fld.ctypes.data_as(C.c_void_p)))
+        return xyz, fld
 
     def vmult(self, src, dst, stream=None):
         prec = L.FP64 if src.dtype == torch.float64 else L.FP32

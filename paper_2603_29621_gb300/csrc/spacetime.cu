@@ -12,6 +12,8 @@
 
 #include "capi_types.hpp"
 #include "op_launch.hpp"
+#include "pdisc.hpp"
+#include "pdisc_dev.hpp"
 #include "spacetime.hpp"
 #include "vec.hpp"
 
@@ -128,7 +130,14 @@ namespace mfns {
 // One level of the space-time multigrid (finest first).
 struct StmgLevel {
   int k = 2, r = 0, Q = 1;
-  std::unique_ptr<OpLevel> A, M, P;  // Taylor--Hood system, velocity mass, pressure space (transfers)
+  // kind 0 (Taylor--Hood): A the Stokes system, P the pressure space (transfers); kind 1
+  // (Q_k / P^disc_{k-1}, uniform meshes): A the velocity block (vector Laplacian), with the cell
+  // block B of the pressure coupling and the pressure embedding Ep towards the next coarser level
+  int kind = 0;
+  std::unique_ptr<OpLevel> A, M, P;  // A, velocity mass, pressure space
+  PdiscGeom pg;
+  DevBuf Bcell, Ep;
+  bool ep_hstep = false;
   TemporalMatrices T;
   int64_t n = 0;
   // transfer to the next coarser level: 0 none (coarsest), 1 temporal, 2 spatial
@@ -162,7 +171,11 @@ struct Stmg {
 }  // namespace mfns
 
 struct mfns_spacetime {
-  mfns_problem* problem = nullptr;  // not owned; outlives the slab
+  mfns_ctx* ctx = nullptr;
+  mfns::Budget* bud = nullptr;
+  mfns_problem* problem = nullptr;  // Taylor--Hood slabs: not owned, outlives the slab
+  std::unique_ptr<mfns::StmgLevel> top;  // P^disc slabs: the slab's own space (FP64)
+  double nu = 1.0;                       // P^disc slabs: viscosity
   int r = 0, Q = 1;
   double tau = 0.0;
   mfns::TemporalMatrices T;
@@ -203,12 +216,77 @@ static void slab_vmult(const OpLevel& A, const OpLevel& M, const std::vector<dou
   MFNS_CUDA(cudaGetLastError());
 }
 
+// spatial P^disc Stokes operator on one vector: y_u = A_uu x_u + B^T x_p (identity rows on Dirichlet
+// velocity entries), y_p = B x_u
+static void pdisc_spatial(const StmgLevel& L, const double* x, double* y, cudaStream_t s) {
+  oplevel_vmult(*L.A, 0, x, y, s);
+  pdisc_grad_add(L.pg, L.Bcell.as<double>(), x, y, s);
+  pdisc_div(L.pg, L.Bcell.as<double>(), x, y, s);
+}
+
+// y = (G (x) M + tau I (x) A_pd) x on the Q stages of a P^disc level
+static void slab_vmult_pdisc(const StmgLevel& L, double tau, void* mx, const double* x, double* y, cudaStream_t s) {
+  const int64_t n = L.n;
+  for (int q = 0; q < L.Q; ++q) pdisc_spatial(L, x + (int64_t)q * n, y + (int64_t)q * n, s);
+  MFNS_CUDA(cudaMemsetAsync(mx, 0, (size_t)L.Q * n * 8, s));
+  op_apply_cols(L.M->L, 0, x, mx, L.Q, n, s);
+  const int64_t nc = (int64_t)L.M->constrained_host.size();
+  for (int q = 0; q < L.Q; ++q)
+    vset_idx<double>((double*)mx + (int64_t)q * n, 0.0, L.M->constrained.as<int32_t>(), nc, s);
+  StageMatrix G{};
+  for (int q = 0; q < L.Q; ++q)
+    for (int j = 0; j < L.Q; ++j) G.g[q][j] = L.T.G[q * L.Q + j];
+  const int64_t total = (int64_t)L.Q * n;
+  k_stage_mix<double><<<stream_grid(total), 256, 0, s>>>(y, (const double*)mx, G, L.Q, n, tau);
+  MFNS_CUDA(cudaGetLastError());
+}
+
 static void st_vmult(mfns_spacetime& st, int prec, const void* x, void* y, cudaStream_t s) {
+  if (st.top) {
+    if (prec != 0) throw Error(kErrUnsupported, "P^disc slabs: FP64 only");
+    return slab_vmult_pdisc(*st.top, st.tau, st.top->vmx.get(), (const double*)x, (double*)y, s);
+  }
   slab_vmult(*st.problem->p->system, *st.mass, st.T.G, st.Q, st.tau, st.n, st.mx[prec].get(), prec, x, y, s);
+}
+
+// the P^disc space of one level: velocity block, velocity mass, cell block
+static void build_pdisc_level(StmgLevel& L, const Forest& f, int k, double nu, Budget* bud) {
+  if (!f.uniform()) throw Error(kErrUnsupported, "P^disc spaces: uniform meshes only");
+  if (k < 2 || k > 4) throw Error(kErrUnsupported, "P^disc spaces: velocity degree 2..4");
+  Physics ph;
+  ph.nu = nu;
+  ph.div_sign = -1.0;
+  L.kind = 1;
+  L.A = std::make_unique<OpLevel>();
+  build_oplevel(*L.A, f, OP_STOKES_A, k, ph, bud);
+  L.M = std::make_unique<OpLevel>();
+  build_oplevel(*L.M, f, OP_VMASS, k, ph, bud);
+  L.pg.dim = f.dim;
+  L.pg.k = k;
+  L.pg.n = f.n;
+  L.pg.npc = (int)pdisc_exponents(f.dim, k - 1).size();
+  L.pg.n_main = L.A->n_main_dofs;
+  const int64_t n_cells = (int64_t)f.n_cells();
+  L.n = L.A->n_main_dofs + n_cells * L.pg.npc;
+  L.Bcell = upload(bud, pdisc_cell_B(f.dim, k, 1.0 / f.n));
+}
+
+static void level_support(const StmgLevel& L, double* xyz, int* field) {
+  oplevel_support(*L.A, xyz, field);  // Taylor--Hood: every entry; P^disc: the velocity entries
+  if (L.kind == 0) return;
+  const Forest& f = L.A->forest;
+  const int dim = f.dim;
+  for (size_t c = 0; c < f.n_cells(); ++c)
+    for (int a = 0; a < L.pg.npc; ++a) {
+      const int64_t i = L.pg.n_main + (int64_t)c * L.pg.npc + a;
+      for (int d = 0; d < 3; ++d) xyz[3 * i + d] = d < dim ? (f.crd[3 * c + d] + 0.5) / f.n : 0.0;
+      field[i] = dim + a;  // coefficient a of the cell's pressure
+    }
 }
 
 // ---------------------------------------------------------------- space-time multigrid (FP64)
 static void level_vmult(Stmg& mg, StmgLevel& L, const double* x, double* y, cudaStream_t s) {
+  if (L.kind == 1) return slab_vmult_pdisc(L, mg.tau, L.vmx.get(), x, y, s);
   slab_vmult(*L.A, *L.M, L.T.G, L.Q, mg.tau, L.n, L.vmx.get(), 0, x, y, s);
 }
 
@@ -218,9 +296,25 @@ static void build_schwarz(Stmg& mg, StmgLevel& L, Budget* bud, cudaStream_t s) {
   const OpLevel& A = *L.A;
   const int64_t n = L.n;
   const int Q = L.Q;
-  const std::vector<std::vector<int32_t>> patches = vertex_star_patches(A.forest, A.nu, A.np);
+  // Taylor--Hood: vertex stars, coloured by the cells they reach; P^disc: one cell per patch, coloured
+  // by the cell coordinates modulo 3 (the cells reached from two patches of a colour -- each cell
+  // and its neighbours -- do not meet)
+  std::vector<std::vector<int32_t>> patches;
   std::vector<int32_t> colour;
-  const int ncol = colour_patches_for_probing(A.forest, A.nu, A.np, patches, colour);
+  int ncol = 0;
+  if (L.kind == 0) {
+    patches = vertex_star_patches(A.forest, A.nu, A.np);
+    ncol = colour_patches_for_probing(A.forest, A.nu, A.np, patches, colour);
+  } else {
+    const int dim = L.pg.dim, nm = L.pg.n;
+    patches = pdisc_cell_patches(dim, nm, L.pg.k);
+    colour.resize(patches.size());
+    for (size_t c = 0; c < patches.size(); ++c) {
+      const int cx = (int)(c % nm), cy = (int)((c / nm) % nm), cz = dim == 3 ? (int)(c / ((size_t)nm * nm)) : 0;
+      colour[c] = (cx % 3) + 3 * (cy % 3) + 9 * (cz % 3);
+    }
+    ncol = dim == 3 ? 27 : 9;
+  }
   std::vector<std::vector<int32_t>> members(ncol);
   for (size_t p = 0; p < patches.size(); ++p) members[colour[p]].push_back((int32_t)p);
   std::vector<std::pair<int, int>> cols;  // (colour, local index)
@@ -249,7 +343,11 @@ static void build_schwarz(Stmg& mg, StmgLevel& L, Budget* bud, cudaStream_t s) {
         if ((size_t)m < patches[p].size()) Xh[(size_t)j * n + patches[p][m]] = 1.0;
     }
     MFNS_CUDA(cudaMemcpyAsync(X.get(), Xh.data(), (size_t)n * nb * 8, cudaMemcpyHostToDevice, s));
-    oplevel_vmult_cols(A, 0, X.get(), YA.get(), nb, s);
+    if (L.kind == 0) {
+      oplevel_vmult_cols(A, 0, X.get(), YA.get(), nb, s);
+    } else {
+      for (int j = 0; j < nb; ++j) pdisc_spatial(L, X.as<double>() + (int64_t)j * n, YA.as<double>() + (int64_t)j * n, s);
+    }
     MFNS_CUDA(cudaMemsetAsync(YM.get(), 0, (size_t)n * nb * 8, s));
     op_apply_cols(L.M->L, 0, X.get(), YM.get(), nb, n, s);
     MFNS_CUDA(cudaMemcpyAsync(Ya.data(), YA.get(), (size_t)n * nb * 8, cudaMemcpyDeviceToHost, s));
@@ -354,7 +452,11 @@ static void level_prolongate_add(StmgLevel& F, StmgLevel& C, const double* xc, d
     const double* c = xc + (int64_t)q * C.n;
     double* f = xf + (int64_t)q * F.n;
     transfer_prolongate_add(*F.tv, *F.A, *C.A, 0, c, f, s);
-    transfer_prolongate_add(*F.tp, *F.P, *C.P, 0, c + C.A->n_main_dofs, f + F.A->n_main_dofs, s);
+    if (F.kind == 1)
+      pdisc_prolongate_add(F.pg.dim, F.pg.n, F.pg.npc, C.pg.npc, F.ep_hstep, F.Ep.as<double>(), c + C.pg.n_main,
+                           f + F.pg.n_main, s);
+    else
+      transfer_prolongate_add(*F.tp, *F.P, *C.P, 0, c + C.A->n_main_dofs, f + F.A->n_main_dofs, s);
   }
 }
 
@@ -367,9 +469,14 @@ static void level_restrict(StmgLevel& F, StmgLevel& C, const double* rf, double*
   for (int q = 0; q < F.Q; ++q) {
     const double* f = rf + (int64_t)q * F.n;
     double* c = rc + (int64_t)q * C.n;
-    // velocity first: it clears the whole coarse vector of the stage; the pressure block follows
+    // velocity first: on Taylor--Hood levels it clears the whole coarse vector of the stage; the
+    // pressure block follows
     transfer_restrict(*F.tv, *F.A, *C.A, 0, f, c, s);
-    transfer_restrict(*F.tp, *F.P, *C.P, 0, f + F.A->n_main_dofs, c + C.A->n_main_dofs, s);
+    if (F.kind == 1)
+      pdisc_restrict(F.pg.dim, F.pg.n, F.pg.npc, C.pg.npc, F.ep_hstep, F.Ep.as<double>(), f + F.pg.n_main,
+                     c + C.pg.n_main, s);
+    else
+      transfer_restrict(*F.tp, *F.P, *C.P, 0, f + F.A->n_main_dofs, c + C.A->n_main_dofs, s);
   }
 }
 
@@ -444,7 +551,7 @@ static int stmg_fgmres(mfns_spacetime& st, const double* b, double* x, double to
   const int64_t N = (int64_t)L.Q * L.n;
   const int m = mg.restart;
   if (!mg.V.get()) {
-    Budget* bud = st.problem->p->bud;
+    Budget* bud = st.bud;
     mg.V.alloc(bud, (size_t)(m + 1) * N * 8);
     mg.Z.alloc(bud, (size_t)m * N * 8);
     mg.w.alloc(bud, (size_t)N * 8);
@@ -529,16 +636,23 @@ static int stmg_fgmres(mfns_spacetime& st, const double* b, double* x, double to
 }
 
 static void build_stmg(mfns_spacetime& st, int nu_s, double omega, int coarse_n, cudaStream_t s) {
-  Problem& P = *st.problem->p;
-  const OpLevel& A0 = *P.system;
+  const bool pd = st.top != nullptr;  // P^disc slab (else Taylor--Hood on st.problem)
+  Budget* bud = st.bud;
+  const OpLevel& A0 = pd ? *st.top->A : *st.problem->p->system;
+  const Physics phys = pd ? Physics() : st.problem->p->phys;
+  const int k0 = pd ? st.top->k : A0.k;
   if (!A0.forest.uniform()) throw Error(kErrUnsupported, "space-time multigrid: uniform meshes only");
   if (nu_s < 1 || !(omega > 0.0) || coarse_n < 2)
     throw Error(kErrArg, "space-time multigrid: nu_s >= 1, omega > 0 and coarse_n >= 2");
   std::vector<Forest> fs{A0.forest};
-  while (forest_can_coarsen(fs.back(), coarse_n)) fs.push_back(forest_coarsen(fs.back()));
-  // temporal steps on the coarsest mesh unless a vertex star there holds every cell
-  const std::vector<StLevelSpec> seq =
-      stmg_sequence(A0.k, st.r, (int)fs.size(), !vertex_star_covers_all(fs.back()));
+  while (forest_can_coarsen(fs.back(), coarse_n)) {
+    if (pd && fs.back().n % 2 != 0)
+      throw Error(kErrUnsupported, "space-time multigrid with P^disc: nested coarsening (even cell counts) only");
+    fs.push_back(forest_coarsen(fs.back()));
+  }
+  // temporal steps on the coarsest mesh, unless (vertex stars) a star there holds every cell
+  const bool time_steps = pd || !vertex_star_covers_all(fs.back());
+  const std::vector<StLevelSpec> seq = stmg_sequence(k0, st.r, (int)fs.size(), time_steps);
   auto mg = std::make_unique<Stmg>();
   mg->nu_s = nu_s;
   mg->omega = omega;
@@ -550,14 +664,18 @@ static void build_stmg(mfns_spacetime& st, int nu_s, double omega, int coarse_n,
     L->Q = sp.r + 1;
     std::string err;
     if (!temporal_matrices(sp.r, L->T, &err)) throw Error(kErrArg, err);
-    L->A = std::make_unique<OpLevel>();
-    build_oplevel(*L->A, fs[sp.forest], OP_STOKES, sp.k, P.phys, P.bud);
-    L->M = std::make_unique<OpLevel>();
-    build_oplevel(*L->M, fs[sp.forest], OP_VMASS, sp.k, P.phys, P.bud);
-    L->n = L->A->n_dofs;
+    if (pd) {
+      build_pdisc_level(*L, fs[sp.forest], sp.k, st.nu, bud);
+    } else {
+      L->A = std::make_unique<OpLevel>();
+      build_oplevel(*L->A, fs[sp.forest], OP_STOKES, sp.k, phys, bud);
+      L->M = std::make_unique<OpLevel>();
+      build_oplevel(*L->M, fs[sp.forest], OP_VMASS, sp.k, phys, bud);
+      L->n = L->A->n_dofs;
+    }
     const size_t qn = (size_t)L->Q * L->n * 8;
     for (DevBuf* v : {&L->vx, &L->vb, &L->vr, &L->vt, &L->vz, &L->vmx}) {
-      v->alloc(P.bud, qn);
+      v->alloc(bud, qn);
       MFNS_CUDA(cudaMemsetAsync(v->get(), 0, qn, s));
     }
     mg->lv.push_back(std::move(L));
@@ -574,17 +692,43 @@ static void build_stmg(mfns_spacetime& st, int nu_s, double omega, int coarse_n,
     } else {
       F.tkind = 2;
       F.tv = std::make_unique<Transfer>();
-      build_transfer(*F.tv, *F.A, *C.A, P.bud);
-      for (StmgLevel* X : {&F, &C})
-        if (!X->P) {
-          X->P = std::make_unique<OpLevel>();
-          build_oplevel(*X->P, X->A->forest, OP_PMASS, X->k - 1, P.phys, P.bud);
+      build_transfer(*F.tv, *F.A, *C.A, bud);
+      if (pd) {
+        const int dim = F.pg.dim;
+        if (F.pg.n == C.pg.n) {  // degree step on one mesh
+          F.ep_hstep = false;
+          F.Ep = upload(bud, pdisc_degree_embedding(dim, F.k - 1, C.k - 1));
+        } else if (F.pg.n == 2 * C.pg.n && F.k == C.k) {  // nested h-step
+          F.ep_hstep = true;
+          std::vector<double> E;
+          for (int child = 0; child < (1 << dim); ++child) {
+            const std::vector<double> e = pdisc_child_embedding(dim, F.k - 1, child);
+            E.insert(E.end(), e.begin(), e.end());
+          }
+          F.Ep = upload(bud, E);
+        } else {
+          throw Error(kErrUnsupported, "P^disc transfer: nested h-steps or degree steps only");
         }
-      F.tp = std::make_unique<Transfer>();
-      build_transfer(*F.tp, *F.P, *C.P, P.bud);
+      } else {
+        for (StmgLevel* X : {&F, &C})
+          if (!X->P) {
+            X->P = std::make_unique<OpLevel>();
+            build_oplevel(*X->P, X->A->forest, OP_PMASS, X->k - 1, phys, bud);
+          }
+        F.tp = std::make_unique<Transfer>();
+        build_transfer(*F.tp, *F.P, *C.P, bud);
+      }
     }
-    build_schwarz(*mg, F, P.bud, s);
+    build_schwarz(*mg, F, bud, s);
   }
+  // free pressure entries of a level: their constant (one per stage) is the null space of K
+  auto pressure_entries = [](const StmgLevel& L) {
+    if (L.kind == 0) return L.A->pres_host;
+    std::vector<int32_t> e;
+    const int64_t cells = (L.n - L.pg.n_main) / L.pg.npc;
+    for (int64_t c = 0; c < cells; ++c) e.push_back((int32_t)(L.pg.n_main + c * L.pg.npc));  // constant monomial
+    return e;
+  };
   // coarsest level: dense operator by unit vectors, plus the constant pressures of every stage
   StmgLevel& C = *mg->lv.back();
   const int64_t N = (int64_t)C.Q * C.n;
@@ -599,7 +743,7 @@ static void build_stmg(mfns_spacetime& st, int nu_s, double omega, int coarse_n,
     MFNS_CUDA(cudaStreamSynchronize(s));
     for (int64_t i = 0; i < N; ++i) K[(size_t)i * N + j] = col[i];
   }
-  const std::vector<int32_t>& pres = C.A->pres_host;
+  const std::vector<int32_t> pres = pressure_entries(C);
   if (!pres.empty()) {
     const double v = 1.0 / double(pres.size());
     for (int q = 0; q < C.Q; ++q)
@@ -607,14 +751,15 @@ static void build_stmg(mfns_spacetime& st, int nu_s, double omega, int coarse_n,
         for (int32_t b : pres) K[(size_t)(q * C.n + a) * N + (q * C.n + b)] += v;
   }
   if (!invert_dense_rel(K, N, 1e-15)) throw Error(kErrArg, "space-time multigrid: singular coarse matrix");
-  mg->cinv = upload(P.bud, K);
+  mg->cinv = upload(bud, K);
   mg->cn = N;
-  mg->pres = upload(P.bud, pres);
+  mg->pres = upload(bud, pres);
   mg->n_pres = (int64_t)pres.size();
-  mg->part.alloc(P.bud, (size_t)kRedBlocks * kMaxDots * 8);
-  mg->scal.alloc(P.bud, 64);
-  mg->pres0 = upload(P.bud, mg->lv[0]->A->pres_host);
-  mg->n_pres0 = (int64_t)mg->lv[0]->A->pres_host.size();
+  mg->part.alloc(bud, (size_t)kRedBlocks * kMaxDots * 8);
+  mg->scal.alloc(bud, 64);
+  const std::vector<int32_t> pres0 = pressure_entries(*mg->lv[0]);
+  mg->pres0 = upload(bud, pres0);
+  mg->n_pres0 = (int64_t)pres0.size();
   MFNS_CUDA(cudaStreamSynchronize(s));
   st.mg = std::move(mg);
 }
@@ -634,6 +779,8 @@ extern "C" int mfns_spacetime_create(mfns_problem* p, int r, double tau, mfns_sp
     if (r < 0 || r + 1 > kMaxStages) return capi_fail(kErrArg, "temporal degree must lie in 0..7");
     MFNS_CUDA(cudaSetDevice(p->ctx->device));
     auto st = std::make_unique<mfns_spacetime>();
+    st->ctx = p->ctx;
+    st->bud = P.bud;
     st->problem = p;
     st->r = r;
     st->Q = r + 1;
@@ -670,7 +817,7 @@ extern "C" int mfns_spacetime_vmult(mfns_spacetime* st, int prec, const void* x,
   try {
     (void)cudaGetLastError();
     if (!st || !x || !y || x == y || (prec != 0 && prec != 1)) return capi_fail(kErrArg, "bad arguments");
-    MFNS_CUDA(cudaSetDevice(st->problem->ctx->device));
+    MFNS_CUDA(cudaSetDevice(st->ctx->device));
     st_vmult(*st, prec, x, y, reinterpret_cast<cudaStream_t>(stream));
   } catch (const Error& e) {
     return capi_fail(e.code, e.what());
@@ -711,7 +858,7 @@ extern "C" int mfns_spacetime_temporal(int r, double* nodes_host, double* m_host
 extern "C" int mfns_spacetime_mg_build(mfns_spacetime* st, int nu_s, double omega, int coarse_n, void* stream) {
   ST_BEGIN
   if (!st) return capi_fail(kErrArg, "bad arguments");
-  MFNS_CUDA(cudaSetDevice(st->problem->ctx->device));
+  MFNS_CUDA(cudaSetDevice(st->ctx->device));
   st->mg.reset();
   build_stmg(*st, nu_s, omega, coarse_n, reinterpret_cast<cudaStream_t>(stream));
   ST_END
@@ -734,7 +881,7 @@ extern "C" int mfns_spacetime_mg_support_points(const mfns_spacetime* st, int le
   ST_BEGIN
   if (!st || !st->mg || level < 0 || level >= (int)st->mg->lv.size() || !xyz_host || !field_host)
     return capi_fail(kErrArg, "bad arguments");
-  oplevel_support(*st->mg->lv[level]->A, xyz_host, field_host);
+  level_support(*st->mg->lv[level], xyz_host, field_host);
   ST_END
 }
 
@@ -747,7 +894,7 @@ extern "C" int mfns_spacetime_mg_apply(mfns_spacetime* st, int level, int what, 
   StmgLevel& L = *mg.lv[level];
   const bool has_coarse = level + 1 < (int)mg.lv.size();
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  MFNS_CUDA(cudaSetDevice(st->problem->ctx->device));
+  MFNS_CUDA(cudaSetDevice(st->ctx->device));
   switch (what) {
     case 0: level_vmult(mg, L, (const double*)in, (double*)out, s); break;
     case 1:
@@ -773,7 +920,7 @@ extern "C" int mfns_spacetime_vcycle(mfns_spacetime* st, const void* b, void* x,
   Stmg& mg = *st->mg;
   StmgLevel& L = *mg.lv[0];
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  MFNS_CUDA(cudaSetDevice(st->problem->ctx->device));
+  MFNS_CUDA(cudaSetDevice(st->ctx->device));
   const size_t bytes = (size_t)L.Q * L.n * 8;
   MFNS_CUDA(cudaMemcpyAsync(L.vb.get(), b, bytes, cudaMemcpyDeviceToDevice, s));
   stmg_cycle(mg, 0, s);
@@ -786,7 +933,7 @@ extern "C" int mfns_spacetime_solve(mfns_spacetime* st, const void* b, void* x, 
   ST_BEGIN
   if (!st || !st->mg || !b || !x || b == x || !(tol > 0.0) || maxit < 1) return capi_fail(kErrArg, "bad arguments");
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  MFNS_CUDA(cudaSetDevice(st->problem->ctx->device));
+  MFNS_CUDA(cudaSetDevice(st->ctx->device));
   double rel = 0.0;
   bool conv = false;
   const int its = stmg_fgmres(*st, (const double*)b, (double*)x, tol, maxit, &rel, &conv, s);
@@ -794,5 +941,44 @@ extern "C" int mfns_spacetime_solve(mfns_spacetime* st, const void* b, void* x, 
   if (relres) *relres = rel;
   if (converged) *converged = conv ? 1 : 0;
   if (!conv) return capi_fail(MFNS_ERR_NOT_CONVERGED, "space-time FGMRES did not reach the tolerance");
+  ST_END
+}
+
+extern "C" int mfns_spacetime_create_pdisc(mfns_ctx* ctx, const mfns_mesh* mesh, int k, double nu, int r, double tau,
+                                           mfns_spacetime** out) {
+  ST_BEGIN
+  if (!ctx || !mesh || !out || !(tau > 0.0) || !(nu > 0.0)) return capi_fail(kErrArg, "bad arguments");
+  *out = nullptr;
+  if (r < 0 || r + 1 > kMaxStages) return capi_fail(kErrArg, "temporal degree must lie in 0..7");
+  MFNS_CUDA(cudaSetDevice(ctx->device));
+  auto st = std::make_unique<mfns_spacetime>();
+  st->ctx = ctx;
+  st->bud = &ctx->budget;
+  st->nu = nu;
+  st->r = r;
+  st->Q = r + 1;
+  st->tau = tau;
+  std::string err;
+  if (!temporal_matrices(r, st->T, &err)) return capi_fail(kErrArg, err.c_str());
+  auto L = std::make_unique<StmgLevel>();
+  L->k = k;
+  L->r = r;
+  L->Q = r + 1;
+  L->T = st->T;
+  build_pdisc_level(*L, mesh->forest, k, nu, st->bud);
+  L->vmx.alloc(st->bud, (size_t)L->Q * L->n * 8);
+  st->n = L->n;
+  st->top = std::move(L);
+  *out = st.release();
+  ST_END
+}
+
+extern "C" int mfns_spacetime_support_points(const mfns_spacetime* st, double* xyz_host, int* field_host) {
+  ST_BEGIN
+  if (!st || !xyz_host || !field_host) return capi_fail(kErrArg, "bad arguments");
+  if (st->top)
+    level_support(*st->top, xyz_host, field_host);
+  else
+    oplevel_support(*st->problem->p->system, xyz_host, field_host);
   ST_END
 }
