@@ -181,7 +181,27 @@ def solve_section(api, L, inputs, torch, tol_ns=1e-13, tol_stokes=1e-14):
         r = {"mg": "fp32" if mgp else "fp64", "hierarchy": "local_smoothing" if hierarchy else "global_coarsening",
              "nu": nu, "dofs": p.info.n_dofs, "cells": p.info.n_cells,
              "levels": p.info.n_levels, "iterations": info.iterations, "rel_residual": info.rel_residual,
-             "converged": bool(info.converged), "solve_s": dt_solve, "setup_s": setup, "error_vs_xstar": err}
+             "converged": bool(info.converged), "solve_s": dt_solve, "setup_s": setup, "error_vs_xstar": err,
+             # the single-device counterpart of the paper's load metrics: the work on every level
+             "level_cells": [int(p.info.level_cells[i]) for i in range(p.info.n_levels)],
+             "level_dofs": [int(p.info.level_dofs[i]) for i in range(p.info.n_levels)]}
+        try:  # one multigrid cycle in the preconditioner's precision (device time, warm)
+            vb = torch.tensor(inputs.uniform_vector(int(p.info.level_dofs[0]), seed=6), device="cuda",
+                              dtype=torch.float32 if mgp == L.FP32 else torch.float64)
+            vx = torch.zeros_like(vb)
+            for _ in range(3):
+                p.vcycle(vb, vx)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(10):
+                p.vcycle(vb, vx)
+            e1.record()
+            e1.synchronize()
+            r["cycle_ms"] = e0.elapsed_time(e1) / 10
+        except Exception as e:  # noqa: BLE001
+            r["cycle_ms_error"] = f"{type(e).__name__}: {e}"
+
         if mgp == L.FP32 and not hierarchy:  # the system operator's apply (indexed cells, hanging nodes)
             for prec, vec in (("fp64", xs), ("fp32", xs.float())):
                 out_v = torch.empty_like(vec)
@@ -302,7 +322,8 @@ def _guarded_solve(api, L, inputs, torch, ctx, build, pslice):
     xr[ps] -= xr[ps].mean()
     r = {"dofs": p.info.n_dofs, "cells": p.info.n_cells, "levels": p.info.n_levels, "iterations": info.iterations,
          "rel_residual": info.rel_residual, "converged": bool(info.converged), "solve_s": dt_solve,
-         "setup_s": setup, "error_vs_xstar": float(torch.linalg.norm(d) / torch.linalg.norm(xr))}
+         "setup_s": setup, "error_vs_xstar": float(torch.linalg.norm(d) / torch.linalg.norm(xr)),
+         "level_cells": [int(p.info.level_cells[i]) for i in range(p.info.n_levels)]}
     p.close()
     m.close()
     return r
