@@ -445,6 +445,82 @@ bool make_hp_space(const Forest& f, const std::vector<int32_t>& degree, HpSpace&
   return eliminate_constraints(f, degree, gll, dom, entity, latt, dirichlet, out, err);
 }
 
+std::vector<std::vector<int32_t>> hp_asm_blocks(const Forest& f, const HpSpace& sp, int ncomp) {
+  const int dim = f.dim;
+  const int L = f.max_level();
+  const int64_t N = (int64_t)f.n << L;
+  const Lattice latt = make_lattice(f);
+  std::vector<char> hang(sp.n_nodes, 0);
+  for (int32_t g : sp.hang_node) hang[g] = 1;
+  // combined faces, found from their finer side: (coarse cell, direction, side of the coarse cell)
+  std::vector<std::array<int64_t, 3>> faces;
+  for (size_t a = 0; a < f.n_cells(); ++a) {
+    const int64_t sa = int64_t(1) << (L - f.lev[a]);
+    for (int d = 0; d < dim; ++d)
+      for (int side = 0; side < 2; ++side) {
+        const int64_t q = (f.crd[3 * a + d] + side) * sa;
+        if (q == 0 || q == N) continue;
+        int64_t pos[3] = {0, 0, 0};
+        for (int j = 0; j < dim; ++j) pos[j] = f.crd[3 * a + j] * sa;
+        pos[d] = side ? q : q - 1;
+        const int32_t b = latt.at((int)pos[0], (int)pos[1], (int)pos[2]);
+        if (b < 0 || f.lev[b] >= f.lev[a] || sp.degree[b] <= sp.degree[a]) continue;
+        faces.push_back({b, d, 1 - side});
+      }
+  }
+  std::sort(faces.begin(), faces.end());
+  faces.erase(std::unique(faces.begin(), faces.end()), faces.end());
+  std::vector<std::vector<int32_t>> out;
+  for (const auto& fc : faces) {
+    const int32_t c = (int32_t)fc[0];
+    const int d = (int)fc[1], side = (int)fc[2];
+    const int64_t sc = int64_t(1) << (L - f.lev[c]);
+    const double plane = double((f.crd[3 * c + d] + side) * sc) / double(N);
+    double lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+    for (int j = 0; j < dim; ++j) {
+      lo[j] = double(f.crd[3 * c + j] * sc) / double(N);
+      hi[j] = double((f.crd[3 * c + j] + 1) * sc) / double(N);
+    }
+    // cells holding nodes of the face: the coarse cell and the cells just across it
+    std::vector<int32_t> cells{c};
+    const int64_t q = (f.crd[3 * c + d] + side) * sc;
+    const int64_t across = side ? q : q - 1;
+    int64_t r0[3] = {0, 0, 0}, r1[3] = {1, 1, 1};
+    for (int j = 0; j < dim; ++j) {
+      r0[j] = f.crd[3 * c + j] * sc;
+      r1[j] = (f.crd[3 * c + j] + 1) * sc;
+    }
+    r0[d] = across;
+    r1[d] = across + 1;
+    if (across >= 0 && across < N)
+      for (int64_t z = r0[2]; z < (dim == 3 ? r1[2] : 1); ++z)
+        for (int64_t y = r0[1]; y < r1[1]; ++y)
+          for (int64_t x = r0[0]; x < r1[0]; ++x) cells.push_back(latt.at((int)x, (int)y, (int)z));
+    std::sort(cells.begin(), cells.end());
+    cells.erase(std::unique(cells.begin(), cells.end()), cells.end());
+    std::vector<int32_t> nodes;
+    for (int32_t cc : cells) {
+      if (cc < 0) continue;
+      for (int64_t j = sp.cell_ptr[cc]; j < sp.cell_ptr[cc + 1]; ++j) {
+        const int32_t g = sp.cell_nodes[j];
+        if (sp.boundary[g] || hang[g]) continue;
+        bool on = std::fabs(sp.x[g * dim + d] - plane) <= 1e-12;
+        for (int jj = 0; jj < dim && on; ++jj)
+          if (sp.x[g * dim + jj] < lo[jj] - 1e-12 || sp.x[g * dim + jj] > hi[jj] + 1e-12) on = false;
+        if (on) nodes.push_back(g);
+      }
+    }
+    std::sort(nodes.begin(), nodes.end());
+    nodes.erase(std::unique(nodes.begin(), nodes.end()), nodes.end());
+    std::vector<int32_t> blk;
+    for (int32_t g : nodes)
+      for (int comp = 0; comp < ncomp; ++comp) blk.push_back((int32_t)(g * ncomp + comp));
+    std::sort(blk.begin(), blk.end());
+    if (!blk.empty()) out.push_back(std::move(blk));
+  }
+  return out;
+}
+
 int hp_color_cells(const HpSpace& sp, const std::vector<int32_t>& cells, std::vector<int32_t>& color) {
   // node -> subset positions (compressed rows)
   std::vector<int64_t> ptr(sp.n_nodes + 1, 0);

@@ -63,4 +63,11 @@ int hp_color_cells(const HpSpace& sp, const std::vector<int32_t>& cells, std::ve
 int hp_probe_groups(const HpSpace& sp, const std::vector<char>& free_node, std::vector<int32_t>& group,
                     bool dirichlet = true);
 
+// Blocks of the additive Schwarz part of Section 3's blended smoother: for every combined h+p face
+// (a cell face whose neighbours across it are finer and of lower degree), the free nodes (not
+// constrained, not on the Dirichlet boundary) lying on the closed face of the coarse cell, each with
+// its ncomp components (entries g * ncomp + c).  Entries ascending; faces in (cell, direction,
+// side) order; faces without free nodes give no block.
+std::vector<std::vector<int32_t>> hp_asm_blocks(const Forest& f, const HpSpace& sp, int ncomp);
+
 }  // namespace mfns

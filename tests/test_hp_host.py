@@ -98,6 +98,12 @@ int main() {
     for (int j = sp.hang_ptr[i]; j < sp.hang_ptr[i + 1]; ++j) std::printf(" %d %.17g", sp.hang_master[j], sp.hang_w[j]);
     std::printf("\n");
   }
+  auto blocks = hp_asm_blocks(f, sp, dim);
+  std::printf("ASM %zu\n", blocks.size());
+  for (auto& b : blocks) {
+    for (int32_t i : b) std::printf("%d ", i);
+    std::printf("\n");
+  }
   return 0;
 }
 """
@@ -131,6 +137,10 @@ def harness(tmp_path_factory):
             t = out[i + 1 + j].split()
             g, m = int(t[0]), int(t[1])
             hang[g] = [(int(t[2 + 2 * q]), float(t[3 + 2 * q])) for q in range(m)]
+        i += 1 + nh
+        nblk = int(out[i].split()[1])
+        run.asm = [[int(v) for v in out[i + 1 + j].split()] for j in range(nblk)]
+        run.x = x
         return x, bnd, hang
     return run
 
@@ -226,3 +236,24 @@ def test_the_local_rule_stays_in_use_where_it_applies(harness):
     deg = _degrees(f, 1)
     x, bnd, hang = harness(f, deg, rule=0)
     assert any(bnd[g] for g in hang)
+
+
+@pytest.mark.parametrize("dim,n,kind", [(2, 4, "3-2"), (2, 3, "4-2"), (3, 2, "3-2"), (3, 3, "3-2")])
+def test_asm_blocks_match_the_oracle(harness, dim, n, kind):
+    """The blocks of Section 3's blended smoother: for every combined face, the free unknowns on the
+    closed face of its coarse cell (all components) -- the oracle's blocks, entry by entry."""
+    f = mesh.refine_ball(mesh.uniform(dim, n), (0.3, 0.35, 0.4), 0.3, 1)
+    deg = _combined(f, kind)
+    got = harness(f, deg, rule=0)
+    assert not isinstance(got, str), got
+    x = harness.x
+    P = hp.HpProblem(f, deg, "stokes_a", rule="elimination")
+    ns = P.dofs.nodesets[0]
+    key = lambda xx, c: (tuple(np.rint(np.asarray(xx) * 2 ** 30).astype(np.int64)), int(c))
+    mine = {frozenset(key(x[i // dim], i % dim) for i in b) for b in harness.asm}
+    ref = set()
+    for B in hp.asm_blocks(P):
+        g, c = (B - P.dofs.offsets[0]) % ns.n_nodes, (B - P.dofs.offsets[0]) // ns.n_nodes
+        ref.add(frozenset(key(ns.x[gg], cc) for gg, cc in zip(g, c)))
+    assert len(ref) > 0 and mine == ref
+    assert len(harness.asm) == len(hp.asm_blocks(P))
