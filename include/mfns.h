@@ -101,7 +101,12 @@ typedef struct {
   double div_sign;      /* sign of the continuity row; 0 = default (STOKES -1, STAB_NS +1) */
   int smoother;         /* 0 = default for the kind: STAB_NS relaxation around point Jacobi (Section 5,
                            Exp. 3), otherwise Chebyshev around point Jacobi (Section 3);
-                           1 = Chebyshev, 2 = Jacobi relaxation */
+                           1 = Chebyshev, 2 = Jacobi relaxation; 3 = Chebyshev around the blend of
+                           Section 3 on the hp levels that have faces h-refined on one side and
+                           p-refined on the other: additive Schwarz blocks there (the free unknowns
+                           on the closed face of the coarse cell, block inverses summed where blocks
+                           overlap), point Jacobi on the unknowns in no block; Chebyshev around point
+                           Jacobi on every other level */
   int smoother_degree;  /* Chebyshev degree / relaxation sweeps; 0 = default (5) */
   int mg_order;         /* 0 default (STOKES_A: p then h; STAB_NS: h then p), 1 p_then_h, 2 h_then_p */
   int mg_precision;     /* MFNS_FP64 or MFNS_FP32: precision of the multigrid preconditioner */

@@ -160,8 +160,9 @@ int mfns_problem_create(mfns_ctx* ctx, const mfns_mesh* mesh, const mfns_problem
 // settings, workspaces, autotuning, smoother bounds and the coarse solver of a built problem
 static int finish_problem(mfns_ctx* ctx, const mfns_problem_desc* desc, std::unique_ptr<Problem> p, size_t used0,
                           mfns_problem** out) {
-  if (desc->smoother < 0 || desc->smoother > 2) return fail(MFNS_ERR_ARG, "smoother must be 0, 1 or 2");
-  // internal: 0 = Chebyshev, 1 = Jacobi relaxation
+  if (desc->smoother < 0 || desc->smoother > 3) return fail(MFNS_ERR_ARG, "smoother must be 0, 1, 2 or 3");
+  // internal: 0 = Chebyshev, 1 = Jacobi relaxation, 2 = Chebyshev around Jacobi + Schwarz blocks on
+  // the combined faces of hp levels (Chebyshev around Jacobi on the other levels)
   p->smoother = desc->smoother == 0 ? (desc->kind == MFNS_STAB_NS ? 1 : 0) : desc->smoother - 1;
   p->smoother_degree = desc->smoother_degree > 0 ? desc->smoother_degree : 5;
   p->mg_precision = desc->mg_precision;

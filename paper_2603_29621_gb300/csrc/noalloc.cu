@@ -79,6 +79,7 @@ extern "C" int mfns_smooth_noalloc(mfns_problem* p, int level, int precision, co
     if (!p || level < 0 || level >= (int)p->p->levels.size() || !b || !x || (precision != 0 && precision != 1))
       return capi_fail(kErrArg, "bad arguments");
     if (p->p->ls) return capi_fail(kErrUnsupported, "single-level smoothing is not exposed for local smoothing");
+    if (p->p->smoother == 2) return capi_fail(kErrUnsupported, "the no-allocation smoother is point-Jacobi based");
     const int64_t n = p->p->levels[level]->n_dofs;
     if (n > kMaxEntries)
       return capi_fail(kErrArg, ("mfns_smooth_noalloc: level has " + std::to_string(n) +

@@ -77,6 +77,16 @@ struct HpData {
   // exact diagonal by probing: free dofs in groups that share no cell after the constraints
   std::vector<int64_t> probe_ptr;
   DevBuf probe_dofs;
+  // Section 3's blended smoother (built on request): additive Schwarz blocks on the combined faces,
+  // point Jacobi on the entries in no block
+  struct Asm {
+    int64_t n_block = 0, max_block = 0;
+    DevBuf b_ptr, b_idx, k_ptr, kinv[2];  // blocks (entries), inverses of A_BB (row-major, FP64 / FP32)
+    DevBuf e_ptr, e_base;                 // per entry: the block results to add (indices into zloc)
+    DevBuf jdinv[2];                      // 1 / A_ii on entries in no block, 0 on block entries
+    DevBuf zloc[2];                       // block results
+  };
+  std::unique_ptr<Asm> asm_;
 };
 // op: OP_STOKES_A (vector Laplacian, degree per cell), OP_STOKES (Taylor--Hood: velocity degree per
 // cell, pressure one lower) or OP_PMASS (scalar mass, degree per cell)
@@ -88,6 +98,11 @@ void hp_diag(const OpLevel& lv, int prec, void* diag, cudaStream_t s);
 void hp_condense(const OpLevel& lv, int prec, void* y, cudaStream_t s);
 // x[slave] = sum of w * x[master] for every constrained (non-Dirichlet) entry
 void hp_distribute(const OpLevel& lv, int prec, void* x, cudaStream_t s);
+// the blended smoother's blocks of an hp level of the vector Laplacian (lv.dinv[0] must hold the
+// diagonal inverse); no-op on a level without combined faces
+void build_hp_asm(OpLevel& lv, Budget* bud, cudaStream_t s);
+// z = P^{-1} r of the blended smoother (requires lv.hp->asm_)
+void hp_asm_apply(const OpLevel& lv, int prec, const void* r, void* z, cudaStream_t s);
 
 // edge_dirichlet (level forests of local smoothing): nodes on the refinement edge are constrained
 // like Dirichlet nodes (identity rows, zero in the operator's input)

@@ -422,6 +422,11 @@ void estimate_lambda(Problem& p, cudaStream_t s) {
   }
   // diagonals, then the Arnoldi estimate of lambda_max(D^{-1} A) per level
   for (auto& lv : p.levels) level_dinv(p, *lv, s);
+  // Section 3's blended smoother: Schwarz blocks on the combined faces of hp levels (the estimate
+  // below is then of lambda_max(P^{-1} A))
+  if (p.smoother == 2)
+    for (auto& lv : p.levels)
+      if (lv->hp && !lv->hp->asm_) build_hp_asm(*lv, p.bud, s);
   // lambda_max of D^{-1} A per level: Arnoldi (classical Gram--Schmidt twice) in FP64 from a
   // seeded random start; the estimate is the spectral radius rho of the m x m Hessenberg matrix
   // (the modulus of its largest Ritz value), times 1.2 for the Chebyshev smoother.  The
@@ -487,7 +492,10 @@ double arnoldi_spectral_radius(Problem& p, OpLevel& lv, cudaStream_t s,
   int mm = 0;
   for (int j = 0; j < m; ++j) {
     oplevel_vmult(lv, 0, V + (size_t)j * stride, p.tmp.get(), s);
-    vmul<double>(w, dinv, p.tmp.as<double>(), n, s);
+    if (lv.hp && lv.hp->asm_)
+      hp_asm_apply(lv, 0, p.tmp.get(), w, s);
+    else
+      vmul<double>(w, dinv, p.tmp.as<double>(), n, s);
     double* hd = p.hvec.as<double>();
     multidot(hd, nullptr, w, j + 1, n, p.part.as<double>(), Vp, s);
     multi_axpy(w, Vp, hd, j + 1, n, s);
@@ -610,6 +618,29 @@ static void smooth_op(const Problem& p, OpLevel& lv, Workspace& w, int prec, con
     cur = out;
   };
   const double lmax = lv.lmax, lmin = lmax / 20.0;
+  if (lv.hp && lv.hp->asm_) {  // Chebyshev around the blended preconditioner (Section 3)
+    T* r = w.r.as<T>();
+    const double theta = 0.5 * (lmax + lmin), delta = 0.5 * (lmax - lmin), sigma = theta / delta;
+    double rho_old = 1.0 / sigma;
+    for (int j = 0; j < degree; ++j) {
+      if (j == 0 && x_is_zero) {
+        vzero<T>(x, n, s);
+        hp_asm_apply(lv, prec, b, t, s);
+      } else {
+        oplevel_vmult(lv, prec, x, t, s);
+        vsub<T>(r, b, t, n, s);
+        hp_asm_apply(lv, prec, r, t, s);
+      }
+      if (j == 0) {
+        vcheby_pre<T>(x, d, t, (T)0, (T)(1.0 / theta), n, s);
+      } else {
+        const double rho = 1.0 / (2.0 * sigma - rho_old);
+        vcheby_pre<T>(x, d, t, (T)(rho * rho_old), (T)(2.0 * rho / delta), n, s);
+        rho_old = rho;
+      }
+    }
+    return;
+  }
   if (p.smoother == 1) {  // Jacobi relaxation
     const T omega = (T)(2.0 / (lmin + lmax));
     for (int it = 0; it < degree; ++it) {

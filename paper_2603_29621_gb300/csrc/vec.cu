@@ -113,6 +113,13 @@ __global__ void k_cheby(T* x, T* d, const T* b, const T* ax, const T* dinv, T c1
     x[i] += di;
   }
 }
+template <typename T> __global__ void k_cheby_pre(T* x, T* d, const T* z, T c1, T c2, int64_t n) {
+  GRID_STRIDE(i, n) {
+    const T di = (c1 != T(0) ? c1 * d[i] : T(0)) + c2 * z[i];
+    d[i] = di;
+    x[i] += di;
+  }
+}
 template <typename T> __global__ void k_cheby0(T* x, T* d, const T* b, const T* dinv, T c2, int64_t n) {
   GRID_STRIDE(i, n) {
     const T di = c2 * dinv[i] * b[i];
@@ -287,6 +294,12 @@ template <typename T>
 void vcheby(T* x, T* d, const T* b, const T* ax, const T* dinv, T c1, T c2, int64_t n, cudaStream_t s) {
   LAUNCH(k_cheby<T>, n, s, x, d, b, ax, dinv, c1, c2, n);
 }
+template <typename T>
+void vcheby_pre(T* x, T* d, const T* z, T c1, T c2, int64_t n, cudaStream_t s) {
+  LAUNCH(k_cheby_pre<T>, n, s, x, d, z, c1, c2, n);
+}
+template void vcheby_pre<double>(double*, double*, const double*, double, double, int64_t, cudaStream_t);
+template void vcheby_pre<float>(float*, float*, const float*, float, float, int64_t, cudaStream_t);
 template <typename T> void vcheby0(T* x, T* d, const T* b, const T* dinv, T c2, int64_t n, cudaStream_t s) {
   LAUNCH(k_cheby0<T>, n, s, x, d, b, dinv, c2, n);
 }

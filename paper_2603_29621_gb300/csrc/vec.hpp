@@ -55,6 +55,10 @@ void vdistribute(T* x, const int32_t* dof, const int32_t* ptr, const int32_t* sr
 // Chebyshev step (Saad, Alg. 12.1 on D^-1 A): d = c1 d + c2 dinv (b - ax); x += d
 template <typename T>
 void vcheby(T* x, T* d, const T* b, const T* ax, const T* dinv, T c1, T c2, int64_t n, cudaStream_t s);
+// Chebyshev step around a general preconditioner, z = P^{-1} (b - A x): d = c1 d + c2 z (c1 = 0: d
+// not read); x += d
+template <typename T>
+void vcheby_pre(T* x, T* d, const T* z, T c1, T c2, int64_t n, cudaStream_t s);
 // first step from a zero iterate: d = c2 dinv b; x = d
 template <typename T> void vcheby0(T* x, T* d, const T* b, const T* dinv, T c2, int64_t n, cudaStream_t s);
 // y = dinv * x (pointwise)

@@ -124,3 +124,38 @@ def test_combined_solve_converges(ctx, mg_precision):
     info = prob.solve(b, x)
     assert info.converged and info.iterations <= 40, info.iterations
     assert float((x - xs).abs().max()) <= 1e-7 * float(xs.abs().max())
+
+
+@pytest.mark.parametrize("case", [(2, 4, "3-2"), (2, 4, "4-2"), (3, 2, "3-2")], ids=lambda c: f"{c[0]}d-n{c[1]}-{c[2]}")
+def test_blended_smoother_vcycle_matches_oracle(ctx, case):
+    """Section 3's Chebyshev around point Jacobi blended with Schwarz blocks on the combined faces
+    (smoother 3): one V-cycle against the oracle's with the same smoother bounds (1e-10; the blocks
+    are principal submatrices of the SPD operator, well conditioned)."""
+    dim, n, kind = case
+    f, deg, prob = _pair(ctx, dim, n, kind, nu=1.0, lambda_max=1.0, smoother=3, smoother_degree=3)
+    lv = hp.hierarchy(f, deg, rule="elimination", smoother="asm")
+    assert prob.info.n_levels == len(lv)
+    assert any(isinstance(l.dinv, hp.JacobiASM) for l in lv)
+    lmax = [1.2 * solvers.power_lmax(l_.A, l_.dinv, iterations=50) for l_ in lv[:-1]]
+    for l, lm in enumerate(lmax):
+        prob.set_lambda_max(l, lm)
+    V = solvers.VCycle(lv, lmax, ("chebyshev", 3))
+    perm = _perm(prob, 0, lv[0].problem)
+    b = inputs.uniform_vector(lv[0].A.shape[0], seed=5)
+    x = torch.zeros(len(b), dtype=torch.float64, device="cuda")
+    prob.vcycle(_to_gpu(b, perm), x)
+    exp = V(b)
+    assert np.abs(_from_gpu(x, perm) - exp).max() <= 1e-10 * np.abs(exp).max()
+
+
+@pytest.mark.parametrize("mg_precision", [0, 1])
+def test_blended_smoother_solve_converges(ctx, mg_precision):
+    f, deg, prob = _pair(ctx, 3, 4, "3-2", nu=1.0, tol=1e-10, smoother=3, mg_precision=mg_precision)
+    xyz, fld = prob.support_points()
+    xs = torch.tensor(inputs.smooth_solution(xyz, fld, 3), device="cuda")
+    b = torch.empty_like(xs)
+    prob.vmult(xs, b)
+    x = torch.zeros_like(xs)
+    info = prob.solve(b, x)
+    assert info.converged and info.iterations <= 40, info.iterations
+    assert float((x - xs).abs().max()) <= 1e-7 * float(xs.abs().max())
