@@ -381,7 +381,8 @@ int mfns_spacetime_support_points(const mfns_spacetime* st, double* xyz_host, in
  * [0, 1] and G_Q (Q x Q, row-major). */
 int mfns_spacetime_info(const mfns_spacetime* st, int* stages, int64_t* n_stage, double* nodes_host,
                         double* g_host);
-/* y = K x (device vectors of length Q * n in `precision`; x and y must not overlap). */
+/* y = K x (device vectors of length Q * n in `precision`; x and y must not overlap).  P^disc slabs:
+ * FP64 only (MFNS_ERR_UNSUPPORTED otherwise). */
 int mfns_spacetime_vmult(mfns_spacetime* st, int precision, const void* x, void* y, void* stream);
 int mfns_spacetime_destroy(mfns_spacetime* st);
 /* Space-time multigrid for the slab (Section 4), FP64, uniform meshes (MFNS_ERR_UNSUPPORTED
