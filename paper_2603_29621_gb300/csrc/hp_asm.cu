@@ -14,7 +14,8 @@ namespace mfns {
 
 namespace {
 
-// one block per thread block: gather r on the block, times the block's inverse, into zloc
+// one block per thread block: gather r on the block, times the block's inverse (stored column by
+// column: the threads of a warp, one row each, read consecutive words), into zloc
 template <typename T>
 __global__ void k_block_solve(const T* __restrict__ r, T* __restrict__ zloc, const int64_t* __restrict__ b_ptr,
                               const int32_t* __restrict__ b_idx, const int64_t* __restrict__ k_ptr,
@@ -28,9 +29,8 @@ __global__ void k_block_solve(const T* __restrict__ r, T* __restrict__ zloc, con
   __syncthreads();
   const T* Kp = kinv + k_ptr[p];
   for (int row = threadIdx.x; row < m; row += blockDim.x) {
-    const T* kr = Kp + (int64_t)row * m;
     T v = 0;
-    for (int j = 0; j < m; ++j) v += kr[j] * rl[j];
+    for (int j = 0; j < m; ++j) v += Kp[(int64_t)j * m + row] * rl[j];
     zloc[b0 + row] = v;
   }
 }
@@ -137,7 +137,9 @@ void build_hp_asm(OpLevel& lv, Budget* bud, cudaStream_t s) {
     if (!invert_dense_rel(K, (int64_t)blocks[b].size(), 1e-14)) throw Error(kErrArg, "singular Schwarz block");
     b_idx.insert(b_idx.end(), blocks[b].begin(), blocks[b].end());
     b_ptr.push_back((int64_t)b_idx.size());
-    kinv.insert(kinv.end(), K.begin(), K.end());
+    const int64_t mb = (int64_t)blocks[b].size();
+    for (int64_t j = 0; j < mb; ++j)  // column by column
+      for (int64_t i = 0; i < mb; ++i) kinv.push_back(K[(size_t)i * mb + j]);
     k_ptr.push_back((int64_t)kinv.size());
     A->max_block = std::max<int64_t>(A->max_block, (int64_t)blocks[b].size());
   }

@@ -67,8 +67,9 @@ __global__ void k_time_restrict(double* __restrict__ coarse, const double* __res
 }
 
 // Patch solves of the Schwarz smoother, one block per patch: the patch's entries of all stages
-// (stage-major, Q m values) gathered into shared memory, times the patch's inverse (row-major),
-// written to the patch's slice of zloc (offset Q * p_ptr[p]).
+// (stage-major, Q m values) gathered into shared memory, times the patch's inverse (stored column
+// by column, so that the threads of a warp, one row each, read consecutive words), written to the
+// patch's slice of zloc (offset Q * p_ptr[p]).
 __global__ void k_patch_solve(const double* __restrict__ r, double* __restrict__ zloc, const int64_t* __restrict__ p_ptr,
                               const int32_t* __restrict__ p_idx, const int64_t* __restrict__ k_ptr,
                               const double* __restrict__ kinv, int Q, int64_t n) {
@@ -85,9 +86,8 @@ __global__ void k_patch_solve(const double* __restrict__ r, double* __restrict__
   const double* Kp = kinv + k_ptr[p];
   double* out = zloc + (int64_t)Q * b0;
   for (int row = threadIdx.x; row < mq; row += blockDim.x) {
-    const double* kr = Kp + (int64_t)row * mq;
     double v = 0.0;
-    for (int j = 0; j < mq; ++j) v += kr[j] * rl[j];
+    for (int j = 0; j < mq; ++j) v += Kp[(int64_t)j * mq + row] * rl[j];
     out[row] = v;
   }
 }
@@ -386,7 +386,8 @@ static void build_schwarz(Stmg& mg, StmgLevel& L, Budget* bud, cudaStream_t s) {
     if (!invert_dense_rel(K, mq, 1e-14)) throw Error(kErrUnsupported, "space-time multigrid: singular Schwarz patch");
     p_idx.insert(p_idx.end(), patches[p].begin(), patches[p].end());
     p_ptr.push_back((int64_t)p_idx.size());
-    kinv.insert(kinv.end(), K.begin(), K.end());
+    for (int64_t j = 0; j < mq; ++j)  // column by column
+      for (int64_t i = 0; i < mq; ++i) kinv.push_back(K[(size_t)i * mq + j]);
     k_ptr.push_back((int64_t)kinv.size());
     max_patch = std::max(max_patch, m);
   }
