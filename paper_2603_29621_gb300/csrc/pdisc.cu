@@ -28,7 +28,8 @@ __device__ __forceinline__ void cell_coords(const PdiscGeom g, int64_t cell, int
 }
 
 // y_p(cell) = B x_u(cell): every lane sums a strided share of the cell's velocity entries for
-// every coefficient, then the warp adds the shares in a fixed order
+// every coefficient (NPC of them, in registers), then the warp adds the shares in a fixed order
+template <int NPC>
 __global__ void k_div(const PdiscGeom g, const double* __restrict__ B, const double* __restrict__ x,
                       double* __restrict__ y, int64_t n_cells) {
   const int lane = threadIdx.x & 31;
@@ -39,19 +40,22 @@ __global__ void k_div(const PdiscGeom g, const double* __restrict__ B, const dou
   int nb = g.k + 1;
   nb = g.dim == 3 ? nb * nb * nb : nb * nb;
   const int nj = nb * g.dim;
-  double acc[20];  // npc <= 20 (3D, k <= 4)
-  for (int a = 0; a < g.npc; ++a) acc[a] = 0.0;
+  double acc[NPC];
+#pragma unroll
+  for (int a = 0; a < NPC; ++a) acc[a] = 0.0;
   for (int j = lane; j < nj; j += 32) {
     const int b = j / g.dim, d = j - b * g.dim;
     bool bnd;
     const int64_t node = slot_node(g, cx, cy, cz, b, bnd);
     const double u = bnd ? 0.0 : x[node * g.dim + d];
-    for (int a = 0; a < g.npc; ++a) acc[a] += B[(int64_t)a * nj + j] * u;
+#pragma unroll
+    for (int a = 0; a < NPC; ++a) acc[a] += B[(int64_t)a * nj + j] * u;
   }
-  for (int a = 0; a < g.npc; ++a) {
+#pragma unroll
+  for (int a = 0; a < NPC; ++a) {
     double v = acc[a];
     for (int o = 16; o; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    if (lane == 0) y[g.n_main + cell * g.npc + a] = v;
+    if (lane == 0) y[g.n_main + cell * NPC + a] = v;
   }
 }
 
@@ -132,9 +136,17 @@ unsigned grid_for_items(int64_t items, int per_block) {
 }  // namespace
 
 void pdisc_div(const PdiscGeom& g, const double* B, const double* x, double* y, cudaStream_t s) {
-  if (g.npc > 20) throw Error(kErrUnsupported, "P^disc: more than 20 pressure coefficients per cell");
   const int64_t n_cells = g.dim == 3 ? (int64_t)g.n * g.n * g.n : (int64_t)g.n * g.n;
-  k_div<<<grid_for_items(n_cells, kWarpsPerBlock), 32 * kWarpsPerBlock, 0, s>>>(g, B, x, y, n_cells);
+  const unsigned grid = grid_for_items(n_cells, kWarpsPerBlock), block = 32 * kWarpsPerBlock;
+  // coefficients per cell: total degree <= k - 1 in dim variables, k = 2..4
+  switch (g.npc) {
+    case 3: k_div<3><<<grid, block, 0, s>>>(g, B, x, y, n_cells); break;
+    case 4: k_div<4><<<grid, block, 0, s>>>(g, B, x, y, n_cells); break;
+    case 6: k_div<6><<<grid, block, 0, s>>>(g, B, x, y, n_cells); break;
+    case 10: k_div<10><<<grid, block, 0, s>>>(g, B, x, y, n_cells); break;
+    case 20: k_div<20><<<grid, block, 0, s>>>(g, B, x, y, n_cells); break;
+    default: throw Error(kErrUnsupported, "P^disc: unsupported number of pressure coefficients per cell");
+  }
   MFNS_CUDA(cudaGetLastError());
 }
 
