@@ -410,6 +410,10 @@ int mfns_spacetime_mg_support_points(const mfns_spacetime* st, int level, double
  * S_l in (Schwarz; not on the coarsest level); 2: out += P_l in (in on level l+1, out on level l);
  * 3: out = P_l^T in (in on level l, out on level l+1).  in and out must not overlap. */
 int mfns_spacetime_mg_apply(mfns_spacetime* st, int level, int what, const void* in, void* out, void* stream);
+/* Bytes of the Schwarz patch inverses of a level (each smoother application reads them once:
+ * the algorithmic traffic of the HBM-bound patch solve) and the number of patches (0 on the
+ * coarsest level). */
+int mfns_spacetime_mg_smoother_bytes(const mfns_spacetime* st, int level, int64_t* inverse_bytes, int64_t* n_patches);
 /* x = one V-cycle of the space-time multigrid applied to b (zero initial guess; FP64, length
  * Q * n of the finest level). */
 int mfns_spacetime_vcycle(mfns_spacetime* st, const void* b, void* x, void* stream);

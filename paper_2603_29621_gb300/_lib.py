@@ -113,6 +113,7 @@ _SIGS = {
     "mfns_spacetime_mg_support_points": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
     "mfns_spacetime_mg_apply": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
     "mfns_spacetime_vcycle": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "mfns_spacetime_mg_smoother_bytes": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
     "mfns_spacetime_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.c_int, C.POINTER(C.c_int),
                                        C.POINTER(C.c_double), C.POINTER(C.c_int), C.c_void_p]),
 }

@@ -358,6 +358,12 @@ class SpaceTime:
         L.check(self.lib.mfns_spacetime_vcycle(self.h, _ptr(b), _ptr(x), _stream(stream)))
         return x
 
+    def mg_smoother_bytes(self, level):
+        """(bytes of the level's Schwarz patch inverses, number of patches)."""
+        nb, npat = C.c_int64(), C.c_int64()
+        L.check(self.lib.mfns_spacetime_mg_smoother_bytes(self.h, level, C.byref(nb), C.byref(npat)))
+        return nb.value, npat.value
+
     def solve(self, b, x, tol=1e-10, maxit=200, stream=None, raise_on_nonconvergence=True):
         """FGMRES preconditioned by the space-time V-cycle; returns (iterations, relres)."""
         its, rel, conv = C.c_int(), C.c_double(), C.c_int()

@@ -130,6 +130,7 @@ namespace mfns {
 // One level of the space-time multigrid (finest first).
 struct StmgLevel {
   int k = 2, r = 0, Q = 1;
+  int64_t kinv_bytes = 0;  // bytes of the Schwarz patch inverses (read once per smoother application)
   // kind 0 (Taylor--Hood): A the Stokes system, P the pressure space (transfers); kind 1
   // (Q_k / P^disc_{k-1}, uniform meshes): A the velocity block (vector Laplacian), with the cell
   // block B of the pressure coupling and the pressure embedding Ep towards the next coarser level
@@ -418,6 +419,7 @@ static void build_schwarz(Stmg& mg, StmgLevel& L, Budget* bud, cudaStream_t s) {
   L.p_idx = upload(bud, p_idx);
   L.k_ptr = upload(bud, k_ptr);
   L.kinv = upload(bud, kinv);
+  L.kinv_bytes = (int64_t)kinv.size() * 8;
   L.e_ptr = upload(bud, cnt);
   L.e_base = upload(bud, e_base);
   L.e_np = upload(bud, e_np);
@@ -982,4 +984,14 @@ extern "C" int mfns_spacetime_support_points(const mfns_spacetime* st, double* x
   else
     oplevel_support(*st->problem->p->system, xyz_host, field_host);
   ST_END
+}
+
+extern "C" int mfns_spacetime_mg_smoother_bytes(const mfns_spacetime* st, int level, int64_t* inverse_bytes,
+                                                int64_t* n_patches) {
+  if (!st || !st->mg || level < 0 || level >= (int)st->mg->lv.size())
+    return mfns::capi_fail(mfns::kErrArg, "bad arguments");
+  const mfns::StmgLevel& L = *st->mg->lv[level];
+  if (inverse_bytes) *inverse_bytes = L.kinv_bytes;
+  if (n_patches) *n_patches = L.n_patch;
+  return MFNS_OK;
 }
