@@ -156,3 +156,16 @@ def test_vertex_star_patches_match_the_oracle(harness, dim, n, ball, k):
     assert mine == ref
     # the same multiplicities (they set the Schwarz weights): no patch repeated on either side
     assert len(patches) == len(mine) and len(ref_list) == len(ref)
+
+
+@pytest.mark.parametrize("n,stop_n", [(8, 2), (8, 4)])
+@pytest.mark.parametrize("k,r", [(2, 1), (4, 3), (3, 2)])
+def test_level_sequence_with_cell_patches_matches_the_oracle(harness, k, r, n, stop_n):
+    """Cell patches (the paper's pair Q_k / P^disc_{k-1}): the temporal steps always follow the
+    spatial ones on the coarsest mesh."""
+    f = mesh.uniform(2, n)
+    fs = solvers.coarse_forests(f, stop_n)
+    seq = harness(f, k, r, len(fs), True)[0]
+    lv = spacetime.stmg_levels(f, k, r, tau=0.1, stop_n=stop_n, pressure="disc")
+    assert [(a, b) for a, b, _ in seq] == [(l.k, l.r) for l in lv]
+    assert [fs[i].n for _, _, i in seq] == [l.st.space.forest.n for l in lv]
