@@ -341,6 +341,27 @@ bool eliminate_constraints(const Forest& f, const std::vector<int32_t>& degree,
 }
 }  // namespace
 
+// Some face of a cell has finer neighbours across it of lower degree than the cell (found from the
+// finer side: the cell just across each interior face of every cell).
+static bool has_combined_face(const Forest& f, const std::vector<int32_t>& degree, const Lattice& latt) {
+  const int dim = f.dim;
+  const int64_t N = (int64_t)f.n << f.max_level();
+  for (size_t a = 0; a < f.n_cells(); ++a) {
+    const int64_t sa = int64_t(1) << (f.max_level() - f.lev[a]);
+    for (int d = 0; d < dim; ++d)
+      for (int side = 0; side < 2; ++side) {
+        const int64_t q = (f.crd[3 * a + d] + side) * sa;
+        if (q == 0 || q == N) continue;
+        int64_t pos[3] = {0, 0, 0};
+        for (int j = 0; j < dim; ++j) pos[j] = f.crd[3 * a + j] * sa;
+        pos[d] = side ? q : q - 1;
+        const int32_t b = latt.at((int)pos[0], (int)pos[1], (int)pos[2]);
+        if (b >= 0 && f.lev[b] < f.lev[a] && degree[b] > degree[a]) return true;
+      }
+  }
+  return false;
+}
+
 bool make_hp_space(const Forest& f, const std::vector<int32_t>& degree, HpSpace& out, std::string* err,
                    HpRule rule, bool dirichlet) {
   auto fail = [&](const char* m) {
@@ -437,6 +458,16 @@ bool make_hp_space(const Forest& f, const std::vector<int32_t>& degree, HpSpace&
     }
   }
   const Lattice latt = make_lattice(f);
+  // A combined face -- a face of a coarse cell whose neighbours across it are finer and of lower
+  // degree -- makes the local rule inapplicable even where no node of the finer cells hangs (coarse
+  // degree 2 against fine degree 1: every fine node is a coarse node, yet the coarse quadratic
+  // trace is not piecewise linear).  The automatic rule then eliminates from the start; an
+  // edge-only contact of that kind is caught by the local rule itself (a fine node hanging on a
+  // coarse cell of higher degree).
+  if (rule == HpRule::kAuto && has_combined_face(f, degree, latt)) {
+    if (!eliminate_constraints(f, degree, gll, dom, entity, latt, dirichlet, out, err)) return false;
+    return true;
+  }
   if (rule != HpRule::kElimination) {
     const int st = dominance_constraints(f, degree, gll, lat, own_ptr, own, dom, latt, out, err);
     if (st == 0) return true;

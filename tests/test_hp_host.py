@@ -197,7 +197,7 @@ def _compare(got, ns):
 
 def _combined(f, kind):
     lev = f.cells[:, 0]
-    return {"3-2": 3 - lev, "4-2": 4 - 2 * lev, "4-3": 4 - lev}[kind]
+    return {"3-2": 3 - lev, "4-2": 4 - 2 * lev, "4-3": 4 - lev, "2-1": 2 - lev}[kind]
 
 
 def test_coarse_higher_degree_across_a_hanging_face_is_rejected_by_the_local_rule(harness):
@@ -219,10 +219,12 @@ def test_elimination_matches_the_oracle_where_the_local_rule_applies(harness, di
 
 @pytest.mark.parametrize("dirichlet", [True, False])
 @pytest.mark.parametrize("dim,n,kind", [(2, 3, "3-2"), (2, 4, "4-2"), (2, 3, "4-3"), (3, 2, "3-2"),
-                                        (3, 3, "3-2")])
+                                        (3, 3, "3-2"), (2, 4, "2-1"), (3, 3, "2-1")])
 def test_combined_faces_by_elimination_match_the_oracle(harness, dim, n, kind, dirichlet):
     """Coarse cells of higher degree than the refined ones: the automatic rule switches to
-    elimination and gives the oracle's constraints."""
+    elimination and gives the oracle's constraints -- also for coarse degree 2 against fine degree
+    1, where every node of the fine cells is a node of the coarse cell and no node hangs, yet the
+    coarse trace must be reduced to a piecewise linear one."""
     f = mesh.refine_ball(mesh.uniform(dim, n), (0.3, 0.35, 0.4), 0.3, 1)
     deg = _combined(f, kind)
     ns = hp.HpNodeSet(f, deg, "elimination", dirichlet=dirichlet)
