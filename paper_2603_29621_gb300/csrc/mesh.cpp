@@ -200,7 +200,7 @@ Forest forest_level(const Forest& f, int l) {
 
 bool ls_owned_nodes(const Forest& fine, const NodeSpace& fns, const Forest& lf, const NodeSpace& lns,
                     const std::vector<uint8_t>& edge, int l, std::vector<int32_t>& owner,
-                    std::vector<int32_t>& cf, std::vector<int32_t>& cl, std::string* err) {
+                    std::vector<int32_t>& cf, std::vector<int32_t>& cl, std::string* err, bool own_boundary) {
   const int nb = fns.nb;
   if (lns.nb != nb || (int64_t)owner.size() != fns.n_nodes || (int64_t)edge.size() != lns.n_nodes) {
     if (err) *err = "inconsistent node spaces";
@@ -221,7 +221,8 @@ bool ls_owned_nodes(const Forest& fine, const NodeSpace& fns, const Forest& lf, 
     }
     for (int b = 0; b < nb; ++b) {
       const int32_t gf = fns.cell_nodes[c * nb + b];
-      if (fns.cell_master[c * nb + b] != gf || hang[gf] || fns.boundary[gf]) continue;  // hanging or Dirichlet
+      if (fns.cell_master[c * nb + b] != gf || hang[gf]) continue;  // hanging
+      if (fns.boundary[gf] && !own_boundary) continue;               // every component Dirichlet
       const int32_t gl = lns.cell_nodes[(size_t)it->second * nb + b];
       if (edge[gl]) continue;
       if (owner[gf] == l) continue;  // already listed from a neighbouring cell of this level
@@ -237,11 +238,11 @@ bool ls_owned_nodes(const Forest& fine, const NodeSpace& fns, const Forest& lf, 
   return true;
 }
 
-bool ls_all_owned(const NodeSpace& fns, const std::vector<int32_t>& owner) {
+bool ls_all_owned(const NodeSpace& fns, const std::vector<int32_t>& owner, bool own_boundary) {
   std::vector<char> hang(fns.n_nodes, 0);
   for (int32_t g : fns.hang_node) hang[g] = 1;
   for (int64_t g = 0; g < fns.n_nodes; ++g)
-    if (!hang[g] && !fns.boundary[g] && owner[g] < 0) return false;
+    if (!hang[g] && (own_boundary || !fns.boundary[g]) && owner[g] < 0) return false;
   return true;
 }
 

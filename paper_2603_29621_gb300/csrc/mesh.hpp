@@ -80,15 +80,19 @@ NodeSpace make_nodes(const Forest& f, const Lattice& lat, const std::vector<uint
 std::vector<uint8_t> refinement_edge(const Forest& f, const NodeSpace& ns);
 
 // Local smoothing: the DoFs a level owns.  For the active cells of the fine forest at refinement
-// level l, every slot whose fine node is free (not hanging, not on the boundary) and whose level
-// node (same cell of the level forest `lf`, same slot) is not on the refinement edge appends the
-// pair (fine node, level node) to (cf, cl) and records owner[fine node] = l.  A node listed by
-// two levels, or an active cell missing from `lf`, is an error (false, message in err).
+// level l, every slot whose fine node is free (not hanging; not on the boundary unless
+// own_boundary) and whose level node (same cell of the level forest `lf`, same slot) is not on the
+// refinement edge appends the pair (fine node, level node) to (cf, cl) and records owner[fine
+// node] = l.  own_boundary: the field has components without a boundary condition (the pressure of
+// the stabilised equal-order system), so boundary nodes carry free DoFs and need an owner too; their
+// Dirichlet components are restored from the right-hand side after the cycle.  A node listed by two
+// levels, or an active cell missing from `lf`, is an error (false, message in err).
 bool ls_owned_nodes(const Forest& fine, const NodeSpace& fns, const Forest& lf, const NodeSpace& lns,
                     const std::vector<uint8_t>& edge, int l, std::vector<int32_t>& owner,
-                    std::vector<int32_t>& cf, std::vector<int32_t>& cl, std::string* err);
-// every free node of the fine space has an owner
-bool ls_all_owned(const NodeSpace& fns, const std::vector<int32_t>& owner);
+                    std::vector<int32_t>& cf, std::vector<int32_t>& cl, std::string* err,
+                    bool own_boundary = false);
+// every free node of the fine space has an owner (boundary nodes included when own_boundary)
+bool ls_all_owned(const NodeSpace& fns, const std::vector<int32_t>& owner, bool own_boundary = false);
 
 // 1D helpers shared by the host code (GLL nodes, Gauss rule, Lagrange values).
 std::vector<double> gll_nodes(int k);

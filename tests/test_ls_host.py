@@ -6,7 +6,9 @@ For ball-refined forests in 2D and 3D and degrees 1-3:
 * level forests have no hanging nodes (all constraint masks zero) and every cell-node index is in
   range;
 * every free fine DoF is owned by exactly one level, the coarsest level of the active cells that
-  hold it (the oracle's ``owner_level``), and constrained fine DoFs by none.
+  hold it (the oracle's ``owner_level``), and constrained fine DoFs by none -- with boundary nodes
+  owned as well when the field has a component without a boundary condition (the stabilised
+  system's pressure).
 """
 import os
 import shutil
@@ -38,8 +40,8 @@ static NodeSpace nodes_of(const Forest& f, int k, bool zero_masks) {
   return ns;
 }
 int main() {
-  int dim, n, k, nc;
-  if (std::scanf("%d %d %d %d", &dim, &n, &k, &nc) != 4) return 1;
+  int dim, n, k, nc, ob;
+  if (std::scanf("%d %d %d %d %d", &dim, &n, &k, &nc, &ob) != 5) return 1;
   Forest f;
   f.dim = dim;
   f.n = n;
@@ -59,7 +61,7 @@ int main() {
     NodeSpace lns = nodes_of(lf, k, true);
     std::vector<uint8_t> edge = l == 0 ? std::vector<uint8_t>(lns.n_nodes, 0) : refinement_edge(lf, lns);
     std::vector<int32_t> cf, cl;
-    if (!ls_owned_nodes(f, fns, lf, lns, edge, l, owner, cf, cl, &err)) fail(err.c_str());
+    if (!ls_owned_nodes(f, fns, lf, lns, edge, l, owner, cf, cl, &err, ob != 0)) fail(err.c_str());
     for (size_t i = 0; i < cf.size(); ++i)
       if (cf[i] < 0 || cf[i] >= fns.n_nodes || cl[i] < 0 || cl[i] >= lns.n_nodes || edge[cl[i]]) fail("copy pair");
     std::printf("LEVEL %d %zu %lld %zu\n", l, lf.n_cells(), (long long)lns.n_nodes, cf.size());
@@ -68,7 +70,7 @@ int main() {
       std::printf("%d %d\n", (int)edge[g], (int)lns.boundary[g]);
     }
   }
-  if (!ls_all_owned(fns, owner)) fail("a free fine node without owner");
+  if (!ls_all_owned(fns, owner, ob != 0)) fail("a free fine node without owner");
   std::printf("FINE %lld\n", (long long)fns.n_nodes);
   for (int64_t g = 0; g < fns.n_nodes; ++g) {
     for (int d = 0; d < dim; ++d) std::printf("%.17g ", fns.x[g * dim + d]);
@@ -90,10 +92,10 @@ def harness(tmp_path_factory):
     subprocess.run(["g++", "-O1", "-std=c++17", "-I", CSRC, str(src), os.path.join(CSRC, "mesh.cpp"), "-o", str(exe)],
                    check=True)
 
-    def run(forest, k):
+    def run(forest, k, own_boundary=False):
         cells = forest.cells
         rows = [f"{c[0]} {c[1]} {c[2]} {c[3] if forest.dim == 3 else 0}" for c in cells]
-        inp = f"{forest.dim} {forest.n} {k} {len(cells)}\n" + "\n".join(rows) + "\n"
+        inp = f"{forest.dim} {forest.n} {k} {len(cells)} {int(own_boundary)}\n" + "\n".join(rows) + "\n"
         out = subprocess.run([str(exe)], input=inp, capture_output=True, text=True, check=True).stdout.split("\n")
         assert not out[0].startswith("FAIL"), out[0]
         levels, i = {}, 0
@@ -132,12 +134,13 @@ def test_level_nodes_and_edges_match_the_oracle(harness, dim, n, levels, k):
             assert ref[key] == (e, b)
 
 
+@pytest.mark.parametrize("own_boundary", [False, True])
 @pytest.mark.parametrize("dim,n,levels,k", CASES)
-def test_every_free_fine_dof_has_one_owner(harness, dim, n, levels, k):
+def test_every_free_fine_dof_has_one_owner(harness, dim, n, levels, k, own_boundary):
     f = mesh.refine_ball(mesh.uniform(dim, n), (0.3, 0.35, 0.4), 0.3, levels)
-    got, xf, owner = harness(f, k)
+    got, xf, owner = harness(f, k, own_boundary)
     ns = mesh.NodeSet(f, k)
-    free = ~ns.boundary
+    free = np.ones(ns.n_nodes, dtype=bool) if own_boundary else ~ns.boundary
     free[list(ns.hanging)] = False
     ref = dict(zip(_key(ns.x), zip(free, ns.owner_level)))
     assert len(xf) == ns.n_nodes
