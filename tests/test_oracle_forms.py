@@ -309,3 +309,51 @@ def test_stab_ns_strong_consistency(dim, newton):
     free = prob.dofs.free
     r = (K @ x - F)[free]
     assert np.abs(r).max() < 1e-11 * max(1.0, np.abs(F).max()), np.abs(r).max()
+
+
+# ---- the stabilisation parameter (reading of Section 5's delta_1: Tezduyar's tau) -------------------
+# Each limit is the published asymptotic behaviour of the parameter (a time-step, an advective and a
+# viscous time scale); the hand values fix how the three combine.  None of the expected numbers is
+# computed by the oracle.
+TAU_LIMITS = [
+    # (|u|, h, nu, dt, expected tau, which term dominates)
+    (0.0, 1.0, 1e-12, 1e-6, 0.5e-6, "transient: tau -> dt / 2"),
+    (1e6, 1.0, 1e-12, np.inf, 0.5e-6, "advective: tau -> h / (2 |u|)"),
+    (0.0, 0.1, 1.0, np.inf, 0.01 / 12.0, "viscous: tau -> h^2 / (12 nu)"),
+]
+TAU_HAND = [
+    # (|u|, h, nu, dt, sum of the three squares worked out by hand)
+    (1.5, 1.0, 1.0 / 12.0, 0.5, 16.0 + 9.0 + 1.0),                # 4^2 + 3^2 + 9 (1/3)^2
+    (3.0, 0.5, 0.25, 0.2, 100.0 + 144.0 + 144.0),                 # 10^2 + 12^2 + 9 * 4^2
+    (0.0, 0.125, 0.02, 0.01, 40000.0 + 0.0 + 235.9296),           # 200^2 + 0 + 9 * 5.12^2
+    (2.0, 0.25, 1e-3, 0.05, 1600.0 + 256.0 + 0.036864),           # 40^2 + 16^2 + 9 * 0.064^2
+]
+
+
+def _check_tau(tau_fn):
+    for u, h, nu, dt, expect, what in TAU_LIMITS:
+        got = tau_fn(u, h, nu, dt)
+        assert abs(got - expect) <= 1e-9 * expect, (what, got, expect)
+    for u, h, nu, dt, s in TAU_HAND:
+        got = tau_fn(u, h, nu, dt)
+        assert abs(got - 1.0 / np.sqrt(s)) <= 1e-13 / np.sqrt(s), (u, h, nu, dt, got)
+
+
+def test_tau_limits_and_hand_values():
+    _check_tau(forms.tau_formula)
+
+
+def test_tau_pin_catches_a_wrong_factor():
+    """The pin fails for the plausible misreadings of each term (planted in copies of the formula,
+    on the CPU): 1/dt instead of 2/dt, |u|/h instead of 2|u|/h, a missing 9, the sum of the
+    inverses instead of the inverse root of the sum of squares."""
+    inf = np.isfinite
+    wrong = [
+        lambda u, h, nu, dt: 1 / np.sqrt((1 / dt if inf(dt) else 0) ** 2 + (2 * u / h) ** 2 + 9 * (4 * nu / h ** 2) ** 2),
+        lambda u, h, nu, dt: 1 / np.sqrt((2 / dt if inf(dt) else 0) ** 2 + (u / h) ** 2 + 9 * (4 * nu / h ** 2) ** 2),
+        lambda u, h, nu, dt: 1 / np.sqrt((2 / dt if inf(dt) else 0) ** 2 + (2 * u / h) ** 2 + (4 * nu / h ** 2) ** 2),
+        lambda u, h, nu, dt: 1 / ((2 / dt if inf(dt) else 0) + 2 * u / h + 12 * nu / h ** 2),
+    ]
+    for fn in wrong:
+        with pytest.raises(AssertionError):
+            _check_tau(fn)
