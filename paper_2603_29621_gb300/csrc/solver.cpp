@@ -108,7 +108,9 @@ std::unique_ptr<Problem> build_problem(const Forest& f, int kind, int k, const P
 static void level_copy_list(const OpLevel& fine, const OpLevel& lvl, int l, const std::vector<uint8_t>& edge,
                             std::vector<int32_t>& owner, std::vector<int32_t>& cf, std::vector<int32_t>& cl) {
   std::string err;
-  if (!ls_owned_nodes(fine.forest, fine.nu, lvl.forest, lvl.nu, edge, l, owner, cf, cl, &err))
+  // the stabilised system's pressure has no boundary condition: its boundary nodes need owners
+  const bool own_boundary = fine.op == OP_STAB_NS;
+  if (!ls_owned_nodes(fine.forest, fine.nu, lvl.forest, lvl.nu, edge, l, owner, cf, cl, &err, own_boundary))
     throw Error(kErrArg, "local smoothing: " + err);
 }
 
@@ -165,7 +167,8 @@ static void build_local_smoothing(Problem& p, const Forest& f, int k, const Phys
     S->lv.push_back(std::move(lv));
   }
   // every free fine node has exactly one owner
-  if (!ls_all_owned(fine.nu, owner)) throw Error(kErrArg, "local smoothing: a free fine DoF is owned by no level");
+  if (!ls_all_owned(fine.nu, owner, fine.op == OP_STAB_NS))
+    throw Error(kErrArg, "local smoothing: a free fine DoF is owned by no level");
   for (int prec = 0; prec < 2; ++prec) {
     const size_t b = S->base->levels[0]->n_dofs * esize(prec);
     S->b[prec].alloc(bud, b);
