@@ -25,6 +25,13 @@
  *     and written asynchronously on `stream` (a cudaStream_t, NULL = the
  *     legacy default stream); the caller synchronises.  src and dst must not
  *     alias.  Host pointers are only used where the name says so (`_host`).
+ *   - Every call that takes device vectors also takes their lengths in
+ *     elements (`n`, `n_fine`, ...).  The library checks each against the
+ *     length the call expects (mfns_problem_info: n_dofs, level_dofs,
+ *     cycle_dofs) and returns MFNS_ERR_ARG, touching nothing, when they
+ *     differ: a wrong-sized buffer is reported instead of read or written
+ *     out of bounds.  The library cannot see the allocation itself: the
+ *     caller guarantees that each pointer holds n elements.
  *   - Precision: MFNS_FP64 vectors hold double, MFNS_FP32 vectors hold float.
  *   - The library owns meshes, hierarchies, diagonals, frozen states and
  *     workspaces; they are allocated against the context's HBM budget at
@@ -55,7 +62,8 @@ extern "C" {
 
 /* status codes */
 #define MFNS_OK 0
-#define MFNS_ERR_ARG (-1)            /* invalid argument (null pointer, bad level, misaligned vector) */
+#define MFNS_ERR_ARG (-1)            /* invalid argument (null pointer, bad level, misaligned vector,
+                                        vector length other than the one the call expects) */
 #define MFNS_ERR_OOM (-2)            /* cudaMalloc failed */
 #define MFNS_ERR_BUDGET (-3)         /* the context's HBM budget would be exceeded */
 #define MFNS_ERR_UNSUPPORTED (-4)    /* (dim, degree, kind) not built */
@@ -147,11 +155,16 @@ typedef struct {
   int64_t n_velocity_dofs;      /* STOKES: start of the pressure block */
   int64_t n_cells;
   int n_colors;                 /* colours of the finest level */
-  int64_t level_dofs[32];       /* vector length per multigrid level */
+  int64_t level_dofs[32];       /* vector length of each multigrid level (mfns_smooth, transfers,
+                                   mfns_set_lambda_max); under local smoothing level 0 is the finest
+                                   refinement level, not the fine operator (see cycle_dofs) */
   int level_degree[32];
   int64_t level_cells[32];
   double lambda_max[32];        /* smoother bound per level (estimate x 1.2, or the override) */
   size_t device_bytes;          /* HBM held by this problem */
+  int64_t cycle_dofs;           /* vector length of mfns_vcycle: the fine operator of the multigrid
+                                   (the velocity A block for STOKES, n_dofs otherwise), for both
+                                   hierarchies */
 } mfns_info;
 
 typedef struct {
@@ -237,11 +250,12 @@ int mfns_problem_destroy(mfns_problem* p);
 
 /* ---- operators ----------------------------------------------------------------------------- */
 /* dst = A src (matrix-free, Section 1 / Eq. 4 per cell); constrained rows dst_i = src_i. */
-int mfns_vmult(mfns_problem* p, int which, int precision, const void* src, void* dst, void* stream);
+int mfns_vmult(mfns_problem* p, int which, int precision, const void* src, void* dst, int64_t n,
+               void* stream);
 /* diag = diag(A) (exact, per-cell unit-vector evaluation; 1 on constrained rows). */
-int mfns_diagonal(mfns_problem* p, int which, int precision, void* diag, void* stream);
+int mfns_diagonal(mfns_problem* p, int which, int precision, void* diag, int64_t n, void* stream);
 /* Hanging entries of x from their masters (x_h = sum_j w_hj x_j), Dirichlet entries kept. */
-int mfns_apply_constraints(mfns_problem* p, int which, int precision, void* x, void* stream);
+int mfns_apply_constraints(mfns_problem* p, int which, int precision, void* x, int64_t n, void* stream);
 
 /* Per-kernel timing of the operator-kernel launches of `which` with CUDA events recorded on
  * the launching stream: mode 1 = reset and enable, 0 = disable, 2 = read (synchronises on the
@@ -252,7 +266,7 @@ int mfns_kernel_timing(mfns_problem* p, int which, int mode, double* total_ms, i
 /* ---- multigrid ----------------------------------------------------------------------------- */
 /* One smoothing step on level `level`: Chebyshev of the problem's degree (or the Jacobi
  * relaxation) around point Jacobi, starting from x (x_is_zero = 1 skips the first product). */
-int mfns_smooth(mfns_problem* p, int level, int precision, const void* b, void* x, int x_is_zero,
+int mfns_smooth(mfns_problem* p, int level, int precision, const void* b, void* x, int64_t n, int x_is_zero,
                 void* stream);
 /* Same smoothing step as mfns_smooth, for callers that must not allocate device memory
  * when they call in -- for example code running while a stream is being captured into a
@@ -266,15 +280,17 @@ int mfns_smooth(mfns_problem* p, int level, int precision, const void* b, void* 
  * make that first call before any stream capture.  All calls share the array and it keeps
  * the last call's contents: calls whose GPU work overlaps in time (different streams,
  * different problems) race on it and must be serialised by the caller. */
-int mfns_smooth_noalloc(mfns_problem* p, int level, int precision, const void* b, void* x, int x_is_zero,
-                        void* stream);
+int mfns_smooth_noalloc(mfns_problem* p, int level, int precision, const void* b, void* x, int64_t n,
+                        int x_is_zero, void* stream);
 /* Transfers between level `level` (fine) and level+1 (coarse), Eq. 4:
  * fine += P coarse;  coarse = P^T fine. */
-int mfns_prolongate_add(mfns_problem* p, int level, int precision, const void* coarse, void* fine,
-                        void* stream);
-int mfns_restrict(mfns_problem* p, int level, int precision, const void* fine, void* coarse, void* stream);
-/* x = V-cycle(b) on the multigrid hierarchy (zero initial guess). */
-int mfns_vcycle(mfns_problem* p, int precision, const void* b, void* x, void* stream);
+int mfns_prolongate_add(mfns_problem* p, int level, int precision, const void* coarse, int64_t n_coarse,
+                        void* fine, int64_t n_fine, void* stream);
+int mfns_restrict(mfns_problem* p, int level, int precision, const void* fine, int64_t n_fine, void* coarse,
+                  int64_t n_coarse, void* stream);
+/* x = V-cycle(b) on the multigrid hierarchy (zero initial guess); b and x have
+ * mfns_info.cycle_dofs entries. */
+int mfns_vcycle(mfns_problem* p, int precision, const void* b, void* x, int64_t n, void* stream);
 
 /* ---- solve ---------------------------------------------------------------------------------- */
 /* FGMRES(m) in FP64 on the system operator, preconditioned by one V-cycle (STAB_NS, STOKES_A)
@@ -282,7 +298,7 @@ int mfns_vcycle(mfns_problem* p, int precision, const void* b, void* x, void* st
  * desc.mg_precision.  b and x are FP64 device vectors; x is overwritten (zero start).
  * The pressure l2 mean of b and of every preconditioned vector is removed when the
  * pressure is only fixed up to a constant.  Returns MFNS_ERR_NOT_CONVERGED when maxit is hit. */
-int mfns_solve(mfns_problem* p, const void* b, void* x, mfns_solve_info* info, void* stream);
+int mfns_solve(mfns_problem* p, const void* b, void* x, int64_t n, mfns_solve_info* info, void* stream);
 
 /* ---- nonlinear and time-dependent stabilised Navier--Stokes (Section 5) ---------------------- */
 /* STAB_NS on uniform meshes: set the time step dt, the BDF coefficient alpha of u^{n+1} (3/2 for
@@ -300,11 +316,11 @@ int mfns_solve(mfns_problem* p, const void* b, void* x, mfns_solve_info* info, v
  * masters first; a coarse level receives the fine function evaluated at its nodes cell by cell
  * (through the children of each coarse cell).  Returns MFNS_ERR_UNSUPPORTED for other kinds. */
 int mfns_set_state(mfns_problem* p, double dt, double alpha, const void* state, const void* explicit_field,
-                   void* stream);
+                   int64_t n, void* stream);
 /* dst = F(state), the nonlinear residual of the SUPG/PSPG BDF discretisation at the state of the
  * last mfns_set_state, on the free rows; constrained rows are set to 0.  With tau frozen at the
  * state, mfns_vmult applies its Jacobian.  dst: device vector in `precision`, system layout. */
-int mfns_residual(mfns_problem* p, int precision, void* dst, void* stream);
+int mfns_residual(mfns_problem* p, int precision, void* dst, int64_t n, void* stream);
 /* One variable-step BDF step for u^{n+1} (Section 5): Newton's method on F(u) = 0 with
  * g = (beta_n u^n + beta_{n-1} u^{n-1}) / dt - forcing, each update solving J(u_k) d = -F(u_k) by
  * FGMRES with the multigrid preconditioner at the current state (mg_precision of the problem).
@@ -316,17 +332,17 @@ int mfns_residual(mfns_problem* p, int precision, void* dst, void* stream);
  * Synchronises `stream`; returns MFNS_ERR_NOT_CONVERGED (result written) after max_newton
  * updates.  Buffers for g, F and the increment are allocated on the first call. */
 int mfns_bdf_step(mfns_problem* p, const mfns_newton_desc* desc, const void* u_n, const void* u_nm1,
-                  const void* forcing, void* u, mfns_newton_info* info, void* stream);
+                  const void* forcing, void* u, int64_t n, mfns_newton_info* info, void* stream);
 /* *umax (host) = max over velocity nodes of |u| for an FP64 device vector u in the system layout
  * (time-step control by a CFL number: dt = CFL h / umax).  Synchronises `stream`. */
-int mfns_max_velocity(mfns_problem* p, const void* u, double* umax, void* stream);
+int mfns_max_velocity(mfns_problem* p, const void* u, int64_t n, double* umax, void* stream);
 
 /* ---- batched solves (continuous batching of many problems) ---------------------------------- */
 /* Start a solve as in mfns_solve (same FGMRES, same preconditioner), without iterating: the
  * right-hand side is projected, x set to zero and the initial residual norm read back (one
  * synchronisation).  All later device work of this solve runs on `stream`; give every problem
  * of a batch its own stream so their work overlaps on the device. */
-int mfns_solve_begin(mfns_problem* p, const void* b, void* x, void* stream);
+int mfns_solve_begin(mfns_problem* p, const void* b, void* x, int64_t n, void* stream);
 /* One round: every listed problem whose solve is still running performs one FGMRES iteration
  * (Section 3).  The device work of all of them is enqueued first, each on its own stream, then
  * each is completed on the host (Givens rotation, and at the end of a restart cycle the update
@@ -341,11 +357,13 @@ int mfns_batch_step(mfns_problem** problems, int n, int* running);
  * operator, precision and smoother run as one launch per level and colour over the cells of all
  * of them, each block reading its problem from a descriptor table (uneven sizes share launches).
  * Results equal n separate mfns_vcycle calls (bitwise: the per-cell arithmetic and its order are
- * those of a single-problem launch).  b[i], x[i]: device vectors of problem i in `precision`.
+ * those of a single-problem launch).  b[i], x[i]: device vectors of problem i in `precision`, of
+ * lengths[i] (host array) entries each, which must equal problem i's cycle_dofs.
  * Problems: STAB_NS or STOKES_A on uniform meshes, fused_smoother = 0 (else
  * MFNS_ERR_UNSUPPORTED).  mfns_batch_step uses the same batching, captured into a CUDA graph, for
  * the preconditioners of such problems.  Synchronises `stream`. */
-int mfns_batch_vcycle(mfns_problem** problems, int n, int precision, void* const* b, void* const* x, void* stream);
+int mfns_batch_vcycle(mfns_problem** problems, int n, int precision, void* const* b, void* const* x,
+                      const int64_t* lengths, void* stream);
 /* Iterations, relative residual and convergence of the last (or current) solve of p. */
 int mfns_solve_status(const mfns_problem* p, mfns_solve_info* info);
 
@@ -381,9 +399,9 @@ int mfns_spacetime_support_points(const mfns_spacetime* st, double* xyz_host, in
  * [0, 1] and G_Q (Q x Q, row-major). */
 int mfns_spacetime_info(const mfns_spacetime* st, int* stages, int64_t* n_stage, double* nodes_host,
                         double* g_host);
-/* y = K x (device vectors of length Q * n in `precision`; x and y must not overlap).  P^disc slabs:
+/* y = K x (device vectors of length n = Q * n_stage in `precision`; x and y must not overlap).  P^disc slabs:
  * FP64 only (MFNS_ERR_UNSUPPORTED otherwise). */
-int mfns_spacetime_vmult(mfns_spacetime* st, int precision, const void* x, void* y, void* stream);
+int mfns_spacetime_vmult(mfns_spacetime* st, int precision, const void* x, void* y, int64_t n, void* stream);
 int mfns_spacetime_destroy(mfns_spacetime* st);
 /* Space-time multigrid for the slab (Section 4), FP64, uniform meshes (MFNS_ERR_UNSUPPORTED
  * otherwise).  Levels, finest first (space before time, polynomial before geometric): the spatial
@@ -408,22 +426,24 @@ int mfns_spacetime_mg_level(const mfns_spacetime* st, int level, int* n_levels, 
 int mfns_spacetime_mg_support_points(const mfns_spacetime* st, int level, double* xyz_host, int* field_host);
 /* One piece of the cycle on device FP64 vectors (stage-major): what = 0: out = K_l in; 1: out =
  * S_l in (Schwarz; not on the coarsest level); 2: out += P_l in (in on level l+1, out on level l);
- * 3: out = P_l^T in (in on level l, out on level l+1).  in and out must not overlap. */
-int mfns_spacetime_mg_apply(mfns_spacetime* st, int level, int what, const void* in, void* out, void* stream);
+ * 3: out = P_l^T in (in on level l, out on level l+1).  in and out must not overlap; n_in and n_out
+ * are their lengths (Q_l * n_stage of the level each lives on). */
+int mfns_spacetime_mg_apply(mfns_spacetime* st, int level, int what, const void* in, int64_t n_in, void* out,
+                            int64_t n_out, void* stream);
 /* Bytes of the Schwarz patch inverses of a level (each smoother application reads them once:
  * the algorithmic traffic of the HBM-bound patch solve) and the number of patches (0 on the
  * coarsest level). */
 int mfns_spacetime_mg_smoother_bytes(const mfns_spacetime* st, int level, int64_t* inverse_bytes, int64_t* n_patches);
 /* x = one V-cycle of the space-time multigrid applied to b (zero initial guess; FP64, length
  * Q * n of the finest level). */
-int mfns_spacetime_vcycle(mfns_spacetime* st, const void* b, void* x, void* stream);
+int mfns_spacetime_vcycle(mfns_spacetime* st, const void* b, void* x, int64_t n, void* stream);
 /* K x = b on the slab by FGMRES(30) in FP64 (classical Gram--Schmidt twice), right-preconditioned
  * by one space-time V-cycle; the constant pressure of every stage (the null space of K) is removed
  * from b and from every preconditioned vector, so x has none.  Stops when ||b - K x|| <= tol ||b||
  * or after maxit iterations (then MFNS_ERR_NOT_CONVERGED, x the last iterate).  iterations,
  * relres, converged: host outputs (may be NULL).  Synchronises `stream` once per iteration. */
-int mfns_spacetime_solve(mfns_spacetime* st, const void* b, void* x, double tol, int maxit, int* iterations,
-                         double* relres, int* converged, void* stream);
+int mfns_spacetime_solve(mfns_spacetime* st, const void* b, void* x, int64_t n, double tol, int maxit,
+                         int* iterations, double* relres, int* converged, void* stream);
 /* The DG(r) reference-slab matrices on the host, no device needed (any pointer may be NULL):
  * nodes (Q), m_Q (Q, m_Q[j] = phi_j(0)), M_Q, A_Q and G_Q (Q x Q, row-major [j][i]).  Error: ARG
  * for r outside 0..7. */

@@ -41,6 +41,7 @@ class Info(C.Structure):
         ("n_dofs", C.c_int64), ("n_velocity_dofs", C.c_int64), ("n_cells", C.c_int64),
         ("n_colors", C.c_int), ("level_dofs", C.c_int64 * 32), ("level_degree", C.c_int * 32),
         ("level_cells", C.c_int64 * 32), ("lambda_max", C.c_double * 32), ("device_bytes", C.c_size_t),
+        ("cycle_dofs", C.c_int64),
     ]
 
 
@@ -78,44 +79,50 @@ _SIGS = {
     "mfns_constrained_dofs": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int64, C.POINTER(C.c_int64)]),
     "mfns_set_lambda_max": (C.c_int, [C.c_void_p, C.c_int, C.c_double]),
     "mfns_problem_destroy": (C.c_int, [C.c_void_p]),
-    "mfns_vmult": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
-    "mfns_diagonal": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p]),
+    "mfns_vmult": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p]),
+    "mfns_diagonal": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_int64, C.c_void_p]),
     "mfns_kernel_timing": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
-    "mfns_apply_constraints": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p]),
-    "mfns_smooth": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
-    "mfns_smooth_noalloc": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
-    "mfns_prolongate_add": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
-    "mfns_restrict": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
-    "mfns_vcycle": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
-    "mfns_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(SolveInfo), C.c_void_p]),
-    "mfns_set_state": (C.c_int, [C.c_void_p, C.c_double, C.c_double, C.c_void_p, C.c_void_p, C.c_void_p]),
-    "mfns_residual": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
+    "mfns_apply_constraints": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_int64, C.c_void_p]),
+    "mfns_smooth": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_int64, C.c_int,
+                              C.c_void_p]),
+    "mfns_smooth_noalloc": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_int64, C.c_int,
+                                      C.c_void_p]),
+    "mfns_prolongate_add": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_int64, C.c_void_p, C.c_int64,
+                                      C.c_void_p]),
+    "mfns_restrict": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_int64, C.c_void_p, C.c_int64,
+                                C.c_void_p]),
+    "mfns_vcycle": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p]),
+    "mfns_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.POINTER(SolveInfo), C.c_void_p]),
+    "mfns_set_state": (C.c_int, [C.c_void_p, C.c_double, C.c_double, C.c_void_p, C.c_void_p, C.c_int64,
+                                 C.c_void_p]),
+    "mfns_residual": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int64, C.c_void_p]),
     "mfns_bdf_step": (C.c_int, [C.c_void_p, C.POINTER(NewtonDesc), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
-                                C.POINTER(NewtonInfo), C.c_void_p]),
-    "mfns_max_velocity": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_double), C.c_void_p]),
-    "mfns_solve_begin": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+                                C.c_int64, C.POINTER(NewtonInfo), C.c_void_p]),
+    "mfns_max_velocity": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.POINTER(C.c_double), C.c_void_p]),
+    "mfns_solve_begin": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p]),
     "mfns_batch_step": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.POINTER(C.c_int)]),
     "mfns_solve_status": (C.c_int, [C.c_void_p, C.POINTER(SolveInfo)]),
     "mfns_batch_vcycle": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.c_int, C.POINTER(C.c_void_p),
-                                    C.POINTER(C.c_void_p), C.c_void_p]),
+                                    C.POINTER(C.c_void_p), C.POINTER(C.c_int64), C.c_void_p]),
     "mfns_spacetime_create": (C.c_int, [C.c_void_p, C.c_int, C.c_double, C.POINTER(C.c_void_p)]),
     "mfns_spacetime_create_pdisc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_double, C.c_int, C.c_double,
                                               C.POINTER(C.c_void_p)]),
     "mfns_spacetime_support_points": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "mfns_spacetime_info": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int64), C.c_void_p,
                                       C.c_void_p]),
-    "mfns_spacetime_vmult": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "mfns_spacetime_vmult": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p]),
     "mfns_spacetime_destroy": (C.c_int, [C.c_void_p]),
     "mfns_spacetime_temporal": (C.c_int, [C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "mfns_spacetime_mg_build": (C.c_int, [C.c_void_p, C.c_int, C.c_double, C.c_int, C.c_void_p]),
     "mfns_spacetime_mg_level": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int),
                                           C.POINTER(C.c_int), C.POINTER(C.c_int64)]),
     "mfns_spacetime_mg_support_points": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
-    "mfns_spacetime_mg_apply": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
-    "mfns_spacetime_vcycle": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "mfns_spacetime_mg_apply": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_int64, C.c_void_p,
+                                          C.c_int64, C.c_void_p]),
+    "mfns_spacetime_vcycle": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p]),
     "mfns_spacetime_mg_smoother_bytes": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
-    "mfns_spacetime_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.c_int, C.POINTER(C.c_int),
-                                       C.POINTER(C.c_double), C.POINTER(C.c_int), C.c_void_p]),
+    "mfns_spacetime_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_double, C.c_int,
+                                       C.POINTER(C.c_int), C.POINTER(C.c_double), C.POINTER(C.c_int), C.c_void_p]),
 }
 
 EXPORTED = tuple(_SIGS)

@@ -20,6 +20,24 @@ def _ptr(t):
     return C.c_void_p(t.data_ptr())
 
 
+def _vec(t, n=None, dtype=None, name="vector"):
+    """Device pointer of a contiguous CUDA tensor after checking its length and dtype against what
+    the call expects (the library checks the length again; the dtype it cannot see)."""
+    if n is not None and t.numel() != n:
+        raise ValueError(f"{name} has {t.numel()} entries, expected {n}")
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError(f"{name} is {t.dtype}, expected {dtype}")
+    return _ptr(t)
+
+
+def _prec_of(t):
+    if t.dtype == torch.float64:
+        return L.FP64
+    if t.dtype == torch.float32:
+        return L.FP32
+    raise ValueError(f"vectors must be float64 or float32, got {t.dtype}")
+
+
 def _f64(*ts):
     for t in ts:
         if t is not None and t.dtype != torch.float64:
@@ -162,13 +180,16 @@ class Problem:
         return torch.zeros(self.n_dofs(which), dtype=_dtype(prec), device=device)
 
     def vmult(self, src, dst, which=L.OP_SYSTEM, prec=None, stream=None):
-        prec = (L.FP64 if src.dtype == torch.float64 else L.FP32) if prec is None else prec
-        L.check(self.lib.mfns_vmult(self.h, which, prec, _ptr(src), _ptr(dst), _stream(stream)))
+        prec = _prec_of(src) if prec is None else prec
+        n, dt = self.n_dofs(which), _dtype(prec)
+        L.check(self.lib.mfns_vmult(self.h, which, prec, _vec(src, n, dt, "src"), _vec(dst, n, dt, "dst"), n,
+                                    _stream(stream)))
         return dst
 
     def diagonal(self, diag, which=L.OP_SYSTEM, stream=None):
-        prec = L.FP64 if diag.dtype == torch.float64 else L.FP32
-        L.check(self.lib.mfns_diagonal(self.h, which, prec, _ptr(diag), _stream(stream)))
+        prec = _prec_of(diag)
+        n = self.n_dofs(which)
+        L.check(self.lib.mfns_diagonal(self.h, which, prec, _vec(diag, n, name="diag"), n, _stream(stream)))
         return diag
 
     def kernel_timing(self, mode, which=L.OP_SYSTEM):
@@ -178,33 +199,44 @@ class Problem:
         return ms.value, n.value
 
     def apply_constraints(self, x, which=L.OP_SYSTEM, stream=None):
-        prec = L.FP64 if x.dtype == torch.float64 else L.FP32
-        L.check(self.lib.mfns_apply_constraints(self.h, which, prec, _ptr(x), _stream(stream)))
+        prec = _prec_of(x)
+        n = self.n_dofs(which)
+        L.check(self.lib.mfns_apply_constraints(self.h, which, prec, _vec(x, n, name="x"), n, _stream(stream)))
         return x
 
     def smooth(self, level, b, x, x_is_zero=False, stream=None):
-        prec = L.FP64 if b.dtype == torch.float64 else L.FP32
-        L.check(self.lib.mfns_smooth(self.h, level, prec, _ptr(b), _ptr(x), int(bool(x_is_zero)), _stream(stream)))
+        prec = _prec_of(b)
+        n, dt = b.numel(), b.dtype          # the library checks n against the level's length
+        L.check(self.lib.mfns_smooth(self.h, level, prec, _vec(b, n, dt, "b"), _vec(x, n, dt, "x"), n,
+                                     int(bool(x_is_zero)), _stream(stream)))
         return x
 
     def prolongate_add(self, level, coarse, fine, stream=None):
-        prec = L.FP64 if coarse.dtype == torch.float64 else L.FP32
-        L.check(self.lib.mfns_prolongate_add(self.h, level, prec, _ptr(coarse), _ptr(fine), _stream(stream)))
+        prec = _prec_of(coarse)
+        nc, nf, dt = self.info.level_dofs[level + 1], self.info.level_dofs[level], coarse.dtype
+        L.check(self.lib.mfns_prolongate_add(self.h, level, prec, _vec(coarse, nc, dt, "coarse"), nc,
+                                             _vec(fine, nf, dt, "fine"), nf, _stream(stream)))
         return fine
 
     def restrict(self, level, fine, coarse, stream=None):
-        prec = L.FP64 if fine.dtype == torch.float64 else L.FP32
-        L.check(self.lib.mfns_restrict(self.h, level, prec, _ptr(fine), _ptr(coarse), _stream(stream)))
+        prec = _prec_of(fine)
+        nc, nf, dt = self.info.level_dofs[level + 1], self.info.level_dofs[level], fine.dtype
+        L.check(self.lib.mfns_restrict(self.h, level, prec, _vec(fine, nf, dt, "fine"), nf,
+                                       _vec(coarse, nc, dt, "coarse"), nc, _stream(stream)))
         return coarse
 
     def vcycle(self, b, x, stream=None):
-        prec = L.FP64 if b.dtype == torch.float64 else L.FP32
-        L.check(self.lib.mfns_vcycle(self.h, prec, _ptr(b), _ptr(x), _stream(stream)))
+        """x = V-cycle(b); b and x have info.cycle_dofs entries (the fine operator of the multigrid)."""
+        prec = _prec_of(b)
+        n, dt = self.info.cycle_dofs, b.dtype
+        L.check(self.lib.mfns_vcycle(self.h, prec, _vec(b, n, dt, "b"), _vec(x, n, dt, "x"), n, _stream(stream)))
         return x
 
     def solve(self, b, x, stream=None, raise_on_nonconvergence=True):
         si = L.SolveInfo()
-        code = self.lib.mfns_solve(self.h, _ptr(b), _ptr(x), C.byref(si), _stream(stream))
+        n, f64 = self.info.n_dofs, torch.float64
+        code = self.lib.mfns_solve(self.h, _vec(b, n, f64, "b"), _vec(x, n, f64, "x"), n, C.byref(si),
+                                   _stream(stream))
         if code != L.OK and (code != L.ERR_NOT_CONVERGED or raise_on_nonconvergence):
             L.check(code)
         return si
@@ -213,12 +245,15 @@ class Problem:
     def set_state(self, dt, alpha, state, explicit_field=None, stream=None):
         """Linearisation state (FP64 system vector), dt, BDF coefficient alpha and the explicit field g."""
         _f64(state, explicit_field)
-        g = None if explicit_field is None else _ptr(explicit_field)
-        L.check(self.lib.mfns_set_state(self.h, float(dt), float(alpha), _ptr(state), g, _stream(stream)))
+        n = self.info.n_dofs
+        g = None if explicit_field is None else _vec(explicit_field, n, name="explicit_field")
+        L.check(self.lib.mfns_set_state(self.h, float(dt), float(alpha), _vec(state, n, name="state"), g, n,
+                                        _stream(stream)))
 
     def residual(self, dst, stream=None):
-        prec = L.FP64 if dst.dtype == torch.float64 else L.FP32
-        L.check(self.lib.mfns_residual(self.h, prec, _ptr(dst), _stream(stream)))
+        prec = _prec_of(dst)
+        n = self.info.n_dofs
+        L.check(self.lib.mfns_residual(self.h, prec, _vec(dst, n, name="dst"), n, _stream(stream)))
         return dst
 
     def bdf_step(self, u, u_n, u_nm1=None, forcing=None, dt=0.0, omega=1.0, rtol=1e-8, atol=0.0, lin_tol=1e-4,
@@ -228,9 +263,11 @@ class Problem:
         desc = L.NewtonDesc(dt=float(dt), omega=float(omega), rtol=float(rtol), atol=float(atol),
                             lin_tol=float(lin_tol), max_newton=int(max_newton), extrapolate=int(bool(extrapolate)))
         info = L.NewtonInfo()
-        opt = lambda t: None if t is None else _ptr(t)
-        code = self.lib.mfns_bdf_step(self.h, C.byref(desc), _ptr(u_n), opt(u_nm1), opt(forcing), _ptr(u),
-                                      C.byref(info), _stream(stream))
+        n = self.info.n_dofs
+        opt = lambda t, nm: None if t is None else _vec(t, n, name=nm)
+        code = self.lib.mfns_bdf_step(self.h, C.byref(desc), _vec(u_n, n, name="u_n"), opt(u_nm1, "u_nm1"),
+                                      opt(forcing, "forcing"), _vec(u, n, name="u"), n, C.byref(info),
+                                      _stream(stream))
         if code != L.OK and (code != L.ERR_NOT_CONVERGED or raise_on_nonconvergence):
             L.check(code)
         return info
@@ -238,11 +275,13 @@ class Problem:
     def max_velocity(self, u, stream=None):
         _f64(u)
         out = C.c_double()
-        L.check(self.lib.mfns_max_velocity(self.h, _ptr(u), C.byref(out), _stream(stream)))
+        n = self.info.n_dofs
+        L.check(self.lib.mfns_max_velocity(self.h, _vec(u, n, name="u"), n, C.byref(out), _stream(stream)))
         return out.value
 
     def solve_begin(self, b, x, stream=None):
-        L.check(self.lib.mfns_solve_begin(self.h, _ptr(b), _ptr(x), _stream(stream)))
+        n, f64 = self.info.n_dofs, torch.float64
+        L.check(self.lib.mfns_solve_begin(self.h, _vec(b, n, f64, "b"), _vec(x, n, f64, "x"), n, _stream(stream)))
 
     def solve_status(self):
         si = L.SolveInfo()
@@ -273,12 +312,14 @@ def batch_step(problems):
 def batch_vcycle(problems, bs, xs, stream=None):
     """One batched V-cycle (zero start) per problem: x_i = V-cycle_i(b_i), shared launches per level."""
     n = len(problems)
-    prec = L.FP64 if bs[0].dtype == torch.float64 else L.FP32
+    prec = _prec_of(bs[0])
+    dt = bs[0].dtype
+    lens = [p.info.cycle_dofs for p in problems]
     arr = (C.c_void_p * n)(*[p.h for p in problems])
-    bp = (C.c_void_p * n)(*[_ptr(b).value for b in bs])
-    xp = (C.c_void_p * n)(*[_ptr(x).value for x in xs])
-    prec = L.FP64 if bs[0].dtype == torch.float64 else L.FP32
-    L.check(L.load().mfns_batch_vcycle(arr, n, prec, bp, xp, _stream(stream)))
+    bp = (C.c_void_p * n)(*[_vec(b, m, dt, "b").value for b, m in zip(bs, lens)])
+    xp = (C.c_void_p * n)(*[_vec(x, m, dt, "x").value for x, m in zip(xs, lens)])
+    ln = (C.c_int64 * n)(*lens)
+    L.check(L.load().mfns_batch_vcycle(arr, n, prec, bp, xp, ln, _stream(stream)))
     return xs
 
 
@@ -325,8 +366,10 @@ class SpaceTime:
         return xyz, fld
 
     def vmult(self, src, dst, stream=None):
-        prec = L.FP64 if src.dtype == torch.float64 else L.FP32
-        L.check(self.lib.mfns_spacetime_vmult(self.h, prec, _ptr(src), _ptr(dst), _stream(stream)))
+        prec = _prec_of(src)
+        n = self.Q * self.n
+        L.check(self.lib.mfns_spacetime_vmult(self.h, prec, _vec(src, n, src.dtype, "src"),
+                                              _vec(dst, n, src.dtype, "dst"), n, _stream(stream)))
         return dst
 
     # -- space-time multigrid (FP64) ------------------------------------------------------------
@@ -351,11 +394,15 @@ class SpaceTime:
 
     def mg_apply(self, level, what, src, dst, stream=None):
         """what: 0 operator, 1 Schwarz smoother, 2 prolongate-add (src coarse), 3 restrict (dst coarse)."""
-        L.check(self.lib.mfns_spacetime_mg_apply(self.h, level, what, _ptr(src), _ptr(dst), _stream(stream)))
+        f64 = torch.float64
+        L.check(self.lib.mfns_spacetime_mg_apply(self.h, level, what, _vec(src, dtype=f64, name="src"), src.numel(),
+                                                 _vec(dst, dtype=f64, name="dst"), dst.numel(), _stream(stream)))
         return dst
 
     def vcycle(self, b, x, stream=None):
-        L.check(self.lib.mfns_spacetime_vcycle(self.h, _ptr(b), _ptr(x), _stream(stream)))
+        n, f64 = self.Q * self.n, torch.float64
+        L.check(self.lib.mfns_spacetime_vcycle(self.h, _vec(b, n, f64, "b"), _vec(x, n, f64, "x"), n,
+                                               _stream(stream)))
         return x
 
     def mg_smoother_bytes(self, level):
@@ -367,8 +414,9 @@ class SpaceTime:
     def solve(self, b, x, tol=1e-10, maxit=200, stream=None, raise_on_nonconvergence=True):
         """FGMRES preconditioned by the space-time V-cycle; returns (iterations, relres)."""
         its, rel, conv = C.c_int(), C.c_double(), C.c_int()
-        code = self.lib.mfns_spacetime_solve(self.h, _ptr(b), _ptr(x), tol, maxit, C.byref(its), C.byref(rel),
-                                             C.byref(conv), _stream(stream))
+        n, f64 = self.Q * self.n, torch.float64
+        code = self.lib.mfns_spacetime_solve(self.h, _vec(b, n, f64, "b"), _vec(x, n, f64, "x"), n, tol, maxit,
+                                             C.byref(its), C.byref(rel), C.byref(conv), _stream(stream))
         if code != L.OK and (code != L.ERR_NOT_CONVERGED or raise_on_nonconvergence):
             L.check(code)
         return its.value, rel.value

@@ -18,10 +18,24 @@ static bool op_supported_kind(int dim, int kind, int k);
 
 static thread_local std::string g_err;
 
+// Every failure also consumes the runtime's pending error, if any: a failed library call (say a
+// memset or launch-configuration error caught by MFNS_CUDA) must not leave an error behind that
+// the caller's next, unrelated CUDA call (PyTorch's, for instance) would report as its own.
 static int fail(int code, const std::string& msg) {
+  (void)cudaGetLastError();
   g_err = msg;
   return code;
 }
+
+// A vector argument's length (elements) against the length the call expects.
+static bool len_ok(int64_t got, int64_t want, const char* what) {
+  if (got == want) return true;
+  fail(MFNS_ERR_ARG, std::string(what) + " has " + std::to_string(got) + " entries, expected " +
+                         std::to_string(want));
+  return false;
+}
+#define CHECK_LEN(got, want, what) \
+  if (!len_ok((got), (want), (what))) return MFNS_ERR_ARG
 
 namespace mfns {
 int capi_fail(int code, const char* msg) { return fail(code, msg); }
@@ -263,6 +277,7 @@ int mfns_problem_info(const mfns_problem* pc, mfns_info* out) {
     out->lambda_max[l] = lv.lmax;
   }
   out->device_bytes = P.bytes;
+  out->cycle_dofs = P.levels[0]->n_dofs;
   return MFNS_OK;
 }
 
@@ -291,10 +306,11 @@ int mfns_set_lambda_max(mfns_problem* p, int level, double lmax) {
   return MFNS_OK;
 }
 
-int mfns_vmult(mfns_problem* p, int which, int prec, const void* src, void* dst, void* stream) {
+int mfns_vmult(mfns_problem* p, int which, int prec, const void* src, void* dst, int64_t n, void* stream) {
   API_BEGIN
   OpLevel* lv = p ? select_op(p, which) : nullptr;
   if (!lv || !src || !dst || src == dst) return fail(MFNS_ERR_ARG, "bad arguments");
+  CHECK_LEN(n, lv->n_dofs, "src/dst");
   if (prec != 0 && prec != 1) return fail(MFNS_ERR_ARG, "bad precision");
   if (!aligned16(src) || !aligned16(dst)) return fail(MFNS_ERR_ARG, "vectors must be 16-byte aligned");
   MFNS_CUDA(cudaSetDevice(p->ctx->device));
@@ -320,57 +336,68 @@ int mfns_kernel_timing(mfns_problem* p, int which, int mode, double* total_ms, i
   API_END
 }
 
-int mfns_diagonal(mfns_problem* p, int which, int prec, void* diag, void* stream) {
+int mfns_diagonal(mfns_problem* p, int which, int prec, void* diag, int64_t n, void* stream) {
   API_BEGIN
   OpLevel* lv = p ? select_op(p, which) : nullptr;
   if (!lv || !diag || (prec != 0 && prec != 1)) return fail(MFNS_ERR_ARG, "bad arguments");
+  CHECK_LEN(n, lv->n_dofs, "diag");
   MFNS_CUDA(cudaSetDevice(p->ctx->device));
   oplevel_diag(*lv, prec, diag, S(stream));
   API_END
 }
 
-int mfns_apply_constraints(mfns_problem* p, int which, int prec, void* x, void* stream) {
+int mfns_apply_constraints(mfns_problem* p, int which, int prec, void* x, int64_t n, void* stream) {
   API_BEGIN
   OpLevel* lv = p ? select_op(p, which) : nullptr;
   if (!lv || !x || (prec != 0 && prec != 1)) return fail(MFNS_ERR_ARG, "bad arguments");
+  CHECK_LEN(n, lv->n_dofs, "x");
   MFNS_CUDA(cudaSetDevice(p->ctx->device));
   oplevel_distribute(*lv, prec, x, S(stream));
   API_END
 }
 
-int mfns_smooth(mfns_problem* p, int level, int prec, const void* b, void* x, int x_is_zero, void* stream) {
+int mfns_smooth(mfns_problem* p, int level, int prec, const void* b, void* x, int64_t n, int x_is_zero,
+                void* stream) {
   API_BEGIN
   if (!p || level < 0 || level >= (int)p->p->levels.size() || !b || !x || (prec != 0 && prec != 1))
     return fail(MFNS_ERR_ARG, "bad arguments");
   if (p->p->ls) return fail(MFNS_ERR_UNSUPPORTED, "single-level smoothing is not exposed for local smoothing");
+  CHECK_LEN(n, p->p->levels[level]->n_dofs, "b/x");
   MFNS_CUDA(cudaSetDevice(p->ctx->device));
   smooth(*p->p, level, prec, b, x, x_is_zero != 0, S(stream));
   API_END
 }
 
-int mfns_prolongate_add(mfns_problem* p, int level, int prec, const void* coarse, void* fine, void* stream) {
+int mfns_prolongate_add(mfns_problem* p, int level, int prec, const void* coarse, int64_t n_coarse, void* fine,
+                        int64_t n_fine, void* stream) {
   API_BEGIN
   if (!p || level < 0 || level + 1 >= (int)p->p->levels.size() || !coarse || !fine || (prec != 0 && prec != 1))
     return fail(MFNS_ERR_ARG, "bad arguments");
-  MFNS_CUDA(cudaSetDevice(p->ctx->device));
   Problem& P = *p->p;
+  CHECK_LEN(n_coarse, P.levels[level + 1]->n_dofs, "coarse");
+  CHECK_LEN(n_fine, P.levels[level]->n_dofs, "fine");
+  MFNS_CUDA(cudaSetDevice(p->ctx->device));
   transfer_prolongate_add(*P.transfers[level], *P.levels[level], *P.levels[level + 1], prec, coarse, fine, S(stream));
   API_END
 }
 
-int mfns_restrict(mfns_problem* p, int level, int prec, const void* fine, void* coarse, void* stream) {
+int mfns_restrict(mfns_problem* p, int level, int prec, const void* fine, int64_t n_fine, void* coarse,
+                  int64_t n_coarse, void* stream) {
   API_BEGIN
   if (!p || level < 0 || level + 1 >= (int)p->p->levels.size() || !coarse || !fine || (prec != 0 && prec != 1))
     return fail(MFNS_ERR_ARG, "bad arguments");
-  MFNS_CUDA(cudaSetDevice(p->ctx->device));
   Problem& P = *p->p;
+  CHECK_LEN(n_fine, P.levels[level]->n_dofs, "fine");
+  CHECK_LEN(n_coarse, P.levels[level + 1]->n_dofs, "coarse");
+  MFNS_CUDA(cudaSetDevice(p->ctx->device));
   transfer_restrict(*P.transfers[level], *P.levels[level], *P.levels[level + 1], prec, fine, coarse, S(stream));
   API_END
 }
 
-int mfns_vcycle(mfns_problem* p, int prec, const void* b, void* x, void* stream) {
+int mfns_vcycle(mfns_problem* p, int prec, const void* b, void* x, int64_t n, void* stream) {
   API_BEGIN
   if (!p || !b || !x || (prec != 0 && prec != 1)) return fail(MFNS_ERR_ARG, "bad arguments");
+  CHECK_LEN(n, p->p->levels[0]->n_dofs, "b/x (cycle_dofs)");
   MFNS_CUDA(cudaSetDevice(p->ctx->device));
   if (p->p->use_graphs)
     vcycle_graph(*p->p, prec, b, x, S(stream));
@@ -379,10 +406,11 @@ int mfns_vcycle(mfns_problem* p, int prec, const void* b, void* x, void* stream)
   API_END
 }
 
-int mfns_solve(mfns_problem* p, const void* b, void* x, mfns_solve_info* info, void* stream) {
+int mfns_solve(mfns_problem* p, const void* b, void* x, int64_t n, mfns_solve_info* info, void* stream) {
   API_BEGIN
   if (!p || !b || !x) return fail(MFNS_ERR_ARG, "bad arguments");
   if (p->p->kind == MFNS_PMASS) return fail(MFNS_ERR_UNSUPPORTED, "no solver for the pressure mass problem");
+  CHECK_LEN(n, select_op(p, MFNS_OP_SYSTEM)->n_dofs, "b/x");
   MFNS_CUDA(cudaSetDevice(p->ctx->device));
   auto t0 = std::chrono::steady_clock::now();
   double rel = 0;
@@ -401,26 +429,29 @@ int mfns_solve(mfns_problem* p, const void* b, void* x, mfns_solve_info* info, v
 }
 
 int mfns_set_state(mfns_problem* p, double dt, double alpha, const void* state, const void* explicit_field,
-                   void* stream) {
+                   int64_t n, void* stream) {
   API_BEGIN
   if (!p || !state) return fail(MFNS_ERR_ARG, "bad arguments");
+  CHECK_LEN(n, select_op(p, MFNS_OP_SYSTEM)->n_dofs, "state/explicit_field");
   MFNS_CUDA(cudaSetDevice(p->ctx->device));
   set_state(*p->p, dt, alpha, (const double*)state, (const double*)explicit_field, S(stream));
   API_END
 }
 
-int mfns_residual(mfns_problem* p, int precision, void* dst, void* stream) {
+int mfns_residual(mfns_problem* p, int precision, void* dst, int64_t n, void* stream) {
   API_BEGIN
   if (!p || !dst || (precision != MFNS_FP64 && precision != MFNS_FP32)) return fail(MFNS_ERR_ARG, "bad arguments");
+  CHECK_LEN(n, select_op(p, MFNS_OP_SYSTEM)->n_dofs, "dst");
   MFNS_CUDA(cudaSetDevice(p->ctx->device));
   residual(*p->p, precision, dst, S(stream));
   API_END
 }
 
 int mfns_bdf_step(mfns_problem* p, const mfns_newton_desc* desc, const void* u_n, const void* u_nm1,
-                  const void* forcing, void* u, mfns_newton_info* info, void* stream) {
+                  const void* forcing, void* u, int64_t n, mfns_newton_info* info, void* stream) {
   API_BEGIN
   if (!p || !desc || !u_n || !u) return fail(MFNS_ERR_ARG, "bad arguments");
+  CHECK_LEN(n, select_op(p, MFNS_OP_SYSTEM)->n_dofs, "u_n/u_nm1/forcing/u");
   MFNS_CUDA(cudaSetDevice(p->ctx->device));
   NewtonParams np;
   np.dt = desc->dt;
@@ -447,18 +478,20 @@ int mfns_bdf_step(mfns_problem* p, const mfns_newton_desc* desc, const void* u_n
   API_END
 }
 
-int mfns_max_velocity(mfns_problem* p, const void* u, double* umax, void* stream) {
+int mfns_max_velocity(mfns_problem* p, const void* u, int64_t n, double* umax, void* stream) {
   API_BEGIN
   if (!p || !u || !umax) return fail(MFNS_ERR_ARG, "bad arguments");
+  CHECK_LEN(n, select_op(p, MFNS_OP_SYSTEM)->n_dofs, "u");
   MFNS_CUDA(cudaSetDevice(p->ctx->device));
   *umax = max_velocity(*p->p, (const double*)u, S(stream));
   API_END
 }
 
-int mfns_solve_begin(mfns_problem* p, const void* b, void* x, void* stream) {
+int mfns_solve_begin(mfns_problem* p, const void* b, void* x, int64_t n, void* stream) {
   API_BEGIN
   if (!p || !b || !x) return fail(MFNS_ERR_ARG, "bad arguments");
   if (p->p->kind == MFNS_PMASS) return fail(MFNS_ERR_UNSUPPORTED, "no solver for the pressure mass problem");
+  CHECK_LEN(n, select_op(p, MFNS_OP_SYSTEM)->n_dofs, "b/x");
   MFNS_CUDA(cudaSetDevice(p->ctx->device));
   krylov_begin(*p->p, (const double*)b, (double*)x, S(stream));
   API_END
@@ -505,9 +538,10 @@ int mfns_batch_step(mfns_problem** ps, int n, int* running) {
   API_END
 }
 
-int mfns_batch_vcycle(mfns_problem** ps, int n, int precision, void* const* b, void* const* x, void* stream) {
+int mfns_batch_vcycle(mfns_problem** ps, int n, int precision, void* const* b, void* const* x,
+                      const int64_t* lengths, void* stream) {
   API_BEGIN
-  if (!ps || n <= 0 || !b || !x || (precision != MFNS_FP64 && precision != MFNS_FP32))
+  if (!ps || n <= 0 || !b || !x || !lengths || (precision != MFNS_FP64 && precision != MFNS_FP32))
     return fail(MFNS_ERR_ARG, "bad arguments");
   std::vector<Problem*> pp;
   std::vector<const void*> bb;
@@ -515,6 +549,7 @@ int mfns_batch_vcycle(mfns_problem** ps, int n, int precision, void* const* b, v
   for (int i = 0; i < n; ++i) {
     if (!ps[i] || !b[i] || !x[i]) return fail(MFNS_ERR_ARG, "null problem or vector in batch");
     if (ps[i]->ctx != ps[0]->ctx) return fail(MFNS_ERR_ARG, "problems of different contexts");
+    CHECK_LEN(lengths[i], ps[i]->p->levels[0]->n_dofs, "b[i]/x[i]");
     if (!batchable(*ps[i]->p))
       return fail(MFNS_ERR_UNSUPPORTED, "batched V-cycle: one-V-cycle problems on uniform levels only");
     pp.push_back(ps[i]->p.get());

@@ -71,8 +71,8 @@ void smooth_with_scratch(mfns::Problem& p, int level, int prec, const T* b, T* x
 
 }  // namespace
 
-extern "C" int mfns_smooth_noalloc(mfns_problem* p, int level, int precision, const void* b, void* x, int x_is_zero,
-                                   void* stream) {
+extern "C" int mfns_smooth_noalloc(mfns_problem* p, int level, int precision, const void* b, void* x, int64_t n_in,
+                                   int x_is_zero, void* stream) {
   using namespace mfns;
   try {
     (void)cudaGetLastError();  // a pending error of another component of the process is not ours
@@ -81,6 +81,8 @@ extern "C" int mfns_smooth_noalloc(mfns_problem* p, int level, int precision, co
     if (p->p->ls) return capi_fail(kErrUnsupported, "single-level smoothing is not exposed for local smoothing");
     if (p->p->smoother == 2) return capi_fail(kErrUnsupported, "the no-allocation smoother is point-Jacobi based");
     const int64_t n = p->p->levels[level]->n_dofs;
+    if (n_in != n)
+      return capi_fail(kErrArg, ("b/x has " + std::to_string(n_in) + " entries, expected " + std::to_string(n)).c_str());
     if (n > kMaxEntries)
       return capi_fail(kErrArg, ("mfns_smooth_noalloc: level has " + std::to_string(n) +
                                  " entries, the fixed scratch holds at most 1048576 per vector").c_str());

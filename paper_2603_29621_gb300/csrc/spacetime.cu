@@ -769,6 +769,12 @@ static void build_stmg(mfns_spacetime& st, int nu_s, double omega, int coarse_n,
 
 }  // namespace mfns
 
+// a vector argument whose length differs from the one the call expects
+static int st_len_fail(const char* what, int64_t got, int64_t want) {
+  return mfns::capi_fail(mfns::kErrArg, (std::string(what) + " has " + std::to_string(got) + " entries, expected " +
+                                         std::to_string(want)).c_str());
+}
+
 extern "C" int mfns_spacetime_create(mfns_problem* p, int r, double tau, mfns_spacetime** out) {
   using namespace mfns;
   try {
@@ -815,11 +821,12 @@ extern "C" int mfns_spacetime_info(const mfns_spacetime* st, int* stages, int64_
   return MFNS_OK;
 }
 
-extern "C" int mfns_spacetime_vmult(mfns_spacetime* st, int prec, const void* x, void* y, void* stream) {
+extern "C" int mfns_spacetime_vmult(mfns_spacetime* st, int prec, const void* x, void* y, int64_t n, void* stream) {
   using namespace mfns;
   try {
     (void)cudaGetLastError();
     if (!st || !x || !y || x == y || (prec != 0 && prec != 1)) return capi_fail(kErrArg, "bad arguments");
+    if (n != (int64_t)st->Q * st->n) return st_len_fail("x/y", n, (int64_t)st->Q * st->n);
     MFNS_CUDA(cudaSetDevice(st->ctx->device));
     st_vmult(*st, prec, x, y, reinterpret_cast<cudaStream_t>(stream));
   } catch (const Error& e) {
@@ -888,14 +895,23 @@ extern "C" int mfns_spacetime_mg_support_points(const mfns_spacetime* st, int le
   ST_END
 }
 
-extern "C" int mfns_spacetime_mg_apply(mfns_spacetime* st, int level, int what, const void* in, void* out,
-                                       void* stream) {
+extern "C" int mfns_spacetime_mg_apply(mfns_spacetime* st, int level, int what, const void* in, int64_t n_in,
+                                       void* out, int64_t n_out, void* stream) {
   ST_BEGIN
   if (!st || !st->mg || !in || !out || in == out || level < 0 || level >= (int)st->mg->lv.size())
     return capi_fail(kErrArg, "bad arguments");
   Stmg& mg = *st->mg;
   StmgLevel& L = *mg.lv[level];
   const bool has_coarse = level + 1 < (int)mg.lv.size();
+  {
+    const int64_t nl = (int64_t)L.Q * L.n;
+    const int64_t nc = has_coarse ? (int64_t)mg.lv[level + 1]->Q * mg.lv[level + 1]->n : 0;
+    const int64_t want_in = what == 2 ? nc : nl, want_out = what == 3 ? nc : nl;
+    if ((what == 2 || what == 3) && !has_coarse)
+      return capi_fail(kErrArg, "the coarsest level has no coarser level");
+    if (n_in != want_in) return st_len_fail("in", n_in, want_in);
+    if (n_out != want_out) return st_len_fail("out", n_out, want_out);
+  }
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   MFNS_CUDA(cudaSetDevice(st->ctx->device));
   switch (what) {
@@ -917,11 +933,12 @@ extern "C" int mfns_spacetime_mg_apply(mfns_spacetime* st, int level, int what, 
   ST_END
 }
 
-extern "C" int mfns_spacetime_vcycle(mfns_spacetime* st, const void* b, void* x, void* stream) {
+extern "C" int mfns_spacetime_vcycle(mfns_spacetime* st, const void* b, void* x, int64_t n, void* stream) {
   ST_BEGIN
   if (!st || !st->mg || !b || !x || b == x) return capi_fail(kErrArg, "bad arguments");
   Stmg& mg = *st->mg;
   StmgLevel& L = *mg.lv[0];
+  if (n != (int64_t)L.Q * L.n) return st_len_fail("b/x", n, (int64_t)L.Q * L.n);
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   MFNS_CUDA(cudaSetDevice(st->ctx->device));
   const size_t bytes = (size_t)L.Q * L.n * 8;
@@ -931,10 +948,11 @@ extern "C" int mfns_spacetime_vcycle(mfns_spacetime* st, const void* b, void* x,
   ST_END
 }
 
-extern "C" int mfns_spacetime_solve(mfns_spacetime* st, const void* b, void* x, double tol, int maxit,
+extern "C" int mfns_spacetime_solve(mfns_spacetime* st, const void* b, void* x, int64_t n, double tol, int maxit,
                                     int* iterations, double* relres, int* converged, void* stream) {
   ST_BEGIN
   if (!st || !st->mg || !b || !x || b == x || !(tol > 0.0) || maxit < 1) return capi_fail(kErrArg, "bad arguments");
+  if (n != (int64_t)st->Q * st->n) return st_len_fail("b/x", n, (int64_t)st->Q * st->n);
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   MFNS_CUDA(cudaSetDevice(st->ctx->device));
   double rel = 0.0;

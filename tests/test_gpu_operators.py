@@ -129,3 +129,48 @@ def test_apply_constraints_matches_oracle(ctx, case):
                     continue
                 expect[base + g] = sum(w * x[base + m] for m, w in masters)
     assert np.abs(y - expect).max() < 1e-13
+
+
+def test_wrong_vector_lengths_are_rejected_and_leave_the_runtime_clean(ctx):
+    """Every vector crosses the C ABI with its length: a length other than the one the call expects
+    is MFNS_ERR_ARG (nothing read or written), and no CUDA error is left pending for the caller's
+    next call.  Local smoothing: the V-cycle takes vectors of cycle_dofs (the fine operator), not of
+    level_dofs[0] (the finest refinement level)."""
+    import ctypes as C
+    from paper_2603_29621_gb300 import _lib as L, api
+    lib = ctx.lib
+    m = api.Mesh(ctx, 3, 2)
+    prob = api.Problem(ctx, m, kind=L.STAB_NS, degree=2, nu=1e-2, dt=1e-2, lambda_max=1.0)
+    n = prob.info.n_dofs
+    s = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    src = torch.rand(n + 8, dtype=torch.float64, device="cuda")
+    dst = torch.full((n + 8,), 7.0, dtype=torch.float64, device="cuda")
+    p = lambda t: C.c_void_p(t.data_ptr())
+    assert lib.mfns_vmult(prob.h, L.OP_SYSTEM, L.FP64, p(src), p(dst), n - 1, s) == L.ERR_ARG
+    assert b"expected" in lib.mfns_last_error()
+    assert lib.mfns_vmult(prob.h, L.OP_SYSTEM, L.FP64, p(src), p(dst), n + 8, s) == L.ERR_ARG
+    assert lib.mfns_vcycle(prob.h, L.FP64, p(src), p(dst), n + 1, s) == L.ERR_ARG
+    assert lib.mfns_solve(prob.h, p(src), p(dst), n - 4, None, s) == L.ERR_ARG
+    assert lib.mfns_smooth(prob.h, 0, L.FP64, p(src), p(dst), n + 1, 0, s) == L.ERR_ARG
+    nc = prob.info.level_dofs[1]
+    assert lib.mfns_prolongate_add(prob.h, 0, L.FP64, p(src), nc + 1, p(dst), n, s) == L.ERR_ARG
+    assert lib.mfns_restrict(prob.h, 0, L.FP64, p(src), n, p(dst), nc - 1, s) == L.ERR_ARG
+    torch.cuda.synchronize()
+    assert bool((dst == 7.0).all())                      # nothing written
+    y = src.clone() * 2                                  # the caller's runtime has no pending error
+    torch.cuda.synchronize()
+    assert float(y.sum()) > 0
+    with pytest.raises(ValueError):
+        prob.vmult(src, dst)                             # the binding checks before calling in
+    # local smoothing: vcycle vectors have cycle_dofs entries
+    m2 = api.Mesh(ctx, 2, 4)
+    m2.refine_ball((0.3, 0.35, 0.4), 0.3, 1)
+    pl = api.Problem(ctx, m2, kind=L.STOKES_A, degree=2, hierarchy=L.LOCAL_SMOOTHING, lambda_max=1.0)
+    assert pl.info.cycle_dofs == pl.info.n_dofs != pl.info.level_dofs[0]
+    short = torch.zeros(pl.info.level_dofs[0], dtype=torch.float64, device="cuda")
+    assert lib.mfns_vcycle(pl.h, L.FP64, p(short), p(torch.zeros_like(short)), short.numel(), s) == L.ERR_ARG
+    b = torch.rand(pl.info.cycle_dofs, dtype=torch.float64, device="cuda")
+    x = torch.zeros_like(b)
+    pl.vcycle(b, x)
+    torch.cuda.synchronize()
+    assert bool(torch.isfinite(x).all()) and float(x.abs().max()) > 0

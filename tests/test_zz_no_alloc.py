@@ -22,8 +22,10 @@ def _smooth_both(lib, prob, level, b, x0, zero, dtype):
     prec = 0 if dtype == torch.float64 else 1
     s = C.c_void_p(torch.cuda.current_stream().cuda_stream)
     from paper_2603_29621_gb300 import _lib as L
-    L.check(lib.mfns_smooth(prob.h, level, prec, C.c_void_p(b.data_ptr()), C.c_void_p(xa.data_ptr()), int(zero), s))
-    L.check(lib.mfns_smooth_noalloc(prob.h, level, prec, C.c_void_p(b.data_ptr()), C.c_void_p(xb.data_ptr()),
+    n = b.numel()
+    L.check(lib.mfns_smooth(prob.h, level, prec, C.c_void_p(b.data_ptr()), C.c_void_p(xa.data_ptr()), n, int(zero),
+                            s))
+    L.check(lib.mfns_smooth_noalloc(prob.h, level, prec, C.c_void_p(b.data_ptr()), C.c_void_p(xb.data_ptr()), n,
                                     int(zero), s))
     torch.cuda.synchronize()
     return xa.double().cpu().numpy(), xb.double().cpu().numpy()
@@ -63,7 +65,7 @@ def test_noalloc_smoother_rejects_levels_beyond_its_scratch():
     assert n > (1 << 20)
     b = torch.zeros(n, dtype=torch.float64, device="cuda")
     x = torch.zeros_like(b)
-    code = ctx.lib.mfns_smooth_noalloc(prob.h, 0, 0, C.c_void_p(b.data_ptr()), C.c_void_p(x.data_ptr()), 0,
+    code = ctx.lib.mfns_smooth_noalloc(prob.h, 0, 0, C.c_void_p(b.data_ptr()), C.c_void_p(x.data_ptr()), n, 0,
                                        C.c_void_p(torch.cuda.current_stream().cuda_stream))
     assert code == L.ERR_ARG
     assert b"at most 1048576" in ctx.lib.mfns_last_error()
