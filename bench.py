@@ -46,6 +46,9 @@ def parse():
     ap.add_argument("--vmult-only", action="store_true", help="time only the FP32 apply (profiling runs)")
     ap.add_argument("--no-solves", action="store_true", help="skip the solve and serving sections")
     ap.add_argument("--serve-requests", type=int, default=32, help="requests of the bounded serving stream")
+    ap.add_argument("--section", default=None, choices=["solves", "transient", "serving", "hp", "spacetime",
+                                                        "next_rows"],
+                    help="run one section of the line alone and print its JSON (used in child processes)")
     return ap.parse_args()
 
 
@@ -122,27 +125,93 @@ def ncu_traffic():
         return None
 
 
-def cpu_baseline(seconds=10.0):
-    """The oracle (assembled CSR, scipy, one thread) on a 16^3-cell sample of the same operator."""
-    from oracle import assemble, mesh
-    from paper_2603_29621_gb300 import inputs
+def _cpu_model():
+    """The host CPU's model string (lscpu, else /proc/cpuinfo)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu part")):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
 
-    t0 = time.perf_counter()
-    op = assemble.Problem(mesh.uniform(3, CPU_SAMPLE_N), "stab_ns", 2, nu=1e-2, dt=1e-2)
-    A = op.assemble()
-    t_asm = time.perf_counter() - t0
-    x = inputs.uniform_vector(A.shape[0])
-    y = A @ x
-    reps, t0 = 0, time.perf_counter()
-    while time.perf_counter() - t0 < seconds:
-        y = A @ x
-        reps += 1
-    dt = time.perf_counter() - t0
-    return {"value": A.shape[0] * reps / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": (f"oracle vmult (scipy CSR SpMV, 1 thread) on {CPU_SAMPLE_N}^3 Q2Q2 cells of the same "
-                       f"operator ({A.shape[0]} DoFs, {A.nnz} nnz), {reps} products in {dt:.1f} s; "
-                       f"assembly {t_asm:.1f} s not timed"),
-            "ms_per_step": 1e3 * dt / reps, "n_dofs": int(A.shape[0])}
+
+class OracleSpmv:
+    """The oracle's vmult (its assembled CSR matrix, scipy's product) over row blocks on `threads`
+    host threads (scipy's sparse product releases the GIL): the arithmetic is the oracle's, only
+    the rows are split between cores."""
+
+    def __init__(self, n_cells=CPU_SAMPLE_N):
+        from concurrent.futures import ThreadPoolExecutor
+
+        from oracle import assemble, mesh
+        from paper_2603_29621_gb300 import inputs
+
+        t0 = time.perf_counter()
+        op = assemble.Problem(mesh.uniform(3, n_cells), "stab_ns", 2, nu=1e-2, dt=1e-2)
+        self.A = op.assemble().tocsr()
+        self.t_asm = time.perf_counter() - t0
+        self.n_cells = n_cells
+        self.x = inputs.uniform_vector(self.A.shape[0])
+        self.y = np.empty_like(self.x)
+        self._pool = ThreadPoolExecutor
+        self.threads = 1
+        self.set_threads(1)
+
+    def set_threads(self, t):
+        n = self.A.shape[0]
+        self.threads = t
+        self.bounds = np.linspace(0, n, t + 1).astype(np.int64)
+        self.blocks = [self.A[self.bounds[i]:self.bounds[i + 1]] for i in range(t)]
+        self.pool = self._pool(t)
+
+    def _job(self, i):
+        self.y[self.bounds[i]:self.bounds[i + 1]] = self.blocks[i] @ self.x
+
+    def __call__(self):
+        list(self.pool.map(self._job, range(self.threads)))
+
+    def rate(self, seconds):
+        """(DoF/s, products, seconds) of back-to-back products for about `seconds`."""
+        self()
+        reps, t0 = 0, time.perf_counter()
+        while time.perf_counter() - t0 < seconds:
+            self()
+            reps += 1
+        dt = time.perf_counter() - t0
+        return self.A.shape[0] * reps / dt, reps, dt
+
+    def sample(self):
+        return (f"oracle vmult (assembled CSR, scipy product over row blocks) on {self.n_cells}^3 Q2Q2 cells "
+                f"of the same operator ({self.A.shape[0]} DoFs, {self.A.nnz} nnz)")
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def cpu_baseline(seconds=8.0):
+    """The oracle on all host cores and on one core, on a 12^3-cell sample of the same operator."""
+    o = OracleSpmv()
+    cores = host_cores()
+    v1, r1, t1 = o.rate(seconds / 2)
+    o.set_threads(cores)
+    vn, rn, tn = o.rate(seconds / 2)
+    return {"value": vn, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": (o.sample() + f"; {rn} products in {tn:.1f} s on {cores} threads; assembly "
+                       f"{o.t_asm:.1f} s not timed"),
+            "cpu_model": _cpu_model(), "nproc": os.cpu_count(),
+            "one_core": {"value": v1, "unit": UNIT, "products": r1, "seconds": t1}}
 
 
 def solve_section(api, L, inputs, torch, tol_ns=1e-13, tol_stokes=1e-14):
@@ -186,7 +255,7 @@ def solve_section(api, L, inputs, torch, tol_ns=1e-13, tol_stokes=1e-14):
              "level_cells": [int(p.info.level_cells[i]) for i in range(p.info.n_levels)],
              "level_dofs": [int(p.info.level_dofs[i]) for i in range(p.info.n_levels)]}
         try:  # one multigrid cycle in the preconditioner's precision (device time, warm)
-            vb = torch.tensor(inputs.uniform_vector(int(p.info.level_dofs[0]), seed=6), device="cuda",
+            vb = torch.tensor(inputs.uniform_vector(int(p.info.cycle_dofs), seed=6), device="cuda",
                               dtype=torch.float32 if mgp == L.FP32 else torch.float64)
             vx = torch.zeros_like(vb)
             for _ in range(3):
@@ -579,31 +648,84 @@ def transient_section(api, L, inputs, torch, n=48, steps=4, cfl=0.5, nu=1e-2):
 
 
 def run_reference(args, world, rank):
+    """The oracle (the reference arm: a plain assembled-matrix program written from the paper) on the
+    host's cores, on a bounded 12^3 sample of the headline workload; rank 0 only."""
     if rank != 0:
         return
-    from oracle import assemble, mesh
-    from paper_2603_29621_gb300 import inputs
-
-    op = assemble.Problem(mesh.uniform(3, CPU_SAMPLE_N), "stab_ns", 2, nu=1e-2, dt=1e-2)
-    A = op.assemble()
-    x = inputs.uniform_vector(A.shape[0])
+    o = OracleSpmv()
+    cores = host_cores()
+    o.set_threads(cores)
     for _ in range(args.warmup):
-        A @ x
+        o()
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        A @ x
+        o()
     dt = time.perf_counter() - t0
-    val = A.shape[0] * args.steps / dt
+    val = o.A.shape[0] * args.steps / dt
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": 0,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
             "config": {"workload": f"stab-NS Q2Q2 vmult on {CPU_SAMPLE_N}^3 cells (bounded sample of the 64^3 "
                                    "workload), nu=1e-2, dt=1e-2, Taylor-Green frozen state"},
-            "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"oracle scipy CSR SpMV on {CPU_SAMPLE_N}^3 Q2Q2 cells, {A.shape[0]} DoFs"},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": o.sample(),
+                             "cpu_model": _cpu_model(), "nproc": os.cpu_count()},
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+SECTIONS = ("solves", "transient", "serving", "hp", "spacetime", "next_rows")
+SECTION_TIMEOUT_S = {"solves": 420, "transient": 240, "serving": 420, "hp": 240, "spacetime": 240, "next_rows": 300}
+
+
+def run_section(name, args):
+    """One section of the line in a child process: a failure there (an exception, a CUDA error that
+    poisons the context, a timeout) is recorded in the line and cannot take the headline with it."""
+    cmd = [sys.executable, os.path.abspath(__file__), "--section", name, "--serve-requests",
+           str(args.serve_requests)]
+    t0 = time.perf_counter()
+    try:
+        r = subprocess.run(cmd, capture_output=True, text=True, timeout=SECTION_TIMEOUT_S[name])
+    except subprocess.TimeoutExpired:
+        return {"error": f"timed out after {SECTION_TIMEOUT_S[name]} s"}
+    wall = time.perf_counter() - t0
+    lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
+    if r.returncode != 0 or not lines:
+        return {"error": f"exit {r.returncode}: " + (r.stderr.strip().splitlines() or ["no output"])[-1][:400],
+                "wall_s": wall}
+    try:
+        out = json.loads(lines[-1])
+    except ValueError as e:
+        return {"error": f"unparsable section output: {e}", "wall_s": wall}
+    out["wall_s"] = wall
+    return out
+
+
+def section_main(args):
+    import torch
+
+    import __graft_entry__ as g
+    from paper_2603_29621_gb300 import _lib as L
+    from paper_2603_29621_gb300 import api, inputs
+
+    torch.cuda.set_device(0)
+    g.build()
+    name = args.section
+    if name == "solves":
+        out = solve_section(api, L, inputs, torch)
+    elif name == "transient":
+        out = transient_section(api, L, inputs, torch)
+    elif name == "serving":
+        out = serving_section(api, L, torch, args.serve_requests)
+    elif name == "hp":
+        out = hp_section(api, L, inputs, torch)
+    elif name == "spacetime":
+        out = spacetime_section(api, L, inputs, torch)
+    elif name == "next_rows":
+        out = next_rows_section(api, L, inputs, torch)
+    else:
+        raise SystemExit(f"unknown section {name}")
+    print(json.dumps(out), flush=True)
 
 
 def run_ours(args, world, rank, local):
@@ -626,6 +748,7 @@ def run_ours(args, world, rank, local):
                        mg_precision=L.FP32)
     ndof = prob.info.n_dofs
     ncell = prob.info.n_cells
+    nodes = ndof // 4
     x64 = torch.tensor(inputs.uniform_vector(ndof), device=dev)
     src32, src64 = x64.float(), x64
     dst32, dst64 = torch.empty_like(src32), torch.empty_like(src64)
@@ -638,12 +761,10 @@ def run_ours(args, world, rank, local):
             torch.distributed.barrier()
             torch.cuda.synchronize()
 
-    def timed(fn, steps, warmup, nvtx=None):
+    def timed(fn, steps, warmup):
         for _ in range(warmup):
             fn()
         barrier()
-        if nvtx:
-            torch.cuda.nvtx.range_push(nvtx)
         total = 0.0
         for s in range(steps):
             flush.fill_(float(s))
@@ -653,19 +774,17 @@ def run_ours(args, world, rank, local):
             e1.record(stream)
             e1.synchronize()
             total += e0.elapsed_time(e1)
-        if nvtx:
-            torch.cuda.nvtx.range_pop()
         barrier()
         return total / steps  # ms per step
 
-    # ---- headline: FP32 vmult
+    # ---- headline: FP32 vmult (the cell kernel's colour launches timed on the launching stream)
     clocks = Clocks(local)
     prob.kernel_timing(1)
-    ms32 = timed(lambda: prob.vmult(src32, dst32), args.steps, args.warmup, nvtx="timed_vmult_fp32")
+    ms32 = timed(lambda: prob.vmult(src32, dst32), args.steps, args.warmup)
     kms, klaunch = prob.kernel_timing(2)
     prob.kernel_timing(0)
     clk = clocks.stop()
-    # the warm-up launches were recorded as well: use the average over all recorded launches
+    # the warm-up launches were recorded as well: the average over all recorded launches
     avg_launch_ms = kms / max(klaunch, 1)
     launches_per_step = klaunch // (args.steps + args.warmup)
     if args.vmult_only:
@@ -673,22 +792,7 @@ def run_ours(args, world, rank, local):
             print(json.dumps({"vmult_fp32_ms": ms32, "dofs_per_s": world * ndof / (ms32 * 1e-3),
                               "avg_launch_ms": avg_launch_ms, "launches_per_step": launches_per_step}))
         return
-    # ---- FP64 vmult, Chebyshev-3 sweep, V-cycle (FP32)
-    steps64 = max(3, args.steps // 4)
-    ms64 = timed(lambda: prob.vmult(src64, dst64), steps64, 3)
-    b32 = src32.clone()
-    xs = torch.zeros_like(b32)
-    ms_cheb = timed(lambda: prob.smooth(0, b32, xs, x_is_zero=False), max(3, args.steps // 2), 3)
-    ms_vc = timed(lambda: prob.vcycle(b32, xs), max(3, args.steps // 4), 3)
-    # the same sweep and cycle with the update / residual fused into the cell kernel's scatter
-    prob_f = api.Problem(ctx, m, kind=L.STAB_NS, degree=2, nu=1e-2, dt=1e-2, smoother=1, smoother_degree=3,
-                         mg_precision=L.FP32, fused_smoother=1)
-    for l in range(prob.info.n_levels - 1):
-        prob_f.set_lambda_max(l, prob.info.lambda_max[l])
-    ms_cheb_f = timed(lambda: prob_f.smooth(0, b32, xs, x_is_zero=False), max(3, args.steps // 2), 3)
-    ms_vc_f = timed(lambda: prob_f.vcycle(b32, xs), max(3, args.steps // 4), 3)
-    prob_f.close()
-    # ---- end to end through the public API with host buffers (pinned)
+    # ---- end to end through the public API with host buffers (pinned), every step
     h_src = torch.empty(ndof, dtype=torch.float32, pin_memory=True)
     h_src.copy_(src32.cpu())
     h_dst = torch.empty(ndof, dtype=torch.float32, pin_memory=True)
@@ -700,17 +804,61 @@ def run_ours(args, world, rank, local):
 
     ms_e2e = timed(e2e_step, args.steps, args.warmup)
     # ---- max over ranks
-    tt = torch.tensor([ms32, ms64, ms_cheb, ms_vc, ms_e2e], device=dev, dtype=torch.float64)
+    tt = torch.tensor([ms32, ms_e2e], device=dev, dtype=torch.float64)
     if world > 1:
         torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-    ms32, ms64, ms_cheb, ms_vc, ms_e2e = tt.tolist()
+    ms32, ms_e2e = tt.tolist()
+    extra = {}
+    if rank == 0:
+        # ---- FP64 vmult, Chebyshev-3 sweep, V-cycle (FP32), each recorded, none can end the run
+        def guarded(key, fn):
+            try:
+                extra[key] = fn()
+            except Exception as e:  # noqa: BLE001 -- reported in the JSON line
+                extra[key] = {"error": f"{type(e).__name__}: {e}"}
+
+        steps_s = max(3, args.steps // 4)
+        guarded("fp64", lambda: (lambda ms: {"value": world * ndof / (ms * 1e-3), "unit": UNIT,
+                                             "ms_per_apply": ms})(
+            timed(lambda: prob.vmult(src64, dst64), steps_s, 3)))
+        b32 = src32.clone()
+        xs = torch.zeros_like(b32)
+
+        def cheb():
+            ms = timed(lambda: prob.smooth(0, b32, xs, x_is_zero=False), max(3, args.steps // 2), 3)
+            return {"ms_per_sweep": ms, "dofs_per_s": world * ndof / (ms * 1e-3)}
+
+        def vcyc():
+            assert prob.info.cycle_dofs == ndof
+            return {"ms": timed(lambda: prob.vcycle(b32, xs), steps_s, 3), "levels": prob.info.n_levels}
+
+        guarded("chebyshev3_fp32", cheb)
+        guarded("vcycle_fp32", vcyc)
+
+        def fused():
+            pf = api.Problem(ctx, m, kind=L.STAB_NS, degree=2, nu=1e-2, dt=1e-2, smoother=1, smoother_degree=3,
+                             mg_precision=L.FP32, fused_smoother=1)
+            try:
+                for lvl in range(prob.info.n_levels - 1):
+                    pf.set_lambda_max(lvl, prob.info.lambda_max[lvl])
+                return {"ms_per_sweep": timed(lambda: pf.smooth(0, b32, xs, x_is_zero=False),
+                                              max(3, args.steps // 2), 3),
+                        "vcycle_ms": timed(lambda: pf.vcycle(b32, xs), steps_s, 3)}
+            finally:
+                pf.close()
+
+        guarded("fused_smoother_fp32", fused)
+    prob.close()
+    m.close()
+    ctx.close()
+    del flush
+    torch.cuda.empty_cache()
     if rank != 0:
         return
     value = world * ndof / (ms32 * 1e-3)
     cells_per_launch = ncell / launches_per_step if launches_per_step else ncell
-    flops_launch = FLOP_PER_CELL * cells_per_launch
     peak_alu = N_SM * FP32_LANES * 2 * SM_MHZ_MAX * 1e6 / 1e12    # TFLOP/s
-    achieved = flops_launch / (avg_launch_ms * 1e-3) / 1e12
+    achieved_alu = FLOP_PER_CELL * cells_per_launch / (avg_launch_ms * 1e-3) / 1e12
     traffic = ncu_traffic()
     peaks = {}
     try:
@@ -718,8 +866,12 @@ def run_ours(args, world, rank, local):
     except (OSError, ValueError):
         pass
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
-    alg_bytes = 8 * (ndof // 4) * 4 + ncell * FQ_BYTES_PER_CELL_F32  # src + dst (4 fields, fp32) + frozen point data
-    bytes_launch = alg_bytes * cells_per_launch / ncell                 # the cells of one colour launch
+    # algorithmic bytes of one apply: src and dst (4 fields each) and the frozen state (u, p: 4
+    # fields) once per node, FP32 -- 12 x 2,146,689 x 4 B = 103.0 MB at 64^3; a colour launch
+    # processes 1/launches_per_step of the cells and is charged that share
+    alg_bytes = 12 * nodes * 4
+    bytes_launch = alg_bytes * cells_per_launch / ncell
+    achieved = bytes_launch / (avg_launch_ms * 1e-3) / 1e9
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms32, "higher_is_better": True, "scaling": "weak",
@@ -729,52 +881,52 @@ def run_ours(args, world, rank, local):
                    "n_cells": ncell, "n_dofs": ndof, "parallelism": f"replicas x{world}",
                    "l2": "flushed between timed steps (512 MiB write)"},
         "clocks": clk,
-        "gpu_launches": launches_per_step * args.steps + args.steps,  # cell-kernel colours + constrained-row copy
+        # cell-kernel colour launches, the dst clear and the constrained-row copy of every step
+        "gpu_launches": (launches_per_step + 2) * args.steps,
         "e2e": {"value": world * ndof / (ms_e2e * 1e-3), "unit": UNIT, "h2d_bytes_per_step": ndof * 4,
-                "d2h_bytes_per_step": ndof * 4},
-        # with the frozen point data precomputed the apply does 17 kflop per ~1.99 kB: below the FP32
-        # ridge (80.5 TFLOP/s / 6.78 TB/s = 11.9 flop/B), so the binding roof is HBM; the ALU
-        # fraction is given beside it
-        "roofline": {"bound": "hbm", "achieved": bytes_launch / (avg_launch_ms * 1e-3) / 1e9, "peak": hbm_peak,
-                     "unit": "GB/s", "frac": bytes_launch / (avg_launch_ms * 1e-3) / 1e9 / hbm_peak,
-                     "traffic": traffic, "peak_source": "MEASURED_PEAKS.json hbm_gbs (copy, burst)",
-                     "kernel": "op_kernel<3,2,STAB_NS,float,structured,precomputed frozen data>",
-                     "alg_bytes_per_launch": bytes_launch, "cells_per_launch": cells_per_launch,
-                     "avg_launch_ms": avg_launch_ms,
-                     "intensity_flop_per_byte": FLOP_PER_CELL * ncell / alg_bytes,
-                     "ridge_flop_per_byte": peak_alu * 1e12 / (hbm_peak * 1e9),
-                     "alu": {"achieved_tflops": achieved, "peak_tflops": peak_alu, "frac": achieved / peak_alu,
-                             "flop_per_cell": FLOP_PER_CELL},
+                "d2h_bytes_per_step": ndof * 4, "ms_per_step": ms_e2e},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                     "frac": achieved / hbm_peak, "traffic": traffic,
+                     "peak_source": "MEASURED_PEAKS.json hbm_gbs (copy, burst), of measured",
+                     "kernel": "op_kernel<3,2,STAB_NS,float,structured> (one colour launch)",
+                     "alg_bytes_per_apply": alg_bytes, "alg_bytes_per_launch": bytes_launch,
+                     "alg_bytes_rule": "12 fields (src 4, dst 4, frozen u,p 4) x nodes x 4 B",
+                     "cells_per_launch": cells_per_launch, "avg_launch_ms": avg_launch_ms,
+                     "launches_per_apply": launches_per_step,
                      "whole_apply": {"achieved_gbs": alg_bytes / (ms32 * 1e-3) / 1e9,
-                                     "frac": alg_bytes / (ms32 * 1e-3) / 1e9 / hbm_peak,
-                                     "alg_bytes_per_apply": alg_bytes}},
-        "fp64": {"value": world * ndof / (ms64 * 1e-3), "unit": UNIT, "ms_per_apply": ms64},
-        "chebyshev3_fp32": {"ms_per_sweep": ms_cheb, "dofs_per_s": world * ndof / (ms_cheb * 1e-3),
-                            "ms_per_sweep_fused": ms_cheb_f},
-        "vcycle_fp32": {"ms": ms_vc, "levels": prob.info.n_levels, "ms_fused": ms_vc_f},
+                                     "frac": alg_bytes / (ms32 * 1e-3) / 1e9 / hbm_peak},
+                     "alu": {"achieved_tflops": achieved_alu, "peak_tflops": peak_alu,
+                             "frac": achieved_alu / peak_alu, "flop_per_cell": FLOP_PER_CELL,
+                             "peak_rule": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz"},
+                     "ridge_flop_per_byte": peak_alu * 1e12 / (hbm_peak * 1e9),
+                     "intensity_flop_per_byte": FLOP_PER_CELL * ncell / alg_bytes,
+                     "with_point_data": {"note": "bytes the kernel reads by design: src, dst and the "
+                                                 "precomputed frozen point block (1,728 B per cell)",
+                                         "bytes_per_launch": (8 * nodes * 4 * cells_per_launch / ncell
+                                                              + cells_per_launch * FQ_BYTES_PER_CELL_F32),
+                                         "achieved_gbs": (8 * nodes * 4 * cells_per_launch / ncell
+                                                          + cells_per_launch * FQ_BYTES_PER_CELL_F32)
+                                         / (avg_launch_ms * 1e-3) / 1e9}},
     }
-    if not args.no_solves:
-        prob.close()
-        m.close()
-        ctx.close()
-        t0 = time.perf_counter()
-        line["solves"] = solve_section(api, L, inputs, torch)
-        line["transient"] = transient_section(api, L, inputs, torch)
-        line["serving"] = serving_section(api, L, torch, args.serve_requests)
-        line["solves_serving_wall_s"] = time.perf_counter() - t0
-        line["hp"] = hp_section(api, L, inputs, torch)
-        line["spacetime"] = spacetime_section(api, L, inputs, torch)
-        line["next_rows"] = next_rows_section(api, L, inputs, torch)
+    line.update(extra)
     if world == 1 and not args.no_cpu_baseline:
-        cb = cpu_baseline()
-        cb.pop("ms_per_step", None)
-        cb.pop("n_dofs", None)
-        line["cpu_baseline"] = cb
+        try:
+            line["cpu_baseline"] = cpu_baseline()
+        except Exception as e:  # noqa: BLE001
+            line["cpu_baseline"] = {"error": f"{type(e).__name__}: {e}", "kind": "oracle"}
+    if world == 1 and not args.no_solves:
+        t0 = time.perf_counter()
+        for name in SECTIONS:
+            line[name] = run_section(name, args)
+        line["sections_wall_s"] = time.perf_counter() - t0
     print(json.dumps(line), flush=True)
 
 
 def main():
     args = parse()
+    if args.section:
+        section_main(args)
+        return
     world, rank, local = dist_setup(args.gpus)
     if args.impl == "reference":
         run_reference(args, world, rank)
