@@ -19,14 +19,14 @@ struct Team {
     constexpr int w = sizeof(T) / 4, m = 32 / w;
     return NBUF * BUF + (((TPC - NBUF * BUF) % m) + m) % m;
   }
-  // Staged frozen blocks live in a second shared-memory region.  Per-team stride in bytes: the
-  // block rounded up so that consecutive teams start TPC values (rounded up to 8 bytes) apart
-  // modulo the 128-byte bank window; the lanes of the CPW teams then read disjoint banks
-  // whenever CPW * TPC values fit in 32 banks.  The stride is a multiple of 8 bytes (cp.async).
+  // Staged frozen blocks live in a later shared-memory region, one per team.  A block is read in
+  // 16-byte quads, the TPC lanes of a team reading consecutive quads; the per-team stride is the
+  // block (a multiple of 16 bytes) rounded up to 16 modulo 128 bytes, so that the next team's
+  // first quad continues the bank sequence where this team's lanes end and the quarter-warp
+  // phases of a 128-bit load hit 8 distinct bank groups.
   template <typename T>
   __host__ __device__ static constexpr size_t stage_stride_bytes(size_t block_bytes) {
-    constexpr size_t shift = ((TPC * sizeof(T) + 7) / 8 * 8) % 128;
-    return block_bytes + (shift + 128 - block_bytes % 128) % 128;
+    return block_bytes + (16 + 128 - block_bytes % 128) % 128;
   }
 };
 
@@ -68,12 +68,42 @@ __device__ __forceinline__ int64_t structured_node(int n, const int cc[3], int a
 template <int DIM>
 struct FrozenPoint {
   static constexpr int NFQ = DIM + DIM * DIM + DIM + 1;  // u, grad u, Rbar, tau
-  // one cell's block: [point l][value k][lane], padded to a multiple of 4 values (16 bytes in FP32)
+  static constexpr int NQ = (NFQ + 3) / 4;                // quads of 4 values per point and lane
+  // one cell's block: [point l][quad][lane][4 values] (values NFQ..4 NQ-1 unused): a lane reads
+  // its point's values as NQ aligned 4-vectors, the lanes of a team consecutive ones
   template <typename T>
   __host__ __device__ static constexpr int block(int q) {
-    return (ipow(q, DIM - 1) * q * NFQ + 3) / 4 * 4;
+    return ipow(q, DIM - 1) * q * NQ * 4;
+  }
+  // offset of value k of point l of lane `lane` (tpc lanes per cell)
+  __host__ __device__ static constexpr int at(int l, int k, int lane, int tpc) {
+    return ((l * NQ + (k >> 2)) * tpc + lane) * 4 + (k & 3);
   }
 };
+
+// Completion of a team's staged block: bounded wait on its mbarrier (phase 0).  A wait that runs
+// out sets bit 0 of *err (when given) and waits once more, so that the copy is not left writing
+// into the block of a finished CTA; the computation then goes on (no early exit: every lane of
+// the warp must reach the same __syncwarp calls).
+__device__ __forceinline__ bool mbar_try_wait0(unsigned addr) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(addr)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ void mbar_wait0_bounded(unsigned addr, int* err) {
+  constexpr uint32_t kLimit = 1u << 22;
+  for (uint32_t it = 0; it < kLimit; ++it)
+    if (mbar_try_wait0(addr)) return;
+  if (err) atomicOr(err, 1);
+  for (uint32_t it = 0; it < kLimit; ++it)
+    if (mbar_try_wait0(addr)) return;
+}
 
 // EPI: the fused smoother / residual epilogue is compiled in (structured launches only).
 // MULTI: one launch over the cells of several problems (structured, plain products); each block
@@ -149,11 +179,14 @@ op_kernel(const OpArgs<T, K + 1, K + 1, (OP == OP_STOKES ? K : K + 1)> args) {
   T* buf0 = smem + (size_t)(warp * (TM::CPW + 1) + team) * TM::template stride<T>();
   T* buf1 = buf0 + BUF;
   T* buf2 = buf1 + BUF;
-  // staged frozen block (FQ == 1): [point][value][lane], 8-byte aligned (second region)
+  // staged frozen blocks (FQ == 1): after the team buffers, one mbarrier per team, then one block
+  // per team (16-byte aligned, see Team::stage_stride_bytes); the spare lanes use team 0's
   const size_t region1 = ((sizeof(T) * (size_t)(blockDim.x >> 5) * (TM::CPW + 1) * TM::template stride<T>() + 15) / 16) * 16;
-  // the spare lanes read team 0's block (same words as its lanes: broadcast, no bank conflict)
-  T* fqs = reinterpret_cast<T*>(smem_raw + region1 + (size_t)(warp * TM::CPW + (lane_active ? team : 0)) *
-                                                         TM::template stage_stride_bytes<T>(sizeof(T) * FQB));
+  const int team_slot = warp * TM::CPW + (lane_active ? team : 0);
+  const size_t mbar_bytes = ((size_t)(blockDim.x >> 5) * TM::CPW * 8 + 15) / 16 * 16;
+  const unsigned mbar_addr = (unsigned)__cvta_generic_to_shared(smem_raw + region1) + 8u * (unsigned)team_slot;
+  T* fqs = reinterpret_cast<T*>(smem_raw + region1 + mbar_bytes +
+                                (size_t)team_slot * TM::template stage_stride_bytes<T>(sizeof(T) * FQB));
 
   // ---- which cell
   int64_t cell;
@@ -185,6 +218,9 @@ op_kernel(const OpArgs<T, K + 1, K + 1, (OP == OP_STOKES ? K : K + 1)> args) {
       cellpos = cell;
     }
   }
+  // the next colour's grid may be scheduled once every block of this one has started (it waits
+  // for this grid's completion before it touches dst)
+  asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
   const T h = STRUCT ? hs : args.hcell[cell];
   const uint32_t mask = STRUCT ? 0u : args.mask[cell];
   // warp-uniform: every team of the warp takes the constraint path if one needs it
@@ -264,15 +300,10 @@ op_kernel(const OpArgs<T, K + 1, K + 1, (OP == OP_STOKES ? K : K + 1)> args) {
         if constexpr (sizeof(T) == 4) {
           const float4 v = own ? __ldg(reinterpret_cast<const float4*>(srcp + node[c] * 4)) : make_float4(0, 0, 0, 0);
           u0[0][c] = v.x; u0[1][c] = v.y; u0[2][c] = v.z; u0[3][c] = v.w;
-          const float4 w = (own && valid) ? *reinterpret_cast<const float4*>(dstp + node[c] * 4) : make_float4(0, 0, 0, 0);
-          d0[0][c] = w.x; d0[1][c] = w.y; d0[2][c] = w.z; d0[3][c] = w.w;
         } else {
           const double2 v0 = own ? __ldg(reinterpret_cast<const double2*>(srcp + node[c] * 4)) : make_double2(0, 0);
           const double2 v1 = own ? __ldg(reinterpret_cast<const double2*>(srcp + node[c] * 4 + 2)) : make_double2(0, 0);
           u0[0][c] = v0.x; u0[1][c] = v0.y; u0[2][c] = v1.x; u0[3][c] = v1.y;
-          const double2 w0 = (own && valid) ? *reinterpret_cast<const double2*>(dstp + node[c] * 4) : make_double2(0, 0);
-          const double2 w1 = (own && valid) ? *reinterpret_cast<const double2*>(dstp + node[c] * 4 + 2) : make_double2(0, 0);
-          d0[0][c] = w0.x; d0[1][c] = w0.y; d0[2][c] = w1.x; d0[3][c] = w1.y;
         }
       } else {
 #pragma unroll
@@ -298,22 +329,23 @@ op_kernel(const OpArgs<T, K + 1, K + 1, (OP == OP_STOKES ? K : K + 1)> args) {
   T gp[DIM][Q], lb[DIM][Q], pb[Q];
   constexpr int NFQ = FrozenPoint<DIM>::NFQ;
   if constexpr (Tr::FROZEN && FQ == 1) {
-    // the team copies its cell's block (contiguous in global memory) with cp.async, in 16-byte
-    // chunks where the team's staging slot is 16-byte aligned and 8-byte chunks otherwise; the
-    // copy overlaps the interpolation of the trial fields and is awaited before first use
-    constexpr int CB = TM::template stage_stride_bytes<T>(sizeof(T) * FQB) % 16 == 0 ? 16 : 8;
-    constexpr int CH = FQB * (int)sizeof(T) / CB;  // chunks per cell
-    const char* gsrc = reinterpret_cast<const char*>(fqd + (size_t)cellpos * FQB);
-    if (lane_active) {
+    // the team's cell block (contiguous in global memory, a multiple of 16 bytes, 16-byte aligned)
+    // comes in with one TMA bulk copy issued by the team's first lane and tracked by the team's
+    // mbarrier; it overlaps the interpolation of the trial fields and is awaited before first use
+    constexpr unsigned BB = (unsigned)(FQB * sizeof(T));
+    static_assert(BB % 16 == 0, "bulk copies move multiples of 16 bytes");
+    if (lane_active && tid == 0) {
       const unsigned sdst = (unsigned)__cvta_generic_to_shared(fqs);
-      for (int c = tid; c < CH; c += TM::TPC) {
-        if constexpr (CB == 16)
-          asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sdst + 16 * c), "l"(gsrc + 16 * c) : "memory");
-        else
-          asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sdst + 8 * c), "l"(gsrc + 8 * c) : "memory");
-      }
+      const T* gsrc = fqd + (size_t)cellpos * FQB;
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mbar_addr) : "memory");
+      asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+      asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(mbar_addr), "r"(BB) : "memory");
+      asm volatile(
+          "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(sdst),
+          "l"(gsrc), "r"(BB), "r"(mbar_addr)
+          : "memory");
     }
-    asm volatile("cp.async.commit_group;\n" ::: "memory");
   }
   if constexpr (Tr::FROZEN && FQ != 1) {
     T fz[DIM + 1][N];
@@ -395,8 +427,8 @@ op_kernel(const OpArgs<T, K + 1, K + 1, (OP == OP_STOKES ? K : K + 1)> args) {
     if constexpr (FQ == 2) {
       if (valid) {
         constexpr int B = FrozenPoint<DIM>::template block<T>(Q);
-        T* fp = fqd + (size_t)cellpos * B + tid;
-        auto at = [&](int l, int k) -> T& { return fp[(l * NFQ + k) * TM::TPC]; };
+        T* fp = fqd + (size_t)cellpos * B;
+        auto at = [&](int l, int k) -> T& { return fp[FrozenPoint<DIM>::at(l, k, tid, TM::TPC)]; };
 #pragma unroll
         for (int l = 0; l < Q; ++l) {
 #pragma unroll
@@ -552,44 +584,12 @@ op_kernel(const OpArgs<T, K + 1, K + 1, (OP == OP_STOKES ? K : K + 1)> args) {
         }
         integrate<DIM, Q, N, true, true, T>(c0, cg, r[DIM], buf1, buf2, ti, tj, tab.S, tab.D);
       }
-    } else {  // OP_STAB_NS
-      // frozen point values: registers (FQ 0) or the staged shared-memory block (FQ 1)
-      // each lane waits for its own copies; the warp barrier then publishes every lane's chunks
-      if constexpr (FQ == 1) {
-        asm volatile("cp.async.wait_group 0;\n" ::: "memory");
-        __syncwarp();
-      }
-      auto UB = [&](int d, int l) -> T {
-        if constexpr (FQ == 1) return fqs[(l * NFQ + d) * TM::TPC + tid];
-        else return Ub[d][l];
-      };
-      auto GB = [&](int i, int j, int l) -> T {
-        if constexpr (FQ == 1) return fqs[(l * NFQ + DIM + i * DIM + j) * TM::TPC + tid];
-        else return Gb[i][j][l];
-      };
-      auto RB = [&](int i, int l) -> T {
-        if constexpr (FQ == 1) return fqs[(l * NFQ + DIM + DIM * DIM + i) * TM::TPC + tid];
-        else return Rb[i][l];
-      };
-      auto TAU = [&](int l) -> T {
-        if constexpr (FQ == 1) return fqs[(l * NFQ + NFQ - 1) * TM::TPC + tid];
-        else return tau[l];
-      };
-      const T cfm = cf_[0], cfc = cf_[1], cfn = cf_[2], cfs = cf_[3], cfsn = cf_[4],
-              cfp = cf_[5], cfl = cf_[6];
-      const T cm = cm_;
-      T Rl[DIM][Q], vc[DIM][Q], gc[DIM][DIM][Q], dv[Q];
-#pragma unroll
-      for (int l = 0; l < Q; ++l) {
-        dv[l] = 0;
-#pragma unroll
-        for (int i = 0; i < DIM; ++i) {
-          Rl[i][l] = 0;
-          vc[i][l] = 0;
-#pragma unroll
-          for (int d = 0; d < DIM; ++d) gc[i][d][l] = 0;
-        }
-      }
+    } else {  // OP_STAB_NS, the Jacobian at the frozen state (Section 5)
+      // Phase 1: every trial field at the lane's points -- velocity values, physical gradients and
+      // the part of the strong residual that needs no frozen data (grad p - nu lap u); pressure.
+      const T cmm = cf_[0] * cm_, cfc = cf_[1], cfn = cf_[2], cfs = cf_[3], cfsn = cf_[4], cfp = cf_[5];
+      const T lapc = cf_[6] * nu * inv_h * inv_h;
+      T tv[DIM][Q], tg[DIM][DIM][Q], tr[DIM][Q];
 #pragma unroll
       for (int j = 0; j < DIM; ++j) {
         T val[Q], g[DIM][Q], h2[DIM][Q];
@@ -597,29 +597,18 @@ op_kernel(const OpArgs<T, K + 1, K + 1, (OP == OP_STOKES ? K : K + 1)> args) {
         derivatives<DIM, Q, true, T>(val, g, h2, buf1, ti, tj, tab.D, tab.D2);
 #pragma unroll
         for (int l = 0; l < Q; ++l) {
-          T ugu = 0, lap = 0;
+          T lap = 0;
 #pragma unroll
           for (int d = 0; d < DIM; ++d) {
-            g[d][l] *= inv_h;
-            ugu += UB(d, l) * g[d][l];
+            tg[j][d][l] = g[d][l] * inv_h;
             lap += h2[d][l];
           }
-          lap *= inv_h * inv_h;
-          const T gal = cfm * cm * val[l] + cfc * ugu;  // component-diagonal Galerkin/residual part
-          vc[j][l] += gal;
-          Rl[j][l] += gal - cfl * nu * lap;
-#pragma unroll
-          for (int i = 0; i < DIM; ++i) {
-            const T nt = cfn * val[l] * GB(i, j, l);   // (du . grad ub)_i from component j
-            vc[i][l] += nt;
-            Rl[i][l] += nt;
-            gc[i][j][l] += cfsn * TAU(l) * RB(i, l) * val[l];  // tau Rbar_i (du . grad v_i)
-          }
-#pragma unroll
-          for (int d = 0; d < DIM; ++d) gc[j][d][l] += nu * g[d][l];
-          dv[l] += g[j][l];
+          tv[j][l] = val[l];
+          tr[j][l] = -lapc * lap;
         }
       }
+      // the arithmetic below is written with explicit fused multiply-adds: every instantiation of
+      // this kernel (single problem, multi-problem, fused epilogue) then rounds identically
       T pval[Q];
       {
         T g[DIM][Q], h2[DIM][Q];
@@ -628,34 +617,83 @@ op_kernel(const OpArgs<T, K + 1, K + 1, (OP == OP_STOKES ? K : K + 1)> args) {
 #pragma unroll
         for (int l = 0; l < Q; ++l)
 #pragma unroll
-          for (int i = 0; i < DIM; ++i) {
-            Rl[i][l] += g[i][l] * inv_h;
-            gc[i][i][l] -= pval[l];
+          for (int i = 0; i < DIM; ++i) tr[i][l] = fma(g[i][l], inv_h, tr[i][l]);
+      }
+      if constexpr (FQ == 1) mbar_wait0_bounded(mbar_addr, args.err);
+      // Phase 2: point by point, the frozen values of the point (read once: NQ aligned 4-vectors
+      // from the staged block, or the registers of the recomputing variant) and the 4 (DIM + 1)
+      // integrand coefficients of the test functions: value c0 and reference gradient cg
+      T c0[DIM + 1][Q], cg[DIM + 1][DIM][Q];
+#pragma unroll
+      for (int l = 0; l < Q; ++l) {
+        T F[FrozenPoint<DIM>::NQ * 4];
+        if constexpr (FQ == 1) {
+          const T* fb = fqs + FrozenPoint<DIM>::at(l, 0, tid, TM::TPC);
+#pragma unroll
+          for (int q4 = 0; q4 < FrozenPoint<DIM>::NQ; ++q4) {
+            const T* src4 = fb + q4 * TM::TPC * 4;
+            if constexpr (sizeof(T) == 4) {
+              const float4 v = *reinterpret_cast<const float4*>(src4);
+              F[4 * q4] = v.x; F[4 * q4 + 1] = v.y; F[4 * q4 + 2] = v.z; F[4 * q4 + 3] = v.w;
+            } else {
+              const double2 v0 = *reinterpret_cast<const double2*>(src4);
+              const double2 v1 = *reinterpret_cast<const double2*>(src4 + 2);
+              F[4 * q4] = v0.x; F[4 * q4 + 1] = v0.y; F[4 * q4 + 2] = v1.x; F[4 * q4 + 3] = v1.y;
+            }
           }
-      }
-      // SUPG (test ub.grad v), scaling, then integrate the velocity components
+        } else {
 #pragma unroll
-      for (int i = 0; i < DIM; ++i) {
-        T c0[Q], cg[DIM][Q];
+          for (int i = 0; i < DIM; ++i) {
+            F[i] = Ub[i][l];
 #pragma unroll
-        for (int l = 0; l < Q; ++l) {
-          const T st = cfs * TAU(l) * Rl[i][l];
-          c0[l] = vc[i][l] * jxw[l];
-#pragma unroll
-          for (int d = 0; d < DIM; ++d) cg[d][l] = (gc[i][d][l] + st * UB(d, l)) * jxw[l] * inv_h;
+            for (int j = 0; j < DIM; ++j) F[DIM + i * DIM + j] = Gb[i][j][l];
+            F[DIM + DIM * DIM + i] = Rb[i][l];
+          }
+          F[NFQ - 1] = tau[l];
         }
-        integrate<DIM, Q, N, true, true, T>(c0, cg, r[i], buf1, buf2, ti, tj, tab.S, tab.D);
-      }
-      {
-        T c0[Q], cg[DIM][Q];
+        const T* U = F;                      // frozen velocity
+        const T* G = F + DIM;                // its gradient, G[i * DIM + j] = d u_i / d x_j
+        const T* RB = F + DIM + DIM * DIM;   // frozen strong residual
+        const T ta = F[NFQ - 1];             // tau
+        T Rl[DIM];
 #pragma unroll
-        for (int l = 0; l < Q; ++l) {
-          c0[l] = div_sign_ * dv[l] * jxw[l];
+        for (int i = 0; i < DIM; ++i) {
+          T ugu = U[0] * tg[i][0][l], nt = tv[0][l] * G[i * DIM];
 #pragma unroll
-          for (int d = 0; d < DIM; ++d) cg[d][l] = cfp * TAU(l) * Rl[d][l] * jxw[l] * inv_h;
+          for (int d = 1; d < DIM; ++d) {
+            ugu = fma(U[d], tg[i][d][l], ugu);       // (ub . grad) du_i
+            nt = fma(tv[d][l], G[i * DIM + d], nt);  // (du . grad) ub_i
+          }
+          const T vci = fma(cmm, tv[i][l], fma(cfc, ugu, cfn * nt));   // Galerkin value coefficient
+          c0[i][l] = vci * jxw[l];
+          Rl[i] = vci + tr[i][l];                                      // linearised strong residual
         }
-        integrate<DIM, Q, N, true, true, T>(c0, cg, r[DIM], buf1, buf2, ti, tj, tab.S, tab.D);
+        const T sg = jxw[l] * inv_h;
+        T dv = tg[0][0][l];
+#pragma unroll
+        for (int i = 1; i < DIM; ++i) dv += tg[i][i][l];
+        const T cst = cfs * ta, csn = cfsn * ta;
+#pragma unroll
+        for (int i = 0; i < DIM; ++i) {
+          const T st = cst * Rl[i];       // SUPG: tau Rlin_i (ub . grad v_i)
+          const T sn = csn * RB[i];       // SUPG, Newton part: tau Rbar_i (du . grad v_i)
+#pragma unroll
+          for (int d = 0; d < DIM; ++d) {
+            T a = fma(nu, tg[i][d][l], d == i ? -pval[l] : T(0));
+            a = fma(sn, tv[d][l], a);
+            a = fma(st, U[d], a);
+            cg[i][d][l] = a * sg;
+          }
+        }
+        c0[DIM][l] = div_sign_ * dv * jxw[l];
+        const T sp = cfp * ta * sg;            // PSPG: tau Rlin . grad q
+#pragma unroll
+        for (int d = 0; d < DIM; ++d) cg[DIM][d][l] = sp * Rl[d];
       }
+      // Phase 3: integrate every test field
+#pragma unroll
+      for (int i = 0; i <= DIM; ++i)
+        integrate<DIM, Q, N, true, true, T>(c0[i], cg[i], r[i], buf1, buf2, ti, tj, tab.S, tab.D);
     }
 
     if (!STRUCT && constrained) {
@@ -664,6 +702,25 @@ op_kernel(const OpArgs<T, K + 1, K + 1, (OP == OP_STOKES ? K : K + 1)> args) {
       if (Tr::SPLIT_P) apply_constraints<DIM, NP, true, T>(rp, buf0, mask, ti_p, tj_p, tab.Pp, ownp);
     }
 
+    // dst: the previous colour's grid (a programmatic dependency when this is a later colour of
+    // the same product) must be complete and visible before dst is read or written
+    if (pass == pass_begin) asm volatile("griddepcontrol.wait;\n" ::: "memory");
+    if constexpr (NU == 4) {
+      if (!DIAG && FQ != 2) {
+#pragma unroll
+        for (int c = 0; c < N; ++c) {
+          const bool rd = own && valid;  // dst holds the partial sums of earlier colours
+          if constexpr (sizeof(T) == 4) {
+            const float4 w = rd ? *reinterpret_cast<const float4*>(dstp + node[c] * 4) : make_float4(0, 0, 0, 0);
+            d0[0][c] = w.x; d0[1][c] = w.y; d0[2][c] = w.z; d0[3][c] = w.w;
+          } else {
+            const double2 w0 = rd ? *reinterpret_cast<const double2*>(dstp + node[c] * 4) : make_double2(0, 0);
+            const double2 w1 = rd ? *reinterpret_cast<const double2*>(dstp + node[c] * 4 + 2) : make_double2(0, 0);
+            d0[0][c] = w0.x; d0[1][c] = w0.y; d0[2][c] = w1.x; d0[3][c] = w1.y;
+          }
+        }
+      }
+    }
     if (DIAG) {
 #pragma unroll
       for (int f = 0; f < NU; ++f)
@@ -729,12 +786,14 @@ op_kernel(const OpArgs<T, K + 1, K + 1, (OP == OP_STOKES ? K : K + 1)> args) {
           }
           if constexpr (NU == 4) {
             // dst values were loaded with the gather (no other cell of this colour touches them)
+            T o[4];
+#pragma unroll
+            for (int f = 0; f < 4; ++f) o[f] = d0[f][c] + r[f][c];
             if constexpr (sizeof(T) == 4) {
-              *reinterpret_cast<float4*>(d) = make_float4(d0[0][c] + r[0][c], d0[1][c] + r[1][c],
-                                                          d0[2][c] + r[2][c], d0[3][c] + r[3][c]);
+              *reinterpret_cast<float4*>(d) = make_float4(o[0], o[1], o[2], o[3]);
             } else {
-              *reinterpret_cast<double2*>(d) = make_double2(d0[0][c] + r[0][c], d0[1][c] + r[1][c]);
-              *reinterpret_cast<double2*>(d + 2) = make_double2(d0[2][c] + r[2][c], d0[3][c] + r[3][c]);
+              *reinterpret_cast<double2*>(d) = make_double2(o[0], o[1]);
+              *reinterpret_cast<double2*>(d + 2) = make_double2(o[2], o[3]);
             }
           } else {
 #pragma unroll
@@ -778,7 +837,8 @@ constexpr size_t op_smem_bytes(int warps = kOpWarps, bool staged_frozen = false)
   const size_t region1 = ((sizeof(T) * (size_t)warps * (TM::CPW + 1) * TM::template stride<T>() + 15) / 16) * 16;
   if (!staged_frozen) return region1;
   const size_t block = sizeof(T) * FrozenPoint<DIM>::template block<T>(K + 1);
-  return region1 + (size_t)warps * TM::CPW * TM::template stage_stride_bytes<T>(block);
+  const size_t mbar_bytes = ((size_t)warps * TM::CPW * 8 + 15) / 16 * 16;
+  return region1 + mbar_bytes + (size_t)warps * TM::CPW * TM::template stage_stride_bytes<T>(block);
 }
 
 }  // namespace mfns

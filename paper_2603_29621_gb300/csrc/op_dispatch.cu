@@ -88,6 +88,7 @@ double KernelTimer::read_ms(int64_t* launches) {
   }
   if (launches) *launches = (int64_t)(used / 2);
   used = 0;
+  op_check_wait_flag();  // the timed launches completed; none of their waits may have run out
   return total;
 }
 KernelTimer::~KernelTimer() {
@@ -95,11 +96,11 @@ KernelTimer::~KernelTimer() {
 }
 
 int64_t frozen_point_values_per_cell(int dim, int k) {
-  // one cell's block [point][value][lane], padded to 16 bytes in FP32 and FP64 alike
+  // one cell's block [point][quad][lane][4 values] (FrozenPoint in op_apply.cuh)
   const int q = k + 1;
   const int64_t lanes = dim == 3 ? q * q : q;
   const int nfq = dim + dim * dim + dim + 1;
-  return ((lanes * q * nfq + 3) / 4) * 4;
+  return lanes * q * ((nfq + 3) / 4) * 4;
 }
 
 void op_precompute_frozen(const OpLaunch& L, int prec, cudaStream_t s) {
@@ -116,6 +117,31 @@ void op_residual(const OpLaunch& L, int prec, void* dst, cudaStream_t s) {
     dispatch<double>(L, nullptr, static_cast<double*>(dst), false, s, 3);
   else
     dispatch<float>(L, nullptr, static_cast<float*>(dst), false, s, 3);
+}
+
+int* op_wait_flag() {
+  static std::mutex mu;
+  static std::map<int, int*> flags;
+  int dev = 0;
+  MFNS_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lock(mu);
+  auto it = flags.find(dev);
+  if (it != flags.end()) return it->second;
+  int* p = nullptr;
+  MFNS_CUDA(cudaMalloc(&p, sizeof(int)));
+  MFNS_CUDA(cudaMemset(p, 0, sizeof(int)));
+  flags[dev] = p;
+  return p;
+}
+
+void op_check_wait_flag() {
+  int* p = op_wait_flag();
+  int h = 0;
+  MFNS_CUDA(cudaMemcpy(&h, p, sizeof(int), cudaMemcpyDeviceToHost));
+  if (h) {
+    MFNS_CUDA(cudaMemset(p, 0, sizeof(int)));
+    throw Error(kErrTimeout, "a cell kernel's wait for its staged frozen block ran out (results invalid)");
+  }
 }
 
 int autotune_warps(OpLaunch& L, int prec, void* src, void* dst, int64_t n, cudaStream_t s) {
@@ -152,6 +178,7 @@ int autotune_warps(OpLaunch& L, int prec, void* src, void* dst, int64_t n, cudaS
   L.timer = saved;
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
+  op_check_wait_flag();
   L.warps[prec] = best;
   std::lock_guard<std::mutex> lock(mu);
   cache[key] = best;

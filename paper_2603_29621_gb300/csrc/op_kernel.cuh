@@ -105,6 +105,8 @@ struct OpArgs {
   // multi-problem launch: descriptor of the problem owning each block
   const ProbArgs<T>* probs;
   const int32_t* block_pid;
+  // device word in which a bounded wait that ran out sets bit 0 (or null)
+  int* err;
 };
 
 // ------------------------------------------------------------ small helpers

@@ -28,6 +28,26 @@ static void build_tables(const OpLaunch& L, Tables<T, Q, N, NP>& t) {
   }
 }
 
+// Launch of one colour; pdl: as a programmatic dependent launch of the previous kernel in `s`.
+template <typename Kern, typename Args>
+static void launch_op(Kern kern, dim3 grid, unsigned block, size_t smem, cudaStream_t s, const Args& a, bool pdl) {
+  if (!pdl) {
+    kern<<<grid, block, smem, s>>>(a);
+    return;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  MFNS_CUDA(cudaLaunchKernelEx(&cfg, kern, a));
+}
+
 template <int DIM, int K, int OP, typename T>
 void op_launch(const OpLaunch& L, const T* src, T* dst, bool diag, cudaStream_t s, int fq_mode, int ncols,
                int64_t col_stride, const OpEpilogue* epi) {
@@ -54,6 +74,7 @@ void op_launch(const OpLaunch& L, const T* src, T* dst, bool diag, cudaStream_t 
   a.div_sign = (T)L.div_sign;
   for (int b = 0; b < 7; ++b) a.cf[b] = (L.terms >> b) & 1 ? T(1) : T(0);
   a.diag = diag;
+  a.err = op_wait_flag();
   if (ncols < 1 || (ncols > 1 && (diag || fq_mode == 2 || fq_mode == 3)))
     throw Error(kErrArg, "several columns only for operator applications");
   a.col_stride = ncols > 1 ? col_stride : 0;
@@ -105,6 +126,7 @@ void op_launch(const OpLaunch& L, const T* src, T* dst, bool diag, cudaStream_t 
   }
   const bool structured = L.structured && !diag;
   int64_t color_offset = 0;
+  bool launched = false;
   for (int c = 0; c < L.n_colors; ++c) {
     int64_t ncell;
     if (structured) {
@@ -131,46 +153,53 @@ void op_launch(const OpLaunch& L, const T* src, T* dst, bool diag, cudaStream_t 
       gy = gx >= want ? 1u : std::min<unsigned>((unsigned)NLOC, (want + gx - 1) / gx);
     }
     const dim3 grid(gx, gy);
-    if (L.timer && L.timer->enabled) L.timer->record_pair_begin(s);
+    const bool timed = L.timer && L.timer->enabled;
+    if (timed) L.timer->record_pair_begin(s);
+    // colours after the first are programmatic dependent launches: their blocks may start while
+    // the previous colour drains and wait (griddepcontrol.wait) only before touching dst; src and
+    // the frozen data are not written by the colour launches.  Timed launches stay serialised.
+    const bool pdl = launched && !timed;
+    launched = true;
+    auto go = [&](auto kern, size_t sm) { launch_op(kern, grid, warps * 32, sm, s, a, pdl); };
     if constexpr (OP == OP_STAB_NS) {
       if (fq == 2) {
         if (L.structured)
-          op_kernel<DIM, K, OP, T, true, false, 2><<<grid, warps * 32, smem, s>>>(a);
+          go(op_kernel<DIM, K, OP, T, true, false, 2>, smem);
         else
-          op_kernel<DIM, K, OP, T, false, false, 2><<<grid, warps * 32, smem, s>>>(a);
+          go(op_kernel<DIM, K, OP, T, false, false, 2>, smem);
       } else if (fq == 3) {
         if (L.structured)
-          op_kernel<DIM, K, OP, T, true, false, 3><<<grid, warps * 32, smem, s>>>(a);
+          go(op_kernel<DIM, K, OP, T, true, false, 3>, smem);
         else
-          op_kernel<DIM, K, OP, T, false, false, 3><<<grid, warps * 32, smem, s>>>(a);
+          go(op_kernel<DIM, K, OP, T, false, false, 3>, smem);
       } else if (fq == 1) {
         if (structured && fused)
-          op_kernel<DIM, K, OP, T, true, false, 1, true><<<grid, warps * 32, smem_fq, s>>>(a);
+          go(op_kernel<DIM, K, OP, T, true, false, 1, true>, smem_fq);
         else if (structured)
-          op_kernel<DIM, K, OP, T, true, false, 1><<<grid, warps * 32, smem_fq, s>>>(a);
+          go(op_kernel<DIM, K, OP, T, true, false, 1>, smem_fq);
         else if (diag)
-          op_kernel<DIM, K, OP, T, false, true, 1><<<grid, warps * 32, smem_fq, s>>>(a);
+          go(op_kernel<DIM, K, OP, T, false, true, 1>, smem_fq);
         else
-          op_kernel<DIM, K, OP, T, false, false, 1><<<grid, warps * 32, smem_fq, s>>>(a);
+          go(op_kernel<DIM, K, OP, T, false, false, 1>, smem_fq);
       } else {
         if (structured && fused)
-          op_kernel<DIM, K, OP, T, true, false, 0, true><<<grid, warps * 32, smem, s>>>(a);
+          go(op_kernel<DIM, K, OP, T, true, false, 0, true>, smem);
         else if (structured)
-          op_kernel<DIM, K, OP, T, true, false, 0><<<grid, warps * 32, smem, s>>>(a);
+          go(op_kernel<DIM, K, OP, T, true, false, 0>, smem);
         else if (diag)
-          op_kernel<DIM, K, OP, T, false, true, 0><<<grid, warps * 32, smem, s>>>(a);
+          go(op_kernel<DIM, K, OP, T, false, true, 0>, smem);
         else
-          op_kernel<DIM, K, OP, T, false, false, 0><<<grid, warps * 32, smem, s>>>(a);
+          go(op_kernel<DIM, K, OP, T, false, false, 0>, smem);
       }
     } else {
       if (structured && fused)
-        op_kernel<DIM, K, OP, T, true, false, 0, true><<<grid, warps * 32, smem, s>>>(a);
+        go(op_kernel<DIM, K, OP, T, true, false, 0, true>, smem);
       else if (structured)
-        op_kernel<DIM, K, OP, T, true, false><<<grid, warps * 32, smem, s>>>(a);
+        go(op_kernel<DIM, K, OP, T, true, false>, smem);
       else if (diag)
-        op_kernel<DIM, K, OP, T, false, true><<<grid, warps * 32, smem, s>>>(a);
+        go(op_kernel<DIM, K, OP, T, false, true>, smem);
       else
-        op_kernel<DIM, K, OP, T, false, false><<<grid, warps * 32, smem, s>>>(a);
+        go(op_kernel<DIM, K, OP, T, false, false>, smem);
     }
     MFNS_CUDA(cudaGetLastError());
     if (L.timer && L.timer->enabled) L.timer->record_pair_end(s);
@@ -192,6 +221,7 @@ void op_launch_multi(const OpLaunch& L, int color, const MultiColour& mc, cudaSt
     a.color = color;
     a.probs = static_cast<const ProbArgs<T>*>(mc.probs);
     a.block_pid = mc.block_pid;
+    a.err = op_wait_flag();
     const int warps = L.warps[prec] > 0 ? L.warps[prec] : kOpWarps;
     bool staged = false;
     if constexpr (OP == OP_STAB_NS) staged = L.fq[prec] != nullptr;

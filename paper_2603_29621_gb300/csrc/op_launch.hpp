@@ -58,6 +58,12 @@ struct OpLaunch {
   const uint8_t* lastc = nullptr;   // per main node: index of the last colour whose cells touch it
 };
 
+// The current device's word in which the cell kernels report a bounded wait that ran out (bit 0);
+// allocated on first use (4 bytes per device, held until exit).
+int* op_wait_flag();
+// Reads and clears the current device's word (synchronous); throws Error(kErrTimeout) if set.
+void op_check_wait_flag();
+
 // Autotuner: pick the warps per block (1, 2 or 4) of the cell kernel for this operator and
 // precision by timing a few applications on scratch vectors; results are cached per
 // (dim, degree, operator, precision, structured) for the process.
