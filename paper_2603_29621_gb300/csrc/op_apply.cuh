@@ -11,7 +11,7 @@ struct Team {
   static constexpr int TPC = ipow(Q, DIM - 1);   // lanes per cell
   static constexpr int CPW = 32 / TPC;           // cells per warp
   static constexpr int BUF = ipow(Q, DIM);       // elements per team buffer
-  static constexpr int NBUF = 3;                 // buffers per team
+  static constexpr int NBUF = 4;                 // buffers per team (4 fields per exchange stage)
   // Team stride padded so that the teams of a warp start TPC banks apart: lanes of different
   // teams touching the same relative element then hit disjoint banks.
   template <typename T>
@@ -31,13 +31,16 @@ struct Team {
 };
 
 // Minimum resident blocks per SM for the register allocator (occupancy vs spills), per
-// instantiation; 1 lets the compiler use up to 255 registers.
+// instantiation; 1 lets the compiler use up to 255 registers.  The 3D Q2 stabilised kernel in
+// FP32 (the headline product) runs best at 6 x 128 threads' worth (80 registers, 8 bytes of
+// spill): measured on the 64^3 apply, 4 / 5 / 6 / 7 / 8 gave 0.222 / 0.208 / 0.199 / 0.214 /
+// 0.232 ms (the latency of the late dst loads and the shared-memory exchanges wants warps).
 template <int DIM, int K, int OP, typename T>
 struct OpMinBlocks {
   static constexpr int value = 1;
 };
 #ifndef MFNS_STABNS_Q2_F32_MINBLOCKS
-#define MFNS_STABNS_Q2_F32_MINBLOCKS 4
+#define MFNS_STABNS_Q2_F32_MINBLOCKS 6
 #endif
 template <>
 struct OpMinBlocks<3, 2, OP_STAB_NS, float> {
@@ -589,35 +592,34 @@ op_kernel(const OpArgs<T, K + 1, K + 1, (OP == OP_STOKES ? K : K + 1)> args) {
       // the part of the strong residual that needs no frozen data (grad p - nu lap u); pressure.
       const T cmm = cf_[0] * cm_, cfc = cf_[1], cfn = cf_[2], cfs = cf_[3], cfsn = cf_[4], cfp = cf_[5];
       const T lapc = cf_[6] * nu * inv_h * inv_h;
+      // All DIM + 1 fields go through each exchange stage together (one warp barrier per stage).
       T tv[DIM][Q], tg[DIM][DIM][Q], tr[DIM][Q];
-#pragma unroll
-      for (int j = 0; j < DIM; ++j) {
-        T val[Q], g[DIM][Q], h2[DIM][Q];
-        values<DIM, Q, N, T>(u[j], val, buf0, ti, tj, tab.S);
-        derivatives<DIM, Q, true, T>(val, g, h2, buf1, ti, tj, tab.D, tab.D2);
-#pragma unroll
-        for (int l = 0; l < Q; ++l) {
-          T lap = 0;
-#pragma unroll
-          for (int d = 0; d < DIM; ++d) {
-            tg[j][d][l] = g[d][l] * inv_h;
-            lap += h2[d][l];
-          }
-          tv[j][l] = val[l];
-          tr[j][l] = -lapc * lap;
-        }
-      }
-      // the arithmetic below is written with explicit fused multiply-adds: every instantiation of
-      // this kernel (single problem, multi-problem, fused epilogue) then rounds identically
       T pval[Q];
       {
-        T g[DIM][Q], h2[DIM][Q];
-        values<DIM, Q, N, T>(u[DIM], pval, buf0, ti, tj, tab.S);
-        derivatives<DIM, Q, false, T>(pval, g, h2, buf1, ti, tj, tab.D, tab.D2);
+        T val[DIM + 1][Q], g[DIM + 1][DIM][Q], h2[DIM + 1][DIM][Q];
+        values_multi<DIM, Q, DIM + 1, T>(u, val, buf0, BUF, ti, tj, tab.S);
+        derivatives_multi<DIM, Q, DIM + 1, DIM, T>(val, g, h2, buf0, BUF, ti, tj, tab.D, tab.D2);
 #pragma unroll
-        for (int l = 0; l < Q; ++l)
+        for (int j = 0; j < DIM; ++j)
 #pragma unroll
-          for (int i = 0; i < DIM; ++i) tr[i][l] = fma(g[i][l], inv_h, tr[i][l]);
+          for (int l = 0; l < Q; ++l) {
+            T lap = 0;
+#pragma unroll
+            for (int d = 0; d < DIM; ++d) {
+              tg[j][d][l] = g[j][d][l] * inv_h;
+              lap += h2[j][d][l];
+            }
+            tv[j][l] = val[j][l];
+            tr[j][l] = -lapc * lap;
+          }
+        // the arithmetic below is written with explicit fused multiply-adds: every instantiation
+        // of this kernel (single problem, multi-problem, fused epilogue) then rounds identically
+#pragma unroll
+        for (int l = 0; l < Q; ++l) {
+          pval[l] = val[DIM][l];
+#pragma unroll
+          for (int i = 0; i < DIM; ++i) tr[i][l] = fma(g[DIM][i][l], inv_h, tr[i][l]);
+        }
       }
       if constexpr (FQ == 1) mbar_wait0_bounded(mbar_addr, args.err);
       // Phase 2: point by point, the frozen values of the point (read once: NQ aligned 4-vectors
@@ -628,16 +630,18 @@ op_kernel(const OpArgs<T, K + 1, K + 1, (OP == OP_STOKES ? K : K + 1)> args) {
       for (int l = 0; l < Q; ++l) {
         T F[FrozenPoint<DIM>::NQ * 4];
         if constexpr (FQ == 1) {
+          // the spare lanes of the warp read nothing (their results are discarded): the 128-bit
+          // loads of the teams then stay free of bank conflicts
           const T* fb = fqs + FrozenPoint<DIM>::at(l, 0, tid, TM::TPC);
 #pragma unroll
           for (int q4 = 0; q4 < FrozenPoint<DIM>::NQ; ++q4) {
             const T* src4 = fb + q4 * TM::TPC * 4;
             if constexpr (sizeof(T) == 4) {
-              const float4 v = *reinterpret_cast<const float4*>(src4);
+              const float4 v = lane_active ? *reinterpret_cast<const float4*>(src4) : make_float4(0, 0, 0, 0);
               F[4 * q4] = v.x; F[4 * q4 + 1] = v.y; F[4 * q4 + 2] = v.z; F[4 * q4 + 3] = v.w;
             } else {
-              const double2 v0 = *reinterpret_cast<const double2*>(src4);
-              const double2 v1 = *reinterpret_cast<const double2*>(src4 + 2);
+              const double2 v0 = lane_active ? *reinterpret_cast<const double2*>(src4) : make_double2(0, 0);
+              const double2 v1 = lane_active ? *reinterpret_cast<const double2*>(src4 + 2) : make_double2(0, 0);
               F[4 * q4] = v0.x; F[4 * q4 + 1] = v0.y; F[4 * q4 + 2] = v1.x; F[4 * q4 + 3] = v1.y;
             }
           }
@@ -690,10 +694,27 @@ op_kernel(const OpArgs<T, K + 1, K + 1, (OP == OP_STOKES ? K : K + 1)> args) {
 #pragma unroll
         for (int d = 0; d < DIM; ++d) cg[DIM][d][l] = sp * Rl[d];
       }
-      // Phase 3: integrate every test field
+      // Phase 3: integrate the test fields, two per exchange stage
 #pragma unroll
-      for (int i = 0; i <= DIM; ++i)
-        integrate<DIM, Q, N, true, true, T>(c0[i], cg[i], r[i], buf1, buf2, ti, tj, tab.S, tab.D);
+      for (int i0 = 0; i0 <= DIM; i0 += 2) {
+        constexpr int F2 = 2;
+        T c0p[F2][Q], cgp[F2][DIM][Q], rp2[F2][Q];
+#pragma unroll
+        for (int f = 0; f < F2; ++f)
+#pragma unroll
+          for (int l = 0; l < Q; ++l) {
+            const int i = i0 + f <= DIM ? i0 + f : DIM;
+            c0p[f][l] = c0[i][l];
+#pragma unroll
+            for (int d = 0; d < DIM; ++d) cgp[f][d][l] = cg[i][d][l];
+          }
+        integrate_multi<DIM, Q, F2, T>(c0p, cgp, rp2, buf0, BUF, ti, tj, tab.S, tab.D);
+#pragma unroll
+        for (int f = 0; f < F2; ++f)
+          if (i0 + f <= DIM)
+#pragma unroll
+            for (int c = 0; c < N; ++c) r[i0 + f][c] = rp2[f][c];
+      }
     }
 
     if (!STRUCT && constrained) {

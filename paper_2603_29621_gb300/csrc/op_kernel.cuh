@@ -512,4 +512,276 @@ __device__ __forceinline__ void integrate(const T (&c0)[Q], const T (&cg)[DIM][Q
   }
 }
 
+// ------------------------------------------------------------ several fields per exchange
+// The same contractions for F fields at once: every shared-memory stage writes the F fields into
+// F team buffers (stride BUF elements from buf), synchronises the warp once and reads them back,
+// so the F fields' loads are independent and in flight together (the single-field versions
+// synchronise per field).  Arithmetic per field is that of values / derivatives / integrate.
+
+// Values at the lane's Gauss-point column of F fields (3D or 2D; N = Q: the nodal and the point
+// grid have the same size).
+template <int DIM, int Q, int F, typename T>
+__device__ __forceinline__ void values_multi(const T (&nod)[F][Q], T (&val)[F][Q], T* buf, int BUF, int ti,
+                                             int tj, const T (&S)[Q][Q]) {
+  if constexpr (DIM == 3) {
+#pragma unroll
+    for (int f = 0; f < F; ++f)
+#pragma unroll
+      for (int c = 0; c < Q; ++c) buf[f * BUF + (c * Q + tj) * Q + ti] = nod[f][c];
+    __syncwarp();
+    T t1[F][Q];
+#pragma unroll
+    for (int f = 0; f < F; ++f)
+#pragma unroll
+      for (int c = 0; c < Q; ++c) {
+        T s = 0;
+#pragma unroll
+        for (int a = 0; a < Q; ++a) s += S[ti][a] * buf[f * BUF + (c * Q + tj) * Q + a];
+        t1[f][c] = s;
+      }
+    __syncwarp();
+#pragma unroll
+    for (int f = 0; f < F; ++f)
+#pragma unroll
+      for (int c = 0; c < Q; ++c) buf[f * BUF + (c * Q + tj) * Q + ti] = t1[f][c];
+    __syncwarp();
+    T t2[F][Q];
+#pragma unroll
+    for (int f = 0; f < F; ++f)
+#pragma unroll
+      for (int c = 0; c < Q; ++c) {
+        T s = 0;
+#pragma unroll
+        for (int b = 0; b < Q; ++b) s += S[tj][b] * buf[f * BUF + (c * Q + b) * Q + ti];
+        t2[f][c] = s;
+      }
+    __syncwarp();
+#pragma unroll
+    for (int f = 0; f < F; ++f)
+#pragma unroll
+      for (int l = 0; l < Q; ++l) {
+        T s = 0;
+#pragma unroll
+        for (int c = 0; c < Q; ++c) s += S[l][c] * t2[f][c];
+        val[f][l] = s;
+      }
+  } else {
+#pragma unroll
+    for (int f = 0; f < F; ++f)
+#pragma unroll
+      for (int b = 0; b < Q; ++b) buf[f * BUF + b * Q + ti] = nod[f][b];
+    __syncwarp();
+    T t1[F][Q];
+#pragma unroll
+    for (int f = 0; f < F; ++f)
+#pragma unroll
+      for (int b = 0; b < Q; ++b) {
+        T s = 0;
+#pragma unroll
+        for (int a = 0; a < Q; ++a) s += S[ti][a] * buf[f * BUF + b * Q + a];
+        t1[f][b] = s;
+      }
+    __syncwarp();
+#pragma unroll
+    for (int f = 0; f < F; ++f)
+#pragma unroll
+      for (int l = 0; l < Q; ++l) {
+        T s = 0;
+#pragma unroll
+        for (int b = 0; b < Q; ++b) s += S[l][b] * t1[f][b];
+        val[f][l] = s;
+      }
+  }
+}
+
+// Reference first derivatives of F fields and, for the first F2 of them, the diagonal of the
+// reference Hessian, at the lane's column.
+template <int DIM, int Q, int F, int F2, typename T>
+__device__ __forceinline__ void derivatives_multi(const T (&val)[F][Q], T (&g)[F][DIM][Q], T (&h2)[F][DIM][Q],
+                                                  T* buf, int BUF, int ti, int tj, const T (&D)[Q][Q],
+                                                  const T (&D2)[Q][Q]) {
+  if constexpr (DIM == 3) {
+#pragma unroll
+    for (int f = 0; f < F; ++f)
+#pragma unroll
+      for (int l = 0; l < Q; ++l) buf[f * BUF + (l * Q + tj) * Q + ti] = val[f][l];
+    __syncwarp();
+#pragma unroll
+    for (int f = 0; f < F; ++f)
+#pragma unroll
+      for (int l = 0; l < Q; ++l) {
+        T sx = 0, sy = 0, sxx = 0, syy = 0;
+#pragma unroll
+        for (int r = 0; r < Q; ++r) {
+          const T vx = buf[f * BUF + (l * Q + tj) * Q + r];
+          const T vy = buf[f * BUF + (l * Q + r) * Q + ti];
+          sx += D[ti][r] * vx;
+          sy += D[tj][r] * vy;
+          if (f < F2) {
+            sxx += D2[ti][r] * vx;
+            syy += D2[tj][r] * vy;
+          }
+        }
+        g[f][0][l] = sx;
+        g[f][1][l] = sy;
+        h2[f][0][l] = sxx;
+        h2[f][1][l] = syy;
+        T sz = 0, szz = 0;
+#pragma unroll
+        for (int r = 0; r < Q; ++r) {
+          sz += D[l][r] * val[f][r];
+          if (f < F2) szz += D2[l][r] * val[f][r];
+        }
+        g[f][2][l] = sz;
+        h2[f][2][l] = szz;
+      }
+    __syncwarp();
+  } else {
+#pragma unroll
+    for (int f = 0; f < F; ++f)
+#pragma unroll
+      for (int l = 0; l < Q; ++l) buf[f * BUF + l * Q + ti] = val[f][l];
+    __syncwarp();
+#pragma unroll
+    for (int f = 0; f < F; ++f)
+#pragma unroll
+      for (int l = 0; l < Q; ++l) {
+        T sx = 0, sxx = 0;
+#pragma unroll
+        for (int r = 0; r < Q; ++r) {
+          const T vx = buf[f * BUF + l * Q + r];
+          sx += D[ti][r] * vx;
+          if (f < F2) sxx += D2[ti][r] * vx;
+        }
+        g[f][0][l] = sx;
+        h2[f][0][l] = sxx;
+        T sy = 0, syy = 0;
+#pragma unroll
+        for (int r = 0; r < Q; ++r) {
+          sy += D[l][r] * val[f][r];
+          if (f < F2) syy += D2[l][r] * val[f][r];
+        }
+        g[f][1][l] = sy;
+        h2[f][1][l] = syy;
+      }
+    __syncwarp();
+  }
+}
+
+// Integration of F test fields, each with a value (c0) and a reference-gradient (cg) coefficient:
+// nodal contributions r (lane (ti, tj)); buf holds 2 F team buffers.
+template <int DIM, int Q, int F, typename T>
+__device__ __forceinline__ void integrate_multi(const T (&c0)[F][Q], const T (&cg)[F][DIM][Q], T (&r)[F][Q], T* buf,
+                                                int BUF, int ti, int tj, const T (&S)[Q][Q], const T (&D)[Q][Q]) {
+  T w[F][Q];
+  if constexpr (DIM == 3) {
+#pragma unroll
+    for (int f = 0; f < F; ++f)
+#pragma unroll
+      for (int l = 0; l < Q; ++l) {
+        buf[(2 * f) * BUF + (l * Q + tj) * Q + ti] = cg[f][0][l];
+        buf[(2 * f + 1) * BUF + (l * Q + tj) * Q + ti] = cg[f][1][l];
+      }
+    __syncwarp();
+#pragma unroll
+    for (int f = 0; f < F; ++f)
+#pragma unroll
+      for (int l = 0; l < Q; ++l) {
+        T s = c0[f][l];
+#pragma unroll
+        for (int rr = 0; rr < Q; ++rr) {
+          s += D[rr][ti] * buf[(2 * f) * BUF + (l * Q + tj) * Q + rr];
+          s += D[rr][tj] * buf[(2 * f + 1) * BUF + (l * Q + rr) * Q + ti];
+          s += D[rr][l] * cg[f][2][rr];
+        }
+        w[f][l] = s;
+      }
+    T t2[F][Q];
+#pragma unroll
+    for (int f = 0; f < F; ++f)
+#pragma unroll
+      for (int c = 0; c < Q; ++c) {
+        T s = 0;
+#pragma unroll
+        for (int l = 0; l < Q; ++l) s += S[l][c] * w[f][l];
+        t2[f][c] = s;
+      }
+    __syncwarp();
+#pragma unroll
+    for (int f = 0; f < F; ++f)
+#pragma unroll
+      for (int c = 0; c < Q; ++c) buf[(2 * f) * BUF + (c * Q + tj) * Q + ti] = t2[f][c];
+    __syncwarp();
+    T t1[F][Q];
+#pragma unroll
+    for (int f = 0; f < F; ++f)
+#pragma unroll
+      for (int c = 0; c < Q; ++c) {
+        T s = 0;
+#pragma unroll
+        for (int j = 0; j < Q; ++j) s += S[j][tj] * buf[(2 * f) * BUF + (c * Q + j) * Q + ti];
+        t1[f][c] = s;
+      }
+#pragma unroll
+    for (int f = 0; f < F; ++f)
+#pragma unroll
+      for (int c = 0; c < Q; ++c) buf[(2 * f + 1) * BUF + (c * Q + tj) * Q + ti] = t1[f][c];
+    __syncwarp();
+#pragma unroll
+    for (int f = 0; f < F; ++f)
+#pragma unroll
+      for (int c = 0; c < Q; ++c) {
+        T s = 0;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) s += S[i][ti] * buf[(2 * f + 1) * BUF + (c * Q + tj) * Q + i];
+        r[f][c] = s;
+      }
+    __syncwarp();
+  } else {
+#pragma unroll
+    for (int f = 0; f < F; ++f)
+#pragma unroll
+      for (int l = 0; l < Q; ++l) buf[(2 * f) * BUF + l * Q + ti] = cg[f][0][l];
+    __syncwarp();
+#pragma unroll
+    for (int f = 0; f < F; ++f)
+#pragma unroll
+      for (int l = 0; l < Q; ++l) {
+        T s = c0[f][l];
+#pragma unroll
+        for (int rr = 0; rr < Q; ++rr) {
+          s += D[rr][ti] * buf[(2 * f) * BUF + l * Q + rr];
+          s += D[rr][l] * cg[f][1][rr];
+        }
+        w[f][l] = s;
+      }
+    T t1[F][Q];
+#pragma unroll
+    for (int f = 0; f < F; ++f)
+#pragma unroll
+      for (int b = 0; b < Q; ++b) {
+        T s = 0;
+#pragma unroll
+        for (int l = 0; l < Q; ++l) s += S[l][b] * w[f][l];
+        t1[f][b] = s;
+      }
+    __syncwarp();
+#pragma unroll
+    for (int f = 0; f < F; ++f)
+#pragma unroll
+      for (int b = 0; b < Q; ++b) buf[(2 * f + 1) * BUF + b * Q + ti] = t1[f][b];
+    __syncwarp();
+#pragma unroll
+    for (int f = 0; f < F; ++f)
+#pragma unroll
+      for (int b = 0; b < Q; ++b) {
+        T s = 0;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) s += S[i][ti] * buf[(2 * f + 1) * BUF + b * Q + i];
+        r[f][b] = s;
+      }
+    __syncwarp();
+  }
+}
+
 }  // namespace mfns

@@ -121,6 +121,11 @@ void op_launch(const OpLaunch& L, const T* src, T* dst, bool diag, cudaStream_t 
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
       MFNS_CUDA(cudaFuncSetAttribute(op_kernel<DIM, K, OP, T, true, false, 1, true>,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+      // the structured product's blocks are one warp with its staged blocks: ask for the largest
+      // shared-memory carveout so that shared memory never caps the resident blocks below the
+      // register limit
+      MFNS_CUDA(cudaFuncSetAttribute(op_kernel<DIM, K, OP, T, true, false, 1>,
+                                     cudaFuncAttributePreferredSharedMemoryCarveout, 100));
       attr_done.fetch_or(bit);
     }
   }
