@@ -35,6 +35,7 @@ struct Team {
 // FP32 (the headline product) runs best at 6 x 128 threads' worth (80 registers, 8 bytes of
 // spill): measured on the 64^3 apply, 4 / 5 / 6 / 7 / 8 gave 0.222 / 0.208 / 0.199 / 0.214 /
 // 0.232 ms (the latency of the late dst loads and the shared-memory exchanges wants warps).
+// The fused-epilogue instantiation gets one block less (its update operands need registers).
 template <int DIM, int K, int OP, typename T>
 struct OpMinBlocks {
   static constexpr int value = 1;
@@ -113,7 +114,9 @@ __device__ __forceinline__ void mbar_wait0_bounded(unsigned addr, int* err) {
 // reads its problem's fields from args.probs.
 template <int DIM, int K, int OP, typename T, bool STRUCT, bool DIAG, int FQ = 0, bool EPI = false,
           bool MULTI = false>
-__global__ void __launch_bounds__(kOpWarps * 32, OpMinBlocks<DIM, K, OP, T>::value)
+__global__ void __launch_bounds__(kOpWarps * 32, (EPI && OpMinBlocks<DIM, K, OP, T>::value > 1)
+                                                     ? OpMinBlocks<DIM, K, OP, T>::value - 1
+                                                     : OpMinBlocks<DIM, K, OP, T>::value)
 op_kernel(const OpArgs<T, K + 1, K + 1, (OP == OP_STOKES ? K : K + 1)> args) {
   constexpr int Q = K + 1, N = K + 1, NP = OP == OP_STOKES ? K : K + 1;
   using Tr = OpTraits<OP, DIM>;
@@ -323,6 +326,25 @@ op_kernel(const OpArgs<T, K + 1, K + 1, (OP == OP_STOKES ? K : K + 1)> args) {
     if (Tr::SPLIT_P) {
 #pragma unroll
       for (int c = 0; c < NP; ++c) pv0[c] = ownp ? srcp[p_offset + pnode[c]] : T(0);
+    }
+  }
+
+  // fused epilogue: which of the lane's nodes this colour completes (bit c), and an early L2
+  // prefetch of their update operands (read-only here, and touched by no other colour)
+  uint32_t epi_last = 0;
+  if constexpr (EPI) {
+    if (own && valid) {
+#pragma unroll
+      for (int c = 0; c < N; ++c)
+        if (args.lastc[node[c]] == (uint8_t)args.color) {
+          epi_last |= 1u << c;
+          const int64_t o = node[c] * NU;
+          asm volatile("prefetch.global.L2 [%0];" ::"l"(args.eb + o));
+          if (args.epi == 1) {
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(args.edinv + o));
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(args.ed + o));
+          }
+        }
     }
   }
 
@@ -763,7 +785,7 @@ op_kernel(const OpArgs<T, K + 1, K + 1, (OP == OP_STOKES ? K : K + 1)> args) {
 #pragma unroll
         for (int c = 0; c < N; ++c) {
           T* d = dstp + node[c] * NU;
-          if (EPI && args.lastc[node[c]] == (uint8_t)args.color) {
+          if (EPI && ((epi_last >> c) & 1u)) {
             // fused epilogue: this colour completes (A src) at the node
             const int64_t o = node[c] * NU;
             const bool cbnd = OP != OP_PMASS && bnd[c];  // velocity entries are identity rows
@@ -781,8 +803,13 @@ op_kernel(const OpArgs<T, K + 1, K + 1, (OP == OP_STOKES ? K : K + 1)> args) {
                 for (int f = 0; f < 4; ++f) {
                   const bool keep = cbnd && f < DIM;
                   dn[f] = keep ? ee[f] : args.ec1 * ee[f] + args.ec2 * qq[f] * (bb[f] - ax[f]);
-                  xo[f] = u0[f][c] + dn[f];
                 }
+                // x' = x + d with x read again (a cache hit: the gather read it) rather than held
+                // in registers through the cell; identity rows are rewritten by a separate pass
+                const float4 x4 = __ldg(reinterpret_cast<const float4*>(srcp + o));
+                const float xx[4] = {x4.x, x4.y, x4.z, x4.w};
+#pragma unroll
+                for (int f = 0; f < 4; ++f) xo[f] = xx[f] + dn[f];
                 *reinterpret_cast<float4*>(args.ed + o) = make_float4(dn[0], dn[1], dn[2], dn[3]);
               } else {
 #pragma unroll
@@ -797,7 +824,7 @@ op_kernel(const OpArgs<T, K + 1, K + 1, (OP == OP_STOKES ? K : K + 1)> args) {
                 if (args.epi == 1) {
                   const T dn = args.ec1 * args.ed[o + f] + args.ec2 * args.edinv[o + f] * (args.eb[o + f] - ax);
                   args.ed[o + f] = dn;
-                  args.exout[o + f] = u0[f][c] + dn;
+                  args.exout[o + f] = srcp[o + f] + dn;
                 } else {
                   args.exout[o + f] = args.eb[o + f] - ax;
                 }

@@ -12,9 +12,11 @@ The oracle cannot assemble these operators, so it computes sampled rows one by o
 * Stokes Q2/Q1 on the 32^3 mesh refined twice inside the ball |x - (1/2,1/2,1/2)| < 1/4 with
   2:1 closure (indexed cells, hanging-node constraints): FP64 and FP32 vmult; random rows
   plus master rows of hanging nodes.
-* 48^3 stabilised NS solve (FP32 multigrid inside FP64 FGMRES, tol 1e-11): the right-hand side
-  b = A x* of the manufactured x* is checked against the oracle on sampled rows, and the
-  solution against x*.
+* 48^3 stabilised NS solves at nu = 1e-1, 1e-2, 1e-3 (FP32 multigrid inside FP64 FGMRES,
+  relative residual 1e-13, as the benchmark runs them): the right-hand side b = A x* of the
+  manufactured x* is checked against the oracle on sampled rows, and the solution against x*
+  to 1e-8 relative (the FP32-multigrid target); the ball-refined Stokes Q2/Q1 solve (FP32
+  multigrid, 1e-14) to 1e-8 as well.
 
 Bounds: relative l2 error over the sample <= 1e-12 (FP64) and <= 2e-5 (FP32), as in the
 small-size tests."""
@@ -125,10 +127,11 @@ def test_stokes_ball_32_vmult_sampled_rows(stokes_ball_32, prec):
     assert rel <= TOL[prec], rel
 
 
-def test_stab_ns_48_solve_fp32_multigrid(ctx):
+@pytest.mark.parametrize("nu", [1e-1, 1e-2, 1e-3])
+def test_stab_ns_48_solve_fp32_multigrid(ctx, nu):
     from paper_2603_29621_gb300 import _lib as L, api
     m = api.Mesh(ctx, 3, 48)
-    prob = api.Problem(ctx, m, kind=L.STAB_NS, degree=2, nu=1e-2, dt=1e-2, mg_precision=L.FP32, tol=1e-11,
+    prob = api.Problem(ctx, m, kind=L.STAB_NS, degree=2, nu=nu, dt=1e-2, mg_precision=L.FP32, tol=1e-13,
                        maxit=300)
     xyz, fld = prob.support_points()
     xs_np = inputs.smooth_solution(xyz, fld, 3)
@@ -139,7 +142,7 @@ def test_stab_ns_48_solve_fp32_multigrid(ctx):
     info = prob.solve(b, x)
     assert info.converged and info.iterations <= 20
     # b = A x* on sampled rows against the oracle
-    op = assemble.Problem(mesh.uniform(3, 48), "stab_ns", 2, nu=1e-2, dt=1e-2)
+    op = assemble.Problem(mesh.uniform(3, 48), "stab_ns", 2, nu=nu, dt=1e-2)
     xo, fo = op.dofs.support_points()
     perm = inputs.match_dofs(xyz, fld, xo, fo)
     rows = np.unique(np.random.default_rng(9).choice(len(perm), 120, replace=False))
@@ -152,4 +155,27 @@ def test_stab_ns_48_solve_fp32_multigrid(ctx):
     ps = slice(3, None, 4)
     d[ps] -= d[ps].mean()
     xr[ps] -= xr[ps].mean()
-    assert np.linalg.norm(d) <= 1e-6 * np.linalg.norm(xr)
+    assert np.linalg.norm(d) <= 1e-8 * np.linalg.norm(xr), np.linalg.norm(d) / np.linalg.norm(xr)
+
+
+def test_stokes_ball_32_solve_fp32_multigrid(ctx):
+    """Config 3's Stokes system with the FP32 multigrid: the solution of b = A x* to 1e-8 of x*
+    (A itself is pinned against the oracle on sampled rows above)."""
+    from paper_2603_29621_gb300 import _lib as L, api
+    m = api.Mesh(ctx, 3, 32)
+    m.refine_ball(*BALL)
+    prob = api.Problem(ctx, m, kind=L.STOKES, degree=2, nu=1.0, mg_precision=L.FP32, tol=1e-14, maxit=300)
+    xyz, fld = prob.support_points()
+    xs_np = inputs.smooth_solution(xyz, fld, 3, 1.0)
+    xs = torch.tensor(xs_np, device="cuda")
+    b = torch.empty_like(xs)
+    prob.vmult(xs, b)
+    x = torch.zeros_like(xs)
+    info = prob.solve(b, x, raise_on_nonconvergence=False)
+    assert info.iterations <= 60, info.iterations
+    d = (x - xs).cpu().numpy()
+    xr = xs_np.copy()
+    ps = slice(prob.info.n_velocity_dofs, None)
+    d[ps] -= d[ps].mean()
+    xr[ps] -= xr[ps].mean()
+    assert np.linalg.norm(d) <= 1e-8 * np.linalg.norm(xr), np.linalg.norm(d) / np.linalg.norm(xr)
