@@ -5,6 +5,10 @@
 namespace mfns {
 
 constexpr int kOpWarps = 4;  // largest number of warps per block (the block size is tuned at run time)
+// The stabilised kernel's x-direction exchanges go through warp shuffles (the x-row of a team is
+// adjacent lanes), the y-direction ones through shared memory: measured on the 64^3 FP32 apply,
+// 0.199 ms against 0.204 ms with both through shared memory.
+constexpr bool kXShfl = true;
 
 template <int DIM, int Q>
 struct Team {
@@ -619,8 +623,8 @@ op_kernel(const OpArgs<T, K + 1, K + 1, (OP == OP_STOKES ? K : K + 1)> args) {
       T pval[Q];
       {
         T val[DIM + 1][Q], g[DIM + 1][DIM][Q], h2[DIM + 1][DIM][Q];
-        values_multi<DIM, Q, DIM + 1, T>(u, val, buf0, BUF, ti, tj, tab.S);
-        derivatives_multi<DIM, Q, DIM + 1, DIM, T>(val, g, h2, buf0, BUF, ti, tj, tab.D, tab.D2);
+        values_multi<DIM, Q, DIM + 1, T, kXShfl>(u, val, buf0, BUF, ti, tj, tab.S);
+        derivatives_multi<DIM, Q, DIM + 1, DIM, T, kXShfl>(val, g, h2, buf0, BUF, ti, tj, tab.D, tab.D2);
 #pragma unroll
         for (int j = 0; j < DIM; ++j)
 #pragma unroll
@@ -730,7 +734,7 @@ op_kernel(const OpArgs<T, K + 1, K + 1, (OP == OP_STOKES ? K : K + 1)> args) {
 #pragma unroll
             for (int d = 0; d < DIM; ++d) cgp[f][d][l] = cg[i][d][l];
           }
-        integrate_multi<DIM, Q, F2, T>(c0p, cgp, rp2, buf0, BUF, ti, tj, tab.S, tab.D);
+        integrate_multi<DIM, Q, F2, T, kXShfl>(c0p, cgp, rp2, buf0, BUF, ti, tj, tab.S, tab.D);
 #pragma unroll
         for (int f = 0; f < F2; ++f)
           if (i0 + f <= DIM)

@@ -520,26 +520,41 @@ __device__ __forceinline__ void integrate(const T (&c0)[Q], const T (&cg)[DIM][Q
 
 // Values at the lane's Gauss-point column of F fields (3D or 2D; N = Q: the nodal and the point
 // grid have the same size).
-template <int DIM, int Q, int F, typename T>
+// XS (3D): the x-direction exchanges go through warp shuffles instead of shared memory (the Q
+// lanes of an x-row of a team are adjacent lanes: lane - ti + a holds column a of the row).
+template <int DIM, int Q, int F, typename T, bool XS = false>
 __device__ __forceinline__ void values_multi(const T (&nod)[F][Q], T (&val)[F][Q], T* buf, int BUF, int ti,
                                              int tj, const T (&S)[Q][Q]) {
   if constexpr (DIM == 3) {
-#pragma unroll
-    for (int f = 0; f < F; ++f)
-#pragma unroll
-      for (int c = 0; c < Q; ++c) buf[f * BUF + (c * Q + tj) * Q + ti] = nod[f][c];
-    __syncwarp();
     T t1[F][Q];
+    if constexpr (XS) {
+      const int row = lane_id() - ti;
 #pragma unroll
-    for (int f = 0; f < F; ++f)
+      for (int f = 0; f < F; ++f)
 #pragma unroll
-      for (int c = 0; c < Q; ++c) {
-        T s = 0;
+        for (int c = 0; c < Q; ++c) {
+          T s = 0;
 #pragma unroll
-        for (int a = 0; a < Q; ++a) s += S[ti][a] * buf[f * BUF + (c * Q + tj) * Q + a];
-        t1[f][c] = s;
-      }
-    __syncwarp();
+          for (int a = 0; a < Q; ++a) s += S[ti][a] * __shfl_sync(0xffffffffu, nod[f][c], row + a);
+          t1[f][c] = s;
+        }
+    } else {
+#pragma unroll
+      for (int f = 0; f < F; ++f)
+#pragma unroll
+        for (int c = 0; c < Q; ++c) buf[f * BUF + (c * Q + tj) * Q + ti] = nod[f][c];
+      __syncwarp();
+#pragma unroll
+      for (int f = 0; f < F; ++f)
+#pragma unroll
+        for (int c = 0; c < Q; ++c) {
+          T s = 0;
+#pragma unroll
+          for (int a = 0; a < Q; ++a) s += S[ti][a] * buf[f * BUF + (c * Q + tj) * Q + a];
+          t1[f][c] = s;
+        }
+      __syncwarp();
+    }
 #pragma unroll
     for (int f = 0; f < F; ++f)
 #pragma unroll
@@ -596,11 +611,12 @@ __device__ __forceinline__ void values_multi(const T (&nod)[F][Q], T (&val)[F][Q
 
 // Reference first derivatives of F fields and, for the first F2 of them, the diagonal of the
 // reference Hessian, at the lane's column.
-template <int DIM, int Q, int F, int F2, typename T>
+template <int DIM, int Q, int F, int F2, typename T, bool XS = false>
 __device__ __forceinline__ void derivatives_multi(const T (&val)[F][Q], T (&g)[F][DIM][Q], T (&h2)[F][DIM][Q],
                                                   T* buf, int BUF, int ti, int tj, const T (&D)[Q][Q],
                                                   const T (&D2)[Q][Q]) {
   if constexpr (DIM == 3) {
+    const int row = lane_id() - ti;
 #pragma unroll
     for (int f = 0; f < F; ++f)
 #pragma unroll
@@ -613,7 +629,7 @@ __device__ __forceinline__ void derivatives_multi(const T (&val)[F][Q], T (&g)[F
         T sx = 0, sy = 0, sxx = 0, syy = 0;
 #pragma unroll
         for (int r = 0; r < Q; ++r) {
-          const T vx = buf[f * BUF + (l * Q + tj) * Q + r];
+          const T vx = XS ? __shfl_sync(0xffffffffu, val[f][l], row + r) : buf[f * BUF + (l * Q + tj) * Q + r];
           const T vy = buf[f * BUF + (l * Q + r) * Q + ti];
           sx += D[ti][r] * vx;
           sy += D[tj][r] * vy;
@@ -670,16 +686,17 @@ __device__ __forceinline__ void derivatives_multi(const T (&val)[F][Q], T (&g)[F
 
 // Integration of F test fields, each with a value (c0) and a reference-gradient (cg) coefficient:
 // nodal contributions r (lane (ti, tj)); buf holds 2 F team buffers.
-template <int DIM, int Q, int F, typename T>
+template <int DIM, int Q, int F, typename T, bool XS = false>
 __device__ __forceinline__ void integrate_multi(const T (&c0)[F][Q], const T (&cg)[F][DIM][Q], T (&r)[F][Q], T* buf,
                                                 int BUF, int ti, int tj, const T (&S)[Q][Q], const T (&D)[Q][Q]) {
   T w[F][Q];
   if constexpr (DIM == 3) {
+    const int row = lane_id() - ti;
 #pragma unroll
     for (int f = 0; f < F; ++f)
 #pragma unroll
       for (int l = 0; l < Q; ++l) {
-        buf[(2 * f) * BUF + (l * Q + tj) * Q + ti] = cg[f][0][l];
+        if (!XS) buf[(2 * f) * BUF + (l * Q + tj) * Q + ti] = cg[f][0][l];
         buf[(2 * f + 1) * BUF + (l * Q + tj) * Q + ti] = cg[f][1][l];
       }
     __syncwarp();
@@ -690,7 +707,8 @@ __device__ __forceinline__ void integrate_multi(const T (&c0)[F][Q], const T (&c
         T s = c0[f][l];
 #pragma unroll
         for (int rr = 0; rr < Q; ++rr) {
-          s += D[rr][ti] * buf[(2 * f) * BUF + (l * Q + tj) * Q + rr];
+          s += D[rr][ti] * (XS ? __shfl_sync(0xffffffffu, cg[f][0][l], row + rr)
+                               : buf[(2 * f) * BUF + (l * Q + tj) * Q + rr]);
           s += D[rr][tj] * buf[(2 * f + 1) * BUF + (l * Q + rr) * Q + ti];
           s += D[rr][l] * cg[f][2][rr];
         }
@@ -706,7 +724,7 @@ __device__ __forceinline__ void integrate_multi(const T (&c0)[F][Q], const T (&c
         for (int l = 0; l < Q; ++l) s += S[l][c] * w[f][l];
         t2[f][c] = s;
       }
-    __syncwarp();
+    if (!XS) __syncwarp();  // with XS nothing read buffer 2f in the gradient stage
 #pragma unroll
     for (int f = 0; f < F; ++f)
 #pragma unroll
@@ -722,20 +740,32 @@ __device__ __forceinline__ void integrate_multi(const T (&c0)[F][Q], const T (&c
         for (int j = 0; j < Q; ++j) s += S[j][tj] * buf[(2 * f) * BUF + (c * Q + j) * Q + ti];
         t1[f][c] = s;
       }
+    if constexpr (XS) {
 #pragma unroll
-    for (int f = 0; f < F; ++f)
+      for (int f = 0; f < F; ++f)
 #pragma unroll
-      for (int c = 0; c < Q; ++c) buf[(2 * f + 1) * BUF + (c * Q + tj) * Q + ti] = t1[f][c];
-    __syncwarp();
+        for (int c = 0; c < Q; ++c) {
+          T s = 0;
 #pragma unroll
-    for (int f = 0; f < F; ++f)
+          for (int i = 0; i < Q; ++i) s += S[i][ti] * __shfl_sync(0xffffffffu, t1[f][c], row + i);
+          r[f][c] = s;
+        }
+    } else {
 #pragma unroll
-      for (int c = 0; c < Q; ++c) {
-        T s = 0;
+      for (int f = 0; f < F; ++f)
 #pragma unroll
-        for (int i = 0; i < Q; ++i) s += S[i][ti] * buf[(2 * f + 1) * BUF + (c * Q + tj) * Q + i];
-        r[f][c] = s;
-      }
+        for (int c = 0; c < Q; ++c) buf[(2 * f + 1) * BUF + (c * Q + tj) * Q + ti] = t1[f][c];
+      __syncwarp();
+#pragma unroll
+      for (int f = 0; f < F; ++f)
+#pragma unroll
+        for (int c = 0; c < Q; ++c) {
+          T s = 0;
+#pragma unroll
+          for (int i = 0; i < Q; ++i) s += S[i][ti] * buf[(2 * f + 1) * BUF + (c * Q + tj) * Q + i];
+          r[f][c] = s;
+        }
+    }
     __syncwarp();
   } else {
 #pragma unroll
