@@ -876,7 +876,8 @@ def run_ours(args, world, rank, local):
         xs = torch.zeros_like(b32)
 
         def cheb():
-            ms = timed(lambda: prob.smooth(0, b32, xs, x_is_zero=False), max(3, args.steps // 2), 3)
+            ms = timed(lambda: prob.smooth(0, b32, xs, x_is_zero=False), max(3, args.steps // 2), 3,
+                       nvtx="timed_cheb")
             return {"ms_per_sweep": ms, "dofs_per_s": world * ndof / (ms * 1e-3)}
 
         def vcyc():
@@ -893,7 +894,7 @@ def run_ours(args, world, rank, local):
                 for lvl in range(prob.info.n_levels - 1):
                     pf.set_lambda_max(lvl, prob.info.lambda_max[lvl])
                 return {"ms_per_sweep": timed(lambda: pf.smooth(0, b32, xs, x_is_zero=False),
-                                              max(3, args.steps // 2), 3),
+                                              max(3, args.steps // 2), 3, nvtx="timed_cheb_fused"),
                         "vcycle_ms": timed(lambda: pf.vcycle(b32, xs), steps_s, 3)}
             finally:
                 pf.close()
