@@ -1,4 +1,5 @@
 // Runtime dispatch of the operator kernels and the host-side 1D tables.
+#include <algorithm>
 #include <map>
 #include <mutex>
 #include <string>
@@ -206,6 +207,40 @@ void op_apply_multi(const OpLaunch& L, int prec, int color, const MultiColour& m
   MFNS_CASE(3, 1, OP_PMASS) MFNS_CASE(3, 2, OP_PMASS) MFNS_CASE(3, 3, OP_PMASS)
 #undef MFNS_CASE
   throw Error(kErrUnsupported, "multi-problem launch: unsupported (dim, degree, operator)");
+}
+
+// dst = 0, then lets the colour launches that follow start early.  16-byte stores when dst is
+// 16-byte aligned; element stores otherwise (the library's own callers pass sub-vectors, e.g. the
+// stages of a space-time vector, that are only element-aligned).
+template <typename T>
+__global__ void k_clear_then_release(T* y, int64_t n) {
+  asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if ((reinterpret_cast<uintptr_t>(y) & 15u) == 0) {
+    constexpr int V = 16 / sizeof(T);
+    const int64_t nv = n / V;
+    for (int64_t i = i0; i < nv; i += stride) reinterpret_cast<float4*>(y)[i] = make_float4(0, 0, 0, 0);
+    for (int64_t i = nv * V + i0; i < n; i += stride) y[i] = T(0);
+  } else {
+    for (int64_t i = i0; i < n; i += stride) y[i] = T(0);
+  }
+}
+
+void op_apply_cleared(const OpLaunch& L, int prec, const void* src, void* dst, int64_t n, cudaStream_t s) {
+  const int64_t nbytes = n * (prec == 0 ? 8 : 4);
+  const unsigned grid = (unsigned)std::min<int64_t>((nbytes / 16 + 255) / 256 + 1, 152 * 8);
+  if (prec == 0)
+    k_clear_then_release<double><<<grid, 256, 0, s>>>(static_cast<double*>(dst), n);
+  else
+    k_clear_then_release<float><<<grid, 256, 0, s>>>(static_cast<float*>(dst), n);
+  MFNS_CUDA(cudaGetLastError());
+  OpEpilogue e;
+  e.after_clear = true;
+  if (prec == 0)
+    dispatch<double>(L, static_cast<const double*>(src), static_cast<double*>(dst), false, s, -1, 1, 0, &e);
+  else
+    dispatch<float>(L, static_cast<const float*>(src), static_cast<float*>(dst), false, s, -1, 1, 0, &e);
 }
 
 void op_apply_epi(const OpLaunch& L, int prec, const void* src, void* dst, const OpEpilogue& epi, cudaStream_t s) {

@@ -79,6 +79,8 @@ void op_launch(const OpLaunch& L, const T* src, T* dst, bool diag, cudaStream_t 
     throw Error(kErrArg, "several columns only for operator applications");
   a.col_stride = ncols > 1 ? col_stride : 0;
   const bool fused = epi && epi->mode;
+  if (epi && epi->after_clear && (fused || diag || ncols != 1 || fq_mode == 2 || fq_mode == 3))
+    throw Error(kErrArg, "products after the clearing kernel: single operator applications");
   if (fused) {
     if (diag || ncols > 1 || fq_mode == 2 || fq_mode == 3 || OpTraits<OP, DIM>::SPLIT_P || !L.lastc ||
         !L.structured)
@@ -131,7 +133,7 @@ void op_launch(const OpLaunch& L, const T* src, T* dst, bool diag, cudaStream_t 
   }
   const bool structured = L.structured && !diag;
   int64_t color_offset = 0;
-  bool launched = false;
+  bool launched = epi && epi->after_clear;  // the clearing kernel before colour 0 lets it start early
   for (int c = 0; c < L.n_colors; ++c) {
     int64_t ncell;
     if (structured) {

@@ -23,6 +23,9 @@ struct KernelTimer {
 // mode 2 = residual; pointers in the launch precision.
 struct OpEpilogue {
   int mode = 0;
+  // the product is preceded in the stream by the library's own clearing kernel of dst (which
+  // lets dependents start early): the first colour is a programmatic dependent launch as well
+  bool after_clear = false;
   const void* b = nullptr;
   const void* dinv = nullptr;
   void* d = nullptr;
@@ -103,6 +106,9 @@ void op_apply_multi(const OpLaunch& L, int prec, int color, const MultiColour& m
 
 // Runtime dispatch over (dim, k, op, precision); prec 0 = fp64, 1 = fp32.
 void op_apply(const OpLaunch& L, int prec, const void* src, void* dst, bool diag, cudaStream_t s);
+// dst = 0, then dst += A src on the free rows: a clearing kernel followed by the colour launches,
+// all of them programmatic dependent launches after the clear (constrained rows untouched)
+void op_apply_cleared(const OpLaunch& L, int prec, const void* src, void* dst, int64_t n, cudaStream_t s);
 // dst (zeroed by the caller) receives partial sums; the epilogue writes the fused result
 void op_apply_epi(const OpLaunch& L, int prec, const void* src, void* dst, const OpEpilogue& epi, cudaStream_t s);
 // ncols applications at once (column j: src + j col_stride -> dst + j col_stride), dst zeroed by the caller

@@ -251,8 +251,8 @@ void build_oplevel(OpLevel& lv, const Forest& f, int op, int k, const Physics& p
 
 void oplevel_vmult(const OpLevel& lv, int prec, const void* src, void* dst, cudaStream_t s) {
   if (lv.hp) return hp_vmult(lv, prec, src, dst, s);
-  MFNS_CUDA(cudaMemsetAsync(dst, 0, lv.n_dofs * esize(prec), s));
-  op_apply(lv.L, prec, src, dst, false, s);
+  // clearing kernel, then the colour launches (each may start before its predecessor drains)
+  op_apply_cleared(lv.L, prec, src, dst, lv.n_dofs, s);
   const int64_t nc = (int64_t)lv.constrained_host.size();
   if (prec == 0)
     vcopy_idx<double>((double*)dst, (const double*)src, lv.constrained.as<int32_t>(), nc, s);
