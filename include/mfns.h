@@ -249,12 +249,17 @@ int mfns_set_lambda_max(mfns_problem* p, int level, double lambda_max);
 int mfns_problem_destroy(mfns_problem* p);
 
 /* ---- operators ----------------------------------------------------------------------------- */
-/* dst = A src (matrix-free, Section 1 / Eq. 4 per cell); constrained rows dst_i = src_i. */
+/* dst = A src (matrix-free, Section 1 / Eq. 4 per cell); constrained rows dst_i = src_i.
+ * n: entries of src and of dst (n_dofs for MFNS_OP_SYSTEM, n_dofs - n_velocity_dofs for
+ * MFNS_OP_PMASS, level_dofs[which] for a level).  On a uniform mesh the colour launches after
+ * the first start while their predecessor drains (programmatic dependent launches). */
 int mfns_vmult(mfns_problem* p, int which, int precision, const void* src, void* dst, int64_t n,
                void* stream);
-/* diag = diag(A) (exact, per-cell unit-vector evaluation; 1 on constrained rows). */
+/* diag = diag(A) (exact, per-cell unit-vector evaluation; 1 on constrained rows); n as in
+ * mfns_vmult. */
 int mfns_diagonal(mfns_problem* p, int which, int precision, void* diag, int64_t n, void* stream);
-/* Hanging entries of x from their masters (x_h = sum_j w_hj x_j), Dirichlet entries kept. */
+/* Hanging entries of x from their masters (x_h = sum_j w_hj x_j), Dirichlet entries kept; n as in
+ * mfns_vmult. */
 int mfns_apply_constraints(mfns_problem* p, int which, int precision, void* x, int64_t n, void* stream);
 
 /* Per-kernel timing of the operator-kernel launches of `which` with CUDA events recorded on
@@ -265,7 +270,8 @@ int mfns_kernel_timing(mfns_problem* p, int which, int mode, double* total_ms, i
 
 /* ---- multigrid ----------------------------------------------------------------------------- */
 /* One smoothing step on level `level`: Chebyshev of the problem's degree (or the Jacobi
- * relaxation) around point Jacobi, starting from x (x_is_zero = 1 skips the first product). */
+ * relaxation) around point Jacobi, starting from x (x_is_zero = 1 skips the first product);
+ * b and x have n = level_dofs[level] entries. */
 int mfns_smooth(mfns_problem* p, int level, int precision, const void* b, void* x, int64_t n, int x_is_zero,
                 void* stream);
 /* Same smoothing step as mfns_smooth, for callers that must not allocate device memory
@@ -283,7 +289,8 @@ int mfns_smooth(mfns_problem* p, int level, int precision, const void* b, void* 
 int mfns_smooth_noalloc(mfns_problem* p, int level, int precision, const void* b, void* x, int64_t n,
                         int x_is_zero, void* stream);
 /* Transfers between level `level` (fine) and level+1 (coarse), Eq. 4:
- * fine += P coarse;  coarse = P^T fine. */
+ * fine += P coarse;  coarse = P^T fine.  n_fine = level_dofs[level], n_coarse =
+ * level_dofs[level + 1]. */
 int mfns_prolongate_add(mfns_problem* p, int level, int precision, const void* coarse, int64_t n_coarse,
                         void* fine, int64_t n_fine, void* stream);
 int mfns_restrict(mfns_problem* p, int level, int precision, const void* fine, int64_t n_fine, void* coarse,
@@ -297,7 +304,8 @@ int mfns_vcycle(mfns_problem* p, int precision, const void* b, void* x, int64_t 
  * or the block-triangular preconditioner of Eq. 5 (STOKES), with the multigrid in
  * desc.mg_precision.  b and x are FP64 device vectors; x is overwritten (zero start).
  * The pressure l2 mean of b and of every preconditioned vector is removed when the
- * pressure is only fixed up to a constant.  Returns MFNS_ERR_NOT_CONVERGED when maxit is hit. */
+ * pressure is only fixed up to a constant.  Returns MFNS_ERR_NOT_CONVERGED when maxit is hit.
+ * n = n_dofs (both vectors). */
 int mfns_solve(mfns_problem* p, const void* b, void* x, int64_t n, mfns_solve_info* info, void* stream);
 
 /* ---- nonlinear and time-dependent stabilised Navier--Stokes (Section 5) ---------------------- */
@@ -314,12 +322,14 @@ int mfns_solve(mfns_problem* p, const void* b, void* x, int64_t n, mfns_solve_in
  * the smoother's correction) and the coarse inverse are recomputed.  The call synchronises
  * `stream`.  On refined meshes the hanging-node entries of the state and of g are set from their
  * masters first; a coarse level receives the fine function evaluated at its nodes cell by cell
- * (through the children of each coarse cell).  Returns MFNS_ERR_UNSUPPORTED for other kinds. */
+ * (through the children of each coarse cell).  Returns MFNS_ERR_UNSUPPORTED for other kinds.
+ * n = n_dofs (state and explicit_field). */
 int mfns_set_state(mfns_problem* p, double dt, double alpha, const void* state, const void* explicit_field,
                    int64_t n, void* stream);
 /* dst = F(state), the nonlinear residual of the SUPG/PSPG BDF discretisation at the state of the
  * last mfns_set_state, on the free rows; constrained rows are set to 0.  With tau frozen at the
- * state, mfns_vmult applies its Jacobian.  dst: device vector in `precision`, system layout. */
+ * state, mfns_vmult applies its Jacobian.  dst: device vector in `precision`, system layout, of
+ * n = n_dofs entries. */
 int mfns_residual(mfns_problem* p, int precision, void* dst, int64_t n, void* stream);
 /* One variable-step BDF step for u^{n+1} (Section 5): Newton's method on F(u) = 0 with
  * g = (beta_n u^n + beta_{n-1} u^{n-1}) / dt - forcing, each update solving J(u_k) d = -F(u_k) by
@@ -330,18 +340,19 @@ int mfns_residual(mfns_problem* p, int precision, void* dst, int64_t n, void* st
  * values at t_{n+1} on entry (the increments vanish on constrained entries) and the result on
  * return.  The pressure is fixed up to a constant when the velocity is Dirichlet everywhere.
  * Synchronises `stream`; returns MFNS_ERR_NOT_CONVERGED (result written) after max_newton
- * updates.  Buffers for g, F and the increment are allocated on the first call. */
+ * updates.  Buffers for g, F and the increment are allocated on the first call.  n = n_dofs (every
+ * vector argument). */
 int mfns_bdf_step(mfns_problem* p, const mfns_newton_desc* desc, const void* u_n, const void* u_nm1,
                   const void* forcing, void* u, int64_t n, mfns_newton_info* info, void* stream);
 /* *umax (host) = max over velocity nodes of |u| for an FP64 device vector u in the system layout
- * (time-step control by a CFL number: dt = CFL h / umax).  Synchronises `stream`. */
+ * (time-step control by a CFL number: dt = CFL h / umax), n = n_dofs.  Synchronises `stream`. */
 int mfns_max_velocity(mfns_problem* p, const void* u, int64_t n, double* umax, void* stream);
 
 /* ---- batched solves (continuous batching of many problems) ---------------------------------- */
 /* Start a solve as in mfns_solve (same FGMRES, same preconditioner), without iterating: the
  * right-hand side is projected, x set to zero and the initial residual norm read back (one
  * synchronisation).  All later device work of this solve runs on `stream`; give every problem
- * of a batch its own stream so their work overlaps on the device. */
+ * of a batch its own stream so their work overlaps on the device.  n = n_dofs. */
 int mfns_solve_begin(mfns_problem* p, const void* b, void* x, int64_t n, void* stream);
 /* One round: every listed problem whose solve is still running performs one FGMRES iteration
  * (Section 3).  The device work of all of them is enqueued first, each on its own stream, then
