@@ -86,9 +86,18 @@ __global__ void k_patch_solve(const double* __restrict__ r, double* __restrict__
   const double* Kp = kinv + k_ptr[p];
   double* out = zloc + (int64_t)Q * b0;
   for (int row = threadIdx.x; row < mq; row += blockDim.x) {
-    double v = 0.0;
-    for (int j = 0; j < mq; ++j) v += Kp[(int64_t)j * mq + row] * rl[j];
-    out[row] = v;
+    // four independent partial sums: the loads and FMAs of a row overlap instead of forming one
+    // dependent chain of mq steps
+    double v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0;
+    int j = 0;
+    for (; j + 3 < mq; j += 4) {
+      v0 += Kp[(int64_t)j * mq + row] * rl[j];
+      v1 += Kp[(int64_t)(j + 1) * mq + row] * rl[j + 1];
+      v2 += Kp[(int64_t)(j + 2) * mq + row] * rl[j + 2];
+      v3 += Kp[(int64_t)(j + 3) * mq + row] * rl[j + 3];
+    }
+    for (; j < mq; ++j) v0 += Kp[(int64_t)j * mq + row] * rl[j];
+    out[row] = (v0 + v1) + (v2 + v3);
   }
 }
 
@@ -156,9 +165,20 @@ struct StmgLevel {
 
 struct Stmg {
   std::vector<std::unique_ptr<StmgLevel>> lv;
-  // FGMRES on the finest level (allocated on first use): basis V (m + 1 vectors), Z (m), work
+  // FGMRES on the finest level (allocated on first use): basis V (m + 1 vectors), Z (m), work,
+  // the device table of the basis vectors and the Gram--Schmidt coefficients (two passes and
+  // the norm) with their pinned host copy
   int restart = 30;
-  DevBuf V, Z, w, bp, pres0;
+  DevBuf V, Z, w, bp, pres0, ptrV, hvec;
+  double* hh_host = nullptr;
+  // the V-cycle captured once into a CUDA graph (replayed by every preconditioner application)
+  cudaGraphExec_t vc_graph = nullptr;
+  cudaStream_t cap_stream = nullptr;
+  ~Stmg() {
+    if (vc_graph) cudaGraphExecDestroy(vc_graph);
+    if (cap_stream) cudaStreamDestroy(cap_stream);
+    if (hh_host) cudaFreeHost(hh_host);
+  }
   int64_t n_pres0 = 0;
   int nu_s = 4;
   double omega = 0.7, tau = 0.1;
@@ -535,6 +555,22 @@ static void project_constants(Stmg& mg, double* v, cudaStream_t s) {
   }
 }
 
+// L.vx = V-cycle(L.vb) on the finest level, replayed from a CUDA graph captured on first use (the
+// cycle has no host synchronisation and works on the levels' own vectors)
+static void stmg_vcycle(Stmg& mg, cudaStream_t s) {
+  if (!mg.vc_graph) {
+    if (!mg.cap_stream) MFNS_CUDA(cudaStreamCreateWithFlags(&mg.cap_stream, cudaStreamNonBlocking));
+    MFNS_CUDA(cudaStreamBeginCapture(mg.cap_stream, cudaStreamCaptureModeThreadLocal));
+    stmg_cycle(mg, 0, mg.cap_stream);
+    cudaGraph_t g;
+    MFNS_CUDA(cudaStreamEndCapture(mg.cap_stream, &g));
+    const cudaError_t e = cudaGraphInstantiate(&mg.vc_graph, g, 0);
+    cudaGraphDestroy(g);
+    MFNS_CUDA(e);
+  }
+  MFNS_CUDA(cudaGraphLaunch(mg.vc_graph, s));
+}
+
 static double dev_dot(Stmg& mg, const double* a, const double* b, int64_t n, cudaStream_t s) {
   dot<double>(mg.scal.as<double>() + 1, a, b, n, mg.part.as<double>(), s);
   double h;
@@ -553,12 +589,18 @@ static int stmg_fgmres(mfns_spacetime& st, const double* b, double* x, double to
   StmgLevel& L = *mg.lv[0];
   const int64_t N = (int64_t)L.Q * L.n;
   const int m = mg.restart;
+  if (m + 1 > kMaxDots) throw Error(kErrUnsupported, "space-time FGMRES restart beyond the multi-dot width");
   if (!mg.V.get()) {
     Budget* bud = st.bud;
     mg.V.alloc(bud, (size_t)(m + 1) * N * 8);
     mg.Z.alloc(bud, (size_t)m * N * 8);
     mg.w.alloc(bud, (size_t)N * 8);
     mg.bp.alloc(bud, (size_t)N * 8);
+    std::vector<const double*> pv(m + 1);
+    for (int i = 0; i <= m; ++i) pv[i] = mg.V.as<double>() + (int64_t)i * N;
+    mg.ptrV = upload(bud, pv);
+    mg.hvec.alloc(bud, (size_t)(2 * kMaxDots + 1) * 8);
+    MFNS_CUDA(cudaMallocHost(&mg.hh_host, (size_t)(2 * kMaxDots + 1) * 8));
   }
   double* V = mg.V.as<double>();
   double* Z = mg.Z.as<double>();
@@ -592,16 +634,27 @@ static int stmg_fgmres(mfns_spacetime& st, const double* b, double* x, double to
       double* Vj = V + (int64_t)j * N;
       double* Zj = Z + (int64_t)j * N;
       MFNS_CUDA(cudaMemcpyAsync(L.vb.get(), Vj, (size_t)N * 8, cudaMemcpyDeviceToDevice, s));
-      stmg_cycle(mg, 0, s);
+      stmg_vcycle(mg, s);
       MFNS_CUDA(cudaMemcpyAsync(Zj, L.vx.get(), (size_t)N * 8, cudaMemcpyDeviceToDevice, s));
       project_constants(mg, Zj, s);
       level_vmult(mg, L, Zj, w, s);
-      for (int i = 0; i <= j; ++i) h[i] = dev_dot(mg, V + (int64_t)i * N, w, N, s);
-      for (int i = 0; i <= j; ++i) vaxpy<double>(w, -h[i], V + (int64_t)i * N, N, s);
-      for (int i = 0; i <= j; ++i) h2[i] = dev_dot(mg, V + (int64_t)i * N, w, N, s);
-      for (int i = 0; i <= j; ++i) vaxpy<double>(w, -h2[i], V + (int64_t)i * N, N, s);
+      // classical Gram--Schmidt twice: all coefficients of a pass in one multi-dot, the update in
+      // one multi-axpy, and one host round trip per iteration for both passes and the norm
+      const double** Vp = (const double**)mg.ptrV.as<const double*>();
+      double* hd = mg.hvec.as<double>();
+      multidot(hd, nullptr, w, j + 1, N, mg.part.as<double>(), Vp, s);
+      multi_axpy(w, Vp, hd, j + 1, N, s);
+      multidot(hd + kMaxDots, nullptr, w, j + 1, N, mg.part.as<double>(), Vp, s);
+      multi_axpy(w, Vp, hd + kMaxDots, j + 1, N, s);
+      dot<double>(hd + 2 * kMaxDots, w, w, N, mg.part.as<double>(), s);
+      MFNS_CUDA(cudaMemcpyAsync(mg.hh_host, hd, (size_t)(2 * kMaxDots + 1) * 8, cudaMemcpyDeviceToHost, s));
+      MFNS_CUDA(cudaStreamSynchronize(s));
+      for (int i = 0; i <= j; ++i) {
+        h[i] = mg.hh_host[i];
+        h2[i] = mg.hh_host[kMaxDots + i];
+      }
       for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = h[i] + h2[i];
-      const double hn = std::sqrt(dev_dot(mg, w, w, N, s));
+      const double hn = std::sqrt(std::max(mg.hh_host[2 * kMaxDots], 0.0));
       H[(size_t)(j + 1) * m + j] = hn;
       if (hn > 0.0) {
         MFNS_CUDA(cudaMemcpyAsync(V + (int64_t)(j + 1) * N, w, (size_t)N * 8, cudaMemcpyDeviceToDevice, s));
@@ -943,7 +996,7 @@ extern "C" int mfns_spacetime_vcycle(mfns_spacetime* st, const void* b, void* x,
   MFNS_CUDA(cudaSetDevice(st->ctx->device));
   const size_t bytes = (size_t)L.Q * L.n * 8;
   MFNS_CUDA(cudaMemcpyAsync(L.vb.get(), b, bytes, cudaMemcpyDeviceToDevice, s));
-  stmg_cycle(mg, 0, s);
+  stmg_vcycle(mg, s);
   MFNS_CUDA(cudaMemcpyAsync(x, L.vx.get(), bytes, cudaMemcpyDeviceToDevice, s));
   ST_END
 }
