@@ -76,6 +76,13 @@ CASES = [
     ("stokes_a", 2, 4, 3, BALL, dict(nu=1.0)),
     ("pmass", 3, 3, 1, None, dict(nu=1.0)),
     ("pmass", 2, 2, 3, BALL, dict(nu=1.0)),
+    # edge cases: one cell (seven empty colours), odd n (colours of unequal size, ragged last
+    # blocks in every colour launch), a level of many blocks
+    ("stab_ns", 3, 1, 2, None, dict(nu=1e-2, dt=1e-2)),
+    ("stab_ns", 3, 5, 2, None, dict(nu=1e-2, dt=1e-2)),
+    ("stab_ns", 3, 7, 2, None, dict(nu=5e-3, dt=2e-2)),
+    ("stab_ns", 2, 1, 2, None, dict(nu=1e-2, dt=1e-2)),
+    ("stokes_a", 3, 1, 2, None, dict(nu=1.0)),
 ]
 
 
