@@ -466,7 +466,8 @@ def spacetime_section(api, L, inputs, torch):
     """Section 4 (space-time): the slab operator K = G_Q (x) M + tau I_Q (x) A of DG(1) in time on the
     Taylor--Hood Q2/Q1 space of the unit cube with 32^3 cells (one product, FP64 and FP32), and
     FGMRES preconditioned by the space-time multigrid (vertex-star Schwarz, nu_s = 4, omega = 0.7)
-    on 8^3 cells, tau = 0.05, for a manufactured slab solution.  Errors are recorded, not raised:
+    on 8^3 cells, tau = 0.05, for a manufactured slab solution, with FP64 and with FP32 patch
+    inverses; one Schwarz application on 16^3 cells with each.  Errors are recorded, not raised:
     this section runs last."""
     out = {}
     ctx = None
@@ -520,6 +521,30 @@ def spacetime_section(api, L, inputs, torch):
                                        "solve_s": time.perf_counter() - t0,
                                        "error_vs_xstar": float(torch.linalg.norm(x - xs) / torch.linalg.norm(xs)),
                                        "schwarz_level0": _schwarz_rate(st, torch)}
+        # the same solve with FP32 patch inverses (stored and applied in FP32, the rest FP64)
+        st.mg_build(nu_s=4, omega=0.7, inverse_precision=1)
+        x.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        its, rel = st.solve(b, x, tol=1e-10, maxit=200, raise_on_nonconvergence=False)
+        torch.cuda.synchronize()
+        out["stmg_solve_8cube_dg1"]["fp32_inverses"] = {
+            "iterations": its, "rel_residual": rel, "solve_s": time.perf_counter() - t0,
+            "error_vs_xstar": float(torch.linalg.norm(x - xs) / torch.linalg.norm(xs)),
+            "schwarz_level0": _schwarz_rate(st, torch)}
+        st.close()
+        p.close()
+        m.close()
+        # the Schwarz application where its patch inverses outgrow the L2: 16^3 cells, FP64 and FP32
+        m = api.Mesh(ctx, 3, 16)
+        p = api.Problem(ctx, m, kind=L.STOKES, degree=2, nu=1.0, lambda_max=1.0)
+        st = api.SpaceTime(p, 1, 0.05)
+        row = {"entries": st.Q * st.n}
+        for prec, name in ((0, "fp64_inverses"), (1, "fp32_inverses")):
+            t0 = time.perf_counter()
+            st.mg_build(nu_s=4, omega=0.7, inverse_precision=prec)
+            row[name] = dict(_schwarz_rate(st, torch), setup_s=time.perf_counter() - t0)
+        out["schwarz_16cube_dg1"] = row
         st.close()
         p.close()
         m.close()

@@ -427,8 +427,12 @@ int mfns_spacetime_destroy(mfns_spacetime* st);
  * entry weighted by the inverse number of patches holding it, constrained rows solved exactly;
  * the coarsest level is solved directly (pseudo-inverse: the constant pressure of every stage is
  * a null direction).  The set-up probes the spatial operators on the device, inverts the patch
- * blocks on the host and synchronises `stream`. */
-int mfns_spacetime_mg_build(mfns_spacetime* st, int nu_s, double omega, int coarse_n, void* stream);
+ * blocks on the host (in FP64) and synchronises `stream`.  inverse_precision: the patch inverses
+ * are stored and applied in FP64 (0) or rounded to FP32 and applied in FP32 (1: half the bytes
+ * of every patch solve; the vectors, the transfers, the coarse solve and the outer FGMRES stay
+ * FP64).  Error: ARG for another inverse_precision. */
+int mfns_spacetime_mg_build(mfns_spacetime* st, int nu_s, double omega, int coarse_n, int inverse_precision,
+                            void* stream);
 /* Number of levels; for 0 <= level < *n_levels also its spatial degree, temporal degree and
  * spatial vector length (level -1: the count only).  ARG if the multigrid is not built. */
 int mfns_spacetime_mg_level(const mfns_spacetime* st, int level, int* n_levels, int* k, int* r, int64_t* n_stage);

@@ -113,7 +113,7 @@ _SIGS = {
     "mfns_spacetime_vmult": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p]),
     "mfns_spacetime_destroy": (C.c_int, [C.c_void_p]),
     "mfns_spacetime_temporal": (C.c_int, [C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
-    "mfns_spacetime_mg_build": (C.c_int, [C.c_void_p, C.c_int, C.c_double, C.c_int, C.c_void_p]),
+    "mfns_spacetime_mg_build": (C.c_int, [C.c_void_p, C.c_int, C.c_double, C.c_int, C.c_int, C.c_void_p]),
     "mfns_spacetime_mg_level": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int),
                                           C.POINTER(C.c_int), C.POINTER(C.c_int64)]),
     "mfns_spacetime_mg_support_points": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),

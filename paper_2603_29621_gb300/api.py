@@ -372,9 +372,11 @@ class SpaceTime:
                                               _vec(dst, n, src.dtype, "dst"), n, _stream(stream)))
         return dst
 
-    # -- space-time multigrid (FP64) ------------------------------------------------------------
-    def mg_build(self, nu_s=4, omega=0.7, coarse_n=2, stream=None):
-        L.check(self.lib.mfns_spacetime_mg_build(self.h, nu_s, omega, coarse_n, _stream(stream)))
+    # -- space-time multigrid (FP64 vectors; patch inverses FP64 or FP32) ----------------------
+    def mg_build(self, nu_s=4, omega=0.7, coarse_n=2, inverse_precision=0, stream=None):
+        """inverse_precision: 0 = FP64 Schwarz patch inverses, 1 = FP32 (stored and applied)."""
+        L.check(self.lib.mfns_spacetime_mg_build(self.h, nu_s, omega, coarse_n, inverse_precision,
+                                                 _stream(stream)))
         nl = C.c_int()
         L.check(self.lib.mfns_spacetime_mg_level(self.h, -1, C.byref(nl), None, None, None))
         self.mg_levels = []

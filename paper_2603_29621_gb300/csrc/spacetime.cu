@@ -69,35 +69,36 @@ __global__ void k_time_restrict(double* __restrict__ coarse, const double* __res
 // Patch solves of the Schwarz smoother, one block per patch: the patch's entries of all stages
 // (stage-major, Q m values) gathered into shared memory, times the patch's inverse (stored column
 // by column, so that the threads of a warp, one row each, read consecutive words), written to the
-// patch's slice of zloc (offset Q * p_ptr[p]).
+// patch's slice of zloc (offset Q * p_ptr[p]).  TK: the type the inverses are stored in and the
+// products formed in (double, or float for the FP32 smoother: half the bytes); zloc is FP64.
+template <typename TK>
 __global__ void k_patch_solve(const double* __restrict__ r, double* __restrict__ zloc, const int64_t* __restrict__ p_ptr,
                               const int32_t* __restrict__ p_idx, const int64_t* __restrict__ k_ptr,
-                              const double* __restrict__ kinv, int Q, int64_t n) {
-  extern __shared__ double rl[];
+                              const TK* __restrict__ kinv, int Q, int64_t n) {
+  extern __shared__ __align__(16) unsigned char rl_raw[];
+  TK* rl = reinterpret_cast<TK*>(rl_raw);
   const int64_t p = blockIdx.x;
   const int64_t b0 = p_ptr[p];
   const int m = (int)(p_ptr[p + 1] - b0);
   const int mq = Q * m;
   for (int t = threadIdx.x; t < mq; t += blockDim.x) {
     const int q = t / m, a = t - q * m;
-    rl[t] = r[(int64_t)q * n + p_idx[b0 + a]];
+    rl[t] = (TK)r[(int64_t)q * n + p_idx[b0 + a]];
   }
   __syncthreads();
-  const double* Kp = kinv + k_ptr[p];
+  const TK* Kp = kinv + k_ptr[p];
   double* out = zloc + (int64_t)Q * b0;
   for (int row = threadIdx.x; row < mq; row += blockDim.x) {
-    // four independent partial sums: the loads and FMAs of a row overlap instead of forming one
-    // dependent chain of mq steps
-    double v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0;
+    // eight independent partial sums: eight loads of a row in flight instead of one dependent
+    // chain of mq steps
+    TK v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     int j = 0;
-    for (; j + 3 < mq; j += 4) {
-      v0 += Kp[(int64_t)j * mq + row] * rl[j];
-      v1 += Kp[(int64_t)(j + 1) * mq + row] * rl[j + 1];
-      v2 += Kp[(int64_t)(j + 2) * mq + row] * rl[j + 2];
-      v3 += Kp[(int64_t)(j + 3) * mq + row] * rl[j + 3];
+    for (; j + 7 < mq; j += 8) {
+#pragma unroll
+      for (int u = 0; u < 8; ++u) v[u] += Kp[(int64_t)(j + u) * mq + row] * rl[j + u];
     }
-    for (; j < mq; ++j) v0 += Kp[(int64_t)j * mq + row] * rl[j];
-    out[row] = (v0 + v1) + (v2 + v3);
+    for (; j < mq; ++j) v[0] += Kp[(int64_t)j * mq + row] * rl[j];
+    out[row] = (double)(((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7])));
   }
 }
 
@@ -157,7 +158,8 @@ struct StmgLevel {
   std::unique_ptr<Transfer> tv, tp;  // spatial: velocity, pressure
   // Schwarz smoother
   int64_t n_patch = 0, max_patch = 0;
-  DevBuf p_ptr, p_idx, k_ptr, kinv, e_ptr, e_base, e_np, w, con;
+  DevBuf p_ptr, p_idx, k_ptr, kinv, e_ptr, e_base, e_np, w, con;  // kinv: FP64, or FP32 (inv_prec 1)
+  int inv_prec = 0;
   int64_t n_con = 0;
   // FP64 work vectors of Q n entries, and the patch results
   DevBuf vx, vb, vr, vt, vz, vmx, zloc;
@@ -181,6 +183,7 @@ struct Stmg {
   }
   int64_t n_pres0 = 0;
   int nu_s = 4;
+  int inv_prec = 0;  // precision of the Schwarz patch inverses: 0 FP64, 1 FP32
   double omega = 0.7, tau = 0.1;
   DevBuf cinv;      // coarsest: inverse of K + sum_q E_q E_q^T, (Q n)^2
   int64_t cn = 0;   // Q n of the coarsest level
@@ -412,7 +415,8 @@ static void build_schwarz(Stmg& mg, StmgLevel& L, Budget* bud, cudaStream_t s) {
     k_ptr.push_back((int64_t)kinv.size());
     max_patch = std::max(max_patch, m);
   }
-  if ((size_t)Q * max_patch * 8 > 48 * 1024) throw Error(kErrUnsupported, "space-time multigrid: patch too large");
+  const size_t tk = mg.inv_prec == 1 ? 4 : 8;
+  if ((size_t)Q * max_patch * tk > 48 * 1024) throw Error(kErrUnsupported, "space-time multigrid: patch too large");
   // occurrences of every spatial entry (patch results to add) and the weights 1 / multiplicity
   std::vector<int64_t> cnt(n + 1, 0);
   for (auto& pt : patches)
@@ -438,8 +442,14 @@ static void build_schwarz(Stmg& mg, StmgLevel& L, Budget* bud, cudaStream_t s) {
   L.p_ptr = upload(bud, p_ptr);
   L.p_idx = upload(bud, p_idx);
   L.k_ptr = upload(bud, k_ptr);
-  L.kinv = upload(bud, kinv);
-  L.kinv_bytes = (int64_t)kinv.size() * 8;
+  L.inv_prec = mg.inv_prec;
+  if (L.inv_prec == 1) {
+    std::vector<float> k32(kinv.begin(), kinv.end());  // rounded to nearest
+    L.kinv = upload(bud, k32);
+  } else {
+    L.kinv = upload(bud, kinv);
+  }
+  L.kinv_bytes = (int64_t)kinv.size() * (int64_t)tk;
   L.e_ptr = upload(bud, cnt);
   L.e_base = upload(bud, e_base);
   L.e_np = upload(bud, e_np);
@@ -452,8 +462,14 @@ static void build_schwarz(Stmg& mg, StmgLevel& L, Budget* bud, cudaStream_t s) {
 // z = S r on level L (weighted additive Schwarz; constrained rows solved exactly)
 static void schwarz(Stmg& mg, StmgLevel& L, const double* r, double* z, cudaStream_t s) {
   const int64_t total = (int64_t)L.Q * L.n;
-  if (L.n_patch > 0)
-    k_patch_solve<<<(unsigned)L.n_patch, 128, (size_t)L.Q * L.max_patch * 8, s>>>(
+  // one thread per row of the largest patch (whole warps, at most 1024): every patch in one pass
+  const unsigned threads = (unsigned)std::min<int64_t>(1024, std::max<int64_t>(32, (L.Q * L.max_patch + 31) / 32 * 32));
+  if (L.n_patch > 0 && L.inv_prec == 1)
+    k_patch_solve<float><<<(unsigned)L.n_patch, threads, (size_t)L.Q * L.max_patch * 4, s>>>(
+        r, L.zloc.as<double>(), L.p_ptr.as<int64_t>(), L.p_idx.as<int32_t>(), L.k_ptr.as<int64_t>(),
+        L.kinv.as<float>(), L.Q, L.n);
+  else if (L.n_patch > 0)
+    k_patch_solve<double><<<(unsigned)L.n_patch, threads, (size_t)L.Q * L.max_patch * 8, s>>>(
         r, L.zloc.as<double>(), L.p_ptr.as<int64_t>(), L.p_idx.as<int32_t>(), L.k_ptr.as<int64_t>(),
         L.kinv.as<double>(), L.Q, L.n);
   k_patch_gather<<<stream_grid(total), 256, 0, s>>>(z, L.zloc.as<double>(), L.e_ptr.as<int64_t>(),
@@ -691,7 +707,7 @@ static int stmg_fgmres(mfns_spacetime& st, const double* b, double* x, double to
   return it;
 }
 
-static void build_stmg(mfns_spacetime& st, int nu_s, double omega, int coarse_n, cudaStream_t s) {
+static void build_stmg(mfns_spacetime& st, int nu_s, double omega, int coarse_n, int inv_prec, cudaStream_t s) {
   const bool pd = st.top != nullptr;  // P^disc slab (else Taylor--Hood on st.problem)
   Budget* bud = st.bud;
   const OpLevel& A0 = pd ? *st.top->A : *st.problem->p->system;
@@ -711,6 +727,7 @@ static void build_stmg(mfns_spacetime& st, int nu_s, double omega, int coarse_n,
   const std::vector<StLevelSpec> seq = stmg_sequence(k0, st.r, (int)fs.size(), time_steps);
   auto mg = std::make_unique<Stmg>();
   mg->nu_s = nu_s;
+  mg->inv_prec = inv_prec;
   mg->omega = omega;
   mg->tau = st.tau;
   for (const StLevelSpec& sp : seq) {
@@ -918,12 +935,13 @@ extern "C" int mfns_spacetime_temporal(int r, double* nodes_host, double* m_host
   catch (const std::exception& e) { return capi_fail(kErrArg, e.what()); } \
   return MFNS_OK;
 
-extern "C" int mfns_spacetime_mg_build(mfns_spacetime* st, int nu_s, double omega, int coarse_n, void* stream) {
+extern "C" int mfns_spacetime_mg_build(mfns_spacetime* st, int nu_s, double omega, int coarse_n, int inverse_precision,
+                                       void* stream) {
   ST_BEGIN
-  if (!st) return capi_fail(kErrArg, "bad arguments");
+  if (!st || (inverse_precision != 0 && inverse_precision != 1)) return capi_fail(kErrArg, "bad arguments");
   MFNS_CUDA(cudaSetDevice(st->ctx->device));
   st->mg.reset();
-  build_stmg(*st, nu_s, omega, coarse_n, reinterpret_cast<cudaStream_t>(stream));
+  build_stmg(*st, nu_s, omega, coarse_n, inverse_precision, reinterpret_cast<cudaStream_t>(stream));
   ST_END
 }
 

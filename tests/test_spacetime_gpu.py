@@ -180,3 +180,55 @@ def test_space_time_solve_converges(ctx, case):
     got = x.cpu().numpy()[full]
     assert rel <= 1e-10 and abs(its - its_o) <= 3, (its, its_o)
     assert np.abs(V.project(got) - xs).max() <= 1e-6 * np.abs(xs).max()
+
+
+@pytest.mark.parametrize("case", [("th", 2, 8, 2, 1), ("th", 3, 4, 2, 1), ("pdisc", 3, 4, 2, 1)],
+                         ids=lambda c: f"{c[0]}-{c[1]}d-n{c[2]}-k{c[3]}-r{c[4]}")
+def test_fp32_patch_inverses(ctx, case):
+    """FP32 Schwarz patch inverses: inverted in FP64, rounded to FP32, the patch products formed in
+    FP32 (half the bytes of every patch solve; vectors, transfers, coarse solve and FGMRES stay
+    FP64).  The smoother application agrees with the FP64 one to single-precision round-off
+    amplified by the patch blocks (<= 2e-5 relative in the 2-norm on uniform random input), the
+    reported inverse bytes halve, and the solve reaches the same tolerance in at most one more
+    iteration, with the same solution (both have no constant pressure per stage) to 1e-6."""
+    from paper_2603_29621_gb300 import _lib as L, api
+    kind, dim, n, k, r = case
+    m = api.Mesh(ctx, dim, n)
+    prob = None
+    if kind == "th":
+        prob = api.Problem(ctx, m, kind=L.STOKES, degree=k, nu=1.0, lambda_max=1.0)
+        st = api.SpaceTime(prob, r, 0.05)
+    else:
+        st = api.SpaceTime.pdisc(ctx, m, k, 1.0, r, 0.05)
+    N = st.Q * st.n
+    x = torch.tensor(inputs.uniform_vector(N, seed=5), device="cuda")
+    xs = torch.tensor(inputs.uniform_vector(N, seed=6), device="cuda")
+    b = torch.empty_like(xs)
+    st.vmult(xs, b)
+    res = {}
+    for prec in (0, 1):
+        st.mg_build(nu_s=4, omega=0.7, inverse_precision=prec)
+        z = torch.zeros(N, dtype=torch.float64, device="cuda")
+        st.mg_apply(0, 1, x, z)
+        nbytes, npatch = st.mg_smoother_bytes(0)
+        xsol = torch.zeros(N, dtype=torch.float64, device="cuda")
+        its, rel = st.solve(b, xsol, tol=1e-10, maxit=200)
+        torch.cuda.synchronize()
+        res[prec] = (z, nbytes, npatch, its, rel, xsol)
+    assert res[0][2] == res[1][2] > 0 and res[1][1] * 2 == res[0][1]
+    z64, z32 = res[0][0], res[1][0]
+    assert float(torch.linalg.norm(z32 - z64) / torch.linalg.norm(z64)) <= 2e-5
+    assert res[1][4] <= 1e-10 and res[1][3] <= res[0][3] + 1, (res[0][3], res[1][3])
+    assert float(torch.linalg.norm(res[1][5] - res[0][5]) / torch.linalg.norm(res[0][5])) <= 1e-6
+    for prec in (0, 1):  # the reported residual is the true one
+        kx = torch.empty_like(b)
+        st.vmult(res[prec][5], kx)
+        torch.cuda.synchronize()
+        assert float(torch.linalg.norm(kx - b) / torch.linalg.norm(b)) <= 1e-9
+    with pytest.raises(L.MfnsError) as e:
+        st.mg_build(inverse_precision=2)
+    assert e.value.code == L.ERR_ARG
+    st.close()
+    if prob is not None:
+        prob.close()
+    m.close()
