@@ -5,9 +5,9 @@
 // input is copied and its constrained entries completed from their masters, every group adds its
 // products, the products on constrained entries are folded into their masters with the same
 // weights (C^T), and constrained rows are identity rows: A = C^T K C on the free DoFs.  The exact
-// diagonal is probed: free DoFs that share no cell once the constraints are resolved are set to
-// one together and read back from one product.
+// diagonal is formed on the host at set-up (hp_exact_diagonal below).
 #include <algorithm>
+#include <cmath>
 #include <map>
 #include <numeric>
 
@@ -20,6 +20,103 @@ template <typename T>
 static DevBuf upload_as(Budget* bud, const std::vector<double>& v) {
   std::vector<T> t(v.begin(), v.end());
   return upload(bud, t);
+}
+
+// Exact diagonal of C^T K C for one field of an hp level, accumulated into diag (FP64, host).
+// The cell forms of hp levels are tensor products of 1D reference matrices on axis-aligned cubes:
+// the vector Laplacian nu (grad u, grad v) acts on every component as the scalar form
+// nu h^(d-2) sum_dir (K1 or M1 per axis), the mass (p, q) as h^d M1 x M1 (x M1), with M1, K1 the
+// degree's 1D mass and stiffness matrices on [0, 1] under the kernels' Gauss rule.  For a free node
+// i and a cell, v_i is i's weight at every slot of the cell (1 at its own slot, its constraint
+// weight at the slots of nodes hanging on it; Dirichlet nodes are zero); the cell adds
+// v_i^T K_cell v_i.  Every component of node i gets the same value.
+static void hp_exact_diagonal(const Forest& f, const HpSpace& S, int ncomp, bool dirichlet, int64_t offset,
+                              bool laplacian, double nu, std::vector<double>& diag) {
+  const int dim = S.dim;
+  std::vector<int32_t> hang_row(S.n_nodes, -1);  // row of a hanging node in the constraint lists
+  for (size_t r = 0; r < S.hang_node.size(); ++r) hang_row[S.hang_node[r]] = (int32_t)r;
+  auto zero = [&](int32_t g) { return dirichlet && S.boundary[g]; };
+  std::map<int, std::pair<std::vector<double>, std::vector<double>>> mats;  // degree -> (M1, K1)
+  auto tables = [&](int k) -> const std::pair<std::vector<double>, std::vector<double>>& {
+    auto it = mats.find(k);
+    if (it != mats.end()) return it->second;
+    OpLaunch L;
+    L.dim = dim;
+    L.k = k;
+    L.op = OP_STOKES_A;
+    fill_tables(L);
+    const int q = L.Q, n = L.N;
+    std::vector<double> dS((size_t)q * n, 0.0);  // basis derivatives at the Gauss points
+    for (int i = 0; i < q; ++i)
+      for (int a = 0; a < n; ++a) {
+        double v = 0.0;
+        for (int r = 0; r < q; ++r) v += L.D[i * q + r] * L.S[r * n + a];
+        dS[(size_t)i * n + a] = v;
+      }
+    std::vector<double> M1((size_t)n * n, 0.0), K1((size_t)n * n, 0.0);
+    for (int a = 0; a < n; ++a)
+      for (int b = 0; b < n; ++b)
+        for (int i = 0; i < q; ++i) {
+          M1[(size_t)a * n + b] += L.W[i] * L.S[i * n + a] * L.S[i * n + b];
+          K1[(size_t)a * n + b] += L.W[i] * dS[(size_t)i * n + a] * dS[(size_t)i * n + b];
+        }
+    return mats.emplace(k, std::make_pair(std::move(M1), std::move(K1))).first->second;
+  };
+  struct Ent {
+    int32_t node;  // free node
+    int slot;
+    double w;
+  };
+  std::vector<Ent> vloc;  // (free node, slot, weight) of the cell, grouped by node
+  for (size_t c = 0; c < f.n_cells(); ++c) {
+    const int k = S.degree[c], n = k + 1;
+    const auto& mk = tables(k);
+    const std::vector<double>& M1 = mk.first;
+    const std::vector<double>& K1 = mk.second;
+    const double h = f.h(c);
+    const double scale = laplacian ? nu * std::pow(h, dim - 2) : std::pow(h, dim);
+    const int64_t base = S.cell_ptr[c];
+    const int nb = (int)(S.cell_ptr[c + 1] - base);
+    vloc.clear();
+    for (int s = 0; s < nb; ++s) {
+      const int32_t g = S.cell_nodes[base + s];
+      if (zero(g)) continue;
+      const int32_t r = hang_row[g];
+      if (r < 0) {
+        vloc.push_back({g, s, 1.0});
+        continue;
+      }
+      for (int32_t j = S.hang_ptr[r]; j < S.hang_ptr[r + 1]; ++j)
+        if (!zero(S.hang_master[j])) vloc.push_back({S.hang_master[j], s, S.hang_w[j]});
+    }
+    std::stable_sort(vloc.begin(), vloc.end(), [](const Ent& a, const Ent& b) { return a.node < b.node; });
+    auto entry = [&](int s, int t) {  // K_cell[s][t] / scale
+      int as[3] = {s % n, (s / n) % n, dim == 3 ? s / (n * n) : 0};
+      int at[3] = {t % n, (t / n) % n, dim == 3 ? t / (n * n) : 0};
+      if (!laplacian) {
+        double v = 1.0;
+        for (int ax = 0; ax < dim; ++ax) v *= M1[(size_t)as[ax] * n + at[ax]];
+        return v;
+      }
+      double v = 0.0;
+      for (int dir = 0; dir < dim; ++dir) {
+        double p = 1.0;
+        for (int ax = 0; ax < dim; ++ax) p *= (ax == dir ? K1 : M1)[(size_t)as[ax] * n + at[ax]];
+        v += p;
+      }
+      return v;
+    };
+    for (size_t b0 = 0; b0 < vloc.size();) {
+      size_t b1 = b0 + 1;
+      while (b1 < vloc.size() && vloc[b1].node == vloc[b0].node) ++b1;
+      double acc = 0.0;
+      for (size_t a = b0; a < b1; ++a)
+        for (size_t b = b0; b < b1; ++b) acc += vloc[a].w * vloc[b].w * entry(vloc[a].slot, vloc[b].slot);
+      for (int comp = 0; comp < ncomp; ++comp)
+        diag[(size_t)(offset + (int64_t)vloc[b0].node * ncomp + comp)] += scale * acc;
+      b0 = b1;
+    }
+  }
 }
 
 void build_hp_oplevel(OpLevel& lv, const Forest& f, const std::vector<int32_t>& degree, const Physics& ph,
@@ -199,31 +296,16 @@ void build_hp_oplevel(OpLevel& lv, const Forest& f, const std::vector<int32_t>& 
   hp->ct_slave = upload(bud, cs);
   hp->ct_w[0] = upload_as<double>(bud, cw);
   hp->ct_w[1] = upload_as<float>(bud, cw);
-  // probing groups for the diagonal, field by field: free nodes that no cell reaches together
-  std::vector<int32_t> pd;
-  hp->probe_ptr.assign(1, 0);
-  for (size_t fi = 0; fi < fields.size(); ++fi) {
-    const Field& F = fields[fi];
-    const HpSpace& S = *F.sp;
-    std::vector<char> free_node(S.n_nodes, 0);
-    for (int64_t g = 0; g < S.n_nodes; ++g) free_node[g] = !(F.dirichlet && S.boundary[g]) && !hangs[fi][g];
-    std::vector<int32_t> pcol;
-    const int npc = hp_probe_groups(S, free_node, pcol, F.dirichlet);
-    std::vector<std::vector<int32_t>> bucket(npc);  // free nodes of every group, ascending
-    for (int64_t m = 0; m < S.n_nodes; ++m)
-      if (pcol[m] >= 0) bucket[pcol[m]].push_back((int32_t)m);
-    for (int col = 0; col < npc; ++col)
-      for (int c = 0; c < F.ncomp; ++c) {
-        for (int32_t m : bucket[col]) pd.push_back((int32_t)(F.offset + m * F.ncomp + c));
-        hp->probe_ptr.push_back((int64_t)pd.size());
-      }
+  // the exact diagonal: the main field's form (the Taylor--Hood pressure rows have no diagonal
+  // block: zero), constrained rows identity
+  {
+    std::vector<double> dg((size_t)lv.n_dofs, 0.0);
+    hp_exact_diagonal(f, sp, lv.NU, dirichlet, 0, op != OP_PMASS, ph.nu, dg);
+    for (int32_t i : lv.constrained_host) dg[(size_t)i] = 1.0;
+    hp->diag[0] = upload_as<double>(bud, dg);
+    hp->diag[1] = upload_as<float>(bud, dg);
   }
-  hp->probe_dofs = upload(bud, pd);
-  for (int prec = 0; prec < 2; ++prec) {
-    hp->tmp[prec].alloc(bud, lv.n_dofs * esize(prec));
-    hp->probe_e[prec].alloc(bud, lv.n_dofs * esize(prec));
-    hp->probe_y[prec].alloc(bud, lv.n_dofs * esize(prec));
-  }
+  for (int prec = 0; prec < 2; ++prec) hp->tmp[prec].alloc(bud, lv.n_dofs * esize(prec));
   if (op == OP_STOKES) hp->pspace = std::move(psp);
   lv.hp = std::move(hp);
 }
@@ -257,31 +339,7 @@ void hp_vmult(const OpLevel& lv, int prec, const void* src, void* dst, cudaStrea
 }
 
 void hp_diag(const OpLevel& lv, int prec, void* diag, cudaStream_t s) {
-  const HpData& H = *lv.hp;
-  const int64_t n = lv.n_dofs;
-  void* e = H.probe_e[prec].get();
-  void* y = H.probe_y[prec].get();
-  MFNS_CUDA(cudaMemsetAsync(diag, 0, n * esize(prec), s));
-  const int32_t* pd = H.probe_dofs.as<int32_t>();
-  for (size_t p = 0; p + 1 < H.probe_ptr.size(); ++p) {
-    const int64_t a = H.probe_ptr[p], m = H.probe_ptr[p + 1] - H.probe_ptr[p];
-    if (m == 0) continue;
-    MFNS_CUDA(cudaMemsetAsync(e, 0, n * esize(prec), s));
-    if (prec == 0)
-      vset_idx<double>((double*)e, 1.0, pd + a, m, s);
-    else
-      vset_idx<float>((float*)e, 1.0f, pd + a, m, s);
-    hp_vmult(lv, prec, e, y, s);
-    if (prec == 0)
-      vcopy_idx<double>((double*)diag, (const double*)y, pd + a, m, s);
-    else
-      vcopy_idx<float>((float*)diag, (const float*)y, pd + a, m, s);
-  }
-  const int64_t nc = (int64_t)lv.constrained_host.size();
-  if (prec == 0)
-    vset_idx<double>((double*)diag, 1.0, lv.constrained.as<int32_t>(), nc, s);
-  else
-    vset_idx<float>((float*)diag, 1.0f, lv.constrained.as<int32_t>(), nc, s);
+  MFNS_CUDA(cudaMemcpyAsync(diag, lv.hp->diag[prec].get(), lv.n_dofs * esize(prec), cudaMemcpyDeviceToDevice, s));
 }
 
 }  // namespace mfns

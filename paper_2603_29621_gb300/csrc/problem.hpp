@@ -69,14 +69,12 @@ struct HpData {
   HpSpace space;                        // the main field's nodes (velocity, or the scalar field)
   HpSpace pspace;                       // Taylor--Hood: the pressure nodes (degrees k - 1)
   std::vector<std::unique_ptr<HpGroup>> groups;
-  DevBuf tmp[2], probe_e[2], probe_y[2];  // distributed input; probing vectors of the diagonal
+  DevBuf tmp[2];                        // distributed input
+  DevBuf diag[2];                       // exact diagonal of C^T K C (identity rows 1), FP64 / FP32
   // transpose of the constraints: for master dof ct_master[i], slaves ct_slave[j] with weights
   // ct_w[j], j in [ct_ptr[i], ct_ptr[i+1])
   DevBuf ct_master, ct_ptr, ct_slave, ct_w[2];
   int64_t n_ct = 0;
-  // exact diagonal by probing: free dofs in groups that share no cell after the constraints
-  std::vector<int64_t> probe_ptr;
-  DevBuf probe_dofs;
   // Section 3's blended smoother (built on request): additive Schwarz blocks on the combined faces,
   // point Jacobi on the entries in no block
   struct Asm {
