@@ -255,6 +255,22 @@ int mfns_problem_destroy(mfns_problem* p);
  * the first start while their predecessor drains (programmatic dependent launches). */
 int mfns_vmult(mfns_problem* p, int which, int precision, const void* src, void* dst, int64_t n,
                void* stream);
+/* dst_host[i] = A src_host[i], i < count, for vectors in HOST memory (a list of requests to the same
+ * operator, the call a host-side client makes): the library copies each input to the device,
+ * applies the operator exactly as mfns_vmult does (bitwise the same result) and copies the result
+ * back, pipelined over two device staging sets -- the input copy of vector i+1 and the read-back of
+ * vector i-1 overlap the product of vector i -- on two internal copy streams ordered after the work
+ * already in `stream`; when `stream` reaches the end of the call, every dst_host[i] is written.
+ * The staging (4 n entries of the precision) is allocated against the context's budget on the first
+ * call for a (which, precision) and kept until the problem is destroyed or another pair is used.
+ * Host vectors should be page-locked (cudaHostAlloc / cudaHostRegister) for the copies to run
+ * asynchronously; pageable memory works, with the copies staged by the driver.  n as for
+ * mfns_vmult; a dst_host[i] must not overlap any src_host[j] of the call (the same source may be
+ * listed several times).  Calls on one problem must be ordered (the same stream, or the caller
+ * orders them).  Error: ARG (null pointers, count < 1, precision, n), OOM (staging beyond the
+ * budget). */
+int mfns_vmult_host(mfns_problem* p, int which, int precision, const void* const* src_host,
+                    void* const* dst_host, int count, int64_t n, void* stream);
 /* diag = diag(A) (exact, per-cell unit-vector evaluation; 1 on constrained rows); n as in
  * mfns_vmult. */
 int mfns_diagonal(mfns_problem* p, int which, int precision, void* diag, int64_t n, void* stream);

@@ -80,6 +80,8 @@ _SIGS = {
     "mfns_set_lambda_max": (C.c_int, [C.c_void_p, C.c_int, C.c_double]),
     "mfns_problem_destroy": (C.c_int, [C.c_void_p]),
     "mfns_vmult": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p]),
+    "mfns_vmult_host": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.POINTER(C.c_void_p), C.POINTER(C.c_void_p),
+                                  C.c_int, C.c_int64, C.c_void_p]),
     "mfns_diagonal": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_int64, C.c_void_p]),
     "mfns_kernel_timing": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
     "mfns_apply_constraints": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_int64, C.c_void_p]),

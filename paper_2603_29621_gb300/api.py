@@ -186,6 +186,24 @@ class Problem:
                                     _stream(stream)))
         return dst
 
+    def vmult_host(self, srcs, dsts, which=L.OP_SYSTEM, stream=None):
+        """dsts[i] = A srcs[i] for contiguous HOST (CPU) tensors of one dtype (page-locked for
+        asynchronous copies): the library stages, applies and reads back, pipelined; the results
+        are written when `stream` reaches the end of the call."""
+        if len(srcs) != len(dsts) or not srcs:
+            raise ValueError("srcs and dsts: equal, nonzero counts")
+        prec = _prec_of(srcs[0])
+        n, dt = self.n_dofs(which), _dtype(prec)
+        for t in list(srcs) + list(dsts):
+            if t.is_cuda or not t.is_contiguous():
+                raise ValueError("host vectors: contiguous CPU tensors")
+            if t.numel() != n or t.dtype != dt:
+                raise ValueError(f"host vector: {t.numel()} entries of {t.dtype}, expected {n} of {dt}")
+        sp = (C.c_void_p * len(srcs))(*[t.data_ptr() for t in srcs])
+        dp = (C.c_void_p * len(dsts))(*[t.data_ptr() for t in dsts])
+        L.check(self.lib.mfns_vmult_host(self.h, which, prec, sp, dp, len(srcs), n, _stream(stream)))
+        return dsts
+
     def diagonal(self, diag, which=L.OP_SYSTEM, stream=None):
         prec = _prec_of(diag)
         n = self.n_dofs(which)

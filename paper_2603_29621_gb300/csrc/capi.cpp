@@ -318,6 +318,70 @@ int mfns_vmult(mfns_problem* p, int which, int prec, const void* src, void* dst,
   API_END
 }
 
+// staging of mfns_vmult_host for (which, prec, n), (re)built when the pair changes
+static HostIO& host_io(mfns_problem* p, int which, int prec, int64_t n) {
+  std::unique_ptr<HostIO>& h = p->hio;
+  if (h && h->which == which && h->prec == prec && h->n == n) return *h;
+  if (h) {
+    MFNS_CUDA(cudaStreamSynchronize(h->s_in));
+    MFNS_CUDA(cudaStreamSynchronize(h->s_out));
+    h.reset();
+  }
+  auto nh = std::make_unique<HostIO>();
+  nh->which = which;
+  nh->prec = prec;
+  nh->n = n;
+  const size_t bytes = (size_t)n * esize(prec);
+  for (int k = 0; k < 2; ++k) {
+    nh->in[k].alloc(p->p->bud, bytes);
+    nh->out[k].alloc(p->p->bud, bytes);
+  }
+  MFNS_CUDA(cudaStreamCreateWithFlags(&nh->s_in, cudaStreamNonBlocking));
+  MFNS_CUDA(cudaStreamCreateWithFlags(&nh->s_out, cudaStreamNonBlocking));
+  for (cudaEvent_t* e : {&nh->ev_start, &nh->ev_done, &nh->ev_in[0], &nh->ev_in[1], &nh->ev_ap[0], &nh->ev_ap[1],
+                         &nh->ev_out[0], &nh->ev_out[1]})
+    MFNS_CUDA(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
+  h = std::move(nh);
+  return *h;
+}
+
+int mfns_vmult_host(mfns_problem* p, int which, int prec, const void* const* src_host, void* const* dst_host,
+                    int count, int64_t n, void* stream) {
+  API_BEGIN
+  OpLevel* lv = p ? select_op(p, which) : nullptr;
+  if (!lv || !src_host || !dst_host || count < 1) return fail(MFNS_ERR_ARG, "bad arguments");
+  CHECK_LEN(n, lv->n_dofs, "src_host/dst_host");
+  if (prec != 0 && prec != 1) return fail(MFNS_ERR_ARG, "bad precision");
+  for (int i = 0; i < count; ++i)
+    if (!src_host[i] || !dst_host[i]) return fail(MFNS_ERR_ARG, "null host vector");
+  MFNS_CUDA(cudaSetDevice(p->ctx->device));
+  HostIO& h = host_io(p, which, prec, n);
+  const cudaStream_t s = S(stream);
+  const size_t bytes = (size_t)n * esize(prec);
+  // the copy streams start after the work already in `stream` (and so after any earlier call)
+  MFNS_CUDA(cudaEventRecord(h.ev_start, s));
+  MFNS_CUDA(cudaStreamWaitEvent(h.s_in, h.ev_start, 0));
+  MFNS_CUDA(cudaStreamWaitEvent(h.s_out, h.ev_start, 0));
+  for (int i = 0; i < count; ++i) {
+    const int k = i & 1;
+    // staging set k: its previous product has read in[k], its previous read-back has read out[k]
+    // (events not yet recorded count as complete)
+    MFNS_CUDA(cudaStreamWaitEvent(h.s_in, h.ev_ap[k], 0));
+    MFNS_CUDA(cudaMemcpyAsync(h.in[k].get(), src_host[i], bytes, cudaMemcpyHostToDevice, h.s_in));
+    MFNS_CUDA(cudaEventRecord(h.ev_in[k], h.s_in));
+    MFNS_CUDA(cudaStreamWaitEvent(s, h.ev_in[k], 0));
+    MFNS_CUDA(cudaStreamWaitEvent(s, h.ev_out[k], 0));
+    oplevel_vmult(*lv, prec, h.in[k].get(), h.out[k].get(), s);
+    MFNS_CUDA(cudaEventRecord(h.ev_ap[k], s));
+    MFNS_CUDA(cudaStreamWaitEvent(h.s_out, h.ev_ap[k], 0));
+    MFNS_CUDA(cudaMemcpyAsync(dst_host[i], h.out[k].get(), bytes, cudaMemcpyDeviceToHost, h.s_out));
+    MFNS_CUDA(cudaEventRecord(h.ev_out[k], h.s_out));
+  }
+  MFNS_CUDA(cudaEventRecord(h.ev_done, h.s_out));
+  MFNS_CUDA(cudaStreamWaitEvent(s, h.ev_done, 0));
+  API_END
+}
+
 int mfns_kernel_timing(mfns_problem* p, int which, int mode, double* total_ms, int64_t* launches) {
   API_BEGIN
   OpLevel* lv = p ? select_op(p, which) : nullptr;

@@ -34,8 +34,25 @@ struct mfns_mesh {
   mfns_ctx* ctx = nullptr;
   mfns::Forest forest;
 };
+// Staging of mfns_vmult_host: two device input and output sets of one (operator, precision),
+// the two copy streams and the events that order the pipeline.
+struct HostIO {
+  int which = 0, prec = 0;
+  int64_t n = 0;
+  mfns::DevBuf in[2], out[2];
+  cudaStream_t s_in = nullptr, s_out = nullptr;
+  cudaEvent_t ev_start = nullptr, ev_done = nullptr, ev_in[2] = {}, ev_ap[2] = {}, ev_out[2] = {};
+  ~HostIO() {
+    for (cudaEvent_t e : {ev_start, ev_done, ev_in[0], ev_in[1], ev_ap[0], ev_ap[1], ev_out[0], ev_out[1]})
+      if (e) cudaEventDestroy(e);
+    if (s_in) cudaStreamDestroy(s_in);
+    if (s_out) cudaStreamDestroy(s_out);
+  }
+};
+
 struct mfns_problem {
   mfns_ctx* ctx = nullptr;
+  std::unique_ptr<HostIO> hio;  // declared before p: destroyed after it
   std::unique_ptr<mfns::Problem> p;
 };
 

@@ -181,3 +181,49 @@ def test_wrong_vector_lengths_are_rejected_and_leave_the_runtime_clean(ctx):
     pl.vcycle(b, x)
     torch.cuda.synchronize()
     assert bool(torch.isfinite(x).all()) and float(x.abs().max()) > 0
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_vmult_host_equals_device_product(ctx, prec):
+    """mfns_vmult_host (host vectors in and out, copies and products pipelined over two staging
+    sets): every result is bitwise the device product of its input -- four vectors (both staging
+    sets used twice, one source listed twice), a second call reusing the staging, and pageable host
+    memory; wrong lengths and counts are rejected without touching memory."""
+    import ctypes as C
+    from paper_2603_29621_gb300 import _lib as L, api
+    m = api.Mesh(ctx, 3, 3)
+    prob = api.Problem(ctx, m, kind=L.STAB_NS, degree=2, nu=1e-2, dt=1e-2, lambda_max=1.0)
+    n = prob.info.n_dofs
+    dt = torch.float64 if prec == 0 else torch.float32
+    hs = [torch.tensor(inputs.uniform_vector(n, seed=20 + i), dtype=dt).pin_memory() for i in range(3)]
+    srcs = [hs[0], hs[1], hs[2], hs[0]]
+    dsts = [torch.full((n,), 7.0, dtype=dt).pin_memory() for _ in srcs]
+    refs = []
+    for s_ in srcs:
+        r = torch.empty(n, dtype=dt, device="cuda")
+        prob.vmult(s_.cuda(), r)
+        refs.append(r)
+    torch.cuda.synchronize()
+    refs = [r.cpu() for r in refs]
+    for _ in range(2):
+        for d_ in dsts:
+            d_.fill_(7.0)
+        prob.vmult_host(srcs, dsts)
+        torch.cuda.synchronize()
+        for d_, r in zip(dsts, refs):
+            assert torch.equal(d_, r)
+    pageable = torch.empty(n, dtype=dt)
+    prob.vmult_host([hs[1].clone()], [pageable])
+    torch.cuda.synchronize()
+    assert torch.equal(pageable, refs[1])
+    lib = ctx.lib
+    sp = (C.c_void_p * 1)(hs[0].data_ptr())
+    dp = (C.c_void_p * 1)(dsts[0].data_ptr())
+    s = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    before = dsts[0].clone()
+    assert lib.mfns_vmult_host(prob.h, L.OP_SYSTEM, prec, sp, dp, 1, n + 1, s) == L.ERR_ARG
+    assert lib.mfns_vmult_host(prob.h, L.OP_SYSTEM, prec, sp, dp, 0, n, s) == L.ERR_ARG
+    torch.cuda.synchronize()
+    assert torch.equal(dsts[0], before)
+    with pytest.raises(ValueError):
+        prob.vmult_host([hs[0].cuda()], [dsts[0]])
