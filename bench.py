@@ -53,6 +53,25 @@ def parse():
     return ap.parse_args()
 
 
+def max_over_ranks(values, world, device):
+    """Every timing entry maximised over the ranks (the job takes as long as its slowest replica);
+    a no-op for one rank.  device: where the reduction runs (CUDA under nccl, CPU under gloo)."""
+    t = torch_mod().tensor(values, device=device, dtype=torch_mod().float64)
+    if world > 1:
+        torch_mod().distributed.all_reduce(t, op=torch_mod().distributed.ReduceOp.MAX)
+    return t.tolist()
+
+
+def whole_job_rate(units_per_rank, world, ms):
+    """Whole-job throughput: the units all replicas processed per second of the slowest one."""
+    return world * units_per_rank / (ms * 1e-3)
+
+
+def torch_mod():
+    import torch
+    return torch
+
+
 def dist_setup(gpus):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -865,10 +884,7 @@ def run_ours(args, world, rank, local):
     ms_e2e = e2e_pipelined(args.steps)
     clk = clocks.stop()
     # ---- max over ranks
-    tt = torch.tensor([ms32, ms_e2e, ms_e2e_serial], device=dev, dtype=torch.float64)
-    if world > 1:
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-    ms32, ms_e2e, ms_e2e_serial = tt.tolist()
+    ms32, ms_e2e, ms_e2e_serial = max_over_ranks([ms32, ms_e2e, ms_e2e_serial], world, dev)
     extra = {}
     if rank == 0:
         # ---- FP64 vmult, Chebyshev-3 sweep, V-cycle (FP32), each recorded, none can end the run
@@ -917,7 +933,7 @@ def run_ours(args, world, rank, local):
     torch.cuda.empty_cache()
     if rank != 0:
         return
-    value = world * ndof / (ms32 * 1e-3)
+    value = whole_job_rate(ndof, world, ms32)
     cells_per_launch = ncell / launches_per_step if launches_per_step else ncell
     peak_alu = N_SM * FP32_LANES * 2 * SM_MHZ_MAX * 1e6 / 1e12    # TFLOP/s
     achieved_alu = FLOP_PER_CELL * cells_per_launch / (avg_launch_ms * 1e-3) / 1e12
@@ -942,13 +958,13 @@ def run_ours(args, world, rank, local):
         "clocks": clk,
         # per step: the clearing kernel, the cell kernel's colour launches and the constrained-row copy
         "gpu_launches": (launches_per_step + 2) * args.steps,
-        "e2e": {"value": world * ndof / (ms_e2e * 1e-3), "unit": UNIT, "h2d_bytes_per_step": ndof * 4,
+        "e2e": {"value": whole_job_rate(ndof, world, ms_e2e), "unit": UNIT, "h2d_bytes_per_step": ndof * 4,
                 "d2h_bytes_per_step": ndof * 4, "ms_per_step": ms_e2e,
                 "how": "C ABI with HOST buffers: one mfns_vmult_host call for all timed steps (pinned "
                        "host vectors); every step's input is copied in and its result read back, the "
                        "library pipelining step i+1's input copy and step i-1's read-back with step i's "
                        "apply over two staging sets; bound by the host link (both directions at once)",
-                "serial": {"value": world * ndof / (ms_e2e_serial * 1e-3), "ms_per_step": ms_e2e_serial,
+                "serial": {"value": whole_job_rate(ndof, world, ms_e2e_serial), "ms_per_step": ms_e2e_serial,
                            "how": "one mfns_vmult_host call per step: copy in, apply, copy out"}},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                      "frac": achieved / hbm_peak, "traffic": traffic,
