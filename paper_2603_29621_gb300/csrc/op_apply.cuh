@@ -9,12 +9,23 @@ constexpr int kOpWarps = 4;  // largest number of warps per block (the block siz
 // adjacent lanes), the y-direction ones through shared memory: measured on the 64^3 FP32 apply,
 // 0.199 ms against 0.204 ms with both through shared memory.
 constexpr bool kXShfl = true;
-// FP32 products with four components per node scatter with vector reductions done by the L2
-// (red.global.add.v4.f32) instead of reading dst after the grid-dependency wait: the same single
-// rounding per contribution, and the colours stay ordered by that wait, so results are unchanged
-// bit for bit; the late, exposed dst loads go away (64^3 apply: 0.186 against 0.196 ms).  The
-// fused epilogue needs the completed sum and keeps the read-modify-write, and so does FP64.
+// FP32 products scatter with reductions done by the L2 (red.global.add.v4.f32 for four components
+// per node, red.global.add.f32 otherwise) instead of reading dst after the grid-dependency wait:
+// the same single rounding per contribution, and the colours stay ordered by that wait, so results
+// are unchanged bit for bit; the late, exposed dst loads go away (64^3 stabilised apply: 0.186
+// against 0.196 ms).  The fused epilogue needs the completed sum and keeps the read-modify-write,
+// and so does FP64.
 constexpr bool kScatterRed = true;
+
+// dst += v for one entry of a colour launch's scatter: an L2 reduction in FP32 (see kScatterRed),
+// a read-modify-write in FP64
+template <typename T>
+__device__ __forceinline__ void scatter_add(T* p, T v) {
+  if constexpr (kScatterRed && sizeof(T) == 4)
+    asm volatile("red.global.add.f32 [%0], %1;" ::"l"(p), "f"(v) : "memory");
+  else
+    *p += v;
+}
 
 template <int DIM, int Q>
 struct Team {
@@ -860,13 +871,13 @@ op_kernel(const OpArgs<T, K + 1, K + 1, (OP == OP_STOKES ? K : K + 1)> args) {
             }
           } else {
 #pragma unroll
-            for (int f = 0; f < NU; ++f) d[f] += r[f][c];
+            for (int f = 0; f < NU; ++f) scatter_add(d + f, r[f][c]);
           }
         }
       }
       if (Tr::SPLIT_P && ownp) {
 #pragma unroll
-        for (int c = 0; c < NP; ++c) dstp[p_offset + pnode[c]] += rp[c];
+        for (int c = 0; c < NP; ++c) scatter_add(dstp + p_offset + pnode[c], rp[c]);
       }
     }
   }
