@@ -15,17 +15,7 @@ constexpr bool kXShfl = true;
 // are unchanged bit for bit; the late, exposed dst loads go away (64^3 stabilised apply: 0.186
 // against 0.196 ms).  The fused epilogue needs the completed sum and keeps the read-modify-write,
 // and so does FP64.
-constexpr bool kScatterRed = true;
-
-// dst += v for one entry of a colour launch's scatter: an L2 reduction in FP32 (see kScatterRed),
-// a read-modify-write in FP64
-template <typename T>
-__device__ __forceinline__ void scatter_add(T* p, T v) {
-  if constexpr (kScatterRed && sizeof(T) == 4)
-    asm volatile("red.global.add.f32 [%0], %1;" ::"l"(p), "f"(v) : "memory");
-  else
-    *p += v;
-}
+constexpr bool kScatterRed = kScatterRedF32;
 
 template <int DIM, int Q>
 struct Team {

@@ -116,6 +116,18 @@ template <> struct V4<double> { using type = double2; };  // two loads per node
 
 __device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
 
+// Scatters whose every destination entry receives one contribution per launch (a colour of a cell
+// kernel, the owners of a transfer): in FP32 the addition is done by the L2 (red.global.add.f32:
+// one rounding, as a read-modify-write, without the load); in FP64 a read-modify-write.
+constexpr bool kScatterRedF32 = true;
+template <typename T>
+__device__ __forceinline__ void scatter_add(T* p, T v) {
+  if constexpr (kScatterRedF32 && sizeof(T) == 4)
+    asm volatile("red.global.add.f32 [%0], %1;" ::"l"(p), "f"(v) : "memory");
+  else
+    *p += v;
+}
+
 // Flags of the hanging-node constraint lines through a slot (see mesh.hpp for the mask layout).
 template <int DIM, int N>
 struct LineFlags {

@@ -186,7 +186,7 @@ __global__ void __launch_bounds__(128) transfer_kernel(const TransferArgs<T, NF,
             const int32_t v = a.fnodes[(int64_t)fc * NBF + slot];
             if (v < 0) continue;                 // not the owner, or a hanging fine node
             if ((v & 0x40000000) && f < NVEL) continue;  // Dirichlet fine entry
-            a.dst[(int64_t)(v & 0x3fffffff) * NCOMP + f] += o[c];
+            scatter_add(a.dst + (int64_t)(v & 0x3fffffff) * NCOMP + f, o[c]);
           }
         }
       }
@@ -227,7 +227,7 @@ __global__ void __launch_bounds__(128) transfer_kernel(const TransferArgs<T, NF,
 #pragma unroll
       for (int c = 0; c < NC; ++c)
 #pragma unroll
-        for (int f = 0; f < NCOMP; ++f) a.dst[(int64_t)(cid[c] & 0x7fffffff) * NCOMP + f] += acc[f][c];
+        for (int f = 0; f < NCOMP; ++f) scatter_add(a.dst + (int64_t)(cid[c] & 0x7fffffff) * NCOMP + f, acc[f][c]);
     }
   }
 }
