@@ -9,12 +9,13 @@ constexpr int kOpWarps = 4;  // largest number of warps per block (the block siz
 // adjacent lanes), the y-direction ones through shared memory: measured on the 64^3 FP32 apply,
 // 0.199 ms against 0.204 ms with both through shared memory.
 constexpr bool kXShfl = true;
-// FP32 products scatter with reductions done by the L2 (red.global.add.v4.f32 for four components
-// per node, red.global.add.f32 otherwise) instead of reading dst after the grid-dependency wait:
-// the same single rounding per contribution, and the colours stay ordered by that wait, so results
-// are unchanged bit for bit; the late, exposed dst loads go away (64^3 stabilised apply: 0.186
-// against 0.196 ms).  The fused epilogue needs the completed sum and keeps the read-modify-write,
-// and so does FP64.
+// Products scatter with reductions done by the L2 (red.global.add.v4.f32 for four FP32 components
+// per node, scalar red.global.add.f32 / .f64 otherwise, see scatter_add) instead of reading dst
+// after the grid-dependency wait: the same single rounding per contribution, and the colours stay
+// ordered by that wait, so results are unchanged bit for bit; the late, exposed dst loads go away
+// (64^3 stabilised FP32 apply: 0.186 against 0.196 ms).  The fused epilogue needs the completed sum
+// and keeps the read-modify-write, and so do FP64 nodes of four components (two 16-byte accesses;
+// that apply is bound by the FP64 rate).
 constexpr bool kScatterRed = kScatterRedF32;
 
 template <int DIM, int Q>
