@@ -908,7 +908,8 @@ def run_ours(args, world, rank, local):
 
         def vcyc():
             assert prob.info.cycle_dofs == ndof
-            return {"ms": timed(lambda: prob.vcycle(b32, xs), steps_s, 3), "levels": prob.info.n_levels}
+            return {"ms": timed(lambda: prob.vcycle(b32, xs), steps_s, 3, nvtx="timed_vcycle_fp32"),
+                    "levels": prob.info.n_levels}
 
         guarded("chebyshev3_fp32", cheb)
         guarded("vcycle_fp32", vcyc)

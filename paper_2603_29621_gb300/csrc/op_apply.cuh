@@ -844,13 +844,20 @@ op_kernel(const OpArgs<T, K + 1, K + 1, (OP == OP_STOKES ? K : K + 1)> args) {
             }
             continue;
           }
+          // uniform meshes: the velocity rows of boundary nodes are the level's constrained (identity)
+          // rows, set by the clearing kernel or by a copy after the colours; the colours add zero there
+          // (selects, not a branch: every lane of the warp issues the same scatter)
+          if constexpr (STRUCT && OP != OP_PMASS) {
+#pragma unroll
+            for (int f = 0; f < DIM && f < NU; ++f) r[f][c] = bnd[c] ? T(0) : r[f][c];
+          }
           if constexpr (NU == 4 && kScatterRed && sizeof(T) == 4) {
             // the addition done by the L2 (one rounding, as the read-modify-write below)
             asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(d), "f"(r[0][c]), "f"(r[1][c]),
                          "f"(r[2][c]), "f"(r[3][c])
                          : "memory");
           } else if constexpr (NU == 4) {
-            // dst values were loaded with the gather (no other cell of this colour touches them)
+            // dst values loaded after the grid-dependency wait (no other cell of this colour touches them)
             T o[4];
 #pragma unroll
             for (int f = 0; f < 4; ++f) o[f] = d0[f][c] + r[f][c];

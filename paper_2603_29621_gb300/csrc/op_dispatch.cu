@@ -227,10 +227,47 @@ __global__ void k_clear_then_release(T* y, int64_t n) {
   }
 }
 
-void op_apply_cleared(const OpLaunch& L, int prec, const void* src, void* dst, int64_t n, cudaStream_t s) {
+// dst = src on the rows marked in keep (bit i % 32 of word i / 32), 0 elsewhere, then lets the
+// colour launches that follow start early.  16-byte accesses when both vectors are 16-byte aligned
+// (the 16 / sizeof(T) entries of one access share a mask word), element accesses otherwise.
+template <typename T>
+__global__ void k_clear_keep_then_release(T* y, const T* x, const uint32_t* __restrict__ keep, int64_t n) {
+  asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  auto bit = [&](int64_t i) { return (keep[i >> 5] >> (i & 31)) & 1u; };
+  int64_t done = 0;
+  if (((reinterpret_cast<uintptr_t>(y) | reinterpret_cast<uintptr_t>(x)) & 15u) == 0) {
+    constexpr int V = 16 / sizeof(T);
+    const int64_t nv = n / V;
+    for (int64_t i = i0; i < nv; i += stride) {
+      const uint32_t b = (keep[(i * V) >> 5] >> ((i * V) & 31)) & ((1u << V) - 1u);
+      float4 v = make_float4(0, 0, 0, 0);
+      if (b) {
+        v = reinterpret_cast<const float4*>(x)[i];
+        T* e = reinterpret_cast<T*>(&v);
+#pragma unroll
+        for (int j = 0; j < V; ++j)
+          if (!((b >> j) & 1u)) e[j] = T(0);
+      }
+      reinterpret_cast<float4*>(y)[i] = v;
+    }
+    done = nv * V;
+  }
+  for (int64_t i = done + i0; i < n; i += stride) y[i] = bit(i) ? x[i] : T(0);
+}
+
+void op_apply_cleared(const OpLaunch& L, int prec, const void* src, void* dst, int64_t n, cudaStream_t s,
+                      const uint32_t* keep) {
   const int64_t nbytes = n * (prec == 0 ? 8 : 4);
   const unsigned grid = (unsigned)std::min<int64_t>((nbytes / 16 + 255) / 256 + 1, 152 * 8);
-  if (prec == 0)
+  if (keep && prec == 0)
+    k_clear_keep_then_release<double><<<grid, 256, 0, s>>>(static_cast<double*>(dst),
+                                                            static_cast<const double*>(src), keep, n);
+  else if (keep)
+    k_clear_keep_then_release<float><<<grid, 256, 0, s>>>(static_cast<float*>(dst), static_cast<const float*>(src),
+                                                           keep, n);
+  else if (prec == 0)
     k_clear_then_release<double><<<grid, 256, 0, s>>>(static_cast<double*>(dst), n);
   else
     k_clear_then_release<float><<<grid, 256, 0, s>>>(static_cast<float*>(dst), n);

@@ -107,8 +107,11 @@ void op_apply_multi(const OpLaunch& L, int prec, int color, const MultiColour& m
 // Runtime dispatch over (dim, k, op, precision); prec 0 = fp64, 1 = fp32.
 void op_apply(const OpLaunch& L, int prec, const void* src, void* dst, bool diag, cudaStream_t s);
 // dst = 0, then dst += A src on the free rows: a clearing kernel followed by the colour launches,
-// all of them programmatic dependent launches after the clear (constrained rows untouched)
-void op_apply_cleared(const OpLaunch& L, int prec, const void* src, void* dst, int64_t n, cudaStream_t s);
+// all of them programmatic dependent launches after the clear (constrained rows untouched).  With
+// keep (a bitmask of n rows that the colour launches do not write: a uniform level's constrained
+// rows), the clearing kernel sets those rows to src instead of 0.
+void op_apply_cleared(const OpLaunch& L, int prec, const void* src, void* dst, int64_t n, cudaStream_t s,
+                      const uint32_t* keep = nullptr);
 // dst (zeroed by the caller) receives partial sums; the epilogue writes the fused result
 void op_apply_epi(const OpLaunch& L, int prec, const void* src, void* dst, const OpEpilogue& epi, cudaStream_t s);
 // ncols applications at once (column j: src + j col_stride -> dst + j col_stride), dst zeroed by the caller

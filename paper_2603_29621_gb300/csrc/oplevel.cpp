@@ -239,6 +239,13 @@ void build_oplevel(OpLevel& lv, const Forest& f, int op, int k, const Physics& p
   }
   std::sort(lv.constrained_host.begin(), lv.constrained_host.end());
   lv.constrained = upload(bud, lv.constrained_host);
+  // uniform meshes: the constrained rows are the velocity rows of boundary nodes, which the
+  // structured cell kernels never write; the clearing kernel of a product sets them from its mask
+  if (lv.L.structured && lv.n_dofs > 0) {
+    std::vector<uint32_t> km((size_t)((lv.n_dofs + 31) / 32), 0u);
+    for (int32_t i : lv.constrained_host) km[(size_t)i >> 5] |= 1u << (i & 31);
+    lv.keep_mask = upload(bud, km);
+  }
   lv.n_hang = (int64_t)hd.size();
   lv.hang_dof = upload(bud, hd);
   lv.hang_ptr = upload(bud, hp);
@@ -251,7 +258,12 @@ void build_oplevel(OpLevel& lv, const Forest& f, int op, int k, const Physics& p
 
 void oplevel_vmult(const OpLevel& lv, int prec, const void* src, void* dst, cudaStream_t s) {
   if (lv.hp) return hp_vmult(lv, prec, src, dst, s);
-  // clearing kernel, then the colour launches (each may start before its predecessor drains)
+  // clearing kernel, then the colour launches (each may start before its predecessor drains);
+  // on uniform meshes the clearing kernel also writes the identity rows, which no colour touches
+  if (lv.keep_mask.get()) {
+    op_apply_cleared(lv.L, prec, src, dst, lv.n_dofs, s, lv.keep_mask.as<uint32_t>());
+    return;
+  }
   op_apply_cleared(lv.L, prec, src, dst, lv.n_dofs, s);
   const int64_t nc = (int64_t)lv.constrained_host.size();
   if (prec == 0)

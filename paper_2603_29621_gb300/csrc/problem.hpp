@@ -37,6 +37,7 @@ struct OpLevel {
   DevBuf lastc;                         // per main node: last colour touching it (fused epilogues)
   std::vector<int32_t> constrained_host;
   DevBuf constrained;                   // identity rows
+  DevBuf keep_mask;                     // uniform meshes: bitmask of the identity rows (see oplevel_vmult)
   int64_t n_hang = 0;
   DevBuf hang_dof, hang_ptr, hang_src, hang_w[2];
   std::vector<int32_t> pres_host;
