@@ -957,8 +957,8 @@ def run_ours(args, world, rank, local):
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": headline_config(n, world),
         "clocks": clk,
-        # per step: the clearing kernel, the cell kernel's colour launches and the constrained-row copy
-        "gpu_launches": (launches_per_step + 2) * args.steps,
+        # per step: the clearing kernel (which also writes the identity rows) and the colour launches
+        "gpu_launches": (launches_per_step + 1) * args.steps,
         "e2e": {"value": whole_job_rate(ndof, world, ms_e2e), "unit": UNIT, "h2d_bytes_per_step": ndof * 4,
                 "d2h_bytes_per_step": ndof * 4, "ms_per_step": ms_e2e,
                 "how": "C ABI with HOST buffers: one mfns_vmult_host call for all timed steps (pinned "
