@@ -124,8 +124,10 @@ __device__ __forceinline__ void mbar_wait0_bounded(unsigned addr, int* err) {
 // EPI: the fused smoother / residual epilogue is compiled in (structured launches only).
 // MULTI: one launch over the cells of several problems (structured, plain products); each block
 // reads its problem's fields from args.probs.
+// DEFER: one launch over every colour of a uniform level (blockIdx.y = colour) that writes each
+// cell's contributions to args.defer instead of adding them into dst (k_gather_cells sums them).
 template <int DIM, int K, int OP, typename T, bool STRUCT, bool DIAG, int FQ = 0, bool EPI = false,
-          bool MULTI = false>
+          bool MULTI = false, bool DEFER = false>
 __global__ void __launch_bounds__(kOpWarps * 32, (EPI && OpMinBlocks<DIM, K, OP, T>::value > 1)
                                                      ? OpMinBlocks<DIM, K, OP, T>::value - 1
                                                      : OpMinBlocks<DIM, K, OP, T>::value)
@@ -167,13 +169,13 @@ op_kernel(const OpArgs<T, K + 1, K + 1, (OP == OP_STOKES ? K : K + 1)> args) {
 #pragma unroll
     for (int i = 0; i < 7; ++i) cf_[i] = pa->cf[i];
   } else {
-    srcp = args.src + (int64_t)blockIdx.y * args.col_stride;
-    dstp = args.dst + (int64_t)blockIdx.y * args.col_stride;
+    srcp = args.src + (DEFER ? 0 : (int64_t)blockIdx.y * args.col_stride);
+    dstp = args.dst + (DEFER ? 0 : (int64_t)blockIdx.y * args.col_stride);
     frozen = args.frozen;
     gexp = args.gexp;
     fqd = args.fq;
     nmesh = args.n;
-    color_offset = args.color_offset;
+    color_offset = DEFER ? args.defer_off[blockIdx.y] : args.color_offset;
     p_offset = args.p_offset;
     bx = (int64_t)blockIdx.x;
     hs = args.h;
@@ -218,10 +220,13 @@ op_kernel(const OpArgs<T, K + 1, K + 1, (OP == OP_STOKES ? K : K + 1)> args) {
       int m[3], bits[3];
       int64_t total = 1;
       for (int d = 0; d < 3; ++d) {
-        bits[d] = d < DIM ? (args.color >> d) & 1 : 0;
+        bits[d] = d < DIM ? ((DEFER ? (int)blockIdx.y : args.color) >> d) & 1 : 0;
         m[d] = d < DIM ? (n - bits[d] + 1) / 2 : 1;
         total *= m[d];
       }
+      // a deferred launch spans all colours, some of which may hold no cell (n = 1): such a
+      // colour's blocks leave before touching memory (total is uniform over the block)
+      if (DEFER && total == 0) return;
       valid = lane_active && t < total;
       const int64_t tt = t < total ? t : total - 1;
       cc[0] = 2 * (int)(tt % m[0]) + bits[0];
@@ -760,7 +765,7 @@ op_kernel(const OpArgs<T, K + 1, K + 1, (OP == OP_STOKES ? K : K + 1)> args) {
     // dst: the previous colour's grid (a programmatic dependency when this is a later colour of
     // the same product) must be complete and visible before dst is read or written
     if (pass == pass_begin) asm volatile("griddepcontrol.wait;\n" ::: "memory");
-    if constexpr (NU == 4 && !(kScatterRed && !EPI && sizeof(T) == 4)) {
+    if constexpr (NU == 4 && !DEFER && !(kScatterRed && !EPI && sizeof(T) == 4)) {
       if (!DIAG && FQ != 2) {
 #pragma unroll
         for (int c = 0; c < N; ++c) {
@@ -851,7 +856,16 @@ op_kernel(const OpArgs<T, K + 1, K + 1, (OP == OP_STOKES ? K : K + 1)> args) {
 #pragma unroll
             for (int f = 0; f < DIM && f < NU; ++f) r[f][c] = bnd[c] ? T(0) : r[f][c];
           }
-          if constexpr (NU == 4 && kScatterRed && sizeof(T) == 4) {
+          if constexpr (DEFER) {
+            const int slot = DIM == 3 ? (c * N + tj_n) * N + ti_n : c * N + ti_n;
+            T* pc = args.defer + ((size_t)cellpos * NB + slot) * NU;
+            if constexpr (NU == 4 && sizeof(T) == 4) {
+              *reinterpret_cast<float4*>(pc) = make_float4(r[0][c], r[1][c], r[2][c], r[3][c]);
+            } else {
+#pragma unroll
+              for (int f = 0; f < NU; ++f) pc[f] = r[f][c];
+            }
+          } else if constexpr (NU == 4 && kScatterRed && sizeof(T) == 4) {
             // the addition done by the L2 (one rounding, as the read-modify-write below)
             asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(d), "f"(r[0][c]), "f"(r[1][c]),
                          "f"(r[2][c]), "f"(r[3][c])

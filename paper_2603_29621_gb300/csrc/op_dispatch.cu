@@ -33,6 +33,13 @@ MFNS_DECL(3, 1, OP_PMASS) MFNS_DECL(3, 2, OP_PMASS) MFNS_DECL(3, 3, OP_PMASS)
 MFNS_DECL(2, 2, OP_VMASS) MFNS_DECL(2, 3, OP_VMASS) MFNS_DECL(2, 4, OP_VMASS)
 MFNS_DECL(3, 2, OP_VMASS) MFNS_DECL(3, 3, OP_VMASS) MFNS_DECL(3, 4, OP_VMASS)
 
+#define MFNS_DECL_DEFER(K)                                                                                   \
+  extern template void op_launch_deferred<3, K, OP_STAB_NS, double>(const OpLaunch&, const double*, double*,      \
+                                                                     cudaStream_t);                                 \
+  extern template void op_launch_deferred<3, K, OP_STAB_NS, float>(const OpLaunch&, const float*, float*, cudaStream_t);
+MFNS_DECL_DEFER(1) MFNS_DECL_DEFER(2) MFNS_DECL_DEFER(3)
+#undef MFNS_DECL_DEFER
+
 bool op_supported(int dim, int k, int op) {
   if (dim != 2 && dim != 3) return false;
   switch (op) {
@@ -255,6 +262,103 @@ __global__ void k_clear_keep_then_release(T* y, const T* x, const uint32_t* __re
     done = nv * V;
   }
   for (int64_t i = done + i0; i < n; i += stride) y[i] = bit(i) ? x[i] : T(0);
+}
+
+struct ColourOffsets {
+  int64_t off[8];
+};
+
+// a + b rounded as the L2's FP32 reduction rounds it (subnormal inputs and result flushed to
+// zero), so that a gathered sum equals the colour-ordered reductions bit for bit; the FP64
+// reduction does not flush
+__device__ __forceinline__ float add_as_reduction(float a, float b) {
+  float r;
+  asm("add.rn.ftz.f32 %0, %1, %2;" : "=f"(r) : "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ double add_as_reduction(double a, double b) { return a + b; }
+
+// dst = A src on a uniform 3D stabilised level from the per-cell contributions of a deferred
+// product: every node adds its cells' contributions in colour order, starting from zero -- the
+// additions, in the same order, that the colour launches' reductions make onto a cleared vector --
+// and the identity rows (velocity of boundary nodes) get src + 0 (src plus the zeros the colours
+// add there).  Node (i0, i1, i2) of the (k n + 1)^3 lattice lies in one cell along a direction where
+// i_d is not a multiple of k, else in the cells i_d / k - 1 and i_d / k that exist; the colour of a
+// cell is the parity of its coordinates.
+template <typename T>
+__global__ void k_gather_cells(T* __restrict__ dst, const T* __restrict__ src, const T* __restrict__ defer, int n,
+                               int K, ColourOffsets co) {
+  const int64_t M = (int64_t)K * n + 1, nn = M * M * M;
+  const int nb1 = K + 1, nbc = nb1 * nb1 * nb1;
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < nn; g += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i[3] = {g % M, (g / M) % M, g / (M * M)};
+    T acc[4] = {T(0), T(0), T(0), T(0)};
+    for (int c = 0; c < 8; ++c) {
+      int64_t cd[3];
+      int loc[3];
+      bool ok = true;
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        const int64_t b = (c >> d) & 1;
+        const int64_t q = i[d] / K, r = i[d] - q * K;
+        int64_t cell;
+        if (r != 0) {
+          cell = q;
+          ok = ok && (cell & 1) == b;
+        } else if ((q & 1) == b) {
+          cell = q;
+          ok = ok && q < n;
+        } else {
+          cell = q - 1;
+          ok = ok && q >= 1;
+        }
+        cd[d] = cell;
+        loc[d] = (int)(i[d] - (int64_t)K * cell);
+      }
+      if (!ok) continue;
+      // the cell's position in the colour-major enumeration of the cell kernels
+      const int64_t m0 = (n - (c & 1) + 1) / 2, m1 = (n - ((c >> 1) & 1) + 1) / 2;
+      const int64_t pos = co.off[c] + (cd[0] >> 1) + m0 * ((cd[1] >> 1) + m1 * (cd[2] >> 1));
+      const int slot = (loc[2] * nb1 + loc[1]) * nb1 + loc[0];
+      const T* v = defer + ((size_t)pos * nbc + slot) * 4;
+#pragma unroll
+      for (int f = 0; f < 4; ++f) acc[f] = add_as_reduction(acc[f], v[f]);
+    }
+    const bool bnd = i[0] == 0 || i[0] == M - 1 || i[1] == 0 || i[1] == M - 1 || i[2] == 0 || i[2] == M - 1;
+#pragma unroll
+    for (int f = 0; f < 3; ++f) dst[g * 4 + f] = bnd ? add_as_reduction(src[g * 4 + f], T(0)) : acc[f];
+    dst[g * 4 + 3] = acc[3];
+  }
+}
+
+void op_apply_deferred(const OpLaunch& L, int prec, const void* src, void* dst, void* defer, cudaStream_t s) {
+  if (L.dim != 3 || L.op != OP_STAB_NS || !L.structured) throw Error(kErrArg, "deferred products: uniform 3D stabilised levels");
+#define MFNS_CASE(K)                                                                                          \
+  if (L.k == K) {                                                                                             \
+    if (prec == 0)                                                                                            \
+      op_launch_deferred<3, K, OP_STAB_NS, double>(L, static_cast<const double*>(src), static_cast<double*>(defer), s); \
+    else                                                                                                      \
+      op_launch_deferred<3, K, OP_STAB_NS, float>(L, static_cast<const float*>(src), static_cast<float*>(defer), s);    \
+  } else
+  MFNS_CASE(1) MFNS_CASE(2) MFNS_CASE(3) throw Error(kErrUnsupported, "deferred products: degree");
+#undef MFNS_CASE
+  ColourOffsets co{};
+  int64_t off = 0;
+  for (int c = 0; c < 8; ++c) {
+    int64_t nc = 1;
+    for (int d = 0; d < 3; ++d) nc *= (L.n - ((c >> d) & 1) + 1) / 2;
+    co.off[c] = off;
+    off += nc;
+  }
+  const int64_t M = (int64_t)L.k * L.n + 1, nn = M * M * M;
+  const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>((nn + 255) / 256, 152 * 16));
+  if (prec == 0)
+    k_gather_cells<double><<<grid, 256, 0, s>>>(static_cast<double*>(dst), static_cast<const double*>(src),
+                                                 static_cast<const double*>(defer), L.n, L.k, co);
+  else
+    k_gather_cells<float><<<grid, 256, 0, s>>>(static_cast<float*>(dst), static_cast<const float*>(src),
+                                                static_cast<const float*>(defer), L.n, L.k, co);
+  MFNS_CUDA(cudaGetLastError());
 }
 
 void op_apply_cleared(const OpLaunch& L, int prec, const void* src, void* dst, int64_t n, cudaStream_t s,

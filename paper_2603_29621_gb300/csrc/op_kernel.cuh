@@ -107,6 +107,11 @@ struct OpArgs {
   const int32_t* block_pid;
   // device word in which a bounded wait that ran out sets bit 0 (or null)
   int* err;
+  // deferred product of a uniform level (one launch over every colour, blockIdx.y = colour): each
+  // cell's contributions go to defer[(cell position * nodes per cell + slot) * NU + f]; the cells of
+  // colour c start at cell position defer_off[c]
+  T* defer;
+  int64_t defer_off[8];
 };
 
 // ------------------------------------------------------------ small helpers

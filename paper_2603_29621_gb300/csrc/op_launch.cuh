@@ -48,16 +48,12 @@ static void launch_op(Kern kern, dim3 grid, unsigned block, size_t smem, cudaStr
   MFNS_CUDA(cudaLaunchKernelEx(&cfg, kern, a));
 }
 
-template <int DIM, int K, int OP, typename T>
-void op_launch(const OpLaunch& L, const T* src, T* dst, bool diag, cudaStream_t s, int fq_mode, int ncols,
-               int64_t col_stride, const OpEpilogue* epi) {
-  constexpr int Q = K + 1, N = K + 1, NP = OP == OP_STOKES ? K : K + 1;
-  OpArgs<T, Q, N, NP> a{};
+// The kernel arguments every launch of L shares: tables, mesh tables, physics.
+template <typename T, int Q, int N, int NP>
+static void fill_common(const OpLaunch& L, OpArgs<T, Q, N, NP>& a) {
   if (L.Q != Q || L.N != N || L.NP != NP) throw Error(kErrArg, "operator tables do not match the degree");
   build_tables(L, a.tab);
   const int prec = sizeof(T) == 8 ? 0 : 1;
-  a.src = src;
-  a.dst = dst;
   a.frozen = reinterpret_cast<const T*>(L.frozen[prec]);
   a.cell_u = L.cell_u;
   a.cell_p = L.cell_p;
@@ -73,8 +69,21 @@ void op_launch(const OpLaunch& L, const T* src, T* dst, bool diag, cudaStream_t 
   a.cm = (T)(L.alpha * dt_inv);
   a.div_sign = (T)L.div_sign;
   for (int b = 0; b < 7; ++b) a.cf[b] = (L.terms >> b) & 1 ? T(1) : T(0);
-  a.diag = diag;
   a.err = op_wait_flag();
+  a.fq = reinterpret_cast<T*>(L.fq[prec]);
+  a.gexp = reinterpret_cast<const T*>(L.gexp[prec]);
+}
+
+template <int DIM, int K, int OP, typename T>
+void op_launch(const OpLaunch& L, const T* src, T* dst, bool diag, cudaStream_t s, int fq_mode, int ncols,
+               int64_t col_stride, const OpEpilogue* epi) {
+  constexpr int Q = K + 1, N = K + 1, NP = OP == OP_STOKES ? K : K + 1;
+  OpArgs<T, Q, N, NP> a{};
+  fill_common(L, a);
+  const int prec = sizeof(T) == 8 ? 0 : 1;
+  a.src = src;
+  a.dst = dst;
+  a.diag = diag;
   if (ncols < 1 || (ncols > 1 && (diag || fq_mode == 2 || fq_mode == 3)))
     throw Error(kErrArg, "several columns only for operator applications");
   a.col_stride = ncols > 1 ? col_stride : 0;
@@ -95,8 +104,6 @@ void op_launch(const OpLaunch& L, const T* src, T* dst, bool diag, cudaStream_t 
     a.ec2 = (T)epi->c2;
   }
   // frozen state: -1 = use the precomputed point data when present; 2 = write it (set-up pass)
-  a.fq = reinterpret_cast<T*>(L.fq[prec]);
-  a.gexp = reinterpret_cast<const T*>(L.gexp[prec]);
   // 3 = residual pass: the state is read from the frozen buffer (src unused, pointed there)
   const int fq = OP != OP_STAB_NS ? 0 : (fq_mode == 2 || fq_mode == 3) ? fq_mode : (a.fq ? 1 : 0);
   if (fq == 3 && diag) throw Error(kErrArg, "residual pass in diagonal mode");
@@ -213,6 +220,53 @@ void op_launch(const OpLaunch& L, const T* src, T* dst, bool diag, cudaStream_t 
   }
 }
 
+// Deferred product of a uniform 3D stabilised level: one launch over every colour (blockIdx.y =
+// colour) writing each cell's contributions to `defer`; k_gather_cells forms dst from them.
+template <int DIM, int K, int OP, typename T>
+void op_launch_deferred(const OpLaunch& L, const T* src, T* defer, cudaStream_t s) {
+  if constexpr (!(DIM == 3 && OP == OP_STAB_NS)) {
+    throw Error(kErrUnsupported, "deferred products: 3D stabilised levels only");
+  } else {
+    constexpr int Q = K + 1, N = K + 1, NP = K + 1;
+    if (!L.structured || L.n_colors != 8) throw Error(kErrArg, "deferred products: uniform levels only");
+    OpArgs<T, Q, N, NP> a{};
+    fill_common(L, a);
+    a.src = src;
+    a.defer = defer;
+    using TM = Team<DIM, Q>;
+    const int prec = sizeof(T) == 8 ? 0 : 1;
+    const int warps = L.warps[prec] > 0 ? L.warps[prec] : kOpWarps;
+    const int cells_per_block = warps * TM::CPW;
+    int64_t off = 0, maxc = 0;
+    for (int c = 0; c < 8; ++c) {
+      int64_t nc = 1;
+      for (int d = 0; d < DIM; ++d) nc *= (L.n - ((c >> d) & 1) + 1) / 2;
+      a.defer_off[c] = off;
+      off += nc;
+      maxc = std::max(maxc, nc);
+    }
+    const dim3 grid((unsigned)((maxc + cells_per_block - 1) / cells_per_block), 8u);
+    if (a.fq) {
+      const size_t sm = op_smem_bytes<DIM, K, OP, T>(warps, true);
+      auto kern = op_kernel<DIM, K, OP, T, true, false, 1, false, false, true>;
+      static std::atomic<uint64_t> attr_done{0};  // per device, for the largest block size
+      int dev = 0;
+      MFNS_CUDA(cudaGetDevice(&dev));
+      const uint64_t bit = 1ull << (dev & 63);
+      if (!(attr_done.load() & bit)) {
+        MFNS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)op_smem_bytes<DIM, K, OP, T>(kOpWarps, true)));
+        attr_done.fetch_or(bit);
+      }
+      kern<<<grid, warps * 32, sm, s>>>(a);
+    } else {
+      op_kernel<DIM, K, OP, T, true, false, 0, false, false, true>
+          <<<grid, warps * 32, op_smem_bytes<DIM, K, OP, T>(warps, false), s>>>(a);
+    }
+    MFNS_CUDA(cudaGetLastError());
+  }
+}
+
 template <int DIM, int K, int OP, typename T>
 void op_launch_multi(const OpLaunch& L, int color, const MultiColour& mc, cudaStream_t s) {
   constexpr int Q = K + 1, N = K + 1, NP = OP == OP_STOKES ? K : K + 1;
@@ -256,6 +310,10 @@ void op_launch_multi(const OpLaunch& L, int color, const MultiColour& mc, cudaSt
   }
 }
 
+#define MFNS_INSTANTIATE_DEFERRED(DIM, K, OP)                                                                  \
+  template void op_launch_deferred<DIM, K, OP, double>(const OpLaunch&, const double*, double*, cudaStream_t);    \
+  template void op_launch_deferred<DIM, K, OP, float>(const OpLaunch&, const float*, float*, cudaStream_t);
+
 #define MFNS_INSTANTIATE_OP(DIM, K, OP)                                                                        \
   template void op_launch<DIM, K, OP, double>(const OpLaunch&, const double*, double*, bool, cudaStream_t, int, int, \
                                                int64_t, const OpEpilogue*);                                        \
@@ -265,3 +323,4 @@ void op_launch_multi(const OpLaunch& L, int color, const MultiColour& mc, cudaSt
   template void op_launch_multi<DIM, K, OP, float>(const OpLaunch&, int, const MultiColour&, cudaStream_t);
 
 }  // namespace mfns
+

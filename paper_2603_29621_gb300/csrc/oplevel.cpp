@@ -10,6 +10,12 @@
 
 namespace mfns {
 
+// uniform 3D stabilised levels of at most this many cells take deferred products
+#ifndef MFNS_DEFER_MAX_CELLS
+#define MFNS_DEFER_MAX_CELLS 4096
+#endif
+constexpr int64_t kDeferMaxCells = MFNS_DEFER_MAX_CELLS;
+
 size_t OpLevel::bytes() const {
   size_t b = fq[0].bytes() + fq[1].bytes() + cell_u.bytes() + cell_p.bytes() + cell_f.bytes() + mask.bytes() + constrained.bytes() +
              hang_dof.bytes() + hang_ptr.bytes() + hang_src.bytes() + pres.bytes() + tnodes.bytes() +
@@ -246,6 +252,12 @@ void build_oplevel(OpLevel& lv, const Forest& f, int op, int k, const Physics& p
     for (int32_t i : lv.constrained_host) km[(size_t)i >> 5] |= 1u << (i & 31);
     lv.keep_mask = upload(bud, km);
   }
+  // small uniform 3D stabilised levels: products as one launch over all colours plus a gather pass
+  // (their eight colour launches are latency, not work)
+  if (lv.L.structured && op == OP_STAB_NS && dim == 3 && (int64_t)lv.L.n_cells <= kDeferMaxCells) {
+    const size_t entries = (size_t)lv.L.n_cells * (size_t)((k + 1) * (k + 1) * (k + 1)) * 4;
+    for (int prec = 0; prec < 2; ++prec) lv.defer[prec].alloc(bud, entries * esize(prec));
+  }
   lv.n_hang = (int64_t)hd.size();
   lv.hang_dof = upload(bud, hd);
   lv.hang_ptr = upload(bud, hp);
@@ -260,6 +272,10 @@ void oplevel_vmult(const OpLevel& lv, int prec, const void* src, void* dst, cuda
   if (lv.hp) return hp_vmult(lv, prec, src, dst, s);
   // clearing kernel, then the colour launches (each may start before its predecessor drains);
   // on uniform meshes the clearing kernel also writes the identity rows, which no colour touches
+  if (lv.defer[prec].get()) {  // small uniform levels: one launch over all colours, one gather pass
+    op_apply_deferred(lv.L, prec, src, dst, lv.defer[prec].get(), s);
+    return;
+  }
   if (lv.keep_mask.get()) {
     op_apply_cleared(lv.L, prec, src, dst, lv.n_dofs, s, lv.keep_mask.as<uint32_t>());
     return;

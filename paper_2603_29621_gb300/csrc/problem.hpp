@@ -38,6 +38,7 @@ struct OpLevel {
   std::vector<int32_t> constrained_host;
   DevBuf constrained;                   // identity rows
   DevBuf keep_mask;                     // uniform meshes: bitmask of the identity rows (see oplevel_vmult)
+  DevBuf defer[2];                      // small uniform 3D stabilised levels: per-cell contributions (FP64 / FP32)
   int64_t n_hang = 0;
   DevBuf hang_dof, hang_ptr, hang_src, hang_w[2];
   std::vector<int32_t> pres_host;
