@@ -4,6 +4,7 @@
 #include <mutex>
 #include <string>
 #include <tuple>
+#include <type_traits>
 
 #include "mesh.hpp"
 #include "op_kernel.cuh"
@@ -33,11 +34,12 @@ MFNS_DECL(3, 1, OP_PMASS) MFNS_DECL(3, 2, OP_PMASS) MFNS_DECL(3, 3, OP_PMASS)
 MFNS_DECL(2, 2, OP_VMASS) MFNS_DECL(2, 3, OP_VMASS) MFNS_DECL(2, 4, OP_VMASS)
 MFNS_DECL(3, 2, OP_VMASS) MFNS_DECL(3, 3, OP_VMASS) MFNS_DECL(3, 4, OP_VMASS)
 
-#define MFNS_DECL_DEFER(K)                                                                                   \
-  extern template void op_launch_deferred<3, K, OP_STAB_NS, double>(const OpLaunch&, const double*, double*,      \
-                                                                     cudaStream_t);                                 \
-  extern template void op_launch_deferred<3, K, OP_STAB_NS, float>(const OpLaunch&, const float*, float*, cudaStream_t);
-MFNS_DECL_DEFER(1) MFNS_DECL_DEFER(2) MFNS_DECL_DEFER(3)
+#define MFNS_DECL_DEFER(K, OP)                                                                                  \
+  extern template void op_launch_deferred<3, K, OP, double>(const OpLaunch&, const double*, double*, cudaStream_t); \
+  extern template void op_launch_deferred<3, K, OP, float>(const OpLaunch&, const float*, float*, cudaStream_t);
+MFNS_DECL_DEFER(1, OP_STAB_NS) MFNS_DECL_DEFER(2, OP_STAB_NS) MFNS_DECL_DEFER(3, OP_STAB_NS)
+MFNS_DECL_DEFER(1, OP_STOKES_A) MFNS_DECL_DEFER(2, OP_STOKES_A) MFNS_DECL_DEFER(3, OP_STOKES_A)
+MFNS_DECL_DEFER(4, OP_STOKES_A)
 #undef MFNS_DECL_DEFER
 
 bool op_supported(int dim, int k, int op) {
@@ -278,21 +280,23 @@ __device__ __forceinline__ float add_as_reduction(float a, float b) {
 }
 __device__ __forceinline__ double add_as_reduction(double a, double b) { return a + b; }
 
-// dst = A src on a uniform 3D stabilised level from the per-cell contributions of a deferred
-// product: every node adds its cells' contributions in colour order, starting from zero -- the
-// additions, in the same order, that the colour launches' reductions make onto a cleared vector --
-// and the identity rows (velocity of boundary nodes) get src + 0 (src plus the zeros the colours
-// add there).  Node (i0, i1, i2) of the (k n + 1)^3 lattice lies in one cell along a direction where
-// i_d is not a multiple of k, else in the cells i_d / k - 1 and i_d / k that exist; the colour of a
-// cell is the parity of its coordinates.
-template <typename T>
+// dst = A src on a uniform 3D level (NU components per node, the first three velocity) from the
+// per-cell contributions of a deferred product: every node adds its cells' contributions in colour
+// order, starting from zero -- the additions, in the same order, that the colour launches'
+// reductions make onto a cleared vector -- and the identity rows (velocity of boundary nodes) get
+// src + 0 (src plus the zeros the colours add there).  Node (i0, i1, i2) of the (k n + 1)^3 lattice
+// lies in one cell along a direction where i_d is not a multiple of k, else in the cells i_d / k - 1
+// and i_d / k that exist; the colour of a cell is the parity of its coordinates.
+template <typename T, int NU>
 __global__ void k_gather_cells(T* __restrict__ dst, const T* __restrict__ src, const T* __restrict__ defer, int n,
                                int K, ColourOffsets co) {
   const int64_t M = (int64_t)K * n + 1, nn = M * M * M;
   const int nb1 = K + 1, nbc = nb1 * nb1 * nb1;
   for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < nn; g += (int64_t)gridDim.x * blockDim.x) {
     const int64_t i[3] = {g % M, (g / M) % M, g / (M * M)};
-    T acc[4] = {T(0), T(0), T(0), T(0)};
+    T acc[NU];
+#pragma unroll
+    for (int f = 0; f < NU; ++f) acc[f] = T(0);
     for (int c = 0; c < 8; ++c) {
       int64_t cd[3];
       int loc[3];
@@ -320,27 +324,30 @@ __global__ void k_gather_cells(T* __restrict__ dst, const T* __restrict__ src, c
       const int64_t m0 = (n - (c & 1) + 1) / 2, m1 = (n - ((c >> 1) & 1) + 1) / 2;
       const int64_t pos = co.off[c] + (cd[0] >> 1) + m0 * ((cd[1] >> 1) + m1 * (cd[2] >> 1));
       const int slot = (loc[2] * nb1 + loc[1]) * nb1 + loc[0];
-      const T* v = defer + ((size_t)pos * nbc + slot) * 4;
+      const T* v = defer + ((size_t)pos * nbc + slot) * NU;
 #pragma unroll
-      for (int f = 0; f < 4; ++f) acc[f] = add_as_reduction(acc[f], v[f]);
+      for (int f = 0; f < NU; ++f) acc[f] = add_as_reduction(acc[f], v[f]);
     }
     const bool bnd = i[0] == 0 || i[0] == M - 1 || i[1] == 0 || i[1] == M - 1 || i[2] == 0 || i[2] == M - 1;
 #pragma unroll
-    for (int f = 0; f < 3; ++f) dst[g * 4 + f] = bnd ? add_as_reduction(src[g * 4 + f], T(0)) : acc[f];
-    dst[g * 4 + 3] = acc[3];
+    for (int f = 0; f < NU; ++f)
+      dst[g * NU + f] = (f < 3 && bnd) ? add_as_reduction(src[g * NU + f], T(0)) : acc[f];
   }
 }
 
 void op_apply_deferred(const OpLaunch& L, int prec, const void* src, void* dst, void* defer, cudaStream_t s) {
-  if (L.dim != 3 || L.op != OP_STAB_NS || !L.structured) throw Error(kErrArg, "deferred products: uniform 3D stabilised levels");
-#define MFNS_CASE(K)                                                                                          \
-  if (L.k == K) {                                                                                             \
+  if (L.dim != 3 || (L.op != OP_STAB_NS && L.op != OP_STOKES_A) || !L.structured)
+    throw Error(kErrArg, "deferred products: uniform 3D stabilised or vector-Laplacian levels");
+#define MFNS_CASE(K, OP)                                                                                      \
+  if (L.k == K && L.op == OP) {                                                                               \
     if (prec == 0)                                                                                            \
-      op_launch_deferred<3, K, OP_STAB_NS, double>(L, static_cast<const double*>(src), static_cast<double*>(defer), s); \
+      op_launch_deferred<3, K, OP, double>(L, static_cast<const double*>(src), static_cast<double*>(defer), s); \
     else                                                                                                      \
-      op_launch_deferred<3, K, OP_STAB_NS, float>(L, static_cast<const float*>(src), static_cast<float*>(defer), s);    \
+      op_launch_deferred<3, K, OP, float>(L, static_cast<const float*>(src), static_cast<float*>(defer), s);    \
   } else
-  MFNS_CASE(1) MFNS_CASE(2) MFNS_CASE(3) throw Error(kErrUnsupported, "deferred products: degree");
+  MFNS_CASE(1, OP_STAB_NS) MFNS_CASE(2, OP_STAB_NS) MFNS_CASE(3, OP_STAB_NS)
+  MFNS_CASE(1, OP_STOKES_A) MFNS_CASE(2, OP_STOKES_A) MFNS_CASE(3, OP_STOKES_A) MFNS_CASE(4, OP_STOKES_A)
+  throw Error(kErrUnsupported, "deferred products: degree");
 #undef MFNS_CASE
   ColourOffsets co{};
   int64_t off = 0;
@@ -352,12 +359,19 @@ void op_apply_deferred(const OpLaunch& L, int prec, const void* src, void* dst, 
   }
   const int64_t M = (int64_t)L.k * L.n + 1, nn = M * M * M;
   const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>((nn + 255) / 256, 152 * 16));
-  if (prec == 0)
-    k_gather_cells<double><<<grid, 256, 0, s>>>(static_cast<double*>(dst), static_cast<const double*>(src),
-                                                 static_cast<const double*>(defer), L.n, L.k, co);
-  else
-    k_gather_cells<float><<<grid, 256, 0, s>>>(static_cast<float*>(dst), static_cast<const float*>(src),
-                                                static_cast<const float*>(defer), L.n, L.k, co);
+  auto go = [&](auto tag, auto nu_tag) {
+    using T = decltype(tag);
+    constexpr int NU = decltype(nu_tag)::value;
+    k_gather_cells<T, NU><<<grid, 256, 0, s>>>(static_cast<T*>(dst), static_cast<const T*>(src),
+                                               static_cast<const T*>(defer), L.n, L.k, co);
+  };
+  if (L.op == OP_STAB_NS) {
+    if (prec == 0) go(double(), std::integral_constant<int, 4>());
+    else go(float(), std::integral_constant<int, 4>());
+  } else {
+    if (prec == 0) go(double(), std::integral_constant<int, 3>());
+    else go(float(), std::integral_constant<int, 3>());
+  }
   MFNS_CUDA(cudaGetLastError());
 }
 

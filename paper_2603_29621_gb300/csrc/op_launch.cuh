@@ -224,8 +224,8 @@ void op_launch(const OpLaunch& L, const T* src, T* dst, bool diag, cudaStream_t 
 // colour) writing each cell's contributions to `defer`; k_gather_cells forms dst from them.
 template <int DIM, int K, int OP, typename T>
 void op_launch_deferred(const OpLaunch& L, const T* src, T* defer, cudaStream_t s) {
-  if constexpr (!(DIM == 3 && OP == OP_STAB_NS)) {
-    throw Error(kErrUnsupported, "deferred products: 3D stabilised levels only");
+  if constexpr (!(DIM == 3 && (OP == OP_STAB_NS || OP == OP_STOKES_A))) {
+    throw Error(kErrUnsupported, "deferred products: 3D stabilised or vector-Laplacian levels only");
   } else {
     constexpr int Q = K + 1, N = K + 1, NP = K + 1;
     if (!L.structured || L.n_colors != 8) throw Error(kErrArg, "deferred products: uniform levels only");
@@ -246,23 +246,26 @@ void op_launch_deferred(const OpLaunch& L, const T* src, T* defer, cudaStream_t 
       maxc = std::max(maxc, nc);
     }
     const dim3 grid((unsigned)((maxc + cells_per_block - 1) / cells_per_block), 8u);
-    if (a.fq) {
-      const size_t sm = op_smem_bytes<DIM, K, OP, T>(warps, true);
-      auto kern = op_kernel<DIM, K, OP, T, true, false, 1, false, false, true>;
-      static std::atomic<uint64_t> attr_done{0};  // per device, for the largest block size
-      int dev = 0;
-      MFNS_CUDA(cudaGetDevice(&dev));
-      const uint64_t bit = 1ull << (dev & 63);
-      if (!(attr_done.load() & bit)) {
-        MFNS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)op_smem_bytes<DIM, K, OP, T>(kOpWarps, true)));
-        attr_done.fetch_or(bit);
+    if constexpr (OP == OP_STAB_NS) {
+      if (a.fq) {  // the precomputed frozen point data, staged per cell
+        const size_t sm = op_smem_bytes<DIM, K, OP, T>(warps, true);
+        auto kern = op_kernel<DIM, K, OP, T, true, false, 1, false, false, true>;
+        static std::atomic<uint64_t> attr_done{0};  // per device, for the largest block size
+        int dev = 0;
+        MFNS_CUDA(cudaGetDevice(&dev));
+        const uint64_t bit = 1ull << (dev & 63);
+        if (!(attr_done.load() & bit)) {
+          MFNS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)op_smem_bytes<DIM, K, OP, T>(kOpWarps, true)));
+          attr_done.fetch_or(bit);
+        }
+        kern<<<grid, warps * 32, sm, s>>>(a);
+        MFNS_CUDA(cudaGetLastError());
+        return;
       }
-      kern<<<grid, warps * 32, sm, s>>>(a);
-    } else {
-      op_kernel<DIM, K, OP, T, true, false, 0, false, false, true>
-          <<<grid, warps * 32, op_smem_bytes<DIM, K, OP, T>(warps, false), s>>>(a);
     }
+    op_kernel<DIM, K, OP, T, true, false, 0, false, false, true>
+        <<<grid, warps * 32, op_smem_bytes<DIM, K, OP, T>(warps, false), s>>>(a);
     MFNS_CUDA(cudaGetLastError());
   }
 }

@@ -66,7 +66,7 @@ def _check(n, K, warps=4, CPW=3):
         assert set(cells) == brute and len(cells) == len(brute), (n, K, i)
 
 
-@pytest.mark.parametrize("K", [1, 2, 3])
+@pytest.mark.parametrize("K", [1, 2, 3, 4])
 @pytest.mark.parametrize("n", [1, 2, 3, 4, 5, 7])
 def test_deferred_launch_and_gather_indexing(n, K):
     _check(n, K)
