@@ -40,6 +40,7 @@ MFNS_DECL(3, 2, OP_VMASS) MFNS_DECL(3, 3, OP_VMASS) MFNS_DECL(3, 4, OP_VMASS)
 MFNS_DECL_DEFER(1, OP_STAB_NS) MFNS_DECL_DEFER(2, OP_STAB_NS) MFNS_DECL_DEFER(3, OP_STAB_NS)
 MFNS_DECL_DEFER(1, OP_STOKES_A) MFNS_DECL_DEFER(2, OP_STOKES_A) MFNS_DECL_DEFER(3, OP_STOKES_A)
 MFNS_DECL_DEFER(4, OP_STOKES_A)
+MFNS_DECL_DEFER(1, OP_PMASS) MFNS_DECL_DEFER(2, OP_PMASS) MFNS_DECL_DEFER(3, OP_PMASS)
 #undef MFNS_DECL_DEFER
 
 bool op_supported(int dim, int k, int op) {
@@ -280,14 +281,14 @@ __device__ __forceinline__ float add_as_reduction(float a, float b) {
 }
 __device__ __forceinline__ double add_as_reduction(double a, double b) { return a + b; }
 
-// dst = A src on a uniform 3D level (NU components per node, the first three velocity) from the
+// dst = A src on a uniform 3D level (NU components per node, the first NVEL velocity) from the
 // per-cell contributions of a deferred product: every node adds its cells' contributions in colour
 // order, starting from zero -- the additions, in the same order, that the colour launches'
 // reductions make onto a cleared vector -- and the identity rows (velocity of boundary nodes) get
 // src + 0 (src plus the zeros the colours add there).  Node (i0, i1, i2) of the (k n + 1)^3 lattice
 // lies in one cell along a direction where i_d is not a multiple of k, else in the cells i_d / k - 1
 // and i_d / k that exist; the colour of a cell is the parity of its coordinates.
-template <typename T, int NU>
+template <typename T, int NU, int NVEL>
 __global__ void k_gather_cells(T* __restrict__ dst, const T* __restrict__ src, const T* __restrict__ defer, int n,
                                int K, ColourOffsets co) {
   const int64_t M = (int64_t)K * n + 1, nn = M * M * M;
@@ -331,13 +332,13 @@ __global__ void k_gather_cells(T* __restrict__ dst, const T* __restrict__ src, c
     const bool bnd = i[0] == 0 || i[0] == M - 1 || i[1] == 0 || i[1] == M - 1 || i[2] == 0 || i[2] == M - 1;
 #pragma unroll
     for (int f = 0; f < NU; ++f)
-      dst[g * NU + f] = (f < 3 && bnd) ? add_as_reduction(src[g * NU + f], T(0)) : acc[f];
+      dst[g * NU + f] = (f < NVEL && bnd) ? add_as_reduction(src[g * NU + f], T(0)) : acc[f];
   }
 }
 
 void op_apply_deferred(const OpLaunch& L, int prec, const void* src, void* dst, void* defer, cudaStream_t s) {
-  if (L.dim != 3 || (L.op != OP_STAB_NS && L.op != OP_STOKES_A) || !L.structured)
-    throw Error(kErrArg, "deferred products: uniform 3D stabilised or vector-Laplacian levels");
+  if (L.dim != 3 || (L.op != OP_STAB_NS && L.op != OP_STOKES_A && L.op != OP_PMASS) || !L.structured)
+    throw Error(kErrArg, "deferred products: uniform 3D stabilised, vector-Laplacian or pressure-mass levels");
 #define MFNS_CASE(K, OP)                                                                                      \
   if (L.k == K && L.op == OP) {                                                                               \
     if (prec == 0)                                                                                            \
@@ -347,6 +348,7 @@ void op_apply_deferred(const OpLaunch& L, int prec, const void* src, void* dst, 
   } else
   MFNS_CASE(1, OP_STAB_NS) MFNS_CASE(2, OP_STAB_NS) MFNS_CASE(3, OP_STAB_NS)
   MFNS_CASE(1, OP_STOKES_A) MFNS_CASE(2, OP_STOKES_A) MFNS_CASE(3, OP_STOKES_A) MFNS_CASE(4, OP_STOKES_A)
+  MFNS_CASE(1, OP_PMASS) MFNS_CASE(2, OP_PMASS) MFNS_CASE(3, OP_PMASS)
   throw Error(kErrUnsupported, "deferred products: degree");
 #undef MFNS_CASE
   ColourOffsets co{};
@@ -359,18 +361,25 @@ void op_apply_deferred(const OpLaunch& L, int prec, const void* src, void* dst, 
   }
   const int64_t M = (int64_t)L.k * L.n + 1, nn = M * M * M;
   const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>((nn + 255) / 256, 152 * 16));
-  auto go = [&](auto tag, auto nu_tag) {
+  auto go = [&](auto tag, auto nu_tag, auto nvel_tag) {
     using T = decltype(tag);
-    constexpr int NU = decltype(nu_tag)::value;
-    k_gather_cells<T, NU><<<grid, 256, 0, s>>>(static_cast<T*>(dst), static_cast<const T*>(src),
-                                               static_cast<const T*>(defer), L.n, L.k, co);
+    constexpr int NU = decltype(nu_tag)::value, NVEL = decltype(nvel_tag)::value;
+    k_gather_cells<T, NU, NVEL><<<grid, 256, 0, s>>>(static_cast<T*>(dst), static_cast<const T*>(src),
+                                                     static_cast<const T*>(defer), L.n, L.k, co);
   };
+  using I0 = std::integral_constant<int, 0>;
+  using I1 = std::integral_constant<int, 1>;
+  using I3 = std::integral_constant<int, 3>;
+  using I4 = std::integral_constant<int, 4>;
   if (L.op == OP_STAB_NS) {
-    if (prec == 0) go(double(), std::integral_constant<int, 4>());
-    else go(float(), std::integral_constant<int, 4>());
-  } else {
-    if (prec == 0) go(double(), std::integral_constant<int, 3>());
-    else go(float(), std::integral_constant<int, 3>());
+    if (prec == 0) go(double(), I4(), I3());
+    else go(float(), I4(), I3());
+  } else if (L.op == OP_STOKES_A) {
+    if (prec == 0) go(double(), I3(), I3());
+    else go(float(), I3(), I3());
+  } else {  // pressure mass: one field, no identity rows
+    if (prec == 0) go(double(), I1(), I0());
+    else go(float(), I1(), I0());
   }
   MFNS_CUDA(cudaGetLastError());
 }

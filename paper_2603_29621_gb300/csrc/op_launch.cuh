@@ -224,8 +224,8 @@ void op_launch(const OpLaunch& L, const T* src, T* dst, bool diag, cudaStream_t 
 // colour) writing each cell's contributions to `defer`; k_gather_cells forms dst from them.
 template <int DIM, int K, int OP, typename T>
 void op_launch_deferred(const OpLaunch& L, const T* src, T* defer, cudaStream_t s) {
-  if constexpr (!(DIM == 3 && (OP == OP_STAB_NS || OP == OP_STOKES_A))) {
-    throw Error(kErrUnsupported, "deferred products: 3D stabilised or vector-Laplacian levels only");
+  if constexpr (!(DIM == 3 && (OP == OP_STAB_NS || OP == OP_STOKES_A || OP == OP_PMASS))) {
+    throw Error(kErrUnsupported, "deferred products: 3D stabilised, vector-Laplacian or pressure-mass levels only");
   } else {
     constexpr int Q = K + 1, N = K + 1, NP = K + 1;
     if (!L.structured || L.n_colors != 8) throw Error(kErrArg, "deferred products: uniform levels only");

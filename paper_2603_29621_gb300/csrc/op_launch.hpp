@@ -103,8 +103,8 @@ struct MultiColour {
 template <int DIM, int K, int OP, typename T>
 void op_launch_multi(const OpLaunch& L, int color, const MultiColour& mc, cudaStream_t s);
 
-// Deferred product of a uniform 3D stabilised or vector-Laplacian level (small levels, where the
-// eight colour launches are latency, not work): one launch over every colour writes each cell's
+// Deferred product of a uniform 3D stabilised, vector-Laplacian or pressure-mass level (small
+// levels, where the eight colour launches are latency, not work): one launch over every colour writes each cell's
 // contributions to `defer` (n_cells * (k+1)^3 * NU entries of the precision), then one gather pass
 // forms dst = A src, every node summing its cells' contributions in colour order -- the additions
 // and the order of the colour-ordered scatter onto a cleared vector, so the result is the same bit

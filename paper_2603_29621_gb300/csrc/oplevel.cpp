@@ -10,7 +10,8 @@
 
 namespace mfns {
 
-// uniform 3D stabilised / vector-Laplacian levels of at most this many cells take deferred products
+// uniform 3D stabilised / vector-Laplacian / pressure-mass levels of at most this many cells take
+// deferred products
 #ifndef MFNS_DEFER_MAX_CELLS
 #define MFNS_DEFER_MAX_CELLS 4096
 #endif
@@ -252,9 +253,9 @@ void build_oplevel(OpLevel& lv, const Forest& f, int op, int k, const Physics& p
     for (int32_t i : lv.constrained_host) km[(size_t)i >> 5] |= 1u << (i & 31);
     lv.keep_mask = upload(bud, km);
   }
-  // small uniform 3D stabilised and vector-Laplacian levels: products as one launch over all
-  // colours plus a gather pass (their eight colour launches are latency, not work)
-  if (lv.L.structured && (op == OP_STAB_NS || op == OP_STOKES_A) && dim == 3 &&
+  // small uniform 3D stabilised, vector-Laplacian and pressure-mass levels: products as one launch
+  // over all colours plus a gather pass (their eight colour launches are latency, not work)
+  if (lv.L.structured && (op == OP_STAB_NS || op == OP_STOKES_A || op == OP_PMASS) && dim == 3 &&
       (int64_t)lv.L.n_cells <= kDeferMaxCells) {
     const size_t entries = (size_t)lv.L.n_cells * (size_t)((k + 1) * (k + 1) * (k + 1)) * lv.NU;
     for (int prec = 0; prec < 2; ++prec) lv.defer[prec].alloc(bud, entries * esize(prec));
