@@ -586,63 +586,4 @@ int hp_color_cells(const HpSpace& sp, const std::vector<int32_t>& cells, std::ve
   return ncol;
 }
 
-int hp_probe_groups(const HpSpace& sp, const std::vector<char>& free_node, std::vector<int32_t>& group,
-                    bool dirichlet) {
-  const int64_t nn = sp.n_nodes;
-  const size_t nc = sp.cell_ptr.size() - 1;
-  // free masters reached by every node: itself when free, its free masters when constrained
-  std::vector<int64_t> mptr(nn + 1, 0);
-  std::vector<int32_t> hrow(nn, -1);
-  for (size_t i = 0; i < sp.hang_node.size(); ++i) hrow[sp.hang_node[i]] = (int32_t)i;
-  auto for_masters = [&](int32_t g, auto&& fn) {
-    if (free_node[g]) {
-      fn(g);
-    } else if (hrow[g] >= 0 && !(dirichlet && sp.boundary[g])) {  // Dirichlet entries do not couple
-      for (int32_t j = sp.hang_ptr[hrow[g]]; j < sp.hang_ptr[hrow[g] + 1]; ++j)
-        if (free_node[sp.hang_master[j]]) fn(sp.hang_master[j]);
-    }
-  };
-  // cell -> its free masters (compressed, duplicates removed)
-  std::vector<int64_t> cptr(nc + 1, 0);
-  std::vector<int32_t> cidx;
-  for (size_t c = 0; c < nc; ++c) {
-    const size_t start = cidx.size();
-    for (int64_t j = sp.cell_ptr[c]; j < sp.cell_ptr[c + 1]; ++j) for_masters(sp.cell_nodes[j], [&](int32_t m) { cidx.push_back(m); });
-    std::sort(cidx.begin() + start, cidx.end());
-    cidx.erase(std::unique(cidx.begin() + start, cidx.end()), cidx.end());
-    cptr[c + 1] = (int64_t)cidx.size();
-  }
-  // master -> cells (compressed)
-  std::vector<int64_t> optr(nn + 1, 0);
-  for (int32_t m : cidx) optr[m + 1]++;
-  for (int64_t g = 0; g < nn; ++g) optr[g + 1] += optr[g];
-  std::vector<int32_t> oidx(optr[nn]);
-  {
-    std::vector<int64_t> fill(optr.begin(), optr.end() - 1);
-    for (size_t c = 0; c < nc; ++c)
-      for (int64_t q = cptr[c]; q < cptr[c + 1]; ++q) oidx[fill[cidx[q]]++] = (int32_t)c;
-  }
-  group.assign(nn, -1);
-  std::vector<int64_t> stamp;
-  int ng = 0;
-  for (int64_t m = 0; m < nn; ++m) {
-    if (!free_node[m]) continue;
-    for (int64_t q = optr[m]; q < optr[m + 1]; ++q) {
-      const int32_t c = oidx[q];
-      for (int64_t r = cptr[c]; r < cptr[c + 1]; ++r) {
-        const int32_t o = group[cidx[r]];
-        if (o >= 0) {
-          if ((size_t)o >= stamp.size()) stamp.resize(o + 1, -1);
-          stamp[o] = m;
-        }
-      }
-    }
-    int col = 0;
-    while ((size_t)col < stamp.size() && stamp[col] == m) ++col;
-    group[m] = col;
-    ng = std::max(ng, col + 1);
-  }
-  return ng;
-}
-
 }  // namespace mfns

@@ -54,15 +54,6 @@ bool make_hp_space(const Forest& f, const std::vector<int32_t>& degree, HpSpace&
 // colour of cells[i]; returns the number of colours.
 int hp_color_cells(const HpSpace& sp, const std::vector<int32_t>& cells, std::vector<int32_t>& color);
 
-// Groups of free nodes for probing the diagonal of C^T K C: two free nodes share a group only if no
-// cell holds a node whose free masters include both (a free node is its own master).  `free_node`
-// marks the free nodes; masters of constrained nodes are hang_master entries that are free.  With
-// `dirichlet` boundary nodes are zero and couple nothing; without it (a field with no boundary
-// condition) a constrained boundary node couples its masters like any other.
-// group[g] is the group of free node g (-1 otherwise); returns the number of groups.
-int hp_probe_groups(const HpSpace& sp, const std::vector<char>& free_node, std::vector<int32_t>& group,
-                    bool dirichlet = true);
-
 // Blocks of the additive Schwarz part of Section 3's blended smoother: for every combined h+p face
 // (a cell face whose neighbours across it are finer and of lower degree), the free nodes (not
 // constrained, not on the Dirichlet boundary) lying on the closed face of the coarse cell, each with

@@ -46,8 +46,7 @@ int main() {
     for (int d = 0; d < dim; ++d) std::printf("%.17g ", sp.x[g * dim + d]);
     std::printf("%d\n", (int)sp.boundary[g]);
   }
-  // colourings: cells of each degree (no shared node within a colour) and probing groups (no cell
-  // reaching two free nodes of a group), checked by brute force
+  // colourings: cells of each degree (no shared node within a colour), checked by brute force
   {
     int kmax = 0;
     for (int32_t k : deg) kmax = std::max(kmax, k);
@@ -67,30 +66,6 @@ int main() {
           return 0;
         }
     }
-    std::vector<char> freen(sp.n_nodes, 1), hang(sp.n_nodes, 0);
-    for (int32_t g : sp.hang_node) hang[g] = 1;
-    for (int64_t g = 0; g < sp.n_nodes; ++g) freen[g] = !(dbc && sp.boundary[g]) && !hang[g];
-    std::vector<int32_t> group;
-    const int ng = hp_probe_groups(sp, freen, group, dbc != 0);
-    std::vector<int32_t> hrow(sp.n_nodes, -1);
-    for (size_t i = 0; i < sp.hang_node.size(); ++i) hrow[sp.hang_node[i]] = (int32_t)i;
-    for (int c = 0; c < nc; ++c) {
-      std::vector<int32_t> ms;
-      for (int64_t j = sp.cell_ptr[c]; j < sp.cell_ptr[c + 1]; ++j) {
-        const int32_t g = sp.cell_nodes[j];
-        if (freen[g]) ms.push_back(g);
-        else if (hrow[g] >= 0 && !(dbc && sp.boundary[g]))
-          for (int32_t q = sp.hang_ptr[hrow[g]]; q < sp.hang_ptr[hrow[g] + 1]; ++q)
-            if (freen[sp.hang_master[q]]) ms.push_back(sp.hang_master[q]);
-      }
-      std::sort(ms.begin(), ms.end());
-      ms.erase(std::unique(ms.begin(), ms.end()), ms.end());
-      for (size_t a = 0; a < ms.size(); ++a)
-        for (size_t b = a + 1; b < ms.size(); ++b)
-          if (group[ms[a]] == group[ms[b]]) { std::printf("FAIL probing\n"); return 0; }
-    }
-    for (int64_t g = 0; g < sp.n_nodes; ++g)
-      if ((group[g] >= 0) != (bool)freen[g] || group[g] >= ng) { std::printf("FAIL probing\n"); return 0; }
   }
   std::printf("HANG %zu\n", sp.hang_node.size());
   for (size_t i = 0; i < sp.hang_node.size(); ++i) {
