@@ -769,7 +769,9 @@ op_kernel(const OpArgs<T, K + 1, K + 1, (OP == OP_STOKES ? K : K + 1)> args) {
       if (!DIAG && FQ != 2) {
 #pragma unroll
         for (int c = 0; c < N; ++c) {
-          const bool rd = own && valid;  // dst holds the partial sums of earlier colours
+          // dst holds the partial sums of earlier colours; with the L2 reduction scatter only the
+          // nodes this colour completes need them (the fused epilogue adds them in registers)
+          const bool rd = own && valid && (!(kScatterRed && sizeof(T) == 4) || ((epi_last >> c) & 1u));
           if constexpr (sizeof(T) == 4) {
             const float4 w = rd ? *reinterpret_cast<const float4*>(dstp + node[c] * 4) : make_float4(0, 0, 0, 0);
             d0[0][c] = w.x; d0[1][c] = w.y; d0[2][c] = w.z; d0[3][c] = w.w;
