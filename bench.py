@@ -94,6 +94,17 @@ class Clocks:
         except FileNotFoundError:
             self.p = None
 
+    def wait_ready(self, timeout_s=5.0):
+        """Return once the sampler has written its first sample (at most timeout_s): nvidia-smi
+        takes a moment to start, longer than the short timed regions that follow."""
+        if self.p is None:
+            return
+        t0 = time.time()
+        while time.time() - t0 < timeout_s and self.p.poll() is None:
+            if os.path.getsize(self.f.name) > 0:
+                return
+            time.sleep(0.02)
+
     def stop(self):
         if self.p is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
@@ -848,6 +859,7 @@ def run_ours(args, world, rank, local):
     # clocks sampled over the headline, the per-launch pass and the end-to-end passes (the headline
     # alone lasts a few milliseconds, shorter than the sampling period)
     clocks = Clocks(local)
+    clocks.wait_ready()
     ms32 = timed(lambda: prob.vmult(src32, dst32), args.steps, args.warmup, nvtx="timed_vmult_fp32")
     # ---- the cell kernel's colour launches one by one, each bracketed by CUDA events on the
     # launching stream (the events serialise the launches): the per-launch roofline figure
