@@ -14,6 +14,7 @@ Multi-GPU (torchrun): every rank runs an independent replica (no collective on
 the data path); value = DoFs processed by all ranks / max time over ranks.
 """
 import argparse
+import datetime
 import hashlib
 import json
 import os
@@ -80,11 +81,15 @@ def dist_setup(gpus):
 
 
 class Clocks:
-    """nvidia-smi sampler during the timed region."""
+    """nvidia-smi sampler during the timed region: rows stamped before mark() (the sampler's start-up,
+    an idle GPU) are left out of the figures."""
+
+    TS_FMT = "%Y/%m/%d %H:%M:%S.%f"
 
     def __init__(self, device):
         self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
-        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+        self.t_mark = None
+        q = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
         try:
@@ -105,6 +110,10 @@ class Clocks:
                 return
             time.sleep(0.02)
 
+    def mark(self):
+        """Start of the timed region: earlier rows are not counted."""
+        self.t_mark = datetime.datetime.now()
+
     def stop(self):
         if self.p is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
@@ -115,14 +124,20 @@ class Clocks:
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for line in self.f.read().strip().splitlines():
             parts = [p.strip() for p in line.split(",")]
-            if len(parts) < 9:
+            if len(parts) < 10:
                 continue
+            if self.t_mark is not None:
+                try:
+                    if datetime.datetime.strptime(parts[0], self.TS_FMT) < self.t_mark:
+                        continue
+                except ValueError:
+                    pass  # an unexpected stamp format: the row counts
             try:
-                sm.append(float(parts[1]))
-                mx.append(float(parts[2]))
+                sm.append(float(parts[2]))
+                mx.append(float(parts[3]))
             except ValueError:
                 continue
-            for nm, v in zip(names, parts[5:9]):
+            for nm, v in zip(names, parts[6:10]):
                 if v.lower() == "active":
                     reasons.add(nm)
         os.unlink(self.f.name)
@@ -860,6 +875,7 @@ def run_ours(args, world, rank, local):
     # alone lasts a few milliseconds, shorter than the sampling period)
     clocks = Clocks(local)
     clocks.wait_ready()
+    clocks.mark()
     ms32 = timed(lambda: prob.vmult(src32, dst32), args.steps, args.warmup, nvtx="timed_vmult_fp32")
     # ---- the cell kernel's colour launches one by one, each bracketed by CUDA events on the
     # launching stream (the events serialise the launches): the per-launch roofline figure

@@ -1,6 +1,7 @@
 """bench.py's clock sampler against a stand-in for nvidia-smi (a shell loop that prints the query's
-CSV rows): the sampler is running before the timed region starts, the median SM clock, the maximum
-and the active throttle reasons come from the rows it printed."""
+CSV rows with a time stamp): the sampler is running before the timed region starts, rows stamped
+before the region are left out, and the median SM clock, the maximum and the active throttle
+reasons come from the rest."""
 import os
 import sys
 import time
@@ -10,38 +11,57 @@ sys.path.insert(0, ROOT)
 
 import bench  # noqa: E402
 
+STAMP = "$(date '+%Y/%m/%d %H:%M:%S.%3N')"
 
-def _fake_smi(tmp_path, rows):
-    body = "".join(f"echo '{r}'; sleep 0.05; " for r in rows)
+
+def _fake_smi(tmp_path, monkeypatch, clock_file, tail):
+    """nvidia-smi stand-in: every 50 ms one row whose SM clock is read from clock_file."""
     fake = tmp_path / "nvidia-smi"
-    fake.write_text(f"#!/bin/sh\nwhile true; do {body}done\n")
+    fake.write_text("#!/bin/sh\nwhile true; do "
+                    f"echo \"{STAMP}, 0, $(cat {clock_file}), 2070, 900.0, {tail}\"; sleep 0.05; done\n")
     fake.chmod(0o755)
-    return fake
-
-
-def test_sampler_is_live_before_the_timed_region(tmp_path, monkeypatch):
-    _fake_smi(tmp_path, ["0, 1965, 2070, 900.5, 0x4, Not Active, Not Active, Not Active, Active",
-                         "0, 2070, 2070, 950.0, 0x0, Not Active, Not Active, Not Active, Not Active",
-                         "0, 1980, 2070, 910.0, 0x4, Not Active, Not Active, Not Active, Active"])
     monkeypatch.setenv("PATH", f"{tmp_path}{os.pathsep}{os.environ['PATH']}")
+
+
+def test_rows_before_the_timed_region_are_left_out(tmp_path, monkeypatch):
+    clk = tmp_path / "clk"
+    clk.write_text("810")                                      # idle GPU while the sampler starts
+    _fake_smi(tmp_path, monkeypatch, clk, "0x4, Not Active, Not Active, Not Active, Active")
     c = bench.Clocks(0)
     c.wait_ready()
-    assert os.path.getsize(c.f.name) > 0       # a sample exists when timing would start
+    assert os.path.getsize(c.f.name) > 0                       # sampling when the region starts
+    time.sleep(0.3)
+    clk.write_text("2055")
+    time.sleep(0.06)
+    c.mark()
     time.sleep(0.4)
     r = c.stop()
     assert r["samples"] >= 3
-    assert r["sm_mhz"] in (1965.0, 1980.0, 2070.0) and r["sm_max_mhz"] == 2070.0
+    assert r["sm_mhz"] == 2055.0 and r["sm_max_mhz"] == 2070.0
     assert r["reasons"] == ["sw_power_cap"]
 
 
 def test_sampler_reports_a_thermal_slowdown(tmp_path, monkeypatch):
-    _fake_smi(tmp_path, ["0, 1500, 2070, 1390.0, 0x40, Not Active, Active, Not Active, Not Active"])
-    monkeypatch.setenv("PATH", f"{tmp_path}{os.pathsep}{os.environ['PATH']}")
+    clk = tmp_path / "clk"
+    clk.write_text("1500")
+    _fake_smi(tmp_path, monkeypatch, clk, "0x40, Not Active, Active, Not Active, Not Active")
+    c = bench.Clocks(0)
+    c.wait_ready()
+    c.mark()
+    time.sleep(0.3)
+    r = c.stop()
+    assert r["sm_mhz"] == 1500.0 and r["reasons"] == ["hw_thermal_slowdown"]
+
+
+def test_unmarked_sampler_counts_every_row(tmp_path, monkeypatch):
+    clk = tmp_path / "clk"
+    clk.write_text("1980")
+    _fake_smi(tmp_path, monkeypatch, clk, "0x0, Not Active, Not Active, Not Active, Not Active")
     c = bench.Clocks(0)
     c.wait_ready()
     time.sleep(0.2)
     r = c.stop()
-    assert r["sm_mhz"] == 1500.0 and r["reasons"] == ["hw_thermal_slowdown"]
+    assert r["samples"] >= 2 and r["sm_mhz"] == 1980.0 and r["reasons"] == []
 
 
 def test_wait_is_bounded_when_nothing_is_printed(tmp_path, monkeypatch):
