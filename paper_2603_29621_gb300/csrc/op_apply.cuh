@@ -799,7 +799,7 @@ op_kernel(const OpArgs<T, K + 1, K + 1, (OP == OP_STOKES ? K : K + 1)> args) {
         }
       }
     } else if (valid) {
-      // ---- scatter (plain read-modify-write: no other cell of this colour touches these DoFs)
+      // ---- scatter (no other cell of this colour touches these DoFs: reductions or read-modify-write)
       if (own) {
 #pragma unroll
         for (int c = 0; c < N; ++c) {

@@ -8,14 +8,14 @@
 // Thread mapping: a "team" of Q^(dim-1) lanes works on one cell, Q = k_u + 1
 // Gauss points per direction.  Lane (i, j) owns the column of points
 // (i, j, 0..Q-1) (3D) or (i, 0..Q-1) (2D) in registers; contractions along
-// x and y go through the team's shared-memory buffers, contractions along the
-// last direction stay in registers.  A warp holds floor(32 / team) teams and
-// synchronises with __syncwarp only.  Gradients use the collocation derivative
-// at the Gauss points (exact for the degree-k interpolant since Q = k + 1).
+// x and y go through the team's shared-memory buffers (x by warp shuffles in
+// the stabilised kernel), along the last direction they stay in registers.  A
+// warp holds floor(32 / team) teams and synchronises with __syncwarp only.
+// Gradients use the collocation derivative at the Gauss points (exact, Q = k+1).
 //
-// Scatter: cells of one colour share no DoF, so every lane adds into dst with
-// a plain read-modify-write; colours run one launch after the other, which
-// fixes the summation order (deterministic, no atomics).
+// Scatter: cells of one colour share no DoF, so each lane's addition into dst
+// (an L2 reduction, or a read-modify-write) meets no other; colours run one
+// launch after the other, which fixes the summation order (deterministic).
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
