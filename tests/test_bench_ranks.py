@@ -39,7 +39,10 @@ def test_timings_reduce_to_the_slowest_rank(tmp_path):
         r, w = dist.get_rank(), dist.get_world_size()
         got = bench.max_over_ranks([1.0 + r, 5.0 - r, 2.5], w, "cpu")
         dist.barrier()
-        print("RANK", r, json.dumps({{"vals": got, "rate": bench.whole_job_rate(1000, w, got[0])}}), flush=True)
+        out = json.dumps({{"vals": got, "rate": bench.whole_job_rate(1000, w, got[0])}})
+        # one write per line (shorter than PIPE_BUF): the two ranks share the pipe
+        sys.stdout.write("RANK %d %s\\n" % (r, out))
+        sys.stdout.flush()
         dist.destroy_process_group()
     """))
     p = _torchrun([str(script)])
